@@ -1,0 +1,111 @@
+"""Seeded synthetic workloads for the SRM3 stochastic-wave hot path.
+
+This module only states inputs: lattice and output sizes, spectrum
+parameters, the bispectrum target, seeds and precision.  It holds none of the
+method's arithmetic, so both the CUDA path and the FP64 oracle take their
+inputs from here.  The random phases of the method are not drawn here: each
+side derives them from the per-sample seeds with its own Philox4x32-10.
+
+Spectral model of the workloads (Sec. 5): Kaimal S(omega) with
+z0 = 0.03 m and von Karman k = 0.4, times the normalised Lorentzian
+wavenumber density a/(pi (a^2 + kappa^2)), a = 7 omega / (2 pi U); bispectrum
+|B| = eps g(i,j) sqrt(S_i S_j S_{i+j}) with a Gaussian envelope of width
+0.25 of the lattice extent per axis, biphase 0, and eps set so that
+max_k sum b_p^2 = target.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n_kappa: int
+    n_omega: int
+    kappa_u: float
+    omega_u: float
+    U: float
+    z: float
+    n_x: int
+    n_t: int
+    seeds: tuple
+    precision: str = "fp32"          # "fp32" or "fp64"
+    storage: str = "auto"            # "auto", "table" or "recompute"
+    target: float = 0.5              # max_k sum b_p^2
+    sigma_g: float = 0.25
+    beta: float = 0.0
+    z0: float = 0.03
+    k_vk: float = 0.4
+    lam: float = 7.0
+
+    @property
+    def n_samples(self) -> int:
+        return len(self.seeds)
+
+    def with_seeds(self, seeds) -> "Workload":
+        return replace(self, seeds=tuple(int(s) for s in seeds))
+
+    def pairs(self) -> int:
+        """Unordered pairs sum_k |Pi(k)| of the quadrant lattice."""
+        kk = np.arange(self.n_kappa, dtype=np.int64)[:, None]
+        kw = np.arange(self.n_omega, dtype=np.int64)[None, :]
+        n = (kk + 1) * (kw + 1) - 2
+        cnt = (n + 1) // 2
+        cnt[0, 0] = 0
+        return int(cnt.sum())
+
+    def pair_terms_per_sample(self) -> int:
+        """One pair-term = one W_ij y_i y_j product for one sheet of one sample."""
+        return 2 * self.pairs()
+
+
+# Tiny plain-method case: 32 x 32 lattice, FP64, one sample, 64 x 64 field.
+TINY = Workload("tiny_32x32_fp64", 32, 32, 0.5, 4 * math.pi, 30.0, 20.0, 64, 64,
+                (1,), precision="fp64", storage="recompute")
+
+# Bridge-span wave: 256 x 512 lattice, stored W table, 64 samples, FP32.
+BRIDGE = Workload("bridge_256x512_table_fp32", 256, 512, 0.25, 4 * math.pi, 40.0,
+                  20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
+                  storage="table")
+
+# Large grid with W recomputed on the fly: 512 x 1024 lattice, 16 samples.
+LARGE = Workload("large_512x1024_recompute_fp32", 512, 1024, 0.25, 4 * math.pi,
+                 40.0, 20.0, 1024, 2048, tuple(range(1, 17)), precision="fp32",
+                 storage="recompute")
+
+CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "large": LARGE}
+
+
+def uneven_batch(n_spectra: int = 200, seed: int = 4):
+    """Uneven batch: spectra with power-of-two grids between 32 and 256 per
+    axis, U in [20, 50] m/s, z in [10, 60] m, target in [0.1, 0.7] and 1..32
+    samples each (numpy PCG64 with the given seed).  Cutoffs as TINY.
+    Sample seeds are 1000 * spectrum_id + j."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.array([32, 64, 128, 256])
+    out = []
+    for s in range(n_spectra):
+        nk = int(rng.choice(sizes))
+        nw = int(rng.choice(sizes))
+        U = float(rng.uniform(20.0, 50.0))
+        z = float(rng.uniform(10.0, 60.0))
+        tgt = float(rng.uniform(0.1, 0.7))
+        ns = int(rng.integers(1, 33))
+        out.append(Workload(f"uneven_{s}", nk, nw, 0.5, 4 * math.pi, U, z, 2 * nk,
+                            2 * nw, tuple(1000 * s + j for j in range(ns)),
+                            precision="fp32", storage="auto", target=tgt))
+    return out
+
+
+def small_case(nk=24, nw=37, nx=64, nt=128, seeds=(1, 2, 3), precision="fp32",
+               storage="recompute", U=30.0, z=20.0, target=0.5, sigma_g=0.25,
+               kappa_u=0.5, omega_u=4 * math.pi, beta=0.0) -> Workload:
+    """A lattice small enough for the oracle in seconds, ragged against the
+    kernels' tiles (neither axis a multiple of 8 by default)."""
+    return Workload(f"small_{nk}x{nw}", nk, nw, kappa_u, omega_u, U, z, nx, nt,
+                    tuple(seeds), precision=precision, storage=storage,
+                    target=target, sigma_g=sigma_g, beta=beta)
