@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the SRM3 stochastic-wave sampler on the bridge-span workload.
+
+One step is one pass of the whole hot path over one batch: build the plan
+(discretise the Kaimal-Lorentzian spectrum on the 256 x 512 lattice, the
+FP64 pure-spectrum recursion with the eps root search, the stored FP32 W
+table), then draw 64 samples (Philox phases, the pair sum, the 2-D inverse
+FFT to 512 x 1024 fields).  The metric is pair-terms/s (one pair-term = one
+W_ij y_i y_j product for one sheet of one sample) with samples/s beside it.
+
+Ranks shard samples (each rank runs its own plan and its own seeds, no
+collective on the data path): weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl srm3|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 latency"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
+    ap.add_argument("--config", default="bridge", choices=["bridge", "large", "tiny"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# oracle on the host cores (CPU baseline / reference arm)
+
+def oracle_baseline(wl, rows=48, seed=1, passes=None):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it
+    to one full step.  The sample is the first ``rows`` lattice rows (kk <
+    rows, all omega): one recursion pass (single-threaded, lexicographic),
+    one sample's coefficients (OpenMP over k) and the direct DFT of those rows.
+    Recursion and coefficient time scale with the pair count, the DFT with
+    the row count; the step is (eps-search passes) recursions plus
+    n_samples coefficient sets and DFTs."""
+    import oracle
+    oracle.build()
+    dk = wl.kappa_u / wl.n_kappa
+    sub = rows
+    S = oracle.kaimal_lorentzian(sub, wl.n_omega, sub * dk, wl.omega_u, wl.U, wl.z, wl.z0,
+                                 wl.k_vk, wl.lam)
+    env = oracle.Envelope("gauss", wl.sigma_g * wl.n_kappa / sub)  # same width per index
+    eps = 1e-3
+    t0 = time.perf_counter()
+    Sp, _ = oracle.recursion(S, sub * dk, wl.omega_u, eps, env)
+    t_rec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    C = oracle.coeffs(S, Sp, sub * dk, wl.omega_u, eps, seed, env)
+    t_coef = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.field_dft(C, wl.n_x, wl.n_t)
+    t_dft = time.perf_counter() - t0
+    from paper_2310_03979_gb300.workloads import Workload
+    sub_pairs = Workload("sub", sub, wl.n_omega, 1.0, 1.0, 1.0, 2.0, 2, 2, ()).pairs()
+    full_pairs = wl.pairs()
+    if passes is None:
+        passes = 48  # plain bisection to 1e-13 from the [0, 2^m] bracket
+    n = wl.n_samples
+    t_step = (passes * full_pairs * (t_rec / sub_pairs)
+              + n * full_pairs * (t_coef / sub_pairs)
+              + n * (wl.n_kappa / sub) * t_dft)
+    terms = 2 * full_pairs * n
+    return {
+        "value": terms / t_step, "unit": "pair-terms/s", "cores": oracle.num_threads(),
+        "kind": "oracle", "step_s": t_step, "samples_per_s": n / t_step,
+        "sample": (f"first {sub} of {wl.n_kappa} lattice rows, all {wl.n_omega} omega: one "
+                   f"FP64 recursion pass ({t_rec:.2f} s, 1 thread), one sample's coefficients "
+                   f"({t_coef:.2f} s) and DFT ({t_dft:.2f} s); scaled by pair count to "
+                   f"{passes} eps-search passes + {n} samples of the full lattice"),
+    }
+
+
+# --------------------------------------------------------------------------
+
+def main():
+    args = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2310_03979_gb300 import workloads as Wl
+    wl = Wl.CONFIGS[args.config]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        vals = []
+        for i in range(args.warmup + args.steps):
+            r = oracle_baseline(wl, rows=32)
+            if i >= args.warmup:
+                vals.append(r)
+        v = statistics.median([x["value"] for x in vals])
+        r = vals[-1]
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pair-terms/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * statistics.median([x["step_s"] for x in vals]),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": wl.name, "n_kappa": wl.n_kappa, "n_omega": wl.n_omega,
+                           "samples_per_step": wl.n_samples},
+                "samples_per_s": statistics.median([x["samples_per_s"] for x in vals]),
+                "cpu_baseline": {"value": v, "unit": "pair-terms/s", "cores": r["cores"],
+                                 "kind": "oracle", "sample": r["sample"]},
+                "e2e": {"value": v, "unit": "pair-terms/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import numpy as np
+    import torch
+    from paper_2310_03979_gb300 import srm3
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    n = wl.n_samples
+    seeds = [1 + rank * n + j for j in range(n)]
+    es = 4 if wl.precision == "fp32" else 8
+    dt = torch.float32 if es == 4 else torch.float64
+    out = torch.empty((n, wl.n_x, wl.n_t), dtype=dt, device="cuda")
+    pairs = wl.pairs()
+    terms_per_step = 2 * pairs * n
+
+    def one_step(host_out=None):
+        plan = srm3.Plan.create(wl, stream=sptr)
+        srm3.enable_timing(plan.handle, True)
+        if host_out is None:
+            srm3.sample(plan.handle, seeds, n, out.data_ptr())
+        else:
+            srm3.sample_host(plan.handle, seeds, n, host_out.data_ptr())
+        t = srm3.get_timings(plan.handle)
+        info = plan.info()
+        plan.destroy()
+        return t, info
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    gpu_index = local
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = cvd.split(",")
+        if local < len(ids) and ids[local].strip().isdigit():
+            gpu_index = int(ids[local])
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    recs = []
+    for _ in range(args.steps):
+        recs.append(one_step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = terms_per_step * world / (ms_per_step * 1e-3)
+
+    # dominant kernel: the pair sum, timed with events on the plan's stream
+    ps_ms = sum(r[0].pairsum_ms for r in recs)
+    ps_launch = sum(r[0].pairsum_launches for r in recs)
+    ps_terms = sum(r[0].pair_terms for r in recs)
+    avg_launch_ms = ps_ms / max(ps_launch, 1)
+    flops_per_launch = 10.0 * ps_terms / max(ps_launch, 1)  # 10 flops per pair-term
+    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12
+    info = recs[-1][1]
+    t_last = recs[-1][0]
+    chunks = math.ceil(n / 128)
+    launches_per_step = (3 + 2 + info.root_passes * (wl.n_kappa + wl.n_omega) + 4
+                         + (1 if info.storage == 1 else 0) + 4 * chunks)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-terms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if es == 4 else "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_kappa": wl.n_kappa, "n_omega": wl.n_omega,
+                   "n_x": wl.n_x, "n_t": wl.n_t, "samples_per_step": n * world,
+                   "storage": "table" if info.storage == 1 else "recompute",
+                   "precision": wl.precision, "l2": "inputs larger than L2 (W table "
+                   f"{info.table_bytes / 1e9:.1f} GB, y {n * 2 * 8 * wl.n_kappa * (wl.n_omega + 32) / 1e6:.0f} MB)",
+                   "step": "plan build (spectrum, FP64 recursion + eps search, W table) + "
+                           f"{n}-sample batch"},
+        "samples_per_s": n * world / (ms_per_step * 1e-3),
+        "wall_ms_per_step": wall * 1e3 / args.steps,
+        "stages_ms_last_step": {"plan_total": info.plan_ms, "recursion": t_last.recursion_ms,
+                                "recursion_passes": t_last.recursion_passes,
+                                "table": t_last.table_ms, "phases": t_last.phases_ms,
+                                "pairsum": t_last.pairsum_ms,
+                                "transform": t_last.transform_ms},
+        "sampling_only_pair_terms_per_s": terms_per_step / (
+            (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "k_pairsum_f32<table>" if info.storage == 1 else
+                               "k_pairsum_f32<recompute>",
+                     "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 "
+                                    f"flop x {sm_max:.0f} MHz (max SM clock of "
+                                    "MEASURED_PEAKS.json); 10 flop per pair-term"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "eps": info.eps, "max_sum_b2": info.max_sum_b2,
+    }
+
+    if not args.no_e2e:
+        host = torch.empty((n, wl.n_x, wl.n_t), dtype=dt).pin_memory()
+        one_step(host)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_step(host)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        line["e2e"] = {"value": terms_per_step * world / e2e_s, "unit": "pair-terms/s",
+                       "h2d_bytes_per_step": 8 * n,
+                       "d2h_bytes_per_step": n * wl.n_x * wl.n_t * es,
+                       "ms_per_step": e2e_s * 1e3}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_baseline(wl)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

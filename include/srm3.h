@@ -1,0 +1,205 @@
+/*
+ * srm3.h - C ABI of the GB300 (sm_103a) sampler for third-order stochastic
+ * waves u(x,t) by the bispectral Spectral Representation Method (SRM3) of
+ * Vandanapu & Shields, arXiv 2310.03979.
+ *
+ * Model (Sec. 4.1-4.3 of the paper, with the readings stated below):
+ *   lattice  k = (kk, kw), 0 <= kk < n_kappa, 0 <= kw < n_omega,
+ *            kappa = kk*dk, omega = kw*dw, dk = kappa_u/n_kappa,
+ *            dw = omega_u/n_omega (Sec. 4.1);
+ *   sheets   s = + and s = -, one quadrant lattice each with independent
+ *            phases (Eq. quadrant_1d_wave); pairs Pi(k) = unordered {i, j},
+ *            i + j = k, i != 0, j != 0 (sum interactions within a sheet);
+ *   pure     S_p(k) = S(k) (1 - sum_{Pi(k)} b_p^2)       (Eq. pure, b_p squared)
+ *   bicoh.   b_p^2 = |B|^2 dk dw / (S_p(i) S_p(j) S(k))  (Sec. 4.1)
+ *   field    u(x,t) = Re sum_s sum_k C^s_k e^{i(kappa x + s omega t)},
+ *            C^s_k = 2 sqrt(dk dw) [sqrt(S_p) e^{i phi^s_k}
+ *                    + sqrt(S) sum_{Pi(k)} b_p e^{i(phi^s_i + phi^s_j + beta)}]
+ *            on x = mx dx, t = mt dt with dk dx = 2pi/n_x, dw dt = 2pi/n_t
+ *            (FFT form and grid relations, Sec. 4.3).
+ *   phases   phi^s_k = 2 pi (w + 1/2) 2^-32, w = word (e & 3) of
+ *            Philox4x32-10 at counter (e >> 2, 0, 0, 0) (low word first) and
+ *            key (seed lo, seed hi), e = (s n_kappa + kk) n_omega + kw,
+ *            s = 0 for the + sheet and 1 for the - sheet.
+ *
+ * Errors: every int-returning call returns SRM3_OK (0) or a negative
+ * SRM3_ERR_* code; srm3_last_error() returns a message for the calling
+ * thread's last failure.  Calls that take a plan never free or replace a
+ * caller buffer.  All device pointers are CUDA device addresses in the
+ * current device's context; all host pointers are ordinary host memory.
+ */
+#ifndef SRM3_H
+#define SRM3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRM3_OK 0
+#define SRM3_ERR_INVALID_ARG (-1)      /* a NULL pointer, a size out of range */
+#define SRM3_ERR_GRID_CONSTRAINT (-2)  /* n_x, n_t not powers of two >= the lattice */
+#define SRM3_ERR_NONPOSITIVE_PURE (-3) /* sum b_p^2 >= 1 somewhere: S_p <= 0 */
+#define SRM3_ERR_BISECTION_FAILED (-4) /* no eps reaches the target */
+#define SRM3_ERR_OUT_OF_MEMORY (-5)
+#define SRM3_ERR_CUDA (-6)             /* a CUDA runtime error; see srm3_last_error */
+#define SRM3_ERR_TIMEOUT (-7)
+#define SRM3_ERR_NOT_SUPPORTED (-8)
+
+/* Power spectrum S(kappa, omega) on the lattice (Sec. 5). */
+enum srm3_spectrum_kind {
+    /* Kaimal S(omega) (Eq. kaimal_spectrum) with u* = k_vk U / ln(z/z0),
+     * times a/(pi (a^2 + kappa^2)), a = lam omega / (2 pi U); S := 0 on the
+     * omega = 0 column. */
+    SRM3_SPECTRUM_KAIMAL_LORENTZIAN = 0,
+    /* Caller table, host, row-major [n_kappa][n_omega], copied at create. */
+    SRM3_SPECTRUM_TABLE = 1
+};
+
+typedef struct srm3_spectrum {
+    int32_t kind;
+    int32_t reserved;
+    double U, z, z0, k_vk, lam; /* KAIMAL_LORENTZIAN parameters */
+    const double *table;        /* TABLE: host, n_kappa*n_omega doubles, >= 0 */
+} srm3_spectrum;
+
+/* Bispectrum |B(i,j)| = eps g(i,j) sqrt(S(i) S(j) S(i+j)) with constant
+ * biphase beta, g(i,j) = exp(-1/2 ((ik-jk)/(sigma_g n_kappa))^2)
+ *                      * exp(-1/2 ((iw-jw)/(sigma_g n_omega))^2). */
+enum srm3_bispectrum_kind { SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0 };
+
+typedef struct srm3_bispectrum {
+    int32_t kind;
+    int32_t reserved;
+    double target_max_sum_b2; /* in (0,1): eps found so that max_k sum b_p^2
+                                 equals it to 1e-13; 0: use eps as given */
+    double eps;               /* used when target_max_sum_b2 == 0; >= 0 */
+    double sigma_g;           /* > 0 */
+    double beta;              /* biphase, radians */
+} srm3_bispectrum;
+
+enum srm3_precision {
+    SRM3_FP32 = 0, /* tiled FP32 pair sum with compensated merge, FP32 FFT */
+    SRM3_FP64 = 1  /* plain FP64 pair sum (one thread per k), FP64 FFT */
+};
+enum srm3_storage {
+    SRM3_STORAGE_AUTO = 0,     /* table if it fits the budget, else recompute */
+    SRM3_STORAGE_TABLE = 1,    /* W streamed from an HBM table (FP32 only) */
+    SRM3_STORAGE_RECOMPUTE = 2 /* W rebuilt from envelope factors in-kernel */
+};
+
+typedef struct srm3_grid {
+    int32_t n_kappa, n_omega; /* lattice, >= 1 each */
+    double kappa_u, omega_u;  /* cutoffs, > 0 */
+    int32_t n_x, n_t;         /* output grid: powers of two, n_x >= n_kappa,
+                                 n_t >= 2 n_omega - 1, each <= 8192 */
+    int32_t precision;        /* enum srm3_precision */
+    int32_t storage;          /* enum srm3_storage */
+    void *stream;             /* cudaStream_t for all plan work; NULL = default */
+    double table_budget_bytes;/* AUTO: largest W table allowed (0 = 64 GiB) */
+} srm3_grid;
+
+typedef struct srm3_plan srm3_plan;
+
+/* Build a plan: discretise S on the lattice, run the pure-spectrum recursion
+ * over the anti-diagonals of the lattice in FP64 (Eq. pure), find eps by a
+ * bracketing root search on max_k sum b_p^2 when a target is given, and,
+ * for STORAGE_TABLE, write the W table to HBM.  The plan owns all of its
+ * device memory.  Synchronous: returns when the plan is ready.  On error
+ * *out stays NULL.  Errors: INVALID_ARG, GRID_CONSTRAINT, NONPOSITIVE_PURE
+ * (an explicit eps drives some S_p <= 0), BISECTION_FAILED, OUT_OF_MEMORY,
+ * CUDA. */
+int srm3_plan_create(const srm3_spectrum *spectrum,
+                     const srm3_bispectrum *bispectrum, const srm3_grid *grid,
+                     srm3_plan **out);
+
+/* Draw n samples: Philox phases per seed, the coefficients C^s_k by the
+ * pair sum (FFT form, Sec. 4.3), then the 2-D inverse transform to
+ * u[n][n_x][n_t].  seeds: host array of n seeds.  out: device buffer of
+ * n*n_x*n_t floats (FP32 plan) or doubles (FP64 plan), row-major
+ * [sample][mx][mt].  Asynchronous on the plan's stream; launch errors
+ * return at once, execution errors surface at srm3_sync.  The same
+ * (plan, seed) gives bit-identical output whatever n or the other seeds.
+ * n == 0 is a no-op.  Not thread-safe per plan (workspace is shared). */
+int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *out);
+
+/* As srm3_sample with a HOST output buffer: copies the seeds in and the
+ * field out (n*n_x*n_t elements) inside the call; returns after the copy. */
+int srm3_sample_host(srm3_plan *plan, const uint64_t *seeds, int n, void *out_host);
+
+/* Free the plan and its device memory.  NULL is a no-op.  The caller must
+ * not have plan work in flight (call srm3_sync first). */
+void srm3_destroy(srm3_plan *plan);
+
+/* Wait for the plan's stream; returns the first asynchronous error. */
+int srm3_sync(srm3_plan *plan);
+
+/* Re-target the plan's stream (cudaStream_t). */
+int srm3_set_stream(srm3_plan *plan, void *stream);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *srm3_last_error(void);
+
+typedef struct srm3_info {
+    double eps;              /* bispectrum scale in use */
+    double max_sum_b2;       /* max_k sum_{Pi(k)} b_p^2 at eps */
+    double min_pure_ratio;   /* min over S>0 of S_p/S = 1 - sum b_p^2 */
+    double variance;         /* exact ensemble variance sum_s sum_k 2 S dk dw */
+    double table_bytes;      /* bytes of the W table (0 when recomputed) */
+    double plan_ms;          /* wall time of srm3_plan_create */
+    int64_t pairs;           /* sum_k |Pi(k)| */
+    int32_t root_passes;     /* recursion passes used by the eps search */
+    int32_t storage;         /* storage actually chosen */
+    int32_t precision;
+    int32_t tile_r;          /* outputs per thread along omega (FP32 path) */
+} srm3_info;
+
+int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
+
+/* Copy the plan's FP64 tables to host arrays of n_kappa*n_omega doubles
+ * (any may be NULL): S, q = S/S_p (1 where S = 0), sum_b2. */
+int srm3_plan_tables(const srm3_plan *plan, double *S, double *q, double *sum_b2);
+
+/* Philox phase words for n seeds: device buffer words[n][2][n_kappa][n_omega]
+ * (uint32), exactly the words behind the phases of srm3_sample.  Async. */
+int srm3_phase_words(srm3_plan *plan, const uint64_t *seeds, int n, uint32_t *words);
+
+/* Coefficients C^s_k for n seeds before the transform: device buffer
+ * C[n][2][n_kappa][n_omega] of interleaved (re, im) floats or doubles per
+ * the plan's precision.  Async. */
+int srm3_coeffs(srm3_plan *plan, const uint64_t *seeds, int n, void *C);
+
+/* The transform stage alone: u = Re sum_s sum_k C^s_k e^{i(...)} for n
+ * coefficient sets laid out as srm3_coeffs writes them (device), into a
+ * device buffer u[n][n_x][n_t].  Async. */
+int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
+
+/* Stage timings from CUDA events recorded on the plan's stream.  The
+ * recursion and W-table figures cover the last plan build (always
+ * recorded); the sampling stages accumulate over srm3_sample /
+ * srm3_sample_host / srm3_coeffs calls made while timing is enabled. */
+typedef struct srm3_timings {
+    double recursion_ms;   /* sum over all recursion passes of the build */
+    double table_ms;       /* W-table build */
+    double phases_ms;      /* Philox phase kernels */
+    double pairsum_ms;     /* pair-sum kernels (the dominant stage) */
+    double transform_ms;   /* both FFT stages */
+    int32_t recursion_passes;
+    int32_t pairsum_launches;
+    int64_t pair_terms;    /* pair-terms issued by the timed pair-sum launches */
+} srm3_timings;
+
+/* on != 0: bracket every sampling-stage launch with CUDA events. */
+int srm3_enable_timing(srm3_plan *plan, int on);
+
+/* Wait for the plan's stream, then report the timings; reset != 0 clears
+ * the sampling-stage sums afterwards. */
+int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRM3_H */

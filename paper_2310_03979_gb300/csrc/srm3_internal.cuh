@@ -1,0 +1,130 @@
+// srm3_internal.cuh - plan object, error plumbing and shared device helpers of
+// the SRM3 sampler.  Not part of the public ABI (include/srm3.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "srm3.h"
+
+#define SRM3_API extern "C" __attribute__((visibility("default")))
+
+namespace srm3 {
+
+// Tile shape of the FP32 pair sum: R outputs along omega per thread, the
+// omega-index loop unrolled by U.  The y rows carry kPad zero entries on
+// both sides so that every window load of the tiled kernel stays in bounds.
+constexpr int kTileR = 8;
+constexpr int kTileU = 8;
+constexpr int kPad = 16;           // >= kTileR + kTileU - 2
+constexpr int kMaxChunk = 128;     // samples per internal launch chunk
+constexpr int kWarpsPerCta = 4;    // FP32 pair-sum CTA: 4 warps = 4 work units
+constexpr int kMaxFft = 8192;
+
+struct SeedChunk {
+  uint64_t s[kMaxChunk];
+};
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define SRM3_CUDA(call)                                 \
+  do {                                                  \
+    cudaError_t e__ = (call);                           \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+}  // namespace srm3
+
+struct srm3_plan {
+  // lattice and grid
+  int nk = 0, nw = 0, nx = 0, nt = 0;
+  int log2nx = 0, log2nt = 0;
+  double ku = 0, wu = 0, dk = 0, dw = 0, dkdw = 0;
+  int precision = SRM3_FP32;
+  int storage = SRM3_STORAGE_RECOMPUTE;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // model
+  double sigma_g = 0.25, beta = 0.0;
+  double eps = 0.0, max_sb2 = 0.0, min_pure = 1.0, variance = 0.0;
+  double plan_ms = 0.0, table_bytes = 0.0, table_budget = 0.0;
+  int root_passes = 0;
+  int64_t pairs = 0;
+
+  // FP64 plan tables [nk*nw]
+  double *S = nullptr;    // spectrum on the lattice
+  double *qm = nullptr;   // q = S/S_p where S > 0, else 0
+  double *sb2 = nullptr;  // sum_{Pi(k)} b_p^2
+  double *EkSq = nullptr; // squared envelope factor along kappa, |d| < nk
+  double *EwSq = nullptr; // squared envelope factor along omega, |d| < nw
+  double *scal = nullptr; // device scalars: [0] eps^2 dk dw, [1] max sb2,
+                          // [2] min (1 - sb2) over S > 0, [3] sum S
+  int *err = nullptr;     // device error word
+
+  // per-precision sampling tables (float or double by precision)
+  void *sqq = nullptr;    // sqrt(q) masked by S > 0, [nk*nw]
+  void *Pk = nullptr;     // pure factor 2 sqrt(dk dw S) (1 - sb2), [nk*nw]
+  void *ck = nullptr;     // pair factor 2 eps dk dw sqrt(S), [nk*nw]
+  void *Ek = nullptr;     // envelope factor along kappa, |d| < nk
+  void *Ews = nullptr;    // envelope factor along omega, signed d, offset ew_off
+  int ew_off = 0, ew_len = 0;
+  void *tw = nullptr;     // FFT twiddles e^{+2 pi i j / nfft}, j < nfft
+  int nfft = 0;
+
+  // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
+  int ntw = 0, ntiles = 0;
+  int2 *tile_order = nullptr;
+  long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
+  float *W = nullptr;             // W table (STORAGE_TABLE)
+
+  // sampling workspace
+  int ws_chunk = 0;
+  void *y = nullptr, *y0 = nullptr, *C = nullptr, *H = nullptr;
+  int rowstride = 0;
+
+  // stage timing (CUDA events on the plan stream)
+  bool timing = false;
+  struct EvRec {
+    int stage;  // 0 phases, 1 pairsum, 2 transform
+    cudaEvent_t a, b;
+    long long pair_terms;
+  };
+  std::vector<EvRec> ev_recs;
+  std::vector<cudaEvent_t> ev_pool;
+  double t_recursion_ms = 0.0, t_table_ms = 0.0;
+  double t_stage_ms[3] = {0.0, 0.0, 0.0};
+  int t_pairsum_launches = 0;
+  long long t_pair_terms = 0;
+
+  // recursion graph (one pass = every anti-diagonal level + reductions)
+  cudaGraphExec_t rec_exec = nullptr;
+  cudaGraph_t rec_graph = nullptr;
+  double *h_pinned = nullptr;  // pinned host scalars
+};
+
+namespace srm3 {
+// plan.cu
+int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs);
+void free_plan(srm3_plan *p);
+// sample.cu
+int ensure_workspace(srm3_plan *p, int chunk);
+int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out);
+int run_pairsum(srm3_plan *p, int n, void *C_out);
+int run_transform(srm3_plan *p, const void *C, int n, void *out);
+int prepare_sampling_tables(srm3_plan *p, cudaStream_t st);
+int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);
+int stage_end(srm3_plan *p, int rec);
+int collect_timings(srm3_plan *p);
+}  // namespace srm3
+
+static inline int ilog2_exact(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return ((1 << l) == v) ? l : -1;
+}

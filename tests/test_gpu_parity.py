@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 plans max|du| <= 1e-10 sigma_u, FP32 plans max|du| <=
+1e-4 sigma_u (sigma_u^2 = the exact ensemble variance); Philox words
+bit-exact; plan tables (FP64 in both precisions) to 1e-11 relative.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_03979_gb300 import srm3
+from paper_2310_03979_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_plan(wl, eps=None):
+    S = oracle.kaimal_lorentzian(wl.n_kappa, wl.n_omega, wl.kappa_u, wl.omega_u, wl.U, wl.z,
+                                 wl.z0, wl.k_vk, wl.lam)
+    env = oracle.Envelope("gauss", wl.sigma_g)
+    if eps is None:
+        return oracle.make_plan(S, wl.kappa_u, wl.omega_u, target=wl.target, env=env,
+                                beta=wl.beta)
+    return oracle.make_plan(S, wl.kappa_u, wl.omega_u, eps=eps, env=env, beta=wl.beta)
+
+
+def sigma_u(op):
+    return math.sqrt(op.moments()[0])
+
+
+def oracle_fields(op, wl, seeds):
+    return np.stack([op.field(s, wl.n_x, wl.n_t) for s in seeds])
+
+
+SMALL = W.small_case(nk=24, nw=37, nx=64, nt=128, seeds=(1, 2, 3, 77))
+
+
+def test_phase_words_bit_exact(oracle_lib):
+    wl = SMALL
+    seeds = [1, 2, 2 ** 40 + 5, 2 ** 64 - 1]
+    with srm3.Plan.create(wl) as p:
+        w = p.phase_words(seeds).cpu().numpy().view(np.uint32)
+    for i, s in enumerate(seeds):
+        ref, _ = oracle.phases(wl.n_kappa, wl.n_omega, s)
+        np.testing.assert_array_equal(w[i], ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plan_tables_and_eps(oracle_lib, precision):
+    wl = SMALL
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl, precision=precision) as p:
+        S, q, sb2 = p.tables()
+        info = p.info()
+    np.testing.assert_allclose(S, op.S, rtol=1e-13, atol=0)
+    assert info.eps == pytest.approx(op.eps, rel=1e-11)
+    assert abs(info.max_sum_b2 - wl.target) <= 1e-13
+    np.testing.assert_allclose(q, op.q, rtol=1e-11)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=1e-11, atol=1e-15)
+    assert info.variance == pytest.approx(op.moments()[0], rel=1e-12)
+    assert np.all(q >= 1.0) and info.min_pure_ratio > 0
+
+
+def test_recursion_at_fixed_eps(oracle_lib):
+    """Same eps on both sides: the anti-diagonal recursion equals the
+    lexicographic one to FP64 rounding."""
+    wl = W.small_case(nk=40, nw=33)
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl, eps=op.eps, precision="fp64") as p:
+        _, q, sb2 = p.tables()
+    np.testing.assert_allclose(q, op.q, rtol=2e-14)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
+
+
+def _cplx(C):
+    C = C.cpu().numpy()
+    return C[..., 0] + 1j * C[..., 1]
+
+
+@pytest.mark.parametrize("precision,storage", [("fp64", "recompute"), ("fp32", "recompute"),
+                                               ("fp32", "table")])
+def test_coefficients(oracle_lib, precision, storage):
+    wl = SMALL
+    op = oracle_plan(wl)
+    seeds = [3, 11]
+    with srm3.Plan.create(wl, precision=precision, storage=storage, eps=op.eps) as p:
+        C = _cplx(p.coeffs(seeds))
+        assert p.info().storage == {"recompute": 2, "table": 1}[storage]
+    tol = 1e-11 if precision == "fp64" else 2e-6
+    for i, s in enumerate(seeds):
+        ref = op.coeffs(s)
+        scale = np.abs(ref).max()
+        assert np.abs(C[i] - ref).max() <= tol * scale
+
+
+def test_field_tiny_fp64_end_to_end(oracle_lib):
+    """The 32 x 32 FP64 plain-method case: spectrum, eps search, phases,
+    pair sum and transform on the GPU vs the oracle's own bisection."""
+    wl = W.TINY
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl) as p:
+        u = p.sample(list(wl.seeds)).cpu().numpy()
+    ref = oracle_fields(op, wl, wl.seeds)
+    err = np.abs(u - ref).max() / sigma_u(op)
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("storage", ["recompute", "table"])
+def test_field_small_fp32_end_to_end(oracle_lib, storage):
+    wl = SMALL
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl, storage=storage) as p:
+        u = p.sample(list(wl.seeds)).cpu().numpy()
+    ref = oracle_fields(op, wl, wl.seeds)
+    err = np.abs(u - ref).max() / sigma_u(op)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("nk,nw,nx,nt", [(1, 9, 2, 32), (2, 3, 2, 8), (9, 1, 16, 2),
+                                         (17, 16, 32, 32), (8, 64, 8, 128)])
+def test_edge_lattices_fp64(oracle_lib, nk, nw, nx, nt):
+    """One-row and one-column lattices (N_kappa = 1 is the 1-D form),
+    minimal sizes, n_x = n_kappa and n_t = 2 n_omega - 1 rounded up."""
+    wl = W.small_case(nk=nk, nw=nw, nx=nx, nt=nt, seeds=(4, 5), precision="fp64")
+    S = oracle.kaimal_lorentzian(nk, nw, wl.kappa_u, wl.omega_u, wl.U, wl.z)
+    eps = 0.2
+    op = oracle.make_plan(S, wl.kappa_u, wl.omega_u, eps=eps, env=oracle.Envelope("gauss", 0.25))
+    with srm3.Plan.create(wl, eps=eps) as p:
+        u = p.sample(list(wl.seeds)).cpu().numpy()
+    ref = oracle_fields(op, wl, wl.seeds)
+    sig = max(sigma_u(op), 1e-300)
+    assert np.abs(u - ref).max() <= 1e-10 * sig + 1e-300
+
+
+def test_eps_zero_and_biphase(oracle_lib):
+    wl = W.small_case(nk=12, nw=10, nx=16, nt=32, seeds=(9,), beta=0.7, precision="fp64")
+    for eps in (0.0, 0.9):
+        S = oracle.kaimal_lorentzian(12, 10, wl.kappa_u, wl.omega_u, wl.U, wl.z)
+        op = oracle.make_plan(S, wl.kappa_u, wl.omega_u, eps=eps,
+                              env=oracle.Envelope("gauss", 0.25), beta=0.7)
+        with srm3.Plan.create(wl, eps=eps) as p:
+            u = p.sample([9]).cpu().numpy()[0]
+        ref = op.field(9, wl.n_x, wl.n_t)
+        assert np.abs(u - ref).max() <= 1e-10 * sigma_u(op)
+
+
+def test_spectrum_table_input(oracle_lib):
+    rng = np.random.default_rng(1)
+    wl = W.small_case(nk=10, nw=12, nx=16, nt=32, seeds=(2,), precision="fp64")
+    S = rng.uniform(0.0, 3.0, size=(10, 12))
+    S[0, 0] = 1.5          # a positive DC entry takes part in no pair
+    S[3, 4] = 0.0
+    op = oracle.make_plan(S, wl.kappa_u, wl.omega_u, target=0.4,
+                          env=oracle.Envelope("gauss", 0.25))
+    with srm3.Plan.create(wl, table=S, target=0.4) as p:
+        u = p.sample([2]).cpu().numpy()[0]
+        _, q, _ = p.tables()
+    np.testing.assert_allclose(q, op.q, rtol=1e-11)
+    ref = op.field(2, wl.n_x, wl.n_t)
+    assert np.abs(u - ref).max() <= 1e-10 * sigma_u(op)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_transform_alone(oracle_lib, precision):
+    rng = np.random.default_rng(3)
+    wl = W.small_case(nk=20, nw=24, nx=32, nt=64, precision=precision)
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    Cn = rng.normal(size=(3, 2, 20, 24)) + 1j * rng.normal(size=(3, 2, 20, 24))
+    C = torch.tensor(np.stack([Cn.real, Cn.imag], -1), dtype=dt, device="cuda")
+    with srm3.Plan.create(wl, eps=0.0) as p:
+        u = p.field_from_coeffs(C).cpu().numpy()
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    for i in range(3):
+        ref = oracle.field_dft(Cn[i], 32, 64)
+        assert np.abs(u[i] - ref).max() <= tol * np.abs(ref).max()
+        # cuFFT cross-check (library, not the oracle)
+        F = torch.zeros((32, 64), dtype=torch.complex128, device="cuda")
+        Ct = torch.tensor(Cn[i], device="cuda")
+        F[:20, :24] += Ct[0]
+        idx = (-torch.arange(24, device="cuda")) % 64
+        F[:20].index_add_(1, idx, Ct[1])
+        cu = (torch.fft.ifft2(F) * (32 * 64)).real.cpu().numpy()
+        assert np.abs(u[i] - cu).max() <= tol * np.abs(cu).max()
+
+
+def test_batch_composition_and_chunking(oracle_lib):
+    """A seed's field is bit-identical alone, inside a batch, and across the
+    internal 128-sample chunk boundary."""
+    wl = W.small_case(nk=16, nw=20, nx=16, nt=64)
+    with srm3.Plan.create(wl) as p:
+        alone = p.sample([5]).cpu().numpy()[0]
+        mix = p.sample(list(range(1, 10))).cpu().numpy()
+        big = p.sample(list(range(1000, 1131))).cpu().numpy()
+        tail = p.sample([1130]).cpu().numpy()[0]
+        head = p.sample([1000]).cpu().numpy()[0]
+        assert p.sample([]).numel() == 0
+    np.testing.assert_array_equal(mix[4], alone)
+    np.testing.assert_array_equal(big[130], tail)
+    np.testing.assert_array_equal(big[0], head)
+
+
+def test_nonpositive_pure_is_reported(oracle_lib):
+    wl = W.small_case(nk=12, nw=12)
+    with pytest.raises(srm3.SRM3Error) as ei:
+        srm3.Plan.create(wl, eps=50.0)
+    assert ei.value.code == -3
+
+
+def test_sample_host_matches_device(oracle_lib):
+    wl = W.small_case(nk=16, nw=20, nx=16, nt=64)
+    with srm3.Plan.create(wl) as p:
+        dev = p.sample([7, 8]).cpu().numpy()
+        host = torch.empty((2, 16, 64), dtype=torch.float32).pin_memory()
+        srm3.sample_host(p.handle, [7, 8], 2, host.data_ptr())
+    np.testing.assert_array_equal(host.numpy(), dev)
