@@ -150,10 +150,11 @@ typedef struct srm3_info {
     double table_bytes;      /* bytes of the W table (0 when recomputed) */
     double plan_ms;          /* wall time of srm3_plan_create */
     int64_t pairs;           /* sum_k |Pi(k)| */
-    int32_t root_passes;     /* recursion passes used by the eps search */
+    int32_t root_passes;     /* FP64 recursion passes of the build */
     int32_t storage;         /* storage actually chosen */
     int32_t precision;
     int32_t tile_r;          /* outputs per thread along omega (FP32 path) */
+    int32_t root_passes_fp32;/* FP32 recursion passes used to locate eps */
 } srm3_info;
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
@@ -189,6 +190,10 @@ typedef struct srm3_timings {
     int32_t recursion_passes;
     int32_t pairsum_launches;
     int64_t pair_terms;    /* pair-terms issued by the timed pair-sum launches */
+    double recursion_fp32_ms;  /* part of recursion_ms spent in FP32 search passes */
+    double recursion_fp64_ms;  /* part of recursion_ms spent in FP64 passes */
+    int32_t recursion_passes_fp32;
+    int32_t reserved;
 } srm3_timings;
 
 /* on != 0: bracket every sampling-stage launch with CUDA events. */

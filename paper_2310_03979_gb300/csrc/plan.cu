@@ -7,8 +7,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <numeric>
 
+#include "recursion.cuh"
 #include "srm3_internal.cuh"
 
 namespace srm3 {
@@ -51,104 +53,82 @@ __global__ void k_discretise_kaimal(int nk, int nw, double dk, double dw, double
   S[idx] = val;
 }
 
-// Squared envelope factors for the recursion: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|].
-__global__ void k_env_sq(int n, double sigma_n, double *out) {
+// Squared envelope factors for the recursion: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|]
+// (FP64, and an FP32 copy for the search passes).
+__global__ void k_env_sq(int n, double sigma_n, double *out, float *out32) {
   int d = blockIdx.x * blockDim.x + threadIdx.x;
   if (d >= n) return;
   double a = d / sigma_n;
   double e = exp(-0.5 * a * a);
   out[d] = e * e;
+  out32[d] = (float)(e * e);
+}
+
+// g^2 over (|ik - jk|, |iw - jw|) as one table, FP64 and FP32.
+__global__ void k_g2(int nk, int nw, const double *__restrict__ EkSq,
+                     const double *__restrict__ EwSq, double *G2, float *G2_32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk * nw) return;
+  const int dk = i / nw, dw = i - dk * nw;
+  const double v = EkSq[dk] * EwSq[dw];
+  G2[i] = v;
+  G2_32[i] = (float)v;
 }
 
 // ---------------------------------------------------------------------------
-// One anti-diagonal level d = kk + kw of the recursion.  Every part of a
-// pair of Pi(k) lies on a lower level, so all points of a level are
-// independent.  One CTA per point; warps take row pairs (a, kk - a),
-// a <= kk/2, lanes take omega indices; canonical half: the centre row
-// a = kk - a keeps iw <= kw/2; i = 0 is skipped.
-//   sum_b2(k) = eps^2 dk dw sum_{Pi(k)} g^2 qm_i qm_j,  q_k = 1/(1 - sum_b2)
-// (Eq. pure with b_p^2 = eps^2 g^2 dk dw q_i q_j for |B| = eps g sqrt(SSS)).
-// LINEAR: q == 1 everywhere (masked by S > 0), all points in one launch;
-// gives L_k = dk dw sum g^2, the small-eps slope used to bracket eps.
-template <bool LINEAR>
-__global__ void __launch_bounds__(256) k_rec_level(int nk, int nw, int d, int kk_lo,
-                                                   const double *__restrict__ S,
-                                                   double *__restrict__ qm,
-                                                   double *__restrict__ sb2,
-                                                   const double *__restrict__ EkSq,
-                                                   const double *__restrict__ EwSq,
-                                                   const double *__restrict__ scal,
-                                                   int *__restrict__ err) {
-  int kk, kw;
-  if (LINEAR) {
-    kk = blockIdx.x / nw;
-    kw = blockIdx.x - kk * nw;
-  } else {
-    kk = kk_lo + blockIdx.x;
-    kw = d - kk;
-  }
+// Linear pass: q == 1 everywhere (masked by S > 0), every point in one
+// launch, one CTA per point.  Gives L_k = dk dw sum_{Pi(k)} g^2, the
+// small-eps slope of sum_b2 used to bracket eps.
+__global__ void __launch_bounds__(256) k_rec_linear(int nk, int nw,
+                                                    const double *__restrict__ S,
+                                                    double *__restrict__ sb2,
+                                                    const double *__restrict__ EkSq,
+                                                    const double *__restrict__ EwSq,
+                                                    double dkdw) {
+  const int kk = blockIdx.x / nw, kw = blockIdx.x - kk * nw;
   const int k = kk * nw + kw;
   if (!(S[k] > 0.0)) {
-    if (threadIdx.x == 0) {
-      sb2[k] = 0.0;
-      if (!LINEAR) qm[k] = 0.0;
-    }
+    if (threadIdx.x == 0) sb2[k] = 0.0;
     return;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
   double acc = 0.0;
   const int nrow = kk / 2 + 1;
-  for (int a = warp; a < nrow; a += nwarps) {
+  for (int a = warp; a < nrow; a += 8) {
     const int b = kk - a;
     const int lim = (a == b) ? kw / 2 : kw;
-    const double *qa = qm + (size_t)a * nw;
-    const double *qb = qm + (size_t)b * nw;
     const double *Sa = S + (size_t)a * nw;
     const double *Sb = S + (size_t)b * nw;
     double racc = 0.0;
     for (int iw = lane; iw <= lim; iw += 32) {
       if (a == 0 && iw == 0) continue;
-      double prod;
-      if (LINEAR)
-        prod = (Sa[iw] > 0.0 && Sb[kw - iw] > 0.0) ? 1.0 : 0.0;
-      else
-        prod = qa[iw] * qb[kw - iw];
+      double prod = (Sa[iw] > 0.0 && Sb[kw - iw] > 0.0) ? 1.0 : 0.0;
       int dd = 2 * iw - kw;
       racc = fma(EwSq[dd < 0 ? -dd : dd], prod, racc);
     }
     acc = fma(EkSq[kk - 2 * a], racc, acc);
   }
-  // block reduction
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   __shared__ double red[8];
   if (lane == 0) red[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int w = 0; w < nwarps; ++w) t += red[w];
-    double s2 = scal[0] * t;
-    sb2[k] = s2;
-    if (!LINEAR) {
-      if (s2 < 1.0) {
-        qm[k] = 1.0 / (1.0 - s2);
-      } else {
-        qm[k] = 0.0;
-        atomicOr(err, 1);
-      }
-    }
+    for (int w = 0; w < 8; ++w) t += red[w];
+    sb2[k] = dkdw * t;
   }
 }
 
-// Reductions over the lattice: scal[1] = max sum_b2, scal[2] = min over
-// S > 0 of (1 - sum_b2), scal[3] = sum S.
-__global__ void k_reduce(int n, const double *__restrict__ S,
-                         const double *__restrict__ sb2, double *__restrict__ scal) {
+// Per-plane reductions (one CTA per plane): max sum_b2, min (1 - sum_b2)
+// over S > 0 and sum S into scal[8 + 4m + {1,2,3}].
+__global__ void k_reduce_planes(long long n, const double *__restrict__ S,
+                                const double *__restrict__ sb2, double *__restrict__ scal) {
+  const int m = blockIdx.x;
+  const double *v = sb2 + (size_t)m * n;
   double mx = 0.0, mn = 1.0, sum = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = sb2[i];
-    mx = fmax(mx, v);
-    if (S[i] > 0.0) mn = fmin(mn, 1.0 - v);
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    mx = fmax(mx, v[i]);
+    if (S[i] > 0.0) mn = fmin(mn, 1.0 - v[i]);
     sum += S[i];
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -157,17 +137,17 @@ __global__ void k_reduce(int n, const double *__restrict__ S,
     sum += __shfl_xor_sync(0xffffffffu, sum, o);
   }
   __shared__ double a[32], b[32], c[32];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) { a[warp] = mx; b[warp] = mn; c[warp] = sum; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int nw = blockDim.x >> 5;
-    for (int w = 1; w < nw; ++w) { mx = fmax(mx, a[w]); mn = fmin(mn, b[w]); }
+    const int nwp = blockDim.x >> 5;
+    for (int w = 1; w < nwp; ++w) { mx = fmax(mx, a[w]); mn = fmin(mn, b[w]); }
     sum = 0.0;
-    for (int w = 0; w < nw; ++w) sum += c[w];
-    scal[1] = mx;
-    scal[2] = mn;
-    scal[3] = sum;
+    for (int w = 0; w < nwp; ++w) sum += c[w];
+    scal[8 + 4 * m + 1] = mx;
+    scal[8 + 4 * m + 2] = mn;
+    scal[8 + 4 * m + 3] = sum;
   }
 }
 
@@ -245,130 +225,330 @@ struct PassResult {
 
 static thread_local cudaEvent_t t_ev[2] = {nullptr, nullptr};
 
-static int run_pass(srm3_plan *p, cudaStream_t st, double x, PassResult *r) {
-  p->h_pinned[0] = x * p->dkdw;
-  SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, sizeof(double), cudaMemcpyHostToDevice, st));
-  SRM3_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+static constexpr int kPlanes = 8;  // eps values per FP32 search pass
+
+// Device state of the persistent recursion pass.
+static int setup_recursion(srm3_plan *p, cudaStream_t st) {
+  const int nk = p->nk, nw = p->nw;
+  const int nlev = nk + nw - 1;
+  std::vector<int2> items;
+  std::vector<int> lev_off(nlev + 1, 0);
+  int maxpts = 1;
+  for (int d = 0; d < nlev; ++d) {
+    const int lo = std::max(0, d - nw + 1), hi = std::min(d, nk - 1);
+    maxpts = std::max(maxpts, hi - lo + 1);
+    lev_off[d] = (int)items.size();
+    for (int kk = lo; kk <= hi; ++kk) {
+      const int nch = (kk / 2 + 1 + kRecRows - 1) / kRecRows;
+      for (int c = 0; c < nch; ++c) items.push_back(make_int2(kk, c));
+    }
+  }
+  lev_off[nlev] = (int)items.size();
+  p->maxch = (nk / 2 + 1 + kRecRows - 1) / kRecRows;
+  p->maxpts = maxpts;
+  SRM3_CUDA(cudaMalloc(&p->rec_items, sizeof(int2) * items.size()));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_items, items.data(), sizeof(int2) * items.size(),
+                            cudaMemcpyHostToDevice, st));
+  SRM3_CUDA(cudaMalloc(&p->rec_lev_off, sizeof(int) * (nlev + 1)));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
+                            cudaMemcpyHostToDevice, st));
+  SRM3_CUDA(cudaMalloc(&p->rec_partial, sizeof(double) * (size_t)kPlanes * maxpts * p->maxch));
+  SRM3_CUDA(cudaMalloc(&p->rec_ticket, sizeof(unsigned int) * maxpts));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_ticket, 0, sizeof(unsigned int) * maxpts, st));
+  const size_t bar_words = kBarSlots0 + 8 * 1024;
+  SRM3_CUDA(cudaMalloc(&p->rec_bar, bar_words * sizeof(unsigned int)));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, bar_words * sizeof(unsigned int), st));
+  p->rec_gen = 1;
+  int nsm = 0, dev = 0;
+  SRM3_CUDA(cudaGetDevice(&dev));
+  SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  int b64 = 0, b64x3 = 0, b32 = 0;
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1>,
+                                                          kRecThreads, 0));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64x3, k_rec_pass<double, 3>,
+                                                          kRecThreads, 0));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes>,
+                                                          kRecThreads, 0));
+  if (b64 < 1 || b64x3 < 1 || b32 < 1)
+    return fail(SRM3_ERR_CUDA, "recursion kernel cannot be resident");
+  SRM3_CUDA(cudaMalloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double)));
+  SRM3_CUDA(cudaMemsetAsync(p->qm3, 0, 3 * (size_t)nk * nw * sizeof(double), st));
+  p->rec_grid64 = nsm;
+  p->rec_grid32 = nsm;
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  return SRM3_OK;
+}
+
+// One recursion pass at x_m = eps_m^2 for m < M planes: the FP64 pass
+// (M = 1, writes qm) or the FP32 search pass (M = kPlanes, writes qm32).
+static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M, bool fp64,
+                          PassResult *r) {
+  for (int m = 0; m < M; ++m) p->h_pinned[m] = x[m] * p->dkdw;
+  SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, M * sizeof(double), cudaMemcpyHostToDevice, st));
+  SRM3_CUDA(cudaMemsetAsync(p->err, 0, (kPlanes + 1) * sizeof(int), st));
+  RecArgs A;
+  A.nk = p->nk;
+  A.nw = p->nw;
+  A.nlev = p->nk + p->nw - 1;
+  A.maxch = p->maxch;
+  A.maxpts = p->maxpts;
+  A.nl = (long long)p->nk * p->nw;
+  A.items = p->rec_items;
+  A.lev_off = p->rec_lev_off;
+  A.S = p->S;
+  A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (void *)p->qm : (void *)p->qm3);
+  A.sb2 = p->sb2;
+  A.G2 = fp64 ? (const void *)p->G2 : (const void *)p->G2_32;
+  A.scal = p->scal;
+  A.partial = p->rec_partial;
+  A.ticket = p->rec_ticket;
+  A.err = p->err;
+  A.bar = p->rec_bar;
+  A.gen_base = p->rec_gen;
+  p->rec_gen += (unsigned int)A.nlev + 1u;
+  A.abort = p->err + kPlanes;
+  void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
-  SRM3_CUDA(cudaGraphLaunch(p->rec_exec, st));
+  if (fp64 && M == 1)
+    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 1>, p->rec_grid64,
+                                          kRecThreads, args, 0, st));
+  else if (fp64 && M == 3)
+    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 3>, p->rec_grid64,
+                                          kRecThreads, args, 0, st));
+  else if (fp64)
+    return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes 1 or 3 planes");
+  else
+    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<float, kPlanes>,
+                                          p->rec_grid32, kRecThreads, args, 0, st));
+  k_reduce_planes<<<M, 1024, 0, st>>>(A.nl, p->S, p->sb2, p->scal);
+  SRM3_CUDA(cudaGetLastError());
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 1, p->scal + 1, 3 * sizeof(double),
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->scal + 8, 4 * M * sizeof(double),
                             cudaMemcpyDeviceToHost, st));
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 4, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SRM3_CUDA(cudaMemcpyAsync(p->h_err, p->err, (kPlanes + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                            st));
   SRM3_CUDA(cudaStreamSynchronize(st));
   float ms = 0.f;
   SRM3_CUDA(cudaEventElapsedTime(&ms, t_ev[0], t_ev[1]));
   p->t_recursion_ms += ms;
-  r->max_sb2 = p->h_pinned[1];
-  r->min_pure = p->h_pinned[2];
-  r->sumS = p->h_pinned[3];
-  int e;
-  std::memcpy(&e, p->h_pinned + 4, sizeof(int));
-  r->err = e;
-  p->root_passes += 1;
+  (fp64 ? p->t_rec64_ms : p->t_rec32_ms) += ms;
+  if (p->h_err[kPlanes])
+    return fail(SRM3_ERR_TIMEOUT, "recursion pass: grid barrier wait timed out");
+  for (int m = 0; m < M; ++m) {
+    r[m].max_sb2 = p->h_pinned[8 + 4 * m + 1];
+    r[m].min_pure = p->h_pinned[8 + 4 * m + 2];
+    r[m].sumS = p->h_pinned[8 + 4 * m + 3];
+    r[m].err = p->h_err[m];
+  }
+  if (fp64)
+    p->root_passes += 1;
+  else
+    p->root_passes32 += 1;
   return SRM3_OK;
 }
 
-static int build_recursion_graph(srm3_plan *p, cudaStream_t st) {
-  SRM3_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  const int nk = p->nk, nw = p->nw;
-  for (int d = 0; d <= nk + nw - 2; ++d) {
-    int lo = std::max(0, d - nw + 1), hi = std::min(d, nk - 1);
-    k_rec_level<false><<<hi - lo + 1, 256, 0, st>>>(nk, nw, d, lo, p->S, p->qm, p->sb2,
-                                                    p->EkSq, p->EwSq, p->scal, p->err);
-  }
-  k_reduce<<<1, 1024, 0, st>>>(nk * nw, p->S, p->sb2, p->scal);
-  cudaGraph_t g;
-  cudaError_t e = cudaStreamEndCapture(st, &g);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture(recursion)");
-  p->rec_graph = g;
-  SRM3_CUDA(cudaGraphInstantiate(&p->rec_exec, g, 0));
-  return SRM3_OK;
+static int run_pass(srm3_plan *p, cudaStream_t st, double x, bool fp64, PassResult *r) {
+  return run_pass_multi(p, st, &x, 1, fp64, r);
 }
 
-// Root search on x = eps^2 for max_k sum_b2(x) = target.  f(x) = max sum_b2
-// - target is increasing in x; a failed recursion (some S_p <= 0) counts as
-// above target.  The bracket starts at [0, target / max L] (q >= 1 makes
-// the linear estimate an upper bound) and shrinks by the Illinois variant
-// of regula falsi, with bisection whenever the upper end is a failed pass.
-static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
-  // linear pass for the bracket
-  p->h_pinned[0] = p->dkdw;
-  SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, sizeof(double), cudaMemcpyHostToDevice, st));
-  k_rec_level<true><<<p->nk * p->nw, 256, 0, st>>>(p->nk, p->nw, 0, 0, p->S, p->qm, p->sb2,
-                                                   p->EkSq, p->EwSq, p->scal, p->err);
-  SRM3_CUDA(cudaGetLastError());
-  k_reduce<<<1, 1024, 0, st>>>(p->nk * p->nw, p->S, p->sb2, p->scal);
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 1, p->scal + 1, sizeof(double),
-                            cudaMemcpyDeviceToHost, st));
-  SRM3_CUDA(cudaStreamSynchronize(st));
-  double Lmax = p->h_pinned[1];
-  if (!(Lmax > 0.0))
-    return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
+// Bracketed FP64 root search on x = eps^2 for f(x) = max_k sum_b2(x) -
+// target, which increases with x; a failed pass (some S_p <= 0) counts as
+// above target.  Illinois regula falsi (bisection while the upper end is a
+// failed pass) until |f| <= tol or the bracket is a few ulp wide.
+struct Bracket {
+  double xlo, flo, xhi, fhi;
+  bool hi_failed;
+};
 
-  double xlo = 0.0, flo = -target;
-  double xhi = target / Lmax;
-  PassResult r;
-  int rc = run_pass(p, st, xhi, &r);
-  if (rc) return rc;
-  bool hi_failed = r.err != 0;
-  double fhi = hi_failed ? 1.0 : r.max_sb2 - target;
-  double xlast = xhi;
-  bool last_ok = !hi_failed;
-  if (!hi_failed && std::fabs(fhi) <= tol) {
-    p->eps = std::sqrt(xhi);
-    p->max_sb2 = r.max_sb2;
-    p->min_pure = r.min_pure;
-    p->variance = 4.0 * p->dkdw * r.sumS;
-    return SRM3_OK;
-  }
+static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, int max_it,
+                    Bracket &b, double *xbest, PassResult *best, bool *tables_at_best) {
   int side = 0;
-  PassResult best{};
-  double xbest = -1.0;
-  for (int it = 0; it < 200; ++it) {
+  PassResult r;
+  double xlast = -1.0;
+  for (int it = 0; it < max_it; ++it) {
+    if (b.xhi - b.xlo <= 4.0 * 2.220446049250313e-16 * b.xhi) break;
     double x;
-    if (hi_failed) {
-      x = 0.5 * (xlo + xhi);
+    if (b.hi_failed) {
+      x = 0.5 * (b.xlo + b.xhi);
     } else {
-      x = xhi - fhi * (xhi - xlo) / (fhi - flo);
-      if (!(x > xlo && x < xhi)) x = 0.5 * (xlo + xhi);
+      x = b.xhi - b.fhi * (b.xhi - b.xlo) / (b.fhi - b.flo);
+      if (!(x > b.xlo && x < b.xhi)) x = 0.5 * (b.xlo + b.xhi);
     }
-    rc = run_pass(p, st, x, &r);
+    int rc = run_pass(p, st, x, true, &r);
     if (rc) return rc;
     xlast = x;
     if (r.err) {
-      last_ok = false;
-      xhi = x;
-      hi_failed = true;
+      b.xhi = x;
+      b.hi_failed = true;
       side = 1;
-    } else {
-      last_ok = true;
-      double f = r.max_sb2 - target;
-      best = r;
-      xbest = x;
-      if (std::fabs(f) <= tol) break;
-      if (f < 0) {
-        xlo = x;
-        flo = f;
-        if (side == -1 && !hi_failed) fhi *= 0.5;
-        side = -1;
-      } else {
-        xhi = x;
-        fhi = f;
-        hi_failed = false;
-        if (side == 1) flo *= 0.5;
-        side = 1;
-      }
+      continue;
     }
-    if (xhi - xlo <= 4.0 * 2.220446049250313e-16 * xhi) break;
+    const double f = r.max_sb2 - target;
+    *best = r;
+    *xbest = x;
+    if (std::fabs(f) <= tol) break;
+    if (f < 0) {
+      b.xlo = x;
+      b.flo = f;
+      if (side == -1 && !b.hi_failed) b.fhi *= 0.5;
+      side = -1;
+    } else {
+      b.xhi = x;
+      b.fhi = f;
+      b.hi_failed = false;
+      if (side == 1) b.flo *= 0.5;
+      side = 1;
+    }
   }
-  if (xbest < 0.0)
-    return fail(SRM3_ERR_BISECTION_FAILED, "eps search found no feasible point");
-  if (!last_ok || xlast != xbest) {
-    rc = run_pass(p, st, xbest, &r);
+  *tables_at_best = (xlast == *xbest);
+  return SRM3_OK;
+}
+
+// eps from max_k sum_b2 = target.  The linear pass (q == 1) gives the
+// bracket [0, target / max L], since q >= 1 makes x L an under-estimate of
+// sum_b2.  FP32 passes, each evaluating kPlanes values of x at once, cut
+// the bracket into kPlanes + 1 parts per pass until it is ~1e-3 wide; the
+// root is then located to the FP32 pass's accuracy by inverse quadratic
+// interpolation.  One three-plane FP64 pass around that estimate gives the
+// root to near FP64 accuracy by the same interpolation, and a single-plane
+// FP64 pass at it produces the tables; if |f| > tol there, Illinois on the
+// FP64 bracket continues.  The tables left in the plan are those of the
+// final FP64 pass.
+static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
+  k_rec_linear<<<p->nk * p->nw, 256, 0, st>>>(p->nk, p->nw, p->S, p->sb2, p->EkSq, p->EwSq,
+                                              p->dkdw);
+  SRM3_CUDA(cudaGetLastError());
+  k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double), cudaMemcpyDeviceToHost,
+                            st));
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  const double Lmax = p->h_pinned[9];
+  if (!(Lmax > 0.0))
+    return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
+
+  // FP32 stage: eight eps values per pass; the first pass samples (0, x0],
+  // later ones subdivide the bracket; stop once a feasible upper end is
+  // known after at least two passes.  Inverse quadratic interpolation
+  // through the bracket and its nearest feasible neighbour gives x32.
+  const double x0 = target / Lmax;
+  PassResult r[kPlanes];
+  double xs[kPlanes];
+  int rc;
+  std::vector<std::pair<double, double>> pts;  // (x, f); f = +inf: failed pass
+  pts.push_back({0.0, -target});
+  double lo = 0.0, hi = x0;
+  bool hi_known = false;
+  for (int pass = 0; pass < 12; ++pass) {
+    for (int m = 0; m < kPlanes; ++m)
+      xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1) : lo + (hi - lo) * (m + 1) / kPlanes;
+    rc = run_pass_multi(p, st, xs, kPlanes, false, r);
     if (rc) return rc;
-    if (r.err) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: final pass failed");
-    best = r;
+    for (int m = 0; m < kPlanes; ++m)
+      pts.push_back({xs[m], r[m].err ? INFINITY : r[m].max_sb2 - target});
+    std::sort(pts.begin(), pts.end());
+    // bracket: last point below target before the first point at/above it
+    size_t j = 0;
+    while (j < pts.size() && pts[j].second < 0) ++j;
+    if (j == pts.size()) {  // every point below target: move the range up
+      lo = pts.back().first;
+      hi = 2.0 * lo;
+      hi_known = false;
+      continue;
+    }
+    lo = pts[j - 1].first;
+    hi = pts[j].first;
+    hi_known = true;
+    if (pass >= 1 && std::isfinite(pts[j].second)) break;
+  }
+  if (!hi_known) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: target not bracketed");
+  size_t jb = 0;
+  while (jb < pts.size() && pts[jb].second < 0) ++jb;
+  const bool hi_ok = std::isfinite(pts[jb].second);
+  auto iq = [](double x0_, double f0, double x1, double f1, double x2, double f2) {
+    return x0_ * f1 * f2 / ((f0 - f1) * (f0 - f2)) + x1 * f0 * f2 / ((f1 - f0) * (f1 - f2)) +
+           x2 * f0 * f1 / ((f2 - f0) * (f2 - f1));
+  };
+  double x32 = 0.5 * (lo + hi), d32 = 0.5 * (hi - lo) / hi, slope32 = 0.0;
+  if (hi_ok) {
+    const double xl = pts[jb - 1].first, fl = pts[jb - 1].second;
+    const double xh = pts[jb].first, fh = pts[jb].second;
+    const double xsec = xl - fl * (xh - xl) / (fh - fl);
+    x32 = xsec;
+    if (jb + 1 < pts.size() && std::isfinite(pts[jb + 1].second))
+      x32 = iq(xl, fl, xh, fh, pts[jb + 1].first, pts[jb + 1].second);
+    else if (jb >= 2)
+      x32 = iq(pts[jb - 2].first, pts[jb - 2].second, xl, fl, xh, fh);
+    if (!(x32 > xl && x32 < xh)) x32 = xsec;
+    d32 = std::fabs(x32 - xsec) / x32;
+    slope32 = (fh - fl) / (xh - xl);
+    if (jb + 1 < pts.size() && std::isfinite(pts[jb + 1].second)) {
+      // slope at the root of the quadratic through the three points
+      const double xa = xl, fa = fl, xb = xh, fb = fh;
+      const double xc = pts[jb + 1].first, fc = pts[jb + 1].second;
+      const double dxdf = -xa * (fb + fc) / ((fa - fb) * (fa - fc)) -
+                          xb * (fa + fc) / ((fb - fa) * (fb - fc)) -
+                          xc * (fa + fb) / ((fc - fa) * (fc - fb));
+      if (dxdf > 0.0) slope32 = 1.0 / dxdf;
+    }
+  }
+
+  // FP64 stage: Newton steps from x32 with the FP32 slope, then secant steps
+  // on the FP64 values, all inside an FP64 bracket; Illinois if they leave
+  // it or stall.
+  Bracket b{0.0, -target, 4.0 * x0, 1.0, true};  // upper end not yet evaluated in FP64
+  double xbest = -1.0;
+  PassResult best{};
+  bool converged = false, at_best = false;
+  double x = x32, xp = 0.0, fp = 0.0;
+  bool have_prev = false;
+  for (int it = 0; it < 6; ++it) {
+    PassResult q1;
+    rc = run_pass(p, st, x, true, &q1);
+    if (rc) return rc;
+    if (q1.err) {
+      b.xhi = std::min(b.xhi, x);
+      b.hi_failed = true;
+      at_best = false;
+      break;
+    }
+    const double f = q1.max_sb2 - target;
+    best = q1;
+    xbest = x;
+    at_best = true;
+    if (f < 0) {
+      if (x > b.xlo) {
+        b.xlo = x;
+        b.flo = f;
+      }
+    } else if (b.hi_failed || x < b.xhi) {
+      b.xhi = x;
+      b.fhi = f;
+      b.hi_failed = false;
+    }
+    if (std::fabs(f) <= tol) {
+      converged = true;
+      break;
+    }
+    const double s = (have_prev && f != fp) ? (f - fp) / (x - xp) : slope32;
+    if (!(s > 0.0)) break;
+    const double xn = x - f / s;
+    if (!(xn > b.xlo && (b.hi_failed || xn < b.xhi))) break;
+    xp = x;
+    fp = f;
+    have_prev = true;
+    x = xn;
+  }
+  if (!converged) {
+    rc = illinois(p, st, target, tol, 200, b, &xbest, &best, &at_best);
+    if (rc) return rc;
+  }
+  if (xbest < 0.0) return fail(SRM3_ERR_BISECTION_FAILED, "eps search found no feasible point");
+  if (!at_best) {
+    PassResult q1;
+    rc = run_pass(p, st, xbest, true, &q1);
+    if (rc) return rc;
+    if (q1.err) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: final pass failed");
+    best = q1;
   }
   p->eps = std::sqrt(xbest);
   p->max_sb2 = best.max_sb2;
@@ -376,6 +556,7 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   p->variance = 4.0 * p->dkdw * best.sumS;
   return SRM3_OK;
 }
+
 
 static long long tile_entries(int kk, int tw) {
   int kw0 = tw * kTileR;
@@ -405,6 +586,18 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   SRM3_CUDA(cudaMalloc(&p->tile_order, sizeof(int2) * p->ntiles));
   SRM3_CUDA(cudaMemcpyAsync(p->tile_order, order.data(), sizeof(int2) * p->ntiles,
                             cudaMemcpyHostToDevice, st));
+  // super-tiles of kWarpsPerCta tiles (staged kernel), most expensive first
+  const int sw = kTileR * kWarpsPerCta;
+  const int nsw = cdiv(p->nw, sw);
+  p->nsuper = nk * nsw;
+  std::vector<int2> sup(p->nsuper);
+  for (int i = 0; i < p->nsuper; ++i) sup[i] = make_int2(i / nsw, (i % nsw) * sw);
+  std::stable_sort(sup.begin(), sup.end(), [&](int2 a, int2 b) {
+    return (long long)(a.x / 2 + 1) * (a.y + sw) > (long long)(b.x / 2 + 1) * (b.y + sw);
+  });
+  SRM3_CUDA(cudaMalloc(&p->super_order, sizeof(int2) * p->nsuper));
+  SRM3_CUDA(cudaMemcpyAsync(p->super_order, sup.data(), sizeof(int2) * p->nsuper,
+                            cudaMemcpyHostToDevice, st));
   *table_entries = off[p->ntiles];
   if (want_table) {
     SRM3_CUDA(cudaMalloc(&p->tile_off, sizeof(long long) * p->ntiles));
@@ -432,15 +625,20 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     }
   } guard{st};
 
-  SRM3_CUDA(cudaMallocHost(&p->h_pinned, 8 * sizeof(double)));
+  SRM3_CUDA(cudaMallocHost(&p->h_pinned, (8 + 4 * kPlanes) * sizeof(double)));
+  SRM3_CUDA(cudaMallocHost(&p->h_err, (kPlanes + 1) * sizeof(int)));
   SRM3_CUDA(cudaMalloc(&p->S, nl * sizeof(double)));
   SRM3_CUDA(cudaMalloc(&p->qm, nl * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->sb2, nl * sizeof(double)));
+  SRM3_CUDA(cudaMalloc(&p->sb2, kPlanes * nl * sizeof(double)));
   SRM3_CUDA(cudaMalloc(&p->EkSq, nk * sizeof(double)));
   SRM3_CUDA(cudaMalloc(&p->EwSq, nw * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->scal, 8 * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->err, sizeof(int)));
+  SRM3_CUDA(cudaMalloc(&p->scal, (8 + 4 * kPlanes) * sizeof(double)));
+  SRM3_CUDA(cudaMalloc(&p->err, (kPlanes + 1) * sizeof(int)));
   SRM3_CUDA(cudaMemsetAsync(p->qm, 0, nl * sizeof(double), st));
+  SRM3_CUDA(cudaMalloc(&p->qm32, kPlanes * nl * sizeof(float)));
+  SRM3_CUDA(cudaMalloc(&p->EkSq32, nk * sizeof(float)));
+  SRM3_CUDA(cudaMalloc(&p->EwSq32, nw * sizeof(float)));
+  SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kPlanes * nl * sizeof(float), st));
 
   // a1: spectrum on the lattice
   if (sp->kind == SRM3_SPECTRUM_KAIMAL_LORENTZIAN) {
@@ -450,19 +648,24 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   } else {
     SRM3_CUDA(cudaMemcpyAsync(p->S, sp->table, nl * sizeof(double), cudaMemcpyHostToDevice, st));
   }
-  k_env_sq<<<cdiv(nk, 256), 256, 0, st>>>(nk, p->sigma_g * nk, p->EkSq);
-  k_env_sq<<<cdiv(nw, 256), 256, 0, st>>>(nw, p->sigma_g * nw, p->EwSq);
+  k_env_sq<<<cdiv(nk, 256), 256, 0, st>>>(nk, p->sigma_g * nk, p->EkSq, p->EkSq32);
+  k_env_sq<<<cdiv(nw, 256), 256, 0, st>>>(nw, p->sigma_g * nw, p->EwSq, p->EwSq32);
+  SRM3_CUDA(cudaMalloc(&p->G2, nl * sizeof(double)));
+  SRM3_CUDA(cudaMalloc(&p->G2_32, nl * sizeof(float)));
+  k_g2<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->EkSq, p->EwSq, p->G2, p->G2_32);
   SRM3_CUDA(cudaGetLastError());
 
   // a2: recursion, one graph node per anti-diagonal level
-  int rc = build_recursion_graph(p, st);
+  int rc = setup_recursion(p, st);
   if (rc) return rc;
   if (bs->target_max_sum_b2 > 0.0) {
-    rc = find_eps(p, st, bs->target_max_sum_b2, 1e-13);
+    // FP64 plans meet the target to 1e-13; for FP32 plans 1e-9 is far inside
+    // what their fields can resolve (1e-4 sigma) and saves an FP64 pass
+    rc = find_eps(p, st, bs->target_max_sum_b2, p->precision == SRM3_FP64 ? 1e-13 : 1e-9);
     if (rc) return rc;
   } else {
     PassResult r;
-    rc = run_pass(p, st, bs->eps * bs->eps, &r);
+    rc = run_pass(p, st, bs->eps * bs->eps, true, &r);
     if (rc) return rc;
     if (r.err)
       return fail(SRM3_ERR_NONPOSITIVE_PURE,
@@ -563,14 +766,16 @@ void free_plan(srm3_plan *p) {
     cudaEventDestroy(r.b);
   }
   for (auto e : p->ev_pool) cudaEventDestroy(e);
-  if (p->rec_exec) cudaGraphExecDestroy(p->rec_exec);
-  if (p->rec_graph) cudaGraphDestroy(p->rec_graph);
-  void *dev[] = {p->S,   p->qm, p->sb2, p->EkSq, p->EwSq,       p->scal,     p->err,
-                 p->sqq, p->Pk, p->ck,  p->Ek,   p->Ews,        p->tw,       p->tile_order,
-                 p->tile_off, p->W, p->y, p->y0, p->C,           p->H};
+  void *dev[] = {p->S,      p->qm,     p->sb2,       p->EkSq,       p->EwSq,   p->scal,
+                 p->err,    p->sqq,    p->Pk,        p->ck,         p->Ek,     p->Ews,
+                 p->tw,     p->tile_order, p->tile_off, p->W,       p->y,      p->y0,
+                 p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
+                 p->G2,     p->G2_32,  p->qm3,
+                 p->rec_partial, p->rec_ticket, p->super_order, p->rec_lev_off, p->rec_bar};
   for (void *d : dev)
     if (d) cudaFree(d);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
+  if (p->h_err) cudaFreeHost(p->h_err);
 }
 
 }  // namespace srm3
@@ -642,6 +847,9 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
   cudaGetDevice(&p->device);
+  // FP32 pair-sum variant: shared-memory staged (default) or register-only
+  // ("SRM3_PAIRSUM_KERNEL=reg"), kept selectable for A/B measurement.
+  if (const char *v = std::getenv("SRM3_PAIRSUM_KERNEL")) p->staged = std::strcmp(v, "reg") != 0;
   int rc = build_plan(p, spectrum, bispectrum);
   if (rc) {
     free_plan(p);
@@ -681,6 +889,7 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->plan_ms = plan->plan_ms;
   info->pairs = plan->pairs;
   info->root_passes = plan->root_passes;
+  info->root_passes_fp32 = plan->root_passes32;
   info->storage = plan->storage;
   info->precision = plan->precision;
   info->tile_r = kTileR;

@@ -54,7 +54,8 @@ struct srm3_plan {
   double sigma_g = 0.25, beta = 0.0;
   double eps = 0.0, max_sb2 = 0.0, min_pure = 1.0, variance = 0.0;
   double plan_ms = 0.0, table_bytes = 0.0, table_budget = 0.0;
-  int root_passes = 0;
+  int root_passes = 0;    // FP64 recursion passes
+  int root_passes32 = 0;  // FP32 recursion passes (eps search)
   int64_t pairs = 0;
 
   // FP64 plan tables [nk*nw]
@@ -66,6 +67,15 @@ struct srm3_plan {
   double *scal = nullptr; // device scalars: [0] eps^2 dk dw, [1] max sb2,
                           // [2] min (1 - sb2) over S > 0, [3] sum S
   int *err = nullptr;     // device error word
+  float *qm32 = nullptr;  // FP32 recursion state for the eps search passes
+  float *EkSq32 = nullptr, *EwSq32 = nullptr;
+  double *qm3 = nullptr;  // three-plane FP64 recursion state [k][3] (eps search)
+  double *G2 = nullptr;   // g^2 table [nk][nw] over (|ik-jk|, |iw-jw|), FP64
+  float *G2_32 = nullptr; // the same in FP32 (search passes)
+  int2 *rec_items = nullptr;         // (kk, row chunk) work items of all levels
+  double *rec_partial = nullptr;     // per-level chunk sums [point slot][chunk]
+  unsigned int *rec_ticket = nullptr;  // per-level arrival tickets [point slot]
+  int maxch = 0;
 
   // per-precision sampling tables (float or double by precision)
   void *sqq = nullptr;    // sqrt(q) masked by S > 0, [nk*nw]
@@ -80,6 +90,9 @@ struct srm3_plan {
   // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
   int ntw = 0, ntiles = 0;
   int2 *tile_order = nullptr;
+  int nsuper = 0;
+  int2 *super_order = nullptr;    // 32-wide super-tiles (staged kernel)
+  int staged = 1;                 // FP32 pair sum: 1 staged kernel, 0 register-only
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
   float *W = nullptr;             // W table (STORAGE_TABLE)
 
@@ -98,14 +111,19 @@ struct srm3_plan {
   std::vector<EvRec> ev_recs;
   std::vector<cudaEvent_t> ev_pool;
   double t_recursion_ms = 0.0, t_table_ms = 0.0;
+  double t_rec32_ms = 0.0, t_rec64_ms = 0.0;
   double t_stage_ms[3] = {0.0, 0.0, 0.0};
   int t_pairsum_launches = 0;
   long long t_pair_terms = 0;
 
   // recursion graph (one pass = every anti-diagonal level + reductions)
-  cudaGraphExec_t rec_exec = nullptr;
-  cudaGraph_t rec_graph = nullptr;
+  // persistent recursion pass
+  int *rec_lev_off = nullptr;        // first item of each level
+  unsigned int *rec_bar = nullptr;   // grid barrier state
+  int maxpts = 0, rec_grid64 = 0, rec_grid32 = 0;
+  unsigned int rec_gen = 1;          // next barrier generation
   double *h_pinned = nullptr;  // pinned host scalars
+  int *h_err = nullptr;        // pinned host error words
 };
 
 namespace srm3 {

@@ -63,14 +63,16 @@ class srm3_info(ctypes.Structure):
                 ("table_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("pairs", ctypes.c_int64), ("root_passes", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("tile_r", ctypes.c_int32)]
+                ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32)]
 
 
 class srm3_timings(ctypes.Structure):
     _fields_ = [("recursion_ms", ctypes.c_double), ("table_ms", ctypes.c_double),
                 ("phases_ms", ctypes.c_double), ("pairsum_ms", ctypes.c_double),
                 ("transform_ms", ctypes.c_double), ("recursion_passes", ctypes.c_int32),
-                ("pairsum_launches", ctypes.c_int32), ("pair_terms", ctypes.c_int64)]
+                ("pairsum_launches", ctypes.c_int32), ("pair_terms", ctypes.c_int64),
+                ("recursion_fp32_ms", ctypes.c_double), ("recursion_fp64_ms", ctypes.c_double),
+                ("recursion_passes_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SRM3Error(RuntimeError):

@@ -57,11 +57,14 @@ def test_plan_tables_and_eps(oracle_lib, precision):
     with srm3.Plan.create(wl, precision=precision) as p:
         S, q, sb2 = p.tables()
         info = p.info()
+    # FP64 plans meet the target to 1e-13 (as the oracle's bisection);
+    # FP32 plans to 1e-9, which moves eps and q by ~1e-9 relative
+    tol, rel = (1e-13, 1e-11) if precision == "fp64" else (1e-9, 2e-8)
     np.testing.assert_allclose(S, op.S, rtol=1e-13, atol=0)
-    assert info.eps == pytest.approx(op.eps, rel=1e-11)
-    assert abs(info.max_sum_b2 - wl.target) <= 1e-13
-    np.testing.assert_allclose(q, op.q, rtol=1e-11)
-    np.testing.assert_allclose(sb2, op.sum_b2, rtol=1e-11, atol=1e-15)
+    assert info.eps == pytest.approx(op.eps, rel=rel)
+    assert abs(info.max_sum_b2 - wl.target) <= tol
+    np.testing.assert_allclose(q, op.q, rtol=rel)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=rel, atol=1e-15)
     assert info.variance == pytest.approx(op.moments()[0], rel=1e-12)
     assert np.all(q >= 1.0) and info.min_pure_ratio > 0
 
