@@ -286,8 +286,8 @@ def main():
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "k_pairsum_f32<table>" if info.storage == 1 else
-                               "k_pairsum_f32<recompute>",
+                     "kernel": "k_pairsum_f32s<table>" if info.storage == 1 else
+                               "k_pairsum_f32s<recompute>",
                      "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                     f"flop x {sm_max:.0f} MHz (max SM clock of "
                                     "MEASURED_PEAKS.json); 10 flop per pair-term"},
@@ -315,7 +315,7 @@ def main():
                        "ms_per_step": e2e_s * 1e3}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_baseline(wl)
+        cb = oracle_baseline(wl, rows=128)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line))
