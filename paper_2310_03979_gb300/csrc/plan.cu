@@ -231,30 +231,24 @@ static constexpr int kPlanes = 8;  // eps values per FP32 search pass
 static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   const int nk = p->nk, nw = p->nw;
   const int nlev = nk + nw - 1;
-  std::vector<int2> items;
+  // lattice points in level order, and the first point of each level
+  std::vector<int2> pts;
   std::vector<int> lev_off(nlev + 1, 0);
-  int maxpts = 1;
+  pts.reserve((size_t)nk * nw);
   for (int d = 0; d < nlev; ++d) {
     const int lo = std::max(0, d - nw + 1), hi = std::min(d, nk - 1);
-    maxpts = std::max(maxpts, hi - lo + 1);
-    lev_off[d] = (int)items.size();
-    for (int kk = lo; kk <= hi; ++kk) {
-      const int nch = (kk / 2 + 1 + kRecRows - 1) / kRecRows;
-      for (int c = 0; c < nch; ++c) items.push_back(make_int2(kk, c));
-    }
+    lev_off[d] = (int)pts.size();
+    for (int kk = lo; kk <= hi; ++kk) pts.push_back(make_int2(kk, d - kk));
   }
-  lev_off[nlev] = (int)items.size();
-  p->maxch = (nk / 2 + 1 + kRecRows - 1) / kRecRows;
-  p->maxpts = maxpts;
-  SRM3_CUDA(cudaMalloc(&p->rec_items, sizeof(int2) * items.size()));
-  SRM3_CUDA(cudaMemcpyAsync(p->rec_items, items.data(), sizeof(int2) * items.size(),
+  lev_off[nlev] = (int)pts.size();
+  SRM3_CUDA(cudaMalloc(&p->rec_items, sizeof(int2) * pts.size()));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_items, pts.data(), sizeof(int2) * pts.size(),
                             cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaMalloc(&p->rec_lev_off, sizeof(int) * (nlev + 1)));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
                             cudaMemcpyHostToDevice, st));
-  SRM3_CUDA(cudaMalloc(&p->rec_partial, sizeof(double) * (size_t)kPlanes * maxpts * p->maxch));
-  SRM3_CUDA(cudaMalloc(&p->rec_ticket, sizeof(unsigned int) * maxpts));
-  SRM3_CUDA(cudaMemsetAsync(p->rec_ticket, 0, sizeof(unsigned int) * maxpts, st));
+  // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
+  SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
   const size_t bar_words = kBarSlots0 + 8 * 1024;
   SRM3_CUDA(cudaMalloc(&p->rec_bar, bar_words * sizeof(unsigned int)));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, bar_words * sizeof(unsigned int), st));
@@ -290,22 +284,19 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.nk = p->nk;
   A.nw = p->nw;
   A.nlev = p->nk + p->nw - 1;
-  A.maxch = p->maxch;
-  A.maxpts = p->maxpts;
   A.nl = (long long)p->nk * p->nw;
-  A.items = p->rec_items;
-  A.lev_off = p->rec_lev_off;
+  A.pts = p->rec_items;
+  A.pt_off = p->rec_lev_off;
   A.S = p->S;
   A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (void *)p->qm : (void *)p->qm3);
+  A.acc = p->rec_partial;
   A.sb2 = p->sb2;
   A.G2 = fp64 ? (const void *)p->G2 : (const void *)p->G2_32;
   A.scal = p->scal;
-  A.partial = p->rec_partial;
-  A.ticket = p->rec_ticket;
   A.err = p->err;
   A.bar = p->rec_bar;
   A.gen_base = p->rec_gen;
-  p->rec_gen += (unsigned int)A.nlev + 1u;
+  p->rec_gen += (unsigned int)rec_barriers(A.nlev) + 1u;
   A.abort = p->err + kPlanes;
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
@@ -415,8 +406,9 @@ static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, in
 // FP64 bracket continues.  The tables left in the plan are those of the
 // final FP64 pass.
 static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
-  k_rec_linear<<<p->nk * p->nw, 256, 0, st>>>(p->nk, p->nw, p->S, p->sb2, p->EkSq, p->EwSq,
-                                              p->dkdw);
+  k_rec_linear<<<cdiv((long long)p->nk * p->nw * 32, 256), 256, 0, st>>>(p->nk, p->nw, p->S,
+                                                                          p->G2_32, p->sb2,
+                                                                          p->dkdw);
   SRM3_CUDA(cudaGetLastError());
   k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double), cudaMemcpyDeviceToHost,

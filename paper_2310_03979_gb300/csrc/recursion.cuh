@@ -1,37 +1,40 @@
 // recursion.cuh - device side of the pure-spectrum / partial-bicoherence
 // recursion (Eq. pure): one pass over the lattice as a persistent
-// cooperative kernel.  Included by plan.cu only.
+// cooperative kernel, and the linear (q = 1) pass that brackets eps.
+// Included by plan.cu only.
 #pragma once
-
-#include <cuda/atomic>
 
 #include "srm3_internal.cuh"
 
 namespace srm3 {
 
-// Rows of one work item: a point's row pairs (a, kk - a), a <= kk/2, are
-// taken kRecRows at a time by one warp.
-constexpr int kRecRows = 4;
 constexpr int kRecThreads = 512;  // one CTA per SM
+constexpr int kRecBL = 16;        // levels per block of the blocked pass
 constexpr int kBarSlots0 = 32;    // first arrival slot of the grid barrier
 
 struct RecArgs {
-  int nk, nw, nlev, maxch, maxpts;
+  int nk, nw, nlev;
   long long nl;
-  const int2 *items;    // (kk, chunk) of every level, level by level
-  const int *lev_off;   // first item of each level
+  const int2 *pts;      // lattice points in level order (level-major, kk ascending)
+  const int *pt_off;    // first point of each level, nlev + 1 entries
   const double *S;
   void *q;              // [nl][M] of T: q = S/S_p (0 where S = 0), plane fastest
+  void *acc;            // [nl][M] of T: pair sums gathered by the bulk phases
   double *sb2;          // [M][nl]
   const void *G2;       // T[nk][nw]: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|]
   const double *scal;   // [M]: eps^2 dk dw per plane
-  void *partial;        // [maxpts][maxch][M] of T
-  unsigned int *ticket; // [maxpts]
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] release generation, [kBarSlots0 + b] arrival of CTA b
   unsigned int gen_base;  // generation of this launch's first barrier
   int *abort;           // barrier wait timed out
 };
+
+// Number of grid barriers one pass uses.
+__host__ __device__ inline int rec_barriers(int nlev) {
+  int n = 1 + (nlev < kRecBL ? nlev : kRecBL);
+  for (int D = kRecBL; D < nlev; D += kRecBL) n += 1 + ((nlev - D) < kRecBL ? (nlev - D) : kRecBL);
+  return n;
+}
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident), without
 // atomics: CTA b stores the barrier's generation number g in its own slot
@@ -117,158 +120,248 @@ struct PlaneVec<float, 8> {
   }
 };
 
-// One recursion pass over all anti-diagonal levels d = kk + kw.  Every part
-// of a pair of Pi(k) lies on a lower level, so the points of a level are
-// independent; the kernel walks the levels in order with a grid barrier in
-// between.  A work item is one warp on up to kRecRows row pairs (a, kk - a)
-// of one point: the rows' omega ranges are laid end to end and the lanes
-// stride over the joined range with four independent accumulators.
-// Canonical half: the centre row a = kk - a keeps iw <= kw/2; i = 0 is
-// skipped.  Per plane m (one eps value each)
+// One pair term g^2(i, j) q_i q_j added to acc (all planes).
+template <typename T, int M>
+__device__ __forceinline__ void add_pair(const RecArgs &A, int kk, int kw, int ia, int iw, int ja,
+                                         int jw, T (&acc)[M]) {
+  const int nw = A.nw;
+  const T *G2 = static_cast<const T *>(A.G2);
+  const T *q = static_cast<const T *>(A.q);
+  const int dk = 2 * ia - kk, dw = 2 * iw - kw;
+  const T g2 = G2[(size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw)];
+  T va[M], vb[M];
+  PlaneVec<T, M>::load(q + ((size_t)ia * nw + iw) * M, va);
+  PlaneVec<T, M>::load(q + ((size_t)ja * nw + jw) * M, vb);
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = fma(g2, va[m] * vb[m], acc[m]);
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void warp_sum(T (&v)[M]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+}
+
+// q_k and sum_b2(k) from the point's complete pair sum t (lane 0 only).
+template <typename T, int M>
+__device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
+  T *q = static_cast<T *>(A.q);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const T s2 = (T)A.scal[m] * t[m];
+    A.sb2[m * A.nl + k] = (double)s2;
+    if (s2 < (T)1) {
+      q[k * M + m] = (T)1 / ((T)1 - s2);
+    } else {
+      q[k * M + m] = (T)0;
+      atomicOr(A.err + m, 1);
+    }
+  }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void point_zero(const RecArgs &A, long long k, int lane) {
+  if (lane < M) {
+    A.sb2[lane * A.nl + k] = 0.0;
+    static_cast<T *>(A.q)[k * M + lane] = (T)0;
+  }
+}
+
+// Levels below kRecBL: the whole canonical pair sum of the point (one warp),
+// rows a <= kk/2 laid end to end as a*(kw+1) + iw, the centre row a = kk - a
+// keeping iw <= kw/2, i = 0 skipped.
+template <typename T, int M>
+__device__ void point_direct(const RecArgs &A, int kk, int kw, int lane) {
+  const long long k = (long long)kk * A.nw + kw;
+  if (!(A.S[k] > 0.0)) {
+    point_zero<T, M>(A, k, lane);
+    return;
+  }
+  T acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = (T)0;
+  const int W = kw + 1, E = (kk / 2 + 1) * W;
+  for (int e = lane; e < E; e += 32) {
+    const int a = e / W, iw = e - a * W, b = kk - a;
+    const int lim = (a == b) ? kw / 2 : kw;
+    if ((a == 0 && iw == 0) || iw > lim) continue;
+    add_pair<T, M>(A, kk, kw, a, iw, b, kw - iw, acc);
+  }
+  warp_sum<T, M>(acc);
+  if (lane == 0) finalize<T, M>(A, k, acc);
+}
+
+// Bulk phase of block D for a point at level d in [D, 2D): the pairs whose
+// higher-level element lies on a level in [D - BL, D).  For a row pair
+// (a, b = kk - a) these are two slivers of at most BL omega indices:
+//   right: i = (a, iw) is the higher element, iw = D - BL - a + u with
+//          2 (D - BL + u) >= d;
+//   left:  j = (b, jw) is the higher element, jw = D - BL - b + u with
+//          2 (D - BL + u) > d.
+// Lanes take (row, u) slots, 16 u per row and two rows per warp step; the
+// canonical limits (centre row, i != 0, iw <= kw) mask the rest.
+template <typename T, int M>
+__device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
+  const long long k = (long long)kk * A.nw + kw;
+  if (!(A.S[k] > 0.0)) return;
+  const int d = kk + kw, base = D - kRecBL, arow = kk / 2 + 1;
+  const int uR0 = max(0, (d + 1) / 2 - base);
+  const int uL0 = max(0, d / 2 - base + 1);
+  const int aR0 = max(0, base + uR0 - kw), aR1 = min(arow - 1, D - 1);
+  const int aL0 = max(0, kk - D + 1), aL1 = arow - 1;
+  const int nR = (uR0 < kRecBL && aR1 >= aR0) ? aR1 - aR0 + 1 : 0;
+  const int nL = (uL0 < kRecBL && aL1 >= aL0) ? aL1 - aL0 + 1 : 0;
+  const int nrows = nR + nL;
+  if (nrows == 0) return;
+  const int u = lane & (kRecBL - 1), rs = lane >> 4;
+  T acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = (T)0;
+  for (int v = rs; v < nrows; v += 2) {
+    int a, iw, jw;
+    bool ok;
+    if (v < nR) {
+      a = aR0 + v;
+      iw = base - a + u;
+      jw = kw - iw;
+      ok = u >= uR0;
+    } else {
+      a = aL0 + (v - nR);
+      jw = base - (kk - a) + u;
+      iw = kw - jw;
+      ok = u >= uL0;
+    }
+    const int b = kk - a;
+    const int lim = (a == b) ? kw / 2 : kw;
+    ok = ok && iw >= (a == 0 ? 1 : 0) && iw <= lim && jw >= 0;
+    if (ok) add_pair<T, M>(A, kk, kw, a, iw, b, jw, acc);
+  }
+  warp_sum<T, M>(acc);
+  if (lane == 0) {
+    T *ac = static_cast<T *>(A.acc);
+#pragma unroll
+    for (int m = 0; m < M; ++m) ac[k * M + m] += acc[m];
+  }
+}
+
+// Fringe of a point at level d in [D, D + BL): the pairs whose higher
+// element lies on a level in [D, d).  Their other element l has level
+// 1 .. d - D < BL <= D, so each such pair is {l, k - l} for exactly one
+// low lattice point l: the t(t+3)/2 points of levels 1..t, t = d - D,
+// enumerated level by level.  Adds the bulk sums and finalizes the point.
+template <typename T, int M>
+__device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) {
+  const long long k = (long long)kk * A.nw + kw;
+  if (!(A.S[k] > 0.0)) {
+    point_zero<T, M>(A, k, lane);
+    return;
+  }
+  const int t = kk + kw - D;
+  const int nlow = t * (t + 3) / 2;
+  T acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = (T)0;
+  for (int e = lane; e < nlow; e += 32) {
+    int l = 1, rem = e;
+    while (rem >= l + 1) {
+      rem -= l + 1;
+      ++l;
+    }
+    const int lk = rem, lw = l - rem;
+    const int hk = kk - lk, hw = kw - lw;
+    if (hk < 0 || hw < 0) continue;
+    add_pair<T, M>(A, kk, kw, lk, lw, hk, hw, acc);
+  }
+  warp_sum<T, M>(acc);
+  if (lane == 0) {
+    const T *ac = static_cast<const T *>(A.acc);
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] += ac[k * M + m];
+    finalize<T, M>(A, k, acc);
+  }
+}
+
+// One recursion pass.  Levels d = kk + kw: every part of a pair of Pi(k)
+// lies on a lower level.  Each pair {i, j} of a point is assigned to the
+// higher of its two levels, M(i, j) in [ceil(d/2), d).  The pass runs:
+//   levels 0 .. BL-1 directly, one grid barrier per level;
+//   then for D = BL, 2 BL, ...: a bulk phase adding every pair with
+//   M in [D - BL, D) to every point of levels [D, 2D) (M >= d/2 bounds the
+//   points that have any), one barrier, and for each level d of [D, D + BL)
+//   the fringe (pairs with M in [D, d)) and the finalisation of q, with a
+//   barrier after each level.
+// Per plane m (one eps value each)
 //   sum_b2(k) = eps_m^2 dk dw sum_{Pi(k)} g^2 q_i q_j,  q_k = 1/(1 - sum_b2)
-// (b_p^2 = eps^2 g^2 dk dw q_i q_j for |B| = eps g sqrt(S_i S_j S_k)).
-// Items of a point write their sums to scratch slots; the last to take the
-// point's ticket (acq_rel atomic) adds the slots in chunk order, so results
-// do not depend on scheduling.  T = double, M = 1 is the exact pass;
-// T = float, M = 8 evaluates eight eps values at once to locate eps.
+// (b_p^2 = eps^2 g^2 dk dw q_i q_j for |B| = eps g sqrt(S_i S_j S_k)).  Each
+// point's sums are formed by one warp at a time in a fixed order, so the
+// result does not depend on scheduling.  T = double, M = 1 is the exact
+// pass; T = float, M = 8 evaluates eight eps values at once to locate eps.
 template <typename T, int M>
 __global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  const T *G2 = static_cast<const T *>(A.G2);
-  T *q = static_cast<T *>(A.q);
-  const int nw = A.nw;
-  constexpr int UNR = 4;  // independent accumulators per lane
-  // the first item of the next level (items and S are read-only, so they
-  // are fetched before the barrier that ends the current level)
-  int2 nx_it = make_int2(0, 0);
-  double nx_S = 0.0;
-  int nx_ok = 0;
-  {
-    const int i0 = A.lev_off[0], n = A.lev_off[1] - i0;
-    if (gw < n) {
-      nx_it = A.items[i0 + gw];
-      nx_S = A.S[(long long)nx_it.x * nw + (0 - nx_it.x)];
-      nx_ok = 1;
+  unsigned int g = A.gen_base;
+  T *ac = static_cast<T *>(A.acc);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nl * M;
+       i += (long long)gridDim.x * blockDim.x)
+    ac[i] = (T)0;
+  if (!grid_barrier(A.bar, A.abort, g++)) return;
+  const int d0 = min(kRecBL, A.nlev);
+  for (int d = 0; d < d0; ++d) {
+    for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
+      const int2 pt = A.pts[p];
+      point_direct<T, M>(A, pt.x, pt.y, lane);
+    }
+    if (!grid_barrier(A.bar, A.abort, g++)) return;
+  }
+  for (int D = kRecBL; D < A.nlev; D += kRecBL) {
+    const int pe = A.pt_off[min(2 * D, A.nlev)];
+    for (int p = A.pt_off[D] + gw; p < pe; p += nwarps) {
+      const int2 pt = A.pts[p];
+      point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+    }
+    if (!grid_barrier(A.bar, A.abort, g++)) return;
+    const int dend = min(D + kRecBL, A.nlev);
+    for (int d = D; d < dend; ++d) {
+      for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
+        const int2 pt = A.pts[p];
+        point_fringe<T, M>(A, pt.x, pt.y, D, lane);
+      }
+      if (!grid_barrier(A.bar, A.abort, g++)) return;
     }
   }
-  for (int d = 0; d < A.nlev; ++d) {
-    const int lo = max(0, d - nw + 1);
-    const int i0 = A.lev_off[d], n = A.lev_off[d + 1] - i0;
-    for (int w = gw; w < n; w += nwarps) {
-      int2 it;
-      double Sk;
-      if (w == gw && nx_ok) {
-        it = nx_it;
-        Sk = nx_S;
-      } else {
-        it = A.items[i0 + w];
-        Sk = A.S[(long long)it.x * nw + (d - it.x)];
-      }
-      const int kk = it.x, c = it.y, kw = d - kk;
-      const long long k = (long long)kk * nw + kw;
-      if (!(Sk > 0.0)) {
-        if (c == 0 && lane < M) {
-          A.sb2[lane * A.nl + k] = 0.0;
-          q[k * M + lane] = (T)0;
-        }
-        continue;
-      }
-      const int nrow = kk / 2 + 1;
-      const int nch = (nrow + kRecRows - 1) / kRecRows;
-      const int a0 = c * kRecRows;
-      // the item's rows laid end to end: row r covers [P[r], P[r+1])
-      int lo_r[kRecRows], P[kRecRows + 1];
-      P[0] = 0;
-#pragma unroll
-      for (int r = 0; r < kRecRows; ++r) {
-        const int a = a0 + r;
-        int len = 0;
-        lo_r[r] = (a == 0) ? 1 : 0;  // i = 0 takes part in no pair
-        if (a < nrow) {
-          const int lim = (a == kk - a) ? kw / 2 : kw;
-          len = max(0, lim - lo_r[r] + 1);
-        }
-        P[r + 1] = P[r] + len;
-      }
-      const int E = P[kRecRows];
-      T acc[UNR][M];
-#pragma unroll
-      for (int j = 0; j < UNR; ++j)
-#pragma unroll
-        for (int m = 0; m < M; ++m) acc[j][m] = (T)0;
-      for (int e0 = lane; e0 < E; e0 += 32 * UNR) {
-#pragma unroll
-        for (int j = 0; j < UNR; ++j) {
-          const int e = e0 + 32 * j;
-          if (e < E) {
-            const int r = (e >= P[1]) + (e >= P[2]) + (e >= P[3]);
-            const int a = a0 + r;
-            const int pr = r == 0 ? P[0] : r == 1 ? P[1] : r == 2 ? P[2] : P[3];
-            const int lr = r == 0 ? lo_r[0] : r == 1 ? lo_r[1] : r == 2 ? lo_r[2] : lo_r[3];
-            const int iw = lr + (e - pr);
-            const int dd = 2 * iw - kw;
-            const T g2 = G2[(size_t)(kk - 2 * a) * nw + (dd < 0 ? -dd : dd)];
-            T va[M], vb[M];
-            PlaneVec<T, M>::load(q + ((size_t)a * nw + iw) * M, va);
-            PlaneVec<T, M>::load(q + ((size_t)(kk - a) * nw + (kw - iw)) * M, vb);
-#pragma unroll
-            for (int m = 0; m < M; ++m) acc[j][m] = fma(g2, va[m] * vb[m], acc[j][m]);
-          }
-        }
-      }
-      T t[M];
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        t[m] = (T)0;
-#pragma unroll
-        for (int j = 0; j < UNR; ++j) t[m] += acc[j][m];
-        for (int o = 16; o > 0; o >>= 1) t[m] += __shfl_xor_sync(0xffffffffu, t[m], o);
-      }
-      if (lane == 0) {
-        bool fin = true;
-        if (nch > 1) {
-          const int slot = kk - lo;
-          volatile T *ps = static_cast<T *>(A.partial) + ((size_t)slot * A.maxch) * M;
-#pragma unroll
-          for (int m = 0; m < M; ++m) ps[c * M + m] = t[m];
-          cuda::atomic_ref<unsigned int, cuda::thread_scope_device> tk(A.ticket[slot]);
-          fin = tk.fetch_add(1u, cuda::memory_order_acq_rel) == (unsigned int)(nch - 1);
-          if (fin) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) t[m] = (T)0;
-            for (int j = 0; j < nch; ++j)
-#pragma unroll
-              for (int m = 0; m < M; ++m) t[m] += ps[j * M + m];
-            tk.store(0u, cuda::memory_order_relaxed);
-          }
-        }
-        if (fin) {
-#pragma unroll
-          for (int m = 0; m < M; ++m) {
-            const T s2 = (T)A.scal[m] * t[m];
-            A.sb2[m * A.nl + k] = (double)s2;
-            if (s2 < (T)1) {
-              q[k * M + m] = (T)1 / ((T)1 - s2);
-            } else {
-              q[k * M + m] = (T)0;
-              atomicOr(A.err + m, 1);
-            }
-          }
-        }
-      }
-    }
-    if (d + 1 < A.nlev) {
-      const int j0 = A.lev_off[d + 1], m1 = A.lev_off[d + 2] - j0;
-      nx_ok = gw < m1;
-      if (nx_ok) {
-        nx_it = A.items[j0 + gw];
-        nx_S = A.S[(long long)nx_it.x * nw + (d + 1 - nx_it.x)];
-      }
-    }
-    if (!grid_barrier(A.bar, A.abort, A.gen_base + (unsigned int)d)) return;
+}
+
+// Linear pass: L_k = dk dw sum_{Pi(k)} g^2 [S_i > 0][S_j > 0] (q == 1), the
+// small-eps slope of sum_b2 used to bracket eps.  No level dependencies: one
+// warp per point over the rows laid end to end, FP32 terms (only the scale of
+// eps is taken from it), written to sb2 plane 0.
+__global__ void __launch_bounds__(256) k_rec_linear(int nk, int nw, const double *__restrict__ S,
+                                                    const float *__restrict__ G2,
+                                                    double *__restrict__ sb2, double dkdw) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (long long)nk * nw) return;
+  const int kk = (int)(gw / nw), kw = (int)(gw - (long long)kk * nw);
+  const long long k = gw;
+  if (!(S[k] > 0.0)) {
+    if (lane == 0) sb2[k] = 0.0;
+    return;
   }
+  const int W = kw + 1, E = (kk / 2 + 1) * W;
+  float acc = 0.f;
+  for (int e = lane; e < E; e += 32) {
+    const int a = e / W, iw = e - a * W, b = kk - a;
+    const int lim = (a == b) ? kw / 2 : kw;
+    if ((a == 0 && iw == 0) || iw > lim) continue;
+    if (!(S[(size_t)a * nw + iw] > 0.0) || !(S[(size_t)b * nw + (kw - iw)] > 0.0)) continue;
+    const int dw = 2 * iw - kw;
+    acc += G2[(size_t)(kk - 2 * a) * nw + (dw < 0 ? -dw : dw)];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) sb2[k] = dkdw * (double)acc;
 }
 
 }  // namespace srm3
