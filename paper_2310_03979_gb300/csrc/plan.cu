@@ -721,8 +721,10 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   const size_t nl = (size_t)nk * nw;
   const bool f32 = p->precision == SRM3_FP32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  p->ew_off = nw + 32;
-  p->ew_len = 2 * nw + 96 + kTileR + kTileU;
+  // signed envelope table Ews[ew_off + d]; ew_off = 7 (mod 8) puts the
+  // staged kernel's 22-value windows on 16-byte boundaries
+  p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
+  p->ew_len = p->ew_off + nw + 96;
   p->nfft = std::max(p->nx, p->nt);
   SRM3_CUDA(cudaMalloc(&p->sqq, nl * es));
   SRM3_CUDA(cudaMalloc(&p->Pk, nl * es));
@@ -839,9 +841,6 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
   cudaGetDevice(&p->device);
-  // FP32 pair-sum variant: shared-memory staged (default) or register-only
-  // ("SRM3_PAIRSUM_KERNEL=reg"), kept selectable for A/B measurement.
-  if (const char *v = std::getenv("SRM3_PAIRSUM_KERNEL")) p->staged = std::strcmp(v, "reg") != 0;
   int rc = build_plan(p, spectrum, bispectrum);
   if (rc) {
     free_plan(p);

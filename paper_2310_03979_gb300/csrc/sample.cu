@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstring>
 
+#include "pairsum.cuh"
 #include "srm3_internal.cuh"
 
 namespace srm3 {
@@ -97,416 +98,6 @@ __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
       v.y = 0;
     }
     y[((size_t)kk * rowstride + kPad + kw) * SSpad + ss] = v;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// a4 + a5, plain FP64 form: one thread per (k, sheet-sample), exact
-// canonical half (centre row iw <= kw/2), W_ij = c_k Ek[|ik-jk|] Ew[iw-jw]
-// rebuilt per pair:
-//   A = sum_a Ek[kk-2a] sum_iw Ew[2iw-kw] y(a,iw) y(kk-a,kw-iw)
-//   C = P_k y_k + c_k e^{i beta} A
-__global__ void __launch_bounds__(256) k_pairsum_f64(
-    int nk, int nw, int SS, int SSpad, int rowstride, const double2 *__restrict__ y,
-    const double2 *__restrict__ y0, const double *__restrict__ Ek,
-    const double *__restrict__ Ews, int ew_off, const double *__restrict__ Pk,
-    const double *__restrict__ ck, double cb, double sb, double2 *__restrict__ C) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int ss = (int)(gid % SSpad);
-  const long long k = gid / SSpad;
-  if (k >= (long long)nk * nw || ss >= SS) return;
-  const int kk = (int)(k / nw), kw = (int)(k - (long long)kk * nw);
-  const double2 *yl = y + ss;
-  double ar = 0.0, ai = 0.0;
-  for (int a = 0; a <= kk / 2; ++a) {
-    const int b = kk - a;
-    const int lim = (a == b) ? kw / 2 : kw;
-    const double2 *pa = yl + (size_t)(a * rowstride + kPad) * SSpad;
-    const double2 *pb = yl + (size_t)(b * rowstride + kPad + kw) * SSpad;
-    double rr = 0.0, ri = 0.0;
-    for (int iw = 0; iw <= lim; ++iw) {
-      double2 u = pa[(size_t)iw * SSpad];
-      double2 v = pb[-(long long)iw * SSpad];
-      double w = Ews[ew_off + 2 * iw - kw];
-      double pr = u.x * v.x - u.y * v.y;
-      double pi = u.x * v.y + u.y * v.x;
-      rr = fma(w, pr, rr);
-      ri = fma(w, pi, ri);
-    }
-    double f = Ek[kk - 2 * a];
-    ar = fma(f, rr, ar);
-    ai = fma(f, ri, ai);
-  }
-  double2 yk = (k == 0) ? y0[ss] : yl[((size_t)kk * rowstride + kPad + kw) * SSpad];
-  double c = ck[k], P = Pk[k];
-  double pr = c * (ar * cb - ai * sb), pim = c * (ar * sb + ai * cb);
-  C[((size_t)ss * nk + kk) * nw + kw] = make_double2(P * yk.x + pr, P * yk.y + pim);
-}
-
-// ---------------------------------------------------------------------------
-// a4 + a5, tiled FP32 form.  A work unit is (tile, group): the tile is R = 8
-// consecutive outputs kw0..kw0+7 of one lattice row kk, the group 32
-// sheet-samples, one per lane.  Per row pair (a, b = kk - a) the thread
-// forms T_r = sum_iw w(r, iw) y_a[iw] y_b[kw0 + r - iw] in U = 8 wide
-// blocks of iw held in registers (a Toeplitz window of y_b serves all R
-// outputs), then merges rowfac * T_r into a Kahan-compensated accumulator.
-// Rows and blocks run over the full range iw in [0, kw0 + R - 1]; terms
-// with iw > kw read the zero padding of y_b, and the centre row a = b is
-// halved with its diagonal added back: T = (T_full + w y_{kw/2}^2) / 2.
-// TABLE: w(r, iw) streamed from the W table (it already holds c_k and the
-// kappa factor).  Otherwise w = Ew[2 iw - kw] from a shared-memory copy of
-// the envelope table, rowfac = Ek[kk - 2a] and c_k is applied at the end.
-template <bool TABLE>
-__global__ void __launch_bounds__(128) k_pairsum_f32(
-    int nk, int nw, int SS, int SSpad, int rowstride, int G, int nwork,
-    const int2 *__restrict__ order, const long long *__restrict__ toff, int ntw,
-    const float2 *__restrict__ y, const float2 *__restrict__ y0,
-    const float *__restrict__ Ek, const float *__restrict__ Ews_g, int ew_off, int ew_len,
-    const float *__restrict__ W, const float *__restrict__ Pk, const float *__restrict__ ck,
-    float cb, float sb, float2 *__restrict__ C) {
-  constexpr int R = kTileR, U = kTileU;
-  extern __shared__ float ews[];
-  if (!TABLE) {
-    for (int i = threadIdx.x; i < ew_len; i += blockDim.x) ews[i] = Ews_g[i];
-    __syncthreads();
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wu = blockIdx.x * kWarpsPerCta + warp;
-  if (wu >= nwork) return;
-  const int tile = wu / G, grp = wu - tile * G;
-  const int2 tk = order[tile];
-  const int kk = tk.x, kw0 = tk.y;
-  const int ss = grp * 32 + lane;
-  const float2 *yl = y + ss;
-  const size_t SP = (size_t)SSpad;
-  const int L = ((kw0 + R + U - 1) / U) * U;
-  const float *Wt = TABLE ? W + toff[kk * ntw + kw0 / R] : nullptr;
-
-  float2 acc[R], cmp[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    acc[r] = make_float2(0.f, 0.f);
-    cmp[r] = make_float2(0.f, 0.f);
-  }
-  const int nrow = kk / 2 + 1;
-  const int iw_last = kw0 + R - 1;
-  for (int a = 0; a < nrow; ++a) {
-    const int b = kk - a;
-    const float2 *pa = yl + (size_t)(a * rowstride + kPad) * SP;
-    const float2 *pb = yl + (size_t)(b * rowstride + kPad) * SP;
-    const float *Wa = TABLE ? Wt + (size_t)a * R * L : nullptr;
-    float2 T[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) T[r] = make_float2(0.f, 0.f);
-    for (int iw0 = 0; iw0 <= iw_last; iw0 += U) {
-      float2 ya[U], yb[R + U - 1];
-#pragma unroll
-      for (int u = 0; u < U; ++u) ya[u] = pa[(size_t)(iw0 + u) * SP];
-      const int jlo = kw0 - iw0 - (U - 1);
-#pragma unroll
-      for (int v = 0; v < R + U - 1; ++v) yb[v] = pb[(long long)(jlo + v) * (long long)SP];
-      if (TABLE) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float4 w0 = *reinterpret_cast<const float4 *>(Wa + r * L + iw0);
-          const float4 w1 = *reinterpret_cast<const float4 *>(Wa + r * L + iw0 + 4);
-          const float w[U] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const float2 p = ya[u], q = yb[r - u + U - 1];
-            const float pr = fmaf(p.x, q.x, -p.y * q.y);
-            const float pi = fmaf(p.x, q.y, p.y * q.x);
-            T[r].x = fmaf(w[u], pr, T[r].x);
-            T[r].y = fmaf(w[u], pi, T[r].y);
-          }
-        }
-      } else {
-        float e[2 * U + R - 2];
-        const int base = ew_off + 2 * iw0 - kw0 - (R - 1);
-#pragma unroll
-        for (int t = 0; t < 2 * U + R - 2; ++t) e[t] = ews[base + t];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const float w = e[2 * u - r + R - 1];
-            const float2 p = ya[u], q = yb[r - u + U - 1];
-            const float pr = fmaf(p.x, q.x, -p.y * q.y);
-            const float pi = fmaf(p.x, q.y, p.y * q.x);
-            T[r].x = fmaf(w, pr, T[r].x);
-            T[r].y = fmaf(w, pi, T[r].y);
-          }
-        }
-      }
-    }
-    if (a == b) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int kw = kw0 + r;
-        if ((kw & 1) == 0) {
-          const float2 h = pa[(size_t)(kw >> 1) * SP];
-          const float w0 = TABLE ? Wa[r * L + (kw >> 1)] : ews[ew_off];
-          T[r].x = 0.5f * (T[r].x + w0 * (h.x * h.x - h.y * h.y));
-          T[r].y = 0.5f * (T[r].y + w0 * (2.f * h.x * h.y));
-        } else {
-          T[r].x *= 0.5f;
-          T[r].y *= 0.5f;
-        }
-      }
-    }
-    const float rowfac = TABLE ? 1.0f : Ek[kk - 2 * a];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      // Kahan merge of the row partial into the running sum
-      float yx = fmaf(rowfac, T[r].x, -cmp[r].x);
-      float tx = acc[r].x + yx;
-      cmp[r].x = (tx - acc[r].x) - yx;
-      acc[r].x = tx;
-      float yy = fmaf(rowfac, T[r].y, -cmp[r].y);
-      float ty = acc[r].y + yy;
-      cmp[r].y = (ty - acc[r].y) - yy;
-      acc[r].y = ty;
-    }
-  }
-  if (ss >= SS) return;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int kw = kw0 + r;
-    if (kw >= nw) break;
-    const int k = kk * nw + kw;
-    const float2 yk = (k == 0) ? y0[ss] : yl[((size_t)kk * rowstride + kPad + kw) * SP];
-    const float ar = acc[r].x - cmp[r].x, ai = acc[r].y - cmp[r].y;
-    const float cf = TABLE ? 1.0f : ck[k];
-    const float P = Pk[k];
-    float2 out;
-    out.x = fmaf(P, yk.x, cf * (ar * cb - ai * sb));
-    out.y = fmaf(P, yk.y, cf * (ar * sb + ai * cb));
-    C[((size_t)ss * nk + kk) * nw + kw] = out;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// a4 + a5, tiled FP32 form with shared-memory staging.  A CTA (4 warps)
-// takes a super-tile of 32 outputs kws0..kws0+31 of lattice row kk for one
-// group of 32 sheet-samples; warp w owns the 8-output tile kws0 + 8w and
-// each lane one sheet-sample, with the same R x U register blocking as
-// k_pairsum_f32.  For each row pair (a, kk - a) the omega range
-// [0, kws0 + 31] is walked in chunks of CH = 32: the chunk's y_a rows, the
-// y_b window that all four tiles need (CH + 31 rows) and, for the table
-// path, the four tiles' W rows are copied global -> shared with 16-byte
-// cp.async (zero-filled outside the lattice), double-buffered so that the
-// copy of chunk t+1 overlaps the arithmetic on chunk t.
-namespace staged {
-constexpr int R = kTileR, U = kTileU, ST = kWarpsPerCta, SW = ST * R, CH = 32;
-constexpr int YB_ROWS = CH + SW - 1;
-constexpr int STAGE_Y = (CH + YB_ROWS) * 32;  // float2 entries per stage
-constexpr int STAGE_W = ST * R * CH;          // floats per stage
-}  // namespace staged
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
-template <bool TABLE>
-__global__ void __launch_bounds__(128, 3) k_pairsum_f32s(
-    int nk, int nw, int SS, int SSpad, int rowstride, int G, const int2 *__restrict__ order,
-    const long long *__restrict__ toff, int ntw, const float2 *__restrict__ y,
-    const float2 *__restrict__ y0, const float *__restrict__ Ek,
-    const float *__restrict__ Ews_g, int ew_off, int ew_len, const float *__restrict__ W,
-    const float *__restrict__ Pk, const float *__restrict__ ck, float cb, float sb,
-    float2 *__restrict__ C) {
-  using namespace staged;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *sy = reinterpret_cast<float2 *>(smem_raw);                 // [2][STAGE_Y]
-  float *sw = reinterpret_cast<float *>(sy + 2 * STAGE_Y);           // [2][STAGE_W] (table)
-  float *ews = TABLE ? nullptr : reinterpret_cast<float *>(sy + 2 * STAGE_Y);  // envelope
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (!TABLE) {
-    for (int i = tid; i < ew_len; i += blockDim.x) ews[i] = Ews_g[i];
-  }
-  const int grp = blockIdx.x % G;
-  const int2 tk = order[blockIdx.x / G];
-  const int kk = tk.x, kws0 = tk.y;
-  const int kw0 = kws0 + R * warp;  // this warp's tile
-  const bool tile_ok = kw0 < nw;
-  const int ss = grp * 32 + lane;
-  const size_t SP = (size_t)SSpad;
-  const float2 *ybase = y + (size_t)grp * 32;  // lane 0 of the group
-  const int nrow = kk / 2 + 1;
-  const int nch = (kws0 + SW + CH - 1) / CH;
-  const int nitems = nrow * nch;
-
-  // W geometry (table path): this warp's tile, and the two tiles whose rows
-  // this thread copies (q = tid and tid + 128 cover tiles tid/64 and +2).
-  auto tile_L = [&](int k0) { return ((k0 + R + U - 1) / U) * U; };
-  auto tile_base = [&](int k0) -> long long {
-    return (TABLE && k0 < nw) ? toff[kk * ntw + k0 / R] : -1;
-  };
-  const int my_L = tile_L(kw0);
-  const long long my_base = tile_base(kw0);
-  const int cp_s0 = tid >> 6;
-  const int cp_L0 = tile_L(kws0 + R * cp_s0), cp_L1 = tile_L(kws0 + R * (cp_s0 + 2));
-  const long long cp_b0 = tile_base(kws0 + R * cp_s0), cp_b1 = tile_base(kws0 + R * (cp_s0 + 2));
-
-  auto issue = [&](int item, int stage) {
-    if (item < nitems) {
-      const int a = item / nch, c = item - (item / nch) * nch;
-      const int b = kk - a, i0 = c * CH;
-      float2 *dya = sy + stage * STAGE_Y;
-      float2 *dyb = dya + CH * 32;
-      const float2 *ra = ybase + (size_t)(a * rowstride + kPad) * SP;
-      const float2 *rb = ybase + (size_t)(b * rowstride + kPad) * SP;
-      for (int q = tid; q < CH * 16; q += 128) {  // 16 x 16 B per 32-lane row
-        const int row = q >> 4, part = q & 15;
-        const int iw = i0 + row;
-        const bool v = iw < nw;
-        cp_async16(dya + row * 32 + part * 2, ra + (size_t)(v ? iw : 0) * SP + part * 2, v);
-      }
-      const int jlo = kws0 - i0 - CH + 1;
-      for (int q = tid; q < YB_ROWS * 16; q += 128) {
-        const int row = q >> 4, part = q & 15;
-        const int jw = jlo + row;
-        const bool v = jw >= 0 && jw < nw;
-        cp_async16(dyb + row * 32 + part * 2, rb + (size_t)(v ? jw : 0) * SP + part * 2, v);
-      }
-      if (TABLE) {
-        static_assert(ST * R * (CH / 4) == 256, "two W copies per thread");
-        float *dw = sw + stage * STAGE_W;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const int q = tid + 128 * j;
-          const int s = q >> 6, rem = q & 63;
-          const int r = rem >> 3, c4 = rem & 7;
-          const int iw = i0 + 4 * c4;
-          const long long wb = j ? cp_b1 : cp_b0;
-          const int wl = j ? cp_L1 : cp_L0;
-          const bool v = wb >= 0 && iw < wl;
-          const float *src = v ? W + wb + ((long long)a * R + r) * wl + iw : W;
-          cp_async16(dw + (s * R + r) * CH + 4 * c4, src, v);
-        }
-      }
-    }
-    cp_async_commit();
-  };
-
-  float2 acc[R], cmp[R], T[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    acc[r] = make_float2(0.f, 0.f);
-    cmp[r] = make_float2(0.f, 0.f);
-    T[r] = make_float2(0.f, 0.f);
-  }
-
-  issue(0, 0);
-  issue(1, 1);
-  for (int t = 0; t < nitems; ++t) {
-    const int stage = t & 1;
-    const int a = t / nch, c = t - (t / nch) * nch;
-    const int i0 = c * CH;
-    cp_async_wait1();
-    __syncthreads();
-    if (tile_ok) {
-      const float2 *sya = sy + stage * STAGE_Y;
-      const float2 *syb = sya + CH * 32;
-      const float *swt = sw + stage * STAGE_W + warp * R * CH;
-#pragma unroll 1
-      for (int ib = 0; ib < CH; ib += U) {
-        if (i0 + ib > kw0 + R - 1) break;
-        float2 ya[U], yb[R + U - 1];
-#pragma unroll
-        for (int u = 0; u < U; ++u) ya[u] = sya[(ib + u) * 32 + lane];
-        const int r0 = R * warp - ib + (CH - 1) - (U - 1);  // window row of v = 0
-#pragma unroll
-        for (int v = 0; v < R + U - 1; ++v) yb[v] = syb[(r0 + v) * 32 + lane];
-        if (TABLE) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float4 w0 = *reinterpret_cast<const float4 *>(swt + r * CH + ib);
-            const float4 w1 = *reinterpret_cast<const float4 *>(swt + r * CH + ib + 4);
-            const float w[U] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const float2 p = ya[u], q = yb[r - u + U - 1];
-              const float pr = fmaf(p.x, q.x, -p.y * q.y);
-              const float pi = fmaf(p.x, q.y, p.y * q.x);
-              T[r].x = fmaf(w[u], pr, T[r].x);
-              T[r].y = fmaf(w[u], pi, T[r].y);
-            }
-          }
-        } else {
-          float e[2 * U + R - 2];
-          const int base = ew_off + 2 * (i0 + ib) - kw0 - (R - 1);
-#pragma unroll
-          for (int q = 0; q < 2 * U + R - 2; ++q) e[q] = ews[base + q];
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const float w = e[2 * u - r + R - 1];
-              const float2 p = ya[u], q = yb[r - u + U - 1];
-              const float pr = fmaf(p.x, q.x, -p.y * q.y);
-              const float pi = fmaf(p.x, q.y, p.y * q.x);
-              T[r].x = fmaf(w, pr, T[r].x);
-              T[r].y = fmaf(w, pi, T[r].y);
-            }
-          }
-        }
-      }
-      if (c == nch - 1) {  // row pair complete: centre-row halving and merge
-        const int b = kk - a;
-        if (a == b) {
-          const float2 *pa = y + ss + (size_t)(a * rowstride + kPad) * SP;
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int kw = kw0 + r;
-            if ((kw & 1) == 0 && kw < nw) {
-              const float2 h = pa[(size_t)(kw >> 1) * SP];
-              const float w0 =
-                  TABLE ? W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)] : ews[ew_off];
-              T[r].x = 0.5f * (T[r].x + w0 * (h.x * h.x - h.y * h.y));
-              T[r].y = 0.5f * (T[r].y + w0 * (2.f * h.x * h.y));
-            } else {
-              T[r].x *= 0.5f;
-              T[r].y *= 0.5f;
-            }
-          }
-        }
-        const float rowfac = TABLE ? 1.0f : Ek[kk - 2 * a];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          float yx = fmaf(rowfac, T[r].x, -cmp[r].x);
-          float tx = acc[r].x + yx;
-          cmp[r].x = (tx - acc[r].x) - yx;
-          acc[r].x = tx;
-          float yy = fmaf(rowfac, T[r].y, -cmp[r].y);
-          float ty = acc[r].y + yy;
-          cmp[r].y = (ty - acc[r].y) - yy;
-          acc[r].y = ty;
-          T[r] = make_float2(0.f, 0.f);
-        }
-      }
-    }
-    __syncthreads();
-    issue(t + 2, stage);
-  }
-  if (!tile_ok || ss >= SS) return;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int kw = kw0 + r;
-    if (kw >= nw) break;
-    const int k = kk * nw + kw;
-    const float2 yk = (k == 0) ? y0[ss] : y[ss + ((size_t)kk * rowstride + kPad + kw) * SP];
-    const float ar = acc[r].x - cmp[r].x, ai = acc[r].y - cmp[r].y;
-    const float cf = TABLE ? 1.0f : ck[k];
-    const float P = Pk[k];
-    float2 out;
-    out.x = fmaf(P, yk.x, cf * (ar * cb - ai * sb));
-    out.y = fmaf(P, yk.y, cf * (ar * sb + ai * cb));
-    C[((size_t)ss * nk + kk) * nw + kw] = out;
   }
 }
 
@@ -671,7 +262,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
         p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
         (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
         (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
-  } else if (p->staged) {
+  } else {
     using namespace staged;
     const int G = sp / 32;
     const int blocks = p->nsuper * G;
@@ -692,27 +283,6 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_pairsum_f32s<false><<<blocks, 32 * kWarpsPerCta, smem, p->stream>>>(
           p->nk, p->nw, SS, sp, p->rowstride, G, p->super_order, p->tile_off, p->ntw,
-          (const float2 *)p->y, (const float2 *)p->y0, (const float *)p->Ek,
-          (const float *)p->Ews, p->ew_off, p->ew_len, nullptr, (const float *)p->Pk,
-          (const float *)p->ck, cbf, sbf, (float2 *)C_out);
-    }
-  } else {
-    const int G = sp / 32;
-    const int nwork = p->ntiles * G;
-    const int blocks = cdiv(nwork, kWarpsPerCta);
-    if (p->storage == SRM3_STORAGE_TABLE) {
-      k_pairsum_f32<true><<<blocks, 32 * kWarpsPerCta, 0, p->stream>>>(
-          p->nk, p->nw, SS, sp, p->rowstride, G, nwork, p->tile_order, p->tile_off, p->ntw,
-          (const float2 *)p->y, (const float2 *)p->y0, (const float *)p->Ek,
-          (const float *)p->Ews, p->ew_off, p->ew_len, p->W, (const float *)p->Pk,
-          (const float *)p->ck, cbf, sbf, (float2 *)C_out);
-    } else {
-      const size_t smem = (size_t)p->ew_len * sizeof(float);
-      if (smem > 48 * 1024)
-        SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_pairsum_f32<false><<<blocks, 32 * kWarpsPerCta, smem, p->stream>>>(
-          p->nk, p->nw, SS, sp, p->rowstride, G, nwork, p->tile_order, p->tile_off, p->ntw,
           (const float2 *)p->y, (const float2 *)p->y0, (const float *)p->Ek,
           (const float *)p->Ews, p->ew_off, p->ew_len, nullptr, (const float *)p->Pk,
           (const float *)p->ck, cbf, sbf, (float2 *)C_out);

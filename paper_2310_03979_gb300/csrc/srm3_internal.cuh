@@ -92,7 +92,6 @@ struct srm3_plan {
   int2 *tile_order = nullptr;
   int nsuper = 0;
   int2 *super_order = nullptr;    // 32-wide super-tiles (staged kernel)
-  int staged = 1;                 // FP32 pair sum: 1 staged kernel, 0 register-only
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
   float *W = nullptr;             // W table (STORAGE_TABLE)
 
