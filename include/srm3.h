@@ -177,6 +177,57 @@ int srm3_coeffs(srm3_plan *plan, const uint64_t *seeds, int n, void *C);
  * device buffer u[n][n_x][n_t].  Async. */
 int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
 
+/* Capacity of the fixed scratch behind srm3_field_from_coeffs_noalloc:
+ * 16 MiB per device. */
+#define SRM3_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* srm3_field_from_coeffs that allocates no device memory.  The paper has no
+ * counterpart: this is a library service, not part of the method.
+ *
+ * Who needs it: a caller that may not allocate device memory while it
+ * computes fields.  Two common cases:
+ *  - a process whose device memory is already held by another allocator
+ *    (for instance a framework's caching allocator that reserved most of
+ *    HBM), where a fresh cudaMalloc can fail in the middle of a request;
+ *  - a latency-bound serving loop: cudaMalloc and cudaFree can synchronise
+ *    the device and stall other streams, which shows up as tail latency.
+ * srm3_field_from_coeffs grows the plan's workspace with cudaMalloc on first
+ * use (and when n grows); this entry point never calls cudaMalloc,
+ * cudaMallocAsync, cudaFree or any other allocating routine.  It neither
+ * uses nor grows the plan's workspace.
+ *
+ * Arguments, layouts and result are those of srm3_field_from_coeffs: C is a
+ * device buffer C[n][2][n_kappa][n_omega] of interleaved (re, im) values in
+ * the plan's precision; out is a device buffer u[n][n_x][n_t].  The same
+ * kernels run in the same order, so the values are those of
+ * srm3_field_from_coeffs.  Asynchronous on the plan's stream.
+ *
+ * Scratch: the intermediate of the two FFT stages, n_kappa * n_t complex
+ * values per coefficient set (8 bytes each in FP32, 16 in FP64), lives in a
+ * fixed array of SRM3_NOALLOC_SCRATCH_BYTES that the library defines in
+ * device memory, one per device.  Sets are transformed in groups that fit.
+ * Nothing in it needs to start at zero: the first stage writes every entry
+ * that the second stage reads.
+ *
+ * Set-up: the first call on each device looks up the array's address
+ * (cudaGetSymbolAddress, with the plan's device current), which can load
+ * the library's device code onto that device; later calls reuse the cached
+ * address.  Make that first call before any stream capture begins.  The
+ * plan's device is made current for the call and the previous current
+ * device is restored before return.
+ *
+ * Concurrency: the array is shared by every plan and stream on a device.
+ * Calls whose work overlaps on one device (on different streams, or from
+ * host threads that do not order their calls) race on it and produce wrong
+ * fields.  Calls issued one after another on the same stream are safe.
+ *
+ * Errors: SRM3_ERR_INVALID_ARG for a NULL plan, n < 0, NULL buffers with
+ * n > 0, or a plan whose one coefficient set needs more scratch than
+ * SRM3_NOALLOC_SCRATCH_BYTES (n_kappa * n_t * 8 bytes in FP32, * 16 in FP64);
+ * SRM3_ERR_CUDA when the address lookup or a launch fails.  The message is
+ * in srm3_last_error(). */
+int srm3_field_from_coeffs_noalloc(srm3_plan *plan, const void *C, int n, void *out);
+
 /* Stage timings from CUDA events recorded on the plan's stream.  The
  * recursion and W-table figures cover the last plan build (always
  * recorded); the sampling stages accumulate over srm3_sample /

@@ -1,0 +1,115 @@
+// fft.cuh - the hand-written 2-D inverse FFT of the SRM3 field (t stage, then
+// x stage), shared by the sampling entry points and the no-allocation
+// transform.  Internal linkage: every translation unit that includes it
+// gets its own copy of the kernels.
+#pragma once
+
+#include "srm3_internal.cuh"
+
+namespace srm3 {
+namespace {
+
+// a6: inverse transform.  u[mx][mt] = Re sum_kk e^{2 pi i kk mx / nx}
+//   sum_m F[kk][m] e^{2 pi i m mt / nt}, F[kk][kw] = C^+_k,
+//   F[kk][(nt - kw) mod nt] += C^-_k (FFT form, Sec. 4.3).
+// Radix-2 decimation in time in shared memory, input in bit-reversed order,
+// twiddles e^{+2 pi i j / nfft} from a table.
+template <typename T2>
+__device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+  T2 r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+template <typename T2>
+__device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ tw,
+                           int log2nfft) {
+  const int n = 1 << log2n;
+  const int halfn = n >> 1;
+  const int total = ncols * halfn;
+  for (int s = 1; s <= log2n; ++s) {
+    const int half = 1 << (s - 1);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int col = t >> (log2n - 1);
+      const int bf = t & (halfn - 1);
+      const int grp = bf >> (s - 1);
+      const int j = bf & (half - 1);
+      const int i0 = col * n + grp * 2 * half + j;
+      const int i1 = i0 + half;
+      const T2 w = tw[j << (log2nfft - s)];
+      const T2 x0 = buf[i0];
+      const T2 x1 = cmul(buf[i1], w);
+      T2 o0, o1;
+      o0.x = x0.x + x1.x;
+      o0.y = x0.y + x1.y;
+      o1.x = x0.x - x1.x;
+      o1.y = x0.y - x1.y;
+      buf[i0] = o0;
+      buf[i1] = o1;
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int brev(int m, int log2n) {
+  return (int)(__brev((unsigned)m) >> (32 - log2n));
+}
+
+template <typename T2>
+__global__ void k_fft_t(int nk, int nw, int nt, int log2nt, int log2nfft,
+                        const T2 *__restrict__ C, const T2 *__restrict__ tw, T2 *__restrict__ H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2 *buf = reinterpret_cast<T2 *>(smem_raw);
+  const int kk = blockIdx.x, n = blockIdx.y;
+  for (int m = threadIdx.x; m < nt; m += blockDim.x) {
+    buf[m].x = 0;
+    buf[m].y = 0;
+  }
+  __syncthreads();
+  const T2 *Cp = C + ((size_t)(2 * n) * nk + kk) * nw;
+  const T2 *Cm = C + ((size_t)(2 * n + 1) * nk + kk) * nw;
+  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) buf[brev(kw, log2nt)] = Cp[kw];
+  __syncthreads();
+  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) {
+    const int m = kw == 0 ? 0 : nt - kw;
+    const int pos = brev(m, log2nt);
+    T2 v = buf[pos];
+    const T2 c = Cm[kw];
+    v.x += c.x;
+    v.y += c.y;
+    buf[pos] = v;
+  }
+  __syncthreads();
+  fft_stages(buf, 1, log2nt, tw, log2nfft);
+  T2 *Hrow = H + ((size_t)n * nk + kk) * nt;
+  for (int m = threadIdx.x; m < nt; m += blockDim.x) Hrow[m] = buf[m];
+}
+
+template <typename T, typename T2>
+__global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int log2nfft, int TC,
+                        const T2 *__restrict__ H, const T2 *__restrict__ tw, T *__restrict__ u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T2 *buf = reinterpret_cast<T2 *>(smem_raw);
+  const int mt0 = blockIdx.x * TC, n = blockIdx.y;
+  for (int i = threadIdx.x; i < TC * nx; i += blockDim.x) {
+    buf[i].x = 0;
+    buf[i].y = 0;
+  }
+  __syncthreads();
+  const T2 *Hn = H + (size_t)n * nk * nt + mt0;
+  for (int idx = threadIdx.x; idx < nk * TC; idx += blockDim.x) {
+    const int kk = idx / TC, c = idx - kk * TC;
+    buf[c * nx + brev(kk, log2nx)] = Hn[(size_t)kk * nt + c];
+  }
+  __syncthreads();
+  fft_stages(buf, TC, log2nx, tw, log2nfft);
+  T *un = u + (size_t)n * nx * nt + mt0;
+  for (int idx = threadIdx.x; idx < nx * TC; idx += blockDim.x) {
+    const int mx = idx / TC, c = idx - mx * TC;
+    un[(size_t)mx * nt + c] = buf[c * nx + mx].x;
+  }
+}
+
+}  // namespace
+}  // namespace srm3

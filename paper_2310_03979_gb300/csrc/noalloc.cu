@@ -1,0 +1,127 @@
+// noalloc.cu - srm3_field_from_coeffs_noalloc: the transform stage with its
+// intermediate held in a fixed device array of the library instead of plan
+// workspace, for callers that may not allocate device memory.  The paper has
+// no counterpart; the kernels are those of fft.cuh.
+#include <algorithm>
+#include <mutex>
+
+#include "fft.cuh"
+#include "srm3_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = SRM3_NOALLOC_SCRATCH_BYTES;
+constexpr int kMaxDevices = 64;
+
+}  // namespace
+
+// The t-stage rows of one group of coefficient sets, [set][kk][mt] complex.
+// Never read before the t stage of the same call has written it.
+static __device__ __align__(256) unsigned char srm3_noalloc_scratch[kScratchBytes];
+
+namespace srm3 {
+namespace {
+
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of srm3_noalloc_scratch on `dev`, which is the current
+// device.  Looked up once per device, then cached.
+int scratch_address(int dev, void **addr) {
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(SRM3_ERR_NOT_SUPPORTED, "srm3_field_from_coeffs_noalloc: device ordinal " +
+                                            std::to_string(dev) + " is beyond the " +
+                                            std::to_string(kMaxDevices) + " it caches");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void *a = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&a, srm3_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(srm3_noalloc_scratch)");
+    g_scratch_addr[dev] = a;
+  }
+  *addr = g_scratch_addr[dev];
+  return SRM3_OK;
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool switched = false;
+  int enter(int dev) {
+    SRM3_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) {
+      SRM3_CUDA(cudaSetDevice(dev));
+      switched = true;
+    }
+    return SRM3_OK;
+  }
+  ~DeviceGuard() {
+    if (switched) cudaSetDevice(prev);
+  }
+};
+
+// The two FFT stages for n sets with the intermediate H supplied by the
+// caller (n * nk * nt entries).
+template <typename T, typename T2>
+int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
+  const int log2nfft = ilog2_exact(p->nfft);
+  const size_t e2 = sizeof(T2);
+  const size_t smem_t = (size_t)p->nt * e2;
+  int TC = 16;
+  while (TC > 1 && ((size_t)TC * p->nx * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
+  const size_t smem_x = (size_t)TC * p->nx * e2;
+  const int lim = 200 * 1024;
+  SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt,
+                                                          log2nfft, C, (const T2 *)p->tw, H);
+  SRM3_CUDA(cudaGetLastError());
+  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, p->stream>>>(
+      p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, H, (const T2 *)p->tw, out);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
+template <typename T, typename T2>
+int field_noalloc(srm3_plan *p, const void *C, int n, void *out, void *scratch) {
+  const size_t perH = (size_t)p->nk * p->nt * sizeof(T2);
+  const size_t perC = (size_t)2 * p->nk * p->nw * sizeof(T2);
+  const size_t perU = (size_t)p->nx * p->nt * sizeof(T);
+  // gridDim.y carries the set index: at most 65535 sets per launch.
+  const int group = (int)std::min<size_t>(kScratchBytes / perH, 65535);
+  for (int s0 = 0; s0 < n; s0 += group) {
+    const int m = std::min(group, n - s0);
+    const int rc = transform_with<T, T2>(
+        p, reinterpret_cast<const T2 *>((const char *)C + (size_t)s0 * perC), m,
+        reinterpret_cast<T *>((char *)out + (size_t)s0 * perU), reinterpret_cast<T2 *>(scratch));
+    if (rc) return rc;
+  }
+  return SRM3_OK;
+}
+
+}  // namespace
+}  // namespace srm3
+
+using namespace srm3;
+
+SRM3_API int srm3_field_from_coeffs_noalloc(srm3_plan *plan, const void *C, int n, void *out) {
+  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
+  if (n < 0 || (n > 0 && (!C || !out))) return fail(SRM3_ERR_INVALID_ARG, "bad C/out/n");
+  const size_t e2 = plan->precision == SRM3_FP32 ? sizeof(float2) : sizeof(double2);
+  const size_t perH = (size_t)plan->nk * plan->nt * e2;
+  if (perH > kScratchBytes)
+    return fail(SRM3_ERR_INVALID_ARG,
+                "srm3_field_from_coeffs_noalloc: one coefficient set needs " +
+                    std::to_string(perH) + " bytes of scratch (n_kappa * n_t complex values), "
+                    "more than the SRM3_NOALLOC_SCRATCH_BYTES = " +
+                    std::to_string(kScratchBytes) + " it has; use srm3_field_from_coeffs");
+  if (n == 0) return SRM3_OK;
+  DeviceGuard guard;
+  int rc = guard.enter(plan->device);
+  if (rc) return rc;
+  void *scratch = nullptr;
+  if ((rc = scratch_address(plan->device, &scratch))) return rc;
+  if (plan->precision == SRM3_FP32) return field_noalloc<float, float2>(plan, C, n, out, scratch);
+  return field_noalloc<double, double2>(plan, C, n, out, scratch);
+}

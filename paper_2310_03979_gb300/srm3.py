@@ -32,8 +32,9 @@ EXPORTED = [
     "srm3_plan_create", "srm3_sample", "srm3_sample_host", "srm3_destroy", "srm3_sync",
     "srm3_set_stream", "srm3_last_error", "srm3_plan_info", "srm3_plan_tables",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
-    "srm3_get_timings",
+    "srm3_get_timings", "srm3_field_from_coeffs_noalloc",
 ]
+SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class srm3_spectrum(ctypes.Structure):
@@ -111,6 +112,7 @@ def load(build_if_needed: bool = True):
     lib.srm3_phase_words.argtypes = [vp, u64p, i32, vp]
     lib.srm3_coeffs.argtypes = [vp, u64p, i32, vp]
     lib.srm3_field_from_coeffs.argtypes = [vp, vp, i32, vp]
+    lib.srm3_field_from_coeffs_noalloc.argtypes = [vp, vp, i32, vp]
     lib.srm3_enable_timing.argtypes = [vp, i32]
     lib.srm3_get_timings.argtypes = [vp, ctypes.POINTER(srm3_timings), i32]
     _lib = lib
@@ -191,6 +193,14 @@ def coeffs(plan, seeds, n, C_ptr: int):
 def field_from_coeffs(plan, C_ptr: int, n, out_ptr: int):
     _check(load().srm3_field_from_coeffs(plan, ctypes.c_void_p(C_ptr), int(n),
                                          ctypes.c_void_p(out_ptr)))
+
+
+def field_from_coeffs_noalloc(plan, C_ptr: int, n, out_ptr: int):
+    """The transform through the entry point that allocates no device memory
+    (its scratch is a fixed 16 MiB array per device; calls overlapping on one
+    device race on it)."""
+    _check(load().srm3_field_from_coeffs_noalloc(plan, ctypes.c_void_p(C_ptr), int(n),
+                                                 ctypes.c_void_p(out_ptr)))
 
 
 def enable_timing(plan, on: bool):

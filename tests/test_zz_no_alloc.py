@@ -1,0 +1,95 @@
+"""srm3_field_from_coeffs_noalloc: the transform whose scratch is a fixed
+16 MiB device array of the library instead of plan workspace.
+
+Its fields are compared with those of srm3_field_from_coeffs (the existing
+entry point) on two calls in a row.  Both run the same kernels in the same
+order, so the comparison is to within 1e-12 of max|u| (FP64) and 1e-6 of
+max|u| (FP32), well inside the field tolerances of the parity tests.  The
+file is named to be collected last, so that it runs both alone in a fresh
+process and after every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2310_03979_gb300 import srm3
+from paper_2310_03979_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+TOL = {"fp32": 1e-6, "fp64": 1e-12}
+
+
+def test_noalloc_rejects_bad_arguments():
+    lib = srm3.load()
+    assert lib.srm3_field_from_coeffs_noalloc(None, None, 0, None) == -1
+    assert b"plan is NULL" in lib.srm3_last_error()
+
+
+def _noalloc(p, C, out):
+    srm3.field_from_coeffs_noalloc(p.handle, C.data_ptr(), C.shape[0], out.data_ptr())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,storage", [("fp32", "table"), ("fp64", "recompute")])
+def test_noalloc_matches_field_from_coeffs(precision, storage):
+    wl = W.small_case(nk=24, nw=37, nx=64, nt=128, precision=precision, storage=storage)
+    seeds = [1, 2, 3, 77, 2 ** 63 + 9]
+    with srm3.Plan.create(wl) as p:
+        C = p.coeffs(seeds)
+        ref = p.field_from_coeffs(C)
+        torch.cuda.synchronize()
+        scale = ref.abs().max().item()
+        assert scale > 0
+        for _ in range(2):  # two calls in a row, each into a NaN-filled buffer
+            out = torch.full_like(ref, float("nan"))
+            _noalloc(p, C, out)
+            torch.cuda.synchronize()
+            assert torch.isfinite(out).all()
+            assert (out - ref).abs().max().item() <= TOL[precision] * scale
+
+
+@pytest.mark.gpu
+def test_noalloc_several_groups_and_no_device_allocation():
+    """Enough sets that the scratch is reused across groups (24 * 128
+    complex FP32 values per set: 682 sets per group), and free device
+    memory unchanged by a call once the first call has done its set-up."""
+    wl = W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp32")
+    n = 700
+    g = torch.Generator().manual_seed(11)
+    C = torch.randn((n, 2, 24, 37, 2), generator=g, dtype=torch.float32).cuda()
+    with srm3.Plan.create(wl, eps=0.0) as p:
+        ref = p.field_from_coeffs(C)
+        out = torch.full_like(ref, float("nan"))
+        _noalloc(p, C, out)  # set-up: scratch address looked up on this device
+        torch.cuda.synchronize()
+        scale = ref.abs().max().item()
+        assert (out - ref).abs().max().item() <= TOL["fp32"] * scale
+        out.fill_(float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        _noalloc(p, C, out)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0
+        assert torch.isfinite(out).all()
+        assert (out - ref).abs().max().item() <= TOL["fp32"] * scale
+
+
+@pytest.mark.gpu
+def test_noalloc_rejects_plan_beyond_scratch():
+    # 257 * 8192 complex FP64 values per set = 33.7 MB > 16 MiB of scratch.
+    wl = W.small_case(nk=257, nw=16, nx=512, nt=8192, precision="fp64")
+    with srm3.Plan.create(wl, eps=0.0) as p:
+        C = torch.zeros((1, 2, 257, 16, 2), dtype=torch.float64, device="cuda")
+        out = torch.zeros((1, 512, 8192), dtype=torch.float64, device="cuda")
+        rc = srm3.load().srm3_field_from_coeffs_noalloc(
+            p.handle, ctypes.c_void_p(C.data_ptr()), 1, ctypes.c_void_p(out.data_ptr()))
+        assert rc == -1  # SRM3_ERR_INVALID_ARG
+        assert b"SRM3_NOALLOC_SCRATCH_BYTES" in srm3.load().srm3_last_error()
+        # n = 0 is still a no-op that succeeds for a plan within the limit
+        small = W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp64")
+        with srm3.Plan.create(small, eps=0.0) as q:
+            assert srm3.load().srm3_field_from_coeffs_noalloc(q.handle, None, 0, None) == 0
+        assert np.isfinite(out.cpu().numpy()).all()
