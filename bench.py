@@ -286,8 +286,8 @@ def main():
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "k_pairsum_f32s<table>" if info.storage == 1 else
-                               "k_pairsum_f32s<recompute>",
+                     "kernel": "k_pairsum_f32p<table>" if info.storage == 1 else
+                               "k_pairsum_f32p<recompute>",
                      "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 "
                                     f"flop x {sm_max:.0f} MHz (max SM clock of "
                                     "MEASURED_PEAKS.json); 10 flop per pair-term"},

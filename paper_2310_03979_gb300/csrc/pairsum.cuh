@@ -1,7 +1,9 @@
 // pairsum.cuh - the pair sum that assembles the coefficients C^s_k (FFT form,
-// Sec. 4.3): the plain FP64 form and the staged FP32 form.  Included by
-// sample.cu only.
+// Sec. 4.3): the plain FP64 form and the FP32 form (persistent, warp-specialised,
+// TMA-fed, packed two-lane arithmetic).  Included by sample.cu only.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap
 
 #include "srm3_internal.cuh"
 
@@ -52,247 +54,448 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
 
 
 // ---------------------------------------------------------------------------
-// a4 + a5, tiled FP32 form with shared-memory staging.  A CTA (4 warps)
-// takes a super-tile of 32 outputs kws0..kws0+31 of lattice row kk for one
-// group of 32 sheet-samples; warp w owns the 8-output tile kws0 + 8w and
-// each lane one sheet-sample.  Per row pair (a, b = kk - a) a thread forms
-//   T_r = sum_iw w(r, iw) y_a[iw] y_b[kw0 + r - iw],  r < 8,
-// in 8-wide blocks of iw held in registers: 8 values of y_a and a window of
-// 15 values of y_b serve all 64 (r, iw) products of a block.  The omega
-// range [0, kws0 + 31] is walked in chunks of 32: the chunk's y_a rows, the
-// y_b rows that the four tiles need (63) and, for the table path, the four
-// tiles' W rows are copied global -> shared with 16-byte cp.async
-// (zero-filled outside the lattice), double-buffered so that the copy of
-// chunk t+1 overlaps the arithmetic on chunk t.  Every shared-memory
-// operand of the inner loop is a compile-time offset from one base pointer
-// per chunk.  Terms with iw > kw read zero padding; the centre row a = b
-// runs the full range and is halved with its diagonal added back,
-// T = (T_full + w y_{kw/2}^2) / 2.  The row partial T is merged into a
-// Kahan-compensated accumulator once per row pair.
-// TABLE: w(r, iw) from the W table (which holds c_k and the kappa factor).
-// Otherwise w = Ew[2 iw - kw] from a shared copy of the envelope table
-// (read as aligned float4 windows), rowfac = Ek[kk - 2a], and c_k is
-// applied at the end.
-namespace staged {
-constexpr int R = kTileR, U = kTileU, ST = kWarpsPerCta, SW = ST * R, CH = 32;
-constexpr int NB = CH / U;                    // blocks per chunk
-constexpr int YB_ROWS = CH + SW - 1;
-constexpr int STAGE_Y = (CH + YB_ROWS) * 32;  // float2 entries per stage
-constexpr int STAGE_W = ST * R * CH;          // floats per stage
-constexpr int EW = 2 * U + R - 2;             // envelope window per block (22)
-constexpr int EW4 = (EW + 3) / 4;             // as float4 (6)
-static_assert(STAGE_W == 2 * 128 * 4, "two W copies of 16 bytes per thread");
-static_assert(YB_ROWS <= 8 * 8, "eight y_b rows per thread");
-}  // namespace staged
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  const int n = valid ? 16 : 0;
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n));
+// a4 + a5, FP32 form: persistent, warp-specialised, packed two-lane
+// arithmetic.
+//
+// Work unit: a super-tile of 32 outputs kws0..kws0+31 of lattice row kk for
+// one group of 64 sheet-samples.  Units are ordered by decreasing cost and
+// dealt to the resident CTAs in a snake order; a CTA walks its units one
+// after another.  Every lane carries two sheet-samples, stored pair-planar
+// as {x0, x1, y0, y1} (the layout k_phases writes for FP32 plans), so that
+// fma.rn.f32x2 / mul.rn.f32x2 act on both samples at once.
+//
+// Warps 0-3 compute: warp w owns the 8-output tile kw0 = kws0 + 8w.  Per row
+// pair (a, b = kk - a) a thread forms, for r < 8,
+//   T_r = sum_iw w(r, iw) y_a[iw] y_b[kw0 + r - iw]
+// in blocks of 4 iw: 4 values of y_a and a window of 11 values of y_b serve 32
+// (r, iw) products; 7 of the 11 carry over to the next block.  A product is
+// w*p*q with the minus sign of the complex product kept in a third
+// accumulator:
+//   Tx+ += (w px) qx,  Tx- += (w py) qy,  Ty += (w px) qy + (w py) qx,
+// six packed instructions for two pair-terms.  Terms with iw > kw read zero
+// padding; the centre row a = b runs the full range and is halved with its
+// diagonal added back, T = (T_full + w y_{kw/2}^2) / 2.  Row partials are
+// merged once per row pair into Kahan-compensated FP32 sums kept in shared
+// memory.
+//
+// Warp 4 produces: the omega range [0, kws0 + 31] of each row pair is
+// walked in chunks of 16, and for each chunk one lane stages the 16 y_a rows
+// and 48 y_b rows (47 used) of the group with four TMA tile loads of 16 rows
+// x 512 bytes through a 2-D tensor map over y (rows outside the lattice read
+// the zero padding of y) into one of two stages, signalled by an mbarrier
+// with a transaction count.  The weights go to shared memory
+// already duplicated as (w, w) pairs: TABLE loads the chunk's W rows (one
+// chunk ahead, through registers); otherwise the chunk's 64-entry window
+// of the duplicated omega envelope Ew2 is bulk-copied, w = Ew[2 iw - kw],
+// with the kappa factor Ek[kk - 2a] applied per row pair and c_k at the end.
+// The compute warps release a stage through a second mbarrier.  Every wait
+// is bounded: past kWaitCycles the waiter raises the CTA's abort flag and
+// the error word, all warps leave their loops, and the producer first waits
+// (bounded again) for the copies it has in flight.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float2 f2_split(f32x2 v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+
+namespace packed {
+constexpr int R = kTileR;                 // outputs per thread (8)
+constexpr int U = 4;                      // iw per register block
+constexpr int NC = kWarpsPerCta;          // compute warps = tiles per super-tile (4)
+constexpr int NCT = 32 * NC;              // compute threads
+constexpr int NT = NCT + 32;              // plus the producer warp
+constexpr int SW = NC * R;                // super-tile width (32)
+constexpr int CH = 16;                    // iw per chunk
+constexpr int NB = CH / U;                // register blocks per chunk
+constexpr int NV = R + U - 1;             // y_b window per block (11)
+constexpr int NE = 2 * U + R - 2;         // envelope window per block (14)
+constexpr int YB_ROWS = CH + SW - 1;      // y_b rows per chunk (47)
+constexpr int BOX_ROWS = 16;              // rows per TMA tile load
+constexpr int YB_BOXES = (YB_ROWS + BOX_ROWS - 1) / BOX_ROWS;  // 3
+constexpr int YROWS = CH + YB_BOXES * BOX_ROWS;  // staged rows per chunk (64)
+constexpr int LANES = 32;                 // sample pairs per group
+constexpr int ROW_BYTES = LANES * 16;     // one staged row
+constexpr int STAGE_Y = YROWS * LANES;    // float4 per stage
+constexpr int STAGE_W = NC * R * CH;      // (w, w) pairs per stage, table
+constexpr int EWIN = 64;                  // (w, w) pairs per stage, envelope
+constexpr int NK = 4 * R;                 // Kahan sums per compute thread
+constexpr int WPL = STAGE_W / 4 / 32;     // float4 of W per producer lane (4)
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+static_assert(WPL * 4 * 32 == STAGE_W && WPL == NC, "W of a chunk: one tile per float4 slot");
+static_assert(2 * (CH - 1) + SW <= EWIN, "envelope window of a chunk");
+static_assert(NB * U == CH && (NE % 2) == 0 && CH == BOX_ROWS, "block shape");
+static_assert(kPad >= SW + CH + 1, "staged rows stay inside the zero padding of y");
+}  // namespace packed
+
+inline size_t pairsum_f32p_smem(bool table) {
+  using namespace packed;
+  return 128 + (size_t)2 * STAGE_Y * sizeof(float4) +
+         (size_t)2 * (table ? STAGE_W : EWIN) * sizeof(float2) +
+         (size_t)2 * NK * NCT * sizeof(float);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+  asm volatile(
+      "{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}" ::"r"(
+          smem_u32(b))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for the phase of b with the given parity.  Returns false when the
+// CTA's abort flag is up or the wait passes kWaitCycles (then it raises the
+// flag and the error word).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity,
+                                          volatile int *abort, int *err) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > packed::kWaitCycles) {
+      *abort = 1;
+      atomicOr(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// 2-D TMA tile load (box from the tensor map) at element coordinates (x, y).
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ ulonglong2 lds_pair(const void *p) {
+  return *reinterpret_cast<const ulonglong2 *>(p);
+}
+
+// One work unit as seen by every warp of the CTA.
+struct PsUnit {
+  int kk, kws0, grp, nch, nitems;
+};
+__device__ __forceinline__ PsUnit ps_unit(int u, int G, const int2 *__restrict__ order) {
+  using namespace packed;
+  const int2 tk = order[u / G];
+  PsUnit w;
+  w.kk = tk.x;
+  w.kws0 = tk.y;
+  w.grp = u - (u / G) * G;
+  w.nch = (w.kws0 + SW + CH - 1) / CH;
+  w.nitems = (w.kk / 2 + 1) * w.nch;
+  return w;
+}
+// The k-th unit of CTA c out of C (snake order over the cost-sorted units).
+__device__ __forceinline__ int ps_unit_id(int k, int c, int C) {
+  return k * C + ((k & 1) ? C - 1 - c : c);
+}
 
 template <bool TABLE>
-__global__ void __launch_bounds__(128, 3) k_pairsum_f32s(
-    int nk, int nw, int SS, int SSpad, int rowstride, int G, const int2 *__restrict__ order,
-    const long long *__restrict__ toff, int ntw, const float2 *__restrict__ y,
-    const float2 *__restrict__ y0, const float *__restrict__ Ek,
-    const float *__restrict__ Ews_g, int ew_off, int ew_len, const float *__restrict__ W,
+__global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
+    int nk, int nw, int SS, int SSpad, int rowstride, int G, int nunits,
+    const int2 *__restrict__ order, const long long *__restrict__ toff, int ntw,
+    const float4 *__restrict__ y, const float2 *__restrict__ y0, const float *__restrict__ Ek,
+    const float2 *__restrict__ Ew2, int ew_off, const float *__restrict__ W,
     const float *__restrict__ Pk, const float *__restrict__ ck, float cb, float sb,
-    float2 *__restrict__ C) {
-  using namespace staged;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *sy = reinterpret_cast<float2 *>(smem_raw);        // [2][STAGE_Y]
-  float *sw = reinterpret_cast<float *>(sy + 2 * STAGE_Y);  // [2][STAGE_W] (table)
-  float *ews = sw;                                          // envelope copy (recompute)
+    float2 *__restrict__ C, int *__restrict__ err, const __grid_constant__ CUtensorMap ymap) {
+  using namespace packed;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [2]
+  unsigned long long *empty = full + 2;                                         // [2]
+  volatile int *abort = reinterpret_cast<volatile int *>(full + 4);
+  float4 *sy = reinterpret_cast<float4 *>(smem_raw + 128);    // [2][STAGE_Y]
+  float2 *sw = reinterpret_cast<float2 *>(sy + 2 * STAGE_Y);  // [2][STAGE_W] or [2][EWIN]
+  float *kst = reinterpret_cast<float *>(sw + 2 * (TABLE ? STAGE_W : EWIN));  // [2 NK][NCT]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (!TABLE) {
-    for (int i = tid; i < ew_len; i += blockDim.x) ews[i] = Ews_g[i];
+  const size_t SP = (size_t)SSpad / 2;  // float4 per lattice entry
+  if (tid == 0) {
+    mbar_init(&full[0], 32);
+    mbar_init(&full[1], 32);
+    mbar_init(&empty[0], NCT);
+    mbar_init(&empty[1], NCT);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const int grp = blockIdx.x % G;
-  const int2 tk = order[blockIdx.x / G];
-  const int kk = tk.x, kws0 = tk.y;
-  const int kw0 = kws0 + R * warp;  // this warp's tile
-  const bool tile_ok = kw0 < nw;
-  const int ss = grp * 32 + lane;
-  const size_t SP = (size_t)SSpad;
-  const int nrow = kk / 2 + 1;
-  const int nch = (kws0 + SW + CH - 1) / CH;
-  const int nitems = nrow * nch;
+  __syncthreads();
 
-  // copy geometry: thread tid copies 16 bytes (two sheet-samples) at
-  // column cpart of rows crow + 8 j
-  const int cpart = tid & 15, crow = tid >> 4;
-  const float2 *ysrc = y + (size_t)grp * 32 + cpart * 2;
-  // W copies: tile cs0 and cs0 + 2 of the super-tile, row cr, float4 cc4
-  const int cs0 = tid >> 6, cr = (tid >> 3) & 7, cc4 = tid & 7;
-  auto tile_L = [&](int k0) { return ((k0 + R + U - 1) / U) * U; };
-  auto tile_base = [&](int k0) -> long long {
-    return (TABLE && k0 < nw) ? toff[kk * ntw + k0 / R] : -1;
-  };
-  const int cL0 = tile_L(kws0 + R * cs0), cL1 = tile_L(kws0 + R * (cs0 + 2));
-  const long long cb0 = tile_base(kws0 + R * cs0), cb1 = tile_base(kws0 + R * (cs0 + 2));
-  const int my_L = tile_L(kw0);
-  const long long my_base = tile_base(kw0);
-
-  auto issue = [&](int item, int stage) {
-    if (item < nitems) {
-      const int a = item / nch, c = item - a * nch;
-      const int b = kk - a, i0 = c * CH;
-      float2 *dya = sy + stage * STAGE_Y + crow * 32 + cpart * 2;
-      float2 *dyb = dya + CH * 32;
-      const float2 *ra = ysrc + (size_t)(a * rowstride + kPad) * SP;
-      const float2 *rb = ysrc + (size_t)(b * rowstride + kPad) * SP;
+  if (warp == NC) {
+    // ---------------- producer ----------------
+    const unsigned tx = YROWS * ROW_BYTES + (TABLE ? 0 : EWIN * (unsigned)sizeof(float2));
+    // W prefetch iterator (TABLE): the chunk after the one being staged
+    int wk = 0, wu = ps_unit_id(0, blockIdx.x, gridDim.x), wa = 0, wc = 0;
+    PsUnit wU = wu < nunits ? ps_unit(wu, G, order) : PsUnit{0, 0, 0, 1, 0};
+    float4 wr[WPL];
+    auto w_load = [&]() {  // W rows of chunk (wU, wa, wc) into registers
 #pragma unroll
-      for (int j = 0; j < CH / 8; ++j) {
-        const int iw = i0 + crow + 8 * j;
-        const bool v = iw < nw;
-        cp_async16(dya + j * 8 * 32, ra + (size_t)(v ? iw : 0) * SP, v);
-      }
-      const int jlo = kws0 - i0 - CH + 1 + crow;
+      for (int h = 0; h < WPL; ++h) wr[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (!TABLE || wu >= nunits) return;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (crow + 8 * j < YB_ROWS) {
-          const int jw = jlo + 8 * j;
-          const bool v = jw >= 0 && jw < nw;
-          cp_async16(dyb + j * 8 * 32, rb + (size_t)(v ? jw : 0) * SP, v);
+      for (int h = 0; h < WPL; ++h) {
+        const int f = lane + 32 * h;  // float4 number: tile f >> 5, row (f >> 2) & 7
+        const int t = f >> 5, r = (f >> 2) & 7, iw = wc * CH + 4 * (f & 3);
+        const int k0 = wU.kws0 + R * t;
+        const int L = ((k0 + R + kTileU - 1) / kTileU) * kTileU;
+        if (k0 < nw && iw < L) {
+          const long long base = toff[wU.kk * ntw + k0 / R];
+          wr[h] = __ldg(reinterpret_cast<const float4 *>(W + base + ((long long)wa * R + r) * L + iw));
         }
       }
-      if (TABLE) {
-        float *dw = sw + stage * STAGE_W + (cs0 * R + cr) * CH + 4 * cc4;
-        const int iw = i0 + 4 * cc4;
-        const bool v0 = cb0 >= 0 && iw < cL0, v1 = cb1 >= 0 && iw < cL1;
-        cp_async16(dw, v0 ? W + cb0 + ((long long)a * R + cr) * cL0 + iw : W, v0);
-        cp_async16(dw + 2 * R * CH, v1 ? W + cb1 + ((long long)a * R + cr) * cL1 + iw : W, v1);
+    };
+    auto w_next = [&]() {
+      if (++wc == wU.nch) {
+        wc = 0;
+        if (++wa > wU.kk / 2) {
+          wa = 0;
+          wu = ps_unit_id(++wk, blockIdx.x, gridDim.x);
+          if (wu < nunits) wU = ps_unit(wu, G, order);
+        }
       }
-    }
-    cp_async_commit();
-  };
-
-  float2 acc[R], cmp[R], T[R];
+    };
+    if (TABLE) w_load();
+    unsigned q = 0;
+    bool ok = true;
+    for (int k = 0; ok; ++k) {
+      const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
+      if (u >= nunits) break;
+      const PsUnit U0 = ps_unit(u, G, order);
+      const int x = U0.grp * LANES * 4;  // first float of the group in a row of y
+      int a = 0, c = 0;
+      for (int item = 0; item < U0.nitems; ++item, ++q) {
+        const int stage = q & 1;
+        if (q >= 2 && !mbar_wait(&empty[stage], ((q >> 1) & 1) ^ 1, abort, err)) {
+          ok = false;
+          break;
+        }
+        const int i0 = c * CH, b = U0.kk - a;
+        if (lane == 0) {
+          float4 *dst = sy + stage * STAGE_Y;
+          mbar_expect_tx(&full[stage], tx);
+          tma_load_2d(dst, &ymap, x, a * rowstride + kPad + i0, &full[stage]);
+          const int jrow = b * rowstride + kPad + U0.kws0 - i0 - CH + 1;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    acc[r] = make_float2(0.f, 0.f);
-    cmp[r] = make_float2(0.f, 0.f);
-    T[r] = make_float2(0.f, 0.f);
-  }
-
-  issue(0, 0);
-  issue(1, 1);
-  int a = 0, c = 0;
-  for (int t = 0; t < nitems; ++t) {
-    const int stage = t & 1;
-    const int i0 = c * CH;
-    cp_async_wait1();
-    __syncthreads();
-    if (tile_ok) {
-      const float2 *pa = sy + stage * STAGE_Y + lane;
-      const float2 *pb = pa + (CH + R * warp + CH - U) * 32;
-      const float *pw = sw + stage * STAGE_W + warp * R * CH;
-      const float *pe = ews + ew_off + 2 * i0 - kw0 - (R - 1);
-#pragma unroll
-      for (int blk = 0; blk < NB; ++blk) {
-        if (i0 + blk * U > kw0 + R - 1) break;
-        float2 ya[U], yb[R + U - 1];
-#pragma unroll
-        for (int u = 0; u < U; ++u) ya[u] = pa[(blk * U + u) * 32];
-#pragma unroll
-        for (int v = 0; v < R + U - 1; ++v) yb[v] = pb[(v - blk * U) * 32];
+          for (int j = 0; j < YB_BOXES; ++j)
+            tma_load_2d(dst + (CH + BOX_ROWS * j) * LANES, &ymap, x, jrow + BOX_ROWS * j,
+                        &full[stage]);
+          if (!TABLE)
+            bulk_g2s(sw + stage * EWIN, Ew2 + ew_off + 2 * i0 - U0.kws0 - (SW - 1),
+                     EWIN * sizeof(float2), &full[stage]);
+        }
         if (TABLE) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float4 w0 = *reinterpret_cast<const float4 *>(pw + r * CH + blk * U);
-            const float4 w1 = *reinterpret_cast<const float4 *>(pw + r * CH + blk * U + 4);
-            const float w[U] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+          for (int h = 0; h < WPL; ++h) {
+            const int f = lane + 32 * h;
+            float4 *d = reinterpret_cast<float4 *>(sw + stage * STAGE_W +
+                                                   ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
+            d[0] = make_float4(wr[h].x, wr[h].x, wr[h].y, wr[h].y);
+            d[1] = make_float4(wr[h].z, wr[h].z, wr[h].w, wr[h].w);
+          }
+          w_next();
+          w_load();
+        }
+        mbar_arrive(&full[stage]);
+        if (++c == U0.nch) {
+          c = 0;
+          ++a;
+        }
+      }
+    }
+    if (!ok) {  // leave no bulk copy in flight: wait (bounded) for the last two stages
+      for (unsigned j = (q >= 2 ? q - 2 : 0); j < q; ++j) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&full[j & 1], (j >> 1) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- compute warps ----------------
+  float *kacc = kst + tid, *kcmp = kst + NK * NCT + tid;
+  unsigned q = 0;
+  for (int k = 0;; ++k) {
+    const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
+    if (u >= nunits) break;
+    const PsUnit U0 = ps_unit(u, G, order);
+    const int kk = U0.kk, kw0 = U0.kws0 + R * warp, nch = U0.nch;
+    const bool tile_ok = kw0 < nw;
+    const int my_L = ((kw0 + R + kTileU - 1) / kTileU) * kTileU;
+    const long long my_base = (TABLE && tile_ok) ? toff[kk * ntw + kw0 / R] : -1;
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const float2 p = ya[u], q = yb[r - u + U - 1];
-              const float pr = fmaf(p.x, q.x, -p.y * q.y);
-              const float pi = fmaf(p.x, q.y, p.y * q.x);
-              T[r].x = fmaf(w[u], pr, T[r].x);
-              T[r].y = fmaf(w[u], pi, T[r].y);
+    for (int j = 0; j < NK; ++j) kacc[j * NCT] = kcmp[j * NCT] = 0.f;
+    f32x2 Txp[R], Txm[R], Ty[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Txp[r] = Txm[r] = Ty[r] = 0ull;
+    int a = 0, c = 0;
+    for (int item = 0; item < U0.nitems; ++item, ++q) {
+      const int stage = q & 1;
+      if (!mbar_wait(&full[stage], (q >> 1) & 1, abort, err)) return;
+      const int i0 = c * CH;
+      if (tile_ok) {
+        const float4 *pa = sy + stage * STAGE_Y + lane;
+        const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
+        const float2 *pw = sw + stage * STAGE_W + warp * R * CH;
+        const float2 *pe = sw + stage * EWIN + 24 - 8 * warp;
+        // y_b rows by their offset m = v + U (NB - 1 - blk) from the lowest
+        // row any block reads: every row keeps one name.
+        ulonglong2 Bc[NV + U * (NB - 1)];
+#pragma unroll
+        for (int blk = 0; blk < NB; ++blk) {
+          if (i0 + blk * U > kw0 + R - 1) break;
+          ulonglong2 A[U];
+#pragma unroll
+          for (int uu = 0; uu < U; ++uu) A[uu] = lds_pair(pa + (blk * U + uu) * LANES);
+          const int m0 = U * (NB - 1 - blk);
+#pragma unroll
+          for (int v = (blk == 0 ? 0 : NV - U); v < NV; ++v) {
+            const int vv = blk == 0 ? v : v - (NV - U);  // rows not loaded yet
+            Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * LANES);
+          }
+          const ulonglong2 *B = Bc + m0;
+          if (TABLE) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const ulonglong2 w01 = lds_pair(pw + r * CH + blk * U);
+              const ulonglong2 w23 = lds_pair(pw + r * CH + blk * U + 2);
+              const f32x2 w[U] = {w01.x, w01.y, w23.x, w23.y};
+#pragma unroll
+              for (int uu = 0; uu < U; ++uu) {
+                const int v = r - uu + U - 1;
+                const f32x2 wpx = f2_mul(w[uu], A[uu].x), wpy = f2_mul(w[uu], A[uu].y);
+                Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
+                Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
+                Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
+                Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
+              }
             }
-          }
-        } else {
-          float e[4 * EW4];
+          } else {
+            f32x2 e[NE];
 #pragma unroll
-          for (int q4 = 0; q4 < EW4; ++q4) {
-            const float4 v4 = *reinterpret_cast<const float4 *>(pe + 2 * blk * U + 4 * q4);
-            e[4 * q4] = v4.x;
-            e[4 * q4 + 1] = v4.y;
-            e[4 * q4 + 2] = v4.z;
-            e[4 * q4 + 3] = v4.w;
-          }
+            for (int j = 0; j < NE / 2; ++j) {
+              const ulonglong2 v2 = lds_pair(pe + 8 * blk + 2 * j);
+              e[2 * j] = v2.x;
+              e[2 * j + 1] = v2.y;
+            }
 #pragma unroll
-          for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < R; ++r) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-              const float w = e[2 * u - r + R - 1];
-              const float2 p = ya[u], q = yb[r - u + U - 1];
-              const float pr = fmaf(p.x, q.x, -p.y * q.y);
-              const float pi = fmaf(p.x, q.y, p.y * q.x);
-              T[r].x = fmaf(w, pr, T[r].x);
-              T[r].y = fmaf(w, pi, T[r].y);
+              for (int uu = 0; uu < U; ++uu) {
+                const int v = r - uu + U - 1;
+                const f32x2 w = e[2 * uu - r + R - 1];
+                const f32x2 wpx = f2_mul(w, A[uu].x), wpy = f2_mul(w, A[uu].y);
+                Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
+                Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
+                Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
+                Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
+              }
             }
           }
         }
       }
-      if (c == nch - 1) {  // row pair complete: centre-row halving and merge
+      mbar_arrive(&empty[stage]);
+      if (tile_ok && c == nch - 1) {  // row pair complete: centre-row halving and merge
         const int b = kk - a;
-        if (a == b) {
-          const float2 *ra = y + ss + (size_t)(a * rowstride + kPad) * SP;
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const int kw = kw0 + r;
-            if ((kw & 1) == 0 && kw < nw) {
-              const float2 h = ra[(size_t)(kw >> 1) * SP];
-              const float w0 =
-                  TABLE ? W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)] : ews[ew_off];
-              T[r].x = 0.5f * (T[r].x + w0 * (h.x * h.x - h.y * h.y));
-              T[r].y = 0.5f * (T[r].y + w0 * (2.f * h.x * h.y));
-            } else {
-              T[r].x *= 0.5f;
-              T[r].y *= 0.5f;
-            }
-          }
-        }
         const float rowfac = TABLE ? 1.0f : Ek[kk - 2 * a];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          float yx = fmaf(rowfac, T[r].x, -cmp[r].x);
-          float tx = acc[r].x + yx;
-          cmp[r].x = (tx - acc[r].x) - yx;
-          acc[r].x = tx;
-          float yy = fmaf(rowfac, T[r].y, -cmp[r].y);
-          float ty = acc[r].y + yy;
-          cmp[r].y = (ty - acc[r].y) - yy;
-          acc[r].y = ty;
-          T[r] = make_float2(0.f, 0.f);
+          const float2 xp = f2_split(Txp[r]), xm = f2_split(Txm[r]), yy = f2_split(Ty[r]);
+          float v[4] = {xp.x - xm.x, xp.y - xm.y, yy.x, yy.y};
+          if (a == b) {
+            const int kw = kw0 + r;
+            if ((kw & 1) == 0 && kw < nw) {
+              const float4 h = y[((size_t)a * rowstride + kPad + (kw >> 1)) * SP +
+                                 (size_t)U0.grp * LANES + lane];
+              const float w0 = TABLE ? W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)]
+                                     : Ew2[ew_off].x;
+              v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
+              v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
+              v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));
+              v[3] = 0.5f * (v[3] + w0 * (2.f * h.y * h.w));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) v[j] *= 0.5f;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // Kahan: s += rowfac v with compensation
+            float &s_ = kacc[(4 * r + j) * NCT], &cp = kcmp[(4 * r + j) * NCT];
+            const float s0 = s_, yv = fmaf(rowfac, v[j], -cp);
+            const float tt = s0 + yv;
+            cp = (tt - s0) - yv;
+            s_ = tt;
+          }
+          Txp[r] = Txm[r] = Ty[r] = 0ull;
         }
       }
+      if (++c == nch) {
+        c = 0;
+        ++a;
+      }
     }
-    __syncthreads();
-    issue(t + 2, stage);
-    if (++c == nch) {
-      c = 0;
-      ++a;
-    }
-  }
-  if (!tile_ok || ss >= SS) return;
+    if (!tile_ok) continue;
+    const int ss0 = U0.grp * 2 * LANES + 2 * lane;
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int kw = kw0 + r;
-    if (kw >= nw) break;
-    const int k = kk * nw + kw;
-    const float2 yk = (k == 0) ? y0[ss] : y[ss + ((size_t)kk * rowstride + kPad + kw) * SP];
-    const float ar = acc[r].x - cmp[r].x, ai = acc[r].y - cmp[r].y;
-    const float cf = TABLE ? 1.0f : ck[k];
-    const float P = Pk[k];
-    float2 out;
-    out.x = fmaf(P, yk.x, cf * (ar * cb - ai * sb));
-    out.y = fmaf(P, yk.y, cf * (ar * sb + ai * cb));
-    C[((size_t)ss * nk + kk) * nw + kw] = out;
+    for (int r = 0; r < R; ++r) {
+      const int kw = kw0 + r;
+      if (kw >= nw) break;
+      const int kidx = kk * nw + kw;
+      const float4 yk4 =
+          y[((size_t)kk * rowstride + kPad + kw) * SP + (size_t)U0.grp * LANES + lane];
+      const float cf = TABLE ? 1.0f : ck[kidx];
+      const float P = Pk[kidx];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ss = ss0 + h;
+        if (ss >= SS) break;
+        const float2 yk = (kidx == 0) ? y0[ss] : (h ? make_float2(yk4.y, yk4.w)
+                                                     : make_float2(yk4.x, yk4.z));
+        const float ar = kacc[(4 * r + h) * NCT] - kcmp[(4 * r + h) * NCT];
+        const float ai = kacc[(4 * r + 2 + h) * NCT] - kcmp[(4 * r + 2 + h) * NCT];
+        float2 out;
+        out.x = fmaf(P, yk.x, cf * (ar * cb - ai * sb));
+        out.y = fmaf(P, yk.y, cf * (ar * sb + ai * cb));
+        C[((size_t)ss * nk + kk) * nw + kw] = out;
+      }
+    }
   }
 }
 

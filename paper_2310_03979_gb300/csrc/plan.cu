@@ -175,6 +175,11 @@ __global__ void k_env(int len, int off, double sigma_n, T *out) {
   out[i] = (T)exp(-0.5 * a * a);
 }
 
+__global__ void k_dup2(int len, const float *__restrict__ in, float2 *__restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) out[i] = make_float2(in[i], in[i]);
+}
+
 template <typename T2>
 __global__ void k_twiddles(int n, T2 *tw) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -578,7 +583,7 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   SRM3_CUDA(cudaMalloc(&p->tile_order, sizeof(int2) * p->ntiles));
   SRM3_CUDA(cudaMemcpyAsync(p->tile_order, order.data(), sizeof(int2) * p->ntiles,
                             cudaMemcpyHostToDevice, st));
-  // super-tiles of kWarpsPerCta tiles (staged kernel), most expensive first
+  // super-tiles of kWarpsPerCta tiles (FP32 pair sum), most expensive first
   const int sw = kTileR * kWarpsPerCta;
   const int nsw = cdiv(p->nw, sw);
   p->nsuper = nk * nsw;
@@ -721,10 +726,13 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   const size_t nl = (size_t)nk * nw;
   const bool f32 = p->precision == SRM3_FP32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  // signed envelope table Ews[ew_off + d]; ew_off = 7 (mod 8) puts the
-  // staged kernel's 22-value windows on 16-byte boundaries
+  // signed envelope table Ews[ew_off + d] (terms outside the lattice meet
+  // zero y, whatever their weight).  ew_off is
+  // odd, which puts the FP32 pair sum's 96-pair chunk windows of Ew2 (first
+  // d = 2 i0 - kws0 - 31, odd) on 16-byte boundaries; the table reaches
+  // d = nw + 127, past the last window.
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
-  p->ew_len = p->ew_off + nw + 96;
+  p->ew_len = p->ew_off + nw + 128;
   p->nfft = std::max(p->nx, p->nt);
   SRM3_CUDA(cudaMalloc(&p->sqq, nl * es));
   SRM3_CUDA(cudaMalloc(&p->Pk, nl * es));
@@ -739,6 +747,10 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_env<float><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (float *)p->Ek);
     k_env<float><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off, p->sigma_g * nw,
                                                       (float *)p->Ews);
+    SRM3_CUDA(cudaMalloc(&p->Ew2, p->ew_len * sizeof(float2)));
+    SRM3_CUDA(cudaMalloc(&p->ps_err, sizeof(int)));
+    SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
+    k_dup2<<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, (const float *)p->Ews, p->Ew2);
     k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, (float2 *)p->tw);
   } else {
     k_sampling_tables<double><<<cdiv(nl, 256), 256, 0, st>>>(
@@ -765,7 +777,8 @@ void free_plan(srm3_plan *p) {
                  p->tw,     p->tile_order, p->tile_off, p->W,       p->y,      p->y0,
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
-                 p->rec_partial, p->rec_ticket, p->super_order, p->rec_lev_off, p->rec_bar};
+                 p->rec_partial, p->rec_ticket, p->super_order, p->rec_lev_off, p->rec_bar,
+                 p->Ew2,    p->ps_err};
   for (void *d : dev)
     if (d) cudaFree(d);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
@@ -861,7 +874,7 @@ SRM3_API void srm3_destroy(srm3_plan *plan) {
 SRM3_API int srm3_sync(srm3_plan *plan) {
   if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
   SRM3_CUDA(cudaStreamSynchronize(plan->stream));
-  return SRM3_OK;
+  return check_pairsum_error(plan);
 }
 
 SRM3_API int srm3_set_stream(srm3_plan *plan, void *stream) {

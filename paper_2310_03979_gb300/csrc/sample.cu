@@ -3,6 +3,9 @@
 // Sec. 4.3), and the hand-written 2-D inverse FFT to u(x,t).
 #include <algorithm>
 #include <cstring>
+#include <string>
+
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
 #include "fft.cuh"
 #include "pairsum.cuh"
@@ -98,7 +101,15 @@ __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
       v.x = 0;
       v.y = 0;
     }
-    y[((size_t)kk * rowstride + kPad + kw) * SSpad + ss] = v;
+    const size_t row = (size_t)kk * rowstride + kPad + kw;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // FP32: pair-planar {x_{2l}, x_{2l+1}, y_{2l}, y_{2l+1}} per sample pair l
+      float *yf = reinterpret_cast<float *>(y) + (row * (SSpad / 2) + (ss >> 1)) * 4 + (ss & 1);
+      yf[0] = v.x;
+      yf[2] = v.y;
+    } else {
+      y[row * SSpad + ss] = v;
+    }
   }
 }
 
@@ -107,7 +118,9 @@ static size_t elem2(const srm3_plan *p) {
   return p->precision == SRM3_FP32 ? sizeof(float2) : sizeof(double2);
 }
 
-static int sspad_for(int chunk) { return ((2 * chunk + 31) / 32) * 32; }
+// sheet-samples per lattice entry, padded to whole 64-wide groups of the
+// FP32 pair sum
+static int sspad_for(int chunk) { return ((2 * chunk + 63) / 64) * 64; }
 
 int ensure_workspace(srm3_plan *p, int chunk) {
   if (p->ws_chunk >= chunk) return SRM3_OK;
@@ -161,30 +174,51 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
         (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
         (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
   } else {
-    using namespace staged;
-    const int G = sp / 32;
-    const int blocks = p->nsuper * G;
+    const int G = sp / (2 * packed::LANES);
+    const int nunits = p->nsuper * G;
     const bool table = p->storage == SRM3_STORAGE_TABLE;
-    const size_t smem = (size_t)2 * STAGE_Y * sizeof(float2) +
-                        (table ? (size_t)2 * STAGE_W * sizeof(float)
-                               : (size_t)p->ew_len * sizeof(float));
-    if (table) {
-      SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32s<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_pairsum_f32s<true><<<blocks, 32 * kWarpsPerCta, smem, p->stream>>>(
-          p->nk, p->nw, SS, sp, p->rowstride, G, p->super_order, p->tile_off, p->ntw,
-          (const float2 *)p->y, (const float2 *)p->y0, (const float *)p->Ek,
-          (const float *)p->Ews, p->ew_off, p->ew_len, p->W, (const float *)p->Pk,
-          (const float *)p->ck, cbf, sbf, (float2 *)C_out);
-    } else {
-      SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32s<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_pairsum_f32s<false><<<blocks, 32 * kWarpsPerCta, smem, p->stream>>>(
-          p->nk, p->nw, SS, sp, p->rowstride, G, p->super_order, p->tile_off, p->ntw,
-          (const float2 *)p->y, (const float2 *)p->y0, (const float *)p->Ek,
-          (const float *)p->Ews, p->ew_off, p->ew_len, nullptr, (const float *)p->Pk,
-          (const float *)p->ck, cbf, sbf, (float2 *)C_out);
+    const size_t smem = pairsum_f32p_smem(table);
+    auto kern = table ? k_pairsum_f32p<true> : k_pairsum_f32p<false>;
+    SRM3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SRM3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel
+      int nsm = 0, per_sm = 0;
+      SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+      SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, packed::NT, smem));
+      if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
+      p->ps_ctas = nsm * per_sm;
     }
+    // 2-D tensor map over y: rows of SSpad / 2 float4 (the sample pairs of
+    // one lattice entry), boxes of one group (512 bytes) x 16 rows
+    CUtensorMap ymap;
+    {
+      static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+      if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        SRM3_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &qr));
+        if (qr != cudaDriverEntryPointSuccess || !fn)
+          return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+      }
+      const cuuint64_t dims[2] = {(cuuint64_t)sp * 2, (cuuint64_t)p->nk * p->rowstride};
+      const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
+      const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
+      const cuuint32_t estr[2] = {1, 1};
+      const CUresult r = encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->y, dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
+    const int grid = std::min(nunits, p->ps_ctas);
+    kern<<<grid, packed::NT, smem, p->stream>>>(
+        p->nk, p->nw, SS, sp, p->rowstride, G, nunits, p->super_order, p->tile_off, p->ntw,
+        (const float4 *)p->y, (const float2 *)p->y0, (const float *)p->Ek, p->Ew2, p->ew_off,
+        table ? p->W : nullptr, (const float *)p->Pk, (const float *)p->ck, cbf, sbf,
+        (float2 *)C_out, p->ps_err, ymap);
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
@@ -215,6 +249,14 @@ int run_transform(srm3_plan *p, const void *C, int n, void *out) {
   if (p->precision == SRM3_FP32)
     return transform_impl<float, float2>(p, (const float2 *)C, n, (float *)out);
   return transform_impl<double, double2>(p, (const double2 *)C, n, (double *)out);
+}
+
+int check_pairsum_error(srm3_plan *p) {
+  if (!p->ps_err) return SRM3_OK;
+  int h = 0;
+  SRM3_CUDA(cudaMemcpy(&h, p->ps_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) return fail(SRM3_ERR_TIMEOUT, "FP32 pair sum: a pipeline wait ran out of time");
+  return SRM3_OK;
 }
 
 int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec) {
@@ -322,7 +364,7 @@ SRM3_API int srm3_sample_host(srm3_plan *plan, const uint64_t *seeds, int n, voi
   cudaFreeAsync(dev, plan->stream);
   if (rc) return rc;
   SRM3_CUDA(cudaStreamSynchronize(plan->stream));
-  return SRM3_OK;
+  return check_pairsum_error(plan);
 }
 
 SRM3_API int srm3_phase_words(srm3_plan *plan, const uint64_t *seeds, int n, uint32_t *words) {

@@ -14,12 +14,13 @@
 
 namespace srm3 {
 
-// Tile shape of the FP32 pair sum: R outputs along omega per thread, the
-// omega-index loop unrolled by U.  The y rows carry kPad zero entries on
-// both sides so that every window load of the tiled kernel stays in bounds.
+// Tile shape of the FP32 pair sum: R outputs along omega per thread; the W
+// table rows of a tile are padded to a multiple of kTileU.  The y rows carry
+// kPad zero entries on both sides: every row the FP32 pair sum stages lies
+// within omega index [-31, nw + 30], so its copies need no bounds checks.
 constexpr int kTileR = 8;
 constexpr int kTileU = 8;
-constexpr int kPad = 16;           // >= kTileR + kTileU - 2
+constexpr int kPad = 64;
 constexpr int kMaxChunk = 128;     // samples per internal launch chunk
 constexpr int kWarpsPerCta = 4;    // FP32 pair-sum CTA: 4 warps = 4 work units
 constexpr int kMaxFft = 8192;
@@ -83,15 +84,18 @@ struct srm3_plan {
   void *ck = nullptr;     // pair factor 2 eps dk dw sqrt(S), [nk*nw]
   void *Ek = nullptr;     // envelope factor along kappa, |d| < nk
   void *Ews = nullptr;    // envelope factor along omega, signed d, offset ew_off
+  float2 *Ew2 = nullptr;  // FP32 plans: the same as (w, w) pairs
   int ew_off = 0, ew_len = 0;
   void *tw = nullptr;     // FFT twiddles e^{+2 pi i j / nfft}, j < nfft
   int nfft = 0;
 
   // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
   int ntw = 0, ntiles = 0;
+  int ps_ctas = 0;                // resident CTAs of the persistent FP32 pair sum
+  int *ps_err = nullptr;          // its error word (bounded waits that ran out)
   int2 *tile_order = nullptr;
   int nsuper = 0;
-  int2 *super_order = nullptr;    // 32-wide super-tiles (staged kernel)
+  int2 *super_order = nullptr;    // 32-wide super-tiles of the FP32 pair sum
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
   float *W = nullptr;             // W table (STORAGE_TABLE)
 
@@ -138,6 +142,7 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st);
 int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);
 int stage_end(srm3_plan *p, int rec);
 int collect_timings(srm3_plan *p);
+int check_pairsum_error(srm3_plan *p);
 }  // namespace srm3
 
 static inline int ilog2_exact(int v) {
