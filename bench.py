@@ -28,6 +28,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 latency"
+
+# DRAM bytes (read + write) of one FP32 pair-sum launch on the 256 x 512 table
+# workload with 64 samples, from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the 128 x 256 table case with 64 samples (same two sample groups per
+# super-tile), scaled by the W table size (x 15.64): profiles/
+# pairsum_f32p_table_128x256.md.  Valid only for the kernel source it was
+# measured on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
+PAIRSUM_TRAFFIC = {"bytes": 10.18e9, "source_sha256": "9ebd0884bcfb2e24"}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -260,8 +268,20 @@ def main():
     info = recs[-1][1]
     t_last = recs[-1][0]
     chunks = math.ceil(n / 128)
-    launches_per_step = (3 + 2 + info.root_passes * (wl.n_kappa + wl.n_omega) + 4
-                         + (1 if info.storage == 1 else 0) + 4 * chunks)
+    # kernels launched per step (matches the ncu launch list): spectrum 1,
+    # envelope tables 2 + g^2 1, linear pass + reduction 2, each recursion
+    # pass + reduction 2, sampling tables 5 (FP32) / 4 (FP64), W table 1 if
+    # stored; per 128-sample chunk: phases, pair sum, two FFT stages
+    launches_per_step = (1 + 3 + 2 + 2 * (info.root_passes + info.root_passes_fp32)
+                         + (5 if es == 4 else 4) + (1 if info.storage == 1 else 0)
+                         + 4 * chunks)
+    traffic = None
+    src = os.path.join(ROOT, "paper_2310_03979_gb300", "csrc", "pairsum.cuh")
+    if wl.name.startswith("bridge") and info.storage == 1 and es == 4:
+        import hashlib
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] == PAIRSUM_TRAFFIC["source_sha256"]:
+                traffic = PAIRSUM_TRAFFIC["bytes"]
 
     line = {
         "metric": METRIC, "value": value, "unit": "pair-terms/s", "n_gpus": world,
@@ -272,7 +292,7 @@ def main():
                    "n_x": wl.n_x, "n_t": wl.n_t, "samples_per_step": n * world,
                    "storage": "table" if info.storage == 1 else "recompute",
                    "precision": wl.precision, "l2": "inputs larger than L2 (W table "
-                   f"{info.table_bytes / 1e9:.1f} GB, y {n * 2 * 8 * wl.n_kappa * (wl.n_omega + 32) / 1e6:.0f} MB)",
+                   f"{info.table_bytes / 1e9:.1f} GB, y {n * 2 * 8 * wl.n_kappa * (wl.n_omega + 128) / 1e6:.0f} MB)",
                    "step": "plan build (spectrum, FP64 recursion + eps search, W table) + "
                            f"{n}-sample batch"},
         "samples_per_s": n * world / (ms_per_step * 1e-3),
@@ -285,7 +305,9 @@ def main():
         "sampling_only_pair_terms_per_s": terms_per_step / (
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": info.table_bytes + n * 2 * 8 * (
+                         wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
                      "kernel": "k_pairsum_f32p<table>" if info.storage == 1 else
                                "k_pairsum_f32p<recompute>",
                      "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 "

@@ -75,49 +75,6 @@ __global__ void k_g2(int nk, int nw, const double *__restrict__ EkSq,
   G2_32[i] = (float)v;
 }
 
-// ---------------------------------------------------------------------------
-// Linear pass: q == 1 everywhere (masked by S > 0), every point in one
-// launch, one CTA per point.  Gives L_k = dk dw sum_{Pi(k)} g^2, the
-// small-eps slope of sum_b2 used to bracket eps.
-__global__ void __launch_bounds__(256) k_rec_linear(int nk, int nw,
-                                                    const double *__restrict__ S,
-                                                    double *__restrict__ sb2,
-                                                    const double *__restrict__ EkSq,
-                                                    const double *__restrict__ EwSq,
-                                                    double dkdw) {
-  const int kk = blockIdx.x / nw, kw = blockIdx.x - kk * nw;
-  const int k = kk * nw + kw;
-  if (!(S[k] > 0.0)) {
-    if (threadIdx.x == 0) sb2[k] = 0.0;
-    return;
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double acc = 0.0;
-  const int nrow = kk / 2 + 1;
-  for (int a = warp; a < nrow; a += 8) {
-    const int b = kk - a;
-    const int lim = (a == b) ? kw / 2 : kw;
-    const double *Sa = S + (size_t)a * nw;
-    const double *Sb = S + (size_t)b * nw;
-    double racc = 0.0;
-    for (int iw = lane; iw <= lim; iw += 32) {
-      if (a == 0 && iw == 0) continue;
-      double prod = (Sa[iw] > 0.0 && Sb[kw - iw] > 0.0) ? 1.0 : 0.0;
-      int dd = 2 * iw - kw;
-      racc = fma(EwSq[dd < 0 ? -dd : dd], prod, racc);
-    }
-    acc = fma(EkSq[kk - 2 * a], racc, acc);
-  }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ double red[8];
-  if (lane == 0) red[warp] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    sb2[k] = dkdw * t;
-  }
-}
 
 // Per-plane reductions (one CTA per plane): max sum_b2, min (1 - sum_b2)
 // over S > 0 and sum S into scal[8 + 4m + {1,2,3}].
@@ -196,27 +153,36 @@ __global__ void k_twiddles(int n, T2 *tw) {
 // then iw < L (L = kw0 + R rounded up to U); W = c_k Ek[kk-2a] Ew[2iw-kw]
 // for iw <= kw < nw, else 0.  Centre rows are stored in full (the kernel
 // halves them).  W is real: the constant biphase is applied afterwards.
-__global__ void k_build_w(int nk, int nw, int ntw, const long long *__restrict__ off,
-                          const float *__restrict__ ck, const float *__restrict__ Ek,
-                          const float *__restrict__ Ews, int ew_off, float *__restrict__ W) {
+// One CTA per tile: thread rows take table rows (a, r), lanes take float4
+// column groups.
+__global__ void __launch_bounds__(256) k_build_w(int nk, int nw, int ntw,
+                                                 const long long *__restrict__ off,
+                                                 const float *__restrict__ ck,
+                                                 const float *__restrict__ Ek,
+                                                 const float *__restrict__ Ews, int ew_off,
+                                                 float *__restrict__ W) {
   const int t = blockIdx.x;
   const int kk = t / ntw, tw = t - kk * ntw;
   const int kw0 = tw * kTileR;
   const int nrow = kk / 2 + 1;
   const int L = ((kw0 + kTileR + kTileU - 1) / kTileU) * kTileU;
-  const long long n = (long long)nrow * kTileR * L;
-  float *dst = W + off[t];
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    int iw = (int)(i % L);
-    long long rest = i / L;
-    int r = (int)(rest % kTileR);
-    int a = (int)(rest / kTileR);
-    int kw = kw0 + r;
-    float v = 0.0f;
-    if (kw < nw && iw <= kw) {
-      v = ck[kk * nw + kw] * Ek[kk - 2 * a] * Ews[ew_off + 2 * iw - kw];
+  const int L4 = L / 4;
+  float4 *dst = reinterpret_cast<float4 *>(W + off[t]);
+  for (int row = threadIdx.y; row < nrow * kTileR; row += blockDim.y) {
+    const int a = row / kTileR, r = row - a * kTileR;
+    const int kw = kw0 + r;
+    const float f = kw < nw ? ck[kk * nw + kw] * Ek[kk - 2 * a] : 0.0f;
+    const float *e = Ews + ew_off - kw;
+    float4 *drow = dst + (size_t)row * L4;
+    for (int c = threadIdx.x; c < L4; c += blockDim.x) {
+      const int iw = 4 * c;
+      float4 v;
+      v.x = (iw + 0 <= kw) ? f * e[2 * (iw + 0)] : 0.0f;
+      v.y = (iw + 1 <= kw) ? f * e[2 * (iw + 1)] : 0.0f;
+      v.z = (iw + 2 <= kw) ? f * e[2 * (iw + 2)] : 0.0f;
+      v.w = (iw + 3 <= kw) ? f * e[2 * (iw + 3)] : 0.0f;
+      drow[c] = v;
     }
-    dst[i] = v;
   }
 }
 
@@ -411,9 +377,14 @@ static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, in
 // FP64 bracket continues.  The tables left in the plan are those of the
 // final FP64 pass.
 static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
-  k_rec_linear<<<cdiv((long long)p->nk * p->nw * 32, 256), 256, 0, st>>>(p->nk, p->nw, p->S,
-                                                                          p->G2_32, p->sb2,
-                                                                          p->dkdw);
+  {
+    const int nblk = cdiv(p->nw, kLinOut);
+    const size_t smem = (size_t)3 * p->nw * sizeof(float);
+    SRM3_CUDA(cudaFuncSetAttribute(k_rec_linear, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
+    k_rec_linear<<<p->nk * nblk, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32, p->EwSq32,
+                                                       p->sb2, p->dkdw);
+  }
   SRM3_CUDA(cudaGetLastError());
   k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double), cudaMemcpyDeviceToHost,
@@ -423,21 +394,39 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   if (!(Lmax > 0.0))
     return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
 
-  // FP32 stage: eight eps values per pass; the first pass samples (0, x0],
-  // later ones subdivide the bracket; stop once a feasible upper end is
-  // known after at least two passes.  Inverse quadratic interpolation
-  // through the bracket and its nearest feasible neighbour gives x32.
+  // FP32 stage: eight values of x = eps^2 per pass.  At the root every
+  // sum_b2 <= target, so q <= 1/(1 - target) and x* lies in
+  // [(1 - target)^2 x0, x0], x0 = target / Lmax (q >= 1 gives the upper end);
+  // the first pass samples that range (with a margin for the FP32 Lmax).
+  // The second pass centres its planes on the first pass's quadratic
+  // estimate, half-width four times that estimate's distance from the
+  // secant root, so that the slope at the root comes out of closely spaced
+  // planes.  Later passes (only when the root was not inside) subdivide the
+  // bracket.  Inverse quadratic interpolation through the bracket and its
+  // nearest feasible neighbour gives x32.
   const double x0 = target / Lmax;
   PassResult r[kPlanes];
   double xs[kPlanes];
   int rc;
   std::vector<std::pair<double, double>> pts;  // (x, f); f = +inf: failed pass
   pts.push_back({0.0, -target});
-  double lo = 0.0, hi = x0;
+  double lo = 0.9 * (1.0 - target) * (1.0 - target) * x0, hi = 1.01 * x0;
   bool hi_known = false;
+  double zoom_c = 0.0, zoom_w = 0.0;  // centre and half-width of the second pass
+  auto quad_root = [](double xa, double fa, double xb, double fb, double xc, double fc) {
+    return xa * fb * fc / ((fa - fb) * (fa - fc)) + xb * fa * fc / ((fb - fa) * (fb - fc)) +
+           xc * fa * fb / ((fc - fa) * (fc - fb));
+  };
   for (int pass = 0; pass < 12; ++pass) {
-    for (int m = 0; m < kPlanes; ++m)
-      xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1) : lo + (hi - lo) * (m + 1) / kPlanes;
+    for (int m = 0; m < kPlanes; ++m) {
+      if (pass == 0)
+        xs[m] = lo + (hi - lo) * m / (kPlanes - 1);
+      else if (pass == 1 && zoom_w > 0.0)
+        xs[m] = zoom_c - zoom_w + 2.0 * zoom_w * m / (kPlanes - 1);
+      else
+        xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1)
+                         : lo + (hi - lo) * (m + 1) / kPlanes;
+    }
     rc = run_pass_multi(p, st, xs, kPlanes, false, r);
     if (rc) return rc;
     for (int m = 0; m < kPlanes; ++m)
@@ -456,6 +445,23 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     hi = pts[j].first;
     hi_known = true;
     if (pass >= 1 && std::isfinite(pts[j].second)) break;
+    zoom_w = 0.0;
+    if (pass == 0 && std::isfinite(pts[j].second) &&
+        ((j + 1 < pts.size() && std::isfinite(pts[j + 1].second)) || j >= 2)) {
+      // quadratic through the bracket and its feasible neighbour above, else
+      // the one below
+      const double xl = pts[j - 1].first, fl = pts[j - 1].second;
+      const double xh = pts[j].first, fh = pts[j].second;
+      const double xsec = xl - fl * (xh - xl) / (fh - fl);
+      const bool above = j + 1 < pts.size() && std::isfinite(pts[j + 1].second);
+      const double xq = above ? quad_root(xl, fl, xh, fh, pts[j + 1].first, pts[j + 1].second)
+                              : quad_root(pts[j - 2].first, pts[j - 2].second, xl, fl, xh, fh);
+      if (xq > xl && xq < xh) {
+        zoom_c = xq;
+        zoom_w = std::max(4.0 * std::fabs(xq - xsec), 2e-4 * xq);
+        zoom_w = std::min(zoom_w, 0.5 * std::min(xq - xl, xh - xq));
+      }
+    }
   }
   if (!hi_known) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: target not bracketed");
   size_t jb = 0;
@@ -700,7 +706,7 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
       cudaError_t e = cudaMalloc(&p->W, (size_t)entries * sizeof(float));
       if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(W table)");
       SRM3_CUDA(cudaEventRecord(t_ev[0], st));
-      k_build_w<<<p->ntiles, 256, 0, st>>>(nk, nw, p->ntw, p->tile_off, (const float *)p->ck,
+      k_build_w<<<p->ntiles, dim3(32, 8), 0, st>>>(nk, nw, p->ntw, p->tile_off, (const float *)p->ck,
                                             (const float *)p->Ek, (const float *)p->Ews,
                                             p->ew_off, p->W);
       SRM3_CUDA(cudaGetLastError());

@@ -335,33 +335,51 @@ __global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
 }
 
 // Linear pass: L_k = dk dw sum_{Pi(k)} g^2 [S_i > 0][S_j > 0] (q == 1), the
-// small-eps slope of sum_b2 used to bracket eps.  No level dependencies: one
-// warp per point over the rows laid end to end, FP32 terms (only the scale of
-// eps is taken from it), written to sb2 plane 0.
-__global__ void __launch_bounds__(256) k_rec_linear(int nk, int nw, const double *__restrict__ S,
-                                                    const float *__restrict__ G2,
-                                                    double *__restrict__ sb2, double dkdw) {
-  const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= (long long)nk * nw) return;
-  const int kk = (int)(gw / nw), kw = (int)(gw - (long long)kk * nw);
-  const long long k = gw;
-  if (!(S[k] > 0.0)) {
-    if (lane == 0) sb2[k] = 0.0;
-    return;
-  }
-  const int W = kw + 1, E = (kk / 2 + 1) * W;
+// small-eps slope of sum_b2 used to bracket eps.  No level dependencies.  A
+// CTA takes lattice row kk and kLinOut consecutive omega outputs, one
+// thread per output; per row pair (a, b = kk - a) it stages the S > 0 masks
+// of rows a and b in shared memory, and every thread sums
+//   R(kw) = sum_iw EwSq[|2 iw - kw|] m_a[iw] m_b[kw - iw]
+// over iw <= kw (iw <= kw/2 on the centre row, i = 0 skipped), weighted by
+// EkSq[kk - 2a].  FP32 terms (only the scale of eps is taken from it);
+// written to sb2 plane 0.  CTAs go in order of decreasing kk (most rows
+// first).
+constexpr int kLinOut = 128;
+
+__global__ void __launch_bounds__(kLinOut) k_rec_linear(int nk, int nw, const double *__restrict__ S,
+                                                        const float *__restrict__ EkSq,
+                                                        const float *__restrict__ EwSq,
+                                                        double *__restrict__ sb2, double dkdw) {
+  extern __shared__ float lin_smem[];
+  float *ma = lin_smem, *mb = lin_smem + nw, *ew = lin_smem + 2 * nw;  // [nw] each
+  const int nblk = (nw + kLinOut - 1) / kLinOut;
+  const int kk = nk - 1 - (int)(blockIdx.x / nblk);
+  const int kw = (int)(blockIdx.x % nblk) * kLinOut + threadIdx.x;
+  const int kwmax = min(nw, (int)(blockIdx.x % nblk) * kLinOut + kLinOut);  // outputs < kwmax
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) ew[i] = EwSq[i];
   float acc = 0.f;
-  for (int e = lane; e < E; e += 32) {
-    const int a = e / W, iw = e - a * W, b = kk - a;
-    const int lim = (a == b) ? kw / 2 : kw;
-    if ((a == 0 && iw == 0) || iw > lim) continue;
-    if (!(S[(size_t)a * nw + iw] > 0.0) || !(S[(size_t)b * nw + (kw - iw)] > 0.0)) continue;
-    const int dw = 2 * iw - kw;
-    acc += G2[(size_t)(kk - 2 * a) * nw + (dw < 0 ? -dw : dw)];
+  for (int a = 0; a <= kk / 2; ++a) {
+    const int b = kk - a;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kwmax; i += blockDim.x) {
+      ma[i] = S[(size_t)a * nw + i] > 0.0 ? 1.f : 0.f;
+      mb[i] = S[(size_t)b * nw + i] > 0.0 ? 1.f : 0.f;
+    }
+    __syncthreads();
+    if (kw < nw) {
+      const int lim = (a == b) ? kw / 2 : kw;
+      float r = 0.f;
+      for (int iw = (a == 0 ? 1 : 0); iw <= lim; ++iw) {
+        const int dw = 2 * iw - kw;
+        r = fmaf(ew[dw < 0 ? -dw : dw], ma[iw] * mb[kw - iw], r);
+      }
+      acc = fmaf(EkSq[kk - 2 * a], r, acc);
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) sb2[k] = dkdw * (double)acc;
+  if (kw < nw) {
+    const size_t k = (size_t)kk * nw + kw;
+    sb2[k] = S[k] > 0.0 ? dkdw * (double)acc : 0.0;
+  }
 }
 
 }  // namespace srm3
