@@ -46,7 +46,9 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
-    ap.add_argument("--config", default="bridge", choices=["bridge", "large", "tiny"])
+    ap.add_argument("--config", default="bridge", choices=["bridge", "large", "tiny", "prof128"],
+                    help="workload; bridge is the benchmark line, the others are for "
+                         "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()

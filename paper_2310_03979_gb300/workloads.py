@@ -77,7 +77,13 @@ LARGE = Workload("large_512x1024_recompute_fp32", 512, 1024, 0.25, 4 * math.pi,
                  40.0, 20.0, 1024, 2048, tuple(range(1, 17)), precision="fp32",
                  storage="recompute")
 
-CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "large": LARGE}
+# Profiling case: the bridge spectrum on a 128 x 256 lattice, stored W table
+# (0.56 GB, above L2), 64 samples -- two 64-wide sample groups per super-tile
+# as in the bridge workload, small enough for multi-pass ncu captures.
+PROF128 = Workload("table_128x256_fp32", 128, 256, 0.25, 4 * math.pi, 40.0, 20.0, 256, 512,
+                   tuple(range(1, 65)), precision="fp32", storage="table")
+
+CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "large": LARGE, "prof128": PROF128}
 
 
 def uneven_batch(n_spectra: int = 200, seed: int = 4):
