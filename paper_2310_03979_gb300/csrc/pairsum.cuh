@@ -133,15 +133,14 @@ constexpr int NK = 4 * R;                 // Kahan sums per compute thread
 constexpr int WPL = STAGE_W / 4 / 32;     // float4 of W per producer lane (4)
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 static_assert(WPL * 4 * 32 == STAGE_W && WPL == NC, "W of a chunk: one tile per float4 slot");
-static_assert(2 * (CH - 1) + SW <= EWIN, "envelope window of a chunk");
+static_assert(2 * (CH - 1) + SW <= EWIN && EWIN <= STAGE_W, "envelope window of a chunk");
 static_assert(NB * U == CH && (NE % 2) == 0 && CH == BOX_ROWS, "block shape");
 static_assert(kPad >= SW + CH + 1, "staged rows stay inside the zero padding of y");
 }  // namespace packed
 
-inline size_t pairsum_f32p_smem(bool table) {
+inline size_t pairsum_f32p_smem() {
   using namespace packed;
-  return 128 + (size_t)2 * STAGE_Y * sizeof(float4) +
-         (size_t)2 * (table ? STAGE_W : EWIN) * sizeof(float2) +
+  return 128 + (size_t)2 * STAGE_Y * sizeof(float4) + (size_t)2 * STAGE_W * sizeof(float2) +
          (size_t)2 * NK * NCT * sizeof(float);
 }
 
@@ -210,44 +209,123 @@ __device__ __forceinline__ ulonglong2 lds_pair(const void *p) {
   return *reinterpret_cast<const ulonglong2 *>(p);
 }
 
-// One work unit as seen by every warp of the CTA.
-struct PsUnit {
-  int kk, kws0, grp, nch, nitems;
+// Per-plan view of an FP32 pair-sum launch.  The tensor map comes first:
+// TMA descriptors need 64-byte alignment.
+struct PsDesc {  // aligned as CUtensorMap
+  CUtensorMap ymap;      // y as rows of SSpad/2 float4; boxes of 512 B x 16 rows
+  const float4 *y;       // pair-planar rows (kPad zero entries each side)
+  const float2 *y0;      // y at k = 0 per sheet-sample
+  const float *Ek;       // kappa envelope factor (recompute)
+  const float2 *Ew2;     // omega envelope as (w, w) pairs (recompute; w0 at ew_off)
+  const float *W;        // W table (table storage)
+  const long long *toff; // W-table offset per tile (table storage)
+  const float *Pk, *ck;  // pure and pair factors
+  float2 *C;             // coefficients out [ss][kk][kw]
+  const int2 *order;     // super-tiles (kk, kws0) by decreasing cost (single-plan launch)
+  int nk, nw, SS, SSpad, rowstride, ntw, ew_off, table, G;
+  float cb, sb;          // cos / sin of the biphase
 };
-__device__ __forceinline__ PsUnit ps_unit(int u, int G, const int2 *__restrict__ order) {
+
+// Work unit {plan, kk, kws0, grp}: the 32-wide super-tile of row kk starting
+// at kws0, for sample group grp of plan `plan`.
+__device__ __forceinline__ int ps_nitems(int kk, int kws0) {
   using namespace packed;
-  const int2 tk = order[u / G];
-  PsUnit w;
-  w.kk = tk.x;
-  w.kws0 = tk.y;
-  w.grp = u - (u / G) * G;
-  w.nch = (w.kws0 + SW + CH - 1) / CH;
-  w.nitems = (w.kk / 2 + 1) * w.nch;
-  return w;
+  return (kk / 2 + 1) * ((kws0 + SW + CH - 1) / CH);
 }
 // The k-th unit of CTA c out of C (snake order over the cost-sorted units).
 __device__ __forceinline__ int ps_unit_id(int k, int c, int C) {
   return k * C + ((k & 1) ? C - 1 - c : c);
 }
+// Unit u: units[u] in a batch launch; in a single-plan launch (units ==
+// NULL) super-tile d0.order[u / G] for group u % G of plan d0.
+__device__ __forceinline__ int4 ps_get_unit(int u, const PsDesc &d0,
+                                            const int4 *__restrict__ units) {
+  if (units) return units[u];
+  const int2 t = d0.order[u / d0.G];
+  return make_int4(0, t.x, t.y, u - (u / d0.G) * d0.G);
+}
 
+// One staged chunk for one compute warp: all register blocks of the chunk.
 template <bool TABLE>
+__device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
+                                         const float4 *__restrict__ pb,
+                                         const float2 *__restrict__ pw,
+                                         const float2 *__restrict__ pe, int i0, int kw0,
+                                         f32x2 (&Txp)[packed::R], f32x2 (&Txm)[packed::R],
+                                         f32x2 (&Ty)[packed::R]) {
+  using namespace packed;
+  // y_b rows by their offset m = v + U (NB - 1 - blk) from the lowest row any
+  // block reads: every row keeps one name.
+  ulonglong2 Bc[NV + U * (NB - 1)];
+#pragma unroll
+  for (int blk = 0; blk < NB; ++blk) {
+    if (i0 + blk * U > kw0 + R - 1) break;
+    ulonglong2 A[U];
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) A[uu] = lds_pair(pa + (blk * U + uu) * LANES);
+    const int m0 = U * (NB - 1 - blk);
+#pragma unroll
+    for (int v = (blk == 0 ? 0 : NV - U); v < NV; ++v) {
+      const int vv = blk == 0 ? v : v - (NV - U);  // rows not loaded yet
+      Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * LANES);
+    }
+    const ulonglong2 *B = Bc + m0;
+    if (TABLE) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const ulonglong2 w01 = lds_pair(pw + r * CH + blk * U);
+        const ulonglong2 w23 = lds_pair(pw + r * CH + blk * U + 2);
+        const f32x2 w[U] = {w01.x, w01.y, w23.x, w23.y};
+#pragma unroll
+        for (int uu = 0; uu < U; ++uu) {
+          const int v = r - uu + U - 1;
+          const f32x2 wpx = f2_mul(w[uu], A[uu].x), wpy = f2_mul(w[uu], A[uu].y);
+          Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
+          Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
+          Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
+          Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
+        }
+      }
+    } else {
+      f32x2 e[NE];
+#pragma unroll
+      for (int j = 0; j < NE / 2; ++j) {
+        const ulonglong2 v2 = lds_pair(pe + 8 * blk + 2 * j);
+        e[2 * j] = v2.x;
+        e[2 * j + 1] = v2.y;
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int uu = 0; uu < U; ++uu) {
+          const int v = r - uu + U - 1;
+          const f32x2 w = e[2 * uu - r + R - 1];
+          const f32x2 wpx = f2_mul(w, A[uu].x), wpy = f2_mul(w, A[uu].y);
+          Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
+          Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
+          Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
+          Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
+        }
+      }
+    }
+  }
+}
+
+// The FP32 pair sum over one plan (d0, with descs = units = NULL) or any
+// number of plans (descs[p] describes plan p, units[0..nunits) the work units
+// sorted by decreasing cost).
 __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
-    int nk, int nw, int SS, int SSpad, int rowstride, int G, int nunits,
-    const int2 *__restrict__ order, const long long *__restrict__ toff, int ntw,
-    const float4 *__restrict__ y, const float2 *__restrict__ y0, const float *__restrict__ Ek,
-    const float2 *__restrict__ Ew2, int ew_off, const float *__restrict__ W,
-    const float *__restrict__ Pk, const float *__restrict__ ck, float cb, float sb,
-    float2 *__restrict__ C, int *__restrict__ err, const __grid_constant__ CUtensorMap ymap) {
+    const __grid_constant__ PsDesc d0, const PsDesc *__restrict__ descs,
+    const int4 *__restrict__ units, int nunits, int *__restrict__ err) {
   using namespace packed;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [2]
   unsigned long long *empty = full + 2;                                         // [2]
   volatile int *abort = reinterpret_cast<volatile int *>(full + 4);
   float4 *sy = reinterpret_cast<float4 *>(smem_raw + 128);    // [2][STAGE_Y]
-  float2 *sw = reinterpret_cast<float2 *>(sy + 2 * STAGE_Y);  // [2][STAGE_W] or [2][EWIN]
-  float *kst = reinterpret_cast<float *>(sw + 2 * (TABLE ? STAGE_W : EWIN));  // [2 NK][NCT]
+  float2 *sw = reinterpret_cast<float2 *>(sy + 2 * STAGE_Y);  // [2][STAGE_W] (W or envelope)
+  float *kst = reinterpret_cast<float *>(sw + 2 * STAGE_W);   // [2 NK][NCT]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const size_t SP = (size_t)SSpad / 2;  // float4 per lattice entry
   if (tid == 0) {
     mbar_init(&full[0], 32);
     mbar_init(&full[1], 32);
@@ -260,80 +338,86 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
 
   if (warp == NC) {
     // ---------------- producer ----------------
-    const unsigned tx = YROWS * ROW_BYTES + (TABLE ? 0 : EWIN * (unsigned)sizeof(float2));
-    // W prefetch iterator (TABLE): the chunk after the one being staged
+    // W prefetch iterator (table plans): the chunk after the one being staged
     int wk = 0, wu = ps_unit_id(0, blockIdx.x, gridDim.x), wa = 0, wc = 0;
-    PsUnit wU = wu < nunits ? ps_unit(wu, G, order) : PsUnit{0, 0, 0, 1, 0};
+    int4 wun = wu < nunits ? ps_get_unit(wu, d0, units) : make_int4(0, 0, 0, 0);
     float4 wr[WPL];
-    auto w_load = [&]() {  // W rows of chunk (wU, wa, wc) into registers
+    auto w_load = [&]() {  // W rows of chunk (wun, wa, wc) into registers
 #pragma unroll
       for (int h = 0; h < WPL; ++h) wr[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (!TABLE || wu >= nunits) return;
+      if (wu >= nunits) return;
+      const PsDesc &d = descs ? descs[wun.x] : d0;
+      if (!d.table) return;
 #pragma unroll
       for (int h = 0; h < WPL; ++h) {
         const int f = lane + 32 * h;  // float4 number: tile f >> 5, row (f >> 2) & 7
         const int t = f >> 5, r = (f >> 2) & 7, iw = wc * CH + 4 * (f & 3);
-        const int k0 = wU.kws0 + R * t;
+        const int k0 = wun.z + R * t;
         const int L = ((k0 + R + kTileU - 1) / kTileU) * kTileU;
-        if (k0 < nw && iw < L) {
-          const long long base = toff[wU.kk * ntw + k0 / R];
-          wr[h] = __ldg(reinterpret_cast<const float4 *>(W + base + ((long long)wa * R + r) * L + iw));
+        if (k0 < d.nw && iw < L) {
+          const long long base = d.toff[wun.y * d.ntw + k0 / R];
+          wr[h] = __ldg(
+              reinterpret_cast<const float4 *>(d.W + base + ((long long)wa * R + r) * L + iw));
         }
       }
     };
     auto w_next = [&]() {
-      if (++wc == wU.nch) {
+      if (++wc == (wun.z + SW + CH - 1) / CH) {
         wc = 0;
-        if (++wa > wU.kk / 2) {
+        if (++wa > wun.y / 2) {
           wa = 0;
           wu = ps_unit_id(++wk, blockIdx.x, gridDim.x);
-          if (wu < nunits) wU = ps_unit(wu, G, order);
+          if (wu < nunits) wun = ps_get_unit(wu, d0, units);
         }
       }
     };
-    if (TABLE) w_load();
+    w_load();
     unsigned q = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
       const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
       if (u >= nunits) break;
-      const PsUnit U0 = ps_unit(u, G, order);
-      const int x = U0.grp * LANES * 4;  // first float of the group in a row of y
+      const int4 un = ps_get_unit(u, d0, units);
+      const PsDesc &d = descs ? descs[un.x] : d0;
+      const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
+      const int nitems = ps_nitems(kk, kws0), tab = d.table, rs = d.rowstride;
+      const unsigned tx = YROWS * ROW_BYTES + (tab ? 0 : EWIN * (unsigned)sizeof(float2));
+      const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
-      for (int item = 0; item < U0.nitems; ++item, ++q) {
+      for (int item = 0; item < nitems; ++item, ++q) {
         const int stage = q & 1;
         if (q >= 2 && !mbar_wait(&empty[stage], ((q >> 1) & 1) ^ 1, abort, err)) {
           ok = false;
           break;
         }
-        const int i0 = c * CH, b = U0.kk - a;
+        const int i0 = c * CH, b = kk - a;
         if (lane == 0) {
           float4 *dst = sy + stage * STAGE_Y;
           mbar_expect_tx(&full[stage], tx);
-          tma_load_2d(dst, &ymap, x, a * rowstride + kPad + i0, &full[stage]);
-          const int jrow = b * rowstride + kPad + U0.kws0 - i0 - CH + 1;
+          tma_load_2d(dst, &d.ymap, x, a * rs + kPad + i0, &full[stage]);
+          const int jrow = b * rs + kPad + kws0 - i0 - CH + 1;
 #pragma unroll
           for (int j = 0; j < YB_BOXES; ++j)
-            tma_load_2d(dst + (CH + BOX_ROWS * j) * LANES, &ymap, x, jrow + BOX_ROWS * j,
+            tma_load_2d(dst + (CH + BOX_ROWS * j) * LANES, &d.ymap, x, jrow + BOX_ROWS * j,
                         &full[stage]);
-          if (!TABLE)
-            bulk_g2s(sw + stage * EWIN, Ew2 + ew_off + 2 * i0 - U0.kws0 - (SW - 1),
+          if (!tab)
+            bulk_g2s(sw + stage * STAGE_W, d.Ew2 + d.ew_off + 2 * i0 - kws0 - (SW - 1),
                      EWIN * sizeof(float2), &full[stage]);
         }
-        if (TABLE) {
+        if (tab) {
 #pragma unroll
           for (int h = 0; h < WPL; ++h) {
             const int f = lane + 32 * h;
-            float4 *d = reinterpret_cast<float4 *>(sw + stage * STAGE_W +
-                                                   ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
-            d[0] = make_float4(wr[h].x, wr[h].x, wr[h].y, wr[h].y);
-            d[1] = make_float4(wr[h].z, wr[h].z, wr[h].w, wr[h].w);
+            float4 *dw = reinterpret_cast<float4 *>(
+                sw + stage * STAGE_W + ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
+            dw[0] = make_float4(wr[h].x, wr[h].x, wr[h].y, wr[h].y);
+            dw[1] = make_float4(wr[h].z, wr[h].z, wr[h].w, wr[h].w);
           }
-          w_next();
-          w_load();
         }
+        w_next();
+        w_load();
         mbar_arrive(&full[stage]);
-        if (++c == U0.nch) {
+        if (++c == nch) {
           c = 0;
           ++a;
         }
@@ -355,18 +439,22 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
   for (int k = 0;; ++k) {
     const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
     if (u >= nunits) break;
-    const PsUnit U0 = ps_unit(u, G, order);
-    const int kk = U0.kk, kw0 = U0.kws0 + R * warp, nch = U0.nch;
+    const int4 un = ps_get_unit(u, d0, units);
+    const PsDesc &d = descs ? descs[un.x] : d0;
+    const int kk = un.y, kws0 = un.z, grp = un.w, nw = d.nw, tab = d.table;
+    const int kw0 = kws0 + R * warp, nch = (kws0 + SW + CH - 1) / CH;
+    const int nitems = ps_nitems(kk, kws0);
+    const size_t SP = (size_t)d.SSpad / 2;  // float4 per lattice entry
     const bool tile_ok = kw0 < nw;
     const int my_L = ((kw0 + R + kTileU - 1) / kTileU) * kTileU;
-    const long long my_base = (TABLE && tile_ok) ? toff[kk * ntw + kw0 / R] : -1;
+    const long long my_base = (tab && tile_ok) ? d.toff[kk * d.ntw + kw0 / R] : -1;
 #pragma unroll
     for (int j = 0; j < NK; ++j) kacc[j * NCT] = kcmp[j * NCT] = 0.f;
     f32x2 Txp[R], Txm[R], Ty[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) Txp[r] = Txm[r] = Ty[r] = 0ull;
     int a = 0, c = 0;
-    for (int item = 0; item < U0.nitems; ++item, ++q) {
+    for (int item = 0; item < nitems; ++item, ++q) {
       const int stage = q & 1;
       if (!mbar_wait(&full[stage], (q >> 1) & 1, abort, err)) return;
       const int i0 = c * CH;
@@ -374,67 +462,16 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
         const float4 *pa = sy + stage * STAGE_Y + lane;
         const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
         const float2 *pw = sw + stage * STAGE_W + warp * R * CH;
-        const float2 *pe = sw + stage * EWIN + 24 - 8 * warp;
-        // y_b rows by their offset m = v + U (NB - 1 - blk) from the lowest
-        // row any block reads: every row keeps one name.
-        ulonglong2 Bc[NV + U * (NB - 1)];
-#pragma unroll
-        for (int blk = 0; blk < NB; ++blk) {
-          if (i0 + blk * U > kw0 + R - 1) break;
-          ulonglong2 A[U];
-#pragma unroll
-          for (int uu = 0; uu < U; ++uu) A[uu] = lds_pair(pa + (blk * U + uu) * LANES);
-          const int m0 = U * (NB - 1 - blk);
-#pragma unroll
-          for (int v = (blk == 0 ? 0 : NV - U); v < NV; ++v) {
-            const int vv = blk == 0 ? v : v - (NV - U);  // rows not loaded yet
-            Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * LANES);
-          }
-          const ulonglong2 *B = Bc + m0;
-          if (TABLE) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-              const ulonglong2 w01 = lds_pair(pw + r * CH + blk * U);
-              const ulonglong2 w23 = lds_pair(pw + r * CH + blk * U + 2);
-              const f32x2 w[U] = {w01.x, w01.y, w23.x, w23.y};
-#pragma unroll
-              for (int uu = 0; uu < U; ++uu) {
-                const int v = r - uu + U - 1;
-                const f32x2 wpx = f2_mul(w[uu], A[uu].x), wpy = f2_mul(w[uu], A[uu].y);
-                Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
-                Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
-                Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
-                Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
-              }
-            }
-          } else {
-            f32x2 e[NE];
-#pragma unroll
-            for (int j = 0; j < NE / 2; ++j) {
-              const ulonglong2 v2 = lds_pair(pe + 8 * blk + 2 * j);
-              e[2 * j] = v2.x;
-              e[2 * j + 1] = v2.y;
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-#pragma unroll
-              for (int uu = 0; uu < U; ++uu) {
-                const int v = r - uu + U - 1;
-                const f32x2 w = e[2 * uu - r + R - 1];
-                const f32x2 wpx = f2_mul(w, A[uu].x), wpy = f2_mul(w, A[uu].y);
-                Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
-                Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
-                Ty[r] = f2_fma(wpx, B[v].y, Ty[r]);
-                Ty[r] = f2_fma(wpy, B[v].x, Ty[r]);
-              }
-            }
-          }
-        }
+        const float2 *pe = sw + stage * STAGE_W + 24 - 8 * warp;
+        if (tab)
+          ps_chunk<true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+        else
+          ps_chunk<false>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
       }
       mbar_arrive(&empty[stage]);
       if (tile_ok && c == nch - 1) {  // row pair complete: centre-row halving and merge
         const int b = kk - a;
-        const float rowfac = TABLE ? 1.0f : Ek[kk - 2 * a];
+        const float rowfac = tab ? 1.0f : d.Ek[kk - 2 * a];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const float2 xp = f2_split(Txp[r]), xm = f2_split(Txm[r]), yy = f2_split(Ty[r]);
@@ -442,10 +479,10 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
           if (a == b) {
             const int kw = kw0 + r;
             if ((kw & 1) == 0 && kw < nw) {
-              const float4 h = y[((size_t)a * rowstride + kPad + (kw >> 1)) * SP +
-                                 (size_t)U0.grp * LANES + lane];
-              const float w0 = TABLE ? W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)]
-                                     : Ew2[ew_off].x;
+              const float4 h = d.y[((size_t)a * d.rowstride + kPad + (kw >> 1)) * SP +
+                                   (size_t)grp * LANES + lane];
+              const float w0 = tab ? d.W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)]
+                                   : d.Ew2[d.ew_off].x;
               v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
               v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
               v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));
@@ -472,28 +509,28 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       }
     }
     if (!tile_ok) continue;
-    const int ss0 = U0.grp * 2 * LANES + 2 * lane;
+    const int ss0 = grp * 2 * LANES + 2 * lane;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int kw = kw0 + r;
       if (kw >= nw) break;
       const int kidx = kk * nw + kw;
       const float4 yk4 =
-          y[((size_t)kk * rowstride + kPad + kw) * SP + (size_t)U0.grp * LANES + lane];
-      const float cf = TABLE ? 1.0f : ck[kidx];
-      const float P = Pk[kidx];
+          d.y[((size_t)kk * d.rowstride + kPad + kw) * SP + (size_t)grp * LANES + lane];
+      const float cf = tab ? 1.0f : d.ck[kidx];
+      const float P = d.Pk[kidx];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int ss = ss0 + h;
-        if (ss >= SS) break;
-        const float2 yk = (kidx == 0) ? y0[ss] : (h ? make_float2(yk4.y, yk4.w)
-                                                     : make_float2(yk4.x, yk4.z));
+        if (ss >= d.SS) break;
+        const float2 yk = (kidx == 0) ? d.y0[ss] : (h ? make_float2(yk4.y, yk4.w)
+                                                       : make_float2(yk4.x, yk4.z));
         const float ar = kacc[(4 * r + h) * NCT] - kcmp[(4 * r + h) * NCT];
         const float ai = kacc[(4 * r + 2 + h) * NCT] - kcmp[(4 * r + 2 + h) * NCT];
         float2 out;
-        out.x = fmaf(P, yk.x, cf * (ar * cb - ai * sb));
-        out.y = fmaf(P, yk.y, cf * (ar * sb + ai * cb));
-        C[((size_t)ss * nk + kk) * nw + kw] = out;
+        out.x = fmaf(P, yk.x, cf * (ar * d.cb - ai * d.sb));
+        out.y = fmaf(P, yk.y, cf * (ar * d.sb + ai * d.cb));
+        d.C[((size_t)ss * d.nk + kk) * nw + kw] = out;
       }
     }
   }

@@ -601,6 +601,7 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   SRM3_CUDA(cudaMalloc(&p->super_order, sizeof(int2) * p->nsuper));
   SRM3_CUDA(cudaMemcpyAsync(p->super_order, sup.data(), sizeof(int2) * p->nsuper,
                             cudaMemcpyHostToDevice, st));
+  p->super_host = sup;
   *table_entries = off[p->ntiles];
   if (want_table) {
     SRM3_CUDA(cudaMalloc(&p->tile_off, sizeof(long long) * p->ntiles));

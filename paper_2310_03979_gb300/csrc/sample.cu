@@ -120,7 +120,7 @@ static size_t elem2(const srm3_plan *p) {
 
 // sheet-samples per lattice entry, padded to whole 64-wide groups of the
 // FP32 pair sum
-static int sspad_for(int chunk) { return ((2 * chunk + 63) / 64) * 64; }
+int sspad_for(int chunk) { return ((2 * chunk + 63) / 64) * 64; }
 
 int ensure_workspace(srm3_plan *p, int chunk) {
   if (p->ws_chunk >= chunk) return SRM3_OK;
@@ -164,9 +164,84 @@ int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out) 
   return SRM3_OK;
 }
 
+// Descriptor of plan p for an FP32 pair-sum launch over n samples whose
+// phasor rows are in p->y (laid out for n) and whose coefficients go to C_out.
+int fill_pairsum_desc(srm3_plan *p, int n, void *C_out, PsDesc *d) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    SRM3_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                               cudaEnableDefault, &qr));
+    if (qr != cudaDriverEntryPointSuccess || !fn)
+      return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const int sp = sspad_for(n);
+  std::memset(static_cast<void *>(d), 0, sizeof(*d));
+  // 2-D tensor map over y: rows of sp / 2 float4 (the sample pairs of one
+  // lattice entry), boxes of one 64-sample group (512 bytes) x 16 rows
+  const cuuint64_t dims[2] = {(cuuint64_t)sp * 2, (cuuint64_t)p->nk * p->rowstride};
+  const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(&d->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->y, dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  const bool table = p->storage == SRM3_STORAGE_TABLE;
+  d->y = (const float4 *)p->y;
+  d->y0 = (const float2 *)p->y0;
+  d->Ek = (const float *)p->Ek;
+  d->Ew2 = p->Ew2;
+  d->W = table ? p->W : nullptr;
+  d->toff = table ? p->tile_off : nullptr;
+  d->Pk = (const float *)p->Pk;
+  d->ck = (const float *)p->ck;
+  d->C = (float2 *)C_out;
+  d->order = p->super_order;
+  d->nk = p->nk;
+  d->nw = p->nw;
+  d->SS = 2 * n;
+  d->SSpad = sp;
+  d->rowstride = p->rowstride;
+  d->ntw = p->ntw;
+  d->ew_off = p->ew_off;
+  d->table = table ? 1 : 0;
+  d->G = sp / (2 * packed::LANES);
+  d->cb = (float)std::cos(p->beta);
+  d->sb = (float)std::sin(p->beta);
+  return SRM3_OK;
+}
+
+// One FP32 pair-sum launch on stream st: plan d0 alone (descs == NULL) or the
+// batch descs/units; the grid is the resident CTA count (persistent kernel).
+// nunits == 0 only prepares (attributes, resident CTA count).
+int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
+                       const int4 *units, int nunits) {
+  const size_t smem = pairsum_f32p_smem();
+  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32p, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100));
+  if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel
+    int nsm = 0, per_sm = 0;
+    SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairsum_f32p, packed::NT,
+                                                            smem));
+    if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
+    p->ps_ctas = nsm * per_sm;
+  }
+  const int grid = std::min(nunits, p->ps_ctas);
+  if (grid == 0) return SRM3_OK;
+  k_pairsum_f32p<<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
 int run_pairsum(srm3_plan *p, int n, void *C_out) {
   const int SS = 2 * n, sp = sspad_for(n);
-  const float cbf = (float)std::cos(p->beta), sbf = (float)std::sin(p->beta);
   if (p->precision == SRM3_FP64) {
     const long long threads = (long long)p->nk * p->nw * sp;
     k_pairsum_f64<<<cdiv(threads, 256), 256, 0, p->stream>>>(
@@ -174,51 +249,10 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
         (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
         (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
   } else {
-    const int G = sp / (2 * packed::LANES);
-    const int nunits = p->nsuper * G;
-    const bool table = p->storage == SRM3_STORAGE_TABLE;
-    const size_t smem = pairsum_f32p_smem(table);
-    auto kern = table ? k_pairsum_f32p<true> : k_pairsum_f32p<false>;
-    SRM3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    SRM3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel
-      int nsm = 0, per_sm = 0;
-      SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-      SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, packed::NT, smem));
-      if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
-      p->ps_ctas = nsm * per_sm;
-    }
-    // 2-D tensor map over y: rows of SSpad / 2 float4 (the sample pairs of
-    // one lattice entry), boxes of one group (512 bytes) x 16 rows
-    CUtensorMap ymap;
-    {
-      static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-      if (!encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        SRM3_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                   cudaEnableDefault, &qr));
-        if (qr != cudaDriverEntryPointSuccess || !fn)
-          return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-      }
-      const cuuint64_t dims[2] = {(cuuint64_t)sp * 2, (cuuint64_t)p->nk * p->rowstride};
-      const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
-      const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
-      const cuuint32_t estr[2] = {1, 1};
-      const CUresult r = encode(&ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->y, dims, strides,
-                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      if (r != CUDA_SUCCESS)
-        return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    }
-    const int grid = std::min(nunits, p->ps_ctas);
-    kern<<<grid, packed::NT, smem, p->stream>>>(
-        p->nk, p->nw, SS, sp, p->rowstride, G, nunits, p->super_order, p->tile_off, p->ntw,
-        (const float4 *)p->y, (const float2 *)p->y0, (const float *)p->Ek, p->Ew2, p->ew_off,
-        table ? p->W : nullptr, (const float *)p->Pk, (const float *)p->ck, cbf, sbf,
-        (float2 *)C_out, p->ps_err, ymap);
+    PsDesc d;
+    int rc = fill_pairsum_desc(p, n, C_out, &d);
+    if (rc) return rc;
+    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G);
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;

@@ -96,6 +96,7 @@ struct srm3_plan {
   int2 *tile_order = nullptr;
   int nsuper = 0;
   int2 *super_order = nullptr;    // 32-wide super-tiles of the FP32 pair sum
+  std::vector<int2> super_host;   // the same order on the host (batch unit lists)
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
   float *W = nullptr;             // W table (STORAGE_TABLE)
 
@@ -143,6 +144,7 @@ int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);
 int stage_end(srm3_plan *p, int rec);
 int collect_timings(srm3_plan *p);
 int check_pairsum_error(srm3_plan *p);
+int sspad_for(int chunk);
 }  // namespace srm3
 
 static inline int ilog2_exact(int v) {
