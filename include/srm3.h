@@ -87,7 +87,9 @@ enum srm3_precision {
 enum srm3_storage {
     SRM3_STORAGE_AUTO = 0,     /* table if it fits the budget, else recompute */
     SRM3_STORAGE_TABLE = 1,    /* W streamed from an HBM table (FP32 only) */
-    SRM3_STORAGE_RECOMPUTE = 2 /* W rebuilt from envelope factors in-kernel */
+    SRM3_STORAGE_RECOMPUTE = 2, /* W rebuilt from envelope factors in-kernel */
+    SRM3_STORAGE_TUNED = 3      /* the storage srm3_autotune chose for this lattice
+                                   shape in this process, else as AUTO */
 };
 
 typedef struct srm3_grid {
@@ -253,6 +255,65 @@ int srm3_enable_timing(srm3_plan *plan, int on);
 /* Wait for the plan's stream, then report the timings; reset != 0 clears
  * the sampling-stage sums afterwards. */
 int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset);
+
+/* ---- Autotuning (FP32 plans) ---------------------------------------------
+ * The FP32 pair sum can read W from the stored table or rebuild it from the
+ * envelope factors; which is faster depends on the lattice and the number of
+ * samples.  srm3_autotune times one pair-sum launch of each on this plan for
+ * n samples (the phases of seeds 1..n, in the plan's workspace), keeps the
+ * faster -- building the W table when it wins and the plan has none (if it
+ * fits the plan's table budget), freeing it when recomputation wins -- and
+ * records the choice for the plan's (n_kappa, n_omega) in this process:
+ * plans created later with SRM3_STORAGE_TUNED use it.  Synchronous.
+ * Errors: INVALID_ARG (n outside 1..128), NOT_SUPPORTED (FP64 plan),
+ * OUT_OF_MEMORY, CUDA. */
+typedef struct srm3_tune_result {
+    double table_ms;      /* one pair-sum launch with the stored table; < 0: not tried */
+    double recompute_ms;  /* one pair-sum launch with W rebuilt in the kernel */
+    int32_t storage;      /* the choice: SRM3_STORAGE_TABLE or SRM3_STORAGE_RECOMPUTE */
+    int32_t samples;      /* n */
+} srm3_tune_result;
+int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *result);
+
+/* ---- Batches of plans ------------------------------------------------------
+ * One sampling job over m plans with uneven lattices and sample counts: the
+ * phases of every plan, ONE persistent pair-sum launch over the work units
+ * of all FP32 plans (cost-sorted across plans; FP64 plans get their own
+ * plain launches), then the transforms, all on one stream.
+ * srm3_batch_create checks the plans (one device, no plan twice), sizes each
+ * plan's workspace for its count (this allocates), and puts the per-plan
+ * descriptors and the unit list on the device.  counts[i] in 1..128;
+ * outs[i]: device buffer u[counts[i]][n_x][n_t] in plan i's precision;
+ * stream: cudaStream_t, NULL = a stream of the batch's own.  While the batch
+ * exists the plans' workspaces belong to it: they may not grow (srm3_sample
+ * with more samples than the batch gave a plan fails with NOT_SUPPORTED),
+ * and sampling from a plan while a batch run may be in flight races.  The
+ * plans must outlive the batch.  Errors: INVALID_ARG, NOT_SUPPORTED,
+ * OUT_OF_MEMORY, CUDA. */
+typedef struct srm3_batch srm3_batch;
+int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts, void *const *outs, int m,
+                      void *stream, srm3_batch **out);
+
+/* Run the batch for seeds[sum of counts] (host; plan 0's seeds first, then
+ * plan 1's, ...).  The seeds go through a pinned staging buffer into a
+ * device buffer that the phase kernels read.  After srm3_batch_capture the
+ * launch sequence is the captured graph.  Asynchronous on the batch stream.
+ * A sample's field is bit-identical to srm3_sample of the same plan and seed. */
+int srm3_batch_run(srm3_batch *b, const uint64_t *seeds);
+
+/* Capture the batch's launch sequence (phases, pair sums, transforms) into a
+ * CUDA graph by stream capture on the batch stream, and replay that graph in
+ * later srm3_batch_run calls.  Nothing is allocated during the capture. */
+int srm3_batch_capture(srm3_batch *b);
+
+/* Wait for the batch stream; returns the first asynchronous error. */
+int srm3_batch_sync(srm3_batch *b);
+
+/* Pair-terms of one run: sum over plans of 2 |Pi| counts[i]. */
+int64_t srm3_batch_pair_terms(const srm3_batch *b);
+
+/* Free the batch (not its plans).  NULL is a no-op.  No run may be in flight. */
+void srm3_batch_destroy(srm3_batch *b);
 
 #ifdef __cplusplus
 }

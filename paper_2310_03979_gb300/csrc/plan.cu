@@ -567,6 +567,33 @@ static long long tile_entries(int kk, int tw) {
   return (long long)(kk / 2 + 1) * kTileR * L;
 }
 
+// W table of an FP32 plan (tile offsets and sampling tables ready), on st;
+// records its build time and size.
+int build_w_table(srm3_plan *p, cudaStream_t st) {
+  if (p->W) return SRM3_OK;
+  const double bytes = (double)p->table_entries * sizeof(float);
+  cudaError_t e = cudaMalloc(&p->W, (size_t)p->table_entries * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(W table)");
+  cudaEvent_t ev[2];
+  SRM3_CUDA(cudaEventCreate(&ev[0]));
+  SRM3_CUDA(cudaEventCreate(&ev[1]));
+  cudaEventRecord(ev[0], st);
+  k_build_w<<<p->ntiles, dim3(32, 8), 0, st>>>(p->nk, p->nw, p->ntw, p->tile_off,
+                                               (const float *)p->ck, (const float *)p->Ek,
+                                               (const float *)p->Ews, p->ew_off, p->W);
+  e = cudaGetLastError();
+  cudaEventRecord(ev[1], st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+  float tms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&tms, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "W table build");
+  p->t_table_ms = tms;
+  p->table_bytes = bytes;
+  return SRM3_OK;
+}
+
 static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long *table_entries) {
   const int nk = p->nk;
   p->ntw = cdiv(p->nw, kTileR);
@@ -603,11 +630,10 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
                             cudaMemcpyHostToDevice, st));
   p->super_host = sup;
   *table_entries = off[p->ntiles];
-  if (want_table) {
-    SRM3_CUDA(cudaMalloc(&p->tile_off, sizeof(long long) * p->ntiles));
-    SRM3_CUDA(cudaMemcpyAsync(p->tile_off, off.data(), sizeof(long long) * p->ntiles,
-                              cudaMemcpyHostToDevice, st));
-  }
+  (void)want_table;  // offsets are kept either way: the autotuner may build W later
+  SRM3_CUDA(cudaMalloc(&p->tile_off, sizeof(long long) * p->ntiles));
+  SRM3_CUDA(cudaMemcpyAsync(p->tile_off, off.data(), sizeof(long long) * p->ntiles,
+                            cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaStreamSynchronize(st));
   return SRM3_OK;
 }
@@ -699,24 +725,17 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     bool maybe_table = p->storage != SRM3_STORAGE_RECOMPUTE;
     rc = build_tiles(p, st, maybe_table, &entries);
     if (rc) return rc;
-    double bytes = (double)entries * sizeof(float);
+    p->table_entries = entries;
+    const double bytes = (double)entries * sizeof(float);
+    if (p->storage == SRM3_STORAGE_TUNED) {  // the autotuner's choice for this lattice
+      const int c = tune_cache_lookup(nk, nw);
+      p->storage = c >= 0 ? c : SRM3_STORAGE_AUTO;
+    }
     if (p->storage == SRM3_STORAGE_AUTO) {
       p->storage = bytes <= p->table_budget ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
     }
     if (p->storage == SRM3_STORAGE_TABLE) {
-      cudaError_t e = cudaMalloc(&p->W, (size_t)entries * sizeof(float));
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(W table)");
-      SRM3_CUDA(cudaEventRecord(t_ev[0], st));
-      k_build_w<<<p->ntiles, dim3(32, 8), 0, st>>>(nk, nw, p->ntw, p->tile_off, (const float *)p->ck,
-                                            (const float *)p->Ek, (const float *)p->Ews,
-                                            p->ew_off, p->W);
-      SRM3_CUDA(cudaGetLastError());
-      SRM3_CUDA(cudaEventRecord(t_ev[1], st));
-      SRM3_CUDA(cudaEventSynchronize(t_ev[1]));
-      float tms = 0.f;
-      SRM3_CUDA(cudaEventElapsedTime(&tms, t_ev[0], t_ev[1]));
-      p->t_table_ms = tms;
-      p->table_bytes = bytes;
+      if ((rc = build_w_table(p, st))) return rc;
     } else {
       p->table_bytes = 0.0;
     }
@@ -812,7 +831,7 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
     return fail(SRM3_ERR_INVALID_ARG, "cutoffs must be positive");
   if (g.precision != SRM3_FP32 && g.precision != SRM3_FP64)
     return fail(SRM3_ERR_INVALID_ARG, "unknown precision");
-  if (g.storage < SRM3_STORAGE_AUTO || g.storage > SRM3_STORAGE_RECOMPUTE)
+  if (g.storage < SRM3_STORAGE_AUTO || g.storage > SRM3_STORAGE_TUNED)
     return fail(SRM3_ERR_INVALID_ARG, "unknown storage");
   if (g.precision == SRM3_FP64 && g.storage == SRM3_STORAGE_TABLE)
     return fail(SRM3_ERR_NOT_SUPPORTED, "the W table is FP32; FP64 plans recompute W");

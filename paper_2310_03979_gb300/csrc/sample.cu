@@ -3,6 +3,8 @@
 // Sec. 4.3), and the hand-written 2-D inverse FFT to u(x,t).
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
@@ -65,6 +67,7 @@ __device__ __forceinline__ double2 phasor(uint32_t w, double) {
 // words != NULL writes the raw words[n][2][nk][nw] instead.
 template <typename T>
 __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
+                         const uint64_t *__restrict__ dseeds,
                          const T *__restrict__ sqq, typename Vec2<T>::type *__restrict__ y,
                          typename Vec2<T>::type *__restrict__ y0, int SSpad, int rowstride,
                          uint32_t *__restrict__ words) {
@@ -75,7 +78,7 @@ __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
   if (gid >= nc * nsamp) return;
   const int n = (int)(gid % nsamp);
   const long long c = gid / nsamp;
-  const uint64_t seed = seeds.s[n];
+  const uint64_t seed = dseeds ? dseeds[n] : seeds.s[n];
   uint4 out = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, 0u),
                             make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
   const uint32_t wv[4] = {out.x, out.y, out.z, out.w};
@@ -124,6 +127,9 @@ int sspad_for(int chunk) { return ((2 * chunk + 63) / 64) * 64; }
 
 int ensure_workspace(srm3_plan *p, int chunk) {
   if (p->ws_chunk >= chunk) return SRM3_OK;
+  if (p->batch_refs > 0)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "the plan's workspace belongs to a batch and cannot grow while the batch exists");
   int cap = std::max(chunk, std::min(kMaxChunk, 64));
   for (void **q : {&p->y, &p->y0, &p->C, &p->H}) {
     if (*q) cudaFree(*q);
@@ -141,27 +147,34 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   return SRM3_OK;
 }
 
-int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out) {
+// Phases of n samples on stream st: seeds from the host array `seeds`
+// (passed by value) or, when dseeds != NULL, from device memory.
+static int phases_on(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
+                     const uint64_t *dseeds, int n, uint32_t *words_out) {
   SeedChunk sc;
   std::memset(&sc, 0, sizeof(sc));
-  std::memcpy(sc.s, seeds, sizeof(uint64_t) * n);
+  if (!dseeds) std::memcpy(sc.s, seeds, sizeof(uint64_t) * n);
   const long long nl = (long long)p->nk * p->nw;
   const long long nc = (2 * nl + 3) / 4;
   const int blocks = cdiv(nc * n, 256);
   const int sp = sspad_for(n);
   if (!words_out) {
-    SRM3_CUDA(cudaMemsetAsync(p->y, 0, (size_t)p->nk * p->rowstride * sp * elem2(p), p->stream));
+    SRM3_CUDA(cudaMemsetAsync(p->y, 0, (size_t)p->nk * p->rowstride * sp * elem2(p), st));
   }
   if (p->precision == SRM3_FP32)
-    k_phases<float><<<blocks, 256, 0, p->stream>>>(p->nk, p->nw, n, sc, (const float *)p->sqq,
-                                                   (float2 *)p->y, (float2 *)p->y0, sp,
-                                                   p->rowstride, words_out);
+    k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, (const float *)p->sqq,
+                                            (float2 *)p->y, (float2 *)p->y0, sp, p->rowstride,
+                                            words_out);
   else
-    k_phases<double><<<blocks, 256, 0, p->stream>>>(p->nk, p->nw, n, sc, (const double *)p->sqq,
-                                                    (double2 *)p->y, (double2 *)p->y0, sp,
-                                                    p->rowstride, words_out);
+    k_phases<double><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds,
+                                             (const double *)p->sqq, (double2 *)p->y,
+                                             (double2 *)p->y0, sp, p->rowstride, words_out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
+}
+
+int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out) {
+  return phases_on(p, p->stream, seeds, nullptr, n, words_out);
 }
 
 // Descriptor of plan p for an FP32 pair-sum launch over n samples whose
@@ -240,6 +253,17 @@ int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const Ps
   return SRM3_OK;
 }
 
+static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
+  const int SS = 2 * n, sp = sspad_for(n);
+  const long long threads = (long long)p->nk * p->nw * sp;
+  k_pairsum_f64<<<cdiv(threads, 256), 256, 0, st>>>(
+      p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
+      (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
+      (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
 int run_pairsum(srm3_plan *p, int n, void *C_out) {
   const int SS = 2 * n, sp = sspad_for(n);
   if (p->precision == SRM3_FP64) {
@@ -259,7 +283,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
 }
 
 template <typename T, typename T2>
-static int transform_impl(srm3_plan *p, const T2 *C, int n, T *out) {
+static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out) {
   const int log2nfft = ilog2_exact(p->nfft);
   const size_t e2 = sizeof(T2);
   const size_t smem_t = (size_t)p->nt * e2;
@@ -269,20 +293,24 @@ static int transform_impl(srm3_plan *p, const T2 *C, int n, T *out) {
   const int lim = 200 * 1024;
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt,
+  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt,
                                                           log2nfft, C, (const T2 *)p->tw,
                                                           (T2 *)p->H);
   SRM3_CUDA(cudaGetLastError());
-  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, p->stream>>>(
+  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, st>>>(
       p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, (const T2 *)p->H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
 
-int run_transform(srm3_plan *p, const void *C, int n, void *out) {
+static int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out) {
   if (p->precision == SRM3_FP32)
-    return transform_impl<float, float2>(p, (const float2 *)C, n, (float *)out);
-  return transform_impl<double, double2>(p, (const double2 *)C, n, (double *)out);
+    return transform_impl<float, float2>(p, st, (const float2 *)C, n, (float *)out);
+  return transform_impl<double, double2>(p, st, (const double2 *)C, n, (double *)out);
+}
+
+int run_transform(srm3_plan *p, const void *C, int n, void *out) {
+  return transform_on(p, p->stream, C, n, out);
 }
 
 int check_pairsum_error(srm3_plan *p) {
@@ -361,9 +389,85 @@ static size_t elem1(const srm3_plan *p) {
   return p->precision == SRM3_FP32 ? sizeof(float) : sizeof(double);
 }
 
+// Autotuner choices per lattice shape, process-wide.
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, int> g_tune;
+
+int tune_cache_lookup(int nk, int nw) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find({nk, nw});
+  return it == g_tune.end() ? -1 : it->second;
+}
+
+void tune_cache_store(int nk, int nw, int storage) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[{nk, nw}] = storage;
+}
+
 }  // namespace srm3
 
+// A sampling job over several plans (see srm3_batch_create).
+struct srm3_batch {
+  std::vector<srm3_plan *> plans;
+  std::vector<int> counts, seed_off;
+  std::vector<void *> outs;
+  int total = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t *dseeds = nullptr;     // device seeds the phase kernels read
+  uint64_t *hseeds = nullptr;     // pinned staging buffer
+  cudaEvent_t staged = nullptr;   // last copy out of the staging buffer
+  bool staged_pending = false;
+  srm3::PsDesc *ddesc = nullptr;  // per FP32 plan
+  int4 *dunits = nullptr;         // work units of all FP32 plans, by decreasing cost
+  int nunits = 0;
+  srm3_plan *lead = nullptr;      // first FP32 plan: CTA count and error word of the launch
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long pair_terms = 0;
+  bool holds_refs = false;        // the plans' batch_refs were raised
+};
+
 using namespace srm3;
+
+// The launch sequence of one batch run on the batch stream.
+static int batch_launch(srm3_batch *b) {
+  int rc;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if ((rc = phases_on(b->plans[i], b->stream, nullptr, b->dseeds + b->seed_off[i], b->counts[i],
+                        nullptr)))
+      return rc;
+  if (b->nunits > 0) {
+    PsDesc none;
+    std::memset(static_cast<void *>(&none), 0, sizeof(none));
+    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits)))
+      return rc;
+  }
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if (b->plans[i]->precision == SRM3_FP64 &&
+        (rc = pairsum_f64_on(b->plans[i], b->stream, b->counts[i], b->plans[i]->C)))
+      return rc;
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    if ((rc = transform_on(b->plans[i], b->stream, b->plans[i]->C, b->counts[i], b->outs[i])))
+      return rc;
+  return SRM3_OK;
+}
+
+static void batch_free(srm3_batch *b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->holds_refs)
+    for (srm3_plan *p : b->plans) --p->batch_refs;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->staged) cudaEventDestroy(b->staged);
+  if (b->dseeds) cudaFree(b->dseeds);
+  if (b->hseeds) cudaFreeHost(b->hseeds);
+  if (b->ddesc) cudaFree(b->ddesc);
+  if (b->dunits) cudaFree(b->dunits);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
 
 SRM3_API int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *out) {
   int rc = check_call(plan, seeds, n, out);
@@ -471,4 +575,209 @@ SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
     plan->t_pair_terms = 0;
   }
   return SRM3_OK;
+}
+
+SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
+  if (!plan || !res) return fail(SRM3_ERR_INVALID_ARG, "plan and result must be non-NULL");
+  if (n < 1 || n > kMaxChunk) return fail(SRM3_ERR_INVALID_ARG, "n must be in 1..128");
+  if (plan->precision != SRM3_FP32)
+    return fail(SRM3_ERR_NOT_SUPPORTED, "autotuning applies to FP32 plans only");
+  int rc = ensure_workspace(plan, n);
+  if (rc) return rc;
+  std::vector<uint64_t> seeds(n);
+  for (int j = 0; j < n; ++j) seeds[j] = (uint64_t)j + 1;
+  if ((rc = run_phases(plan, seeds.data(), n, nullptr))) return rc;
+  const bool can_table = (double)plan->table_entries * sizeof(float) <= plan->table_budget;
+  if (can_table && !plan->W) {
+    if ((rc = build_w_table(plan, plan->stream))) return rc;
+  }
+  cudaEvent_t ev[2];
+  SRM3_CUDA(cudaEventCreate(&ev[0]));
+  SRM3_CUDA(cudaEventCreate(&ev[1]));
+  auto time_one = [&](int storage, double *ms) -> int {
+    plan->storage = storage;
+    PsDesc d;
+    int r = fill_pairsum_desc(plan, n, plan->C, &d);
+    if (r) return r;
+    const int nunits = plan->nsuper * d.G;
+    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits))) return r;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      SRM3_CUDA(cudaEventRecord(ev[0], plan->stream));
+      if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits))) return r;
+      SRM3_CUDA(cudaEventRecord(ev[1], plan->stream));
+      SRM3_CUDA(cudaEventSynchronize(ev[1]));
+      float t = 0.f;
+      SRM3_CUDA(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      best = std::min(best, t);
+    }
+    *ms = best;
+    return SRM3_OK;
+  };
+  double t_tab = -1.0, t_rec = -1.0;
+  if (plan->W) rc = time_one(SRM3_STORAGE_TABLE, &t_tab);
+  if (!rc) rc = time_one(SRM3_STORAGE_RECOMPUTE, &t_rec);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  const int choice =
+      (t_tab >= 0.0 && t_tab < t_rec) ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
+  plan->storage = choice;
+  if (choice == SRM3_STORAGE_RECOMPUTE && plan->W) {
+    SRM3_CUDA(cudaStreamSynchronize(plan->stream));
+    SRM3_CUDA(cudaFree(plan->W));
+    plan->W = nullptr;
+    plan->table_bytes = 0.0;
+  }
+  tune_cache_store(plan->nk, plan->nw, choice);
+  res->table_ms = t_tab;
+  res->recompute_ms = t_rec;
+  res->storage = choice;
+  res->samples = n;
+  SRM3_CUDA(cudaStreamSynchronize(plan->stream));
+  return check_pairsum_error(plan);
+}
+
+SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
+                               void *const *outs, int m, void *stream, srm3_batch **out) {
+  if (!out) return fail(SRM3_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || !plans || !counts || !outs)
+    return fail(SRM3_ERR_INVALID_ARG, "need m >= 1 plans, counts and outputs");
+  int dev = -1;
+  for (int i = 0; i < m; ++i) {
+    if (!plans[i] || !outs[i])
+      return fail(SRM3_ERR_INVALID_ARG, "NULL plan or output in the batch");
+    if (counts[i] < 1 || counts[i] > kMaxChunk)
+      return fail(SRM3_ERR_INVALID_ARG, "batch sample counts must be in 1..128");
+    if (dev < 0) dev = plans[i]->device;
+    if (plans[i]->device != dev)
+      return fail(SRM3_ERR_NOT_SUPPORTED, "the plans of a batch must be on one device");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i])
+        return fail(SRM3_ERR_INVALID_ARG,
+                    "a plan appears twice in the batch (it has one workspace)");
+  }
+  srm3_batch *b = new srm3_batch();
+  auto bail = [&](int rc) {
+    batch_free(b);
+    return rc;
+  };
+  int rc;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreateWithFlags"));
+    b->own_stream = true;
+  }
+  std::vector<PsDesc> descs;
+  std::vector<std::pair<long long, int4>> units;
+  for (int i = 0; i < m; ++i) {
+    srm3_plan *p = plans[i];
+    if ((rc = ensure_workspace(p, counts[i]))) return bail(rc);
+    b->plans.push_back(p);
+    b->counts.push_back(counts[i]);
+    b->outs.push_back(outs[i]);
+    b->seed_off.push_back(b->total);
+    b->total += counts[i];
+    b->pair_terms += 2LL * p->pairs * counts[i];
+    if (p->precision == SRM3_FP32) {
+      PsDesc d;
+      if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
+      const int j = (int)descs.size();
+      descs.push_back(d);
+      if (!b->lead) b->lead = p;
+      for (const int2 &t : p->super_host) {
+        const long long cost =
+            (long long)(t.x / 2 + 1) * ((t.y + packed::SW + packed::CH - 1) / packed::CH);
+        for (int g = 0; g < d.G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
+      }
+    }
+  }
+  std::stable_sort(units.begin(), units.end(),
+                   [](const std::pair<long long, int4> &x, const std::pair<long long, int4> &y) {
+                     return x.first > y.first;
+                   });
+  b->nunits = (int)units.size();
+  cudaError_t e;
+  if (!descs.empty()) {
+    e = cudaMalloc(&b->ddesc, sizeof(PsDesc) * descs.size());
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch descriptors)"));
+    e = cudaMemcpy(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy(batch descriptors)"));
+    std::vector<int4> u(units.size());
+    for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
+    e = cudaMalloc(&b->dunits, sizeof(int4) * u.size());
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch units)"));
+    e = cudaMemcpy(b->dunits, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy(batch units)"));
+    // kernel attributes and resident CTA count, set before any capture
+    PsDesc none;
+    std::memset(static_cast<void *>(&none), 0, sizeof(none));
+    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0)))
+      return bail(rc);
+  }
+  e = cudaMalloc(&b->dseeds, sizeof(uint64_t) * b->total);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch seeds)"));
+  e = cudaMallocHost(&b->hseeds, sizeof(uint64_t) * b->total);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(batch seeds)"));
+  e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+  for (srm3_plan *p : b->plans) ++p->batch_refs;
+  b->holds_refs = true;
+  *out = b;
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_batch_run(srm3_batch *b, const uint64_t *seeds) {
+  if (!b || !seeds) return fail(SRM3_ERR_INVALID_ARG, "batch and seeds must be non-NULL");
+  if (b->staged_pending) SRM3_CUDA(cudaEventSynchronize(b->staged));
+  std::memcpy(b->hseeds, seeds, sizeof(uint64_t) * b->total);
+  SRM3_CUDA(cudaMemcpyAsync(b->dseeds, b->hseeds, sizeof(uint64_t) * b->total,
+                            cudaMemcpyHostToDevice, b->stream));
+  SRM3_CUDA(cudaEventRecord(b->staged, b->stream));
+  b->staged_pending = true;
+  if (b->exec) {
+    SRM3_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    return SRM3_OK;
+  }
+  return batch_launch(b);
+}
+
+SRM3_API int srm3_batch_capture(srm3_batch *b) {
+  if (!b) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL");
+  SRM3_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  SRM3_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  const int rc = batch_launch(b);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  b->graph = g;
+  SRM3_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_batch_sync(srm3_batch *b) {
+  if (!b) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL");
+  SRM3_CUDA(cudaStreamSynchronize(b->stream));
+  return b->lead ? check_pairsum_error(b->lead) : SRM3_OK;
+}
+
+SRM3_API int64_t srm3_batch_pair_terms(const srm3_batch *b) { return b ? b->pair_terms : 0; }
+
+SRM3_API void srm3_batch_destroy(srm3_batch *b) {
+  if (b) batch_free(b);
 }

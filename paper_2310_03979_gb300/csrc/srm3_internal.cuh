@@ -91,6 +91,7 @@ struct srm3_plan {
 
   // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
   int ntw = 0, ntiles = 0;
+  long long table_entries = 0;    // floats of the W table (built or not)
   int ps_ctas = 0;                // resident CTAs of the persistent FP32 pair sum
   int *ps_err = nullptr;          // its error word (bounded waits that ran out)
   int2 *tile_order = nullptr;
@@ -102,6 +103,7 @@ struct srm3_plan {
 
   // sampling workspace
   int ws_chunk = 0;
+  int batch_refs = 0;             // batches holding this workspace (it may not grow)
   void *y = nullptr, *y0 = nullptr, *C = nullptr, *H = nullptr;
   int rowstride = 0;
 
@@ -145,6 +147,10 @@ int stage_end(srm3_plan *p, int rec);
 int collect_timings(srm3_plan *p);
 int check_pairsum_error(srm3_plan *p);
 int sspad_for(int chunk);
+int build_w_table(srm3_plan *p, cudaStream_t st);
+// autotuner choices per lattice shape (process-wide): storage or -1
+int tune_cache_lookup(int nk, int nw);
+void tune_cache_store(int nk, int nw, int storage);
 }  // namespace srm3
 
 static inline int ilog2_exact(int v) {

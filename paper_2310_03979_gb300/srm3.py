@@ -27,14 +27,21 @@ SRM3_SPECTRUM_KAIMAL_LORENTZIAN = 0
 SRM3_SPECTRUM_TABLE = 1
 SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0
 SRM3_FP32, SRM3_FP64 = 0, 1
-SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE = 0, 1, 2
+SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE, SRM3_STORAGE_TUNED = 0, 1, 2, 3
 EXPORTED = [
     "srm3_plan_create", "srm3_sample", "srm3_sample_host", "srm3_destroy", "srm3_sync",
     "srm3_set_stream", "srm3_last_error", "srm3_plan_info", "srm3_plan_tables",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
-    "srm3_get_timings", "srm3_field_from_coeffs_noalloc",
+    "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
+    "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
+    "srm3_batch_pair_terms", "srm3_batch_destroy",
 ]
 SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+class srm3_tune_result(ctypes.Structure):
+    _fields_ = [("table_ms", ctypes.c_double), ("recompute_ms", ctypes.c_double),
+                ("storage", ctypes.c_int32), ("samples", ctypes.c_int32)]
 
 
 class srm3_spectrum(ctypes.Structure):
@@ -115,6 +122,16 @@ def load(build_if_needed: bool = True):
     lib.srm3_field_from_coeffs_noalloc.argtypes = [vp, vp, i32, vp]
     lib.srm3_enable_timing.argtypes = [vp, i32]
     lib.srm3_get_timings.argtypes = [vp, ctypes.POINTER(srm3_timings), i32]
+    lib.srm3_autotune.argtypes = [vp, i32, ctypes.POINTER(srm3_tune_result)]
+    lib.srm3_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(vp), i32, vp, ctypes.POINTER(vp)]
+    lib.srm3_batch_run.argtypes = [vp, u64p]
+    lib.srm3_batch_capture.argtypes = [vp]
+    lib.srm3_batch_sync.argtypes = [vp]
+    lib.srm3_batch_pair_terms.argtypes = [vp]
+    lib.srm3_batch_pair_terms.restype = ctypes.c_int64
+    lib.srm3_batch_destroy.argtypes = [vp]
+    lib.srm3_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -203,6 +220,58 @@ def field_from_coeffs_noalloc(plan, C_ptr: int, n, out_ptr: int):
                                                  ctypes.c_void_p(out_ptr)))
 
 
+def autotune(plan, n) -> srm3_tune_result:
+    r = srm3_tune_result()
+    _check(load().srm3_autotune(plan, int(n), ctypes.byref(r)))
+    return r
+
+
+class Batch:
+    """One sampling job over several plans (srm3_batch_*): uneven lattices and
+    sample counts, one persistent pair-sum launch, optionally replayed from a
+    captured CUDA graph.  ``outs`` are device tensors u[counts[i]][n_x][n_t]."""
+
+    def __init__(self, plans, counts, outs, stream=None):
+        m = len(plans)
+        self._plans = list(plans)
+        self._outs = list(outs)
+        self.counts = [int(c) for c in counts]
+        ph = (ctypes.c_void_p * m)(*[p.handle if hasattr(p, "handle") else p for p in plans])
+        cn = (ctypes.c_int32 * m)(*self.counts)
+        op = (ctypes.c_void_p * m)(*[o.data_ptr() if hasattr(o, "data_ptr") else o
+                                     for o in outs])
+        h = ctypes.c_void_p()
+        _check(load().srm3_batch_create(ph, cn, op, m, stream, ctypes.byref(h)))
+        self.handle = h
+
+    @property
+    def pair_terms(self) -> int:
+        return int(load().srm3_batch_pair_terms(self.handle))
+
+    def run(self, seeds):
+        a, p = _seeds(seeds)
+        if len(a) != sum(self.counts):
+            raise ValueError("need one seed per sample of the batch")
+        _check(load().srm3_batch_run(self.handle, p))
+
+    def capture(self):
+        _check(load().srm3_batch_capture(self.handle))
+
+    def sync(self):
+        _check(load().srm3_batch_sync(self.handle))
+
+    def destroy(self):
+        if self.handle:
+            load().srm3_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
 def enable_timing(plan, on: bool):
     _check(load().srm3_enable_timing(plan, int(bool(on))))
 
@@ -217,7 +286,7 @@ def get_timings(plan, reset: bool = False) -> srm3_timings:
 
 _PREC = {"fp32": SRM3_FP32, "fp64": SRM3_FP64}
 _STOR = {"auto": SRM3_STORAGE_AUTO, "table": SRM3_STORAGE_TABLE,
-         "recompute": SRM3_STORAGE_RECOMPUTE}
+         "recompute": SRM3_STORAGE_RECOMPUTE, "tuned": SRM3_STORAGE_TUNED}
 
 
 @dataclass

@@ -1,0 +1,98 @@
+"""Batches of plans (one persistent pair-sum launch over uneven lattices and
+sample counts, optionally replayed from a captured CUDA graph) and the
+storage autotuner, through the C ABI.
+
+A batch runs the same kernels with the same per-unit arithmetic as
+srm3_sample, so its fields must be bit-identical to each plan's own
+srm3_sample for the same seeds, whatever the mix."""
+import pytest
+
+from paper_2310_03979_gb300 import srm3
+from paper_2310_03979_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIX = [  # (lattice, storage, samples)
+    (W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp32"), "recompute", 3),
+    (W.small_case(nk=32, nw=16, nx=32, nt=32, precision="fp32", U=25.0, target=0.3), "table", 1),
+    (W.small_case(nk=17, nw=40, nx=32, nt=128, precision="fp32", z=45.0, target=0.65),
+     "recompute", 5),
+    (W.small_case(nk=16, nw=16, nx=16, nt=32, precision="fp64"), "recompute", 2),
+    (W.small_case(nk=40, nw=70, nx=64, nt=256, precision="fp32", target=0.1), "table", 32),
+]
+
+
+def _dtype(wl):
+    return torch.float32 if wl.precision == "fp32" else torch.float64
+
+
+def _seed_lists(base):
+    seeds = []
+    for i, (_, _, n) in enumerate(MIX):
+        seeds.append([base + i + 1000 * j + 7 for j in range(n)])
+    return seeds
+
+
+def test_batch_matches_srm3_sample_direct_and_graph():
+    plans = [srm3.Plan.create(wl, storage=st) for wl, st, _ in MIX]
+    try:
+        outs = [torch.full((n, wl.n_x, wl.n_t), float("nan"), dtype=_dtype(wl), device="cuda")
+                for wl, _, n in MIX]
+        with srm3.Batch(plans, [n for _, _, n in MIX], outs) as b:
+            assert b.pair_terms == sum(2 * p.info().pairs * n for p, (_, _, n) in zip(plans, MIX))
+            for base, capture in ((1, False), (50, True), (90, False)):
+                if capture:
+                    b.capture()
+                seeds = _seed_lists(base)
+                b.run([s for ss in seeds for s in ss])
+                b.sync()
+                for p, o, ss in zip(plans, outs, seeds):
+                    ref = p.sample(ss)
+                    torch.cuda.synchronize()
+                    assert torch.equal(o, ref), (p.nk, p.nw, base)
+    finally:
+        for p in plans:
+            p.destroy()
+
+
+def test_batch_holds_workspace_and_checks_arguments():
+    wl = MIX[0][0]
+    with srm3.Plan.create(wl) as p:
+        out = torch.empty((2, wl.n_x, wl.n_t), dtype=torch.float32, device="cuda")
+        with pytest.raises(srm3.SRM3Error):
+            srm3.Batch([p, p], [1, 1], [out, out])  # one plan, one workspace
+        with pytest.raises(srm3.SRM3Error):
+            srm3.Batch([p], [0], [out])
+        with srm3.Batch([p], [2], [out]) as b:
+            b.run([1, 2])
+            b.sync()
+            with pytest.raises(srm3.SRM3Error):  # the workspace may not grow under the batch
+                p.sample(list(range(1, 101)))
+        u = p.sample(list(range(1, 101)))  # and may again once the batch is gone
+        torch.cuda.synchronize()
+        assert torch.isfinite(u).all()
+
+
+def test_autotune_chooses_a_storage_and_tuned_plans_use_it():
+    wl = W.small_case(nk=48, nw=96, nx=64, nt=256, precision="fp32", storage="table")
+    seeds = [3, 4, 5, 6]
+    with srm3.Plan.create(wl, storage="recompute") as ref_plan:
+        ref = ref_plan.sample(seeds)
+        torch.cuda.synchronize()
+    with srm3.Plan.create(wl, storage="table") as p:
+        r = srm3.autotune(p.handle, 4)
+        assert r.storage in (srm3.SRM3_STORAGE_TABLE, srm3.SRM3_STORAGE_RECOMPUTE)
+        assert r.table_ms > 0 and r.recompute_ms > 0 and r.samples == 4
+        assert p.info().storage == r.storage
+        assert (p.info().table_bytes > 0) == (r.storage == srm3.SRM3_STORAGE_TABLE)
+        u = p.sample(seeds)
+        torch.cuda.synchronize()
+        scale = ref.abs().max().item()
+        assert (u - ref).abs().max().item() <= 2e-5 * scale
+    with srm3.Plan.create(wl, storage="tuned") as q:
+        assert q.info().storage == r.storage
+    fp64 = W.small_case(nk=16, nw=16, nx=16, nt=32, precision="fp64")
+    with srm3.Plan.create(fp64) as d:
+        with pytest.raises(srm3.SRM3Error):
+            srm3.autotune(d.handle, 2)
