@@ -312,6 +312,15 @@ int srm3_batch_sync(srm3_batch *b);
 /* Pair-terms of one run: sum over plans of 2 |Pi| counts[i]. */
 int64_t srm3_batch_pair_terms(const srm3_batch *b);
 
+/* on != 0: record CUDA events around the batch's FP32 pair-sum launch in
+ * later runs (set it before srm3_batch_capture for graph replays: the
+ * events become event-record nodes of the graph). */
+int srm3_batch_enable_timing(srm3_batch *b, int on);
+
+/* Duration of the pair-sum launch of the last run, in ms (waits for it);
+ * 0 when timing is off or the batch has no FP32 plan. */
+int srm3_batch_pairsum_ms(srm3_batch *b, double *ms);
+
 /* Free the batch (not its plans).  NULL is a no-op.  No run may be in flight. */
 void srm3_batch_destroy(srm3_batch *b);
 

@@ -426,6 +426,8 @@ struct srm3_batch {
   cudaGraphExec_t exec = nullptr;
   long long pair_terms = 0;
   bool holds_refs = false;        // the plans' batch_refs were raised
+  bool timing = false;            // events around the pair-sum launch
+  cudaEvent_t ps_ev[2] = {nullptr, nullptr};
 };
 
 using namespace srm3;
@@ -440,8 +442,10 @@ static int batch_launch(srm3_batch *b) {
   if (b->nunits > 0) {
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
+    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, cudaEventRecordExternal));
     if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits)))
       return rc;
+    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, cudaEventRecordExternal));
   }
   for (size_t i = 0; i < b->plans.size(); ++i)
     if (b->plans[i]->precision == SRM3_FP64 &&
@@ -460,6 +464,8 @@ static void batch_free(srm3_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->staged) cudaEventDestroy(b->staged);
+  for (cudaEvent_t e : b->ps_ev)
+    if (e) cudaEventDestroy(e);
   if (b->dseeds) cudaFree(b->dseeds);
   if (b->hseeds) cudaFreeHost(b->hseeds);
   if (b->ddesc) cudaFree(b->ddesc);
@@ -777,6 +783,27 @@ SRM3_API int srm3_batch_sync(srm3_batch *b) {
 }
 
 SRM3_API int64_t srm3_batch_pair_terms(const srm3_batch *b) { return b ? b->pair_terms : 0; }
+
+SRM3_API int srm3_batch_enable_timing(srm3_batch *b, int on) {
+  if (!b) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL");
+  if (on && !b->ps_ev[0]) {
+    SRM3_CUDA(cudaEventCreate(&b->ps_ev[0]));
+    SRM3_CUDA(cudaEventCreate(&b->ps_ev[1]));
+  }
+  b->timing = on != 0 && b->nunits > 0;
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_batch_pairsum_ms(srm3_batch *b, double *ms) {
+  if (!b || !ms) return fail(SRM3_ERR_INVALID_ARG, "batch and ms must be non-NULL");
+  *ms = 0.0;
+  if (!b->timing) return SRM3_OK;
+  SRM3_CUDA(cudaEventSynchronize(b->ps_ev[1]));
+  float t = 0.f;
+  SRM3_CUDA(cudaEventElapsedTime(&t, b->ps_ev[0], b->ps_ev[1]));
+  *ms = t;
+  return SRM3_OK;
+}
 
 SRM3_API void srm3_batch_destroy(srm3_batch *b) {
   if (b) batch_free(b);

@@ -34,7 +34,8 @@ EXPORTED = [
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
-    "srm3_batch_pair_terms", "srm3_batch_destroy",
+    "srm3_batch_pair_terms", "srm3_batch_destroy", "srm3_batch_enable_timing",
+    "srm3_batch_pairsum_ms",
 ]
 SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -132,6 +133,8 @@ def load(build_if_needed: bool = True):
     lib.srm3_batch_pair_terms.restype = ctypes.c_int64
     lib.srm3_batch_destroy.argtypes = [vp]
     lib.srm3_batch_destroy.restype = None
+    lib.srm3_batch_enable_timing.argtypes = [vp, i32]
+    lib.srm3_batch_pairsum_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     _lib = lib
     return lib
 
@@ -256,6 +259,14 @@ class Batch:
 
     def capture(self):
         _check(load().srm3_batch_capture(self.handle))
+
+    def enable_timing(self, on=True):
+        _check(load().srm3_batch_enable_timing(self.handle, int(bool(on))))
+
+    def pairsum_ms(self) -> float:
+        v = ctypes.c_double()
+        _check(load().srm3_batch_pairsum_ms(self.handle, ctypes.byref(v)))
+        return v.value
 
     def sync(self):
         _check(load().srm3_batch_sync(self.handle))

@@ -41,12 +41,14 @@ def test_batch_matches_srm3_sample_direct_and_graph():
                 for wl, _, n in MIX]
         with srm3.Batch(plans, [n for _, _, n in MIX], outs) as b:
             assert b.pair_terms == sum(2 * p.info().pairs * n for p, (_, _, n) in zip(plans, MIX))
+            b.enable_timing(True)
             for base, capture in ((1, False), (50, True), (90, False)):
                 if capture:
                     b.capture()
                 seeds = _seed_lists(base)
                 b.run([s for ss in seeds for s in ss])
                 b.sync()
+                assert b.pairsum_ms() > 0.0
                 for p, o, ss in zip(plans, outs, seeds):
                     ref = p.sample(ss)
                     torch.cuda.synchronize()
