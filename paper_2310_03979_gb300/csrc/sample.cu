@@ -427,6 +427,7 @@ struct srm3_batch {
   long long pair_terms = 0;
   bool holds_refs = false;        // the plans' batch_refs were raised
   bool timing = false;            // events around the pair-sum launch
+  bool capturing = false;         // inside srm3_batch_capture
   cudaEvent_t ps_ev[2] = {nullptr, nullptr};
 };
 
@@ -442,10 +443,12 @@ static int batch_launch(srm3_batch *b) {
   if (b->nunits > 0) {
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
-    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, cudaEventRecordExternal));
+    // in a capture the events must be external nodes of the graph
+    const unsigned evf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, evf));
     if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits)))
       return rc;
-    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, cudaEventRecordExternal));
+    if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
   for (size_t i = 0; i < b->plans.size(); ++i)
     if (b->plans[i]->precision == SRM3_FP64 &&
@@ -763,7 +766,9 @@ SRM3_API int srm3_batch_capture(srm3_batch *b) {
     b->graph = nullptr;
   }
   SRM3_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  b->capturing = true;
   const int rc = batch_launch(b);
+  b->capturing = false;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
   if (rc) {
