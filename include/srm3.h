@@ -279,10 +279,16 @@ int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *result);
  * One sampling job over m plans with uneven lattices and sample counts: the
  * phases of every plan, ONE persistent pair-sum launch over the work units
  * of all FP32 plans (cost-sorted across plans; FP64 plans get their own
- * plain launches), then the transforms, all on one stream.
- * srm3_batch_create checks the plans (one device, no plan twice), sizes each
- * plan's workspace for its count (this allocates), and puts the per-plan
- * descriptors and the unit list on the device.  counts[i] in 1..128;
+ * plain launches), then the transforms, all on one stream.  FP32 plans with
+ * W recomputed that share a lattice shape (n_kappa, n_omega, n_x, n_t,
+ * cutoffs, envelope width, biphase) form a shape group: their samples share
+ * the lanes of the pair sum -- the weights depend only on the shape, each
+ * sample keeps its own pure and pair factors -- so many spectra with one or
+ * a few samples each still fill the kernel; a group uses buffers of the
+ * batch, not the plans' workspaces.  srm3_batch_create checks the plans
+ * (one device, no plan twice), allocates the group buffers and sizes the
+ * other plans' workspaces for their counts, and puts the descriptors and
+ * the unit list on the device (at most 4096 samples per shape group).  counts[i] in 1..128;
  * outs[i]: device buffer u[counts[i]][n_x][n_t] in plan i's precision;
  * stream: cudaStream_t, NULL = a stream of the batch's own.  While the batch
  * exists the plans' workspaces belong to it: they may not grow (srm3_sample

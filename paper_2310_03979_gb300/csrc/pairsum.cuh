@@ -222,6 +222,10 @@ struct PsDesc {  // aligned as CUtensorMap
   const float *Pk, *ck;  // pure and pair factors
   float2 *C;             // coefficients out [ss][kk][kw]
   const int2 *order;     // super-tiles (kk, kws0) by decreasing cost (single-plan launch)
+  // Shape groups (samples of several plans with one lattice, W recomputed):
+  // per-sample pure and pair factors; NULL = Pk, ck for every sample.
+  const float *const *pk_of;
+  const float *const *ck_of;
   int nk, nw, SS, SSpad, rowstride, ntw, ew_off, table, G;
   float cb, sb;          // cos / sin of the biphase
 };
@@ -510,6 +514,9 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
     }
     if (!tile_ok) continue;
     const int ss0 = grp * 2 * LANES + 2 * lane;
+    if (ss0 >= d.SS) continue;  // padding lanes
+    const float *Pk = d.pk_of ? d.pk_of[ss0 >> 1] : d.Pk;
+    const float *ck = d.ck_of ? d.ck_of[ss0 >> 1] : d.ck;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int kw = kw0 + r;
@@ -517,8 +524,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const int kidx = kk * nw + kw;
       const float4 yk4 =
           d.y[((size_t)kk * d.rowstride + kPad + kw) * SP + (size_t)grp * LANES + lane];
-      const float cf = tab ? 1.0f : d.ck[kidx];
-      const float P = d.Pk[kidx];
+      const float cf = tab ? 1.0f : ck[kidx];
+      const float P = Pk[kidx];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int ss = ss0 + h;

@@ -62,12 +62,12 @@ __device__ __forceinline__ double2 phasor(uint32_t w, double) {
 // a3: phases.  Thread per (Philox counter, sample), sample index fastest.
 // Counter c covers lattice entries e = 4c .. 4c+3 of e = (s nk + kk) nw + kw.
 // Writes y^s_k = sqrt(q_k) z^s_k (0 where S = 0) into the padded layout
-// y[kk][kPad + kw][ss], ss = 2 n + s, except that y at k = 0 goes to y0[ss]
+// y[kk][kPad + kw][ss], ss = ss_off + 2 n + s, except that y at k = 0 goes to y0[ss]
 // and the lattice slot of k = 0 holds 0 (it takes part in no pair).  With
 // words != NULL writes the raw words[n][2][nk][nw] instead.
 template <typename T>
 __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
-                         const uint64_t *__restrict__ dseeds,
+                         const uint64_t *__restrict__ dseeds, int ss_off,
                          const T *__restrict__ sqq, typename Vec2<T>::type *__restrict__ y,
                          typename Vec2<T>::type *__restrict__ y0, int SSpad, int rowstride,
                          uint32_t *__restrict__ words) {
@@ -98,7 +98,7 @@ __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
     T2 v;
     v.x = a * z.x;
     v.y = a * z.y;
-    int ss = 2 * n + s;
+    int ss = ss_off + 2 * n + s;
     if (r == 0) {
       y0[ss] = v;
       v.x = 0;
@@ -147,30 +147,39 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   return SRM3_OK;
 }
 
-// Phases of n samples on stream st: seeds from the host array `seeds`
-// (passed by value) or, when dseeds != NULL, from device memory.
-static int phases_on(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
-                     const uint64_t *dseeds, int n, uint32_t *words_out) {
+// Phases of n samples of plan p on stream st into y / y0 laid out for sp
+// sheet-samples per lattice entry, from sheet-sample ss_off on; seeds from
+// the host array `seeds` (passed by value) or, when dseeds != NULL, from
+// device memory.  The zero padding of y is the caller's.
+static int phases_into(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
+                       const uint64_t *dseeds, int n, void *y, void *y0, int sp, int ss_off,
+                       uint32_t *words_out) {
   SeedChunk sc;
   std::memset(&sc, 0, sizeof(sc));
   if (!dseeds) std::memcpy(sc.s, seeds, sizeof(uint64_t) * n);
   const long long nl = (long long)p->nk * p->nw;
   const long long nc = (2 * nl + 3) / 4;
   const int blocks = cdiv(nc * n, 256);
+  if (p->precision == SRM3_FP32)
+    k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
+                                            (const float *)p->sqq, (float2 *)y, (float2 *)y0,
+                                            sp, p->rowstride, words_out);
+  else
+    k_phases<double><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
+                                             (const double *)p->sqq, (double2 *)y,
+                                             (double2 *)y0, sp, p->rowstride, words_out);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
+// Phases of n samples into the plan's own workspace (zeroed first).
+static int phases_on(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
+                     const uint64_t *dseeds, int n, uint32_t *words_out) {
   const int sp = sspad_for(n);
   if (!words_out) {
     SRM3_CUDA(cudaMemsetAsync(p->y, 0, (size_t)p->nk * p->rowstride * sp * elem2(p), st));
   }
-  if (p->precision == SRM3_FP32)
-    k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, (const float *)p->sqq,
-                                            (float2 *)p->y, (float2 *)p->y0, sp, p->rowstride,
-                                            words_out);
-  else
-    k_phases<double><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds,
-                                             (const double *)p->sqq, (double2 *)p->y,
-                                             (double2 *)p->y0, sp, p->rowstride, words_out);
-  SRM3_CUDA(cudaGetLastError());
-  return SRM3_OK;
+  return phases_into(p, st, seeds, dseeds, n, p->y, p->y0, sp, 0, words_out);
 }
 
 int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out) {
@@ -179,7 +188,15 @@ int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out) 
 
 // Descriptor of plan p for an FP32 pair-sum launch over n samples whose
 // phasor rows are in p->y (laid out for n) and whose coefficients go to C_out.
+static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *C_out,
+                                  PsDesc *d);
 int fill_pairsum_desc(srm3_plan *p, int n, void *C_out, PsDesc *d) {
+  return fill_pairsum_desc_into(p, n, p->y, p->y0, C_out, d);
+}
+
+// The same for phasor rows y / y0 of n samples laid out for sspad_for(n).
+static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *C_out,
+                                  PsDesc *d) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -198,14 +215,14 @@ int fill_pairsum_desc(srm3_plan *p, int n, void *C_out, PsDesc *d) {
   const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
   const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(&d->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p->y, dims, strides,
+  const CUresult r = encode(&d->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, y, dims, strides,
                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   const bool table = p->storage == SRM3_STORAGE_TABLE;
-  d->y = (const float4 *)p->y;
-  d->y0 = (const float2 *)p->y0;
+  d->y = (const float4 *)y;
+  d->y0 = (const float2 *)y0;
   d->Ek = (const float *)p->Ek;
   d->Ew2 = p->Ew2;
   d->W = table ? p->W : nullptr;
@@ -283,7 +300,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
 }
 
 template <typename T, typename T2>
-static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out) {
+static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2 *H) {
   const int log2nfft = ilog2_exact(p->nfft);
   const size_t e2 = sizeof(T2);
   const size_t smem_t = (size_t)p->nt * e2;
@@ -295,22 +312,27 @@ static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt,
                                                           log2nfft, C, (const T2 *)p->tw,
-                                                          (T2 *)p->H);
+                                                          H);
   SRM3_CUDA(cudaGetLastError());
   k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, st>>>(
-      p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, (const T2 *)p->H, (const T2 *)p->tw, out);
+      p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, (const T2 *)H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
 
-static int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out) {
+// The transform of n coefficient sets with the t-stage rows in H (n*nk*nt
+// complex), on stream st.
+static int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out,
+                        void *H) {
   if (p->precision == SRM3_FP32)
-    return transform_impl<float, float2>(p, st, (const float2 *)C, n, (float *)out);
-  return transform_impl<double, double2>(p, st, (const double2 *)C, n, (double *)out);
+    return transform_impl<float, float2>(p, st, (const float2 *)C, n, (float *)out,
+                                         (float2 *)H);
+  return transform_impl<double, double2>(p, st, (const double2 *)C, n, (double *)out,
+                                         (double2 *)H);
 }
 
 int run_transform(srm3_plan *p, const void *C, int n, void *out) {
-  return transform_on(p, p->stream, C, n, out);
+  return transform_on(p, p->stream, C, n, out, p->H);
 }
 
 int check_pairsum_error(srm3_plan *p) {
@@ -406,11 +428,24 @@ void tune_cache_store(int nk, int nw, int storage) {
 
 }  // namespace srm3
 
-// A sampling job over several plans (see srm3_batch_create).
+// A sampling job over several plans (see srm3_batch_create).  FP32 plans
+// with W recomputed and the same lattice shape form one shape group: their
+// samples share the lanes of the pair sum (the weights depend only on the
+// shape; each sample brings its own pure and pair factors) and batch-owned
+// buffers.  Other plans (stored W table, FP64) run on their own workspace.
 struct srm3_batch {
+  struct Group {
+    std::vector<int> members;     // plan indices of the batch
+    std::vector<int> sample_off;  // per member: first sample within the group
+    int total = 0, sp = 0, nmax = 0;
+    void *y = nullptr, *y0 = nullptr, *C = nullptr, *H = nullptr;
+    size_t ybytes = 0;
+    const float **pk_of = nullptr, **ck_of = nullptr;  // device, [total]
+  };
   std::vector<srm3_plan *> plans;
-  std::vector<int> counts, seed_off;
+  std::vector<int> counts, seed_off, group_of;  // group_of[i]: group index or -1
   std::vector<void *> outs;
+  std::vector<Group> groups;
   int total = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -418,8 +453,8 @@ struct srm3_batch {
   uint64_t *hseeds = nullptr;     // pinned staging buffer
   cudaEvent_t staged = nullptr;   // last copy out of the staging buffer
   bool staged_pending = false;
-  srm3::PsDesc *ddesc = nullptr;  // per FP32 plan
-  int4 *dunits = nullptr;         // work units of all FP32 plans, by decreasing cost
+  srm3::PsDesc *ddesc = nullptr;  // per group and per FP32 table plan
+  int4 *dunits = nullptr;         // work units of all of them, by decreasing cost
   int nunits = 0;
   srm3_plan *lead = nullptr;      // first FP32 plan: CTA count and error word of the launch
   cudaGraph_t graph = nullptr;
@@ -436,9 +471,19 @@ using namespace srm3;
 // The launch sequence of one batch run on the batch stream.
 static int batch_launch(srm3_batch *b) {
   int rc;
+  for (auto &g : b->groups) {
+    SRM3_CUDA(cudaMemsetAsync(g.y, 0, g.ybytes, b->stream));
+    for (size_t m = 0; m < g.members.size(); ++m) {
+      const int i = g.members[m];
+      if ((rc = phases_into(b->plans[i], b->stream, nullptr, b->dseeds + b->seed_off[i],
+                            b->counts[i], g.y, g.y0, g.sp, 2 * g.sample_off[m], nullptr)))
+        return rc;
+    }
+  }
   for (size_t i = 0; i < b->plans.size(); ++i)
-    if ((rc = phases_on(b->plans[i], b->stream, nullptr, b->dseeds + b->seed_off[i], b->counts[i],
-                        nullptr)))
+    if (b->group_of[i] < 0 &&
+        (rc = phases_on(b->plans[i], b->stream, nullptr, b->dseeds + b->seed_off[i],
+                        b->counts[i], nullptr)))
       return rc;
   if (b->nunits > 0) {
     PsDesc none;
@@ -454,8 +499,18 @@ static int batch_launch(srm3_batch *b) {
     if (b->plans[i]->precision == SRM3_FP64 &&
         (rc = pairsum_f64_on(b->plans[i], b->stream, b->counts[i], b->plans[i]->C)))
       return rc;
+  for (auto &g : b->groups)
+    for (size_t m = 0; m < g.members.size(); ++m) {
+      const int i = g.members[m];
+      srm3_plan *p = b->plans[i];
+      const char *C = (const char *)g.C + (size_t)2 * g.sample_off[m] * p->nk * p->nw *
+                                              sizeof(float2);
+      if ((rc = transform_on(p, b->stream, C, b->counts[i], b->outs[i], g.H))) return rc;
+    }
   for (size_t i = 0; i < b->plans.size(); ++i)
-    if ((rc = transform_on(b->plans[i], b->stream, b->plans[i]->C, b->counts[i], b->outs[i])))
+    if (b->group_of[i] < 0 &&
+        (rc = transform_on(b->plans[i], b->stream, b->plans[i]->C, b->counts[i], b->outs[i],
+                           b->plans[i]->H)))
       return rc;
   return SRM3_OK;
 }
@@ -469,121 +524,15 @@ static void batch_free(srm3_batch *b) {
   if (b->staged) cudaEventDestroy(b->staged);
   for (cudaEvent_t e : b->ps_ev)
     if (e) cudaEventDestroy(e);
+  for (auto &g : b->groups)
+    for (void *q : {g.y, g.y0, g.C, g.H, (void *)g.pk_of, (void *)g.ck_of})
+      if (q) cudaFree(q);
   if (b->dseeds) cudaFree(b->dseeds);
   if (b->hseeds) cudaFreeHost(b->hseeds);
   if (b->ddesc) cudaFree(b->ddesc);
   if (b->dunits) cudaFree(b->dunits);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
-}
-
-
-SRM3_API int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *out) {
-  int rc = check_call(plan, seeds, n, out);
-  if (rc || n == 0) return rc;
-  const int chunk = std::min(n, kMaxChunk);
-  rc = ensure_workspace(plan, chunk);
-  if (rc) return rc;
-  for (int s0 = 0; s0 < n; s0 += chunk) {
-    const int m = std::min(chunk, n - s0);
-    char *o = (char *)out + (size_t)s0 * field_elems(plan) * elem1(plan);
-    if ((rc = run_chunk(plan, seeds + s0, m, plan->C, o))) return rc;
-  }
-  return SRM3_OK;
-}
-
-SRM3_API int srm3_sample_host(srm3_plan *plan, const uint64_t *seeds, int n, void *out_host) {
-  int rc = check_call(plan, seeds, n, out_host);
-  if (rc || n == 0) return rc;
-  const int chunk = std::min(n, kMaxChunk);
-  rc = ensure_workspace(plan, chunk);
-  if (rc) return rc;
-  const size_t bytes_per = field_elems(plan) * elem1(plan);
-  void *dev = nullptr;
-  SRM3_CUDA(cudaMallocAsync(&dev, (size_t)chunk * bytes_per, plan->stream));
-  for (int s0 = 0; s0 < n && rc == SRM3_OK; s0 += chunk) {
-    const int m = std::min(chunk, n - s0);
-    if ((rc = run_chunk(plan, seeds + s0, m, plan->C, dev))) break;
-    cudaError_t e = cudaMemcpyAsync((char *)out_host + (size_t)s0 * bytes_per, dev,
-                                    (size_t)m * bytes_per, cudaMemcpyDeviceToHost, plan->stream);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(field to host)");
-  }
-  cudaFreeAsync(dev, plan->stream);
-  if (rc) return rc;
-  SRM3_CUDA(cudaStreamSynchronize(plan->stream));
-  return check_pairsum_error(plan);
-}
-
-SRM3_API int srm3_phase_words(srm3_plan *plan, const uint64_t *seeds, int n, uint32_t *words) {
-  int rc = check_call(plan, seeds, n, words);
-  if (rc || n == 0) return rc;
-  const size_t per = (size_t)2 * plan->nk * plan->nw;
-  for (int s0 = 0; s0 < n; s0 += kMaxChunk) {
-    const int m = std::min(kMaxChunk, n - s0);
-    if ((rc = run_phases(plan, seeds + s0, m, words + (size_t)s0 * per))) return rc;
-  }
-  return SRM3_OK;
-}
-
-SRM3_API int srm3_coeffs(srm3_plan *plan, const uint64_t *seeds, int n, void *C) {
-  int rc = check_call(plan, seeds, n, C);
-  if (rc || n == 0) return rc;
-  const int chunk = std::min(n, kMaxChunk);
-  rc = ensure_workspace(plan, chunk);
-  if (rc) return rc;
-  const size_t per = (size_t)2 * plan->nk * plan->nw * elem2(plan);
-  for (int s0 = 0; s0 < n; s0 += chunk) {
-    const int m = std::min(chunk, n - s0);
-    if ((rc = run_chunk(plan, seeds + s0, m, (char *)C + (size_t)s0 * per, nullptr))) return rc;
-  }
-  return SRM3_OK;
-}
-
-SRM3_API int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out) {
-  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
-  if (n < 0 || (n > 0 && (!C || !out))) return fail(SRM3_ERR_INVALID_ARG, "bad C/out/n");
-  if (n == 0) return SRM3_OK;
-  const int chunk = std::min(n, kMaxChunk);
-  int rc = ensure_workspace(plan, chunk);
-  if (rc) return rc;
-  const size_t perC = (size_t)2 * plan->nk * plan->nw * elem2(plan);
-  const size_t perU = field_elems(plan) * elem1(plan);
-  for (int s0 = 0; s0 < n; s0 += chunk) {
-    const int m = std::min(chunk, n - s0);
-    if ((rc = run_transform(plan, (const char *)C + (size_t)s0 * perC, m,
-                            (char *)out + (size_t)s0 * perU)))
-      return rc;
-  }
-  return SRM3_OK;
-}
-
-SRM3_API int srm3_enable_timing(srm3_plan *plan, int on) {
-  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
-  plan->timing = on != 0;
-  return SRM3_OK;
-}
-
-SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
-  if (!plan || !t) return fail(SRM3_ERR_INVALID_ARG, "plan and t must be non-NULL");
-  int rc = collect_timings(plan);
-  if (rc) return rc;
-  t->recursion_ms = plan->t_recursion_ms;
-  t->recursion_fp32_ms = plan->t_rec32_ms;
-  t->recursion_fp64_ms = plan->t_rec64_ms;
-  t->recursion_passes_fp32 = plan->root_passes32;
-  t->table_ms = plan->t_table_ms;
-  t->phases_ms = plan->t_stage_ms[0];
-  t->pairsum_ms = plan->t_stage_ms[1];
-  t->transform_ms = plan->t_stage_ms[2];
-  t->recursion_passes = plan->root_passes;
-  t->pairsum_launches = plan->t_pairsum_launches;
-  t->pair_terms = plan->t_pair_terms;
-  if (reset) {
-    plan->t_stage_ms[0] = plan->t_stage_ms[1] = plan->t_stage_ms[2] = 0.0;
-    plan->t_pairsum_launches = 0;
-    plan->t_pair_terms = 0;
-  }
-  return SRM3_OK;
 }
 
 SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
@@ -682,34 +631,94 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
   }
   std::vector<PsDesc> descs;
   std::vector<std::pair<long long, int4>> units;
+  auto add_units = [&](srm3_plan *p, int j, int G) {
+    for (const int2 &t : p->super_host) {
+      const long long cost =
+          (long long)(t.x / 2 + 1) * ((t.y + packed::SW + packed::CH - 1) / packed::CH);
+      for (int g = 0; g < G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
+    }
+  };
+  auto same_shape = [](const srm3_plan *a, const srm3_plan *c) {
+    return a->nk == c->nk && a->nw == c->nw && a->nx == c->nx && a->nt == c->nt &&
+           a->ku == c->ku && a->wu == c->wu && a->sigma_g == c->sigma_g && a->beta == c->beta;
+  };
   for (int i = 0; i < m; ++i) {
     srm3_plan *p = plans[i];
-    if ((rc = ensure_workspace(p, counts[i]))) return bail(rc);
     b->plans.push_back(p);
     b->counts.push_back(counts[i]);
     b->outs.push_back(outs[i]);
     b->seed_off.push_back(b->total);
     b->total += counts[i];
     b->pair_terms += 2LL * p->pairs * counts[i];
-    if (p->precision == SRM3_FP32) {
-      PsDesc d;
-      if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
-      const int j = (int)descs.size();
-      descs.push_back(d);
-      if (!b->lead) b->lead = p;
-      for (const int2 &t : p->super_host) {
-        const long long cost =
-            (long long)(t.x / 2 + 1) * ((t.y + packed::SW + packed::CH - 1) / packed::CH);
-        for (int g = 0; g < d.G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
+    int gi = -1;
+    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE) {
+      for (size_t g = 0; g < b->groups.size() && gi < 0; ++g)
+        if (same_shape(b->plans[b->groups[g].members[0]], p)) gi = (int)g;
+      if (gi < 0) {
+        gi = (int)b->groups.size();
+        b->groups.emplace_back();
+      }
+      auto &g = b->groups[gi];
+      g.members.push_back(i);
+      g.sample_off.push_back(g.total);
+      g.total += counts[i];
+      g.nmax = std::max(g.nmax, counts[i]);
+    } else if ((rc = ensure_workspace(p, counts[i]))) {
+      return bail(rc);
+    }
+    b->group_of.push_back(gi);
+    if (p->precision == SRM3_FP32 && !b->lead) b->lead = p;
+  }
+  cudaError_t e;
+  for (auto &g : b->groups) {  // batch-owned buffers of each shape group
+    srm3_plan *p = b->plans[g.members[0]];
+    if (g.total > 4096) return bail(fail(SRM3_ERR_INVALID_ARG,
+                                         "more than 4096 samples of one lattice shape"));
+    g.sp = sspad_for(g.total);
+    g.ybytes = (size_t)p->nk * p->rowstride * g.sp * sizeof(float2);
+    const size_t cb = (size_t)2 * g.total * p->nk * p->nw * sizeof(float2);
+    const size_t hb = (size_t)g.nmax * p->nk * p->nt * sizeof(float2);
+    if ((e = cudaMalloc(&g.y, g.ybytes)) != cudaSuccess ||
+        (e = cudaMalloc(&g.y0, (size_t)g.sp * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&g.C, cb)) != cudaSuccess || (e = cudaMalloc(&g.H, hb)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&g.pk_of, sizeof(float *) * g.total)) != cudaSuccess ||
+        (e = cudaMalloc((void **)&g.ck_of, sizeof(float *) * g.total)) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMalloc(batch shape group)"));
+    std::vector<const float *> pk(g.total), ck(g.total);
+    for (size_t mm = 0; mm < g.members.size(); ++mm) {
+      srm3_plan *q = b->plans[g.members[mm]];
+      for (int j = 0; j < b->counts[g.members[mm]]; ++j) {
+        pk[g.sample_off[mm] + j] = (const float *)q->Pk;
+        ck[g.sample_off[mm] + j] = (const float *)q->ck;
       }
     }
+    if ((e = cudaMemcpy(g.pk_of, pk.data(), sizeof(float *) * g.total,
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(g.ck_of, ck.data(), sizeof(float *) * g.total,
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMemcpy(batch factor tables)"));
+    PsDesc d;
+    if ((rc = fill_pairsum_desc_into(p, g.total, g.y, g.y0, g.C, &d))) return bail(rc);
+    d.pk_of = g.pk_of;
+    d.ck_of = g.ck_of;
+    const int j = (int)descs.size();
+    descs.push_back(d);
+    add_units(p, j, d.G);
+  }
+  for (int i = 0; i < m; ++i) {  // FP32 plans with a stored W table, on their workspace
+    srm3_plan *p = b->plans[i];
+    if (b->group_of[i] >= 0 || p->precision != SRM3_FP32) continue;
+    PsDesc d;
+    if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
+    const int j = (int)descs.size();
+    descs.push_back(d);
+    add_units(p, j, d.G);
   }
   std::stable_sort(units.begin(), units.end(),
                    [](const std::pair<long long, int4> &x, const std::pair<long long, int4> &y) {
                      return x.first > y.first;
                    });
   b->nunits = (int)units.size();
-  cudaError_t e;
   if (!descs.empty()) {
     e = cudaMalloc(&b->ddesc, sizeof(PsDesc) * descs.size());
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch descriptors)"));

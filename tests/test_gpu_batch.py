@@ -13,8 +13,10 @@ from paper_2310_03979_gb300 import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-MIX = [  # (lattice, storage, samples)
+MIX = [  # (lattice, storage, samples); the two 24 x 37 spectra form one shape group
     (W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp32"), "recompute", 3),
+    (W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp32", U=45.0, target=0.4),
+     "recompute", 2),
     (W.small_case(nk=32, nw=16, nx=32, nt=32, precision="fp32", U=25.0, target=0.3), "table", 1),
     (W.small_case(nk=17, nw=40, nx=32, nt=128, precision="fp32", z=45.0, target=0.65),
      "recompute", 5),
