@@ -535,6 +535,114 @@ static void batch_free(srm3_batch *b) {
   delete b;
 }
 
+SRM3_API int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *out) {
+  int rc = check_call(plan, seeds, n, out);
+  if (rc || n == 0) return rc;
+  const int chunk = std::min(n, kMaxChunk);
+  rc = ensure_workspace(plan, chunk);
+  if (rc) return rc;
+  for (int s0 = 0; s0 < n; s0 += chunk) {
+    const int m = std::min(chunk, n - s0);
+    char *o = (char *)out + (size_t)s0 * field_elems(plan) * elem1(plan);
+    if ((rc = run_chunk(plan, seeds + s0, m, plan->C, o))) return rc;
+  }
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_sample_host(srm3_plan *plan, const uint64_t *seeds, int n, void *out_host) {
+  int rc = check_call(plan, seeds, n, out_host);
+  if (rc || n == 0) return rc;
+  const int chunk = std::min(n, kMaxChunk);
+  rc = ensure_workspace(plan, chunk);
+  if (rc) return rc;
+  const size_t bytes_per = field_elems(plan) * elem1(plan);
+  void *dev = nullptr;
+  SRM3_CUDA(cudaMallocAsync(&dev, (size_t)chunk * bytes_per, plan->stream));
+  for (int s0 = 0; s0 < n && rc == SRM3_OK; s0 += chunk) {
+    const int m = std::min(chunk, n - s0);
+    if ((rc = run_chunk(plan, seeds + s0, m, plan->C, dev))) break;
+    cudaError_t e = cudaMemcpyAsync((char *)out_host + (size_t)s0 * bytes_per, dev,
+                                    (size_t)m * bytes_per, cudaMemcpyDeviceToHost, plan->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(field to host)");
+  }
+  cudaFreeAsync(dev, plan->stream);
+  if (rc) return rc;
+  SRM3_CUDA(cudaStreamSynchronize(plan->stream));
+  return check_pairsum_error(plan);
+}
+
+SRM3_API int srm3_phase_words(srm3_plan *plan, const uint64_t *seeds, int n, uint32_t *words) {
+  int rc = check_call(plan, seeds, n, words);
+  if (rc || n == 0) return rc;
+  const size_t per = (size_t)2 * plan->nk * plan->nw;
+  for (int s0 = 0; s0 < n; s0 += kMaxChunk) {
+    const int m = std::min(kMaxChunk, n - s0);
+    if ((rc = run_phases(plan, seeds + s0, m, words + (size_t)s0 * per))) return rc;
+  }
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_coeffs(srm3_plan *plan, const uint64_t *seeds, int n, void *C) {
+  int rc = check_call(plan, seeds, n, C);
+  if (rc || n == 0) return rc;
+  const int chunk = std::min(n, kMaxChunk);
+  rc = ensure_workspace(plan, chunk);
+  if (rc) return rc;
+  const size_t per = (size_t)2 * plan->nk * plan->nw * elem2(plan);
+  for (int s0 = 0; s0 < n; s0 += chunk) {
+    const int m = std::min(chunk, n - s0);
+    if ((rc = run_chunk(plan, seeds + s0, m, (char *)C + (size_t)s0 * per, nullptr))) return rc;
+  }
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out) {
+  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
+  if (n < 0 || (n > 0 && (!C || !out))) return fail(SRM3_ERR_INVALID_ARG, "bad C/out/n");
+  if (n == 0) return SRM3_OK;
+  const int chunk = std::min(n, kMaxChunk);
+  int rc = ensure_workspace(plan, chunk);
+  if (rc) return rc;
+  const size_t perC = (size_t)2 * plan->nk * plan->nw * elem2(plan);
+  const size_t perU = field_elems(plan) * elem1(plan);
+  for (int s0 = 0; s0 < n; s0 += chunk) {
+    const int m = std::min(chunk, n - s0);
+    if ((rc = run_transform(plan, (const char *)C + (size_t)s0 * perC, m,
+                            (char *)out + (size_t)s0 * perU)))
+      return rc;
+  }
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_enable_timing(srm3_plan *plan, int on) {
+  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
+  plan->timing = on != 0;
+  return SRM3_OK;
+}
+
+SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
+  if (!plan || !t) return fail(SRM3_ERR_INVALID_ARG, "plan and t must be non-NULL");
+  int rc = collect_timings(plan);
+  if (rc) return rc;
+  t->recursion_ms = plan->t_recursion_ms;
+  t->recursion_fp32_ms = plan->t_rec32_ms;
+  t->recursion_fp64_ms = plan->t_rec64_ms;
+  t->recursion_passes_fp32 = plan->root_passes32;
+  t->table_ms = plan->t_table_ms;
+  t->phases_ms = plan->t_stage_ms[0];
+  t->pairsum_ms = plan->t_stage_ms[1];
+  t->transform_ms = plan->t_stage_ms[2];
+  t->recursion_passes = plan->root_passes;
+  t->pairsum_launches = plan->t_pairsum_launches;
+  t->pair_terms = plan->t_pair_terms;
+  if (reset) {
+    plan->t_stage_ms[0] = plan->t_stage_ms[1] = plan->t_stage_ms[2] = 0.0;
+    plan->t_pairsum_launches = 0;
+    plan->t_pair_terms = 0;
+  }
+  return SRM3_OK;
+}
+
 SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   if (!plan || !res) return fail(SRM3_ERR_INVALID_ARG, "plan and result must be non-NULL");
   if (n < 1 || n > kMaxChunk) return fail(SRM3_ERR_INVALID_ARG, "n must be in 1..128");
