@@ -760,6 +760,7 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
   p->ew_len = p->ew_off + nw + 128;
   p->nfft = std::max(p->nx, p->nt);
+  p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
   SRM3_CUDA(cudaMalloc(&p->sqq, nl * es));
   SRM3_CUDA(cudaMalloc(&p->Pk, nl * es));
   SRM3_CUDA(cudaMalloc(&p->ck, nl * es));
