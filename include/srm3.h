@@ -291,9 +291,10 @@ int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *result);
  * the unit list on the device (at most 4096 samples per shape group).  counts[i] in 1..128;
  * outs[i]: device buffer u[counts[i]][n_x][n_t] in plan i's precision;
  * stream: cudaStream_t, NULL = a stream of the batch's own.  While the batch
- * exists the plans' workspaces belong to it: they may not grow (srm3_sample
- * with more samples than the batch gave a plan fails with NOT_SUPPORTED),
- * and sampling from a plan while a batch run may be in flight races.  The
+ * exists the workspaces of the plans outside shape groups belong to it: they
+ * may not grow (srm3_sample with more samples than the batch gave such a
+ * plan fails with NOT_SUPPORTED), and sampling from such a plan while a
+ * batch run may be in flight races.  The
  * plans must outlive the batch.  Errors: INVALID_ARG, NOT_SUPPORTED,
  * OUT_OF_MEMORY, CUDA. */
 typedef struct srm3_batch srm3_batch;

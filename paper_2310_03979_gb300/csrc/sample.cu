@@ -518,7 +518,8 @@ static int batch_launch(srm3_batch *b) {
 static void batch_free(srm3_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->holds_refs)
-    for (srm3_plan *p : b->plans) --p->batch_refs;
+    for (size_t i = 0; i < b->plans.size(); ++i)
+      if (b->group_of[i] < 0) --b->plans[i]->batch_refs;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->staged) cudaEventDestroy(b->staged);
@@ -850,7 +851,8 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(batch seeds)"));
   e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
-  for (srm3_plan *p : b->plans) ++p->batch_refs;
+  for (int i = 0; i < m; ++i)  // plans whose own workspace the batch uses
+    if (b->group_of[i] < 0) ++b->plans[i]->batch_refs;
   b->holds_refs = true;
   *out = b;
   return SRM3_OK;

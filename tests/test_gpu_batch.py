@@ -62,7 +62,7 @@ def test_batch_matches_srm3_sample_direct_and_graph():
 
 def test_batch_holds_workspace_and_checks_arguments():
     wl = MIX[0][0]
-    with srm3.Plan.create(wl) as p:
+    with srm3.Plan.create(wl, storage="table") as p:  # outside a shape group
         out = torch.empty((2, wl.n_x, wl.n_t), dtype=torch.float32, device="cuda")
         with pytest.raises(srm3.SRM3Error):
             srm3.Batch([p, p], [1, 1], [out, out])  # one plan, one workspace
