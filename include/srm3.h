@@ -302,8 +302,10 @@ int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts, void *cons
                       void *stream, srm3_batch **out);
 
 /* Run the batch for seeds[sum of counts] (host; plan 0's seeds first, then
- * plan 1's, ...).  The seeds go through a pinned staging buffer into a
- * device buffer that the phase kernels read.  After srm3_batch_capture the
+ * plan 1's, ...), read before the call returns; they are copied into a
+ * device buffer that the phase kernels read.  The batch's own buffers are
+ * stream-ordered allocations on its stream: creating or destroying a batch
+ * does not wait for work on other streams.  After srm3_batch_capture the
  * launch sequence is the captured graph.  Asynchronous on the batch stream.
  * A sample's field is bit-identical to srm3_sample of the same plan and seed. */
 int srm3_batch_run(srm3_batch *b, const uint64_t *seeds);

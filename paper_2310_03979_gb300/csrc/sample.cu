@@ -450,9 +450,7 @@ struct srm3_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   uint64_t *dseeds = nullptr;     // device seeds the phase kernels read
-  uint64_t *hseeds = nullptr;     // pinned staging buffer
-  cudaEvent_t staged = nullptr;   // last copy out of the staging buffer
-  bool staged_pending = false;
+  std::vector<uint64_t> hseeds;   // pageable staging copy (read before run returns)
   srm3::PsDesc *ddesc = nullptr;  // per group and per FP32 table plan
   int4 *dunits = nullptr;         // work units of all of them, by decreasing cost
   int nunits = 0;
@@ -515,6 +513,8 @@ static int batch_launch(srm3_batch *b) {
   return SRM3_OK;
 }
 
+// Device buffers of a batch are stream-ordered allocations on its stream, so
+// that creating and freeing batches never waits for work on other streams.
 static void batch_free(srm3_batch *b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->holds_refs)
@@ -522,16 +522,14 @@ static void batch_free(srm3_batch *b) {
       if (b->group_of[i] < 0) --b->plans[i]->batch_refs;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  if (b->staged) cudaEventDestroy(b->staged);
   for (cudaEvent_t e : b->ps_ev)
     if (e) cudaEventDestroy(e);
   for (auto &g : b->groups)
     for (void *q : {g.y, g.y0, g.C, g.H, (void *)g.pk_of, (void *)g.ck_of})
-      if (q) cudaFree(q);
-  if (b->dseeds) cudaFree(b->dseeds);
-  if (b->hseeds) cudaFreeHost(b->hseeds);
-  if (b->ddesc) cudaFree(b->ddesc);
-  if (b->dunits) cudaFree(b->dunits);
+      if (q) cudaFreeAsync(q, b->stream);
+  for (void *q : {(void *)b->dseeds, (void *)b->ddesc, (void *)b->dunits})
+    if (q) cudaFreeAsync(q, b->stream);
+  if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
 }
@@ -787,12 +785,14 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     g.ybytes = (size_t)p->nk * p->rowstride * g.sp * sizeof(float2);
     const size_t cb = (size_t)2 * g.total * p->nk * p->nw * sizeof(float2);
     const size_t hb = (size_t)g.nmax * p->nk * p->nt * sizeof(float2);
-    if ((e = cudaMalloc(&g.y, g.ybytes)) != cudaSuccess ||
-        (e = cudaMalloc(&g.y0, (size_t)g.sp * sizeof(float2))) != cudaSuccess ||
-        (e = cudaMalloc(&g.C, cb)) != cudaSuccess || (e = cudaMalloc(&g.H, hb)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&g.pk_of, sizeof(float *) * g.total)) != cudaSuccess ||
-        (e = cudaMalloc((void **)&g.ck_of, sizeof(float *) * g.total)) != cudaSuccess)
-      return bail(cuda_fail(e, "cudaMalloc(batch shape group)"));
+    cudaStream_t st = b->stream;
+    if ((e = cudaMallocAsync(&g.y, g.ybytes, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&g.y0, (size_t)g.sp * sizeof(float2), st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&g.C, cb, st)) != cudaSuccess ||
+        (e = cudaMallocAsync(&g.H, hb, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&g.pk_of, sizeof(float *) * g.total, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&g.ck_of, sizeof(float *) * g.total, st)) != cudaSuccess)
+      return bail(cuda_fail(e, "cudaMallocAsync(batch shape group)"));
     std::vector<const float *> pk(g.total), ck(g.total);
     for (size_t mm = 0; mm < g.members.size(); ++mm) {
       srm3_plan *q = b->plans[g.members[mm]];
@@ -801,10 +801,11 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
         ck[g.sample_off[mm] + j] = (const float *)q->ck;
       }
     }
-    if ((e = cudaMemcpy(g.pk_of, pk.data(), sizeof(float *) * g.total,
-                        cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(g.ck_of, ck.data(), sizeof(float *) * g.total,
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(g.pk_of, pk.data(), sizeof(float *) * g.total,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(g.ck_of, ck.data(), sizeof(float *) * g.total,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
       return bail(cuda_fail(e, "cudaMemcpy(batch factor tables)"));
     PsDesc d;
     if ((rc = fill_pairsum_desc_into(p, g.total, g.y, g.y0, g.C, &d))) return bail(rc);
@@ -829,28 +830,29 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
                    });
   b->nunits = (int)units.size();
   if (!descs.empty()) {
-    e = cudaMalloc(&b->ddesc, sizeof(PsDesc) * descs.size());
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch descriptors)"));
-    e = cudaMemcpy(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy(batch descriptors)"));
+    e = cudaMallocAsync(&b->ddesc, sizeof(PsDesc) * descs.size(), b->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch descriptors)"));
+    e = cudaMemcpyAsync(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(),
+                        cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(batch descriptors)"));
     std::vector<int4> u(units.size());
     for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
-    e = cudaMalloc(&b->dunits, sizeof(int4) * u.size());
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch units)"));
-    e = cudaMemcpy(b->dunits, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpy(batch units)"));
+    e = cudaMallocAsync(&b->dunits, sizeof(int4) * u.size(), b->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch units)"));
+    e = cudaMemcpyAsync(b->dunits, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(batch units)"));
     // kernel attributes and resident CTA count, set before any capture
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
     if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0)))
       return bail(rc);
   }
-  e = cudaMalloc(&b->dseeds, sizeof(uint64_t) * b->total);
-  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc(batch seeds)"));
-  e = cudaMallocHost(&b->hseeds, sizeof(uint64_t) * b->total);
-  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocHost(batch seeds)"));
-  e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
-  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaEventCreate"));
+  e = cudaMallocAsync(&b->dseeds, sizeof(uint64_t) * b->total, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch seeds)"));
+  b->hseeds.resize(b->total);
   for (int i = 0; i < m; ++i)  // plans whose own workspace the batch uses
     if (b->group_of[i] < 0) ++b->plans[i]->batch_refs;
   b->holds_refs = true;
@@ -860,12 +862,10 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
 
 SRM3_API int srm3_batch_run(srm3_batch *b, const uint64_t *seeds) {
   if (!b || !seeds) return fail(SRM3_ERR_INVALID_ARG, "batch and seeds must be non-NULL");
-  if (b->staged_pending) SRM3_CUDA(cudaEventSynchronize(b->staged));
-  std::memcpy(b->hseeds, seeds, sizeof(uint64_t) * b->total);
-  SRM3_CUDA(cudaMemcpyAsync(b->dseeds, b->hseeds, sizeof(uint64_t) * b->total,
+  // from pageable memory the copy has read the host buffer when it returns
+  std::memcpy(b->hseeds.data(), seeds, sizeof(uint64_t) * b->total);
+  SRM3_CUDA(cudaMemcpyAsync(b->dseeds, b->hseeds.data(), sizeof(uint64_t) * b->total,
                             cudaMemcpyHostToDevice, b->stream));
-  SRM3_CUDA(cudaEventRecord(b->staged, b->stream));
-  b->staged_pending = true;
   if (b->exec) {
     SRM3_CUDA(cudaGraphLaunch(b->exec, b->stream));
     return SRM3_OK;
