@@ -16,6 +16,7 @@ collective on the data path): weak scaling.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -47,10 +48,12 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
     ap.add_argument("--config", default="bridge",
-                    choices=["bridge", "large", "tiny", "prof128", "uneven"],
+                    choices=["bridge", "large", "tiny", "prof128", "uneven", "serve"],
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=10000,
+                    help="serve: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -267,10 +270,131 @@ def run_uneven(args):
     return 0
 
 
+def run_serve(args):
+    """The serving loop: Poisson arrivals (seed 5) of one-sample requests, 90 %
+    on the 32 x 32 lattice (64 x 64 field) and 10 % on the 512 x 1024 lattice
+    (1024 x 2048 field, W recomputed), spectra from a pool of 32 (U, z) draws
+    in the uneven batch's ranges; plan cache under a 150 GB budget; results
+    copied to host at completion; FP64 audit of 1 % of the requests."""
+    import numpy as np
+    import torch
+    from paper_2310_03979_gb300 import serve, srm3
+    from paper_2310_03979_gb300 import workloads as Wl
+
+    rng = np.random.Generator(np.random.PCG64(5))
+    pool = [(float(rng.uniform(20.0, 50.0)), float(rng.uniform(10.0, 60.0))) for _ in range(32)]
+
+    def small(U, z):
+        return Wl.Workload("serve_small", 32, 32, 0.5, 4 * math.pi, U, z, 64, 64, (1,),
+                           precision="fp32", storage="recompute", target=0.5)
+
+    def large(U, z):
+        return Wl.Workload("serve_large", 512, 1024, 0.25, 4 * math.pi, U, z, 1024, 2048, (1,),
+                           precision="fp32", storage="recompute", target=0.5)
+
+    torch.cuda.init()
+    cache = serve.PlanCache(150e9)
+    t0 = time.perf_counter()
+    for U, z in pool:  # warm cache: every plan of the pool built before the timed run
+        cache.build(small(U, z))
+        cache.build(large(U, z))
+    t_warm = time.perf_counter() - t0
+    # capacity of the large class: one full 64-lane group (32 spectra x 1 sample)
+    plans = [cache.lookup(large(U, z)) for U, z in pool]
+    outs = [torch.empty((1, 1024, 2048), device="cuda") for _ in pool]
+    with srm3.Batch(plans, [1] * len(pool), outs) as b:
+        b.run(list(range(len(pool))))
+        b.sync()
+        t1 = time.perf_counter()
+        b.run(list(range(len(pool))))
+        b.sync()
+        t_group = time.perf_counter() - t1
+    del outs
+    rate = 0.7 * (len(pool) / t_group) / 0.1   # requests/s for 70 % of the large-class capacity
+    nreq = args.requests
+    gaps = rng.exponential(1.0 / rate, size=nreq)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    reqs = []
+    for i in range(nreq):
+        U, z = pool[int(rng.integers(0, len(pool)))]
+        wl = large(U, z) if rng.uniform() < 0.1 else small(U, z)
+        reqs.append(serve.Request(i, wl, (1_000_000 + i,), arrival=float(arrivals[i])))
+    srv = serve.Server(budget_bytes=150e9, slots=2, max_samples=512, cache=cache)
+    host = {}
+
+    orig_poll = srv._poll
+
+    def poll_with_copy(now):  # results to host as they complete (end to end)
+        before = len(srv.finished)
+        orig_poll(now)
+        for r in srv.finished[before:]:
+            h = r.out.cpu()
+            if r.rid % 100 == 0:
+                host[r.rid] = h
+            r.out = None
+            r.done = time.perf_counter() - t_run0
+    srv._poll = poll_with_copy
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    time.sleep(0.3)
+    t_run0 = time.perf_counter()
+    wall = srv.run(reqs)
+    clocks = sampler.stop()
+    srv.close()
+    lat = [r.latency * 1e3 for r in reqs]
+    lat_s = [r.latency * 1e3 for r in reqs if r.wl.n_kappa == 32]
+    lat_l = [r.latency * 1e3 for r in reqs if r.wl.n_kappa == 512]
+    pairs = {32: None, 512: None}
+    for r in reqs:
+        k = r.wl.n_kappa
+        if pairs[k] is None:
+            pairs[k] = r.wl.pairs()
+    terms = sum(2 * pairs[r.wl.n_kappa] for r in reqs)
+    # audit: the same seeds through an FP64 plan of the same spectrum
+    worst, audited = 0.0, 0
+    for rid, h in sorted(host.items()):
+        r = reqs[rid]
+        wl64 = dataclasses.replace(r.wl, precision="fp64")
+        with srm3.Plan.create(wl64) as p64:
+            u64 = p64.sample(list(r.seeds)).cpu().double()
+            sigma = math.sqrt(p64.info().variance)
+        worst = max(worst, float((h.double() - u64).abs().max()) / sigma)
+        audited += 1
+    nplans = len(cache.plans)
+    cache.clear()
+    line = {
+        "metric": METRIC, "value": terms / wall, "unit": "pair-terms/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving_loop_poisson_seed5", "requests": nreq,
+                   "mix": "90% 32x32 (64x64 field), 10% 512x1024 (1024x2048 field), 1 sample",
+                   "spectra_pool": len(pool), "arrival_rate_per_s": rate,
+                   "slots": 2, "hbm_budget_bytes": 150e9,
+                   "step": "the whole request stream, results copied to host at completion"},
+        "samples_per_s": nreq / wall,
+        "latency_ms": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99),
+                       "p50_small": serve.percentile(lat_s, 50),
+                       "p99_small": serve.percentile(lat_s, 99),
+                       "p50_large": serve.percentile(lat_l, 50),
+                       "p99_large": serve.percentile(lat_l, 99)},
+        "busy_fraction": srv.busy / wall, "batches": srv.batches,
+        "plan_cache": {"warm_build_s": t_warm, "plans": nplans,
+                       "builds": cache.builds, "evictions": cache.evictions},
+        "large_group_ms": t_group * 1e3,
+        "audit": {"requests": audited, "max_abs_du_over_sigma": worst, "tolerance": 1e-4},
+        "gpu_launches": srv.launches, "clocks": clocks,
+        "e2e": {"value": terms / wall, "unit": "pair-terms/s", "h2d_bytes_per_step": 8 * nreq,
+                "d2h_bytes_per_step": int(sum(r.wl.n_x * r.wl.n_t * 4 for r in reqs))},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = _args()
     if args.config == "uneven" and args.impl != "reference":
         return run_uneven(args)
+    if args.config == "serve" and args.impl != "reference":
+        return run_serve(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -145,6 +145,7 @@ class Server:
         self.missing = collections.deque()      # plans being built
         self.finished = []
         self.batches = 0
+        self.launches = 0                       # kernels: phases + 2 FFT stages per plan, 1 pair sum
         self.busy = 0.0                         # seconds with a batch in flight
         self._busy_since = None
         self._cv = threading.Condition()
@@ -216,6 +217,7 @@ class Server:
         ev.record(s)
         self.inflight[slot] = (b, ev, take, [rs[0].wl for rs in groups.values()], outs)
         self.batches += 1
+        self.launches += 3 * len(plans) + 1
         return True
 
     def _poll(self, now):
