@@ -319,7 +319,8 @@ def run_serve(args):
         U, z = pool[int(rng.integers(0, len(pool)))]
         wl = large(U, z) if rng.uniform() < 0.1 else small(U, z)
         reqs.append(serve.Request(i, wl, (1_000_000 + i,), arrival=float(arrivals[i])))
-    srv = serve.Server(budget_bytes=150e9, slots=2, max_samples=512, cache=cache)
+    srv = serve.Server(budget_bytes=150e9, light_slots=1, heavy_slots=1, max_samples=512,
+                       cache=cache)
     host = {}
 
     orig_poll = srv._poll
@@ -368,7 +369,8 @@ def run_serve(args):
         "config": {"workload": "serving_loop_poisson_seed5", "requests": nreq,
                    "mix": "90% 32x32 (64x64 field), 10% 512x1024 (1024x2048 field), 1 sample",
                    "spectra_pool": len(pool), "arrival_rate_per_s": rate,
-                   "slots": 2, "hbm_budget_bytes": 150e9,
+                   "slots": {"light": 1, "heavy": 1, "heavy_cta_cap": srv.heavy_ctas},
+                   "hbm_budget_bytes": 150e9,
                    "step": "the whole request stream, results copied to host at completion"},
         "samples_per_s": nreq / wall,
         "latency_ms": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99),

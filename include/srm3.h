@@ -321,6 +321,13 @@ int srm3_batch_sync(srm3_batch *b);
 /* Pair-terms of one run: sum over plans of 2 |Pi| counts[i]. */
 int64_t srm3_batch_pair_terms(const srm3_batch *b);
 
+/* Cap the batch's FP32 pair-sum launch at max_ctas CTAs (0: as many as are
+ * resident, the default).  The launch is persistent and otherwise fills
+ * every SM; a cap leaves room for work on other streams to run beside it
+ * (a serving loop keeps short requests moving this way).  Set it before
+ * srm3_batch_capture for graph replays. */
+int srm3_batch_set_max_ctas(srm3_batch *b, int max_ctas);
+
 /* on != 0: record CUDA events around the batch's FP32 pair-sum launch in
  * later runs (set it before srm3_batch_capture for graph replays: the
  * events become event-record nodes of the graph). */

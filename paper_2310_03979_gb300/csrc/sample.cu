@@ -249,7 +249,7 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
 // batch descs/units; the grid is the resident CTA count (persistent kernel).
 // nunits == 0 only prepares (attributes, resident CTA count).
 int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
-                       const int4 *units, int nunits) {
+                       const int4 *units, int nunits, int max_ctas) {
   const size_t smem = pairsum_f32p_smem();
   SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
@@ -263,7 +263,8 @@ int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const Ps
     if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
     p->ps_ctas = nsm * per_sm;
   }
-  const int grid = std::min(nunits, p->ps_ctas);
+  int grid = std::min(nunits, p->ps_ctas);
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (grid == 0) return SRM3_OK;
   k_pairsum_f32p<<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
   SRM3_CUDA(cudaGetLastError());
@@ -293,7 +294,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
     PsDesc d;
     int rc = fill_pairsum_desc(p, n, C_out, &d);
     if (rc) return rc;
-    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G);
+    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0);
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
@@ -461,6 +462,7 @@ struct srm3_batch {
   bool holds_refs = false;        // the plans' batch_refs were raised
   bool timing = false;            // events around the pair-sum launch
   bool capturing = false;         // inside srm3_batch_capture
+  int max_ctas = 0;               // cap on the pair sum's CTAs (0: all resident)
   cudaEvent_t ps_ev[2] = {nullptr, nullptr};
 };
 
@@ -489,7 +491,8 @@ static int batch_launch(srm3_batch *b) {
     // in a capture the events must be external nodes of the graph
     const unsigned evf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, evf));
-    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits)))
+    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits,
+                                 b->max_ctas)))
       return rc;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
@@ -665,11 +668,11 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
     int r = fill_pairsum_desc(plan, n, plan->C, &d);
     if (r) return r;
     const int nunits = plan->nsuper * d.G;
-    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits))) return r;
+    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0))) return r;
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       SRM3_CUDA(cudaEventRecord(ev[0], plan->stream));
-      if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits))) return r;
+      if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0))) return r;
       SRM3_CUDA(cudaEventRecord(ev[1], plan->stream));
       SRM3_CUDA(cudaEventSynchronize(ev[1]));
       float t = 0.f;
@@ -846,7 +849,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     // kernel attributes and resident CTA count, set before any capture
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
-    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0)))
+    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0)))
       return bail(rc);
   }
   e = cudaMallocAsync(&b->dseeds, sizeof(uint64_t) * b->total, b->stream);
@@ -907,6 +910,12 @@ SRM3_API int srm3_batch_sync(srm3_batch *b) {
 }
 
 SRM3_API int64_t srm3_batch_pair_terms(const srm3_batch *b) { return b ? b->pair_terms : 0; }
+
+SRM3_API int srm3_batch_set_max_ctas(srm3_batch *b, int max_ctas) {
+  if (!b || max_ctas < 0) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL or max_ctas < 0");
+  b->max_ctas = max_ctas;
+  return SRM3_OK;
+}
 
 SRM3_API int srm3_batch_enable_timing(srm3_batch *b, int on) {
   if (!b) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL");

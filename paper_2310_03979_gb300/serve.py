@@ -6,10 +6,13 @@ on the device in an LRU cache bounded by an HBM budget, builds missing
 plans on a background thread, and admits waiting requests whenever one of
 its stream slots is free: all admitted requests go into one batch
 (srm3_batch_*), where requests for the same spectrum share a plan and
-spectra of one lattice shape share the lanes of the pair sum.  Up to
-`slots` batches are in flight at once on separate CUDA streams, so work
-admitted while others run overlaps with them on the device.  A request's
-latency runs from its arrival to the completion of its batch.
+spectra of one lattice shape share the lanes of the pair sum.  Requests
+are light or heavy by the pair-terms of one sample (heavy above
+`heavy_terms`); each class has its own queue and stream slots, and a heavy
+batch's persistent pair sum is capped at one CTA per SM so that light
+batches run beside it instead of queueing behind it.  Batches admitted
+while others run overlap with them on the device.  A request's latency runs
+from its arrival to the completion of its batch.
 
 Device memory of a plan (the estimate the budget counts): the FP64/FP32
 plan tables, about 136 bytes per lattice point, plus the W table when
@@ -133,15 +136,19 @@ class PlanCache:
 class Server:
     """Continuous batching over `slots` CUDA streams (see the module text)."""
 
-    def __init__(self, budget_bytes: float = 150e9, slots: int = 2,
-                 max_samples: int = 4096, cache: PlanCache | None = None):
+    def __init__(self, budget_bytes: float = 150e9, light_slots: int = 1, heavy_slots: int = 1,
+                 max_samples: int = 4096, cache: PlanCache | None = None,
+                 heavy_terms: float = 1e9):
         import torch
         self.torch = torch
         self.cache = cache or PlanCache(budget_bytes)
-        self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.inflight = [None] * slots
+        self.slot_class = ["light"] * light_slots + ["heavy"] * heavy_slots
+        self.streams = [torch.cuda.Stream() for _ in self.slot_class]
+        self.inflight = [None] * len(self.slot_class)
         self.max_samples = max_samples
-        self.waiting = collections.deque()      # plans ready
+        self.heavy_terms = heavy_terms
+        self.heavy_ctas = torch.cuda.get_device_properties(0).multi_processor_count
+        self.queues = {"light": collections.deque(), "heavy": collections.deque()}
         self.missing = collections.deque()      # plans being built
         self.finished = []
         self.batches = 0
@@ -164,16 +171,22 @@ class Server:
                 req = self.missing[0]
             self.cache.build(req.wl)
             with self._cv:
-                # every waiting request whose plan now exists moves to the queue
+                # every waiting request whose plan now exists moves to its queue
                 keep = collections.deque()
                 for r in self.missing:
-                    (self.waiting if self.cache.lookup(r.wl) is not None else keep).append(r)
+                    if self.cache.lookup(r.wl) is not None:
+                        self.queues[self._class(r)].append(r)
+                    else:
+                        keep.append(r)
                 self.missing = keep
+
+    def _class(self, req):
+        return "heavy" if 2 * req.wl.pairs() > self.heavy_terms else "light"
 
     def submit(self, req: Request):
         with self._cv:
             if self.cache.lookup(req.wl) is not None:
-                self.waiting.append(req)
+                self.queues[self._class(req)].append(req)
             else:
                 self.missing.append(req)
                 self._cv.notify()
@@ -181,10 +194,11 @@ class Server:
     # -- batches -----------------------------------------------------------
     def _launch(self, slot, now):
         torch = self.torch
+        q = self.queues[self.slot_class[slot]]
         with self._cv:
             take, total = [], 0
-            while self.waiting and total + self.waiting[0].n <= self.max_samples:
-                r = self.waiting.popleft()
+            while q and total + q[0].n <= self.max_samples:
+                r = q.popleft()
                 take.append(r)
                 total += r.n
         if not take:
@@ -212,6 +226,8 @@ class Server:
                 counts.append(n)
                 outs.append(o)
         b = srm3.Batch(plans, counts, outs, stream=s.cuda_stream)
+        if self.slot_class[slot] == "heavy":
+            b.set_max_ctas(self.heavy_ctas)
         b.run(seeds)
         ev = torch.cuda.Event()
         ev.record(s)
@@ -256,7 +272,7 @@ class Server:
             self._account(now)
             launched = False
             for i in range(len(self.streams)):
-                if self.inflight[i] is None and self.waiting:
+                if self.inflight[i] is None and self.queues[self.slot_class[i]]:
                     launched |= self._launch(i, time.perf_counter() - t0)
             self._account(time.perf_counter() - t0)
             if not launched:

@@ -35,7 +35,7 @@ EXPORTED = [
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
     "srm3_batch_pair_terms", "srm3_batch_destroy", "srm3_batch_enable_timing",
-    "srm3_batch_pairsum_ms",
+    "srm3_batch_pairsum_ms", "srm3_batch_set_max_ctas",
 ]
 SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -135,6 +135,7 @@ def load(build_if_needed: bool = True):
     lib.srm3_batch_destroy.restype = None
     lib.srm3_batch_enable_timing.argtypes = [vp, i32]
     lib.srm3_batch_pairsum_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.srm3_batch_set_max_ctas.argtypes = [vp, i32]
     _lib = lib
     return lib
 
@@ -259,6 +260,9 @@ class Batch:
 
     def capture(self):
         _check(load().srm3_batch_capture(self.handle))
+
+    def set_max_ctas(self, n):
+        _check(load().srm3_batch_set_max_ctas(self.handle, int(n)))
 
     def enable_timing(self, on=True):
         _check(load().srm3_batch_enable_timing(self.handle, int(bool(on))))

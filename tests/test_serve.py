@@ -59,7 +59,8 @@ def test_server_results_equal_requests_alone():
         n = 1 + (i * 7) % 4
         reqs.append(serve.Request(i, wl, tuple(100 * i + j for j in range(n)),
                                   arrival=0.002 * i))
-    srv = serve.Server(budget_bytes=1e9, slots=2, max_samples=9)
+    srv = serve.Server(budget_bytes=1e9, light_slots=1, heavy_slots=1, max_samples=9,
+                       heavy_terms=2e5)
     try:
         srv.run(reqs)
         assert len(srv.finished) == 40 and srv.batches >= 2
