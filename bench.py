@@ -299,10 +299,12 @@ def run_serve(args):
         cache.build(small(U, z))
         cache.build(large(U, z))
     t_warm = time.perf_counter() - t0
-    # capacity of the large class: one full 64-lane group (32 spectra x 1 sample)
+    # capacity of the large class as the server runs it: one full 64-lane group
+    # (32 spectra x 1 sample) with the heavy-slot cap of one CTA per SM
     plans = [cache.lookup(large(U, z)) for U, z in pool]
     outs = [torch.empty((1, 1024, 2048), device="cuda") for _ in pool]
     with srm3.Batch(plans, [1] * len(pool), outs) as b:
+        b.set_max_ctas(torch.cuda.get_device_properties(0).multi_processor_count)
         b.run(list(range(len(pool))))
         b.sync()
         t1 = time.perf_counter()
