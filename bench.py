@@ -33,10 +33,11 @@ METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 l
 # DRAM bytes (read + write) of one FP32 pair-sum launch on the 256 x 512 table
 # workload with 64 samples, from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the 128 x 256 table case with 64 samples (same two sample groups per
-# super-tile), scaled by the W table size (x 15.64): profiles/
+# super-tile), reads scaled by the W table size (x 15.64), writes by the
+# coefficient count (x 4): profiles/
 # pairsum_f32p_table_128x256.md.  Valid only for the kernel source it was
 # measured on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
-PAIRSUM_TRAFFIC = {"bytes": 10.18e9, "source_sha256": "9ebd0884bcfb2e24"}
+PAIRSUM_TRAFFIC = {"bytes": 10.23e9, "source_sha256": "ec4134cd6bc62d1d"}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
