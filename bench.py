@@ -53,6 +53,8 @@ def _args():
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip timing the plain FP64 GPU form beside the FP32 line")
     ap.add_argument("--requests", type=int, default=10000,
                     help="serve: number of requests")
     ap.add_argument("--no-e2e", action="store_true")
@@ -578,6 +580,31 @@ def main():
                        "d2h_bytes_per_step": n * wl.n_x * wl.n_t * es,
                        "ms_per_step": e2e_s * 1e3}
 
+    if rank == 0 and wl.precision == "fp32" and not args.no_fp64_form:
+        # the plain FP64 GPU form on the same workload and seeds: sampling only
+        # (plans built beforehand), against the FP32 form's sampling stages
+        fp64_ms, fp32_ms = [], []
+        for prec, sink in (("fp64", fp64_ms), ("fp32", fp32_ms)):
+            p = srm3.Plan.create(wl, precision=prec,
+                                 storage="recompute" if prec == "fp64" else None, stream=sptr)
+            o = torch.empty((n, wl.n_x, wl.n_t),
+                            dtype=torch.float64 if prec == "fp64" else torch.float32,
+                            device="cuda")
+            srm3.sample(p.handle, seeds, n, o.data_ptr())
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                srm3.sample(p.handle, seeds, n, o.data_ptr())
+                e1.record(stream)
+                torch.cuda.synchronize()
+                sink.append(e0.elapsed_time(e1))
+            p.destroy()
+            del o
+        line["vs_fp64_form"] = {
+            "fp64_samples_per_s": n / (min(fp64_ms) * 1e-3),
+            "fp32_samples_per_s": n / (min(fp32_ms) * 1e-3),
+            "speedup": min(fp64_ms) / min(fp32_ms),
+            "note": "sampling only (plans prebuilt), same workload and seeds"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_baseline(wl, rows=128)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
