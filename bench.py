@@ -69,6 +69,31 @@ def _peaks():
         return {}
 
 
+def _pairsum_roofline(terms_per_s, traffic=None, **extra):
+    """Roofline object of the FP32 pair sum from its kernel-only rate.
+
+    The bound is the FP32 pipe.  A pair-term is 6 FP32-pipe lane operations
+    (2 FMUL + 4 FFMA, 10 flop), so the fraction is pair-terms/s x 6 over the
+    pipe's lane-operation rate, 152 SM x 128 lanes x the maximum SM clock.
+    The same rate in flops (10 per pair-term against 2 flop per lane-cycle)
+    is given beside it: its ceiling is 10/12 because an FMUL fills a lane
+    slot for one flop."""
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    lane_rate = FP32_LANES_PER_SM * N_SM * sm_max * 1e6  # lane-ops/s
+    ops = 6.0 * terms_per_s
+    flops = 10.0 * terms_per_s
+    out = {"bound": "alu", "achieved": ops / 1e12, "peak": lane_rate / 1e12,
+           "unit": "T FP32-pipe lane-ops/s", "frac": ops / lane_rate, "traffic": traffic,
+           "per_unit": "6 FP32-pipe lane-ops (2 FMUL + 4 FFMA = 10 flop) per pair-term",
+           "flops": {"achieved": flops / 1e12, "peak": 2.0 * lane_rate / 1e12,
+                     "unit": "TFLOP/s", "frac": flops / (2.0 * lane_rate)},
+           "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x "
+                          f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"}
+    out.update(extra)
+    return out
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 
@@ -233,11 +258,7 @@ def run_uneven(args):
             h.copy_(o, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12
     ps_ms = statistics.median(ps)
-    achieved = 10.0 * terms / (ps_ms * 1e-3) / 1e12
     choice = {}
     for k, v in tuned.items():
         choice[v["storage"]] = choice.get(v["storage"], 0) + 1
@@ -256,9 +277,8 @@ def run_uneven(args):
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "plan_build_s_all_spectra": t_plans, "autotune_s": t_tune,
         "autotune_choices": choice,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "k_pairsum_f32p (batched, one launch)"},
+        "roofline": _pairsum_roofline(terms / (ps_ms * 1e-3),
+                                      kernel="k_pairsum_f32p (batched, one launch)"),
         "gpu_launches": (3 * len(wls) + 1) * args.steps,
         "clocks": clocks,
         "e2e": {"value": terms / (statistics.median(e2e_ms) * 1e-3), "unit": "pair-terms/s",
@@ -504,11 +524,7 @@ def main():
     ps_launch = sum(r[0].pairsum_launches for r in recs)
     ps_terms = sum(r[0].pair_terms for r in recs)
     avg_launch_ms = ps_ms / max(ps_launch, 1)
-    flops_per_launch = 10.0 * ps_terms / max(ps_launch, 1)  # 10 flops per pair-term
-    achieved = flops_per_launch / (avg_launch_ms * 1e-3) / 1e12
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = 2.0 * FP32_LANES_PER_SM * N_SM * sm_max * 1e6 / 1e12
+    terms_per_launch = ps_terms / max(ps_launch, 1)
     info = recs[-1][1]
     t_last = recs[-1][0]
     chunks = math.ceil(n / 128)
@@ -548,15 +564,12 @@ def main():
                                 "transform": t_last.transform_ms},
         "sampling_only_pair_terms_per_s": terms_per_step / (
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": info.table_bytes + n * 2 * 8 * (
-                         wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
-                     "kernel": "k_pairsum_f32p<table>" if info.storage == 1 else
-                               "k_pairsum_f32p<recompute>",
-                     "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 "
-                                    f"flop x {sm_max:.0f} MHz (max SM clock of "
-                                    "MEASURED_PEAKS.json); 10 flop per pair-term"},
+        "roofline": _pairsum_roofline(
+            terms_per_launch / (avg_launch_ms * 1e-3), traffic,
+            algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (
+                wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
+            kernel="k_pairsum_f32p<table>" if info.storage == 1 else
+                   "k_pairsum_f32p<recompute>"),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "eps": info.eps, "max_sum_b2": info.max_sum_b2,
