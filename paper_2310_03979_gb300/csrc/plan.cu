@@ -220,10 +220,8 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
-  const size_t bar_words = kBarSlots0 + 8 * 1024;
-  SRM3_CUDA(cudaMalloc(&p->rec_bar, bar_words * sizeof(unsigned int)));
-  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, bar_words * sizeof(unsigned int), st));
-  p->rec_gen = 1;
+  SRM3_CUDA(cudaMalloc(&p->rec_bar, 32 * sizeof(unsigned int)));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, 32 * sizeof(unsigned int), st));
   int nsm = 0, dev = 0;
   SRM3_CUDA(cudaGetDevice(&dev));
   SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -251,6 +249,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   for (int m = 0; m < M; ++m) p->h_pinned[m] = x[m] * p->dkdw;
   SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, M * sizeof(double), cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaMemsetAsync(p->err, 0, (kPlanes + 1) * sizeof(int), st));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, sizeof(unsigned int), st));
   RecArgs A;
   A.nk = p->nk;
   A.nw = p->nw;
@@ -266,8 +265,6 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.scal = p->scal;
   A.err = p->err;
   A.bar = p->rec_bar;
-  A.gen_base = p->rec_gen;
-  p->rec_gen += (unsigned int)rec_barriers(A.nlev) + 1u;
   A.abort = p->err + kPlanes;
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));

@@ -10,7 +10,6 @@ namespace srm3 {
 
 constexpr int kRecThreads = 512;  // one CTA per SM
 constexpr int kRecBL = 16;        // levels per block of the blocked pass
-constexpr int kBarSlots0 = 32;    // first arrival slot of the grid barrier
 
 struct RecArgs {
   int nk, nw, nlev;
@@ -24,73 +23,37 @@ struct RecArgs {
   const void *G2;       // T[nk][nw]: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|]
   const double *scal;   // [M]: eps^2 dk dw per plane
   int *err;             // [M]: some S_p <= 0 on this plane
-  unsigned int *bar;    // [0] release generation, [kBarSlots0 + b] arrival of CTA b
-  unsigned int gen_base;  // generation of this launch's first barrier
+  unsigned int *bar;    // [0] grid barrier arrivals (zero at launch)
   int *abort;           // barrier wait timed out
 };
 
-// Number of grid barriers one pass uses.
-__host__ __device__ inline int rec_barriers(int nlev) {
-  int n = 1 + (nlev < kRecBL ? nlev : kRecBL);
-  for (int D = kRecBL; D < nlev; D += kRecBL) n += 1 + ((nlev - D) < kRecBL ? (nlev - D) : kRecBL);
-  return n;
-}
-
-// Grid-wide barrier for a cooperative launch (all CTAs resident), without
-// atomics: CTA b stores the barrier's generation number g in its own slot
-// bar[kBarSlots0 + b]; warp 0 of CTA 0 polls every slot until all show g,
-// then stores g into the release word bar[0], which the other CTAs poll.
-// Generations never repeat across launches (the host advances the base),
-// so a slot left over from an earlier pass cannot pass for an arrival.  The
-// fences on both sides order every CTA's writes before the barrier with
-// every read after it.  Waits are bounded: past ~2^22 polls a CTA raises
-// *abort and every CTA returns false from this or its next barrier.
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int g) {
+// Grid-wide barrier for a cooperative launch (all CTAs resident): one
+// arrival counter bar[0], zeroed on the stream before each launch.  Thread 0
+// of every CTA adds 1 after a fence and polls until the counter reaches
+// `target` (the barrier's number within the launch x gridDim.x); the fences
+// on both sides order every CTA's writes before the barrier with every read
+// after it.  Waits are bounded: past ~2^22 polls a CTA raises *abort and
+// every CTA returns false from this or its next barrier.
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int target) {
   __shared__ int s_ok;
-  const long long limit = 1ll << 22;
-  volatile unsigned int *vb = bar;
-  volatile int *vab = abort;
   __syncthreads();
   if (threadIdx.x == 0) {
+    const long long limit = 1ll << 22;
+    volatile unsigned int *cnt = bar;
+    volatile int *vab = abort;
     __threadfence();
-    vb[kBarSlots0 + blockIdx.x] = g;
-  }
-  if (blockIdx.x == 0) {
-    if (threadIdx.x < 32) {
-      // each round reads all of this lane's slots with independent loads
-      bool ok = true;
-      long long spins = 0;
-      for (;;) {
-        bool mine = true;
-        for (unsigned int i = threadIdx.x; i < gridDim.x; i += 32)
-          mine &= vb[kBarSlots0 + i] == g;
-        if (__all_sync(0xffffffffu, mine)) break;
-        if (*vab || ++spins > limit) {
-          ok = false;
-          break;
-        }
-      }
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (threadIdx.x == 0) atomicExch(abort, 1);
-      } else if (threadIdx.x == 0) {
-        __threadfence();
-        vb[0] = g;
-      }
-    }
-  } else if (threadIdx.x == 0) {
+    atomicAdd(bar, 1u);
+    bool ok = true;
     long long spins = 0;
-    while (vb[0] != g) {
-      if (*vab) break;
-      if (++spins > limit) {
-        atomicExch(abort, 1);
+    while (*cnt < target) {
+      if ((++spins & 63) == 0 && (*vab || spins > limit)) {
+        ok = false;
         break;
       }
-      __nanosleep(20);
     }
-  }
-  if (threadIdx.x == 0) {
+    if (!ok) atomicExch(abort, 1);
     __threadfence();
-    s_ok = *vab == 0;
+    s_ok = ok && *vab == 0;
   }
   __syncthreads();
   return s_ok != 0;
@@ -200,7 +163,12 @@ __device__ void point_direct(const RecArgs &A, int kk, int kw, int lane) {
 //   left:  j = (b, jw) is the higher element, jw = D - BL - b + u with
 //          2 (D - BL + u) > d.
 // Lanes take (row, u) slots, 16 u per row and two rows per warp step; the
-// canonical limits (centre row, i != 0, iw <= kw) mask the rest.
+// canonical limits (centre row, i != 0, iw <= kw) mask the rest.  The loads
+// of kBulkUnroll steps are issued before their products: a masked slot reads
+// point (0, 0) and adds g^2 = 0, which leaves each lane's running sum and its
+// order of additions exactly as if the slot were skipped.
+constexpr int kBulkUnroll = 4;
+
 template <typename T, int M>
 __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   const long long k = (long long)kk * A.nw + kw;
@@ -218,24 +186,42 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   T acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = (T)0;
-  for (int v = rs; v < nrows; v += 2) {
-    int a, iw, jw;
-    bool ok;
-    if (v < nR) {
-      a = aR0 + v;
-      iw = base - a + u;
-      jw = kw - iw;
-      ok = u >= uR0;
-    } else {
-      a = aL0 + (v - nR);
-      jw = base - (kk - a) + u;
-      iw = kw - jw;
-      ok = u >= uL0;
+  const int nw = A.nw;
+  const T *G2 = static_cast<const T *>(A.G2);
+  const T *q = static_cast<const T *>(A.q);
+  for (int v0 = rs; v0 < nrows; v0 += 2 * kBulkUnroll) {
+    T g2[kBulkUnroll], va[kBulkUnroll][M], vb[kBulkUnroll][M];
+#pragma unroll
+    for (int s = 0; s < kBulkUnroll; ++s) {
+      const int v = v0 + 2 * s;
+      int a, iw, jw;
+      bool ok;
+      if (v < nR) {
+        a = aR0 + v;
+        iw = base - a + u;
+        jw = kw - iw;
+        ok = u >= uR0;
+      } else {
+        a = aL0 + (v - nR);
+        jw = base - (kk - a) + u;
+        iw = kw - jw;
+        ok = u >= uL0;
+      }
+      const int b = kk - a;
+      const int lim = (a == b) ? kw / 2 : kw;
+      ok = ok && v < nrows && iw >= (a == 0 ? 1 : 0) && iw <= lim && jw >= 0;
+      const int dk = 2 * a - kk, dw = 2 * iw - kw;
+      const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+      const size_t qa = ok ? ((size_t)a * nw + iw) * M : 0;
+      const size_t qb = ok ? ((size_t)b * nw + jw) * M : 0;
+      g2[s] = ok ? G2[gi] : (T)0;
+      PlaneVec<T, M>::load(q + qa, va[s]);
+      PlaneVec<T, M>::load(q + qb, vb[s]);
     }
-    const int b = kk - a;
-    const int lim = (a == b) ? kw / 2 : kw;
-    ok = ok && iw >= (a == 0 ? 1 : 0) && iw <= lim && jw >= 0;
-    if (ok) add_pair<T, M>(A, kk, kw, a, iw, b, jw, acc);
+#pragma unroll
+    for (int s = 0; s < kBulkUnroll; ++s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
   }
   warp_sum<T, M>(acc);
   if (lane == 0) {
@@ -244,6 +230,8 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
     for (int m = 0; m < M; ++m) ac[k * M + m] += acc[m];
   }
 }
+
+constexpr int kFringeUnroll = 4;
 
 // Fringe of a point at level d in [D, D + BL): the pairs whose higher
 // element lies on a level in [D, d).  Their other element l has level
@@ -262,16 +250,36 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   T acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = (T)0;
-  for (int e = lane; e < nlow; e += 32) {
-    int l = 1, rem = e;
-    while (rem >= l + 1) {
-      rem -= l + 1;
-      ++l;
+  const int nw = A.nw;
+  const T *G2 = static_cast<const T *>(A.G2);
+  const T *q = static_cast<const T *>(A.q);
+  for (int e0 = lane; e0 < nlow; e0 += 32 * kFringeUnroll) {
+    T g2[kFringeUnroll], va[kFringeUnroll][M], vb[kFringeUnroll][M];
+#pragma unroll
+    for (int s = 0; s < kFringeUnroll; ++s) {
+      // e -> level l of the low point (levels 1..l hold l (l + 3) / 2
+      // points) and its place rem on that level
+      const int e = e0 + 32 * s;
+      int l = (int)ceilf((sqrtf(9.f + 8.f * (float)(e + 1)) - 3.f) * 0.5f);
+      l = max(l, 1);
+      while (l * (l + 3) / 2 <= e) ++l;
+      while (l > 1 && (l - 1) * (l + 2) / 2 > e) --l;
+      const int rem = e - (l - 1) * (l + 2) / 2;
+      const int lk = rem, lw = l - rem;
+      const int hk = kk - lk, hw = kw - lw;
+      const bool ok = e < nlow && hk >= 0 && hw >= 0;
+      const int dk = 2 * lk - kk, dw = 2 * lw - kw;
+      const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+      const size_t qa = ok ? ((size_t)lk * nw + lw) * M : 0;
+      const size_t qb = ok ? ((size_t)hk * nw + hw) * M : 0;
+      g2[s] = ok ? G2[gi] : (T)0;
+      PlaneVec<T, M>::load(q + qa, va[s]);
+      PlaneVec<T, M>::load(q + qb, vb[s]);
     }
-    const int lk = rem, lw = l - rem;
-    const int hk = kk - lk, hw = kw - lw;
-    if (hk < 0 || hw < 0) continue;
-    add_pair<T, M>(A, kk, kw, lk, lw, hk, hw, acc);
+#pragma unroll
+    for (int s = 0; s < kFringeUnroll; ++s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
   }
   warp_sum<T, M>(acc);
   if (lane == 0) {
@@ -300,21 +308,24 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
 template <typename T, int M>
 __global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
   const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // consecutive points (neighbours on a level, of similar cost) go to
+  // different SMs
+  const int gw = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
   const int nwarps = gridDim.x * (blockDim.x >> 5);
-  unsigned int g = A.gen_base;
+  unsigned int g = 1;  // barriers passed, counting the next one
+  const unsigned int nb = gridDim.x;
   T *ac = static_cast<T *>(A.acc);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.nl * M;
        i += (long long)gridDim.x * blockDim.x)
     ac[i] = (T)0;
-  if (!grid_barrier(A.bar, A.abort, g++)) return;
+  if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   const int d0 = min(kRecBL, A.nlev);
   for (int d = 0; d < d0; ++d) {
     for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
       const int2 pt = A.pts[p];
       point_direct<T, M>(A, pt.x, pt.y, lane);
     }
-    if (!grid_barrier(A.bar, A.abort, g++)) return;
+    if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
   for (int D = kRecBL; D < A.nlev; D += kRecBL) {
     const int pe = A.pt_off[min(2 * D, A.nlev)];
@@ -322,14 +333,14 @@ __global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
       const int2 pt = A.pts[p];
       point_bulk<T, M>(A, pt.x, pt.y, D, lane);
     }
-    if (!grid_barrier(A.bar, A.abort, g++)) return;
+    if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     const int dend = min(D + kRecBL, A.nlev);
     for (int d = D; d < dend; ++d) {
       for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
         const int2 pt = A.pts[p];
         point_fringe<T, M>(A, pt.x, pt.y, D, lane);
       }
-      if (!grid_barrier(A.bar, A.abort, g++)) return;
+      if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
   }
 }

@@ -127,7 +127,6 @@ struct srm3_plan {
   int *rec_lev_off = nullptr;        // first item of each level
   unsigned int *rec_bar = nullptr;   // grid barrier state
   int maxpts = 0, rec_grid64 = 0, rec_grid32 = 0;
-  unsigned int rec_gen = 1;          // next barrier generation
   double *h_pinned = nullptr;  // pinned host scalars
   int *h_err = nullptr;        // pinned host error words
 };
