@@ -559,6 +559,9 @@ def main():
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "stages_ms_last_step": {"plan_total": info.plan_ms, "recursion": t_last.recursion_ms,
                                 "recursion_passes": t_last.recursion_passes,
+                                "recursion_fp32_ms": t_last.recursion_fp32_ms,
+                                "recursion_fp32_passes": t_last.recursion_passes_fp32,
+                                "recursion_fp64_ms": t_last.recursion_fp64_ms,
                                 "table": t_last.table_ms, "phases": t_last.phases_ms,
                                 "pairsum": t_last.pairsum_ms,
                                 "transform": t_last.transform_ms},

@@ -220,8 +220,9 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
-  SRM3_CUDA(cudaMalloc(&p->rec_bar, 32 * sizeof(unsigned int)));
-  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, 32 * sizeof(unsigned int), st));
+  p->rec_bar_words = 2 + (nk + nw) / kRecBL + 1;  // barrier counter + a ticket per bulk phase
+  SRM3_CUDA(cudaMalloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int)));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
   int nsm = 0, dev = 0;
   SRM3_CUDA(cudaGetDevice(&dev));
   SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -249,7 +250,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   for (int m = 0; m < M; ++m) p->h_pinned[m] = x[m] * p->dkdw;
   SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, M * sizeof(double), cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaMemsetAsync(p->err, 0, (kPlanes + 1) * sizeof(int), st));
-  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, sizeof(unsigned int), st));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
   RecArgs A;
   A.nk = p->nk;
   A.nw = p->nw;
@@ -801,7 +802,7 @@ void free_plan(srm3_plan *p) {
                  p->tw,     p->tile_order, p->tile_off, p->W,       p->y,      p->y0,
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
-                 p->rec_partial, p->rec_ticket, p->super_order, p->rec_lev_off, p->rec_bar,
+                 p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar,
                  p->Ew2,    p->ps_err};
   for (void *d : dev)
     if (d) cudaFree(d);

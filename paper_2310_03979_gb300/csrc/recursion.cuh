@@ -23,7 +23,7 @@ struct RecArgs {
   const void *G2;       // T[nk][nw]: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|]
   const double *scal;   // [M]: eps^2 dk dw per plane
   int *err;             // [M]: some S_p <= 0 on this plane
-  unsigned int *bar;    // [0] grid barrier arrivals (zero at launch)
+  unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
   int *abort;           // barrier wait timed out
 };
 
@@ -245,6 +245,12 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
     point_zero<T, M>(A, k, lane);
     return;
   }
+  T bulk[M];  // the point's bulk sums, loaded ahead of the pair loads
+  if (lane == 0) {
+    const T *ac = static_cast<const T *>(A.acc);
+#pragma unroll
+    for (int m = 0; m < M; ++m) bulk[m] = ac[k * M + m];
+  }
   const int t = kk + kw - D;
   const int nlow = t * (t + 3) / 2;
   T acc[M];
@@ -283,9 +289,8 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   }
   warp_sum<T, M>(acc);
   if (lane == 0) {
-    const T *ac = static_cast<const T *>(A.acc);
 #pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] += ac[k * M + m];
+    for (int m = 0; m < M; ++m) acc[m] += bulk[m];
     finalize<T, M>(A, k, acc);
   }
 }
@@ -306,7 +311,7 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
 // result does not depend on scheduling.  T = double, M = 1 is the exact
 // pass; T = float, M = 8 evaluates eight eps values at once to locate eps.
 template <typename T, int M>
-__global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
+__global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
   const int lane = threadIdx.x & 31;
   // consecutive points (neighbours on a level, of similar cost) go to
   // different SMs
@@ -327,11 +332,20 @@ __global__ void __launch_bounds__(kRecThreads) k_rec_pass(RecArgs A) {
     }
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
-  for (int D = kRecBL; D < A.nlev; D += kRecBL) {
-    const int pe = A.pt_off[min(2 * D, A.nlev)];
-    for (int p = A.pt_off[D] + gw; p < pe; p += nwarps) {
-      const int2 pt = A.pts[p];
+  for (int D = kRecBL, ph = 1; D < A.nlev; D += kRecBL, ++ph) {
+    // bulk: warps take points in turn from the phase's ticket counter
+    // (the next ticket is drawn while the current point is summed)
+    const int pb = A.pt_off[D], pe = A.pt_off[min(2 * D, A.nlev)];
+    unsigned int *tk = A.bar + ph;
+    int t = 0;
+    if (lane == 0) t = (int)atomicAdd(tk, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    while (pb + t < pe) {
+      int tn = 0;
+      if (lane == 0) tn = (int)atomicAdd(tk, 1u);
+      const int2 pt = A.pts[pb + t];
       point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+      t = __shfl_sync(0xffffffffu, tn, 0);
     }
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     const int dend = min(D + kRecBL, A.nlev);

@@ -75,7 +75,6 @@ struct srm3_plan {
   float *G2_32 = nullptr; // the same in FP32 (search passes)
   int2 *rec_items = nullptr;         // (kk, row chunk) work items of all levels
   double *rec_partial = nullptr;     // per-level chunk sums [point slot][chunk]
-  unsigned int *rec_ticket = nullptr;  // per-level arrival tickets [point slot]
   int maxch = 0;
 
   // per-precision sampling tables (float or double by precision)
@@ -125,7 +124,8 @@ struct srm3_plan {
   // recursion graph (one pass = every anti-diagonal level + reductions)
   // persistent recursion pass
   int *rec_lev_off = nullptr;        // first item of each level
-  unsigned int *rec_bar = nullptr;   // grid barrier state
+  unsigned int *rec_bar = nullptr;   // grid barrier counter and bulk-phase tickets
+  int rec_bar_words = 0;
   int maxpts = 0, rec_grid64 = 0, rec_grid32 = 0;
   double *h_pinned = nullptr;  // pinned host scalars
   int *h_err = nullptr;        // pinned host error words
