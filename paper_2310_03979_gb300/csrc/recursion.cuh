@@ -245,10 +245,10 @@ constexpr int kFringeUnroll = 4;
 template <typename T, int M>
 __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) {
   const long long k = (long long)kk * A.nw + kw;
-  if (!(A.S[k] > 0.0)) {
-    point_zero<T, M>(A, k, lane);
-    return;
-  }
+  // S_k is read beside the pair loads rather than ahead of them: a point
+  // with S_k = 0 sums its (finite) terms like any other and is zeroed at
+  // the end, which keeps one memory round trip off the level's critical path
+  const double Sk = A.S[k];
   T bulk[M];  // the point's bulk sums, loaded ahead of the pair loads
   if (lane == 0) {
     const T *ac = static_cast<const T *>(A.acc);
@@ -292,6 +292,10 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
       for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
   }
   warp_sum<T, M>(acc);
+  if (!(Sk > 0.0)) {
+    point_zero<T, M>(A, k, lane);
+    return;
+  }
   if (lane == 0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) acc[m] += bulk[m];
