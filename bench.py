@@ -49,7 +49,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
     ap.add_argument("--config", default="bridge",
-                    choices=["bridge", "large", "tiny", "prof128", "uneven", "serve"],
+                    choices=["bridge", "bridge_rc", "large", "tiny", "prof128", "uneven",
+                             "serve"],
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")

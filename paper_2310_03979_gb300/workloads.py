@@ -83,7 +83,15 @@ LARGE = Workload("large_512x1024_recompute_fp32", 512, 1024, 0.25, 4 * math.pi,
 PROF128 = Workload("table_128x256_fp32", 128, 256, 0.25, 4 * math.pi, 40.0, 20.0, 256, 512,
                    tuple(range(1, 65)), precision="fp32", storage="table")
 
-CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "large": LARGE, "prof128": PROF128}
+# The bridge-span wave with W recomputed from its envelope factors instead of
+# stored: the same lattice, samples and seeds, the storage the autotuner picks
+# for this shape.
+BRIDGE_RC = Workload("bridge_256x512_recompute_fp32", 256, 512, 0.25, 4 * math.pi, 40.0,
+                     20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
+                     storage="recompute")
+
+CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "bridge_rc": BRIDGE_RC, "large": LARGE,
+           "prof128": PROF128}
 
 
 def uneven_batch(n_spectra: int = 200, seed: int = 4):

@@ -69,10 +69,14 @@ def test_plan_tables_and_eps(oracle_lib, precision):
     assert np.all(q >= 1.0) and info.min_pure_ratio > 0
 
 
-def test_recursion_at_fixed_eps(oracle_lib):
+@pytest.mark.parametrize("nk,nw", [(40, 33), (96, 64), (130, 20), (12, 200)])
+def test_recursion_at_fixed_eps(oracle_lib, nk, nw):
     """Same eps on both sides: the anti-diagonal recursion equals the
-    lexicographic one to FP64 rounding."""
-    wl = W.small_case(nk=40, nw=33)
+    lexicographic one to FP64 rounding.  The shapes take the pass through
+    several bulk phases and fringe blocks, points with more than 32 row
+    pairs (96 x 64, 130 x 20) and rows far longer than the lattice is tall."""
+    pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
+    wl = W.small_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw))
     op = oracle_plan(wl)
     with srm3.Plan.create(wl, eps=op.eps, precision="fp64") as p:
         _, q, sb2 = p.tables()
