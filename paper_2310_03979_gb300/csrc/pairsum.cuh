@@ -227,14 +227,22 @@ struct PsDesc {  // aligned as CUtensorMap
   const float *const *pk_of;
   const float *const *ck_of;
   int nk, nw, SS, SSpad, rowstride, ntw, ew_off, table, G;
+  // half = 1: at most 32 sheet-samples (16 lanes) with W recomputed; the two
+  // half-warps then take two row pairs of a work item (a = 2i and 2i + 1),
+  // reading 256-byte rows through a tensor map with 64-float boxes
+  int half;
   float cb, sb;          // cos / sin of the biphase
 };
 
 // Work unit {plan, kk, kws0, grp}: the 32-wide super-tile of row kk starting
 // at kws0, for sample group grp of plan `plan`.
-__device__ __forceinline__ int ps_nitems(int kk, int kws0) {
+// Row-pair steps of a unit: kk/2 + 1 row pairs, two per step in half mode.
+__host__ __device__ __forceinline__ int ps_rowsteps(int kk, int half) {
+  return half ? (kk / 2 + 2) / 2 : kk / 2 + 1;
+}
+__host__ __device__ __forceinline__ int ps_nitems(int kk, int kws0, int half) {
   using namespace packed;
-  return (kk / 2 + 1) * ((kws0 + SW + CH - 1) / CH);
+  return ps_rowsteps(kk, half) * ((kws0 + SW + CH - 1) / CH);
 }
 // The k-th unit of CTA c out of C (snake order over the cost-sorted units).
 __device__ __forceinline__ int ps_unit_id(int k, int c, int C) {
@@ -250,7 +258,8 @@ __device__ __forceinline__ int4 ps_get_unit(int u, const PsDesc &d0,
 }
 
 // One staged chunk for one compute warp: all register blocks of the chunk.
-template <bool TABLE>
+// RS: float4 per staged row (32, or 16 in half mode).
+template <bool TABLE, int RS>
 __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
                                          const float4 *__restrict__ pb,
                                          const float2 *__restrict__ pw,
@@ -266,12 +275,12 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
     if (i0 + blk * U > kw0 + R - 1) break;
     ulonglong2 A[U];
 #pragma unroll
-    for (int uu = 0; uu < U; ++uu) A[uu] = lds_pair(pa + (blk * U + uu) * LANES);
+    for (int uu = 0; uu < U; ++uu) A[uu] = lds_pair(pa + (blk * U + uu) * RS);
     const int m0 = U * (NB - 1 - blk);
 #pragma unroll
     for (int v = (blk == 0 ? 0 : NV - U); v < NV; ++v) {
       const int vv = blk == 0 ? v : v - (NV - U);  // rows not loaded yet
-      Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * LANES);
+      Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * RS);
     }
     const ulonglong2 *B = Bc + m0;
     if (TABLE) {
@@ -317,7 +326,10 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
 
 // The FP32 pair sum over one plan (d0, with descs = units = NULL) or any
 // number of plans (descs[p] describes plan p, units[0..nunits) the work units
-// sorted by decreasing cost).
+// sorted by decreasing cost).  MIXED = false compiles the full-group path
+// alone (every descriptor has half = 0); MIXED = true also takes half-mode
+// descriptors.
+template <bool MIXED>
 __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
     const __grid_constant__ PsDesc d0, const PsDesc *__restrict__ descs,
     const int4 *__restrict__ units, int nunits, int *__restrict__ err) {
@@ -368,7 +380,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
     auto w_next = [&]() {
       if (++wc == (wun.z + SW + CH - 1) / CH) {
         wc = 0;
-        if (++wa > wun.y / 2) {
+        if (++wa >= ps_rowsteps(wun.y, MIXED ? (descs ? descs[wun.x] : d0).half : 0)) {
           wa = 0;
           wu = ps_unit_id(++wk, blockIdx.x, gridDim.x);
           if (wu < nunits) wun = ps_get_unit(wu, d0, units);
@@ -384,7 +396,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const int4 un = ps_get_unit(u, d0, units);
       const PsDesc &d = descs ? descs[un.x] : d0;
       const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
-      const int nitems = ps_nitems(kk, kws0), tab = d.table, rs = d.rowstride;
+      const int half = MIXED ? d.half : 0;
+      const int nitems = ps_nitems(kk, kws0, half), tab = d.table, rs = d.rowstride;
       const unsigned tx = YROWS * ROW_BYTES + (tab ? 0 : EWIN * (unsigned)sizeof(float2));
       const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
@@ -394,16 +407,23 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
           ok = false;
           break;
         }
-        const int i0 = c * CH, b = kk - a;
+        const int i0 = c * CH;
         if (lane == 0) {
-          float4 *dst = sy + stage * STAGE_Y;
           mbar_expect_tx(&full[stage], tx);
-          tma_load_2d(dst, &d.ymap, x, a * rs + kPad + i0, &full[stage]);
-          const int jrow = b * rs + kPad + kws0 - i0 - CH + 1;
+          // one row pair (full rows), or two in half mode (half rows each; a
+          // second row pair past the centre repeats the first and is
+          // weighted 0 by the compute warps)
+          for (int h = 0; h <= half; ++h) {
+            const int ah = half ? min(2 * a + h, kk / 2) : a, bh = kk - ah;
+            const int rw = half ? LANES / 2 : LANES;  // float4 per staged row
+            float4 *dst = sy + stage * STAGE_Y + h * YROWS * (LANES / 2);
+            tma_load_2d(dst, &d.ymap, x, ah * rs + kPad + i0, &full[stage]);
+            const int jrow = bh * rs + kPad + kws0 - i0 - CH + 1;
 #pragma unroll
-          for (int j = 0; j < YB_BOXES; ++j)
-            tma_load_2d(dst + (CH + BOX_ROWS * j) * LANES, &d.ymap, x, jrow + BOX_ROWS * j,
-                        &full[stage]);
+            for (int j = 0; j < YB_BOXES; ++j)
+              tma_load_2d(dst + (CH + BOX_ROWS * j) * rw, &d.ymap, x, jrow + BOX_ROWS * j,
+                          &full[stage]);
+          }
           if (!tab)
             bulk_g2s(sw + stage * STAGE_W, d.Ew2 + d.ew_off + 2 * i0 - kws0 - (SW - 1),
                      EWIN * sizeof(float2), &full[stage]);
@@ -447,7 +467,10 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
     const PsDesc &d = descs ? descs[un.x] : d0;
     const int kk = un.y, kws0 = un.z, grp = un.w, nw = d.nw, tab = d.table;
     const int kw0 = kws0 + R * warp, nch = (kws0 + SW + CH - 1) / CH;
-    const int nitems = ps_nitems(kk, kws0);
+    const int half = MIXED ? d.half : 0;
+    const int nitems = ps_nitems(kk, kws0, half);
+    const int hl = half ? lane >> 4 : 0;        // which row pair of a step this lane takes
+    const int ln = half ? lane & 15 : lane;     // the lane's sample pair within the group
     const size_t SP = (size_t)d.SSpad / 2;  // float4 per lattice entry
     const bool tile_ok = kw0 < nw;
     const int my_L = ((kw0 + R + kTileU - 1) / kTileU) * kTileU;
@@ -463,29 +486,43 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       if (!mbar_wait(&full[stage], (q >> 1) & 1, abort, err)) return;
       const int i0 = c * CH;
       if (tile_ok) {
-        const float4 *pa = sy + stage * STAGE_Y + lane;
-        const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
         const float2 *pw = sw + stage * STAGE_W + warp * R * CH;
         const float2 *pe = sw + stage * STAGE_W + 24 - 8 * warp;
-        if (tab)
-          ps_chunk<true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
-        else
-          ps_chunk<false>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+        if (half) {
+          const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;
+          const float4 *pb = pa + (CH + R * warp + CH - U) * (LANES / 2);
+          ps_chunk<false, LANES / 2>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+        } else {
+          const float4 *pa = sy + stage * STAGE_Y + lane;
+          const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
+          if (tab)
+            ps_chunk<true, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+          else
+            ps_chunk<false, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+        }
       }
       mbar_arrive(&empty[stage]);
       if (tile_ok && c == nch - 1) {  // row pair complete: centre-row halving and merge
-        const int b = kk - a;
-        const float rowfac = tab ? 1.0f : d.Ek[kk - 2 * a];
+        // Half mode: lanes 16-31 hand the odd row pair's terms to lanes 0-15,
+        // which merge both row pairs in order -- the same sums, in the same
+        // order, as the full mode, so a sample's result does not depend on
+        // how many samples share its launch.
+        const int ah = half ? 2 * a + hl : a;  // this lane's row pair
+        const bool live = ah <= kk / 2;
+        const int b = kk - (live ? ah : a);
+        const float rowfac = tab ? 1.0f : (live ? d.Ek[kk - 2 * ah] : 0.0f);
+        const bool odd_live = half && 2 * a + 1 <= kk / 2;
+        const float rowfac_odd = odd_live ? d.Ek[kk - 2 * (2 * a + 1)] : 0.0f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const float2 xp = f2_split(Txp[r]), xm = f2_split(Txm[r]), yy = f2_split(Ty[r]);
           float v[4] = {xp.x - xm.x, xp.y - xm.y, yy.x, yy.y};
-          if (a == b) {
+          if (live && ah == b) {
             const int kw = kw0 + r;
             if ((kw & 1) == 0 && kw < nw) {
-              const float4 h = d.y[((size_t)a * d.rowstride + kPad + (kw >> 1)) * SP +
-                                   (size_t)grp * LANES + lane];
-              const float w0 = tab ? d.W[my_base + ((long long)a * R + r) * my_L + (kw >> 1)]
+              const float4 h = d.y[((size_t)ah * d.rowstride + kPad + (kw >> 1)) * SP +
+                                   (size_t)grp * LANES + ln];
+              const float w0 = tab ? d.W[my_base + ((long long)ah * R + r) * my_L + (kw >> 1)]
                                    : d.Ew2[d.ew_off].x;
               v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
               v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
@@ -496,13 +533,28 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
               for (int j = 0; j < 4; ++j) v[j] *= 0.5f;
             }
           }
+          float vo[4];  // the odd row pair (half mode, lanes 0-15)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {  // Kahan: s += rowfac v with compensation
-            float &s_ = kacc[(4 * r + j) * NCT], &cp = kcmp[(4 * r + j) * NCT];
-            const float s0 = s_, yv = fmaf(rowfac, v[j], -cp);
-            const float tt = s0 + yv;
-            cp = (tt - s0) - yv;
-            s_ = tt;
+          for (int j = 0; j < 4; ++j) vo[j] = half ? __shfl_down_sync(0xffffffffu, v[j], 16) : 0.f;
+          if (hl == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {  // Kahan: s += rowfac v with compensation
+              float &s_ = kacc[(4 * r + j) * NCT], &cp = kcmp[(4 * r + j) * NCT];
+              const float s0 = s_, yv = fmaf(rowfac, v[j], -cp);
+              const float tt = s0 + yv;
+              cp = (tt - s0) - yv;
+              s_ = tt;
+            }
+            if (odd_live) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float &s_ = kacc[(4 * r + j) * NCT], &cp = kcmp[(4 * r + j) * NCT];
+                const float s0 = s_, yv = fmaf(rowfac_odd, vo[j], -cp);
+                const float tt = s0 + yv;
+                cp = (tt - s0) - yv;
+                s_ = tt;
+              }
+            }
           }
           Txp[r] = Txm[r] = Ty[r] = 0ull;
         }
@@ -513,7 +565,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       }
     }
     if (!tile_ok) continue;
-    const int ss0 = grp * 2 * LANES + 2 * lane;
+    if (hl) continue;  // half mode: the sums are held by lanes 0-15
+    const int ss0 = grp * 2 * LANES + 2 * ln;
     if (ss0 >= d.SS) continue;  // padding lanes
     const float *Pk = d.pk_of ? d.pk_of[ss0 >> 1] : d.Pk;
     const float *ck = d.ck_of ? d.ck_of[ss0 >> 1] : d.ck;
@@ -523,7 +576,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       if (kw >= nw) break;
       const int kidx = kk * nw + kw;
       const float4 yk4 =
-          d.y[((size_t)kk * d.rowstride + kPad + kw) * SP + (size_t)grp * LANES + lane];
+          d.y[((size_t)kk * d.rowstride + kPad + kw) * SP + (size_t)grp * LANES + ln];
       const float cf = tab ? 1.0f : ck[kidx];
       const float P = Pk[kidx];
 #pragma unroll

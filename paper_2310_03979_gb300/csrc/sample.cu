@@ -209,18 +209,23 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
   }
   const int sp = sspad_for(n);
   std::memset(static_cast<void *>(d), 0, sizeof(*d));
+  const bool table = p->storage == SRM3_STORAGE_TABLE;
+  // at most 32 sheet-samples with W recomputed: half-group mode (two row
+  // pairs per work item, one on each half-warp)
+  const bool half = !table && 2 * n <= packed::LANES;
   // 2-D tensor map over y: rows of sp / 2 float4 (the sample pairs of one
-  // lattice entry), boxes of one 64-sample group (512 bytes) x 16 rows
+  // lattice entry), boxes of one 64-sample group (512 bytes), or of its first
+  // 32 sheet-samples (256 bytes) in half mode, x 16 rows
   const cuuint64_t dims[2] = {(cuuint64_t)sp * 2, (cuuint64_t)p->nk * p->rowstride};
   const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
+  const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * (half ? 2 : 4),
+                             (cuuint32_t)packed::BOX_ROWS};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(&d->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, y, dims, strides,
                             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS)
     return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-  const bool table = p->storage == SRM3_STORAGE_TABLE;
   d->y = (const float4 *)y;
   d->y0 = (const float2 *)y0;
   d->Ek = (const float *)p->Ek;
@@ -240,6 +245,7 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
   d->ew_off = p->ew_off;
   d->table = table ? 1 : 0;
   d->G = sp / (2 * packed::LANES);
+  d->half = half ? 1 : 0;
   d->cb = (float)std::cos(p->beta);
   d->sb = (float)std::sin(p->beta);
   return SRM3_OK;
@@ -249,24 +255,31 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
 // batch descs/units; the grid is the resident CTA count (persistent kernel).
 // nunits == 0 only prepares (attributes, resident CTA count).
 int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
-                       const int4 *units, int nunits, int max_ctas) {
+                       const int4 *units, int nunits, int max_ctas, bool mixed) {
   const size_t smem = pairsum_f32p_smem();
-  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32p, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32p, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 100));
-  if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel
-    int nsm = 0, per_sm = 0;
+  const void *kf[2] = {(const void *)k_pairsum_f32p<false>, (const void *)k_pairsum_f32p<true>};
+  for (const void *f : kf) {
+    SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  }
+  if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel (both forms)
+    int nsm = 0, per_sm = 1 << 30;
     SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairsum_f32p, packed::NT,
-                                                            smem));
+    for (const void *f : kf) {
+      int n = 0;
+      SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, packed::NT, smem));
+      per_sm = std::min(per_sm, n);
+    }
     if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
     p->ps_ctas = nsm * per_sm;
   }
   int grid = std::min(nunits, p->ps_ctas);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (grid == 0) return SRM3_OK;
-  k_pairsum_f32p<<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
+  if (mixed)
+    k_pairsum_f32p<true><<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
+  else
+    k_pairsum_f32p<false><<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -294,7 +307,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
     PsDesc d;
     int rc = fill_pairsum_desc(p, n, C_out, &d);
     if (rc) return rc;
-    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0);
+    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0, d.half != 0);
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
@@ -455,6 +468,7 @@ struct srm3_batch {
   srm3::PsDesc *ddesc = nullptr;  // per group and per FP32 table plan
   int4 *dunits = nullptr;         // work units of all of them, by decreasing cost
   int nunits = 0;
+  bool mixed = false;             // some descriptor takes the half-group mode
   srm3_plan *lead = nullptr;      // first FP32 plan: CTA count and error word of the launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -492,7 +506,7 @@ static int batch_launch(srm3_batch *b) {
     const unsigned evf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, evf));
     if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits,
-                                 b->max_ctas)))
+                                 b->max_ctas, b->mixed)))
       return rc;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
@@ -668,11 +682,14 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
     int r = fill_pairsum_desc(plan, n, plan->C, &d);
     if (r) return r;
     const int nunits = plan->nsuper * d.G;
-    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0))) return r;
+    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0, d.half != 0)))
+      return r;
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       SRM3_CUDA(cudaEventRecord(ev[0], plan->stream));
-      if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0))) return r;
+      if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0,
+                                  d.half != 0)))
+        return r;
       SRM3_CUDA(cudaEventRecord(ev[1], plan->stream));
       SRM3_CUDA(cudaEventSynchronize(ev[1]));
       float t = 0.f;
@@ -741,11 +758,10 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
   }
   std::vector<PsDesc> descs;
   std::vector<std::pair<long long, int4>> units;
-  auto add_units = [&](srm3_plan *p, int j, int G) {
+  auto add_units = [&](srm3_plan *p, int j, const PsDesc &d) {
     for (const int2 &t : p->super_host) {
-      const long long cost =
-          (long long)(t.x / 2 + 1) * ((t.y + packed::SW + packed::CH - 1) / packed::CH);
-      for (int g = 0; g < G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
+      const long long cost = ps_nitems(t.x, t.y, d.half);
+      for (int g = 0; g < d.G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
     }
   };
   auto same_shape = [](const srm3_plan *a, const srm3_plan *c) {
@@ -815,8 +831,9 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     d.pk_of = g.pk_of;
     d.ck_of = g.ck_of;
     const int j = (int)descs.size();
+    b->mixed = b->mixed || d.half != 0;
     descs.push_back(d);
-    add_units(p, j, d.G);
+    add_units(p, j, d);
   }
   for (int i = 0; i < m; ++i) {  // FP32 plans with a stored W table, on their workspace
     srm3_plan *p = b->plans[i];
@@ -824,8 +841,9 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     PsDesc d;
     if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
     const int j = (int)descs.size();
+    b->mixed = b->mixed || d.half != 0;
     descs.push_back(d);
-    add_units(p, j, d.G);
+    add_units(p, j, d);
   }
   std::stable_sort(units.begin(), units.end(),
                    [](const std::pair<long long, int4> &x, const std::pair<long long, int4> &y) {
@@ -849,7 +867,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     // kernel attributes and resident CTA count, set before any capture
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
-    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0)))
+    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0, b->mixed)))
       return bail(rc);
   }
   e = cudaMallocAsync(&b->dseeds, sizeof(uint64_t) * b->total, b->stream);
