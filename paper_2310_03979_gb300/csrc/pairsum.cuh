@@ -88,6 +88,13 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
 // chunk ahead, through registers); otherwise the chunk's 64-entry window
 // of the duplicated omega envelope Ew2 is bulk-copied, w = Ew[2 iw - kw],
 // with the kappa factor Ek[kk - 2a] applied per row pair and c_k at the end.
+// Half-group mode (at most 32 sheet-samples, W recomputed): the lanes of a
+// group would be half empty, so each half-warp takes one of two row pairs
+// (a = 2i, 2i + 1) of a work item, on 256-byte rows staged by eight tile
+// loads; at the end of the pair the upper half passes its terms to the lower
+// half, which merges the two row pairs in order -- the same sums in the same
+// order as the full form, so a sample's result does not depend on how many
+// samples share its launch.
 // The compute warps release a stage through a second mbarrier.  Every wait
 // is bounded: past kWaitCycles the waiter raises the CTA's abort flag and
 // the error word, all warps leave their loops, and the producer first waits
