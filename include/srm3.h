@@ -66,18 +66,31 @@ typedef struct srm3_spectrum {
 } srm3_spectrum;
 
 /* Bispectrum |B(i,j)| = eps g(i,j) sqrt(S(i) S(j) S(i+j)) with constant
- * biphase beta, g(i,j) = exp(-1/2 ((ik-jk)/(sigma_g n_kappa))^2)
- *                      * exp(-1/2 ((iw-jw)/(sigma_g n_omega))^2). */
-enum srm3_bispectrum_kind { SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0 };
+ * biphase beta (Sec. 4, the bicoherence form of Eq. pure), and either
+ *   GAUSS_ENVELOPE: g(i,j) = exp(-1/2 ((ik-jk)/(sigma_g n_kappa))^2)
+ *                          * exp(-1/2 ((iw-jw)/(sigma_g n_omega))^2), or
+ *   SEPARABLE:      g(i,j) = e(i) e(j) e(i+j), e from env_table.
+ * A separable g turns the pair sum of every lattice point into a
+ * self-convolution: plans with it sample through a zero-padded 2-D FFT
+ * instead of the O(N^2) pair sum (Sec. 4.3 FFT form; any storage setting is
+ * ignored). */
+enum srm3_bispectrum_kind {
+    SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0,
+    SRM3_BISPECTRUM_SEPARABLE = 1
+};
 
 typedef struct srm3_bispectrum {
-    int32_t kind;
+    int32_t kind;             /* enum srm3_bispectrum_kind */
     int32_t reserved;
     double target_max_sum_b2; /* in (0,1): eps found so that max_k sum b_p^2
                                  equals it to 1e-13; 0: use eps as given */
     double eps;               /* used when target_max_sum_b2 == 0; >= 0 */
-    double sigma_g;           /* > 0 */
+    double sigma_g;           /* GAUSS_ENVELOPE: > 0; ignored otherwise */
     double beta;              /* biphase, radians */
+    const double *env_table;  /* SEPARABLE: host, n_kappa*n_omega doubles
+                                 e[kk*n_omega + kw], finite and >= 0; read
+                                 during srm3_plan_create only (the caller
+                                 keeps ownership); ignored otherwise */
 } srm3_bispectrum;
 
 enum srm3_precision {

@@ -65,6 +65,18 @@ __global__ void k_env_sq(int n, double sigma_n, double *out, float *out32) {
 }
 
 // g^2 over (|ik - jk|, |iw - jw|) as one table, FP64 and FP32.
+// Separable envelope: e^2 and e in FP32 per lattice point, and g^2 tables of
+// ones (the envelope factors are carried by h = e^2 q and e_k^2).
+__global__ void k_sep_tables(int nl, const double *__restrict__ e, double *e2, float *e32,
+                             double *G2, float *G2_32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nl) return;
+  e2[i] = e[i] * e[i];
+  e32[i] = (float)e[i];
+  G2[i] = 1.0;
+  G2_32[i] = 1.0f;
+}
+
 __global__ void k_g2(int nk, int nw, const double *__restrict__ EkSq,
                      const double *__restrict__ EwSq, double *G2, float *G2_32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,7 +271,11 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.pts = p->rec_items;
   A.pt_off = p->rec_lev_off;
   A.S = p->S;
-  A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (void *)p->qm : (void *)p->qm3);
+  if (p->sep && fp64 && M != 1)
+    return fail(SRM3_ERR_NOT_SUPPORTED, "separable envelope: one-plane FP64 passes only");
+  A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (p->sep ? (void *)p->qh : (void *)p->qm) : (void *)p->qm3);
+  A.e2 = p->sep ? p->env_e2 : nullptr;
+  A.qout = (p->sep && fp64) ? p->qm : nullptr;
   A.acc = p->rec_partial;
   A.sb2 = p->sb2;
   A.G2 = fp64 ? (const void *)p->G2 : (const void *)p->G2_32;
@@ -375,20 +391,31 @@ static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, in
 // FP64 bracket continues.  The tables left in the plan are those of the
 // final FP64 pass.
 static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
-  {
+  double Lmax = 0.0;
+  if (p->sep) {
+    // separable envelope: the slope at q = 1 from one FP32 pass at a
+    // vanishing x (every q rounds to 1), L = sum_b2 / x
+    const double xt = 1e-20;
+    double xs0[kPlanes];
+    PassResult r0[kPlanes];
+    for (int m = 0; m < kPlanes; ++m) xs0[m] = xt;
+    int rc0 = run_pass_multi(p, st, xs0, kPlanes, false, r0);
+    if (rc0) return rc0;
+    Lmax = r0[0].max_sb2 / xt;
+  } else {
     const int nblk = cdiv(p->nw, kLinOut);
     const size_t smem = (size_t)3 * p->nw * sizeof(float);
     SRM3_CUDA(cudaFuncSetAttribute(k_rec_linear, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
     k_rec_linear<<<p->nk * nblk, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32, p->EwSq32,
                                                        p->sb2, p->dkdw);
+    SRM3_CUDA(cudaGetLastError());
+    k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
+    SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double),
+                              cudaMemcpyDeviceToHost, st));
+    SRM3_CUDA(cudaStreamSynchronize(st));
+    Lmax = p->h_pinned[9];
   }
-  SRM3_CUDA(cudaGetLastError());
-  k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double), cudaMemcpyDeviceToHost,
-                            st));
-  SRM3_CUDA(cudaStreamSynchronize(st));
-  const double Lmax = p->h_pinned[9];
   if (!(Lmax > 0.0))
     return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
 
@@ -680,7 +707,21 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   k_env_sq<<<cdiv(nw, 256), 256, 0, st>>>(nw, p->sigma_g * nw, p->EwSq, p->EwSq32);
   SRM3_CUDA(cudaMalloc(&p->G2, nl * sizeof(double)));
   SRM3_CUDA(cudaMalloc(&p->G2_32, nl * sizeof(float)));
-  k_g2<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->EkSq, p->EwSq, p->G2, p->G2_32);
+  if (p->sep) {
+    // separable envelope: the pair factor e_i^2 e_j^2 rides on h = e^2 q and
+    // e_k^2 is applied when q_k is formed, so the g^2 table is all ones
+    SRM3_CUDA(cudaMalloc(&p->env_e, nl * sizeof(double)));
+    SRM3_CUDA(cudaMalloc(&p->env_e2, nl * sizeof(double)));
+    SRM3_CUDA(cudaMalloc(&p->env_e32, nl * sizeof(float)));
+    SRM3_CUDA(cudaMalloc(&p->qh, nl * sizeof(double)));
+    SRM3_CUDA(cudaMemsetAsync(p->qh, 0, nl * sizeof(double), st));
+    SRM3_CUDA(cudaMemcpyAsync(p->env_e, bs->env_table, nl * sizeof(double),
+                              cudaMemcpyHostToDevice, st));
+    k_sep_tables<<<cdiv(nl, 256), 256, 0, st>>>((int)nl, p->env_e, p->env_e2, p->env_e32,
+                                                p->G2, p->G2_32);
+  } else {
+    k_g2<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->EkSq, p->EwSq, p->G2, p->G2_32);
+  }
   SRM3_CUDA(cudaGetLastError());
 
   // a2: recursion, one graph node per anti-diagonal level
@@ -717,8 +758,9 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   rc = prepare_sampling_tables(p, st);
   if (rc) return rc;
 
-  // tiles, storage choice and the W table
-  if (p->precision == SRM3_FP32) {
+  // tiles, storage choice and the W table (the O(N^2) FP32 pair sum only;
+  // separable envelopes sample through the FFT self-convolution)
+  if (p->precision == SRM3_FP32 && !p->sep) {
     long long entries = 0;
     bool maybe_table = p->storage != SRM3_STORAGE_RECOMPUTE;
     rc = build_tiles(p, st, maybe_table, &entries);
@@ -758,6 +800,15 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
   p->ew_len = p->ew_off + nw + 128;
   p->nfft = std::max(p->nx, p->nt);
+  if (p->sep) {  // zero-padded self-convolution grid
+    p->log2cNk = 1;
+    while ((1 << p->log2cNk) < 2 * nk - 1) ++p->log2cNk;
+    p->log2cNw = 1;
+    while ((1 << p->log2cNw) < 2 * nw - 1) ++p->log2cNw;
+    p->cNk = 1 << p->log2cNk;
+    p->cNw = 1 << p->log2cNw;
+    p->log2ntwc = std::max(p->log2cNk, p->log2cNw);
+  }
   p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
   SRM3_CUDA(cudaMalloc(&p->sqq, nl * es));
   SRM3_CUDA(cudaMalloc(&p->Pk, nl * es));
@@ -777,6 +828,11 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
     k_dup2<<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, (const float *)p->Ews, p->Ew2);
     k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, (float2 *)p->tw);
+    if (p->sep) {
+      SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2)));
+      k_twiddles<float2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
+                                                                        (float2 *)p->tw_conv);
+    }
   } else {
     k_sampling_tables<double><<<cdiv(nl, 256), 256, 0, st>>>(
         (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (double *)p->sqq, (double *)p->Pk,
@@ -785,6 +841,11 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_env<double><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off,
                                                        p->sigma_g * nw, (double *)p->Ews);
     k_twiddles<double2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, (double2 *)p->tw);
+    if (p->sep) {
+      SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2)));
+      k_twiddles<double2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
+                                                                         (double2 *)p->tw_conv);
+    }
   }
   SRM3_CUDA(cudaGetLastError());
   SRM3_CUDA(cudaStreamSynchronize(st));
@@ -803,7 +864,8 @@ void free_plan(srm3_plan *p) {
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar,
-                 p->Ew2,    p->ps_err};
+                 p->Ew2,    p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
+                 p->tw_conv, p->Zc};
   for (void *d : dev)
     if (d) cudaFree(d);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
@@ -851,9 +913,16 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   } else {
     return fail(SRM3_ERR_INVALID_ARG, "unknown spectrum kind");
   }
-  if (bispectrum->kind != SRM3_BISPECTRUM_GAUSS_ENVELOPE)
+  if (bispectrum->kind == SRM3_BISPECTRUM_GAUSS_ENVELOPE) {
+    if (!(bispectrum->sigma_g > 0.0)) return fail(SRM3_ERR_INVALID_ARG, "sigma_g must be > 0");
+  } else if (bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE) {
+    if (!bispectrum->env_table) return fail(SRM3_ERR_INVALID_ARG, "env_table is NULL");
+    for (size_t i = 0; i < (size_t)g.n_kappa * g.n_omega; ++i)
+      if (!(bispectrum->env_table[i] >= 0.0) || !std::isfinite(bispectrum->env_table[i]))
+        return fail(SRM3_ERR_INVALID_ARG, "env_table must be finite and >= 0");
+  } else {
     return fail(SRM3_ERR_INVALID_ARG, "unknown bispectrum kind");
-  if (!(bispectrum->sigma_g > 0.0)) return fail(SRM3_ERR_INVALID_ARG, "sigma_g must be > 0");
+  }
   const double tgt = bispectrum->target_max_sum_b2;
   if (!(tgt >= 0.0 && tgt < 1.0)) return fail(SRM3_ERR_INVALID_ARG, "target must be in [0, 1)");
   if (tgt == 0.0 && !(bispectrum->eps >= 0.0))
@@ -875,7 +944,8 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->precision = g.precision;
   p->storage = g.storage;
   p->stream = (cudaStream_t)g.stream;
-  p->sigma_g = bispectrum->sigma_g;
+  p->sep = bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE;
+  p->sigma_g = p->sep ? 0.25 : bispectrum->sigma_g;
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
   cudaGetDevice(&p->device);

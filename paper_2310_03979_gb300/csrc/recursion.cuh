@@ -22,6 +22,11 @@ struct RecArgs {
   double *sb2;          // [M][nl]
   const void *G2;       // T[nk][nw]: g^2 = EkSq[|ik-jk|] EwSq[|iw-jw|]
   const double *scal;   // [M]: eps^2 dk dw per plane
+  // separable envelope (else NULL): e^2 per point.  The pair sums then run
+  // over h = e^2 q (stored in q, G2 all ones), sum_b2(k) takes the factor
+  // e_k^2, and the FP64 pass writes q itself to qout
+  const double *e2;
+  double *qout;
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
   int *abort;           // barrier wait timed out
@@ -114,14 +119,18 @@ __device__ __forceinline__ void warp_sum(T (&v)[M]) {
 template <typename T, int M>
 __device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
   T *q = static_cast<T *>(A.q);
+  const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const T s2 = (T)A.scal[m] * t[m];
+    const T s2 = (T)A.scal[m] * ek2 * t[m];
     A.sb2[m * A.nl + k] = (double)s2;
     if (s2 < (T)1) {
-      q[k * M + m] = (T)1 / ((T)1 - s2);
+      const T qk = (T)1 / ((T)1 - s2);
+      q[k * M + m] = A.e2 ? ek2 * qk : qk;
+      if (A.qout) A.qout[k] = (double)qk;
     } else {
       q[k * M + m] = (T)0;
+      if (A.qout) A.qout[k] = 0.0;
       atomicOr(A.err + m, 1);
     }
   }
@@ -133,6 +142,7 @@ __device__ __forceinline__ void point_zero(const RecArgs &A, long long k, int la
     A.sb2[lane * A.nl + k] = 0.0;
     static_cast<T *>(A.q)[k * M + lane] = (T)0;
   }
+  if (lane == 0 && A.qout) A.qout[k] = 0.0;
 }
 
 // Levels below kRecBL: the whole canonical pair sum of the point (one warp),

@@ -6,9 +6,11 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
+#include "conv.cuh"
 #include "fft.cuh"
 #include "pairsum.cuh"
 #include "srm3_internal.cuh"
@@ -34,16 +36,6 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
-template <typename T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-  using type = float2;
-};
-template <>
-struct Vec2<double> {
-  using type = double2;
-};
 
 // Unit phasor e^{i 2 pi (w + 1/2) 2^-32}.
 __device__ __forceinline__ float2 phasor(uint32_t w, float) {
@@ -143,6 +135,12 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   SRM3_CUDA(cudaMalloc(&p->y0, (size_t)sp * e2));
   SRM3_CUDA(cudaMalloc(&p->C, (size_t)2 * cap * p->nk * p->nw * e2));
   SRM3_CUDA(cudaMalloc(&p->H, (size_t)cap * p->nk * p->nt * e2));
+  if (p->sep) {  // the self-convolution grid of every sheet-sample of a chunk
+    if (p->Zc) cudaFree(p->Zc);
+    p->Zc = nullptr;
+    SRM3_CUDA(cudaMalloc(&p->Zc, (size_t)2 * cap * p->cNk * p->cNw * e2));
+    p->zc_ss = 2LL * cap;
+  }
   p->ws_chunk = cap;
   return SRM3_OK;
 }
@@ -295,8 +293,52 @@ static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
   return SRM3_OK;
 }
 
+// The separable pair sum of n samples (y / y0 laid out for sspad_for(n)) by
+// FFT self-convolution on stream st (conv.cuh), into C_out.
+template <typename T>
+static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y, const void *y0,
+                             void *C_out) {
+  using T2 = typename Vec2<T>::type;
+  const int SS = 2 * n, sp = sspad_for(n);
+  if (SS > p->zc_ss) return fail(SRM3_ERR_INVALID_ARG, "separable pair sum: workspace too small");
+  const T *e = std::is_same<T, float>::value ? (const T *)p->env_e32 : (const T *)p->env_e;
+  const T2 *tw = (const T2 *)p->tw_conv;
+  T2 *Z = (T2 *)p->Zc;
+  const size_t srow = (size_t)p->cNw * sizeof(T2);
+  int TC = 16;
+  while (TC > 1 && (size_t)TC * p->cNk * sizeof(T2) > 96 * 1024) TC >>= 1;
+  TC = std::min(TC, p->cNw);
+  const size_t scol = (size_t)TC * p->cNk * sizeof(T2);
+  if (srow > 200 * 1024 || scol > 200 * 1024)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "separable pair sum: a padded row or column does not fit in shared memory");
+  SRM3_CUDA(cudaFuncSetAttribute(k_conv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)srow));
+  SRM3_CUDA(cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)scol));
+  SRM3_CUDA(cudaFuncSetAttribute(k_conv_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)srow));
+  k_conv_rows<T><<<dim3(p->nk, SS), 256, srow, st>>>(p->nk, p->nw, p->log2cNw, p->cNk, sp,
+                                                      p->rowstride, y, e, tw, p->log2ntwc, Z);
+  k_conv_cols<T><<<dim3(p->cNw / TC, SS), 256, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
+                                                            p->log2ntwc, Z);
+  k_conv_out<T><<<dim3(p->nk, SS), 256, srow, st>>>(
+      p->nk, p->nw, p->log2cNw, p->cNk, sp, p->rowstride, y, (const T2 *)y0, e,
+      (const T *)p->Pk, (const T *)p->ck, (T)std::cos(p->beta), (T)std::sin(p->beta), tw,
+      p->log2ntwc, Z, (T2 *)C_out);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
+int conv_pairsum_on(srm3_plan *p, cudaStream_t st, int n, const void *y, const void *y0,
+                    void *C_out) {
+  return p->precision == SRM3_FP32 ? conv_pairsum_impl<float>(p, st, n, y, y0, C_out)
+                                   : conv_pairsum_impl<double>(p, st, n, y, y0, C_out);
+}
+
 int run_pairsum(srm3_plan *p, int n, void *C_out) {
   const int SS = 2 * n, sp = sspad_for(n);
+  if (p->sep) return conv_pairsum_on(p, p->stream, n, p->y, p->y0, C_out);
   if (p->precision == SRM3_FP64) {
     const long long threads = (long long)p->nk * p->nw * sp;
     k_pairsum_f64<<<cdiv(threads, 256), 256, 0, p->stream>>>(
@@ -510,10 +552,15 @@ static int batch_launch(srm3_batch *b) {
       return rc;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
-  for (size_t i = 0; i < b->plans.size(); ++i)
-    if (b->plans[i]->precision == SRM3_FP64 &&
-        (rc = pairsum_f64_on(b->plans[i], b->stream, b->counts[i], b->plans[i]->C)))
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    srm3_plan *p = b->plans[i];
+    if (p->sep) {
+      if ((rc = conv_pairsum_on(p, b->stream, b->counts[i], p->y, p->y0, p->C))) return rc;
+    } else if (p->precision == SRM3_FP64 &&
+               (rc = pairsum_f64_on(p, b->stream, b->counts[i], p->C))) {
       return rc;
+    }
+  }
   for (auto &g : b->groups)
     for (size_t m = 0; m < g.members.size(); ++m) {
       const int i = g.members[m];
@@ -662,8 +709,9 @@ SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
 SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   if (!plan || !res) return fail(SRM3_ERR_INVALID_ARG, "plan and result must be non-NULL");
   if (n < 1 || n > kMaxChunk) return fail(SRM3_ERR_INVALID_ARG, "n must be in 1..128");
-  if (plan->precision != SRM3_FP32)
-    return fail(SRM3_ERR_NOT_SUPPORTED, "autotuning applies to FP32 plans only");
+  if (plan->precision != SRM3_FP32 || plan->sep)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "autotuning applies to FP32 plans of the O(N^2) pair sum only");
   int rc = ensure_workspace(plan, n);
   if (rc) return rc;
   std::vector<uint64_t> seeds(n);
@@ -777,7 +825,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     b->total += counts[i];
     b->pair_terms += 2LL * p->pairs * counts[i];
     int gi = -1;
-    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE) {
+    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE && !p->sep) {
       for (size_t g = 0; g < b->groups.size() && gi < 0; ++g)
         if (same_shape(b->plans[b->groups[g].members[0]], p)) gi = (int)g;
       if (gi < 0) {
@@ -793,7 +841,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
       return bail(rc);
     }
     b->group_of.push_back(gi);
-    if (p->precision == SRM3_FP32 && !b->lead) b->lead = p;
+    if (p->precision == SRM3_FP32 && !p->sep && !b->lead) b->lead = p;
   }
   cudaError_t e;
   for (auto &g : b->groups) {  // batch-owned buffers of each shape group
@@ -837,7 +885,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
   }
   for (int i = 0; i < m; ++i) {  // FP32 plans with a stored W table, on their workspace
     srm3_plan *p = b->plans[i];
-    if (b->group_of[i] >= 0 || p->precision != SRM3_FP32) continue;
+    if (b->group_of[i] >= 0 || p->precision != SRM3_FP32 || p->sep) continue;
     PsDesc d;
     if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
     const int j = (int)descs.size();

@@ -14,6 +14,18 @@
 
 namespace srm3 {
 
+// The complex pair type of a precision.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
 // Tile shape of the FP32 pair sum: R outputs along omega per thread; the W
 // table rows of a tile are padded to a multiple of kTileU.  The y rows carry
 // kPad zero entries on both sides: every row the FP32 pair sum stages lies
@@ -53,6 +65,19 @@ struct srm3_plan {
 
   // model
   double sigma_g = 0.25, beta = 0.0;
+  // separable envelope g(i,j) = e(i) e(j) e(i+j): the recursion keeps
+  // h = e^2 q for its pair sums (G2 = 1) and sampling is an FFT convolution
+  bool sep = false;
+  double *env_e = nullptr, *env_e2 = nullptr;  // e and e^2 per lattice point
+  float *env_e32 = nullptr;                     // e in FP32
+  double *qh = nullptr;                         // h = e^2 q of the FP64 passes
+  // FFT self-convolution grid of the separable pair sum (powers of two,
+  // cNk >= 2 nk - 1, cNw >= 2 nw - 1), its twiddles e^{+2 pi i j / ntwc},
+  // and the workspace of zc_ss sheet-samples (complex, plan precision)
+  int cNk = 0, cNw = 0, log2cNk = 0, log2cNw = 0, log2ntwc = 0;
+  void *tw_conv = nullptr;
+  void *Zc = nullptr;
+  long long zc_ss = 0;
   double eps = 0.0, max_sb2 = 0.0, min_pure = 1.0, variance = 0.0;
   double plan_ms = 0.0, table_bytes = 0.0, table_budget = 0.0;
   int root_passes = 0;    // FP64 recursion passes

@@ -26,6 +26,7 @@ SRM3_ERR = {
 SRM3_SPECTRUM_KAIMAL_LORENTZIAN = 0
 SRM3_SPECTRUM_TABLE = 1
 SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0
+SRM3_BISPECTRUM_SEPARABLE = 1
 SRM3_FP32, SRM3_FP64 = 0, 1
 SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE, SRM3_STORAGE_TUNED = 0, 1, 2, 3
 EXPORTED = [
@@ -55,7 +56,8 @@ class srm3_spectrum(ctypes.Structure):
 class srm3_bispectrum(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("target_max_sum_b2", ctypes.c_double), ("eps", ctypes.c_double),
-                ("sigma_g", ctypes.c_double), ("beta", ctypes.c_double)]
+                ("sigma_g", ctypes.c_double), ("beta", ctypes.c_double),
+                ("env_table", ctypes.POINTER(ctypes.c_double))]
 
 
 class srm3_grid(ctypes.Structure):
@@ -329,6 +331,11 @@ class Plan:
             sp.table = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         bs = srm3_bispectrum()
         bs.kind = SRM3_BISPECTRUM_GAUSS_ENVELOPE
+        env = None
+        if wl.envelope == "separable":
+            env = np.ascontiguousarray(wl.envelope_table(), dtype=np.float64)
+            bs.kind = SRM3_BISPECTRUM_SEPARABLE
+            bs.env_table = env.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         tgt = wl.target if target is None else target
         if eps is not None:
             bs.target_max_sum_b2, bs.eps = 0.0, float(eps)
@@ -344,7 +351,7 @@ class Plan:
         g.stream = stream
         g.table_budget_bytes = float(budget_bytes)
         h = plan_create(sp, bs, g)
-        del keep
+        del keep, env
         return cls(h, wl.n_kappa, wl.n_omega, wl.n_x, wl.n_t, prec)
 
     def info(self) -> srm3_info:

@@ -41,6 +41,15 @@ class Workload:
     z0: float = 0.03
     k_vk: float = 0.4
     lam: float = 7.0
+    envelope: str = "gauss"          # "gauss" (sigma_g) or "separable" (sigma_e)
+    sigma_e: float = 0.5
+
+    def envelope_table(self) -> np.ndarray:
+        """Separable envelope e(kk, kw) = exp(-1/2 ((kk/(sigma_e Nk))^2 +
+        (kw/(sigma_e Nw))^2)), so that g(i, j) = e(i) e(j) e(i+j)."""
+        kk = np.arange(self.n_kappa, dtype=np.float64)[:, None] / (self.sigma_e * self.n_kappa)
+        kw = np.arange(self.n_omega, dtype=np.float64)[None, :] / (self.sigma_e * self.n_omega)
+        return np.exp(-0.5 * (kk * kk + kw * kw))
 
     @property
     def n_samples(self) -> int:

@@ -1,0 +1,125 @@
+"""Separable envelope g(i, j) = e(i) e(j) e(i+j): the recursion with the
+envelope factors carried on h = e^2 q, and the pair sum as a zero-padded FFT
+self-convolution, against the FP64 oracle's O(N^2) sums for the same
+envelope (the oracle's separable form is pinned to a numpy FFT convolution in
+test_oracle_pins.py).
+
+Tolerances as in test_gpu_parity.py: FP64 fields 1e-10 sigma_u, FP32 fields
+1e-4 sigma_u; coefficients 1e-11 (FP64) and 2e-6 (FP32) of max|C|; plan
+tables 1e-11 (FP64 plans) and 2e-8 (FP32 plans, eps to 1e-9 of the target).
+"""
+import dataclasses
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_03979_gb300 import srm3
+from paper_2310_03979_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def sep_case(nk=24, nw=37, nx=64, nt=128, seeds=(1, 2, 3), precision="fp64", sigma_e=0.5):
+    wl = W.small_case(nk=nk, nw=nw, nx=nx, nt=nt, seeds=seeds, precision=precision)
+    return dataclasses.replace(wl, envelope="separable", sigma_e=sigma_e,
+                               name=f"sep_{nk}x{nw}")
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_plan(wl, eps=None):
+    S = oracle.kaimal_lorentzian(wl.n_kappa, wl.n_omega, wl.kappa_u, wl.omega_u, wl.U, wl.z,
+                                 wl.z0, wl.k_vk, wl.lam)
+    env = oracle.Envelope("separable", table=wl.envelope_table())
+    if eps is None:
+        return oracle.make_plan(S, wl.kappa_u, wl.omega_u, target=wl.target, env=env,
+                                beta=wl.beta)
+    return oracle.make_plan(S, wl.kappa_u, wl.omega_u, eps=eps, env=env, beta=wl.beta)
+
+
+def _cplx(C):
+    C = C.cpu().numpy()
+    return C[..., 0] + 1j * C[..., 1]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_separable_plan_tables_and_eps(oracle_lib, precision):
+    wl = sep_case(precision=precision)
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl) as p:
+        S, q, sb2 = p.tables()
+        info = p.info()
+    tol, rel = (1e-13, 1e-11) if precision == "fp64" else (1e-9, 2e-8)
+    np.testing.assert_allclose(S, op.S, rtol=1e-13, atol=0)
+    assert info.eps == pytest.approx(op.eps, rel=rel)
+    assert abs(info.max_sum_b2 - wl.target) <= tol
+    np.testing.assert_allclose(q, op.q, rtol=rel)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=rel, atol=1e-15)
+
+
+@pytest.mark.parametrize("nk,nw", [(24, 37), (40, 70), (1, 9), (9, 1)])
+def test_separable_recursion_at_fixed_eps(oracle_lib, nk, nw):
+    pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
+    wl = sep_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw))
+    eps = 0.2 if nk > 1 and nw > 1 else 0.5
+    op = oracle_plan(wl, eps=eps)
+    with srm3.Plan.create(wl, eps=eps) as p:
+        _, q, sb2 = p.tables()
+    np.testing.assert_allclose(q, op.q, rtol=2e-14)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
+
+
+@pytest.mark.parametrize("precision,nk,nw,beta", [("fp64", 24, 37, 0.0), ("fp32", 24, 37, 0.0),
+                                                  ("fp64", 40, 70, 0.6), ("fp32", 33, 20, 0.6)])
+def test_separable_coefficients(oracle_lib, precision, nk, nw, beta):
+    pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
+    wl = dataclasses.replace(sep_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw),
+                                      precision=precision), beta=beta)
+    op = oracle_plan(wl)
+    seeds = [3, 11, 2 ** 40 + 1]
+    with srm3.Plan.create(wl, eps=op.eps) as p:
+        C = _cplx(p.coeffs(seeds))
+    tol = 1e-11 if precision == "fp64" else 2e-6
+    for i, s in enumerate(seeds):
+        ref = op.coeffs(s)
+        scale = np.abs(ref).max()
+        assert np.abs(C[i] - ref).max() <= tol * scale
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_separable_field_end_to_end(oracle_lib, precision):
+    wl = sep_case(precision=precision, seeds=(1, 7))
+    op = oracle_plan(wl)
+    sig = math.sqrt(op.moments()[0])
+    with srm3.Plan.create(wl) as p:
+        u = p.sample(list(wl.seeds)).cpu().numpy()
+    ref = np.stack([op.field(s, wl.n_x, wl.n_t) for s in wl.seeds])
+    tol = 1e-10 if precision == "fp64" else 1e-4
+    assert np.abs(u - ref).max() <= tol * sig
+
+
+def test_separable_in_a_batch_is_bit_identical_to_alone():
+    """A batch holding a separable plan next to Gaussian ones (one of them
+    with a stored W table) gives each plan the fields of srm3_sample."""
+    sep = sep_case(precision="fp32", seeds=(5, 6, 7))
+    g1 = W.small_case(nk=24, nw=37, precision="fp32", storage="recompute", seeds=(1, 2))
+    g2 = W.small_case(nk=16, nw=20, nx=32, nt=64, precision="fp32", storage="table",
+                      seeds=(9,))
+    wls = [sep, g1, g2]
+    plans = [srm3.Plan.create(w) for w in wls]
+    try:
+        alone = [p.sample(list(w.seeds)).clone() for p, w in zip(plans, wls)]
+        outs = [torch.empty_like(a) for a in alone]
+        seeds = [s for w in wls for s in w.seeds]
+        with srm3.Batch(plans, [w.n_samples for w in wls], outs) as b:
+            b.run(seeds)
+            b.sync()
+        torch.cuda.synchronize()
+        for a, o in zip(alone, outs):
+            assert torch.equal(a, o)
+    finally:
+        for p in plans:
+            p.destroy()
