@@ -49,8 +49,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
     ap.add_argument("--config", default="bridge",
-                    choices=["bridge", "bridge_rc", "large", "tiny", "prof128", "uneven",
-                             "serve"],
+                    choices=["bridge", "bridge_rc", "bridge_sep", "large", "tiny", "prof128",
+                             "uneven", "serve"],
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -68,6 +68,25 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def _conv_roofline(wl, n, es, launch_ms):
+    """Roofline of the separable pair sum (three FFT self-convolution passes
+    over a zero-padded Nk x Nw grid per sheet-sample), bound by HBM: per
+    sheet-sample y read twice and C written once (n_kappa n_omega complex
+    each), and n_kappa padded rows of Nw complex written, read, written and
+    read once more between the passes."""
+    nk, nw = wl.n_kappa, wl.n_omega
+    Nw = 1 << max(1, (2 * nw - 2).bit_length())
+    per_ss = 2 * es * (3 * nk * nw + 4 * nk * Nw)
+    nbytes = 2 * n * per_ss
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    gbs = nbytes / (launch_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "traffic": None, "algorithmic_bytes_per_launch": nbytes,
+            "per_unit": f"{per_ss} B per sheet-sample (y twice, C once, padded rows 4x)",
+            "kernel": "k_conv_rows + k_conv_cols + k_conv_out (one sampling chunk)",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
 
 
 def _pairsum_roofline(terms_per_s, traffic=None, **extra):
@@ -152,13 +171,18 @@ def oracle_baseline(wl, rows=48, seed=1, passes=None):
     Recursion and coefficient time scale with the pair count, the DFT with
     the row count; the step is (eps-search passes) recursions plus
     n_samples coefficient sets and DFTs."""
+    import numpy as np
     import oracle
     oracle.build()
     dk = wl.kappa_u / wl.n_kappa
     sub = rows
     S = oracle.kaimal_lorentzian(sub, wl.n_omega, sub * dk, wl.omega_u, wl.U, wl.z, wl.z0,
                                  wl.k_vk, wl.lam)
-    env = oracle.Envelope("gauss", wl.sigma_g * wl.n_kappa / sub)  # same width per index
+    if wl.envelope == "separable":  # the workload's e on the sampled rows
+        env = oracle.Envelope("separable", table=np.ascontiguousarray(
+            wl.envelope_table()[:sub], dtype=np.float64))
+    else:
+        env = oracle.Envelope("gauss", wl.sigma_g * wl.n_kappa / sub)  # same width per index
     eps = 1e-3
     t0 = time.perf_counter()
     Sp, _ = oracle.recursion(S, sub * dk, wl.omega_u, eps, env)
@@ -536,6 +560,12 @@ def main():
     launches_per_step = (1 + 3 + 2 + 2 * (info.root_passes + info.root_passes_fp32)
                          + (5 if es == 4 else 4) + (1 if info.storage == 1 else 0)
                          + 4 * chunks)
+    if wl.envelope == "separable":
+        # the bracketing pass is an FP32 pass (counted above) instead of the
+        # linear pass; conv twiddles 1; per chunk phases, three FFT
+        # self-convolution passes, two output FFT stages
+        launches_per_step = (1 + 3 + 2 * (info.root_passes + info.root_passes_fp32)
+                             + (5 if es == 4 else 4) + 1 + 6 * chunks)
     traffic = None
     src = os.path.join(ROOT, "paper_2310_03979_gb300", "csrc", "pairsum.cuh")
     if wl.name.startswith("bridge") and info.storage == 1 and es == 4:
@@ -568,12 +598,13 @@ def main():
                                 "transform": t_last.transform_ms},
         "sampling_only_pair_terms_per_s": terms_per_step / (
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
-        "roofline": _pairsum_roofline(
+        "roofline": (_conv_roofline(wl, n, es, avg_launch_ms) if wl.envelope == "separable"
+                     else _pairsum_roofline(
             terms_per_launch / (avg_launch_ms * 1e-3), traffic,
             algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (
                 wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
             kernel="k_pairsum_f32p<table>" if info.storage == 1 else
-                   "k_pairsum_f32p<recompute>"),
+                   "k_pairsum_f32p<recompute>")),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "eps": info.eps, "max_sum_b2": info.max_sum_b2,

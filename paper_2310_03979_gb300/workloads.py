@@ -99,8 +99,15 @@ BRIDGE_RC = Workload("bridge_256x512_recompute_fp32", 256, 512, 0.25, 4 * math.p
                      20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
                      storage="recompute")
 
-CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "bridge_rc": BRIDGE_RC, "large": LARGE,
-           "prof128": PROF128}
+# The bridge-span lattice with a separable envelope g = e(i) e(j) e(i+j)
+# (e a Gaussian of width 0.5 of the lattice per axis): the pair sum becomes
+# an FFT self-convolution.
+BRIDGE_SEP = Workload("bridge_256x512_separable_fp32", 256, 512, 0.25, 4 * math.pi, 40.0,
+                      20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
+                      storage="recompute", envelope="separable", sigma_e=0.5)
+
+CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "bridge_rc": BRIDGE_RC, "bridge_sep": BRIDGE_SEP,
+           "large": LARGE, "prof128": PROF128}
 
 
 def uneven_batch(n_spectra: int = 200, seed: int = 4):
