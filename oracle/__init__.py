@@ -106,10 +106,13 @@ def _check(rc, what):
 class Envelope:
     """Bispectrum envelope g(i, j): ``kind='gauss'`` with width ``sigma_g``
     (fraction of the lattice extent per axis), or ``kind='separable'`` with
-    g = e(i) e(j) e(i+j) from ``table`` of shape (Nk, Nw)."""
+    g = e(i) e(j) e(i+j) from ``table`` of shape (Nk, Nw), or, when
+    ``table_b`` is given too, g = a(i) a(j) b(i+j) with a = ``table`` and
+    b = ``table_b``."""
     kind: str = "gauss"
     sigma_g: float = 0.25
     table: np.ndarray | None = None
+    table_b: np.ndarray | None = None
 
     def args(self, nk, nw):
         if self.kind == "gauss":
@@ -117,7 +120,11 @@ class Envelope:
         if self.kind == "separable":
             t = np.ascontiguousarray(self.table, dtype=np.float64)
             assert t.shape == (nk, nw)
-            return 1, 0.0, t
+            if self.table_b is None:
+                return 1, 0.0, t
+            b = np.ascontiguousarray(self.table_b, dtype=np.float64)
+            assert b.shape == (nk, nw)
+            return 2, 0.0, np.ascontiguousarray(np.concatenate([t.ravel(), b.ravel()]))
         raise ValueError(self.kind)
 
 

@@ -25,8 +25,9 @@
  *   bispec.   |B(i,j)| = eps * g(i,j) * sqrt(S(i) S(j) S(k)),  B real times
  *             exp(i*beta) with a constant biphase beta.
  *   envelope  kind 0: g = exp(-1/2 ((ik-jk)/(sg*Nk))^2) * exp(-1/2 ((iw-jw)/(sg*Nw))^2)
- *             kind 1: g = e(i) e(j) e(k) for a caller table e (test-only
- *             separable envelope)
+ *             kind 1: g = e(i) e(j) e(k) for a caller table e (separable)
+ *             kind 2: g = a(i) a(j) b(k) for caller tables a, b (separable;
+ *             a = 1 gives envelopes of k alone, as in Sec. 5)
  *
  * Field (Eq. quadrant_1d_wave; FFT form of Sec. 4.3):
  *   u(x,t) = sum_s sum_k Re[ C^s_k exp(i(kappa_k x + s omega_k t)) ],
@@ -88,9 +89,9 @@ int or_kaimal_lorentzian(int nk, int nw, double kappa_u, double omega_u,
 /* Bispectrum modulus |B(i,j)| for i + j = k (all three inside the lattice). */
 typedef struct {
     int nk, nw;
-    int env_kind;          /* 0 gaussian, 1 separable table */
+    int env_kind;          /* 0 gaussian, 1 separable table, 2 separable pair */
     double sigma_g;
-    const double *env_tab; /* kind 1: e[kk*nw + kw] */
+    const double *env_tab; /* kind 1: e[kk*nw + kw]; kind 2: a then b (2 nk nw) */
     double eps;
 } or_bispec;
 
@@ -101,9 +102,14 @@ static double or_envelope(const or_bispec *B, int ik, int iw, int jk, int jw)
         double aw = (double)(iw - jw) / (B->sigma_g * B->nw);
         return exp(-0.5 * ak * ak) * exp(-0.5 * aw * aw);
     }
+    /* kind 1: g = e(i) e(j) e(i+j); kind 2: g = a(i) a(j) b(i+j), which holds
+     * envelopes that depend on i + j alone (a = 1), as the bispectrum of the
+     * wind-field example of Sec. 5 does */
     int kk = ik + jk, kw = iw + jw;
-    return B->env_tab[(size_t)ik * B->nw + iw] * B->env_tab[(size_t)jk * B->nw + jw]
-         * B->env_tab[(size_t)kk * B->nw + kw];
+    const double *a = B->env_tab;
+    const double *b = B->env_kind == 2 ? B->env_tab + (size_t)B->nk * B->nw : B->env_tab;
+    return a[(size_t)ik * B->nw + iw] * a[(size_t)jk * B->nw + jw]
+         * b[(size_t)kk * B->nw + kw];
 }
 
 static double or_modB(const or_bispec *B, const double *S,

@@ -394,3 +394,32 @@ def test_pair_counts(oracle_lib):
     assert W.TINY.pairs() == 138496
     assert abs(W.BRIDGE.pairs() - 2.16e9) / 2.16e9 < 0.01
     assert abs(W.LARGE.pairs() - 3.45e10) / 3.45e10 < 0.01
+
+
+def test_two_table_separable_recursion_and_coeffs_fft(oracle_lib):
+    """g = a(i) a(j) b(i+j): sum_b2(k) = eps^2 dk dw b_k^2 [S_k > 0] sum_{Pi(k)}
+    v_i v_j with v = a^2 q [S > 0], and the pair part of C^s_k is
+    2 eps dk dw sqrt(S_k) b_k e^{i beta} sum_{Pi(k)} w_i w_j with
+    w = a sqrt(q) z [S > 0]; both pair sums by numpy FFT self-convolution.
+    b is not a multiple of a, so a swapped or dropped table fails."""
+    S, a = _sep_setup(nk=7, nw=9, seed=13)
+    nk, nw = S.shape
+    rng = np.random.default_rng(21)
+    b = 0.3 + rng.random((nk, nw))
+    ku, wu, eps, beta, seed = 0.5, 4 * math.pi, 0.07, -0.4, 5
+    env = oracle.Envelope("separable", table=a, table_b=b)
+    Sp, sb2 = oracle.recursion(S, ku, wu, eps, env)
+    pos = S > 0
+    q = np.where(pos, S / np.where(pos, Sp, 1.0), 1.0)
+    dkdw = (ku / nk) * (wu / nw)
+    v = np.where(pos, a * a * q, 0.0)
+    pred = eps ** 2 * dkdw * b ** 2 * _self_conv_half(v).real * pos
+    assert sb2.max() > 0.01
+    np.testing.assert_allclose(sb2, pred, rtol=1e-11, atol=1e-14 * sb2.max())
+    C = oracle.coeffs(S, Sp, ku, wu, eps, seed, env, beta)
+    z = _z(nk, nw, seed)
+    for s in range(2):
+        pure = 2 * np.sqrt(dkdw * np.maximum(Sp, 0)) * z[s]
+        w = np.where(pos, a * np.sqrt(q) * z[s], 0)
+        pair = 2 * eps * dkdw * np.sqrt(S) * b * np.exp(1j * beta) * _self_conv_half(w) * pos
+        np.testing.assert_allclose(C[s], pure + pair, rtol=0, atol=1e-12 * np.abs(C[s]).max())
