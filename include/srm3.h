@@ -69,7 +69,10 @@ typedef struct srm3_spectrum {
  * biphase beta (Sec. 4, the bicoherence form of Eq. pure), and either
  *   GAUSS_ENVELOPE: g(i,j) = exp(-1/2 ((ik-jk)/(sigma_g n_kappa))^2)
  *                          * exp(-1/2 ((iw-jw)/(sigma_g n_omega))^2), or
- *   SEPARABLE:      g(i,j) = e(i) e(j) e(i+j), e from env_table.
+ *   SEPARABLE:      g(i,j) = a(i) a(j) b(i+j), a from env_table and b from
+ *                   env_table_b (b = a when env_table_b is NULL); a = 1 gives
+ *                   envelopes of i + j alone, as in the wind-field example
+ *                   of Sec. 5.
  * A separable g turns the pair sum of every lattice point into a
  * self-convolution: plans with it sample through a zero-padded 2-D FFT
  * instead of the O(N^2) pair sum (Sec. 4.3 FFT form; any storage setting is
@@ -88,9 +91,11 @@ typedef struct srm3_bispectrum {
     double sigma_g;           /* GAUSS_ENVELOPE: > 0; ignored otherwise */
     double beta;              /* biphase, radians */
     const double *env_table;  /* SEPARABLE: host, n_kappa*n_omega doubles
-                                 e[kk*n_omega + kw], finite and >= 0; read
+                                 a[kk*n_omega + kw], finite and >= 0; read
                                  during srm3_plan_create only (the caller
                                  keeps ownership); ignored otherwise */
+    const double *env_table_b;/* SEPARABLE: b in the same layout and rules,
+                                 or NULL for b = a; ignored otherwise */
 } srm3_bispectrum;
 
 enum srm3_precision {

@@ -1,9 +1,9 @@
 // conv.cuh - the pair sum of a separable envelope as an FFT self-convolution
-// (a4 + a5 for g(i,j) = e(i) e(j) e(i+j)).  Included by sample.cu after
+// (a4 + a5 for g(i,j) = a(i) a(j) b(i+j)).  Included by sample.cu after
 // fft.cuh, whose radix-2 stages it reuses.
 //
-// With W_ij = c_k e_i e_j e_k the pair part of C_k is
-//   c_k e^{i beta} e_k sum_{Pi(k)} z_i z_j,   z = e y  (z_0 = 0),
+// With W_ij = c_k a_i a_j b_k the pair part of C_k is
+//   c_k e^{i beta} b_k sum_{Pi(k)} z_i z_j,   z = a y  (z_0 = 0),
 // and over unordered pairs {i, j}, i + j = k,
 //   sum_{Pi(k)} z_i z_j = ((z * z)_k + [k even] z_{k/2}^2) / 2,
 // with (z * z) the linear 2-D self-convolution on the quadrant lattice.  It
@@ -35,7 +35,7 @@ __device__ __forceinline__ typename Vec2<T>::type conv_y(const void *y, int SSpa
   }
 }
 
-// Pass 1: z = e y along each lattice row kk < n_kappa, zero-padded to Nw,
+// Pass 1: z = a y along each lattice row kk < n_kappa, zero-padded to Nw,
 // transformed; block (kk, ss).  Rows kk >= n_kappa of the grid are zero
 // and never stored.
 template <typename T>
@@ -111,11 +111,12 @@ __global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC, const typename V
 // Pass 3: row kk of the twice-transformed grid, transformed along omega; the
 // ordered self-convolution at (kk, kw) is its entry (Nw - kw) mod Nw over
 // Nk Nw.  Epilogue as in the O(N^2) pair sums:
-//   C_k = P_k y_k + c_k e^{i beta} e_k ((z * z)_k + [k even] z_{k/2}^2) / 2.
+//   C_k = P_k y_k + c_k e^{i beta} b_k ((z * z)_k + [k even] z_{k/2}^2) / 2.
 template <typename T>
 __global__ void k_conv_out(int nk, int nw, int log2Nw, int Nk, int SSpad, int rowstride,
                            const void *__restrict__ y, const typename Vec2<T>::type *__restrict__ y0,
-                           const T *__restrict__ e, const T *__restrict__ Pk,
+                           const T *__restrict__ e, const T *__restrict__ eb,
+                           const T *__restrict__ Pk,
                            const T *__restrict__ ck, T cb, T sb,
                            const typename Vec2<T>::type *__restrict__ tw, int log2ntw,
                            const typename Vec2<T>::type *__restrict__ Z,
@@ -144,7 +145,7 @@ __global__ void k_conv_out(int nk, int nw, int log2Nw, int Nk, int SSpad, int ro
     ai *= (T)0.5;
     const size_t k = (size_t)kk * nw + kw;
     const T2 yk = (k == 0) ? y0[ss] : conv_y<T>(y, SSpad, rowstride, kk, kw, ss);
-    const T f = ck[k] * e[k], P = Pk[k];
+    const T f = ck[k] * eb[k], P = Pk[k];
     T2 out;
     out.x = P * yk.x + f * (ar * cb - ai * sb);
     out.y = P * yk.y + f * (ar * sb + ai * cb);

@@ -275,6 +275,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
     return fail(SRM3_ERR_NOT_SUPPORTED, "separable envelope: one-plane FP64 passes only");
   A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (p->sep ? (void *)p->qh : (void *)p->qm) : (void *)p->qm3);
   A.e2 = p->sep ? p->env_e2 : nullptr;
+  A.e2k = p->sep ? p->env_b2 : nullptr;
   A.qout = (p->sep && fp64) ? p->qm : nullptr;
   A.acc = p->rec_partial;
   A.sb2 = p->sb2;
@@ -719,6 +720,20 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
                               cudaMemcpyHostToDevice, st));
     k_sep_tables<<<cdiv(nl, 256), 256, 0, st>>>((int)nl, p->env_e, p->env_e2, p->env_e32,
                                                 p->G2, p->G2_32);
+    p->sep_b = bs->env_table_b != nullptr;
+    if (p->sep_b) {
+      SRM3_CUDA(cudaMalloc(&p->env_b, nl * sizeof(double)));
+      SRM3_CUDA(cudaMalloc(&p->env_b2, nl * sizeof(double)));
+      SRM3_CUDA(cudaMalloc(&p->env_b32, nl * sizeof(float)));
+      SRM3_CUDA(cudaMemcpyAsync(p->env_b, bs->env_table_b, nl * sizeof(double),
+                                cudaMemcpyHostToDevice, st));
+      k_sep_tables<<<cdiv(nl, 256), 256, 0, st>>>((int)nl, p->env_b, p->env_b2, p->env_b32,
+                                                  p->G2, p->G2_32);
+    } else {
+      p->env_b = p->env_e;
+      p->env_b2 = p->env_e2;
+      p->env_b32 = p->env_e32;
+    }
   } else {
     k_g2<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->EkSq, p->EwSq, p->G2, p->G2_32);
   }
@@ -865,7 +880,9 @@ void free_plan(srm3_plan *p) {
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar,
                  p->Ew2,    p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
-                 p->tw_conv, p->Zc};
+                 p->tw_conv, p->Zc,
+                 p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
+                 p->sep_b ? (void *)p->env_b32 : nullptr};
   for (void *d : dev)
     if (d) cudaFree(d);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
@@ -917,9 +934,12 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
     if (!(bispectrum->sigma_g > 0.0)) return fail(SRM3_ERR_INVALID_ARG, "sigma_g must be > 0");
   } else if (bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE) {
     if (!bispectrum->env_table) return fail(SRM3_ERR_INVALID_ARG, "env_table is NULL");
-    for (size_t i = 0; i < (size_t)g.n_kappa * g.n_omega; ++i)
-      if (!(bispectrum->env_table[i] >= 0.0) || !std::isfinite(bispectrum->env_table[i]))
-        return fail(SRM3_ERR_INVALID_ARG, "env_table must be finite and >= 0");
+    for (const double *t : {bispectrum->env_table, bispectrum->env_table_b}) {
+      if (!t) continue;
+      for (size_t i = 0; i < (size_t)g.n_kappa * g.n_omega; ++i)
+        if (!(t[i] >= 0.0) || !std::isfinite(t[i]))
+          return fail(SRM3_ERR_INVALID_ARG, "env_table and env_table_b must be finite and >= 0");
+    }
   } else {
     return fail(SRM3_ERR_INVALID_ARG, "unknown bispectrum kind");
   }

@@ -25,7 +25,8 @@ struct RecArgs {
   // separable envelope (else NULL): e^2 per point.  The pair sums then run
   // over h = e^2 q (stored in q, G2 all ones), sum_b2(k) takes the factor
   // e_k^2, and the FP64 pass writes q itself to qout
-  const double *e2;
+  const double *e2;   // a^2: h = a^2 q
+  const double *e2k;  // b^2: the factor of sum_b2(k)
   double *qout;
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
@@ -119,10 +120,11 @@ __device__ __forceinline__ void warp_sum(T (&v)[M]) {
 template <typename T, int M>
 __device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
   T *q = static_cast<T *>(A.q);
-  const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;
+  const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;    // a_k^2
+  const T bk2 = A.e2k ? (T)A.e2k[k] : (T)1;  // b_k^2
 #pragma unroll
   for (int m = 0; m < M; ++m) {
-    const T s2 = (T)A.scal[m] * ek2 * t[m];
+    const T s2 = (T)A.scal[m] * bk2 * t[m];
     A.sb2[m * A.nl + k] = (double)s2;
     if (s2 < (T)1) {
       const T qk = (T)1 / ((T)1 - s2);

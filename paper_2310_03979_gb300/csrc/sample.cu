@@ -322,8 +322,9 @@ static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y
                                                       p->rowstride, y, e, tw, p->log2ntwc, Z);
   k_conv_cols<T><<<dim3(p->cNw / TC, SS), 256, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
                                                             p->log2ntwc, Z);
+  const T *eb = std::is_same<T, float>::value ? (const T *)p->env_b32 : (const T *)p->env_b;
   k_conv_out<T><<<dim3(p->nk, SS), 256, srow, st>>>(
-      p->nk, p->nw, p->log2cNw, p->cNk, sp, p->rowstride, y, (const T2 *)y0, e,
+      p->nk, p->nw, p->log2cNw, p->cNk, sp, p->rowstride, y, (const T2 *)y0, e, eb,
       (const T *)p->Pk, (const T *)p->ck, (T)std::cos(p->beta), (T)std::sin(p->beta), tw,
       p->log2ntwc, Z, (T2 *)C_out);
   SRM3_CUDA(cudaGetLastError());

@@ -68,8 +68,12 @@ struct srm3_plan {
   // separable envelope g(i,j) = e(i) e(j) e(i+j): the recursion keeps
   // h = e^2 q for its pair sums (G2 = 1) and sampling is an FFT convolution
   bool sep = false;
-  double *env_e = nullptr, *env_e2 = nullptr;  // e and e^2 per lattice point
-  float *env_e32 = nullptr;                     // e in FP32
+  double *env_e = nullptr, *env_e2 = nullptr;  // a and a^2 per lattice point
+  float *env_e32 = nullptr;                     // a in FP32
+  // b and b^2 (g = a(i) a(j) b(i+j)); the a tables when b = a
+  double *env_b = nullptr, *env_b2 = nullptr;
+  float *env_b32 = nullptr;
+  bool sep_b = false;                           // b has tables of its own
   double *qh = nullptr;                         // h = e^2 q of the FP64 passes
   // FFT self-convolution grid of the separable pair sum (powers of two,
   // cNk >= 2 nk - 1, cNw >= 2 nw - 1), its twiddles e^{+2 pi i j / ntwc},

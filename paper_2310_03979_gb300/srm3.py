@@ -57,7 +57,8 @@ class srm3_bispectrum(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("target_max_sum_b2", ctypes.c_double), ("eps", ctypes.c_double),
                 ("sigma_g", ctypes.c_double), ("beta", ctypes.c_double),
-                ("env_table", ctypes.POINTER(ctypes.c_double))]
+                ("env_table", ctypes.POINTER(ctypes.c_double)),
+                ("env_table_b", ctypes.POINTER(ctypes.c_double))]
 
 
 class srm3_grid(ctypes.Structure):
@@ -331,11 +332,15 @@ class Plan:
             sp.table = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         bs = srm3_bispectrum()
         bs.kind = SRM3_BISPECTRUM_GAUSS_ENVELOPE
-        env = None
-        if wl.envelope == "separable":
-            env = np.ascontiguousarray(wl.envelope_table(), dtype=np.float64)
+        env = env_b = None
+        if wl.envelope != "gauss":
+            ta, tb = wl.envelope_tables()
+            env = np.ascontiguousarray(ta, dtype=np.float64)
             bs.kind = SRM3_BISPECTRUM_SEPARABLE
             bs.env_table = env.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            if tb is not None:
+                env_b = np.ascontiguousarray(tb, dtype=np.float64)
+                bs.env_table_b = env_b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         tgt = wl.target if target is None else target
         if eps is not None:
             bs.target_max_sum_b2, bs.eps = 0.0, float(eps)
@@ -351,7 +356,7 @@ class Plan:
         g.stream = stream
         g.table_budget_bytes = float(budget_bytes)
         h = plan_create(sp, bs, g)
-        del keep, env
+        del keep, env, env_b
         return cls(h, wl.n_kappa, wl.n_omega, wl.n_x, wl.n_t, prec)
 
     def info(self) -> srm3_info:

@@ -41,7 +41,9 @@ class Workload:
     z0: float = 0.03
     k_vk: float = 0.4
     lam: float = 7.0
-    envelope: str = "gauss"          # "gauss" (sigma_g) or "separable" (sigma_e)
+    # "gauss" (sigma_g), "separable" (g = e(i) e(j) e(i+j), sigma_e) or
+    # "sum" (g = b(i+j) alone)
+    envelope: str = "gauss"
     sigma_e: float = 0.5
 
     def envelope_table(self) -> np.ndarray:
@@ -50,6 +52,19 @@ class Workload:
         kk = np.arange(self.n_kappa, dtype=np.float64)[:, None] / (self.sigma_e * self.n_kappa)
         kw = np.arange(self.n_omega, dtype=np.float64)[None, :] / (self.sigma_e * self.n_omega)
         return np.exp(-0.5 * (kk * kk + kw * kw))
+
+    def envelope_tables(self):
+        """(a, b) with g(i, j) = a(i) a(j) b(i+j); b None means b = a.
+        "sum": a = 1 and b(k) = 1 / (2 sqrt((kk + 1/2)(kw + 1/2))), the
+        1/sqrt(omega_k kappa_k) shape of the wind-field bispectrum of Sec. 5
+        with the lattice points taken at their cell centres."""
+        if self.envelope == "separable":
+            return self.envelope_table(), None
+        if self.envelope == "sum":
+            kk = np.arange(self.n_kappa, dtype=np.float64)[:, None] + 0.5
+            kw = np.arange(self.n_omega, dtype=np.float64)[None, :] + 0.5
+            return np.ones((self.n_kappa, self.n_omega)), 0.5 / np.sqrt(kk * kw)
+        raise ValueError(self.envelope)
 
     @property
     def n_samples(self) -> int:

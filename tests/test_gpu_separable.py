@@ -1,12 +1,15 @@
-"""Separable envelope g(i, j) = e(i) e(j) e(i+j): the recursion with the
-envelope factors carried on h = e^2 q, and the pair sum as a zero-padded FFT
-self-convolution, against the FP64 oracle's O(N^2) sums for the same
-envelope (the oracle's separable form is pinned to a numpy FFT convolution in
-test_oracle_pins.py).
+"""Separable envelopes g(i, j) = a(i) a(j) b(i+j) -- one table (a = b = e,
+envelope "separable") or an envelope of i + j alone (a = 1, envelope "sum",
+the shape of the wind-field bispectrum of Sec. 5): the recursion with the
+envelope factors carried on h = a^2 q and b_k^2, and the pair sum as a
+zero-padded FFT self-convolution, against the FP64 oracle's O(N^2) sums for
+the same envelope (the oracle's separable forms are pinned to a numpy FFT
+convolution in test_oracle_pins.py).
 
 Tolerances as in test_gpu_parity.py: FP64 fields 1e-10 sigma_u, FP32 fields
-1e-4 sigma_u; coefficients 1e-11 (FP64) and 2e-6 (FP32) of max|C|; plan
-tables 1e-11 (FP64 plans) and 2e-8 (FP32 plans, eps to 1e-9 of the target).
+1e-4 sigma_u; FP64 coefficients 1e-11 of max|C|; plan
+tables 1e-11 (FP64 plans) and 2e-8 (FP32 plans, eps to 1e-9 of the target);
+FP32 coefficients 1e-5 of max|C| (FFT rounding, see the test).
 """
 import dataclasses
 import functools
@@ -23,17 +26,19 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def sep_case(nk=24, nw=37, nx=64, nt=128, seeds=(1, 2, 3), precision="fp64", sigma_e=0.5):
+def sep_case(nk=24, nw=37, nx=64, nt=128, seeds=(1, 2, 3), precision="fp64", sigma_e=0.5,
+             envelope="separable"):
     wl = W.small_case(nk=nk, nw=nw, nx=nx, nt=nt, seeds=seeds, precision=precision)
-    return dataclasses.replace(wl, envelope="separable", sigma_e=sigma_e,
-                               name=f"sep_{nk}x{nw}")
+    return dataclasses.replace(wl, envelope=envelope, sigma_e=sigma_e,
+                               name=f"{envelope}_{nk}x{nw}")
 
 
 @functools.lru_cache(maxsize=None)
 def oracle_plan(wl, eps=None):
     S = oracle.kaimal_lorentzian(wl.n_kappa, wl.n_omega, wl.kappa_u, wl.omega_u, wl.U, wl.z,
                                  wl.z0, wl.k_vk, wl.lam)
-    env = oracle.Envelope("separable", table=wl.envelope_table())
+    a, b = wl.envelope_tables()
+    env = oracle.Envelope("separable", table=a, table_b=b)
     if eps is None:
         return oracle.make_plan(S, wl.kappa_u, wl.omega_u, target=wl.target, env=env,
                                 beta=wl.beta)
@@ -45,9 +50,10 @@ def _cplx(C):
     return C[..., 0] + 1j * C[..., 1]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_separable_plan_tables_and_eps(oracle_lib, precision):
-    wl = sep_case(precision=precision)
+@pytest.mark.parametrize("precision,envelope", [("fp64", "separable"), ("fp32", "separable"),
+                                                ("fp64", "sum"), ("fp32", "sum")])
+def test_separable_plan_tables_and_eps(oracle_lib, precision, envelope):
+    wl = sep_case(precision=precision, envelope=envelope)
     op = oracle_plan(wl)
     with srm3.Plan.create(wl) as p:
         S, q, sb2 = p.tables()
@@ -72,26 +78,33 @@ def test_separable_recursion_at_fixed_eps(oracle_lib, nk, nw):
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
 
 
-@pytest.mark.parametrize("precision,nk,nw,beta", [("fp64", 24, 37, 0.0), ("fp32", 24, 37, 0.0),
-                                                  ("fp64", 40, 70, 0.6), ("fp32", 33, 20, 0.6)])
-def test_separable_coefficients(oracle_lib, precision, nk, nw, beta):
+@pytest.mark.parametrize("precision,nk,nw,beta,envelope", [
+    ("fp64", 24, 37, 0.0, "separable"), ("fp32", 24, 37, 0.0, "separable"),
+    ("fp64", 40, 70, 0.6, "separable"), ("fp32", 33, 20, 0.6, "separable"),
+    ("fp64", 24, 37, 0.3, "sum"), ("fp32", 40, 70, 0.0, "sum")])
+def test_separable_coefficients(oracle_lib, precision, nk, nw, beta, envelope):
     pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
     wl = dataclasses.replace(sep_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw),
-                                      precision=precision), beta=beta)
+                                      precision=precision, envelope=envelope), beta=beta)
     op = oracle_plan(wl)
     seeds = [3, 11, 2 ** 40 + 1]
     with srm3.Plan.create(wl, eps=op.eps) as p:
         C = _cplx(p.coeffs(seeds))
-    tol = 1e-11 if precision == "fp64" else 2e-6
+    # FP32: a radix-2 FFT convolution's rounding is bounded by about
+    # log2(Nk Nw) u sum |z|^2 (u = 2^-24) for every output at once, 14 x 6e-8 x
+    # the norm of z on these grids, so the bound is taken as 1e-5 of max|C|
+    # (the O(N^2) kernel holds 2e-6); the fields stay within 1e-4 sigma_u below
+    tol = 1e-11 if precision == "fp64" else 1e-5
     for i, s in enumerate(seeds):
         ref = op.coeffs(s)
         scale = np.abs(ref).max()
         assert np.abs(C[i] - ref).max() <= tol * scale
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_separable_field_end_to_end(oracle_lib, precision):
-    wl = sep_case(precision=precision, seeds=(1, 7))
+@pytest.mark.parametrize("precision,envelope", [("fp64", "separable"), ("fp32", "separable"),
+                                                ("fp32", "sum")])
+def test_separable_field_end_to_end(oracle_lib, precision, envelope):
+    wl = sep_case(precision=precision, seeds=(1, 7), envelope=envelope)
     op = oracle_plan(wl)
     sig = math.sqrt(op.moments()[0])
     with srm3.Plan.create(wl) as p:
