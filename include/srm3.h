@@ -179,6 +179,14 @@ typedef struct srm3_info {
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
 
+/* Exact ensemble moments of u at any (x, t): the variance
+ * sum_s sum_k 2 S_k dk dw and the third moment
+ * E[u^3] = 4 eps cos(beta) (dk dw)^2 sum_k sqrt(S_k) sum_{Pi(k)} m g sqrt(S_i S_j)
+ * (m = 6 for i != j, 3 for i = j; Sec. 2 moments of the quadrant form of
+ * Sec. 4), the pair sum taken on the GPU in FP64.  Synchronous on the plan's
+ * stream; allocates nk*nw doubles (stream-ordered) for the duration. */
+int srm3_plan_moments(const srm3_plan *plan, double *variance, double *third_moment);
+
 /* Copy the plan's FP64 tables to host arrays of n_kappa*n_omega doubles
  * (any may be NULL): S, q = S/S_p (1 where S = 0), sum_b2. */
 int srm3_plan_tables(const srm3_plan *plan, double *S, double *q, double *sum_b2);

@@ -1015,6 +1015,68 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   return SRM3_OK;
 }
 
+// Exact third moment of u (Sec. 2, the third-order moment of the wave; the
+// quadrant form of Sec. 4): with b_p(i,j) = eps g sqrt(dk dw q_i q_j) every
+// factor of S_p cancels, and over both sheets
+//   E[u^3] = 4 eps cos(beta) (dk dw)^2 sum_k sqrt(S_k)
+//            sum_{Pi(k)} m_ij g_ij sqrt(S_i S_j),   m = 6 (i != j), 3 (i = j).
+// One warp per lattice point, pairs enumerated as in the direct levels of the
+// recursion (rows a <= kk/2, centre row iw <= kw/2, i = 0 skipped); FP64.
+// part[k] = sqrt(S_k) times the point's pair sum.
+__global__ void k_moment3(int nk, int nw, const double *__restrict__ S,
+                          const double *__restrict__ G2, const double *__restrict__ ea,
+                          const double *__restrict__ eb, double *__restrict__ part) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (long long)nk * nw) return;
+  const int kk = (int)(gw / nw), kw = (int)(gw - (long long)kk * nw);
+  double acc = 0.0;
+  if (S[gw] > 0.0) {
+    const int W = kw + 1, E = (kk / 2 + 1) * W;
+    for (int e = lane; e < E; e += 32) {
+      const int a = e / W, iw = e - a * W, b = kk - a, jw = kw - iw;
+      const int lim = (a == b) ? kw / 2 : kw;
+      if ((a == 0 && iw == 0) || iw > lim) continue;
+      const size_t i = (size_t)a * nw + iw, j = (size_t)b * nw + jw;
+      const double si = S[i], sj = S[j];
+      if (!(si > 0.0) || !(sj > 0.0)) continue;
+      const int dk = 2 * a - kk, dw = 2 * iw - kw;
+      double g = sqrt(G2[(size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw)]);
+      if (ea) g *= ea[i] * ea[j] * eb[gw];
+      const double m = (i == j) ? 3.0 : 6.0;
+      acc += m * g * sqrt(si * sj);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) part[gw] = acc * sqrt(S[gw] > 0.0 ? S[gw] : 0.0);
+}
+
+SRM3_API int srm3_plan_moments(const srm3_plan *plan, double *variance, double *third_moment) {
+  if (!plan || !variance || !third_moment)
+    return fail(SRM3_ERR_INVALID_ARG, "plan and outputs must be non-NULL");
+  const long long nl = (long long)plan->nk * plan->nw;
+  cudaStream_t st = plan->stream;
+  double *part = nullptr;
+  SRM3_CUDA(cudaMallocAsync(&part, nl * sizeof(double), st));
+  const long long threads = nl * 32;
+  k_moment3<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      plan->nk, plan->nw, plan->S, plan->G2, plan->sep ? plan->env_e : nullptr,
+      plan->sep ? plan->env_b : nullptr, part);
+  cudaError_t e = cudaGetLastError();
+  std::vector<double> h(nl);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), part, nl * sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = cudaFreeAsync(part, st);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "srm3_plan_moments");
+  long double sum = 0.0L;
+  for (long long k = 0; k < nl; ++k) sum += h[k];
+  *variance = plan->variance;
+  *third_moment = (double)(4.0L * plan->eps * std::cos(plan->beta) * plan->dkdw * plan->dkdw * sum);
+  return SRM3_OK;
+}
+
 SRM3_API int srm3_plan_tables(const srm3_plan *plan, double *S, double *q, double *sum_b2) {
   if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
   const size_t nl = (size_t)plan->nk * plan->nw;

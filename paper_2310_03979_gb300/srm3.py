@@ -32,6 +32,7 @@ SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE, SRM3_STORAGE_TUNE
 EXPORTED = [
     "srm3_plan_create", "srm3_sample", "srm3_sample_host", "srm3_destroy", "srm3_sync",
     "srm3_set_stream", "srm3_last_error", "srm3_plan_info", "srm3_plan_tables",
+    "srm3_plan_moments",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
@@ -120,6 +121,7 @@ def load(build_if_needed: bool = True):
     lib.srm3_plan_info.argtypes = [vp, ctypes.POINTER(srm3_info)]
     dp = ctypes.POINTER(ctypes.c_double)
     lib.srm3_plan_tables.argtypes = [vp, dp, dp, dp]
+    lib.srm3_plan_moments.argtypes = [vp, dp, dp]
     lib.srm3_phase_words.argtypes = [vp, u64p, i32, vp]
     lib.srm3_coeffs.argtypes = [vp, u64p, i32, vp]
     lib.srm3_field_from_coeffs.argtypes = [vp, vp, i32, vp]
@@ -364,6 +366,12 @@ class Plan:
 
     def tables(self):
         return plan_tables(self.handle, self.nk, self.nw)
+
+    def moments(self):
+        """(variance, third moment) of u, exact (srm3_plan_moments)."""
+        v, m3 = ctypes.c_double(), ctypes.c_double()
+        _check(load().srm3_plan_moments(self.handle, ctypes.byref(v), ctypes.byref(m3)))
+        return v.value, m3.value
 
     def _torch_dtype(self):
         import torch

@@ -136,3 +136,28 @@ def test_separable_in_a_batch_is_bit_identical_to_alone():
     finally:
         for p in plans:
             p.destroy()
+
+
+@pytest.mark.parametrize("envelope,precision,beta", [("gauss", "fp64", 0.0), ("gauss", "fp32", 0.4),
+                                                     ("separable", "fp64", 0.3),
+                                                     ("sum", "fp64", -0.5)])
+def test_exact_moments_against_oracle(oracle_lib, envelope, precision, beta):
+    """srm3_plan_moments: the exact variance and third moment against the
+    oracle's direct sums over (S_p, b_p) at the same eps."""
+    wl = dataclasses.replace(W.small_case(nk=24, nw=37, precision=precision), beta=beta,
+                             envelope=envelope)
+    S = oracle.kaimal_lorentzian(wl.n_kappa, wl.n_omega, wl.kappa_u, wl.omega_u, wl.U, wl.z,
+                                 wl.z0, wl.k_vk, wl.lam)
+    if envelope == "gauss":
+        env = oracle.Envelope("gauss", wl.sigma_g)
+    else:
+        a, b = wl.envelope_tables()
+        env = oracle.Envelope("separable", table=a, table_b=b)
+    with srm3.Plan.create(wl) as p:
+        eps = p.info().eps
+        var, m3 = p.moments()
+    op = oracle.make_plan(S, wl.kappa_u, wl.omega_u, eps=eps, env=env, beta=beta)
+    ovar, om3 = op.moments()
+    assert var == pytest.approx(ovar, rel=1e-12)
+    assert abs(om3) > 1e-3 * ovar ** 1.5
+    assert m3 == pytest.approx(om3, rel=1e-11)
