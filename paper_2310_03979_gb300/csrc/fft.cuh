@@ -22,31 +22,68 @@ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   return r;
 }
 
+// One radix-2 butterfly: (a, b) <- (a + w b, a - w b).
+template <typename T2>
+__device__ __forceinline__ void bfly(T2 &a, T2 &b, T2 w) {
+  const T2 x1 = cmul(b, w);
+  T2 o0, o1;
+  o0.x = a.x + x1.x;
+  o0.y = a.y + x1.y;
+  o1.x = a.x - x1.x;
+  o1.y = a.y - x1.y;
+  a = o0;
+  b = o1;
+}
+
+// Stages 1..log2n of ncols transforms of length n = 2^log2n stored
+// column after column in buf (input in bit-reversed order).  Stages go in
+// pairs (s, s + 1) held in registers: four elements j, j + h, j + 2h, j + 3h
+// of a block of 4h (h = 2^(s-1)) take the two butterflies of stage s and the
+// two of stage s + 1 -- the same butterflies, in the same order, as one
+// stage at a time, with half the shared-memory round trips and barriers.
+// An odd last stage runs alone.
 template <typename T2>
 __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ tw,
                            int log2nfft) {
   const int n = 1 << log2n;
-  const int halfn = n >> 1;
-  const int total = ncols * halfn;
-  for (int s = 1; s <= log2n; ++s) {
+  int s = 1;
+  for (; s + 1 <= log2n; s += 2) {
     const int half = 1 << (s - 1);
+    const int quarter_n = n >> 2;
+    const int total = ncols * quarter_n;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int col = t >> (log2n - 2);
+      const int g = t & (quarter_n - 1);
+      const int blk = g >> (s - 1);
+      const int j = g & (half - 1);
+      const int i0 = col * n + blk * 4 * half + j;
+      T2 e0 = buf[i0], e1 = buf[i0 + half], e2 = buf[i0 + 2 * half], e3 = buf[i0 + 3 * half];
+      const T2 ws = tw[j << (log2nfft - s)];
+      bfly(e0, e1, ws);
+      bfly(e2, e3, ws);
+      bfly(e0, e2, tw[j << (log2nfft - s - 1)]);
+      bfly(e1, e3, tw[(j + half) << (log2nfft - s - 1)]);
+      buf[i0] = e0;
+      buf[i0 + half] = e1;
+      buf[i0 + 2 * half] = e2;
+      buf[i0 + 3 * half] = e3;
+    }
+    __syncthreads();
+  }
+  if (s == log2n) {  // odd number of stages: the last one alone
+    const int half = 1 << (s - 1);
+    const int halfn = n >> 1;
+    const int total = ncols * halfn;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
       const int col = t >> (log2n - 1);
       const int bf = t & (halfn - 1);
       const int grp = bf >> (s - 1);
       const int j = bf & (half - 1);
       const int i0 = col * n + grp * 2 * half + j;
-      const int i1 = i0 + half;
-      const T2 w = tw[j << (log2nfft - s)];
-      const T2 x0 = buf[i0];
-      const T2 x1 = cmul(buf[i1], w);
-      T2 o0, o1;
-      o0.x = x0.x + x1.x;
-      o0.y = x0.y + x1.y;
-      o1.x = x0.x - x1.x;
-      o1.y = x0.y - x1.y;
-      buf[i0] = o0;
-      buf[i1] = o1;
+      T2 a = buf[i0], b = buf[i0 + half];
+      bfly(a, b, tw[j << (log2nfft - s)]);
+      buf[i0] = a;
+      buf[i0 + half] = b;
     }
     __syncthreads();
   }
