@@ -185,6 +185,39 @@ __device__ void point_direct(const RecArgs &A, int kk, int kw, int lane) {
 // order of additions exactly as if the slot were skipped.
 constexpr int kBulkUnroll = 4;
 
+// One sliver of a point's bulk pairs for this lane: rows v = v0, v0 + 2, ...
+// < n with i = (a0 + v, iw0 - v) and j = k - i; uok: the lane's omega slot
+// lies inside the sliver.  Offsets step linearly with v; the canonical
+// limits (centre row, i != 0, iw <= kw) mask the rest.
+template <typename T, int M>
+__device__ __forceinline__ void bulk_rows(int kk, int kw, int nw, const T *__restrict__ G2,
+                                          const T *__restrict__ q, int n, int v0, int a0,
+                                          int iw0, bool uok, T (&acc)[M]) {
+  const int qa0 = (a0 * nw + iw0) * M, qb0 = ((kk - a0) * nw + (kw - iw0)) * M;
+  const int qstep = (nw - 1) * M;  // qa grows and qb shrinks by this per row
+  for (int v = v0; v < n; v += 2 * kBulkUnroll) {
+    T g2[kBulkUnroll], va[kBulkUnroll][M], vb[kBulkUnroll][M];
+#pragma unroll
+    for (int s = 0; s < kBulkUnroll; ++s) {
+      const int vs = v + 2 * s;
+      const int a = a0 + vs, iw = iw0 - vs, b = kk - a;
+      const bool ok = uok && vs < n && iw >= (a == 0 ? 1 : 0) &&
+                      iw <= ((a == b) ? kw / 2 : kw) && iw <= kw;
+      const int dk = 2 * a - kk, dw = 2 * iw - kw;
+      const int gi = ok ? (dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+      const int qa = ok ? qa0 + vs * qstep : 0;
+      const int qb = ok ? qb0 - vs * qstep : 0;
+      g2[s] = ok ? G2[gi] : (T)0;
+      PlaneVec<T, M>::load(q + qa, va[s]);
+      PlaneVec<T, M>::load(q + qb, vb[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < kBulkUnroll; ++s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
+  }
+}
+
 template <typename T, int M>
 __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   const long long k = (long long)kk * A.nw + kw;
@@ -196,8 +229,7 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   const int aL0 = max(0, kk - D + 1), aL1 = arow - 1;
   const int nR = (uR0 < kRecBL && aR1 >= aR0) ? aR1 - aR0 + 1 : 0;
   const int nL = (uL0 < kRecBL && aL1 >= aL0) ? aL1 - aL0 + 1 : 0;
-  const int nrows = nR + nL;
-  if (nrows == 0) return;
+  if (nR + nL == 0) return;
   const int u = lane & (kRecBL - 1), rs = lane >> 4;
   T acc[M];
 #pragma unroll
@@ -205,40 +237,13 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   const int nw = A.nw;
   const T *G2 = static_cast<const T *>(A.G2);
   const T *q = static_cast<const T *>(A.q);
-  for (int v0 = rs; v0 < nrows; v0 += 2 * kBulkUnroll) {
-    T g2[kBulkUnroll], va[kBulkUnroll][M], vb[kBulkUnroll][M];
-#pragma unroll
-    for (int s = 0; s < kBulkUnroll; ++s) {
-      const int v = v0 + 2 * s;
-      int a, iw, jw;
-      bool ok;
-      if (v < nR) {
-        a = aR0 + v;
-        iw = base - a + u;
-        jw = kw - iw;
-        ok = u >= uR0;
-      } else {
-        a = aL0 + (v - nR);
-        jw = base - (kk - a) + u;
-        iw = kw - jw;
-        ok = u >= uL0;
-      }
-      const int b = kk - a;
-      const int lim = (a == b) ? kw / 2 : kw;
-      ok = ok && v < nrows && iw >= (a == 0 ? 1 : 0) && iw <= lim && jw >= 0;
-      const int dk = 2 * a - kk, dw = 2 * iw - kw;
-      const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
-      const size_t qa = ok ? ((size_t)a * nw + iw) * M : 0;
-      const size_t qb = ok ? ((size_t)b * nw + jw) * M : 0;
-      g2[s] = ok ? G2[gi] : (T)0;
-      PlaneVec<T, M>::load(q + qa, va[s]);
-      PlaneVec<T, M>::load(q + qb, vb[s]);
-    }
-#pragma unroll
-    for (int s = 0; s < kBulkUnroll; ++s)
-#pragma unroll
-      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
-  }
+  // rows v < nR: right sliver, i = (aR0 + v, base - aR0 - v + u);
+  // rows v = nR + m: left sliver, j = (kk - aL0 - m, base - kk + aL0 + m + u).
+  // Each lane takes the rows of its parity rs, right then left: the order of
+  // one sequence over v.
+  bulk_rows<T, M>(kk, kw, nw, G2, q, nR, rs, aR0, base - aR0 + u, u >= uR0, acc);
+  bulk_rows<T, M>(kk, kw, nw, G2, q, nL, (rs + nR) & 1, aL0, kw - base + kk - aL0 - u, u >= uL0,
+                  acc);
   warp_sum<T, M>(acc);
   if (lane == 0) {
     T *ac = static_cast<T *>(A.acc);
