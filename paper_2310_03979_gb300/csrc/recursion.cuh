@@ -116,26 +116,30 @@ __device__ __forceinline__ void warp_sum(T (&v)[M]) {
     for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
 }
 
-// q_k and sum_b2(k) from the point's complete pair sum t (lane 0 only).
+// q_k and sum_b2(k) of plane m from the point's complete pair sum t.
 template <typename T, int M>
-__device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
+__device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, int m, T t) {
   T *q = static_cast<T *>(A.q);
   const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;    // a_k^2
   const T bk2 = A.e2k ? (T)A.e2k[k] : (T)1;  // b_k^2
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-    const T s2 = (T)A.scal[m] * bk2 * t[m];
-    A.sb2[m * A.nl + k] = (double)s2;
-    if (s2 < (T)1) {
-      const T qk = (T)1 / ((T)1 - s2);
-      q[k * M + m] = A.e2 ? ek2 * qk : qk;
-      if (A.qout) A.qout[k] = (double)qk;
-    } else {
-      q[k * M + m] = (T)0;
-      if (A.qout) A.qout[k] = 0.0;
-      atomicOr(A.err + m, 1);
-    }
+  const T s2 = (T)A.scal[m] * bk2 * t;
+  A.sb2[m * A.nl + k] = (double)s2;
+  if (s2 < (T)1) {
+    const T qk = (T)1 / ((T)1 - s2);
+    q[k * M + m] = A.e2 ? ek2 * qk : qk;
+    if (A.qout) A.qout[k] = (double)qk;
+  } else {
+    q[k * M + m] = (T)0;
+    if (A.qout) A.qout[k] = 0.0;
+    atomicOr(A.err + m, 1);
   }
+}
+
+// All planes of a point (lane 0 only).
+template <typename T, int M>
+__device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) finalize_plane<T, M>(A, k, m, t[m]);
 }
 
 template <typename T, int M>
@@ -266,12 +270,8 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   // with S_k = 0 sums its (finite) terms like any other and is zeroed at
   // the end, which keeps one memory round trip off the level's critical path
   const double Sk = A.S[k];
-  T bulk[M];  // the point's bulk sums, loaded ahead of the pair loads
-  if (lane == 0) {
-    const T *ac = static_cast<const T *>(A.acc);
-#pragma unroll
-    for (int m = 0; m < M; ++m) bulk[m] = ac[k * M + m];
-  }
+  // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
+  const T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
   const int t = kk + kw - D;
   const int nlow = t * (t + 3) / 2;
   T acc[M];
@@ -313,10 +313,12 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
     point_zero<T, M>(A, k, lane);
     return;
   }
-  if (lane == 0) {
+  if (lane < M) {
+    T t = (T)0;
 #pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] += bulk[m];
-    finalize<T, M>(A, k, acc);
+    for (int m = 0; m < M; ++m)
+      if (m == lane) t = acc[m];
+    finalize_plane<T, M>(A, k, lane, t + bulk);
   }
 }
 
