@@ -81,3 +81,36 @@ def test_null_and_noop_calls():
     h = ctypes.c_void_p()
     assert lib.srm3_plan_create(ctypes.byref(sp), ctypes.byref(bs), ctypes.byref(g),
                                 ctypes.byref(h)) == -8
+
+
+def test_separable_envelope_validation():
+    """SEPARABLE needs a finite, non-negative env_table (env_table_b may be
+    NULL, but if given it obeys the same rules); an unknown kind is refused.
+    All checked on the host before any device work."""
+    import numpy as np
+    lib = srm3.load()
+    wl = W.small_case(nk=24, nw=20, nx=64, nt=64)
+    good = np.ones((24, 20))
+    bad = good.copy()
+    bad[3, 4] = -1.0
+    nan = good.copy()
+    nan[0, 1] = np.nan
+    dp = ctypes.POINTER(ctypes.c_double)
+    for a, b in [(None, None), (bad, None), (nan, None), (good, bad), (good, nan)]:
+        sp, bs, g = _structs(wl)
+        bs.kind = srm3.SRM3_BISPECTRUM_SEPARABLE
+        if a is not None:
+            bs.env_table = np.ascontiguousarray(a).ctypes.data_as(dp)
+        if b is not None:
+            bs.env_table_b = np.ascontiguousarray(b).ctypes.data_as(dp)
+        h = ctypes.c_void_p(123)
+        rc = lib.srm3_plan_create(ctypes.byref(sp), ctypes.byref(bs), ctypes.byref(g),
+                                  ctypes.byref(h))
+        assert rc == -1 and h.value is None
+        assert b"env_table" in lib.srm3_last_error()
+    sp, bs, g = _structs(wl)
+    bs.kind = 7
+    h = ctypes.c_void_p(123)
+    assert lib.srm3_plan_create(ctypes.byref(sp), ctypes.byref(bs), ctypes.byref(g),
+                                ctypes.byref(h)) == -1
+    assert h.value is None
