@@ -39,27 +39,35 @@ struct RecArgs {
 // `target` (the barrier's number within the launch x gridDim.x); the fences
 // on both sides order every CTA's writes before the barrier with every read
 // after it.  Waits are bounded: past ~2^22 polls a CTA raises *abort and
-// every CTA returns false from this or its next barrier.
+// sets kBarAbort in the counter, which every poll sees at once (the counter
+// then exceeds any target), so every CTA returns false from this or its next
+// barrier without a second memory read on the normal path.
+constexpr unsigned int kBarAbort = 1u << 30;
+
 __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int target) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     const long long limit = 1ll << 22;
     volatile unsigned int *cnt = bar;
-    volatile int *vab = abort;
     __threadfence();
     atomicAdd(bar, 1u);
     bool ok = true;
     long long spins = 0;
-    while (*cnt < target) {
-      if ((++spins & 63) == 0 && (*vab || spins > limit)) {
+    unsigned int v;
+    while ((v = *cnt) < target) {
+      if (++spins > limit) {
         ok = false;
         break;
       }
     }
-    if (!ok) atomicExch(abort, 1);
+    if (v & kBarAbort) ok = false;
+    if (!ok) {
+      atomicOr(bar, kBarAbort);
+      atomicExch(abort, 1);
+    }
     __threadfence();
-    s_ok = ok && *vab == 0;
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
