@@ -178,9 +178,10 @@ def oracle_baseline(wl, rows=48, seed=1, passes=None):
     sub = rows
     S = oracle.kaimal_lorentzian(sub, wl.n_omega, sub * dk, wl.omega_u, wl.U, wl.z, wl.z0,
                                  wl.k_vk, wl.lam)
-    if wl.envelope == "separable":  # the workload's e on the sampled rows
-        env = oracle.Envelope("separable", table=np.ascontiguousarray(
-            wl.envelope_table()[:sub], dtype=np.float64))
+    if wl.envelope != "gauss":  # the workload's tables on the sampled rows
+        ta, tb = wl.envelope_tables()
+        env = oracle.Envelope("separable", table=np.ascontiguousarray(ta[:sub]),
+                              table_b=None if tb is None else np.ascontiguousarray(tb[:sub]))
     else:
         env = oracle.Envelope("gauss", wl.sigma_g * wl.n_kappa / sub)  # same width per index
     eps = 1e-3
@@ -554,17 +555,17 @@ def main():
     t_last = recs[-1][0]
     chunks = math.ceil(n / 128)
     # kernels launched per step (matches the ncu launch list): spectrum 1,
-    # envelope tables 2 + g^2 1, linear pass + reduction 2, each recursion
-    # pass + reduction 2, sampling tables 5 (FP32) / 4 (FP64), W table 1 if
-    # stored; per 128-sample chunk: phases, pair sum, two FFT stages
-    launches_per_step = (1 + 3 + 2 + 2 * (info.root_passes + info.root_passes_fp32)
+    # envelope tables 2 + g^2 1, the sum of S 1, linear pass + reduction 2,
+    # each recursion pass 1, sampling tables 5 (FP32) / 4 (FP64), W table 1
+    # if stored; per 128-sample chunk: phases, pair sum, two FFT stages
+    launches_per_step = (1 + 3 + 1 + 2 + (info.root_passes + info.root_passes_fp32)
                          + (5 if es == 4 else 4) + (1 if info.storage == 1 else 0)
                          + 4 * chunks)
-    if wl.envelope == "separable":
+    if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
         # self-convolution passes, two output FFT stages
-        launches_per_step = (1 + 3 + 2 * (info.root_passes + info.root_passes_fp32)
+        launches_per_step = (1 + 3 + 1 + (info.root_passes + info.root_passes_fp32)
                              + (5 if es == 4 else 4) + 1 + 6 * chunks)
     traffic = None
     src = os.path.join(ROOT, "paper_2310_03979_gb300", "csrc", "pairsum.cuh")
@@ -598,7 +599,7 @@ def main():
                                 "transform": t_last.transform_ms},
         "sampling_only_pair_terms_per_s": terms_per_step / (
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
-        "roofline": (_conv_roofline(wl, n, es, avg_launch_ms) if wl.envelope == "separable"
+        "roofline": (_conv_roofline(wl, n, es, avg_launch_ms) if wl.envelope != "gauss"
                      else _pairsum_roofline(
             terms_per_launch / (avg_launch_ms * 1e-3), traffic,
             algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (

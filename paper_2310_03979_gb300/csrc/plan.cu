@@ -232,6 +232,16 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
+  SRM3_CUDA(cudaMalloc(&p->rec_max, kPlanes * sizeof(unsigned long long)));
+  // sum of S (the exact variance), once: the plane-0 results of this
+  // reduction are not used
+  SRM3_CUDA(cudaMemsetAsync(p->sb2, 0, (size_t)nk * nw * sizeof(double), st));
+  k_reduce_planes<<<1, 1024, 0, st>>>((long long)nk * nw, p->S, p->sb2, p->scal);
+  SRM3_CUDA(cudaGetLastError());
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 11, p->scal + 11, sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  p->sumS = p->h_pinned[11];
   p->rec_bar_words = 2 + (nk + nw) / kRecBL + 1;  // barrier counter + a ticket per bulk phase
   SRM3_CUDA(cudaMalloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int)));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
@@ -263,6 +273,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   SRM3_CUDA(cudaMemcpyAsync(p->scal, p->h_pinned, M * sizeof(double), cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaMemsetAsync(p->err, 0, (kPlanes + 1) * sizeof(int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
+  SRM3_CUDA(cudaMemsetAsync(p->rec_max, 0, kPlanes * sizeof(unsigned long long), st));
   RecArgs A;
   A.nk = p->nk;
   A.nw = p->nw;
@@ -284,6 +295,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.err = p->err;
   A.bar = p->rec_bar;
   A.abort = p->err + kPlanes;
+  A.maxb = p->rec_max;
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
   if (fp64 && M == 1)
@@ -297,10 +309,9 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   else
     SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<float, kPlanes>,
                                           p->rec_grid32, kRecThreads, args, 0, st));
-  k_reduce_planes<<<M, 1024, 0, st>>>(A.nl, p->S, p->sb2, p->scal);
   SRM3_CUDA(cudaGetLastError());
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->scal + 8, 4 * M * sizeof(double),
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, M * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st));
   SRM3_CUDA(cudaMemcpyAsync(p->h_err, p->err, (kPlanes + 1) * sizeof(int), cudaMemcpyDeviceToHost,
                             st));
@@ -312,9 +323,9 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   if (p->h_err[kPlanes])
     return fail(SRM3_ERR_TIMEOUT, "recursion pass: grid barrier wait timed out");
   for (int m = 0; m < M; ++m) {
-    r[m].max_sb2 = p->h_pinned[8 + 4 * m + 1];
-    r[m].min_pure = p->h_pinned[8 + 4 * m + 2];
-    r[m].sumS = p->h_pinned[8 + 4 * m + 3];
+    r[m].max_sb2 = p->h_pinned[8 + m];  // the bits of a double, copied as such
+    r[m].min_pure = 1.0 - r[m].max_sb2;
+    r[m].sumS = p->sumS;
     r[m].err = p->h_err[m];
   }
   if (fp64)
@@ -878,7 +889,7 @@ void free_plan(srm3_plan *p) {
                  p->tw,     p->tile_order, p->tile_off, p->W,       p->y,      p->y0,
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
-                 p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar,
+                 p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
                  p->Ew2,    p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
                  p->tw_conv, p->Zc,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,

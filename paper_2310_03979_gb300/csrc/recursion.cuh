@@ -31,6 +31,7 @@ struct RecArgs {
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
   int *abort;           // barrier wait timed out
+  unsigned long long *maxb;  // [M]: max_k sum_b2 per plane, as the bits of a double >= 0
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident): one
@@ -132,6 +133,8 @@ __device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, in
   const T bk2 = A.e2k ? (T)A.e2k[k] : (T)1;  // b_k^2
   const T s2 = (T)A.scal[m] * bk2 * t;
   A.sb2[m * A.nl + k] = (double)s2;
+  // non-negative doubles order as their bit patterns
+  atomicMax(A.maxb + m, (unsigned long long)__double_as_longlong((double)s2));
   if (s2 < (T)1) {
     const T qk = (T)1 / ((T)1 - s2);
     q[k * M + m] = A.e2 ? ek2 * qk : qk;

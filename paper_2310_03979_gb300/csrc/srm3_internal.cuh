@@ -155,6 +155,8 @@ struct srm3_plan {
   int *rec_lev_off = nullptr;        // first item of each level
   unsigned int *rec_bar = nullptr;   // grid barrier counter and bulk-phase tickets
   int rec_bar_words = 0;
+  unsigned long long *rec_max = nullptr;  // per-plane max sum_b2 of a pass (bits)
+  double sumS = 0.0;                      // sum of S over the lattice
   int maxpts = 0, rec_grid64 = 0, rec_grid32 = 0;
   double *h_pinned = nullptr;  // pinned host scalars
   int *h_err = nullptr;        // pinned host error words
