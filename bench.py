@@ -89,6 +89,22 @@ def _conv_roofline(wl, n, es, launch_ms):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
 
 
+def _pairsum_roofline_fp64(terms_per_s, **extra):
+    """Roofline of the plain FP64 pair sum (one thread per output): 6 FP64
+    lane operations per pair-term (complex product 2 DMUL + 2 DFMA, weighted
+    accumulate 2 DFMA) over the FP64 rate 152 SM x 2 lanes x the maximum SM
+    clock (GB300's nominal 1.25 TFLOP/s dense FP64)."""
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    lane_rate = 2 * N_SM * sm_max * 1e6
+    ops = 6.0 * terms_per_s
+    out = {"bound": "alu", "achieved": ops / 1e12, "peak": lane_rate / 1e12,
+           "unit": "T FP64-pipe lane-ops/s", "frac": ops / lane_rate, "traffic": None,
+           "per_unit": "6 FP64-pipe lane-ops per pair-term",
+           "peak_source": f"derived: {N_SM} SM x 2 FP64 lanes x {sm_max:.0f} MHz"}
+    out.update(extra)
+    return out
+
+
 def _pairsum_roofline(terms_per_s, traffic=None, **extra):
     """Roofline object of the FP32 pair sum from its kernel-only rate.
 
@@ -600,6 +616,8 @@ def main():
         "sampling_only_pair_terms_per_s": terms_per_step / (
             (t_last.phases_ms + t_last.pairsum_ms + t_last.transform_ms) * 1e-3),
         "roofline": (_conv_roofline(wl, n, es, avg_launch_ms) if wl.envelope != "gauss"
+                     else _pairsum_roofline_fp64(terms_per_launch / (avg_launch_ms * 1e-3),
+                                                 kernel="k_pairsum_f64") if es == 8
                      else _pairsum_roofline(
             terms_per_launch / (avg_launch_ms * 1e-3), traffic,
             algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (
