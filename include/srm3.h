@@ -187,6 +187,15 @@ int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
  * stream; allocates nk*nw doubles (stream-ordered) for the duration. */
 int srm3_plan_moments(const srm3_plan *plan, double *variance, double *third_moment);
 
+/* Failure path of the bounded waits, exercised on the current device without
+ * a fault: a cooperative launch whose CTA 0 never reaches a grid barrier (the
+ * recursion's barrier, polling limit 2^14) and a wait on an mbarrier that
+ * nothing arrives at (the FP32 pair sum's wait, limit 2e7 cycles).  Each
+ * wait gives up, raises its error word and returns; *barrier_timed_out and
+ * *wait_timed_out receive those words (1 when the timeout fired).  Takes about
+ * 20 ms; synchronous; the device stays usable. */
+int srm3_selftest_timeouts(int *barrier_timed_out, int *wait_timed_out);
+
 /* Copy the plan's FP64 tables to host arrays of n_kappa*n_omega doubles
  * (any may be NULL): S, q = S/S_p (1 where S = 0), sum_b2. */
 int srm3_plan_tables(const srm3_plan *plan, double *S, double *q, double *sum_b2);

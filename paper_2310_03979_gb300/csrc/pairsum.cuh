@@ -182,12 +182,13 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
 // CTA's abort flag is up or the wait passes kWaitCycles (then it raises the
 // flag and the error word).
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity,
-                                          volatile int *abort, int *err) {
+                                          volatile int *abort, int *err,
+                                          long long limit = packed::kWaitCycles) {
   if (mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > packed::kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort = 1;
       atomicOr(err, 1);
       return false;

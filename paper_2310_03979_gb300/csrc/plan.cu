@@ -1101,3 +1101,34 @@ SRM3_API int srm3_plan_tables(const srm3_plan *plan, double *S, double *q, doubl
   if (sum_b2) SRM3_CUDA(cudaMemcpy(sum_b2, plan->sb2, nl * sizeof(double), cudaMemcpyDeviceToHost));
   return SRM3_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Failure path of the grid barrier, without a fault: every CTA but 0 waits at
+// a barrier CTA 0 never reaches, gives up after `polls` polls and raises the
+// abort word, which the host reads (the context stays usable).
+namespace srm3 {
+__global__ void k_selftest_barrier(unsigned int *bar, int *abort, long long limit) {
+  if (blockIdx.x == 0) return;  // the arrival nothing makes
+  grid_barrier(bar, abort, gridDim.x, limit);
+}
+
+int selftest_barrier(long long polls, int *timed_out) {
+  unsigned int *bar = nullptr;
+  int *ab = nullptr;
+  SRM3_CUDA(cudaMalloc(&bar, 64));
+  SRM3_CUDA(cudaMalloc(&ab, sizeof(int)));
+  cudaError_t e = cudaMemset(bar, 0, 64);
+  if (e == cudaSuccess) e = cudaMemset(ab, 0, sizeof(int));
+  void *args[] = {&bar, &ab, &polls};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void *)k_selftest_barrier, 2, 32, args, 0, 0);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, ab, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(ab);
+  if (e != cudaSuccess) return cuda_fail(e, "grid barrier self-test");
+  *timed_out = h;
+  return SRM3_OK;
+}
+}  // namespace srm3

@@ -45,11 +45,11 @@ struct RecArgs {
 // barrier without a second memory read on the normal path.
 constexpr unsigned int kBarAbort = 1u << 30;
 
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int target) {
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int target,
+                                             long long limit = 1ll << 22) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const long long limit = 1ll << 22;
     volatile unsigned int *cnt = bar;
     __threadfence();
     atomicAdd(bar, 1u);

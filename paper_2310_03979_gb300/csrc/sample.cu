@@ -1008,3 +1008,43 @@ SRM3_API int srm3_batch_pairsum_ms(srm3_batch *b, double *ms) {
 SRM3_API void srm3_batch_destroy(srm3_batch *b) {
   if (b) batch_free(b);
 }
+
+// ---------------------------------------------------------------------------
+// Failure path of the bounded mbarrier wait of the FP32 pair sum, without a
+// fault: one thread waits on an mbarrier (count 1) that nothing arrives at,
+// gives up after `cycles` clock cycles and raises the error word.
+namespace srm3 {
+__global__ void k_selftest_mbar(int *err, long long limit) {
+  __shared__ unsigned long long b;
+  __shared__ int ab;
+  if (threadIdx.x == 0) {
+    mbar_init(&b, 1);
+    ab = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(&b, 0, &ab, err, limit);
+}
+}  // namespace srm3
+
+SRM3_API int srm3_selftest_timeouts(int *barrier_timed_out, int *wait_timed_out) {
+  if (!barrier_timed_out || !wait_timed_out)
+    return fail(SRM3_ERR_INVALID_ARG, "outputs must be non-NULL");
+  // about 10 ms of waiting each: 2^14 polls of an L2 word, 2e7 clock cycles
+  int rc = selftest_barrier(1ll << 14, barrier_timed_out);
+  if (rc) return rc;
+  int *er = nullptr;
+  SRM3_CUDA(cudaMalloc(&er, sizeof(int)));
+  cudaError_t e = cudaMemset(er, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_selftest_mbar<<<1, 32>>>(er, 20000000ll);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, er, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(er);
+  if (e != cudaSuccess) return cuda_fail(e, "mbarrier wait self-test");
+  *wait_timed_out = h;
+  return SRM3_OK;
+}

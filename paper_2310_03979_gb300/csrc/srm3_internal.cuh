@@ -44,6 +44,8 @@ struct SeedChunk {
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+// Grid-barrier timeout self-test (plan.cu): *timed_out = the abort word.
+int selftest_barrier(long long polls, int *timed_out);
 
 #define SRM3_CUDA(call)                                 \
   do {                                                  \

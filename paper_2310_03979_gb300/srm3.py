@@ -32,7 +32,7 @@ SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE, SRM3_STORAGE_TUNE
 EXPORTED = [
     "srm3_plan_create", "srm3_sample", "srm3_sample_host", "srm3_destroy", "srm3_sync",
     "srm3_set_stream", "srm3_last_error", "srm3_plan_info", "srm3_plan_tables",
-    "srm3_plan_moments",
+    "srm3_plan_moments", "srm3_selftest_timeouts",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
@@ -122,6 +122,7 @@ def load(build_if_needed: bool = True):
     dp = ctypes.POINTER(ctypes.c_double)
     lib.srm3_plan_tables.argtypes = [vp, dp, dp, dp]
     lib.srm3_plan_moments.argtypes = [vp, dp, dp]
+    lib.srm3_selftest_timeouts.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2
     lib.srm3_phase_words.argtypes = [vp, u64p, i32, vp]
     lib.srm3_coeffs.argtypes = [vp, u64p, i32, vp]
     lib.srm3_field_from_coeffs.argtypes = [vp, vp, i32, vp]
