@@ -41,7 +41,7 @@ __device__ __forceinline__ typename Vec2<T>::type conv_y(const void *y, int SSpa
 template <typename T>
 __global__ void k_conv_rows(int nk, int nw, int log2Nw, int Nk, int SSpad, int rowstride,
                             const void *__restrict__ y, const T *__restrict__ e,
-                            const typename Vec2<T>::type *__restrict__ tw, int log2ntw,
+                            const typename Vec2<T>::type *__restrict__ tw,
                             typename Vec2<T>::type *__restrict__ Z) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char conv_smem[];
@@ -60,7 +60,7 @@ __global__ void k_conv_rows(int nk, int nw, int log2Nw, int Nk, int SSpad, int r
     buf[brev(m, log2Nw)] = v;
   }
   __syncthreads();
-  fft_stages(buf, 1, log2Nw, tw, log2ntw);
+  fft_stages(buf, 1, log2Nw, tw);
   T2 *out = Z + ((size_t)ss * Nk + kk) * Nw;
   for (int m = threadIdx.x; m < Nw; m += blockDim.x) out[m] = buf[m];
 }
@@ -69,8 +69,9 @@ __global__ void k_conv_rows(int nk, int nw, int log2Nw, int Nk, int SSpad, int r
 // (rows >= n_kappa are zero), square, forward again, and store the n_kappa
 // rows needed, row kk taking grid row (Nk - kk) mod Nk.  In place in Z.
 template <typename T>
-__global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC, const typename Vec2<T>::type *__restrict__ tw,
-                            int log2ntw, typename Vec2<T>::type *__restrict__ Z) {
+__global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC,
+                            const typename Vec2<T>::type *__restrict__ tw,
+                            typename Vec2<T>::type *__restrict__ Z) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char conv_smem[];
   T2 *buf = reinterpret_cast<T2 *>(conv_smem);  // [TC][Nk]
@@ -85,7 +86,7 @@ __global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC, const typename V
     buf[c * Nk + brev(r, log2Nk)] = v;
   }
   __syncthreads();
-  fft_stages(buf, TC, log2Nk, tw, log2ntw);
+  fft_stages(buf, TC, log2Nk, tw);
   // square, then back to bit-reversed order for the second transform
   for (int t = threadIdx.x; t < Nk * TC; t += blockDim.x) {
     const int c = t / Nk, r = t - c * Nk, rb = brev(r, log2Nk);
@@ -101,7 +102,7 @@ __global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC, const typename V
     }
   }
   __syncthreads();
-  fft_stages(buf, TC, log2Nk, tw, log2ntw);
+  fft_stages(buf, TC, log2Nk, tw);
   for (int t = threadIdx.x; t < nk * TC; t += blockDim.x) {
     const int r = t / TC, c = t - r * TC;
     base[(size_t)r * Nw + c] = buf[c * Nk + ((Nk - r) & (Nk - 1))];
@@ -118,7 +119,7 @@ __global__ void k_conv_out(int nk, int nw, int log2Nw, int Nk, int SSpad, int ro
                            const T *__restrict__ e, const T *__restrict__ eb,
                            const T *__restrict__ Pk,
                            const T *__restrict__ ck, T cb, T sb,
-                           const typename Vec2<T>::type *__restrict__ tw, int log2ntw,
+                           const typename Vec2<T>::type *__restrict__ tw,
                            const typename Vec2<T>::type *__restrict__ Z,
                            typename Vec2<T>::type *__restrict__ C) {
   using T2 = typename Vec2<T>::type;
@@ -128,7 +129,7 @@ __global__ void k_conv_out(int nk, int nw, int log2Nw, int Nk, int SSpad, int ro
   const T2 *in = Z + ((size_t)ss * Nk + kk) * Nw;
   for (int m = threadIdx.x; m < Nw; m += blockDim.x) buf[brev(m, log2Nw)] = in[m];
   __syncthreads();
-  fft_stages(buf, 1, log2Nw, tw, log2ntw);
+  fft_stages(buf, 1, log2Nw, tw);
   const T inv = (T)1 / ((T)Nk * (T)Nw);
   for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) {
     const T2 cv = buf[(Nw - kw) & (Nw - 1)];

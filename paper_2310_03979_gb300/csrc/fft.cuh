@@ -13,7 +13,9 @@ namespace {
 //   sum_m F[kk][m] e^{2 pi i m mt / nt}, F[kk][kw] = C^+_k,
 //   F[kk][(nt - kw) mod nt] += C^-_k (FFT form, Sec. 4.3).
 // Radix-2 decimation in time in shared memory, input in bit-reversed order,
-// twiddles e^{+2 pi i j / nfft} from a table.
+// twiddles from a table packed by stage: stage s (1-based) reads
+// e^{+2 pi i j / 2^s}, j < 2^(s-1), at twp[2^(s-1) - 1 + j], so the lanes of
+// a warp read consecutive entries in every stage.
 template <typename T2>
 __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
   T2 r;
@@ -43,8 +45,7 @@ __device__ __forceinline__ void bfly(T2 &a, T2 &b, T2 w) {
 // stage at a time, with half the shared-memory round trips and barriers.
 // An odd last stage runs alone.
 template <typename T2>
-__device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ tw,
-                           int log2nfft) {
+__device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ twp) {
   const int n = 1 << log2n;
   int s = 1;
   for (; s + 1 <= log2n; s += 2) {
@@ -58,11 +59,11 @@ __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__
       const int j = g & (half - 1);
       const int i0 = col * n + blk * 4 * half + j;
       T2 e0 = buf[i0], e1 = buf[i0 + half], e2 = buf[i0 + 2 * half], e3 = buf[i0 + 3 * half];
-      const T2 ws = tw[j << (log2nfft - s)];
+      const T2 ws = twp[half - 1 + j];
       bfly(e0, e1, ws);
       bfly(e2, e3, ws);
-      bfly(e0, e2, tw[j << (log2nfft - s - 1)]);
-      bfly(e1, e3, tw[(j + half) << (log2nfft - s - 1)]);
+      bfly(e0, e2, twp[2 * half - 1 + j]);
+      bfly(e1, e3, twp[3 * half - 1 + j]);
       buf[i0] = e0;
       buf[i0 + half] = e1;
       buf[i0 + 2 * half] = e2;
@@ -81,7 +82,7 @@ __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__
       const int j = bf & (half - 1);
       const int i0 = col * n + grp * 2 * half + j;
       T2 a = buf[i0], b = buf[i0 + half];
-      bfly(a, b, tw[j << (log2nfft - s)]);
+      bfly(a, b, twp[half - 1 + j]);
       buf[i0] = a;
       buf[i0 + half] = b;
     }
@@ -94,7 +95,7 @@ __device__ __forceinline__ int brev(int m, int log2n) {
 }
 
 template <typename T2>
-__global__ void k_fft_t(int nk, int nw, int nt, int log2nt, int log2nfft,
+__global__ void k_fft_t(int nk, int nw, int nt, int log2nt,
                         const T2 *__restrict__ C, const T2 *__restrict__ tw, T2 *__restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *buf = reinterpret_cast<T2 *>(smem_raw);
@@ -118,13 +119,13 @@ __global__ void k_fft_t(int nk, int nw, int nt, int log2nt, int log2nfft,
     buf[pos] = v;
   }
   __syncthreads();
-  fft_stages(buf, 1, log2nt, tw, log2nfft);
+  fft_stages(buf, 1, log2nt, tw);
   T2 *Hrow = H + ((size_t)n * nk + kk) * nt;
   for (int m = threadIdx.x; m < nt; m += blockDim.x) Hrow[m] = buf[m];
 }
 
 template <typename T, typename T2>
-__global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int log2nfft, int TC,
+__global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int TC,
                         const T2 *__restrict__ H, const T2 *__restrict__ tw, T *__restrict__ u) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *buf = reinterpret_cast<T2 *>(smem_raw);
@@ -140,7 +141,7 @@ __global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int log2nfft, int TC
     buf[c * nx + brev(kk, log2nx)] = Hn[(size_t)kk * nt + c];
   }
   __syncthreads();
-  fft_stages(buf, TC, log2nx, tw, log2nfft);
+  fft_stages(buf, TC, log2nx, tw);
   T *un = u + (size_t)n * nx * nt + mt0;
   for (int idx = threadIdx.x; idx < nx * TC; idx += blockDim.x) {
     const int mx = idx / TC, c = idx - mx * TC;

@@ -65,7 +65,6 @@ struct DeviceGuard {
 // caller (n * nk * nt entries).
 template <typename T, typename T2>
 int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
-  const int log2nfft = ilog2_exact(p->nfft);
   const size_t e2 = sizeof(T2);
   const size_t smem_t = (size_t)p->nt * e2;
   int TC = 16;
@@ -74,11 +73,11 @@ int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
   const int lim = 200 * 1024;
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt,
-                                                          log2nfft, C, (const T2 *)p->tw, H);
+  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt, C,
+                                                          (const T2 *)p->tw, H);
   SRM3_CUDA(cudaGetLastError());
   k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, p->stream>>>(
-      p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, H, (const T2 *)p->tw, out);
+      p->nk, p->nx, p->nt, p->log2nx, TC, H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }

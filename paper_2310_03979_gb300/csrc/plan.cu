@@ -149,16 +149,27 @@ __global__ void k_dup2(int len, const float *__restrict__ in, float2 *__restrict
   if (i < len) out[i] = make_float2(in[i], in[i]);
 }
 
+// Twiddles of the radix-2 stages for every transform length up to n = 2^log2n,
+// packed by stage: entry 2^(s-1) - 1 + j holds e^{+2 pi i m / n} with
+// m = j 2^(log2n - s) (= e^{+2 pi i j / 2^s}), j < 2^(s-1), s = 1..log2n; the
+// last entry is unused.
 template <typename T2>
-__global__ void k_twiddles(int n, T2 *tw) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  double s, c;
-  sincospi(2.0 * (double)j / (double)n, &s, &c);
+__global__ void k_twiddles(int n, int log2n, T2 *tw) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n) return;
   T2 v;
-  v.x = c;
-  v.y = s;
-  tw[j] = v;
+  v.x = 1;
+  v.y = 0;
+  if (idx < n - 1) {
+    const int s = 32 - __clz(idx + 1);  // stage of this entry
+    const int j = idx + 1 - (1 << (s - 1));
+    const int m = j << (log2n - s);
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+    v.x = cs;
+    v.y = sn;
+  }
+  tw[idx] = v;
 }
 
 // W table, tile-major: for tile (kk, kw0): rows a = 0..kk/2, then r < R,
@@ -853,10 +864,12 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     SRM3_CUDA(cudaMalloc(&p->ps_err, sizeof(int)));
     SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
     k_dup2<<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, (const float *)p->Ews, p->Ew2);
-    k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, (float2 *)p->tw);
+    k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
+                                                          (float2 *)p->tw);
     if (p->sep) {
       SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2)));
       k_twiddles<float2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
+                                                                        p->log2ntwc,
                                                                         (float2 *)p->tw_conv);
     }
   } else {
@@ -866,10 +879,12 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_env<double><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (double *)p->Ek);
     k_env<double><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off,
                                                        p->sigma_g * nw, (double *)p->Ews);
-    k_twiddles<double2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, (double2 *)p->tw);
+    k_twiddles<double2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
+                                                           (double2 *)p->tw);
     if (p->sep) {
       SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2)));
       k_twiddles<double2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
+                                                                         p->log2ntwc,
                                                                          (double2 *)p->tw_conv);
     }
   }

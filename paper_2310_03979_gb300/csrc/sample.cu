@@ -319,14 +319,14 @@ static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y
   SRM3_CUDA(cudaFuncSetAttribute(k_conv_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)srow));
   k_conv_rows<T><<<dim3(p->nk, SS), 256, srow, st>>>(p->nk, p->nw, p->log2cNw, p->cNk, sp,
-                                                      p->rowstride, y, e, tw, p->log2ntwc, Z);
+                                                      p->rowstride, y, e, tw, Z);
   k_conv_cols<T><<<dim3(p->cNw / TC, SS), 256, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
-                                                            p->log2ntwc, Z);
+                                                            Z);
   const T *eb = std::is_same<T, float>::value ? (const T *)p->env_b32 : (const T *)p->env_b;
   k_conv_out<T><<<dim3(p->nk, SS), 256, srow, st>>>(
       p->nk, p->nw, p->log2cNw, p->cNk, sp, p->rowstride, y, (const T2 *)y0, e, eb,
-      (const T *)p->Pk, (const T *)p->ck, (T)std::cos(p->beta), (T)std::sin(p->beta), tw,
-      p->log2ntwc, Z, (T2 *)C_out);
+      (const T *)p->Pk, (const T *)p->ck, (T)std::cos(p->beta), (T)std::sin(p->beta), tw, Z,
+      (T2 *)C_out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -358,7 +358,6 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
 
 template <typename T, typename T2>
 static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2 *H) {
-  const int log2nfft = ilog2_exact(p->nfft);
   const size_t e2 = sizeof(T2);
   const size_t smem_t = (size_t)p->nt * e2;
   int TC = 16;
@@ -367,12 +366,11 @@ static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *
   const int lim = 200 * 1024;
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt,
-                                                          log2nfft, C, (const T2 *)p->tw,
-                                                          H);
+  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt, C,
+                                                          (const T2 *)p->tw, H);
   SRM3_CUDA(cudaGetLastError());
   k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, st>>>(
-      p->nk, p->nx, p->nt, p->log2nx, log2nfft, TC, (const T2 *)H, (const T2 *)p->tw, out);
+      p->nk, p->nx, p->nt, p->log2nx, TC, (const T2 *)H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
