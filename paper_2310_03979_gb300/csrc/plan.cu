@@ -244,6 +244,36 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
   SRM3_CUDA(cudaMalloc(&p->rec_max, kPlanes * sizeof(unsigned long long)));
+  // separable envelope: the FFT form of the bulk when its grids fit the
+  // pass's shared memory (else the direct bulk, as for any envelope)
+  if (p->sep) {
+    int log2Lmax = 0;
+    for (int D = kRecBL; D < nlev; D += kRecBL)
+      log2Lmax = std::max(log2Lmax, ilog2_exact(kRecBL) + __builtin_ctz(D / kRecBL));
+    const int L2max = 2 << log2Lmax;
+    int log2Nc = 1;
+    while ((1 << log2Nc) < nk + std::min(L2max, nk) - 1) ++log2Nc;
+    const int cap = kRecSmem / (int)sizeof(double2);  // FP64 is the tighter case
+    if (nlev > kRecBL && (1 << log2Nc) <= cap && L2max <= cap) {
+      const int ntw = std::max(1 << log2Nc, L2max);
+      p->rec_fft = true;
+      p->rec_log2Nc = log2Nc;
+      SRM3_CUDA(cudaMalloc(&p->rec_z, (size_t)L2max * ((size_t)1 << log2Nc) *
+                                          std::max(kPlanes * sizeof(float2), sizeof(double2))));
+      SRM3_CUDA(cudaMalloc(&p->tw_rec32, ntw * sizeof(float2)));
+      SRM3_CUDA(cudaMalloc(&p->tw_rec64, ntw * sizeof(double2)));
+      k_twiddles<float2><<<cdiv(ntw, 256), 256, 0, st>>>(ntw, ilog2_exact(ntw),
+                                                         (float2 *)p->tw_rec32);
+      k_twiddles<double2><<<cdiv(ntw, 256), 256, 0, st>>>(ntw, ilog2_exact(ntw),
+                                                          (double2 *)p->tw_rec64);
+      SRM3_CUDA(cudaGetLastError());
+    }
+  }
+  const int rec_smem = p->rec_fft ? kRecSmem : 0;
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
   // sum of S (the exact variance), once: the plane-0 results of this
   // reduction are not used
   SRM3_CUDA(cudaMemsetAsync(p->sb2, 0, (size_t)nk * nw * sizeof(double), st));
@@ -261,11 +291,11 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   int b64 = 0, b64x3 = 0, b32 = 0;
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1>,
-                                                          kRecThreads, 0));
+                                                          kRecThreads, rec_smem));
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64x3, k_rec_pass<double, 3>,
                                                           kRecThreads, 0));
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes>,
-                                                          kRecThreads, 0));
+                                                          kRecThreads, rec_smem));
   if (b64 < 1 || b64x3 < 1 || b32 < 1)
     return fail(SRM3_ERR_CUDA, "recursion kernel cannot be resident");
   SRM3_CUDA(cudaMalloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double)));
@@ -307,11 +337,16 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.bar = p->rec_bar;
   A.abort = p->err + kPlanes;
   A.maxb = p->rec_max;
+  A.zr = p->rec_fft ? p->rec_z : nullptr;
+  A.twr = fp64 ? p->tw_rec64 : p->tw_rec32;
+  A.log2Nc = p->rec_log2Nc;
+  A.zcap = kRecSmem / (fp64 ? (int)sizeof(double2) : (int)sizeof(float2));
+  const int smem = p->rec_fft ? kRecSmem : 0;
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
   if (fp64 && M == 1)
     SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 1>, p->rec_grid64,
-                                          kRecThreads, args, 0, st));
+                                          kRecThreads, args, smem, st));
   else if (fp64 && M == 3)
     SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 3>, p->rec_grid64,
                                           kRecThreads, args, 0, st));
@@ -319,7 +354,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
     return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes 1 or 3 planes");
   else
     SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<float, kPlanes>,
-                                          p->rec_grid32, kRecThreads, args, 0, st));
+                                          p->rec_grid32, kRecThreads, args, smem, st));
   SRM3_CUDA(cudaGetLastError());
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, M * sizeof(unsigned long long),
@@ -906,7 +941,7 @@ void free_plan(srm3_plan *p) {
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
                  p->Ew2,    p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
-                 p->tw_conv, p->Zc,
+                 p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr};
   for (void *d : dev)

@@ -4,12 +4,14 @@
 // Included by plan.cu only.
 #pragma once
 
+#include "fft.cuh"
 #include "srm3_internal.cuh"
 
 namespace srm3 {
 
 constexpr int kRecThreads = 512;  // one CTA per SM
 constexpr int kRecBL = 16;        // levels per block of the blocked pass
+constexpr int kRecSmem = 64 << 10;  // dynamic shared memory of a pass in FFT form
 
 struct RecArgs {
   int nk, nw, nlev;
@@ -28,6 +30,13 @@ struct RecArgs {
   const double *e2;   // a^2: h = a^2 q
   const double *e2k;  // b^2: the factor of sum_b2(k)
   double *qout;
+  // separable envelope with the FFT form of the bulk (else NULL): the
+  // product grid [M][2 L][Nc] of complex T, the packed twiddles (complex T)
+  // for every length up to max(Nc, 2 L), log2 Nc, and the complex T elements
+  // of dynamic shared memory
+  void *zr;
+  const void *twr;
+  int log2Nc, zcap;
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
   int *abort;           // barrier wait timed out
@@ -131,7 +140,11 @@ __device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, in
   T *q = static_cast<T *>(A.q);
   const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;    // a_k^2
   const T bk2 = A.e2k ? (T)A.e2k[k] : (T)1;  // b_k^2
-  const T s2 = (T)A.scal[m] * bk2 * t;
+  // t >= 0 (a sum of non-negative terms) up to the rounding of the FFT form,
+  // which can leave a small negative value, of the order of the rounding of
+  // the largest sums, where every term is zero; a NaN passes through
+  const T s2r = (T)A.scal[m] * bk2 * t;
+  const T s2 = s2r < (T)0 ? (T)0 : s2r;
   A.sb2[m * A.nl + k] = (double)s2;
   // non-negative doubles order as their bit patterns
   atomicMax(A.maxb + m, (unsigned long long)__double_as_longlong((double)s2));
@@ -282,7 +295,13 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   // the end, which keeps one memory round trip off the level's critical path
   const double Sk = A.S[k];
   // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
-  const T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
+  T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
+  if (A.zr && lane < M && ((kk | kw) & 1) == 0) {
+    // FFT form: the bulk holds half the ordered pairs; the pair {k/2, k/2}
+    // enters the unordered sum once
+    const T hh = static_cast<const T *>(A.q)[((long long)(kk >> 1) * A.nw + (kw >> 1)) * M + lane];
+    bulk += (T)0.5 * hh * hh;
+  }
   const int t = kk + kw - D;
   const int nlow = t * (t + 3) / 2;
   T acc[M];
@@ -333,6 +352,116 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   }
 }
 
+// ---- separable envelope: the bulk as an online FFT self-convolution ----
+// With g = a_i a_j b_k every pair term of a plane is h_i h_j (h = a^2 q), and
+// i + j = k is d_i + d_j = d_k with kk_i + kk_j = kk_k, so the pairs of the
+// points of a level form a 2-D self-convolution of h over (level, kk).  A
+// divide and conquer over levels (leaves of kRecBL levels, sizes 2L = 2 BL,
+// 4 BL, ...) supplies it online: before leaf [D, D + BL) the product of the
+// node with mid D (L = BL 2^{v2(D / BL)}, l0 = D - L) adds to the levels
+// [D, D + L) every ordered pair (d1, d2) with d1 in [l0, D) and d2 in
+// [0, 2L) in either order (l0 > 0; then 2L <= l0), or with both in [0, L)
+// (l0 = 0).  When leaf D starts, every ordered pair with both levels below D
+// has been added exactly once (the pair's larger level and d first fall in
+// different halves of one node, which adds it), so the leaf's bulk is half
+// the ordered sum plus half the diagonal term h_{k/2}^2, and the fringe adds
+// the pairs with a part in [D, d) as before.
+//
+// A product on a 2L x Nc grid over (level offset o, kk):
+//   z[o][kk] = h(l0 + o, kk) [o < L] + i h(o, kk)   (l0 > 0),
+//   z[o][kk] = h(o, kk) [o < L]                      (l0 = 0),
+// so that Im (z * z) = 2 A * B and Re (z * z) = A * A; z * z comes from one
+// transform direction, F(F(z)^2)[-o, -kk] = 2L Nc (z * z)[o, kk] (cyclic).
+// The cyclic length 2L in o suffices: the wanted offsets [L, 2L) could only
+// meet aliases from [3L, 4L), beyond the support [0, 3L - 1); Nc >= nk +
+// min(2L, nk) - 1 keeps kk free of aliases.  Three phases, a grid barrier
+// after each: rows along kk; columns along o, squared, along o again and
+// stored at negated o; rows along kk again, read at negated kk, added to
+// acc.  Returns false when a barrier gave up.
+template <typename T, int M>
+__device__ __forceinline__ T sep_h(const RecArgs &A, int d, int kk, int m) {
+  const int kw = d - kk;
+  if (d == 0 || kk >= A.nk || kw < 0 || kw >= A.nw) return (T)0;
+  return static_cast<const T *>(A.q)[((long long)kk * A.nw + kw) * M + m];
+}
+
+template <typename T, int M>
+__device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g,
+                            typename Vec2<T>::type *buf) {
+  using T2 = typename Vec2<T>::type;
+  const int L = 1 << log2L, L2 = 2 * L, Nc = 1 << A.log2Nc;
+  const unsigned int nb = gridDim.x;
+  T2 *Z = static_cast<T2 *>(A.zr);
+  const T2 *tw = static_cast<const T2 *>(A.twr);
+  // rows: z along kk
+  for (int it = blockIdx.x; it < L2 * M; it += gridDim.x) {
+    const int m = it / L2, o = it - m * L2;
+    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) {
+      T2 v;
+      v.x = o < L ? sep_h<T, M>(A, l0 + o, kk, m) : (T)0;
+      v.y = l0 > 0 ? sep_h<T, M>(A, o, kk, m) : (T)0;
+      buf[brev(kk, A.log2Nc)] = v;
+    }
+    __syncthreads();
+    fft_stages(buf, 1, A.log2Nc, tw);
+    T2 *row = Z + ((size_t)m * L2 + o) * Nc;
+    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) row[kk] = buf[kk];
+    __syncthreads();
+  }
+  if (!grid_barrier(A.bar, A.abort, nb * g++)) return false;
+  // columns: along o, square, along o, store at negated o (rows [L, 2L))
+  const int TC = min(Nc, A.zcap >> (log2L + 1)), ng = Nc / TC;
+  for (int it = blockIdx.x; it < ng * M; it += gridDim.x) {
+    const int m = it / ng, c0 = (it - m * ng) * TC;
+    T2 *base = Z + (size_t)m * L2 * Nc + c0;
+    for (int t = threadIdx.x; t < L2 * TC; t += blockDim.x) {
+      const int r = t / TC, c = t - r * TC;
+      buf[c * L2 + brev(r, log2L + 1)] = base[(size_t)r * Nc + c];
+    }
+    __syncthreads();
+    fft_stages(buf, TC, log2L + 1, tw);
+    for (int t = threadIdx.x; t < L2 * TC; t += blockDim.x) {
+      const int c = t >> (log2L + 1), r = t & (L2 - 1), rb = brev(r, log2L + 1);
+      if (r <= rb) {
+        const T2 a = buf[c * L2 + r], b = buf[c * L2 + rb];
+        T2 a2, b2;
+        a2.x = a.x * a.x - a.y * a.y;
+        a2.y = 2 * a.x * a.y;
+        b2.x = b.x * b.x - b.y * b.y;
+        b2.y = 2 * b.x * b.y;
+        buf[c * L2 + r] = b2;
+        buf[c * L2 + rb] = a2;
+      }
+    }
+    __syncthreads();
+    fft_stages(buf, TC, log2L + 1, tw);
+    for (int t = threadIdx.x; t < L * TC; t += blockDim.x) {
+      const int r = L + t / TC, c = t % TC;
+      base[(size_t)r * Nc + c] = buf[c * L2 + ((L2 - r) & (L2 - 1))];
+    }
+    __syncthreads();
+  }
+  if (!grid_barrier(A.bar, A.abort, nb * g++)) return false;
+  // rows again: along kk, read at negated kk, half the ordered sum into acc
+  const T inv = (T)0.5 / ((T)L2 * (T)Nc);
+  T *ac = static_cast<T *>(A.acc);
+  for (int it = blockIdx.x; it < L * M; it += gridDim.x) {
+    const int m = it / L, o = L + (it - m * L), d = l0 + o;
+    if (d >= A.nlev) continue;  // uniform over the CTA
+    const T2 *row = Z + ((size_t)m * L2 + o) * Nc;
+    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) buf[brev(kk, A.log2Nc)] = row[kk];
+    __syncthreads();
+    fft_stages(buf, 1, A.log2Nc, tw);
+    const int kk0 = max(0, d - A.nw + 1), kk1 = min(d, A.nk - 1);
+    for (int kk = kk0 + threadIdx.x; kk <= kk1; kk += blockDim.x) {
+      const T2 v = buf[(Nc - kk) & (Nc - 1)];
+      ac[((long long)kk * A.nw + (d - kk)) * M + m] += (l0 > 0 ? v.y : v.x) * inv;
+    }
+    __syncthreads();
+  }
+  return grid_barrier(A.bar, A.abort, nb * g++);
+}
+
 // One recursion pass.  Levels d = kk + kw: every part of a pair of Pi(k)
 // lies on a lower level.  Each pair {i, j} of a point is assigned to the
 // higher of its two levels, M(i, j) in [ceil(d/2), d).  The pass runs:
@@ -371,21 +500,29 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
   for (int D = kRecBL, ph = 1; D < A.nlev; D += kRecBL, ++ph) {
-    // bulk: warps take points in turn from the phase's ticket counter
-    // (the next ticket is drawn while the current point is summed)
-    const int pb = A.pt_off[D], pe = A.pt_off[min(2 * D, A.nlev)];
-    unsigned int *tk = A.bar + ph;
-    int t = 0;
-    if (lane == 0) t = (int)atomicAdd(tk, 1u);
-    t = __shfl_sync(0xffffffffu, t, 0);
-    while (pb + t < pe) {
-      int tn = 0;
-      if (lane == 0) tn = (int)atomicAdd(tk, 1u);
-      const int2 pt = A.pts[pb + t];
-      point_bulk<T, M>(A, pt.x, pt.y, D, lane);
-      t = __shfl_sync(0xffffffffu, tn, 0);
+    if (A.zr) {  // separable envelope: the bulk by one FFT product
+      extern __shared__ __align__(16) unsigned char rec_smem[];
+      const int log2L = (31 - __clz(kRecBL)) + (__ffs(D / kRecBL) - 1);
+      if (!sep_product<T, M>(A, D - (1 << log2L), log2L, g,
+                             reinterpret_cast<typename Vec2<T>::type *>(rec_smem)))
+        return;
+    } else {
+      // bulk: warps take points in turn from the phase's ticket counter
+      // (the next ticket is drawn while the current point is summed)
+      const int pb = A.pt_off[D], pe = A.pt_off[min(2 * D, A.nlev)];
+      unsigned int *tk = A.bar + ph;
+      int t = 0;
+      if (lane == 0) t = (int)atomicAdd(tk, 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      while (pb + t < pe) {
+        int tn = 0;
+        if (lane == 0) tn = (int)atomicAdd(tk, 1u);
+        const int2 pt = A.pts[pb + t];
+        point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+        t = __shfl_sync(0xffffffffu, tn, 0);
+      }
+      if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
-    if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     const int dend = min(D + kRecBL, A.nlev);
     for (int d = D; d < dend; ++d) {
       for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {

@@ -159,6 +159,13 @@ struct srm3_plan {
   int rec_bar_words = 0;
   unsigned long long *rec_max = nullptr;  // per-plane max sum_b2 of a pass (bits)
   double sumS = 0.0;                      // sum of S over the lattice
+  // separable envelope: the bulk of a pass as an online FFT self-convolution
+  // (rec_fft), its product grid (room for kPlanes FP32 planes or one FP64
+  // plane of 2 Lmax x Nc complex values) and packed twiddles in both
+  // precisions
+  bool rec_fft = false;
+  int rec_log2Nc = 0;
+  void *rec_z = nullptr, *tw_rec32 = nullptr, *tw_rec64 = nullptr;
   int maxpts = 0, rec_grid64 = 0, rec_grid32 = 0;
   double *h_pinned = nullptr;  // pinned host scalars
   int *h_err = nullptr;        // pinned host error words

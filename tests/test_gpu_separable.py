@@ -66,16 +66,20 @@ def test_separable_plan_tables_and_eps(oracle_lib, precision, envelope):
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=rel, atol=1e-15)
 
 
-@pytest.mark.parametrize("nk,nw", [(24, 37), (40, 70), (1, 9), (9, 1)])
+@pytest.mark.parametrize("nk,nw", [(24, 37), (40, 70), (1, 9), (9, 1), (100, 180)])
 def test_separable_recursion_at_fixed_eps(oracle_lib, nk, nw):
+    """The bulk of a separable pass is an online FFT self-convolution of h
+    (levels 16 and up); its rounding is bounded norm-wise, |ds_k| <~ u
+    log2(N) sum_i h_i^2, about 1e-14 of the largest pair sum here, hence an
+    absolute term of 1e-13 max(sum_b2) beside the relative one."""
     pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
     wl = sep_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw))
-    eps = 0.2 if nk > 1 and nw > 1 else 0.5
+    eps = 1.5 if nk > 1 and nw > 1 else 0.5  # max sum_b2 0.2 - 0.3 on the 2-D lattices
     op = oracle_plan(wl, eps=eps)
     with srm3.Plan.create(wl, eps=eps) as p:
         _, q, sb2 = p.tables()
-    np.testing.assert_allclose(q, op.q, rtol=2e-14)
-    np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
+    np.testing.assert_allclose(q, op.q, rtol=1e-13)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=1e-13, atol=1e-13 * op.sum_b2.max())
 
 
 @pytest.mark.parametrize("precision,nk,nw,beta,envelope", [
