@@ -44,14 +44,15 @@ struct RecArgs {
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident): one
-// arrival counter bar[0], zeroed on the stream before each launch.  Thread 0
-// of every CTA adds 1 after a fence and polls until the counter reaches
-// `target` (the barrier's number within the launch x gridDim.x); the fences
-// on both sides order every CTA's writes before the barrier with every read
-// after it.  Waits are bounded: past ~2^22 polls a CTA raises *abort and
-// sets kBarAbort in the counter, which every poll sees at once (the counter
-// then exceeds any target), so every CTA returns false from this or its next
-// barrier without a second memory read on the normal path.
+// arrival counter bar[0], zeroed on the stream before each launch.  After a
+// CTA barrier, thread 0 of every CTA adds 1 with release semantics at GPU
+// scope (ordering every write the CTA made before it) and polls with acquire
+// loads until the counter reaches `target` (the barrier's number within the
+// launch x gridDim.x), which orders every read after the barrier with every
+// CTA's writes before it.  Waits are bounded: past ~2^22 polls a CTA raises
+// *abort and sets kBarAbort in the counter, which every poll sees at once
+// (the counter then exceeds any target), so every CTA returns false from
+// this or its next barrier without a second memory read on the normal path.
 constexpr unsigned int kBarAbort = 1u << 30;
 
 __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsigned int target,
@@ -59,13 +60,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsi
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *cnt = bar;
-    __threadfence();
-    atomicAdd(bar, 1u);
+    unsigned int v;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(bar) : "memory");
     bool ok = true;
     long long spins = 0;
-    unsigned int v;
-    while ((v = *cnt) < target) {
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
       if (++spins > limit) {
         ok = false;
         break;
@@ -76,7 +77,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsi
       atomicOr(bar, kBarAbort);
       atomicExch(abort, 1);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -396,6 +396,11 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
   // rows: z along kk
   for (int it = blockIdx.x; it < L2 * M; it += gridDim.x) {
     const int m = it / L2, o = it - m * L2;
+    T2 *row = Z + ((size_t)m * L2 + o) * Nc;
+    if (l0 == 0 && o >= L) {  // a zero row (uniform over the CTA)
+      for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) row[kk] = T2{};
+      continue;
+    }
     for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) {
       T2 v;
       v.x = o < L ? sep_h<T, M>(A, l0 + o, kk, m) : (T)0;
@@ -404,13 +409,16 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
     }
     __syncthreads();
     fft_stages(buf, 1, A.log2Nc, tw);
-    T2 *row = Z + ((size_t)m * L2 + o) * Nc;
     for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) row[kk] = buf[kk];
     __syncthreads();
   }
   if (!grid_barrier(A.bar, A.abort, nb * g++)) return false;
-  // columns: along o, square, along o, store at negated o (rows [L, 2L))
-  const int TC = min(Nc, A.zcap >> (log2L + 1)), ng = Nc / TC;
+  // columns: along o, square, along o, store at negated o (rows [L, 2L)),
+  // TC columns per CTA: enough groups for every CTA where there are columns
+  // for them (the FP64 pipe of one SM would otherwise carry a whole product)
+  int TC = min(Nc, A.zcap >> (log2L + 1));
+  while (TC > 1 && (Nc / TC) * M < (int)gridDim.x) TC >>= 1;
+  const int ng = Nc / TC;
   for (int it = blockIdx.x; it < ng * M; it += gridDim.x) {
     const int m = it / ng, c0 = (it - m * ng) * TC;
     T2 *base = Z + (size_t)m * L2 * Nc + c0;
@@ -491,12 +499,14 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
        i += (long long)gridDim.x * blockDim.x)
     ac[i] = (T)0;
   if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
+  // the points of level d are kk = lo .. hi, lo = max(0, d - nw + 1),
+  // hi = min(d, nk - 1), in the order of the level list; their coordinates
+  // are formed here rather than loaded, which keeps a memory round trip off
+  // every level's critical path
   const int d0 = min(kRecBL, A.nlev);
   for (int d = 0; d < d0; ++d) {
-    for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
-      const int2 pt = A.pts[p];
-      point_direct<T, M>(A, pt.x, pt.y, lane);
-    }
+    const int lo = max(0, d - A.nw + 1), n = min(d, A.nk - 1) - lo + 1;
+    for (int i = gw; i < n; i += nwarps) point_direct<T, M>(A, lo + i, d - lo - i, lane);
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
   for (int D = kRecBL, ph = 1; D < A.nlev; D += kRecBL, ++ph) {
@@ -525,10 +535,8 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     }
     const int dend = min(D + kRecBL, A.nlev);
     for (int d = D; d < dend; ++d) {
-      for (int p = A.pt_off[d] + gw; p < A.pt_off[d + 1]; p += nwarps) {
-        const int2 pt = A.pts[p];
-        point_fringe<T, M>(A, pt.x, pt.y, D, lane);
-      }
+      const int lo = max(0, d - A.nw + 1), n = min(d, A.nk - 1) - lo + 1;
+      for (int i = gw; i < n; i += nwarps) point_fringe<T, M>(A, lo + i, d - lo - i, D, lane);
       if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
   }
