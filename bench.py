@@ -50,7 +50,7 @@ def _args():
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
     ap.add_argument("--config", default="bridge",
                     choices=["bridge", "bridge_rc", "bridge_sep", "large", "tiny", "prof128",
-                             "uneven", "serve"],
+                             "uneven", "serve", "paper_bridge"],
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -458,10 +458,148 @@ def run_serve(args):
     return 0
 
 
+def run_paper_bridge(args):
+    """The bridge wind-field experiment of Sec. 5/6: plan build, 1000 samples
+    in batches of 50 and their ensemble statistics (moments, histogram) on
+    the device; the fields never leave HBM.  The 2nd-order (eps = 0)
+    experiment on the same seeds and the exact moments are taken once,
+    outside the timed region, for the statistics table."""
+    import numpy as np
+    import torch
+    from paper_2310_03979_gb300 import srm3
+    from paper_2310_03979_gb300 import workloads as Wl
+
+    wl = Wl.PAPER_BRIDGE
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    n, B, nbins = wl.n_samples, 50, 240
+    seeds = list(wl.seeds)
+    out = torch.empty((B, wl.n_x, wl.n_t), dtype=torch.float32, device="cuda")
+    probe = srm3.Plan.create(wl, stream=sptr)
+    var_exact, m3_exact = probe.moments()
+    probe.destroy()
+    sig = math.sqrt(var_exact)
+    st = srm3.Stats(nbins, -6 * sig, 6 * sig, stream=sptr)
+    stats_ms = []
+
+    def experiment(eps=None, timed_stats=False):
+        st.reset()
+        plan = srm3.Plan.create(wl, stream=sptr, eps=eps)
+        srm3.enable_timing(plan.handle, True)
+        sms = 0.0
+        evs = []
+        for b0 in range(0, n, B):
+            s = seeds[b0:b0 + B]
+            srm3.sample(plan.handle, s, len(s), out.data_ptr())
+            if timed_stats:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st.add(out[:len(s)])
+                e1.record(stream)
+                evs.append((e0, e1))
+            else:
+                st.add(out[:len(s)])
+        r = st.read()
+        for e0, e1 in evs:
+            sms += e0.elapsed_time(e1)
+        t = srm3.get_timings(plan.handle)
+        info = plan.info()
+        plan.destroy()
+        return r, t, info, sms
+
+    for _ in range(args.warmup):
+        experiment()
+    torch.cuda.synchronize()
+    gpu_index = 0
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if cvd.split(",")[0].strip().isdigit():
+        gpu_index = int(cvd.split(",")[0])
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    ev0.record(stream)
+    recs = [experiment() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - w0) / args.steps
+    clocks = sampler.stop()
+    ms_per_step = ev0.elapsed_time(ev1) / args.steps
+    r3, t3, info, _ = recs[-1]
+    # stage split and the stats kernel's own time (one more, untimed run)
+    _, _, _, s_ms = experiment(timed_stats=True)
+    r2 = experiment(eps=0.0)[0]
+    pairs = wl.pairs()
+    value = 2 * pairs * n / (ms_per_step * 1e-3)
+    peaks = _peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    stage_ms = {"plan": info.plan_ms, "recursion": t3.recursion_ms, "phases": t3.phases_ms,
+                "pairsum_fft_conv": t3.pairsum_ms, "transform": t3.transform_ms,
+                "stats": s_ms}
+    # algorithmic HBM bytes per sample: transform (C in, H out and in, u out),
+    # statistics (u in)
+    cNw = 1 << max(1, (2 * wl.n_omega - 2).bit_length())
+    per = {"transform": 2 * wl.n_kappa * wl.n_omega * 8 + 2 * wl.n_kappa * wl.n_t * 8
+                        + wl.n_x * wl.n_t * 4,
+           "stats": wl.n_x * wl.n_t * 4,
+           # as _conv_roofline: per sheet-sample y twice, C once, padded rows 4x
+           "pairsum_fft_conv": 2 * 2 * 4 * (3 * wl.n_kappa * wl.n_omega + 4 * wl.n_kappa * cNw)}
+    roofs = {}
+    for k, b in per.items():
+        if stage_ms[k] > 0:
+            gbs = b * n / (stage_ms[k] * 1e-3) / 1e9
+            roofs[k] = {"achieved_gbs": gbs, "frac": gbs / hbm, "bytes_per_sample": b}
+    dom = max(per, key=lambda k: stage_ms[k])
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-terms/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "n_kappa": wl.n_kappa, "n_omega": wl.n_omega,
+                   "n_x": wl.n_x, "n_t": wl.n_t, "samples_per_step": n, "batch": B,
+                   "l2": "inputs larger than L2 (fields 400 MB per batch)",
+                   "step": "plan build + 1000 samples + device statistics"},
+        "samples_per_s": n / (ms_per_step * 1e-3),
+        "wall_ms_per_step": wall * 1e3,
+        "stages_ms_last_step": stage_ms,
+        "roofline": {"bound": "hbm", "achieved": roofs[dom]["achieved_gbs"], "peak": hbm,
+                     "unit": "GB/s", "frac": roofs[dom]["frac"], "traffic": None,
+                     "kernel": dom, "per_unit": f"{per[dom]} B per sample",
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"},
+        "stage_rooflines": roofs,
+        "statistics": {
+            "third_order": {k: r3[k] for k in ("mean", "variance", "skewness", "kurtosis")},
+            "second_order": {k: r2[k] for k in ("mean", "variance", "skewness", "kurtosis")},
+            "exact": {"mean": 0.0, "variance": var_exact,
+                      "skewness": m3_exact / var_exact ** 1.5},
+            "values": r3["count"], "histogram_bins": nbins, "range_sigma": 6},
+        # per step: spectrum 1, envelope tables 3, sum of S 1, recursion
+        # passes, sampling tables 5, conv twiddles 1; per batch of 50 (one
+        # sampling chunk): phases, three FFT self-convolution passes, two
+        # output FFT stages, statistics pass and merge
+        "gpu_launches": args.steps * (1 + 3 + 1 + info.root_passes + info.root_passes_fp32
+                                      + 5 + 1 + 8 * math.ceil(n / B)),
+        "clocks": clocks,
+        "eps": info.eps, "max_sum_b2": info.max_sum_b2,
+        "e2e": {"value": 2 * pairs * n / wall, "unit": "pair-terms/s",
+                "h2d_bytes_per_step": 8 * n,
+                "d2h_bytes_per_step": 8 * (nbins + 6),
+                "ms_per_step": wall * 1e3,
+                "note": "wall clock of the experiment through the public API; only "
+                        "seeds go in and the statistics come out"},
+    }
+    st.destroy()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = _args()
     if args.config == "uneven" and args.impl != "reference":
         return run_uneven(args)
+    if args.config == "paper_bridge" and args.impl != "reference":
+        return run_paper_bridge(args)
     if args.config == "serve" and args.impl != "reference":
         return run_serve(args)
     rank = int(os.environ.get("RANK", "0"))

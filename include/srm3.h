@@ -375,6 +375,56 @@ int srm3_batch_pairsum_ms(srm3_batch *b, double *ms);
 /* Free the batch (not its plans).  NULL is a no-op.  No run may be in flight. */
 void srm3_batch_destroy(srm3_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Ensemble statistics of sampled fields (Sec. 6: sample mean, variance and
+ * skewness of the simulated waves against their targets, and the empirical
+ * PDF and CDF).  A running accumulator on the device, fed with any number of
+ * sampled batches (srm3_sample output, or any device array), read at the end:
+ *   power sums  sum (u - shift)^p, p = 1..4, in FP64 (FP32 input is summed
+ *               in FP32 over runs of 16 values, then in FP64);
+ *   histogram   nbins equal bins over [lo, hi): bin floor((u - lo) *
+ *               (nbins / (hi - lo))), evaluated in the input's precision
+ *               with each operation rounded once; values below lo and at or
+ *               above hi (or NaN) are counted apart.
+ * Deterministic: the same values given in the same calls give bit-identical
+ * sums and counts on a given device.  Calls on one accumulator must not run
+ * concurrently (one stream, or ordered streams).
+ * ------------------------------------------------------------------------- */
+#define SRM3_STATS_MAX_BINS 16384
+
+typedef struct srm3_stats srm3_stats;
+
+typedef struct srm3_stats_result {
+    double count;          /* values accumulated */
+    double power_sum[4];   /* sum (u - shift)^p, p = 1..4 */
+    double mean;           /* shift + power_sum[0] / count */
+    double variance;       /* population central moments from the power sums */
+    double skewness;       /* c3 / c2^1.5 (0 when c2 = 0) */
+    double kurtosis;       /* c4 / c2^2 (0 when c2 = 0) */
+    uint64_t below, above; /* values outside [lo, hi) */
+} srm3_stats_result;
+
+/* New accumulator on the current device (zeroed).  1 <= nbins <=
+ * SRM3_STATS_MAX_BINS, finite lo < hi, finite shift (a value near the mean
+ * keeps the power sums well conditioned; 0 for zero-mean waves). */
+int srm3_stats_create(int32_t nbins, double lo, double hi, double shift, srm3_stats **out);
+
+/* Add count values of the device array u (16-byte aligned; float when
+ * precision == SRM3_FP32, double when SRM3_FP64).  Asynchronous on stream
+ * (a cudaStream_t; NULL = the legacy default stream).  count == 0 is a
+ * no-op. */
+int srm3_stats_add(srm3_stats *s, const void *u, int32_t precision, int64_t count, void *stream);
+
+/* Wait for stream and read the running results; hist (host, nbins entries,
+ * may be NULL) receives the bin counts. */
+int srm3_stats_read(srm3_stats *s, void *stream, srm3_stats_result *r, uint64_t *hist);
+
+/* Zero the accumulator (asynchronous on stream). */
+int srm3_stats_reset(srm3_stats *s, void *stream);
+
+/* Free the accumulator.  NULL is a no-op.  No call may be in flight. */
+void srm3_stats_destroy(srm3_stats *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
   field_dft          numpy FFT of the same coefficients
   field_series       equals coefficients + DFT (FFT form, Sec. 4.3)
   exact_moments      Monte Carlo moments of the series over many seeds
+  field_stats        closed-form moments of a sampled sinusoid, a centred
+                     uniform grid and a two-point distribution; exact bin
+                     counts of the uniform grid (sample statistics, Sec. 6)
 """
 from __future__ import annotations
 
@@ -305,3 +308,39 @@ def make_plan(S, kappa_u, omega_u, *, target=None, eps=None, env=None, beta=0.0,
         Sp, sb2 = recursion(S, kappa_u, omega_u, e, env)
     return OraclePlan(np.ascontiguousarray(S, dtype=np.float64), Sp, sb2, e, kappa_u,
                       omega_u, env, beta)
+
+
+def field_stats(u, nbins, lo, hi, shift=0.0):
+    """Sample statistics of field values (Sec. 6: sample mean, variance and
+    skewness; empirical PDF and CDF by histogram), by their definitions.
+
+    Power sums sum (u - shift)^p, p = 1..4, exactly rounded (math.fsum over
+    FP64 terms; FP32 values convert exactly).  Bins: floor((u - lo) * scale)
+    with scale = nbins / (hi - lo), both operations in the dtype of u and
+    rounded once each (the precision the bin decision is taken in); below lo
+    and at or above hi (or NaN) are counted apart.  Moments about the mean
+    follow from the power sums."""
+    import math
+    u = np.asarray(u).ravel()
+    dt = np.float32 if u.dtype == np.float32 else np.float64
+    u = u.astype(dt, copy=False)
+    d = u.astype(np.float64) - np.float64(shift)
+    ps = [math.fsum((d ** p).tolist()) for p in (1, 2, 3, 4)]
+    n = float(u.size)
+    scale = dt(float(nbins) / (hi - lo))
+    with np.errstate(invalid="ignore"):
+        t = (u - dt(lo)) * scale
+        below = int(np.count_nonzero(t < 0))
+        inb = (t >= 0) & (t < nbins)
+    above = int(u.size - below - np.count_nonzero(inb))
+    hist = np.bincount(np.floor(t[inb]).astype(np.int64), minlength=nbins).astype(np.uint64)
+    out = {"count": n, "power_sum": ps, "hist": hist, "below": below, "above": above}
+    if n > 0:
+        m1, e2, e3, e4 = (x / n for x in ps)
+        c2 = e2 - m1 * m1
+        c3 = e3 - 3 * m1 * e2 + 2 * m1 ** 3
+        c4 = e4 - 4 * m1 * e3 + 6 * m1 * m1 * e2 - 3 * m1 ** 4
+        out.update(mean=shift + m1, variance=c2,
+                   skewness=c3 / c2 ** 1.5 if c2 > 0 else 0.0,
+                   kurtosis=c4 / c2 ** 2 if c2 > 0 else 0.0)
+    return out

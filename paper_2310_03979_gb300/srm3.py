@@ -38,7 +38,10 @@ EXPORTED = [
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
     "srm3_batch_pair_terms", "srm3_batch_destroy", "srm3_batch_enable_timing",
     "srm3_batch_pairsum_ms", "srm3_batch_set_max_ctas",
+    "srm3_stats_create", "srm3_stats_add", "srm3_stats_read", "srm3_stats_reset",
+    "srm3_stats_destroy",
 ]
+SRM3_STATS_MAX_BINS = 16384
 SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -86,6 +89,13 @@ class srm3_timings(ctypes.Structure):
                 ("pairsum_launches", ctypes.c_int32), ("pair_terms", ctypes.c_int64),
                 ("recursion_fp32_ms", ctypes.c_double), ("recursion_fp64_ms", ctypes.c_double),
                 ("recursion_passes_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class srm3_stats_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_double), ("power_sum", ctypes.c_double * 4),
+                ("mean", ctypes.c_double), ("variance", ctypes.c_double),
+                ("skewness", ctypes.c_double), ("kurtosis", ctypes.c_double),
+                ("below", ctypes.c_uint64), ("above", ctypes.c_uint64)]
 
 
 class SRM3Error(RuntimeError):
@@ -142,6 +152,13 @@ def load(build_if_needed: bool = True):
     lib.srm3_batch_enable_timing.argtypes = [vp, i32]
     lib.srm3_batch_pairsum_ms.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     lib.srm3_batch_set_max_ctas.argtypes = [vp, i32]
+    lib.srm3_stats_create.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(vp)]
+    lib.srm3_stats_add.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int64, vp]
+    lib.srm3_stats_read.argtypes = [vp, vp, ctypes.POINTER(srm3_stats_result), u64p]
+    lib.srm3_stats_reset.argtypes = [vp, vp]
+    lib.srm3_stats_destroy.argtypes = [vp]
+    lib.srm3_stats_destroy.restype = None
     _lib = lib
     return lib
 
@@ -293,6 +310,62 @@ class Batch:
         self.destroy()
 
 
+class Stats:
+    """Running ensemble statistics of sampled fields on the device
+    (srm3_stats_*): power sums about ``shift`` and a histogram of ``nbins``
+    bins over [lo, hi).  ``add`` takes a device tensor (float32 or float64,
+    any shape, contiguous); ``read`` returns mean, variance, skewness,
+    kurtosis, the bin counts and the empirical PDF and CDF over the bins."""
+
+    def __init__(self, nbins, lo, hi, shift=0.0, stream=None):
+        h = ctypes.c_void_p()
+        _check(load().srm3_stats_create(int(nbins), float(lo), float(hi), float(shift),
+                                        ctypes.byref(h)))
+        self.handle = h
+        self.nbins, self.lo, self.hi = int(nbins), float(lo), float(hi)
+        self.stream = stream
+
+    def add(self, u, precision=None, count=None):
+        if precision is None:
+            precision = SRM3_FP64 if str(getattr(u, "dtype", "")) == "torch.float64" else SRM3_FP32
+        if count is None:
+            count = u.numel()
+        ptr = u.data_ptr() if hasattr(u, "data_ptr") else int(u)
+        _check(load().srm3_stats_add(self.handle, ptr, int(precision), int(count), self.stream))
+
+    def read(self):
+        import numpy as np
+        r = srm3_stats_result()
+        hist = np.zeros(self.nbins, dtype=np.uint64)
+        _check(load().srm3_stats_read(self.handle, self.stream, ctypes.byref(r),
+                                      hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        width = (self.hi - self.lo) / self.nbins
+        n = r.count
+        cum = np.cumsum(hist.astype(np.float64)) + float(r.below)
+        return {
+            "count": n, "power_sum": list(r.power_sum), "mean": r.mean,
+            "variance": r.variance, "skewness": r.skewness, "kurtosis": r.kurtosis,
+            "below": int(r.below), "above": int(r.above), "hist": hist,
+            "edges": self.lo + width * np.arange(self.nbins + 1),
+            "pdf": hist / (n * width) if n > 0 else hist.astype(np.float64),
+            "cdf": cum / n if n > 0 else cum,
+        }
+
+    def reset(self):
+        _check(load().srm3_stats_reset(self.handle, self.stream))
+
+    def destroy(self):
+        if self.handle:
+            load().srm3_stats_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+
 def enable_timing(plan, on: bool):
     _check(load().srm3_enable_timing(plan, int(bool(on))))
 
@@ -345,6 +418,8 @@ class Plan:
                 env_b = np.ascontiguousarray(tb, dtype=np.float64)
                 bs.env_table_b = env_b.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         tgt = wl.target if target is None else target
+        if eps is None and target is None and getattr(wl, "eps", 0.0) > 0.0:
+            eps = wl.eps
         if eps is not None:
             bs.target_max_sum_b2, bs.eps = 0.0, float(eps)
         else:

@@ -45,6 +45,8 @@ class Workload:
     # "sum" (g = b(i+j) alone)
     envelope: str = "gauss"
     sigma_e: float = 0.5
+    # fixed bispectrum scale (> 0: used as given, no search on target)
+    eps: float = 0.0
 
     def envelope_table(self) -> np.ndarray:
         """Separable envelope e(kk, kw) = exp(-1/2 ((kk/(sigma_e Nk))^2 +
@@ -121,8 +123,31 @@ BRIDGE_SEP = Workload("bridge_256x512_separable_fp32", 256, 512, 0.25, 4 * math.
                       20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
                       storage="recompute", envelope="separable", sigma_e=0.5)
 
+# The wind field along the long-span bridge of Sec. 5: L = 628 m, omega_u =
+# pi rad/s, N_omega = 128, N_t = 2048, N_x = 1024, N_kappa = 256, kappa_u =
+# 2 (N_kappa - 1) pi / L; Kaimal with z = 50 m, z0 = 0.03 m, U = 40 m/s,
+# k = 0.4; Davenport coherence with lambda = 10, whose wavenumber density
+# has half-width lambda omega / (pi U), i.e. lam = 2 lambda = 20 in this
+# module's a = lam omega / (2 pi U); 1000 samples, FP32.  Bispectrum of
+# Sec. 5: |B| = (2 / (3 sqrt 3)) sqrt(S_i S_j S_k) / sqrt(omega_k kappa_k),
+# an envelope of i + j alone, with omega_k kappa_k taken at the cell centres
+# ((kk + 1/2) dk (kw + 1/2) dw, the "sum" envelope b(k) = 1 / (2 sqrt((kk +
+# 1/2)(kw + 1/2)))), so b_p^2 = eps^2 dk dw b_k^2 q_i q_j matches the paper's
+# (2 / (3 sqrt 3))^2 q_i q_j / ((kk + 1/2)(kw + 1/2)) at
+# eps = (4 / (3 sqrt 3)) / sqrt(dk dw), a fixed scale (no search).
+def _paper_bridge():
+    L, nk, nw = 628.0, 256, 128
+    ku, wu = 2.0 * (nk - 1) * math.pi / L, math.pi
+    eps = (4.0 / (3.0 * math.sqrt(3.0))) / math.sqrt((ku / nk) * (wu / nw))
+    return Workload("paper_bridge_256x128_fp32", nk, nw, ku, wu, 40.0, 50.0, 1024, 2048,
+                    tuple(range(1, 1001)), precision="fp32", storage="recompute",
+                    lam=20.0, envelope="sum", eps=eps)
+
+
+PAPER_BRIDGE = _paper_bridge()
+
 CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "bridge_rc": BRIDGE_RC, "bridge_sep": BRIDGE_SEP,
-           "large": LARGE, "prof128": PROF128}
+           "large": LARGE, "prof128": PROF128, "paper_bridge": PAPER_BRIDGE}
 
 
 def uneven_batch(n_spectra: int = 200, seed: int = 4):
