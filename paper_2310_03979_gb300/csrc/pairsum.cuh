@@ -83,11 +83,14 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
 // and 48 y_b rows (47 used) of the group with four TMA tile loads of 16 rows
 // x 512 bytes through a 2-D tensor map over y (rows outside the lattice read
 // the zero padding of y) into one of two stages, signalled by an mbarrier
-// with a transaction count.  The weights go to shared memory
-// already duplicated as (w, w) pairs: TABLE loads the chunk's W rows (one
-// chunk ahead, through registers); otherwise the chunk's 64-entry window
-// of the duplicated omega envelope Ew2 is bulk-copied, w = Ew[2 iw - kw],
-// with the kappa factor Ek[kk - 2a] applied per row pair and c_k at the end.
+// with a transaction count.  TABLE: the chunk's W rows go to shared memory
+// as they are (loaded one chunk ahead, through registers), four weights per
+// 16-byte load on the compute side, each paired with itself (w, w) in
+// registers for the packed products -- half the shared-memory loads of
+// storing the pairs, worth 4 % of the launch; otherwise the chunk's
+// 64-entry window of the omega envelope, stored as (w, w) pairs (Ew2), is
+// bulk-copied, w = Ew[2 iw - kw], with the kappa factor Ek[kk - 2a] applied
+// per row pair and c_k at the end.
 // Half-group mode (at most 32 sheet-samples, W recomputed): the lanes of a
 // group would be half empty, so each half-warp takes one of two row pairs
 // (a = 2i, 2i + 1) of a work item, on 256-byte rows staged by eight tile
@@ -108,6 +111,11 @@ __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
 __device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
   f32x2 d;
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 f2_dup(float x) {
+  f32x2 d;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(x));
   return d;
 }
 __device__ __forceinline__ float2 f2_split(f32x2 v) {
@@ -134,7 +142,7 @@ constexpr int YROWS = CH + YB_BOXES * BOX_ROWS;  // staged rows per chunk (64)
 constexpr int LANES = 32;                 // sample pairs per group
 constexpr int ROW_BYTES = LANES * 16;     // one staged row
 constexpr int STAGE_Y = YROWS * LANES;    // float4 per stage
-constexpr int STAGE_W = NC * R * CH;      // (w, w) pairs per stage, table
+constexpr int STAGE_W = NC * R * CH;      // float2 slots per stage (W: the first half)
 constexpr int EWIN = 64;                  // (w, w) pairs per stage, envelope
 constexpr int NK = 4 * R;                 // Kahan sums per compute thread
 constexpr int WPL = STAGE_W / 4 / 32;     // float4 of W per producer lane (4)
@@ -294,9 +302,9 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
     if (TABLE) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const ulonglong2 w01 = lds_pair(pw + r * CH + blk * U);
-        const ulonglong2 w23 = lds_pair(pw + r * CH + blk * U + 2);
-        const f32x2 w[U] = {w01.x, w01.y, w23.x, w23.y};
+        const float4 w4 =
+            *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(pw) + r * CH + blk * U);
+        const f32x2 w[U] = {f2_dup(w4.x), f2_dup(w4.y), f2_dup(w4.z), f2_dup(w4.w)};
 #pragma unroll
         for (int uu = 0; uu < U; ++uu) {
           const int v = r - uu + U - 1;
@@ -441,9 +449,9 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
           for (int h = 0; h < WPL; ++h) {
             const int f = lane + 32 * h;
             float4 *dw = reinterpret_cast<float4 *>(
-                sw + stage * STAGE_W + ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
-            dw[0] = make_float4(wr[h].x, wr[h].x, wr[h].y, wr[h].y);
-            dw[1] = make_float4(wr[h].z, wr[h].z, wr[h].w, wr[h].w);
+                reinterpret_cast<float *>(sw + stage * STAGE_W) +
+                ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
+            *dw = wr[h];
           }
         }
         w_next();
@@ -494,7 +502,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       if (!mbar_wait(&full[stage], (q >> 1) & 1, abort, err)) return;
       const int i0 = c * CH;
       if (tile_ok) {
-        const float2 *pw = sw + stage * STAGE_W + warp * R * CH;
+        const float2 *pw = reinterpret_cast<const float2 *>(
+            reinterpret_cast<const float *>(sw + stage * STAGE_W) + warp * R * CH);
         const float2 *pe = sw + stage * STAGE_W + 24 - 8 * warp;
         if (half) {
           const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;

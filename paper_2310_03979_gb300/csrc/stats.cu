@@ -10,10 +10,12 @@
 // per step: the FP64 pipe of this part is far narrower than its FP32 pipe),
 // FP64 input in FP64 throughout.  Bins are b = floor((u - lo) * (nbins /
 // (hi - lo))) in the input's precision, each operation rounded once; b < 0
-// counts below, b >= nbins (or a NaN) above.  Per-CTA shared histograms
-// merge into the global one with integer atomics; the per-CTA power sums go
-// to a partials array and one thread per power adds them in CTA order.  The
-// same values given in the same calls yield bit-identical results.
+// counts below, b >= nbins (or a NaN) above, as two extra slots of the
+// shared histogram, so that every value costs one shared atomic and no
+// branch.  Per-CTA shared histograms merge into the global one with integer
+// atomics; the per-CTA power sums go to a partials array, added in a fixed
+// order of runs.  The same values given in the same calls yield
+// bit-identical results.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -56,21 +58,28 @@ struct StatVec<double> {
   static __device__ __forceinline__ double at(const double2 &v, int i) { return i == 0 ? v.x : v.y; }
 };
 
+// The shared-histogram slot of a value: its bin, nbins for below lo,
+// nbins + 1 at or above hi or for a NaN.
 template <typename T>
-__device__ __forceinline__ void stat_bin(T u, T lo, T scale, int nbins, unsigned int *sh,
-                                         unsigned long long &below, unsigned long long &above) {
+__device__ __forceinline__ int stat_slot(T u, T lo, T scale, int nbins) {
   T t;
   if constexpr (sizeof(T) == sizeof(float))
     t = __fmul_rn(__fsub_rn(u, lo), scale);
   else
     t = __dmul_rn(__dsub_rn(u, lo), scale);
-  if (t < (T)0) {
-    ++below;
-  } else if (t < (T)nbins) {
-    atomicAdd(sh + (int)t, 1u);
-  } else {
-    ++above;  // t >= nbins or NaN
-  }
+  return t < (T)0 ? nbins : (t < (T)nbins ? (int)t : nbins + 1);
+}
+
+// One value into the running FP32 (or FP64) power sums and the histogram.
+template <typename T>
+__device__ __forceinline__ void stat_one(T val, T sh, T lo, T scale, int nbins,
+                                         unsigned int *hist, T &s1, T &s2, T &s3, T &s4) {
+  const T d = val - sh, d2 = d * d;
+  s1 += d;
+  s2 += d2;
+  s3 = fma(d2, d, s3);
+  s4 = fma(d2, d2, s4);
+  atomicAdd(hist + stat_slot<T>(val, lo, scale, nbins), 1u);
 }
 
 template <typename T>
@@ -80,10 +89,9 @@ __global__ void __launch_bounds__(kStatThreads) k_stats(const T *__restrict__ u,
                                                         unsigned long long *__restrict__ hist) {
   using SV = StatVec<T>;
   using V = typename SV::V;
-  extern __shared__ unsigned int sh_hist[];
+  extern __shared__ unsigned int sh_hist[];  // nbins + 2 slots
   __shared__ double sh_sum[kStatThreads / 32][4];
-  __shared__ unsigned long long sh_out[kStatThreads / 32][2];
-  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh_hist[b] = 0;
+  for (int b = threadIdx.x; b < nbins + 2; b += blockDim.x) sh_hist[b] = 0;
   __syncthreads();
   const long long nv = count / SV::N;
   const long long nth = (long long)gridDim.x * blockDim.x;
@@ -91,36 +99,30 @@ __global__ void __launch_bounds__(kStatThreads) k_stats(const T *__restrict__ u,
   const V *uv = reinterpret_cast<const V *>(u);
   const T sh = (T)shift;
   double a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
-  unsigned long long below = 0, above = 0;
-  for (long long v0 = tid; v0 < nv; v0 += nth * kStatVec) {
+  // steps whose kStatVec vectors all exist, without per-value checks
+  const long long full = nv / (nth * kStatVec) * (nth * kStatVec);
+  for (long long v0 = tid; v0 < full; v0 += nth * kStatVec) {
     V x[kStatVec];
 #pragma unroll
-    for (int j = 0; j < kStatVec; ++j) {
-      const long long v = v0 + (long long)j * nth;
-      if (v < nv) {
-        x[j] = __ldcs(uv + v);  // streamed once
-      } else {
-        x[j] = V{};
-        // padding values: shift + 0 contributes nothing to the power sums;
-        // they are kept out of the histogram below
-      }
-    }
+    for (int j = 0; j < kStatVec; ++j) x[j] = __ldcs(uv + v0 + (long long)j * nth);
     T s1 = 0, s2 = 0, s3 = 0, s4 = 0;
 #pragma unroll
-    for (int j = 0; j < kStatVec; ++j) {
-      const bool live = v0 + (long long)j * nth < nv;
+    for (int j = 0; j < kStatVec; ++j)
 #pragma unroll
-      for (int i = 0; i < SV::N; ++i) {
-        const T val = SV::at(x[j], i);
-        const T d = live ? val - sh : (T)0;
-        const T d2 = d * d;
-        s1 += d;
-        s2 += d2;
-        s3 = fma(d2, d, s3);
-        s4 = fma(d2, d2, s4);
-        if (live) stat_bin<T>(val, lo, scale, nbins, sh_hist, below, above);
-      }
-    }
+      for (int i = 0; i < SV::N; ++i)
+        stat_one<T>(SV::at(x[j], i), sh, lo, scale, nbins, sh_hist, s1, s2, s3, s4);
+    a1 += (double)s1;
+    a2 += (double)s2;
+    a3 += (double)s3;
+    a4 += (double)s4;
+  }
+  // the last partial step: one vector at a time
+  for (long long v = full + tid; v < nv; v += nth) {
+    const V x = __ldcs(uv + v);
+    T s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+#pragma unroll
+    for (int i = 0; i < SV::N; ++i)
+      stat_one<T>(SV::at(x, i), sh, lo, scale, nbins, sh_hist, s1, s2, s3, s4);
     a1 += (double)s1;
     a2 += (double)s2;
     a3 += (double)s3;
@@ -129,13 +131,12 @@ __global__ void __launch_bounds__(kStatThreads) k_stats(const T *__restrict__ u,
   // the count % N trailing values: block 0, thread 0, in index order
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (long long e = nv * SV::N; e < count; ++e) {
-      const T val = u[e];
-      const double d = (double)(val - sh);
-      a1 += d;
-      a2 += d * d;
-      a3 += d * d * d;
-      a4 += (d * d) * (d * d);
-      stat_bin<T>(val, lo, scale, nbins, sh_hist, below, above);
+      T s1 = 0, s2 = 0, s3 = 0, s4 = 0;
+      stat_one<T>(u[e], sh, lo, scale, nbins, sh_hist, s1, s2, s3, s4);
+      a1 += (double)s1;
+      a2 += (double)s2;
+      a3 += (double)s3;
+      a4 += (double)s4;
     }
   }
   // CTA reduction in a fixed order: butterflies within warps, then warps in order
@@ -143,38 +144,39 @@ __global__ void __launch_bounds__(kStatThreads) k_stats(const T *__restrict__ u,
 #pragma unroll
   for (int p = 0; p < 4; ++p)
     for (int o = 16; o > 0; o >>= 1) a[p] += __shfl_xor_sync(0xffffffffu, a[p], o);
-  for (int o = 16; o > 0; o >>= 1) {
-    below += __shfl_xor_sync(0xffffffffu, below, o);
-    above += __shfl_xor_sync(0xffffffffu, above, o);
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
 #pragma unroll
     for (int p = 0; p < 4; ++p) sh_sum[warp][p] = a[p];
-    sh_out[warp][0] = below;
-    sh_out[warp][1] = above;
   }
   __syncthreads();
   if (threadIdx.x < 4) {
     double s = 0.0;
     for (int w = 0; w < kStatThreads / 32; ++w) s += sh_sum[w][threadIdx.x];
     part[(size_t)blockIdx.x * 4 + threadIdx.x] = s;
-  } else if (threadIdx.x < 6) {
-    unsigned long long s = 0;
-    for (int w = 0; w < kStatThreads / 32; ++w) s += sh_out[w][threadIdx.x - 4];
-    if (s) atomicAdd(hist + nbins + (threadIdx.x - 4), s);
   }
-  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+  for (int b = threadIdx.x; b < nbins + 2; b += blockDim.x)
     if (sh_hist[b]) atomicAdd(hist + b, (unsigned long long)sh_hist[b]);
 }
 
-// acc[p] += sum over CTAs, in CTA order (one thread per power).
-__global__ void k_stats_merge(const double *__restrict__ part, int grid, double *__restrict__ acc) {
-  const int p = threadIdx.x;
-  if (p >= 4) return;
+// acc[p] += sum over CTAs in a fixed order: thread t sums power t & 3 over
+// the t >> 2-th contiguous run of CTAs, then thread p < 4 adds the runs in
+// order.
+constexpr int kMergeThreads = 256;
+__global__ void __launch_bounds__(kMergeThreads) k_stats_merge(const double *__restrict__ part,
+                                                               int grid, double *__restrict__ acc) {
+  __shared__ double run[kMergeThreads];
+  const int t = threadIdx.x, p = t & 3, r = t >> 2, nr = kMergeThreads / 4;
+  const int per = (grid + nr - 1) / nr, c0 = r * per, c1 = min(grid, c0 + per);
   double s = 0.0;
-  for (int c = 0; c < grid; ++c) s += part[(size_t)c * 4 + p];
-  acc[p] += s;
+  for (int c = c0; c < c1; ++c) s += part[(size_t)c * 4 + p];
+  run[t] = s;
+  __syncthreads();
+  if (t < 4) {
+    double tot = 0.0;
+    for (int q = 0; q < nr; ++q) tot += run[4 * q + t];
+    acc[t] += tot;
+  }
 }
 
 }  // namespace
@@ -224,7 +226,7 @@ SRM3_API int srm3_stats_add(srm3_stats *s, const void *u, int32_t precision, int
   if (reinterpret_cast<uintptr_t>(u) % 16)
     return fail(SRM3_ERR_INVALID_ARG, "u must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t smem = (size_t)s->nbins * sizeof(unsigned int);
+  const size_t smem = ((size_t)s->nbins + 2) * sizeof(unsigned int);
   const double scale = (double)s->nbins / (s->hi - s->lo);
   if (precision == SRM3_FP32) {
     SRM3_CUDA(cudaFuncSetAttribute(k_stats<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -240,7 +242,7 @@ SRM3_API int srm3_stats_add(srm3_stats *s, const void *u, int32_t precision, int
         s->hist);
   }
   SRM3_CUDA(cudaGetLastError());
-  k_stats_merge<<<1, 32, 0, st>>>(s->part, s->grid, s->acc);
+  k_stats_merge<<<1, kMergeThreads, 0, st>>>(s->part, s->grid, s->acc);
   SRM3_CUDA(cudaGetLastError());
   s->count += (double)count;
   return SRM3_OK;
