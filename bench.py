@@ -575,11 +575,11 @@ def run_paper_bridge(args):
                       "skewness": m3_exact / var_exact ** 1.5},
             "values": r3["count"], "histogram_bins": nbins, "range_sigma": 6},
         # per step: spectrum 1, envelope tables 3, sum of S 1, recursion
-        # passes, sampling tables 5, conv twiddles 1; per batch of 50 (one
+        # passes, sampling tables 4, conv twiddles 1; per batch of 50 (one
         # sampling chunk): phases, three FFT self-convolution passes, two
         # output FFT stages, statistics pass and merge
         "gpu_launches": args.steps * (1 + 3 + 1 + info.root_passes + info.root_passes_fp32
-                                      + 5 + 1 + 8 * math.ceil(n / B)),
+                                      + 4 + 1 + 8 * math.ceil(n / B)),
         "clocks": clocks,
         "eps": info.eps, "max_sum_b2": info.max_sum_b2,
         "e2e": {"value": 2 * pairs * n / wall, "unit": "pair-terms/s",
@@ -710,17 +710,16 @@ def main():
     chunks = math.ceil(n / 128)
     # kernels launched per step (matches the ncu launch list): spectrum 1,
     # envelope tables 2 + g^2 1, the sum of S 1, linear pass + reduction 2,
-    # each recursion pass 1, sampling tables 5 (FP32) / 4 (FP64), W table 1
-    # if stored; per 128-sample chunk: phases, pair sum, two FFT stages
+    # each recursion pass 1, sampling tables 4, W table 1 if stored; per
+    # 128-sample chunk: phases, pair sum, two FFT stages
     launches_per_step = (1 + 3 + 1 + 2 + (info.root_passes + info.root_passes_fp32)
-                         + (5 if es == 4 else 4) + (1 if info.storage == 1 else 0)
-                         + 4 * chunks)
+                         + 4 + (1 if info.storage == 1 else 0) + 4 * chunks)
     if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
         # self-convolution passes, two output FFT stages
         launches_per_step = (1 + 3 + 1 + (info.root_passes + info.root_passes_fp32)
-                             + (5 if es == 4 else 4) + 1 + 6 * chunks)
+                             + 4 + 1 + 6 * chunks)
     traffic = None
     src = os.path.join(ROOT, "paper_2310_03979_gb300", "csrc", "pairsum.cuh")
     if wl.name.startswith("bridge") and info.storage == 1 and es == 4:

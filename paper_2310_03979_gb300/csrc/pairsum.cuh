@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
 // 16-byte load on the compute side, each paired with itself (w, w) in
 // registers for the packed products -- half the shared-memory loads of
 // storing the pairs, worth 4 % of the launch; otherwise the chunk's
-// 64-entry window of the omega envelope, stored as (w, w) pairs (Ew2), is
-// bulk-copied, w = Ew[2 iw - kw], with the kappa factor Ek[kk - 2a] applied
+// 64-entry window of the omega envelope table Ew is bulk-copied, w =
+// Ew[2 iw - kw], each weight paired with itself in registers as above, with the kappa factor Ek[kk - 2a] applied
 // per row pair and c_k at the end.
 // Half-group mode (at most 32 sheet-samples, W recomputed): the lanes of a
 // group would be half empty, so each half-warp takes one of two row pairs
@@ -232,7 +232,7 @@ struct PsDesc {  // aligned as CUtensorMap
   const float4 *y;       // pair-planar rows (kPad zero entries each side)
   const float2 *y0;      // y at k = 0 per sheet-sample
   const float *Ek;       // kappa envelope factor (recompute)
-  const float2 *Ew2;     // omega envelope as (w, w) pairs (recompute; w0 at ew_off)
+  const float *Ew;       // omega envelope by signed offset (recompute; w0 at ew_off)
   const float *W;        // W table (table storage)
   const long long *toff; // W-table offset per tile (table storage)
   const float *Pk, *ck;  // pure and pair factors
@@ -316,19 +316,26 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
         }
       }
     } else {
-      f32x2 e[NE];
+      // the block's NE = 14 weights: three 16-byte loads and one 8-byte load
+      const float *pef = reinterpret_cast<const float *>(pe) + 8 * blk;
+      float e[NE];
 #pragma unroll
-      for (int j = 0; j < NE / 2; ++j) {
-        const ulonglong2 v2 = lds_pair(pe + 8 * blk + 2 * j);
-        e[2 * j] = v2.x;
-        e[2 * j + 1] = v2.y;
+      for (int j = 0; j < 3; ++j) {
+        const float4 v4 = reinterpret_cast<const float4 *>(pef)[j];
+        e[4 * j] = v4.x;
+        e[4 * j + 1] = v4.y;
+        e[4 * j + 2] = v4.z;
+        e[4 * j + 3] = v4.w;
       }
+      const float2 v2 = reinterpret_cast<const float2 *>(pef)[6];
+      e[12] = v2.x;
+      e[13] = v2.y;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
 #pragma unroll
         for (int uu = 0; uu < U; ++uu) {
           const int v = r - uu + U - 1;
-          const f32x2 w = e[2 * uu - r + R - 1];
+          const f32x2 w = f2_dup(e[2 * uu - r + R - 1]);
           const f32x2 wpx = f2_mul(w, A[uu].x), wpy = f2_mul(w, A[uu].y);
           Txp[r] = f2_fma(wpx, B[v].x, Txp[r]);
           Txm[r] = f2_fma(wpy, B[v].y, Txm[r]);
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
       const int half = MIXED ? d.half : 0;
       const int nitems = ps_nitems(kk, kws0, half), tab = d.table, rs = d.rowstride;
-      const unsigned tx = YROWS * ROW_BYTES + (tab ? 0 : EWIN * (unsigned)sizeof(float2));
+      const unsigned tx = YROWS * ROW_BYTES + (tab ? 0 : EWIN * (unsigned)sizeof(float));
       const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
       for (int item = 0; item < nitems; ++item, ++q) {
@@ -441,8 +448,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
                           &full[stage]);
           }
           if (!tab)
-            bulk_g2s(sw + stage * STAGE_W, d.Ew2 + d.ew_off + 2 * i0 - kws0 - (SW - 1),
-                     EWIN * sizeof(float2), &full[stage]);
+            bulk_g2s(sw + stage * STAGE_W, d.Ew + d.ew_off + 2 * i0 - kws0 - (SW - 1),
+                     EWIN * sizeof(float), &full[stage]);
         }
         if (tab) {
 #pragma unroll
@@ -504,7 +511,8 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       if (tile_ok) {
         const float2 *pw = reinterpret_cast<const float2 *>(
             reinterpret_cast<const float *>(sw + stage * STAGE_W) + warp * R * CH);
-        const float2 *pe = sw + stage * STAGE_W + 24 - 8 * warp;
+        const float2 *pe = reinterpret_cast<const float2 *>(
+            reinterpret_cast<const float *>(sw + stage * STAGE_W) + 24 - 8 * warp);
         if (half) {
           const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;
           const float4 *pb = pa + (CH + R * warp + CH - U) * (LANES / 2);
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
               const float4 h = d.y[((size_t)ah * d.rowstride + kPad + (kw >> 1)) * SP +
                                    (size_t)grp * LANES + ln];
               const float w0 = tab ? d.W[my_base + ((long long)ah * R + r) * my_L + (kw >> 1)]
-                                   : d.Ew2[d.ew_off].x;
+                                   : d.Ew[d.ew_off];
               v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
               v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
               v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));

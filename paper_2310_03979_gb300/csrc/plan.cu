@@ -144,11 +144,6 @@ __global__ void k_env(int len, int off, double sigma_n, T *out) {
   out[i] = (T)exp(-0.5 * a * a);
 }
 
-__global__ void k_dup2(int len, const float *__restrict__ in, float2 *__restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < len) out[i] = make_float2(in[i], in[i]);
-}
-
 // Twiddles of the radix-2 stages for every transform length up to n = 2^log2n,
 // packed by stage: entry 2^(s-1) - 1 + j holds e^{+2 pi i m / n} with
 // m = j 2^(log2n - s) (= e^{+2 pi i j / 2^s}), j < 2^(s-1), s = 1..log2n; the
@@ -866,9 +861,9 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   // signed envelope table Ews[ew_off + d] (terms outside the lattice meet
   // zero y, whatever their weight).  ew_off is
-  // odd, which puts the FP32 pair sum's 96-pair chunk windows of Ew2 (first
-  // d = 2 i0 - kws0 - 31, odd) on 16-byte boundaries; the table reaches
-  // d = nw + 127, past the last window.
+  // 3 mod 4, which puts the FP32 pair sum's 64-entry chunk windows of the
+  // FP32 table (first d = 2 i0 - kws0 - 31, 1 mod 4) on 16-byte boundaries;
+  // the table reaches d = nw + 127, past the last window.
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
   p->ew_len = p->ew_off + nw + 128;
   p->nfft = std::max(p->nx, p->nt);
@@ -895,10 +890,8 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_env<float><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (float *)p->Ek);
     k_env<float><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off, p->sigma_g * nw,
                                                       (float *)p->Ews);
-    SRM3_CUDA(cudaMalloc(&p->Ew2, p->ew_len * sizeof(float2)));
     SRM3_CUDA(cudaMalloc(&p->ps_err, sizeof(int)));
     SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
-    k_dup2<<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, (const float *)p->Ews, p->Ew2);
     k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
                                                           (float2 *)p->tw);
     if (p->sep) {
@@ -940,7 +933,7 @@ void free_plan(srm3_plan *p) {
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
-                 p->Ew2,    p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
+                 p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr};

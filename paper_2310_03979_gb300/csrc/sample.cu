@@ -227,7 +227,7 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
   d->y = (const float4 *)y;
   d->y0 = (const float2 *)y0;
   d->Ek = (const float *)p->Ek;
-  d->Ew2 = p->Ew2;
+  d->Ew = (const float *)p->Ews;
   d->W = table ? p->W : nullptr;
   d->toff = table ? p->tile_off : nullptr;
   d->Pk = (const float *)p->Pk;

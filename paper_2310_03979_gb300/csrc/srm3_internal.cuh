@@ -114,7 +114,6 @@ struct srm3_plan {
   void *ck = nullptr;     // pair factor 2 eps dk dw sqrt(S), [nk*nw]
   void *Ek = nullptr;     // envelope factor along kappa, |d| < nk
   void *Ews = nullptr;    // envelope factor along omega, signed d, offset ew_off
-  float2 *Ew2 = nullptr;  // FP32 plans: the same as (w, w) pairs
   int ew_off = 0, ew_len = 0;
   void *tw = nullptr;     // FFT twiddles e^{+2 pi i j / nfft}, j < nfft
   int nfft = 0;
