@@ -57,12 +57,12 @@ __global__ void k_conv_rows(int nk, int nw, int log2Nw, int Nk, int SSpad, int r
       v.x = ev * yv.x;
       v.y = ev * yv.y;
     }
-    buf[brev(m, log2Nw)] = v;
+    buf[rp(brev(m, log2Nw))] = v;
   }
   __syncthreads();
-  fft_stages(buf, 1, log2Nw, tw);
+  fft_stages<false>(buf, 1, log2Nw, tw);
   T2 *out = Z + ((size_t)ss * Nk + kk) * Nw;
-  for (int m = threadIdx.x; m < Nw; m += blockDim.x) out[m] = buf[m];
+  for (int m = threadIdx.x; m < Nw; m += blockDim.x) out[m] = buf[rp(m)];
 }
 
 // Pass 2: TC columns of one sheet-sample: forward transform along kappa
@@ -74,8 +74,8 @@ __global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC,
                             typename Vec2<T>::type *__restrict__ Z) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char conv_smem[];
-  T2 *buf = reinterpret_cast<T2 *>(conv_smem);  // [TC][Nk]
-  const int Nk = 1 << log2Nk, col0 = blockIdx.x * TC, ss = blockIdx.y;
+  T2 *buf = reinterpret_cast<T2 *>(conv_smem);  // [TC][Nk + 1]
+  const int Nk = 1 << log2Nk, col0 = blockIdx.x * TC, ss = blockIdx.y, cs = fft_col_stride(Nk);
   T2 *base = Z + (size_t)ss * Nk * Nw + col0;
   for (int t = threadIdx.x; t < Nk * TC; t += blockDim.x) {
     const int r = t / TC, c = t - r * TC;
@@ -83,29 +83,29 @@ __global__ void k_conv_cols(int nk, int log2Nk, int Nw, int TC,
     v.x = 0;
     v.y = 0;
     if (r < nk) v = base[(size_t)r * Nw + c];
-    buf[c * Nk + brev(r, log2Nk)] = v;
+    buf[c * cs + brev(r, log2Nk)] = v;
   }
   __syncthreads();
-  fft_stages(buf, TC, log2Nk, tw);
+  fft_stages<true>(buf, TC, log2Nk, tw);
   // square, then back to bit-reversed order for the second transform
   for (int t = threadIdx.x; t < Nk * TC; t += blockDim.x) {
     const int c = t / Nk, r = t - c * Nk, rb = brev(r, log2Nk);
     if (r <= rb) {
-      const T2 a = buf[c * Nk + r], b = buf[c * Nk + rb];
+      const T2 a = buf[c * cs + r], b = buf[c * cs + rb];
       T2 a2, b2;
       a2.x = a.x * a.x - a.y * a.y;
       a2.y = 2 * a.x * a.y;
       b2.x = b.x * b.x - b.y * b.y;
       b2.y = 2 * b.x * b.y;
-      buf[c * Nk + r] = b2;
-      buf[c * Nk + rb] = a2;
+      buf[c * cs + r] = b2;
+      buf[c * cs + rb] = a2;
     }
   }
   __syncthreads();
-  fft_stages(buf, TC, log2Nk, tw);
+  fft_stages<true>(buf, TC, log2Nk, tw);
   for (int t = threadIdx.x; t < nk * TC; t += blockDim.x) {
     const int r = t / TC, c = t - r * TC;
-    base[(size_t)r * Nw + c] = buf[c * Nk + ((Nk - r) & (Nk - 1))];
+    base[(size_t)r * Nw + c] = buf[c * cs + ((Nk - r) & (Nk - 1))];
   }
 }
 
@@ -127,12 +127,12 @@ __global__ void k_conv_out(int nk, int nw, int log2Nw, int Nk, int SSpad, int ro
   T2 *buf = reinterpret_cast<T2 *>(conv_smem);
   const int kk = blockIdx.x, ss = blockIdx.y, Nw = 1 << log2Nw;
   const T2 *in = Z + ((size_t)ss * Nk + kk) * Nw;
-  for (int m = threadIdx.x; m < Nw; m += blockDim.x) buf[brev(m, log2Nw)] = in[m];
+  for (int m = threadIdx.x; m < Nw; m += blockDim.x) buf[rp(brev(m, log2Nw))] = in[m];
   __syncthreads();
-  fft_stages(buf, 1, log2Nw, tw);
+  fft_stages<false>(buf, 1, log2Nw, tw);
   const T inv = (T)1 / ((T)Nk * (T)Nw);
   for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) {
-    const T2 cv = buf[(Nw - kw) & (Nw - 1)];
+    const T2 cv = buf[rp((Nw - kw) & (Nw - 1))];
     T ar = cv.x * inv, ai = cv.y * inv;
     if ((kk & 1) == 0 && (kw & 1) == 0) {  // the diagonal pair {k/2, k/2}
       const int hk = kk >> 1, hw = kw >> 1;

@@ -37,54 +37,67 @@ __device__ __forceinline__ void bfly(T2 &a, T2 &b, T2 w) {
   b = o1;
 }
 
-// Stages 1..log2n of ncols transforms of length n = 2^log2n stored
-// column after column in buf (input in bit-reversed order).  Stages go in
+// Shared-memory layouts.  One transform (a row): element i at rp(i) = i +
+// i / 64 -- the pad spreads over the banks both the bit-reversed scatter of a
+// row's first entries (multiples of n / 32 apart) and the stride-4 groups of
+// the first radix-4 stage pair.  Several transforms (columns): column c at
+// c (n + 1), and the threads of a stage take consecutive columns, so that
+// the lanes of a warp meet different banks in every stage.
+__host__ __device__ constexpr int fft_row_len(int n) { return n + (n >> 6); }
+__host__ __device__ constexpr int fft_col_stride(int n) { return n + 1; }
+__device__ __forceinline__ int rp(int i) { return i + (i >> 6); }
+
+// Stages 1..log2n of transforms of length n = 2^log2n in buf (input in
+// bit-reversed order): one padded row (COLS = false, ncols = 1), or ncols
+// (a power of two, 1 allowed) columns of stride n + 1 (COLS = true).  Stages go in
 // pairs (s, s + 1) held in registers: four elements j, j + h, j + 2h, j + 3h
 // of a block of 4h (h = 2^(s-1)) take the two butterflies of stage s and the
 // two of stage s + 1 -- the same butterflies, in the same order, as one
 // stage at a time, with half the shared-memory round trips and barriers.
 // An odd last stage runs alone.
-template <typename T2>
+template <bool COLS, typename T2>
 __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ twp) {
-  const int n = 1 << log2n;
+  const int n = 1 << log2n, cs = fft_col_stride(n), lc = __ffs(ncols) - 1;
+  auto at = [&](int col, int i) { return COLS ? col * cs + i : rp(i); };
   int s = 1;
   for (; s + 1 <= log2n; s += 2) {
     const int half = 1 << (s - 1);
-    const int quarter_n = n >> 2;
-    const int total = ncols * quarter_n;
+    const int total = ncols * (n >> 2);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int col = t >> (log2n - 2);
-      const int g = t & (quarter_n - 1);
+      const int col = t & (ncols - 1);
+      const int g = t >> lc;
       const int blk = g >> (s - 1);
       const int j = g & (half - 1);
-      const int i0 = col * n + blk * 4 * half + j;
-      T2 e0 = buf[i0], e1 = buf[i0 + half], e2 = buf[i0 + 2 * half], e3 = buf[i0 + 3 * half];
+      const int i0 = blk * 4 * half + j;
+      const int a0 = at(col, i0), a1 = at(col, i0 + half), a2 = at(col, i0 + 2 * half),
+                a3 = at(col, i0 + 3 * half);
+      T2 e0 = buf[a0], e1 = buf[a1], e2 = buf[a2], e3 = buf[a3];
       const T2 ws = twp[half - 1 + j];
       bfly(e0, e1, ws);
       bfly(e2, e3, ws);
       bfly(e0, e2, twp[2 * half - 1 + j]);
       bfly(e1, e3, twp[3 * half - 1 + j]);
-      buf[i0] = e0;
-      buf[i0 + half] = e1;
-      buf[i0 + 2 * half] = e2;
-      buf[i0 + 3 * half] = e3;
+      buf[a0] = e0;
+      buf[a1] = e1;
+      buf[a2] = e2;
+      buf[a3] = e3;
     }
     __syncthreads();
   }
   if (s == log2n) {  // odd number of stages: the last one alone
     const int half = 1 << (s - 1);
-    const int halfn = n >> 1;
-    const int total = ncols * halfn;
+    const int total = ncols * (n >> 1);
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int col = t >> (log2n - 1);
-      const int bf = t & (halfn - 1);
+      const int col = t & (ncols - 1);
+      const int bf = t >> lc;
       const int grp = bf >> (s - 1);
       const int j = bf & (half - 1);
-      const int i0 = col * n + grp * 2 * half + j;
-      T2 a = buf[i0], b = buf[i0 + half];
+      const int i0 = grp * 2 * half + j;
+      const int a0 = at(col, i0), a1 = at(col, i0 + half);
+      T2 a = buf[a0], b = buf[a1];
       bfly(a, b, twp[half - 1 + j]);
-      buf[i0] = a;
-      buf[i0 + half] = b;
+      buf[a0] = a;
+      buf[a1] = b;
     }
     __syncthreads();
   }
@@ -100,18 +113,18 @@ __global__ void k_fft_t(int nk, int nw, int nt, int log2nt,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *buf = reinterpret_cast<T2 *>(smem_raw);
   const int kk = blockIdx.x, n = blockIdx.y;
-  for (int m = threadIdx.x; m < nt; m += blockDim.x) {
+  for (int m = threadIdx.x; m < fft_row_len(nt); m += blockDim.x) {
     buf[m].x = 0;
     buf[m].y = 0;
   }
   __syncthreads();
   const T2 *Cp = C + ((size_t)(2 * n) * nk + kk) * nw;
   const T2 *Cm = C + ((size_t)(2 * n + 1) * nk + kk) * nw;
-  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) buf[brev(kw, log2nt)] = Cp[kw];
+  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) buf[rp(brev(kw, log2nt))] = Cp[kw];
   __syncthreads();
   for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) {
     const int m = kw == 0 ? 0 : nt - kw;
-    const int pos = brev(m, log2nt);
+    const int pos = rp(brev(m, log2nt));
     T2 v = buf[pos];
     const T2 c = Cm[kw];
     v.x += c.x;
@@ -119,9 +132,9 @@ __global__ void k_fft_t(int nk, int nw, int nt, int log2nt,
     buf[pos] = v;
   }
   __syncthreads();
-  fft_stages(buf, 1, log2nt, tw);
+  fft_stages<false>(buf, 1, log2nt, tw);
   T2 *Hrow = H + ((size_t)n * nk + kk) * nt;
-  for (int m = threadIdx.x; m < nt; m += blockDim.x) Hrow[m] = buf[m];
+  for (int m = threadIdx.x; m < nt; m += blockDim.x) Hrow[m] = buf[rp(m)];
 }
 
 template <typename T, typename T2>
@@ -129,8 +142,8 @@ __global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int TC,
                         const T2 *__restrict__ H, const T2 *__restrict__ tw, T *__restrict__ u) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *buf = reinterpret_cast<T2 *>(smem_raw);
-  const int mt0 = blockIdx.x * TC, n = blockIdx.y;
-  for (int i = threadIdx.x; i < TC * nx; i += blockDim.x) {
+  const int mt0 = blockIdx.x * TC, n = blockIdx.y, cs = fft_col_stride(nx);
+  for (int i = threadIdx.x; i < TC * cs; i += blockDim.x) {
     buf[i].x = 0;
     buf[i].y = 0;
   }
@@ -138,14 +151,14 @@ __global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int TC,
   const T2 *Hn = H + (size_t)n * nk * nt + mt0;
   for (int idx = threadIdx.x; idx < nk * TC; idx += blockDim.x) {
     const int kk = idx / TC, c = idx - kk * TC;
-    buf[c * nx + brev(kk, log2nx)] = Hn[(size_t)kk * nt + c];
+    buf[c * cs + brev(kk, log2nx)] = Hn[(size_t)kk * nt + c];
   }
   __syncthreads();
-  fft_stages(buf, TC, log2nx, tw);
+  fft_stages<true>(buf, TC, log2nx, tw);
   T *un = u + (size_t)n * nx * nt + mt0;
   for (int idx = threadIdx.x; idx < nx * TC; idx += blockDim.x) {
     const int mx = idx / TC, c = idx - mx * TC;
-    un[(size_t)mx * nt + c] = buf[c * nx + mx].x;
+    un[(size_t)mx * nt + c] = buf[c * cs + mx].x;
   }
 }
 

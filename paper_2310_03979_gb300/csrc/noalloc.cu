@@ -66,10 +66,10 @@ struct DeviceGuard {
 template <typename T, typename T2>
 int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
   const size_t e2 = sizeof(T2);
-  const size_t smem_t = (size_t)p->nt * e2;
+  const size_t smem_t = (size_t)fft_row_len(p->nt) * e2;
   int TC = 16;
-  while (TC > 1 && ((size_t)TC * p->nx * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
-  const size_t smem_x = (size_t)TC * p->nx * e2;
+  while (TC > 1 && ((size_t)TC * fft_col_stride(p->nx) * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
+  const size_t smem_x = (size_t)TC * fft_col_stride(p->nx) * e2;
   const int lim = 200 * 1024;
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));

@@ -249,7 +249,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
     int log2Nc = 1;
     while ((1 << log2Nc) < nk + std::min(L2max, nk) - 1) ++log2Nc;
     const int cap = kRecSmem / (int)sizeof(double2);  // FP64 is the tighter case
-    if (nlev > kRecBL && (1 << log2Nc) <= cap && L2max <= cap) {
+    if (nlev > kRecBL && fft_row_len(1 << log2Nc) <= cap && fft_col_stride(L2max) <= cap) {
       const int ntw = std::max(1 << log2Nc, L2max);
       p->rec_fft = true;
       p->rec_log2Nc = log2Nc;

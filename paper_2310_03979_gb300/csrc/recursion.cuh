@@ -405,47 +405,48 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
       T2 v;
       v.x = o < L ? sep_h<T, M>(A, l0 + o, kk, m) : (T)0;
       v.y = l0 > 0 ? sep_h<T, M>(A, o, kk, m) : (T)0;
-      buf[brev(kk, A.log2Nc)] = v;
+      buf[rp(brev(kk, A.log2Nc))] = v;
     }
     __syncthreads();
-    fft_stages(buf, 1, A.log2Nc, tw);
-    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) row[kk] = buf[kk];
+    fft_stages<false>(buf, 1, A.log2Nc, tw);
+    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) row[kk] = buf[rp(kk)];
     __syncthreads();
   }
   if (!grid_barrier(A.bar, A.abort, nb * g++)) return false;
   // columns: along o, square, along o, store at negated o (rows [L, 2L)),
   // TC columns per CTA: enough groups for every CTA where there are columns
   // for them (the FP64 pipe of one SM would otherwise carry a whole product)
-  int TC = min(Nc, A.zcap >> (log2L + 1));
-  while (TC > 1 && (Nc / TC) * M < (int)gridDim.x) TC >>= 1;
+  const int cs = fft_col_stride(L2);
+  int TC = Nc;
+  while (TC > 1 && (TC * cs > A.zcap || (Nc / TC) * M < (int)gridDim.x)) TC >>= 1;
   const int ng = Nc / TC;
   for (int it = blockIdx.x; it < ng * M; it += gridDim.x) {
     const int m = it / ng, c0 = (it - m * ng) * TC;
     T2 *base = Z + (size_t)m * L2 * Nc + c0;
     for (int t = threadIdx.x; t < L2 * TC; t += blockDim.x) {
       const int r = t / TC, c = t - r * TC;
-      buf[c * L2 + brev(r, log2L + 1)] = base[(size_t)r * Nc + c];
+      buf[c * cs + brev(r, log2L + 1)] = base[(size_t)r * Nc + c];
     }
     __syncthreads();
-    fft_stages(buf, TC, log2L + 1, tw);
+    fft_stages<true>(buf, TC, log2L + 1, tw);
     for (int t = threadIdx.x; t < L2 * TC; t += blockDim.x) {
       const int c = t >> (log2L + 1), r = t & (L2 - 1), rb = brev(r, log2L + 1);
       if (r <= rb) {
-        const T2 a = buf[c * L2 + r], b = buf[c * L2 + rb];
+        const T2 a = buf[c * cs + r], b = buf[c * cs + rb];
         T2 a2, b2;
         a2.x = a.x * a.x - a.y * a.y;
         a2.y = 2 * a.x * a.y;
         b2.x = b.x * b.x - b.y * b.y;
         b2.y = 2 * b.x * b.y;
-        buf[c * L2 + r] = b2;
-        buf[c * L2 + rb] = a2;
+        buf[c * cs + r] = b2;
+        buf[c * cs + rb] = a2;
       }
     }
     __syncthreads();
-    fft_stages(buf, TC, log2L + 1, tw);
+    fft_stages<true>(buf, TC, log2L + 1, tw);
     for (int t = threadIdx.x; t < L * TC; t += blockDim.x) {
       const int r = L + t / TC, c = t % TC;
-      base[(size_t)r * Nc + c] = buf[c * L2 + ((L2 - r) & (L2 - 1))];
+      base[(size_t)r * Nc + c] = buf[c * cs + ((L2 - r) & (L2 - 1))];
     }
     __syncthreads();
   }
@@ -457,12 +458,12 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
     const int m = it / L, o = L + (it - m * L), d = l0 + o;
     if (d >= A.nlev) continue;  // uniform over the CTA
     const T2 *row = Z + ((size_t)m * L2 + o) * Nc;
-    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) buf[brev(kk, A.log2Nc)] = row[kk];
+    for (int kk = threadIdx.x; kk < Nc; kk += blockDim.x) buf[rp(brev(kk, A.log2Nc))] = row[kk];
     __syncthreads();
-    fft_stages(buf, 1, A.log2Nc, tw);
+    fft_stages<false>(buf, 1, A.log2Nc, tw);
     const int kk0 = max(0, d - A.nw + 1), kk1 = min(d, A.nk - 1);
     for (int kk = kk0 + threadIdx.x; kk <= kk1; kk += blockDim.x) {
-      const T2 v = buf[(Nc - kk) & (Nc - 1)];
+      const T2 v = buf[rp((Nc - kk) & (Nc - 1))];
       ac[((long long)kk * A.nw + (d - kk)) * M + m] += (l0 > 0 ? v.y : v.x) * inv;
     }
     __syncthreads();

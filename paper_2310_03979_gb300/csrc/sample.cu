@@ -304,11 +304,11 @@ static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y
   const T *e = std::is_same<T, float>::value ? (const T *)p->env_e32 : (const T *)p->env_e;
   const T2 *tw = (const T2 *)p->tw_conv;
   T2 *Z = (T2 *)p->Zc;
-  const size_t srow = (size_t)p->cNw * sizeof(T2);
+  const size_t srow = (size_t)fft_row_len(p->cNw) * sizeof(T2);
   int TC = 16;
-  while (TC > 1 && (size_t)TC * p->cNk * sizeof(T2) > 96 * 1024) TC >>= 1;
+  while (TC > 1 && (size_t)TC * fft_col_stride(p->cNk) * sizeof(T2) > 96 * 1024) TC >>= 1;
   TC = std::min(TC, p->cNw);
-  const size_t scol = (size_t)TC * p->cNk * sizeof(T2);
+  const size_t scol = (size_t)TC * fft_col_stride(p->cNk) * sizeof(T2);
   if (srow > 200 * 1024 || scol > 200 * 1024)
     return fail(SRM3_ERR_NOT_SUPPORTED,
                 "separable pair sum: a padded row or column does not fit in shared memory");
@@ -359,10 +359,10 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
 template <typename T, typename T2>
 static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2 *H) {
   const size_t e2 = sizeof(T2);
-  const size_t smem_t = (size_t)p->nt * e2;
+  const size_t smem_t = (size_t)fft_row_len(p->nt) * e2;
   int TC = 16;
-  while (TC > 1 && ((size_t)TC * p->nx * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
-  const size_t smem_x = (size_t)TC * p->nx * e2;
+  while (TC > 1 && ((size_t)TC * fft_col_stride(p->nx) * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
+  const size_t smem_x = (size_t)TC * fft_col_stride(p->nx) * e2;
   const int lim = 200 * 1024;
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
