@@ -47,19 +47,21 @@ __host__ __device__ constexpr int fft_row_len(int n) { return n + (n >> 6); }
 __host__ __device__ constexpr int fft_col_stride(int n) { return n + 1; }
 __device__ __forceinline__ int rp(int i) { return i + (i >> 6); }
 
-// Stages 1..log2n of transforms of length n = 2^log2n in buf (input in
+// Stages s0..log2n of transforms of length n = 2^log2n in buf (input in
 // bit-reversed order): one padded row (COLS = false, ncols = 1), or ncols
-// (a power of two, 1 allowed) columns of stride n + 1 (COLS = true).  Stages go in
+// (a power of two, 1 allowed) columns of stride n + 1 (COLS = true).  s0 > 1
+// when the caller has done stages 1..s0-1 itself.  Stages go in
 // pairs (s, s + 1) held in registers: four elements j, j + h, j + 2h, j + 3h
 // of a block of 4h (h = 2^(s-1)) take the two butterflies of stage s and the
 // two of stage s + 1 -- the same butterflies, in the same order, as one
 // stage at a time, with half the shared-memory round trips and barriers.
 // An odd last stage runs alone.
 template <bool COLS, typename T2>
-__device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ twp) {
+__device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__ twp,
+                           int s0 = 1) {
   const int n = 1 << log2n, cs = fft_col_stride(n), lc = __ffs(ncols) - 1;
   auto at = [&](int col, int i) { return COLS ? col * cs + i : rp(i); };
-  int s = 1;
+  int s = s0;
   for (; s + 1 <= log2n; s += 2) {
     const int half = 1 << (s - 1);
     const int total = ncols * (n >> 2);
@@ -143,18 +145,27 @@ __global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int TC,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T2 *buf = reinterpret_cast<T2 *>(smem_raw);
   const int mt0 = blockIdx.x * TC, n = blockIdx.y, cs = fft_col_stride(nx);
-  for (int i = threadIdx.x; i < TC * cs; i += blockDim.x) {
-    buf[i].x = 0;
-    buf[i].y = 0;
-  }
-  __syncthreads();
+  // Inputs kk >= nk are zero.  With nk <= nkp = 2^q, the entries x[kk +
+  // j nkp] (j < 2^r, r = log2nx - q) sit at bit-reversed positions brev(kk)
+  // + brev_r(j), one aligned group of 2^r, and only j = 0 is nonzero; the
+  // first r stages of butterflies turn such a group into 2^r copies of
+  // x[kk].  The copies are written here and the stages start at r + 1;
+  // every position is written, so the buffer needs no clearing.
+  int q = 0;
+  while ((1 << q) < nk) ++q;
+  const int r = log2nx - q, rep = 1 << r;
   const T2 *Hn = H + (size_t)n * nk * nt + mt0;
-  for (int idx = threadIdx.x; idx < nk * TC; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < (TC << q); idx += blockDim.x) {
     const int kk = idx / TC, c = idx - kk * TC;
-    buf[c * cs + brev(kk, log2nx)] = Hn[(size_t)kk * nt + c];
+    T2 v;
+    v.x = 0;
+    v.y = 0;
+    if (kk < nk) v = Hn[(size_t)kk * nt + c];
+    T2 *dst = buf + c * cs + brev(kk, log2nx);
+    for (int j = 0; j < rep; ++j) dst[j] = v;
   }
   __syncthreads();
-  fft_stages<true>(buf, TC, log2nx, tw);
+  fft_stages<true>(buf, TC, log2nx, tw, r + 1);
   T *un = u + (size_t)n * nx * nt + mt0;
   for (int idx = threadIdx.x; idx < nx * TC; idx += blockDim.x) {
     const int mx = idx / TC, c = idx - mx * TC;
