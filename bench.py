@@ -37,7 +37,7 @@ METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 l
 # coefficient count (x 4): profiles/
 # pairsum_f32p_table_128x256.md.  Valid only for the kernel source it was
 # measured on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
-PAIRSUM_TRAFFIC = {"bytes": 644.36e6 * 15.64 + 32.28e6 * 4, "source_sha256": "1159029efd5ed3a2"}
+PAIRSUM_TRAFFIC = {"bytes": 665.51e6 * 15.41 + 31.88e6 * 4, "source_sha256": "564a3068d1dd846a"}
 FP32_LANES_PER_SM = 128
 N_SM = 152
 

@@ -83,11 +83,13 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
 // and 48 y_b rows (47 used) of the group with four TMA tile loads of 16 rows
 // x 512 bytes through a 2-D tensor map over y (rows outside the lattice read
 // the zero padding of y) into one of two stages, signalled by an mbarrier
-// with a transaction count.  TABLE: the chunk's W rows go to shared memory
-// as they are (loaded one chunk ahead, through registers), four weights per
-// 16-byte load on the compute side, each paired with itself (w, w) in
-// registers for the packed products -- half the shared-memory loads of
-// storing the pairs, worth 4 % of the launch; otherwise the chunk's
+// with a transaction count.  TABLE: the chunk's W rows of each tile reaching
+// the chunk arrive on the same mbarrier by one 512-byte bulk copy per tile
+// (the table is chunk-major; the producer's register round trip it replaced
+// cost 3 % of the launch), four weights per 16-byte load on the compute side,
+// each paired with itself (w, w) in registers for the packed products --
+// half the shared-memory loads of storing the pairs, worth 4 % of the launch;
+// otherwise the chunk's
 // 64-entry window of the omega envelope table Ew is bulk-copied, w =
 // Ew[2 iw - kw], each weight paired with itself in registers as above, with the kappa factor Ek[kk - 2a] applied
 // per row pair and c_k at the end.
@@ -145,9 +147,8 @@ constexpr int STAGE_Y = YROWS * LANES;    // float4 per stage
 constexpr int STAGE_W = NC * R * CH;      // float2 slots per stage (W: the first half)
 constexpr int EWIN = 64;                  // (w, w) pairs per stage, envelope
 constexpr int NK = 4 * R;                 // Kahan sums per compute thread
-constexpr int WPL = STAGE_W / 4 / 32;     // float4 of W per producer lane (4)
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
-static_assert(WPL * 4 * 32 == STAGE_W && WPL == NC, "W of a chunk: one tile per float4 slot");
+static_assert(kTileU == CH && kTileR == R, "W table chunks: one 512-byte span per tile");
 static_assert(2 * (CH - 1) + SW <= EWIN && EWIN <= STAGE_W, "envelope window of a chunk");
 static_assert(NB * U == CH && (NE % 2) == 0 && CH == BOX_ROWS, "block shape");
 static_assert(kPad >= SW + CH + 1, "staged rows stay inside the zero padding of y");
@@ -377,40 +378,6 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
 
   if (warp == NC) {
     // ---------------- producer ----------------
-    // W prefetch iterator (table plans): the chunk after the one being staged
-    int wk = 0, wu = ps_unit_id(0, blockIdx.x, gridDim.x), wa = 0, wc = 0;
-    int4 wun = wu < nunits ? ps_get_unit(wu, d0, units) : make_int4(0, 0, 0, 0);
-    float4 wr[WPL];
-    auto w_load = [&]() {  // W rows of chunk (wun, wa, wc) into registers
-#pragma unroll
-      for (int h = 0; h < WPL; ++h) wr[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (wu >= nunits) return;
-      const PsDesc &d = descs ? descs[wun.x] : d0;
-      if (!d.table) return;
-#pragma unroll
-      for (int h = 0; h < WPL; ++h) {
-        const int f = lane + 32 * h;  // float4 number: tile f >> 5, row (f >> 2) & 7
-        const int t = f >> 5, r = (f >> 2) & 7, iw = wc * CH + 4 * (f & 3);
-        const int k0 = wun.z + R * t;
-        const int L = ((k0 + R + kTileU - 1) / kTileU) * kTileU;
-        if (k0 < d.nw && iw < L) {
-          const long long base = d.toff[wun.y * d.ntw + k0 / R];
-          wr[h] = __ldg(
-              reinterpret_cast<const float4 *>(d.W + base + ((long long)wa * R + r) * L + iw));
-        }
-      }
-    };
-    auto w_next = [&]() {
-      if (++wc == (wun.z + SW + CH - 1) / CH) {
-        wc = 0;
-        if (++wa >= ps_rowsteps(wun.y, MIXED ? (descs ? descs[wun.x] : d0).half : 0)) {
-          wa = 0;
-          wu = ps_unit_id(++wk, blockIdx.x, gridDim.x);
-          if (wu < nunits) wun = ps_get_unit(wu, d0, units);
-        }
-      }
-    };
-    w_load();
     unsigned q = 0;
     bool ok = true;
     for (int k = 0; ok; ++k) {
@@ -421,7 +388,6 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
       const int half = MIXED ? d.half : 0;
       const int nitems = ps_nitems(kk, kws0, half), tab = d.table, rs = d.rowstride;
-      const unsigned tx = YROWS * ROW_BYTES + (tab ? 0 : EWIN * (unsigned)sizeof(float));
       const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
       for (int item = 0; item < nitems; ++item, ++q) {
@@ -432,6 +398,17 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
         }
         const int i0 = c * CH;
         if (lane == 0) {
+          // TABLE: the chunk's W rows of each tile whose rows reach it, one
+          // contiguous 512-byte span per tile (the table is chunk-major)
+          int ntile = 0;
+          if (tab)
+            for (int t = 0; t < NC; ++t) {
+              const int k0 = kws0 + R * t;
+              if (k0 < d.nw && c * CH < ((k0 + R + kTileU - 1) / kTileU) * kTileU) ++ntile;
+            }
+          const unsigned tx = YROWS * ROW_BYTES +
+                              (tab ? ntile * R * CH * (unsigned)sizeof(float)
+                                   : EWIN * (unsigned)sizeof(float));
           mbar_expect_tx(&full[stage], tx);
           // one row pair (full rows), or two in half mode (half rows each; a
           // second row pair past the centre repeats the first and is
@@ -447,22 +424,21 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
               tma_load_2d(dst + (CH + BOX_ROWS * j) * rw, &d.ymap, x, jrow + BOX_ROWS * j,
                           &full[stage]);
           }
-          if (!tab)
+          if (!tab) {
             bulk_g2s(sw + stage * STAGE_W, d.Ew + d.ew_off + 2 * i0 - kws0 - (SW - 1),
                      EWIN * sizeof(float), &full[stage]);
-        }
-        if (tab) {
-#pragma unroll
-          for (int h = 0; h < WPL; ++h) {
-            const int f = lane + 32 * h;
-            float4 *dw = reinterpret_cast<float4 *>(
-                reinterpret_cast<float *>(sw + stage * STAGE_W) +
-                ((f >> 5) * R + ((f >> 2) & 7)) * CH + 4 * (f & 3));
-            *dw = wr[h];
+          } else {
+            for (int t = 0; t < NC; ++t) {  // the tiles counted above
+              const int k0 = kws0 + R * t;
+              const int ncht = ((k0 + R + kTileU - 1) / kTileU) * kTileU / CH;
+              if (k0 >= d.nw || c >= ncht) continue;
+              const long long base = d.toff[kk * d.ntw + k0 / R];
+              bulk_g2s(reinterpret_cast<float *>(sw + stage * STAGE_W) + t * R * CH,
+                       d.W + base + ((long long)a * ncht + c) * R * CH,
+                       R * CH * (unsigned)sizeof(float), &full[stage]);
+            }
           }
         }
-        w_next();
-        w_load();
         mbar_arrive(&full[stage]);
         if (++c == nch) {
           c = 0;
@@ -547,8 +523,11 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
             if ((kw & 1) == 0 && kw < nw) {
               const float4 h = d.y[((size_t)ah * d.rowstride + kPad + (kw >> 1)) * SP +
                                    (size_t)grp * LANES + ln];
-              const float w0 = tab ? d.W[my_base + ((long long)ah * R + r) * my_L + (kw >> 1)]
-                                   : d.Ew[d.ew_off];
+              const float w0 =
+                  tab ? d.W[my_base +
+                            (((long long)ah * (my_L / CH) + ((kw >> 1) / CH)) * R + r) * CH +
+                            ((kw >> 1) % CH)]
+                      : d.Ew[d.ew_off];
               v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
               v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
               v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));

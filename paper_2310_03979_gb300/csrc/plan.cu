@@ -167,12 +167,14 @@ __global__ void k_twiddles(int n, int log2n, T2 *tw) {
   tw[idx] = v;
 }
 
-// W table, tile-major: for tile (kk, kw0): rows a = 0..kk/2, then r < R,
-// then iw < L (L = kw0 + R rounded up to U); W = c_k Ek[kk-2a] Ew[2iw-kw]
-// for iw <= kw < nw, else 0.  Centre rows are stored in full (the kernel
-// halves them).  W is real: the constant biphase is applied afterwards.
-// One CTA per tile: thread rows take table rows (a, r), lanes take float4
-// column groups.
+// W table, tile-major: for tile (kk, kw0), entry (a, r, iw) -- row pair
+// a = 0..kk/2, output kw = kw0 + r, r < R, iw < L (L = kw0 + R rounded up to
+// U) -- at ((a nch + iw / U) R + r) U + iw % U, nch = L / U: chunk-major, so
+// the R rows of one omega chunk are one contiguous span the pair sum fetches
+// with a single bulk copy.  W = c_k Ek[kk-2a] Ew[2iw-kw] for iw <= kw < nw,
+// else 0.  Centre rows are stored in full (the kernel halves them).  W is
+// real: the constant biphase is applied afterwards.  One CTA per tile, its
+// threads writing the tile's float4 in storage order.
 __global__ void __launch_bounds__(256) k_build_w(int nk, int nw, int ntw,
                                                  const long long *__restrict__ off,
                                                  const float *__restrict__ ck,
@@ -184,23 +186,24 @@ __global__ void __launch_bounds__(256) k_build_w(int nk, int nw, int ntw,
   const int kw0 = tw * kTileR;
   const int nrow = kk / 2 + 1;
   const int L = ((kw0 + kTileR + kTileU - 1) / kTileU) * kTileU;
-  const int L4 = L / 4;
+  const int nch = L / kTileU;
+  constexpr int V = kTileU / 4;  // float4 per chunk row
   float4 *dst = reinterpret_cast<float4 *>(W + off[t]);
-  for (int row = threadIdx.y; row < nrow * kTileR; row += blockDim.y) {
-    const int a = row / kTileR, r = row - a * kTileR;
-    const int kw = kw0 + r;
-    const float f = kw < nw ? ck[kk * nw + kw] * Ek[kk - 2 * a] : 0.0f;
+  // float4 number f of the tile in storage order: (a nch + c, r, v)
+  const int nf = nrow * nch * kTileR * V;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int f = tid; f < nf; f += nth) {
+    const int v = f % V, r = (f / V) % kTileR, ac = f / (V * kTileR);
+    const int a = ac / nch, c = ac - a * nch;
+    const int kw = kw0 + r, iw = c * kTileU + 4 * v;
+    const float g = kw < nw ? ck[kk * nw + kw] * Ek[kk - 2 * a] : 0.0f;
     const float *e = Ews + ew_off - kw;
-    float4 *drow = dst + (size_t)row * L4;
-    for (int c = threadIdx.x; c < L4; c += blockDim.x) {
-      const int iw = 4 * c;
-      float4 v;
-      v.x = (iw + 0 <= kw) ? f * e[2 * (iw + 0)] : 0.0f;
-      v.y = (iw + 1 <= kw) ? f * e[2 * (iw + 1)] : 0.0f;
-      v.z = (iw + 2 <= kw) ? f * e[2 * (iw + 2)] : 0.0f;
-      v.w = (iw + 3 <= kw) ? f * e[2 * (iw + 3)] : 0.0f;
-      drow[c] = v;
-    }
+    float4 w;
+    w.x = (iw + 0 <= kw) ? g * e[2 * (iw + 0)] : 0.0f;
+    w.y = (iw + 1 <= kw) ? g * e[2 * (iw + 1)] : 0.0f;
+    w.z = (iw + 2 <= kw) ? g * e[2 * (iw + 2)] : 0.0f;
+    w.w = (iw + 3 <= kw) ? g * e[2 * (iw + 3)] : 0.0f;
+    dst[f] = w;
   }
 }
 

@@ -27,11 +27,15 @@ struct Vec2<double> {
 };
 
 // Tile shape of the FP32 pair sum: R outputs along omega per thread; the W
-// table rows of a tile are padded to a multiple of kTileU.  The y rows carry
+// table rows of a tile are padded to a multiple of kTileU (the pair sum's
+// omega chunk) and stored chunk-major: entry (a, r, iw) of a tile at
+// ((a nch + iw / kTileU) kTileR + r) kTileU + iw % kTileU, nch = L / kTileU,
+// so that the kTileR rows of one chunk are one contiguous 512-byte span.
+// The y rows carry
 // kPad zero entries on both sides: every row the FP32 pair sum stages lies
 // within omega index [-31, nw + 30], so its copies need no bounds checks.
 constexpr int kTileR = 8;
-constexpr int kTileU = 8;
+constexpr int kTileU = 16;
 constexpr int kPad = 64;
 constexpr int kMaxChunk = 128;     // samples per internal launch chunk
 constexpr int kWarpsPerCta = 4;    // FP32 pair-sum CTA: 4 warps = 4 work units
