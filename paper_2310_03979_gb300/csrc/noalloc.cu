@@ -76,7 +76,7 @@ int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
   k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt, C,
                                                           (const T2 *)p->tw, H);
   SRM3_CUDA(cudaGetLastError());
-  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, p->stream>>>(
+  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 512, smem_x, p->stream>>>(
       p->nk, p->nx, p->nt, p->log2nx, TC, H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;

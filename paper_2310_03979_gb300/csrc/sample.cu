@@ -320,7 +320,7 @@ static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y
                                  (int)srow));
   k_conv_rows<T><<<dim3(p->nk, SS), 256, srow, st>>>(p->nk, p->nw, p->log2cNw, p->cNk, sp,
                                                       p->rowstride, y, e, tw, Z);
-  k_conv_cols<T><<<dim3(p->cNw / TC, SS), 256, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
+  k_conv_cols<T><<<dim3(p->cNw / TC, SS), 512, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
                                                             Z);
   const T *eb = std::is_same<T, float>::value ? (const T *)p->env_b32 : (const T *)p->env_b;
   k_conv_out<T><<<dim3(p->nk, SS), 256, srow, st>>>(
@@ -369,7 +369,7 @@ static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *
   k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt, C,
                                                           (const T2 *)p->tw, H);
   SRM3_CUDA(cudaGetLastError());
-  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 256, smem_x, st>>>(
+  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 512, smem_x, st>>>(
       p->nk, p->nx, p->nt, p->log2nx, TC, (const T2 *)H, (const T2 *)p->tw, out);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
