@@ -239,6 +239,25 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaMalloc(&p->rec_lev_off, sizeof(int) * (nlev + 1)));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
                             cudaMemcpyHostToDevice, st));
+  // bulk phase D = ph BL: the points of levels [D, min(2D, nlev)) as pairs
+  // (kk, kw), (kk, kw + 1) along each lattice row
+  std::vector<int2> pairs;
+  std::vector<int> pair_off(1, 0);
+  for (int D = kRecBL; D < nlev; D += kRecBL) {
+    const int dend = std::min(2 * D, nlev);
+    for (int kk = 0; kk < nk; ++kk) {
+      const int lo = std::max(0, D - kk), hi = std::min(nw - 1, dend - 1 - kk);
+      for (int kw = lo; kw <= hi; kw += 2) pairs.push_back(make_int2(kk, kw));
+    }
+    pair_off.push_back((int)pairs.size());
+  }
+  if (pairs.empty()) pairs.push_back(make_int2(0, 0));
+  SRM3_CUDA(cudaMalloc(&p->rec_pairs, sizeof(int2) * pairs.size()));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_pairs, pairs.data(), sizeof(int2) * pairs.size(),
+                            cudaMemcpyHostToDevice, st));
+  SRM3_CUDA(cudaMalloc(&p->rec_pair_off, sizeof(int) * pair_off.size()));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_pair_off, pair_off.data(), sizeof(int) * pair_off.size(),
+                            cudaMemcpyHostToDevice, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
   SRM3_CUDA(cudaMalloc(&p->rec_max, kPlanes * sizeof(unsigned long long)));
@@ -320,6 +339,8 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.nl = (long long)p->nk * p->nw;
   A.pts = p->rec_items;
   A.pt_off = p->rec_lev_off;
+  A.pairs = p->rec_pairs;
+  A.pair_off = p->rec_pair_off;
   A.S = p->S;
   if (p->sep && fp64 && M != 1)
     return fail(SRM3_ERR_NOT_SUPPORTED, "separable envelope: one-plane FP64 passes only");
@@ -936,6 +957,7 @@ void free_plan(srm3_plan *p) {
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
+                 p->rec_pairs, p->rec_pair_off,
                  p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,

@@ -18,6 +18,11 @@ struct RecArgs {
   long long nl;
   const int2 *pts;      // lattice points in level order (level-major, kk ascending)
   const int *pt_off;    // first point of each level, nlev + 1 entries
+  // bulk phase ph (D = ph BL) works on point pairs (kk, kw), (kk, kw + 1)
+  // of its band of levels [D, min(2D, nlev)): starts pairs[pair_off[ph - 1]
+  // .. pair_off[ph])
+  const int2 *pairs;
+  const int *pair_off;
   const double *S;
   void *q;              // [nl][M] of T: q = S/S_p (0 where S = 0), plane fastest
   void *acc;            // [nl][M] of T: pair sums gathered by the bulk phases
@@ -280,6 +285,109 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   }
 }
 
+// Bulk of two neighbouring points of a lattice row, k0 = (kk, kw) and
+// k1 = (kk, kw + 1) (has1: k1 lies in the phase's band).  In both slivers
+// the pair's element on the levels [D - BL, D) -- the higher one -- is the
+// same for the two points at a given (row a, slot u), and their other
+// elements are lattice neighbours (0, 1) apart: one load of the higher
+// element and two adjacent loads of the lower ones serve both points, a
+// quarter less traffic per pair than one point at a time.  RIGHT: the
+// higher element is i = (a, base - a + u); else it is j = (kk - a, base -
+// (kk - a) + u).  Rows a run over the union of the two points' ranges, the
+// lanes of row parity rs taking every other row; each point keeps its own
+// limits (the sliver's u and row ranges, i != 0, the centre row, iw <= kw),
+// a masked slot reading point (0, 0) with weight 0.
+constexpr int kPairUnroll = 2;
+
+template <bool RIGHT, typename T, int M>
+__device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__restrict__ G2,
+                                           const T *__restrict__ q, int base, int u, int rs,
+                                           const int (&alo)[2], const int (&ahi)[2],
+                                           const bool (&uok)[2], T (&acc0)[M], T (&acc1)[M]) {
+  const int a_first = min(alo[0], alo[1]), a_last = max(ahi[0], ahi[1]);
+  for (int a00 = a_first + rs; a00 <= a_last; a00 += 2 * kPairUnroll) {
+    T g2[kPairUnroll][2], vh[kPairUnroll][M], vl[kPairUnroll][2][M];
+#pragma unroll
+    for (int s = 0; s < kPairUnroll; ++s) {
+      const int a = a00 + 2 * s, b = kk - a;
+      // higher element (shared) and the lower elements' omega for point p
+      const int hw = RIGHT ? base - a + u : base - b + u;
+      bool okp[2];
+      int gi[2], ql[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int kwp = kw + p;
+        const int iw = RIGHT ? hw : kwp - hw;  // omega of i = (a, iw)
+        okp[p] = uok[p] && a >= alo[p] && a <= ahi[p] && iw >= (a == 0 ? 1 : 0) &&
+                 iw <= ((a == b) ? kwp / 2 : kwp) && iw <= kwp;
+        const int dk = 2 * a - kk, dw = 2 * iw - kwp;
+        gi[p] = okp[p] ? (dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+        // the lower element: j = k_p - i (RIGHT) or i itself
+        ql[p] = okp[p] ? (RIGHT ? (b * nw + (kwp - iw)) * M : (a * nw + iw) * M) : 0;
+      }
+      const bool any = okp[0] || okp[1];
+      const int qh = any ? (RIGHT ? (a * nw + hw) * M : (b * nw + hw) * M) : 0;
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        g2[s][p] = okp[p] ? G2[gi[p]] : (T)0;
+        PlaneVec<T, M>::load(q + ql[p], vl[s][p]);
+      }
+      PlaneVec<T, M>::load(q + qh, vh[s]);
+    }
+#pragma unroll
+    for (int s = 0; s < kPairUnroll; ++s)
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        acc0[m] = fma(g2[s][0], vh[s][m] * vl[s][0][m], acc0[m]);
+        acc1[m] = fma(g2[s][1], vh[s][m] * vl[s][1][m], acc1[m]);
+      }
+  }
+}
+
+template <typename T, int M>
+__device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, int lane) {
+  const int base = D - kRecBL, arow = kk / 2 + 1, nw = A.nw;
+  const int u = lane & (kRecBL - 1), rs = lane >> 4;
+  int aRlo[2], aRhi[2], aLlo[2], aLhi[2];
+  bool uR[2], uL[2];
+  bool live[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int kwp = kw + p, d = kk + kwp;
+    live[p] = (p == 0 || has1) && A.S[(long long)kk * nw + kwp] > 0.0;
+    const int uR0 = max(0, (d + 1) / 2 - base), uL0 = max(0, d / 2 - base + 1);
+    aRlo[p] = max(0, base + uR0 - kwp);
+    aRhi[p] = min(arow - 1, D - 1);
+    aLlo[p] = max(0, kk - D + 1);
+    aLhi[p] = arow - 1;
+    uR[p] = live[p] && uR0 < kRecBL && u >= uR0;
+    uL[p] = live[p] && uL0 < kRecBL && u >= uL0;
+    if (!(live[p] && uR0 < kRecBL)) aRhi[p] = -1;  // no right rows for this point
+    if (!(live[p] && uL0 < kRecBL)) aLhi[p] = -1;
+  }
+  if (!live[0] && !live[1]) return;
+  T acc0[M], acc1[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc0[m] = acc1[m] = (T)0;
+  const T *G2 = static_cast<const T *>(A.G2);
+  const T *q = static_cast<const T *>(A.q);
+  if (max(aRhi[0], aRhi[1]) >= 0)
+    bulk_rows2<true, T, M>(kk, kw, nw, G2, q, base, u, rs, aRlo, aRhi, uR, acc0, acc1);
+  if (max(aLhi[0], aLhi[1]) >= 0)
+    bulk_rows2<false, T, M>(kk, kw, nw, G2, q, base, u, rs, aLlo, aLhi, uL, acc0, acc1);
+  warp_sum<T, M>(acc0);
+  warp_sum<T, M>(acc1);
+  if (lane == 0) {
+    T *ac = static_cast<T *>(A.acc);
+    const long long k0 = (long long)kk * nw + kw;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      if (live[0]) ac[k0 * M + m] += acc0[m];
+      if (live[1]) ac[(k0 + 1) * M + m] += acc1[m];
+    }
+  }
+}
+
 constexpr int kFringeUnroll = 4;
 
 // Fringe of a point at level d in [D, D + BL): the pairs whose higher
@@ -520,7 +628,12 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     } else {
       // bulk: warps take points in turn from the phase's ticket counter
       // (the next ticket is drawn while the current point is summed)
-      const int pb = A.pt_off[D], pe = A.pt_off[min(2 * D, A.nlev)];
+      // (the FP32 search pass, bound by its q loads, takes the points in
+      // pairs; the FP64 pass, bound by its FP64 pipe, one at a time)
+      constexpr bool kPairs = sizeof(T) == sizeof(float);
+      const int pb = kPairs ? A.pair_off[ph - 1] : A.pt_off[D];
+      const int pe = kPairs ? A.pair_off[ph] : A.pt_off[min(2 * D, A.nlev)];
+      const int dend = min(2 * D, A.nlev);
       unsigned int *tk = A.bar + ph;
       int t = 0;
       if (lane == 0) t = (int)atomicAdd(tk, 1u);
@@ -528,8 +641,14 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
       while (pb + t < pe) {
         int tn = 0;
         if (lane == 0) tn = (int)atomicAdd(tk, 1u);
-        const int2 pt = A.pts[pb + t];
-        point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+        if constexpr (kPairs) {
+          const int2 pt = A.pairs[pb + t];
+          const bool has1 = pt.y + 1 <= min(A.nw - 1, dend - 1 - pt.x);
+          point2_bulk<T, M>(A, pt.x, pt.y, has1, D, lane);
+        } else {
+          const int2 pt = A.pts[pb + t];
+          point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+        }
         t = __shfl_sync(0xffffffffu, tn, 0);
       }
       if (!grid_barrier(A.bar, A.abort, nb * g++)) return;

@@ -158,6 +158,8 @@ struct srm3_plan {
   // recursion graph (one pass = every anti-diagonal level + reductions)
   // persistent recursion pass
   int *rec_lev_off = nullptr;        // first item of each level
+  int2 *rec_pairs = nullptr;         // bulk point pairs of every phase
+  int *rec_pair_off = nullptr;       // first pair of each bulk phase
   unsigned int *rec_bar = nullptr;   // grid barrier counter and bulk-phase tickets
   int rec_bar_words = 0;
   unsigned long long *rec_max = nullptr;  // per-plane max sum_b2 of a pass (bits)
