@@ -41,8 +41,9 @@ __device__ __forceinline__ void bfly(T2 &a, T2 &b, T2 w) {
 // i / 64 -- the pad spreads over the banks both the bit-reversed scatter of a
 // row's first entries (multiples of n / 32 apart) and the stride-4 groups of
 // the first radix-4 stage pair.  Several transforms (columns): column c at
-// c (n + 1), and the threads of a stage take consecutive columns, so that
-// the lanes of a warp meet different banks in every stage.
+// c (n + 1); in the stages with h < 16 consecutive threads take consecutive
+// columns (the lanes then meet different banks), in the later ones
+// consecutive butterflies of one column (contiguous runs of 16 or more).
 __host__ __device__ constexpr int fft_row_len(int n) { return n + (n >> 6); }
 __host__ __device__ constexpr int fft_col_stride(int n) { return n + 1; }
 __device__ __forceinline__ int rp(int i) { return i + (i >> 6); }
@@ -65,9 +66,10 @@ __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__
   for (; s + 1 <= log2n; s += 2) {
     const int half = 1 << (s - 1);
     const int total = ncols * (n >> 2);
+    const bool cf = COLS && half < 16;  // consecutive threads on consecutive columns
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int col = t & (ncols - 1);
-      const int g = t >> lc;
+      const int col = cf ? t & (ncols - 1) : t >> (log2n - 2);
+      const int g = cf ? t >> lc : t & ((n >> 2) - 1);
       const int blk = g >> (s - 1);
       const int j = g & (half - 1);
       const int i0 = blk * 4 * half + j;
@@ -89,9 +91,10 @@ __device__ void fft_stages(T2 *buf, int ncols, int log2n, const T2 *__restrict__
   if (s == log2n) {  // odd number of stages: the last one alone
     const int half = 1 << (s - 1);
     const int total = ncols * (n >> 1);
+    const bool cf = COLS && half < 16;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int col = t & (ncols - 1);
-      const int bf = t >> lc;
+      const int col = cf ? t & (ncols - 1) : t >> (log2n - 1);
+      const int bf = cf ? t >> lc : t & ((n >> 1) - 1);
       const int grp = bf >> (s - 1);
       const int j = bf & (half - 1);
       const int i0 = grp * 2 * half + j;
