@@ -37,16 +37,18 @@ __device__ __forceinline__ void bfly(T2 &a, T2 &b, T2 w) {
   b = o1;
 }
 
-// Shared-memory layouts.  One transform (a row): element i at rp(i) = i +
-// i / 64 -- the pad spreads over the banks both the bit-reversed scatter of a
-// row's first entries (multiples of n / 32 apart) and the stride-4 groups of
-// the first radix-4 stage pair.  Several transforms (columns): column c at
+// Shared-memory layouts.  One transform (a row): element i at rp(i) = i XOR
+// (((i >> 4) XOR (i >> 8)) & 15), a permutation of each 16-element (128-byte
+// for FP32) group by the bits above it, which spreads over the banks both
+// the bit-reversed scatter of a row's first entries (multiples of n / 32
+// apart) and the stride-4 and stride-16 groups of the first two radix-4
+// stage pairs.  Several transforms (columns): column c at
 // c (n + 1); in the stages with h < 16 consecutive threads take consecutive
 // columns (the lanes then meet different banks), in the later ones
 // consecutive butterflies of one column (contiguous runs of 16 or more).
-__host__ __device__ constexpr int fft_row_len(int n) { return n + (n >> 6); }
+__host__ __device__ constexpr int fft_row_len(int n) { return n; }
 __host__ __device__ constexpr int fft_col_stride(int n) { return n + 1; }
-__device__ __forceinline__ int rp(int i) { return i + (i >> 6); }
+__device__ __forceinline__ int rp(int i) { return i ^ (((i >> 4) ^ (i >> 8)) & 15); }
 
 // Stages s0..log2n of transforms of length n = 2^log2n in buf (input in
 // bit-reversed order): one padded row (COLS = false, ncols = 1), or ncols
