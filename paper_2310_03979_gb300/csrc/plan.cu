@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <cstdlib>
+#include <mutex>
 #include <numeric>
 
 #include "recursion.cuh"
@@ -233,10 +234,10 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
     for (int kk = lo; kk <= hi; ++kk) pts.push_back(make_int2(kk, d - kk));
   }
   lev_off[nlev] = (int)pts.size();
-  SRM3_CUDA(cudaMalloc(&p->rec_items, sizeof(int2) * pts.size()));
+  SRM3_CUDA(dev_alloc(&p->rec_items, sizeof(int2) * pts.size(), st));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_items, pts.data(), sizeof(int2) * pts.size(),
                             cudaMemcpyHostToDevice, st));
-  SRM3_CUDA(cudaMalloc(&p->rec_lev_off, sizeof(int) * (nlev + 1)));
+  SRM3_CUDA(dev_alloc(&p->rec_lev_off, sizeof(int) * (nlev + 1), st));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
                             cudaMemcpyHostToDevice, st));
   // bulk phase D = ph BL: the points of levels [D, min(2D, nlev)) as pairs
@@ -252,15 +253,15 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
     pair_off.push_back((int)pairs.size());
   }
   if (pairs.empty()) pairs.push_back(make_int2(0, 0));
-  SRM3_CUDA(cudaMalloc(&p->rec_pairs, sizeof(int2) * pairs.size()));
+  SRM3_CUDA(dev_alloc(&p->rec_pairs, sizeof(int2) * pairs.size(), st));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_pairs, pairs.data(), sizeof(int2) * pairs.size(),
                             cudaMemcpyHostToDevice, st));
-  SRM3_CUDA(cudaMalloc(&p->rec_pair_off, sizeof(int) * pair_off.size()));
+  SRM3_CUDA(dev_alloc(&p->rec_pair_off, sizeof(int) * pair_off.size(), st));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_pair_off, pair_off.data(), sizeof(int) * pair_off.size(),
                             cudaMemcpyHostToDevice, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
-  SRM3_CUDA(cudaMalloc(&p->rec_partial, (size_t)nk * nw * 32));
-  SRM3_CUDA(cudaMalloc(&p->rec_max, kPlanes * sizeof(unsigned long long)));
+  SRM3_CUDA(dev_alloc(&p->rec_partial, (size_t)nk * nw * 32, st));
+  SRM3_CUDA(dev_alloc(&p->rec_max, kPlanes * sizeof(unsigned long long), st));
   // separable envelope: the FFT form of the bulk when its grids fit the
   // pass's shared memory (else the direct bulk, as for any envelope)
   if (p->sep) {
@@ -275,10 +276,10 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
       const int ntw = std::max(1 << log2Nc, L2max);
       p->rec_fft = true;
       p->rec_log2Nc = log2Nc;
-      SRM3_CUDA(cudaMalloc(&p->rec_z, (size_t)L2max * ((size_t)1 << log2Nc) *
-                                          std::max(kPlanes * sizeof(float2), sizeof(double2))));
-      SRM3_CUDA(cudaMalloc(&p->tw_rec32, ntw * sizeof(float2)));
-      SRM3_CUDA(cudaMalloc(&p->tw_rec64, ntw * sizeof(double2)));
+      SRM3_CUDA(dev_alloc(&p->rec_z, (size_t)L2max * ((size_t)1 << log2Nc) *
+                                          std::max(kPlanes * sizeof(float2), sizeof(double2)), st));
+      SRM3_CUDA(dev_alloc(&p->tw_rec32, ntw * sizeof(float2), st));
+      SRM3_CUDA(dev_alloc(&p->tw_rec64, ntw * sizeof(double2), st));
       k_twiddles<float2><<<cdiv(ntw, 256), 256, 0, st>>>(ntw, ilog2_exact(ntw),
                                                          (float2 *)p->tw_rec32);
       k_twiddles<double2><<<cdiv(ntw, 256), 256, 0, st>>>(ntw, ilog2_exact(ntw),
@@ -301,7 +302,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaStreamSynchronize(st));
   p->sumS = p->h_pinned[11];
   p->rec_bar_words = 2 + (nk + nw) / kRecBL + 1;  // barrier counter + a ticket per bulk phase
-  SRM3_CUDA(cudaMalloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int)));
+  SRM3_CUDA(dev_alloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
   int nsm = 0, dev = 0;
   SRM3_CUDA(cudaGetDevice(&dev));
@@ -315,7 +316,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
                                                           kRecThreads, rec_smem));
   if (b64 < 1 || b64x3 < 1 || b32 < 1)
     return fail(SRM3_ERR_CUDA, "recursion kernel cannot be resident");
-  SRM3_CUDA(cudaMalloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double)));
+  SRM3_CUDA(dev_alloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double), st));
   SRM3_CUDA(cudaMemsetAsync(p->qm3, 0, 3 * (size_t)nk * nw * sizeof(double), st));
   p->rec_grid64 = nsm;
   p->rec_grid32 = nsm;
@@ -674,8 +675,8 @@ static long long tile_entries(int kk, int tw) {
 int build_w_table(srm3_plan *p, cudaStream_t st) {
   if (p->W) return SRM3_OK;
   const double bytes = (double)p->table_entries * sizeof(float);
-  cudaError_t e = cudaMalloc(&p->W, (size_t)p->table_entries * sizeof(float));
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(W table)");
+  cudaError_t e = dev_alloc(&p->W, (size_t)p->table_entries * sizeof(float), st);
+  if (e != cudaSuccess) return cuda_fail(e, "dev_alloc(W table, st)");
   cudaEvent_t ev[2];
   SRM3_CUDA(cudaEventCreate(&ev[0]));
   SRM3_CUDA(cudaEventCreate(&ev[1]));
@@ -715,7 +716,7 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
     int t = ids[i];
     order[i] = make_int2(t / p->ntw, (t % p->ntw) * kTileR);
   }
-  SRM3_CUDA(cudaMalloc(&p->tile_order, sizeof(int2) * p->ntiles));
+  SRM3_CUDA(dev_alloc(&p->tile_order, sizeof(int2) * p->ntiles, st));
   SRM3_CUDA(cudaMemcpyAsync(p->tile_order, order.data(), sizeof(int2) * p->ntiles,
                             cudaMemcpyHostToDevice, st));
   // super-tiles of kWarpsPerCta tiles (FP32 pair sum), most expensive first
@@ -727,13 +728,13 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   std::stable_sort(sup.begin(), sup.end(), [&](int2 a, int2 b) {
     return (long long)(a.x / 2 + 1) * (a.y + sw) > (long long)(b.x / 2 + 1) * (b.y + sw);
   });
-  SRM3_CUDA(cudaMalloc(&p->super_order, sizeof(int2) * p->nsuper));
+  SRM3_CUDA(dev_alloc(&p->super_order, sizeof(int2) * p->nsuper, st));
   SRM3_CUDA(cudaMemcpyAsync(p->super_order, sup.data(), sizeof(int2) * p->nsuper,
                             cudaMemcpyHostToDevice, st));
   p->super_host = sup;
   *table_entries = off[p->ntiles];
   (void)want_table;  // offsets are kept either way: the autotuner may build W later
-  SRM3_CUDA(cudaMalloc(&p->tile_off, sizeof(long long) * p->ntiles));
+  SRM3_CUDA(dev_alloc(&p->tile_off, sizeof(long long) * p->ntiles, st));
   SRM3_CUDA(cudaMemcpyAsync(p->tile_off, off.data(), sizeof(long long) * p->ntiles,
                             cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaStreamSynchronize(st));
@@ -759,17 +760,17 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
 
   SRM3_CUDA(cudaMallocHost(&p->h_pinned, (8 + 4 * kPlanes) * sizeof(double)));
   SRM3_CUDA(cudaMallocHost(&p->h_err, (kPlanes + 1) * sizeof(int)));
-  SRM3_CUDA(cudaMalloc(&p->S, nl * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->qm, nl * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->sb2, kPlanes * nl * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->EkSq, nk * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->EwSq, nw * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->scal, (8 + 4 * kPlanes) * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->err, (kPlanes + 1) * sizeof(int)));
+  SRM3_CUDA(dev_alloc(&p->S, nl * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->qm, nl * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->sb2, kPlanes * nl * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->EkSq, nk * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->EwSq, nw * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->scal, (8 + 4 * kPlanes) * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->err, (kPlanes + 1) * sizeof(int), st));
   SRM3_CUDA(cudaMemsetAsync(p->qm, 0, nl * sizeof(double), st));
-  SRM3_CUDA(cudaMalloc(&p->qm32, kPlanes * nl * sizeof(float)));
-  SRM3_CUDA(cudaMalloc(&p->EkSq32, nk * sizeof(float)));
-  SRM3_CUDA(cudaMalloc(&p->EwSq32, nw * sizeof(float)));
+  SRM3_CUDA(dev_alloc(&p->qm32, kPlanes * nl * sizeof(float), st));
+  SRM3_CUDA(dev_alloc(&p->EkSq32, nk * sizeof(float), st));
+  SRM3_CUDA(dev_alloc(&p->EwSq32, nw * sizeof(float), st));
   SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kPlanes * nl * sizeof(float), st));
 
   // a1: spectrum on the lattice
@@ -782,15 +783,15 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   }
   k_env_sq<<<cdiv(nk, 256), 256, 0, st>>>(nk, p->sigma_g * nk, p->EkSq, p->EkSq32);
   k_env_sq<<<cdiv(nw, 256), 256, 0, st>>>(nw, p->sigma_g * nw, p->EwSq, p->EwSq32);
-  SRM3_CUDA(cudaMalloc(&p->G2, nl * sizeof(double)));
-  SRM3_CUDA(cudaMalloc(&p->G2_32, nl * sizeof(float)));
+  SRM3_CUDA(dev_alloc(&p->G2, nl * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&p->G2_32, nl * sizeof(float), st));
   if (p->sep) {
     // separable envelope: the pair factor e_i^2 e_j^2 rides on h = e^2 q and
     // e_k^2 is applied when q_k is formed, so the g^2 table is all ones
-    SRM3_CUDA(cudaMalloc(&p->env_e, nl * sizeof(double)));
-    SRM3_CUDA(cudaMalloc(&p->env_e2, nl * sizeof(double)));
-    SRM3_CUDA(cudaMalloc(&p->env_e32, nl * sizeof(float)));
-    SRM3_CUDA(cudaMalloc(&p->qh, nl * sizeof(double)));
+    SRM3_CUDA(dev_alloc(&p->env_e, nl * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&p->env_e2, nl * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&p->env_e32, nl * sizeof(float), st));
+    SRM3_CUDA(dev_alloc(&p->qh, nl * sizeof(double), st));
     SRM3_CUDA(cudaMemsetAsync(p->qh, 0, nl * sizeof(double), st));
     SRM3_CUDA(cudaMemcpyAsync(p->env_e, bs->env_table, nl * sizeof(double),
                               cudaMemcpyHostToDevice, st));
@@ -798,9 +799,9 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
                                                 p->G2, p->G2_32);
     p->sep_b = bs->env_table_b != nullptr;
     if (p->sep_b) {
-      SRM3_CUDA(cudaMalloc(&p->env_b, nl * sizeof(double)));
-      SRM3_CUDA(cudaMalloc(&p->env_b2, nl * sizeof(double)));
-      SRM3_CUDA(cudaMalloc(&p->env_b32, nl * sizeof(float)));
+      SRM3_CUDA(dev_alloc(&p->env_b, nl * sizeof(double), st));
+      SRM3_CUDA(dev_alloc(&p->env_b2, nl * sizeof(double), st));
+      SRM3_CUDA(dev_alloc(&p->env_b32, nl * sizeof(float), st));
       SRM3_CUDA(cudaMemcpyAsync(p->env_b, bs->env_table_b, nl * sizeof(double),
                                 cudaMemcpyHostToDevice, st));
       k_sep_tables<<<cdiv(nl, 256), 256, 0, st>>>((int)nl, p->env_b, p->env_b2, p->env_b32,
@@ -901,12 +902,12 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     p->log2ntwc = std::max(p->log2cNk, p->log2cNw);
   }
   p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
-  SRM3_CUDA(cudaMalloc(&p->sqq, nl * es));
-  SRM3_CUDA(cudaMalloc(&p->Pk, nl * es));
-  SRM3_CUDA(cudaMalloc(&p->ck, nl * es));
-  SRM3_CUDA(cudaMalloc(&p->Ek, nk * es));
-  SRM3_CUDA(cudaMalloc(&p->Ews, p->ew_len * es));
-  SRM3_CUDA(cudaMalloc(&p->tw, p->nfft * 2 * es));
+  SRM3_CUDA(dev_alloc(&p->sqq, nl * es, st));
+  SRM3_CUDA(dev_alloc(&p->Pk, nl * es, st));
+  SRM3_CUDA(dev_alloc(&p->ck, nl * es, st));
+  SRM3_CUDA(dev_alloc(&p->Ek, nk * es, st));
+  SRM3_CUDA(dev_alloc(&p->Ews, p->ew_len * es, st));
+  SRM3_CUDA(dev_alloc(&p->tw, p->nfft * 2 * es, st));
   if (f32) {
     k_sampling_tables<float><<<cdiv(nl, 256), 256, 0, st>>>(
         (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (float *)p->sqq, (float *)p->Pk,
@@ -914,12 +915,12 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_env<float><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (float *)p->Ek);
     k_env<float><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off, p->sigma_g * nw,
                                                       (float *)p->Ews);
-    SRM3_CUDA(cudaMalloc(&p->ps_err, sizeof(int)));
+    SRM3_CUDA(dev_alloc(&p->ps_err, sizeof(int), st));
     SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
     k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
                                                           (float2 *)p->tw);
     if (p->sep) {
-      SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2)));
+      SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2), st));
       k_twiddles<float2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
                                                                         p->log2ntwc,
                                                                         (float2 *)p->tw_conv);
@@ -934,7 +935,7 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     k_twiddles<double2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
                                                            (double2 *)p->tw);
     if (p->sep) {
-      SRM3_CUDA(cudaMalloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2)));
+      SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2), st));
       k_twiddles<double2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
                                                                          p->log2ntwc,
                                                                          (double2 *)p->tw_conv);
@@ -944,6 +945,28 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaStreamSynchronize(st));
   return SRM3_OK;
 }
+
+// Freed plan memory the default pool keeps for reuse (a bridge-size plan
+// with its W table is about 9.5 GB); beyond this it goes back to the device.
+constexpr uint64_t kPoolKeepBytes = 32ull << 30;
+
+cudaError_t dev_alloc(void **ptr, size_t bytes, cudaStream_t st) {
+  static std::once_flag once[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64)
+    std::call_once(once[dev], [dev] {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = kPoolKeepBytes;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+    });
+  return cudaMallocAsync(ptr, bytes, st);
+}
+
+cudaError_t dev_free(void *ptr, cudaStream_t st) { return cudaFreeAsync(ptr, st); }
 
 void free_plan(srm3_plan *p) {
   for (auto &r : p->ev_recs) {
@@ -962,8 +985,10 @@ void free_plan(srm3_plan *p) {
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr};
+  // no plan work may be in flight; the blocks go back to the pool
+  cudaDeviceSynchronize();
   for (void *d : dev)
-    if (d) cudaFree(d);
+    if (d) dev_free(d, nullptr);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
   if (p->h_err) cudaFreeHost(p->h_err);
 }

@@ -124,23 +124,25 @@ int ensure_workspace(srm3_plan *p, int chunk) {
                 "the plan's workspace belongs to a batch and cannot grow while the batch exists");
   int cap = std::max(chunk, std::min(kMaxChunk, 64));
   for (void **q : {&p->y, &p->y0, &p->C, &p->H}) {
-    if (*q) cudaFree(*q);
+    if (*q) dev_free(*q, p->stream);
     *q = nullptr;
   }
   p->ws_chunk = 0;
   const size_t e2 = elem2(p);
   p->rowstride = p->nw + 2 * kPad;
   const int sp = sspad_for(cap);
-  SRM3_CUDA(cudaMalloc(&p->y, (size_t)p->nk * p->rowstride * sp * e2));
-  SRM3_CUDA(cudaMalloc(&p->y0, (size_t)sp * e2));
-  SRM3_CUDA(cudaMalloc(&p->C, (size_t)2 * cap * p->nk * p->nw * e2));
-  SRM3_CUDA(cudaMalloc(&p->H, (size_t)cap * p->nk * p->nt * e2));
+  SRM3_CUDA(dev_alloc(&p->y, (size_t)p->nk * p->rowstride * sp * e2, p->stream));
+  SRM3_CUDA(dev_alloc(&p->y0, (size_t)sp * e2, p->stream));
+  SRM3_CUDA(dev_alloc(&p->C, (size_t)2 * cap * p->nk * p->nw * e2, p->stream));
+  SRM3_CUDA(dev_alloc(&p->H, (size_t)cap * p->nk * p->nt * e2, p->stream));
   if (p->sep) {  // the self-convolution grid of every sheet-sample of a chunk
-    if (p->Zc) cudaFree(p->Zc);
+    if (p->Zc) dev_free(p->Zc, p->stream);
     p->Zc = nullptr;
-    SRM3_CUDA(cudaMalloc(&p->Zc, (size_t)2 * cap * p->cNk * p->cNw * e2));
+    SRM3_CUDA(dev_alloc(&p->Zc, (size_t)2 * cap * p->cNk * p->cNw * e2, p->stream));
     p->zc_ss = 2LL * cap;
   }
+  // stream-ordered blocks: usable from any stream (batches) once this passes
+  SRM3_CUDA(cudaStreamSynchronize(p->stream));
   p->ws_chunk = cap;
   return SRM3_OK;
 }
@@ -757,7 +759,7 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   plan->storage = choice;
   if (choice == SRM3_STORAGE_RECOMPUTE && plan->W) {
     SRM3_CUDA(cudaStreamSynchronize(plan->stream));
-    SRM3_CUDA(cudaFree(plan->W));
+    SRM3_CUDA(dev_free(plan->W, plan->stream));
     plan->W = nullptr;
     plan->table_bytes = 0.0;
   }

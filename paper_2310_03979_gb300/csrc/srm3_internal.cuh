@@ -48,6 +48,17 @@ struct SeedChunk {
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
+// Device memory of plans and their workspaces: stream-ordered allocations
+// from the device's default memory pool, whose release threshold is raised
+// on first use (to 32 GB) so that freed memory stays in the pool -- building
+// and freeing plans back to back then maps no pages.  dev_free returns a
+// block to the pool in the order of stream st.
+cudaError_t dev_alloc(void **ptr, size_t bytes, cudaStream_t st);
+template <typename T>
+cudaError_t dev_alloc(T **ptr, size_t bytes, cudaStream_t st) {
+  return dev_alloc(reinterpret_cast<void **>(ptr), bytes, st);
+}
+cudaError_t dev_free(void *ptr, cudaStream_t st);
 // Grid-barrier timeout self-test (plan.cu): *timed_out = the abort word.
 int selftest_barrier(long long polls, int *timed_out);
 
