@@ -62,6 +62,23 @@ def _args():
     return ap.parse_args()
 
 
+def rank_seeds(rank, n):
+    """Seeds of rank `rank` when every rank samples n fields (weak scaling):
+    disjoint consecutive ranges, 1 + rank n + j."""
+    return [1 + rank * n + j for j in range(n)]
+
+
+def max_over_ranks(x, dist, device):
+    """The largest value of x over the ranks (the slowest rank's time), one
+    all-reduce on `device` ("cuda" under NCCL, "cpu" under gloo)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -645,7 +662,7 @@ def main():
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
     n = wl.n_samples
-    seeds = [1 + rank * n + j for j in range(n)]
+    seeds = rank_seeds(rank, n)
     es = 4 if wl.precision == "fp32" else 8
     dt = torch.float32 if es == 4 else torch.float64
     out = torch.empty((n, wl.n_x, wl.n_t), dtype=dt, device="cuda")
@@ -692,10 +709,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    if dist:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     value = terms_per_step * world / (ms_per_step * 1e-3)
 
@@ -775,10 +789,7 @@ def main():
         for _ in range(args.steps):
             one_step(host)
         e2e_s = (time.perf_counter() - t0) / args.steps
-        if dist:
-            tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(e2e_s, dist, "cuda")
         line["e2e"] = {"value": terms_per_step * world / e2e_s, "unit": "pair-terms/s",
                        "h2d_bytes_per_step": 8 * n,
                        "d2h_bytes_per_step": n * wl.n_x * wl.n_t * es,
