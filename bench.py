@@ -33,13 +33,19 @@ METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 l
 # DRAM bytes (read + write) of one FP32 pair-sum launch on the 256 x 512 table
 # workload with 64 samples, from ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # on the 128 x 256 table case with 64 samples (same two sample groups per
-# super-tile), reads scaled by the W table size (x 15.64), writes by the
-# coefficient count (x 4): profiles/
-# pairsum_f32p_table_128x256.md.  Valid only for the kernel source it was
-# measured on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
+# super-tile), reads scaled by the W table size (x 15.41), writes by the
+# coefficient count (x 4).  Valid only for the kernel source it was measured
+# on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
 PAIRSUM_TRAFFIC = {"bytes": 665.51e6 * 15.41 + 31.88e6 * 4, "source_sha256": "564a3068d1dd846a"}
 FP32_LANES_PER_SM = 128
-N_SM = 152
+
+
+def n_sm():
+    """Streaming multiprocessors of the current CUDA device
+    (cudaDevAttrMultiProcessorCount through torch)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+               .multi_processor_count)
 
 
 def _args():
@@ -112,12 +118,13 @@ def _pairsum_roofline_fp64(terms_per_s, **extra):
     accumulate 2 DFMA) over the FP64 rate 152 SM x 2 lanes x the maximum SM
     clock (GB300's nominal 1.25 TFLOP/s dense FP64)."""
     sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
-    lane_rate = 2 * N_SM * sm_max * 1e6
+    nsm = n_sm()
+    lane_rate = 2 * nsm * sm_max * 1e6
     ops = 6.0 * terms_per_s
     out = {"bound": "alu", "achieved": ops / 1e12, "peak": lane_rate / 1e12,
            "unit": "T FP64-pipe lane-ops/s", "frac": ops / lane_rate, "traffic": None,
            "per_unit": "6 FP64-pipe lane-ops per pair-term",
-           "peak_source": f"derived: {N_SM} SM x 2 FP64 lanes x {sm_max:.0f} MHz"}
+           "peak_source": f"derived: {nsm} SM x 2 FP64 lanes x {sm_max:.0f} MHz"}
     out.update(extra)
     return out
 
@@ -133,7 +140,8 @@ def _pairsum_roofline(terms_per_s, traffic=None, **extra):
     slot for one flop."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    lane_rate = FP32_LANES_PER_SM * N_SM * sm_max * 1e6  # lane-ops/s
+    nsm = n_sm()
+    lane_rate = FP32_LANES_PER_SM * nsm * sm_max * 1e6  # lane-ops/s
     ops = 6.0 * terms_per_s
     flops = 10.0 * terms_per_s
     out = {"bound": "alu", "achieved": ops / 1e12, "peak": lane_rate / 1e12,
@@ -141,7 +149,7 @@ def _pairsum_roofline(terms_per_s, traffic=None, **extra):
            "per_unit": "6 FP32-pipe lane-ops (2 FMUL + 4 FFMA = 10 flop) per pair-term",
            "flops": {"achieved": flops / 1e12, "peak": 2.0 * lane_rate / 1e12,
                      "unit": "TFLOP/s", "frac": flops / (2.0 * lane_rate)},
-           "peak_source": f"derived: {N_SM} SM x {FP32_LANES_PER_SM} FP32 lanes x "
+           "peak_source": f"derived: {nsm} SM x {FP32_LANES_PER_SM} FP32 lanes x "
                           f"{sm_max:.0f} MHz (max SM clock of MEASURED_PEAKS.json)"}
     out.update(extra)
     return out

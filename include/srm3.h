@@ -215,7 +215,10 @@ int srm3_coeffs(srm3_plan *plan, const uint64_t *seeds, int n, void *C);
 int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
 
 /* Capacity of the fixed scratch behind srm3_field_from_coeffs_noalloc:
- * 16 MiB per device. */
+ * 16 MiB per device.  The array is part of the library's device code, so
+ * these 16 MiB are held on every device where any srm3 kernel has been
+ * loaded, whether or not the no-allocation entry point is ever called, and
+ * stay held until the process exits. */
 #define SRM3_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* srm3_field_from_coeffs that allocates no device memory.  The paper has no
@@ -235,9 +238,11 @@ int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
  *
  * Arguments, layouts and result are those of srm3_field_from_coeffs: C is a
  * device buffer C[n][2][n_kappa][n_omega] of interleaved (re, im) values in
- * the plan's precision; out is a device buffer u[n][n_x][n_t].  The same
- * kernels run in the same order, so the values are those of
- * srm3_field_from_coeffs.  Asynchronous on the plan's stream.
+ * the plan's precision; out is a device buffer u[n][n_x][n_t].  The launch
+ * sequence is the one srm3_field_from_coeffs runs, with the scratch in
+ * place of the workspace, and each set is transformed independently of the
+ * others, so the values are bit-identical to srm3_field_from_coeffs.
+ * Asynchronous on the plan's stream.
  *
  * Scratch: the intermediate of the two FFT stages, n_kappa * n_t complex
  * values per coefficient set (8 bytes each in FP32, 16 in FP64), lives in a
@@ -250,8 +255,11 @@ int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
  * (cudaGetSymbolAddress, with the plan's device current), which can load
  * the library's device code onto that device; later calls reuse the cached
  * address.  Make that first call before any stream capture begins.  The
- * plan's device is made current for the call and the previous current
- * device is restored before return.
+ * cached address lives as long as the process: after a cudaDeviceReset (or
+ * any other reset of the device's primary context) it is stale, so do not
+ * call this entry point on a device that has been reset.  The plan's device
+ * is made current for the call and the previous current device is restored
+ * before return.
  *
  * Concurrency: the array is shared by every plan and stream on a device.
  * Calls whose work overlaps on one device (on different streams, or from

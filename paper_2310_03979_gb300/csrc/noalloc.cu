@@ -1,11 +1,10 @@
 // noalloc.cu - srm3_field_from_coeffs_noalloc: the transform stage with its
 // intermediate held in a fixed device array of the library instead of plan
 // workspace, for callers that may not allocate device memory.  The paper has
-// no counterpart; the kernels are those of fft.cuh.
+// no counterpart; the launch sequence is that of srm3_field_from_coeffs.
 #include <algorithm>
 #include <mutex>
 
-#include "fft.cuh"
 #include "srm3_internal.cuh"
 
 namespace {
@@ -26,7 +25,9 @@ std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of srm3_noalloc_scratch on `dev`, which is the current
-// device.  Looked up once per device, then cached.
+// device.  Looked up once per device, then cached for the life of the
+// process: a cudaDeviceReset (or any reset of the device's primary context)
+// unloads the module, and the cached address is then stale.
 int scratch_address(int dev, void **addr) {
   if (dev < 0 || dev >= kMaxDevices)
     return fail(SRM3_ERR_NOT_SUPPORTED, "srm3_field_from_coeffs_noalloc: device ordinal " +
@@ -61,39 +62,21 @@ struct DeviceGuard {
   }
 };
 
-// The two FFT stages for n sets with the intermediate H supplied by the
-// caller (n * nk * nt entries).
-template <typename T, typename T2>
-int transform_with(const srm3_plan *p, const T2 *C, int n, T *out, T2 *H) {
-  const size_t e2 = sizeof(T2);
-  const size_t smem_t = (size_t)fft_row_len(p->nt) * e2;
-  int TC = 16;
-  while (TC > 1 && ((size_t)TC * fft_col_stride(p->nx) * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
-  const size_t smem_x = (size_t)TC * fft_col_stride(p->nx) * e2;
-  const int lim = 200 * 1024;
-  SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, p->stream>>>(p->nk, p->nw, p->nt, p->log2nt, C,
-                                                          (const T2 *)p->tw, H);
-  SRM3_CUDA(cudaGetLastError());
-  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 512, smem_x, p->stream>>>(
-      p->nk, p->nx, p->nt, p->log2nx, TC, H, (const T2 *)p->tw, out);
-  SRM3_CUDA(cudaGetLastError());
-  return SRM3_OK;
-}
-
-template <typename T, typename T2>
+// The transform of n sets in groups whose t-stage rows fit the scratch, by
+// the launch sequence of srm3_field_from_coeffs (transform_on) with the
+// scratch in place of the plan workspace.
 int field_noalloc(srm3_plan *p, const void *C, int n, void *out, void *scratch) {
-  const size_t perH = (size_t)p->nk * p->nt * sizeof(T2);
-  const size_t perC = (size_t)2 * p->nk * p->nw * sizeof(T2);
-  const size_t perU = (size_t)p->nx * p->nt * sizeof(T);
+  const size_t e2 = p->precision == SRM3_FP32 ? sizeof(float2) : sizeof(double2);
+  const size_t e1 = p->precision == SRM3_FP32 ? sizeof(float) : sizeof(double);
+  const size_t perH = (size_t)p->nk * p->nt * e2;
+  const size_t perC = (size_t)2 * p->nk * p->nw * e2;
+  const size_t perU = (size_t)p->nx * p->nt * e1;
   // gridDim.y carries the set index: at most 65535 sets per launch.
   const int group = (int)std::min<size_t>(kScratchBytes / perH, 65535);
   for (int s0 = 0; s0 < n; s0 += group) {
     const int m = std::min(group, n - s0);
-    const int rc = transform_with<T, T2>(
-        p, reinterpret_cast<const T2 *>((const char *)C + (size_t)s0 * perC), m,
-        reinterpret_cast<T *>((char *)out + (size_t)s0 * perU), reinterpret_cast<T2 *>(scratch));
+    const int rc = transform_on(p, p->stream, (const char *)C + (size_t)s0 * perC, m,
+                                (char *)out + (size_t)s0 * perU, scratch);
     if (rc) return rc;
   }
   return SRM3_OK;
@@ -121,6 +104,5 @@ SRM3_API int srm3_field_from_coeffs_noalloc(srm3_plan *plan, const void *C, int 
   if (rc) return rc;
   void *scratch = nullptr;
   if ((rc = scratch_address(plan->device, &scratch))) return rc;
-  if (plan->precision == SRM3_FP32) return field_noalloc<float, float2>(plan, C, n, out, scratch);
-  return field_noalloc<double, double2>(plan, C, n, out, scratch);
+  return field_noalloc(plan, C, n, out, scratch);
 }

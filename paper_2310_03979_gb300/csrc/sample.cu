@@ -379,8 +379,7 @@ static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *
 
 // The transform of n coefficient sets with the t-stage rows in H (n*nk*nt
 // complex), on stream st.
-static int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out,
-                        void *H) {
+int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out, void *H) {
   if (p->precision == SRM3_FP32)
     return transform_impl<float, float2>(p, st, (const float2 *)C, n, (float *)out,
                                          (float2 *)H);

@@ -196,6 +196,10 @@ int ensure_workspace(srm3_plan *p, int chunk);
 int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out);
 int run_pairsum(srm3_plan *p, int n, void *C_out);
 int run_transform(srm3_plan *p, const void *C, int n, void *out);
+// The two FFT stages for n coefficient sets on stream st with the t-stage
+// rows in H (n * nk * nt complex values in the plan's precision), which the
+// caller supplies: the plan workspace, a batch buffer or fixed scratch.
+int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out, void *H);
 int prepare_sampling_tables(srm3_plan *p, cudaStream_t st);
 int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);
 int stage_end(srm3_plan *p, int rec);

@@ -100,3 +100,43 @@ def test_autotune_chooses_a_storage_and_tuned_plans_use_it():
     with srm3.Plan.create(fp64) as d:
         with pytest.raises(srm3.SRM3Error):
             srm3.autotune(d.handle, 2)
+
+
+def test_uneven_batch_spectra_against_oracle(oracle_lib):
+    """The uneven-batch workload's own spectra (seed 4, the benchmark's draw):
+    its smallest lattices, autotuned storage as in the benchmark, through one
+    captured batch graph, against the FP64 oracle (its own bisection on each
+    spectrum's target, coefficients and direct DFT), max|du| <= 1e-4 sigma_u."""
+    import math
+
+    import numpy as np
+
+    import oracle
+
+    spectra = [wl for wl in W.uneven_batch() if wl.n_kappa * wl.n_omega <= 32 * 64][:4]
+    assert len(spectra) >= 3
+    plans = [srm3.Plan.create(wl, storage="recompute") for wl in spectra]
+    try:
+        outs = [torch.full((wl.n_samples, wl.n_x, wl.n_t), float("nan"), device="cuda")
+                for wl in spectra]
+        with srm3.Batch(plans, [wl.n_samples for wl in spectra], outs) as b:
+            b.capture()
+            b.run([s for wl in spectra for s in wl.seeds])
+            b.sync()
+        worst = 0.0
+        for wl, o in zip(spectra, outs):
+            S = oracle.kaimal_lorentzian(wl.n_kappa, wl.n_omega, wl.kappa_u, wl.omega_u,
+                                         wl.U, wl.z, wl.z0, wl.k_vk, wl.lam)
+            op = oracle.make_plan(S, wl.kappa_u, wl.omega_u, target=wl.target,
+                                  env=oracle.Envelope("gauss", wl.sigma_g))
+            sig = math.sqrt(op.moments()[0])
+            u = o.cpu().double().numpy()
+            for i, s in enumerate(wl.seeds[:3]):
+                err = np.abs(u[i] - op.field(s, wl.n_x, wl.n_t)).max() / sig
+                worst = max(worst, err)
+                assert err <= 1e-4, (wl.name, s, err)
+        print(f"uneven-batch spectra {[w.name for w in spectra]}: max|du|/sigma_u = "
+              f"{worst:.3e} against the FP64 oracle")
+    finally:
+        for p in plans:
+            p.destroy()

@@ -2,11 +2,13 @@
 16 MiB device array of the library instead of plan workspace.
 
 Its fields are compared with those of srm3_field_from_coeffs (the existing
-entry point) on two calls in a row.  Both run the same kernels in the same
-order, so the comparison is to within 1e-12 of max|u| (FP64) and 1e-6 of
-max|u| (FP32), well inside the field tolerances of the parity tests.  The
-file is named to be collected last, so that it runs both alone in a fresh
-process and after every other test.
+entry point) on two calls in a row.  Both run one launch sequence (the same
+kernels, launch shapes and order; only the buffer of the t-stage rows
+differs) and every set is transformed on its own, so the fields must be
+bit-identical: the tests compare with torch.equal, which also catches a
+change of grouping or launch shape that moves the last bits.  The file is
+named to be collected last, so that it runs both alone in a fresh process
+and after every other test.
 """
 import ctypes
 
@@ -17,9 +19,6 @@ from paper_2310_03979_gb300 import srm3
 from paper_2310_03979_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
-
-TOL = {"fp32": 1e-6, "fp64": 1e-12}
-
 
 def test_noalloc_rejects_bad_arguments():
     lib = srm3.load()
@@ -40,14 +39,12 @@ def test_noalloc_matches_field_from_coeffs(precision, storage):
         C = p.coeffs(seeds)
         ref = p.field_from_coeffs(C)
         torch.cuda.synchronize()
-        scale = ref.abs().max().item()
-        assert scale > 0
+        assert ref.abs().max().item() > 0
         for _ in range(2):  # two calls in a row, each into a NaN-filled buffer
             out = torch.full_like(ref, float("nan"))
             _noalloc(p, C, out)
             torch.cuda.synchronize()
-            assert torch.isfinite(out).all()
-            assert (out - ref).abs().max().item() <= TOL[precision] * scale
+            assert torch.equal(out, ref)
 
 
 @pytest.mark.gpu
@@ -64,8 +61,7 @@ def test_noalloc_several_groups_and_no_device_allocation():
         out = torch.full_like(ref, float("nan"))
         _noalloc(p, C, out)  # set-up: scratch address looked up on this device
         torch.cuda.synchronize()
-        scale = ref.abs().max().item()
-        assert (out - ref).abs().max().item() <= TOL["fp32"] * scale
+        assert torch.equal(out, ref)
         out.fill_(float("nan"))
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
@@ -73,8 +69,7 @@ def test_noalloc_several_groups_and_no_device_allocation():
         torch.cuda.synchronize()
         free1 = torch.cuda.mem_get_info()[0]
         assert free1 == free0
-        assert torch.isfinite(out).all()
-        assert (out - ref).abs().max().item() <= TOL["fp32"] * scale
+        assert torch.equal(out, ref)
 
 
 @pytest.mark.gpu
