@@ -12,14 +12,21 @@ Parity status per function (what pins it, see ``tests/test_oracle_pins.py``):
                      kaimal_davenport_spectrum)
   recursion          hand-worked 3x3 lattice, separable-envelope FFT
                      self-convolution, scale invariance (Eq. pure)
+  recursion_mixed    the plain recursion when no difference pair carries
+                     weight; a hand-worked 2x4 lattice with difference pairs;
+                     the fixed-point residual; scale invariance
   bisect_eps         monotonicity and the target it reaches
   philox4x32_10      cuRAND's host Philox4_32_10 generator (library)
   phases             counter/key map of the same generator
   coeffs             ordered-pair brute force, separable FFT convolution,
-                     eps = 0 reduction to the 2nd-order SRM (Sec. 3)
+                     eps = 0 reduction to the 2nd-order SRM (Sec. 3); with
+                     difference pairs, a brute force over all ordered pairs
+                     of signed lattice points
   field_dft          numpy FFT of the same coefficients
   field_series       equals coefficients + DFT (FFT form, Sec. 4.3)
-  exact_moments      Monte Carlo moments of the series over many seeds
+  exact_moments      Monte Carlo moments of the series over many seeds;
+                     with difference pairs, the closed form in S and g
+                     alone and a Monte Carlo skewness
   field_stats        closed-form moments of a sampled sinusoid, a centred
                      uniform grid and a two-point distribution; exact bin
                      counts of the uniform grid (sample statistics, Sec. 6)
@@ -67,18 +74,19 @@ def _load():
         i, d, u64 = ctypes.c_int, ctypes.c_double, ctypes.c_uint64
         lib.or_kaimal_lorentzian.argtypes = [i, i, d, d, d, d, d, d, d, dp]
         lib.or_recursion.argtypes = [i, i, d, d, dp, i, d, dp, d, dp, dp]
-        lib.or_bisect_eps.argtypes = [i, i, d, d, dp, i, d, dp, d, d, i, dp, dp,
+        lib.or_recursion_mixed.argtypes = [i, i, d, d, dp, i, d, dp, d, d, i, dp, dp, ip]
+        lib.or_bisect_eps.argtypes = [i, i, d, d, dp, i, d, dp, i, d, d, i, dp, dp,
                                       ip, dp, dp]
         lib.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
         lib.or_philox4x32_10.restype = None
         lib.or_phases.argtypes = [i, i, u64, u32p, dp]
         lib.or_phases.restype = None
-        lib.or_coeffs.argtypes = [i, i, d, d, dp, dp, i, d, dp, d, d, u64, dp]
+        lib.or_coeffs.argtypes = [i, i, d, d, dp, dp, i, d, dp, i, d, d, u64, dp]
         lib.or_field_dft.argtypes = [i, i, i, i, dp, dp]
         lib.or_field_points.argtypes = [i, i, i, i, dp, i, ip, ip, dp]
-        lib.or_field_series.argtypes = [i, i, d, d, i, i, dp, dp, i, d, dp, d, d,
+        lib.or_field_series.argtypes = [i, i, d, d, i, i, dp, dp, i, d, dp, i, d, d,
                                         u64, i, ip, ip, dp]
-        lib.or_exact_moments.argtypes = [i, i, d, d, dp, dp, i, d, dp, d, d, dp, dp]
+        lib.or_exact_moments.argtypes = [i, i, d, d, dp, dp, i, d, dp, i, d, d, dp, dp]
         lib.or_num_threads.argtypes = []
         _lib = lib
     return _lib
@@ -160,8 +168,26 @@ def recursion(S, kappa_u, omega_u, eps, env=None):
     return Sp, sb2
 
 
-def bisect_eps(S, kappa_u, omega_u, target, env=None, tol=1e-13, max_iter=200):
-    """FP64 bisection on eps so that max_k sum_b2 = target.
+def recursion_mixed(S, kappa_u, omega_u, eps, env=None, tol=1e-15, max_sweeps=100000):
+    """Pure spectrum with sum and difference (mixed-sign) interactions: the
+    largest fixed point of Eq. pure by lexicographic Gauss-Seidel sweeps from
+    S_p = S.  Returns (S_p, sum_b2, sweeps)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    nk, nw = S.shape
+    kind, sg, tab, tabp = _env(env, nk, nw)
+    Sp = np.zeros_like(S)
+    sb2 = np.zeros_like(S)
+    sw = ctypes.c_int()
+    _check(_load().or_recursion_mixed(nk, nw, kappa_u, omega_u, _dp(S), kind, sg, tabp,
+                                      eps, tol, max_sweeps, _dp(Sp), _dp(sb2),
+                                      ctypes.byref(sw)), "recursion_mixed")
+    return Sp, sb2, sw.value
+
+
+def bisect_eps(S, kappa_u, omega_u, target, env=None, tol=1e-13, max_iter=200,
+               mixed=False):
+    """FP64 bisection on eps so that max_k sum_b2 = target (with difference
+    interactions when ``mixed``).
     Returns (eps, max_sum_b2, evaluations, S_p, sum_b2)."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     nk, nw = S.shape
@@ -172,7 +198,7 @@ def bisect_eps(S, kappa_u, omega_u, target, env=None, tol=1e-13, max_iter=200):
     mx = ctypes.c_double()
     it = ctypes.c_int()
     _check(_load().or_bisect_eps(nk, nw, kappa_u, omega_u, _dp(S), kind, sg, tabp,
-                                 target, tol, max_iter, ctypes.byref(eps),
+                                 int(bool(mixed)), target, tol, max_iter, ctypes.byref(eps),
                                  ctypes.byref(mx), ctypes.byref(it), _dp(Sp),
                                  _dp(sb2)), "bisect_eps")
     return eps.value, mx.value, it.value, Sp, sb2
@@ -194,15 +220,17 @@ def phases(nk, nw, seed):
     return words, phi
 
 
-def coeffs(S, Sp, kappa_u, omega_u, eps, seed, env=None, beta=0.0):
-    """C^s_k, complex128 shape (2, Nk, Nw) (FFT form, Sec. 4.3)."""
+def coeffs(S, Sp, kappa_u, omega_u, eps, seed, env=None, beta=0.0, mixed=False):
+    """C^s_k, complex128 shape (2, Nk, Nw) (FFT form, Sec. 4.3); ``mixed``
+    adds the difference pairs."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     Sp = np.ascontiguousarray(Sp, dtype=np.float64)
     nk, nw = S.shape
     kind, sg, tab, tabp = _env(env, nk, nw)
     C = np.zeros((2, nk, nw, 2), dtype=np.float64)
     _check(_load().or_coeffs(nk, nw, kappa_u, omega_u, _dp(S), _dp(Sp), kind, sg,
-                             tabp, eps, beta, int(seed), _dp(C)), "coeffs")
+                             tabp, int(bool(mixed)), eps, beta, int(seed), _dp(C)),
+           "coeffs")
     return C[..., 0] + 1j * C[..., 1]
 
 
@@ -236,8 +264,9 @@ def field_points(C, nx, nt, mx, mt):
 
 
 def field_series(S, Sp, kappa_u, omega_u, eps, seed, nx, nt, mx, mt, env=None,
-                 beta=0.0):
-    """u at points by the literal cosine series (Eq. quadrant_1d_wave)."""
+                 beta=0.0, mixed=False):
+    """u at points by the literal cosine series (Eq. quadrant_1d_wave; its
+    mixed cosines too when ``mixed``)."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     Sp = np.ascontiguousarray(Sp, dtype=np.float64)
     nk, nw = S.shape
@@ -246,12 +275,13 @@ def field_series(S, Sp, kappa_u, omega_u, eps, seed, nx, nt, mx, mt, env=None,
     mt = np.ascontiguousarray(mt, dtype=np.int32)
     u = np.zeros(len(mx), dtype=np.float64)
     _check(_load().or_field_series(nk, nw, kappa_u, omega_u, nx, nt, _dp(S), _dp(Sp),
-                                   kind, sg, tabp, eps, beta, int(seed), len(mx),
+                                   kind, sg, tabp, int(bool(mixed)), eps, beta,
+                                   int(seed), len(mx),
                                    _ip(mx), _ip(mt), _dp(u)), "field_series")
     return u
 
 
-def exact_moments(S, Sp, kappa_u, omega_u, eps, env=None, beta=0.0):
+def exact_moments(S, Sp, kappa_u, omega_u, eps, env=None, beta=0.0, mixed=False):
     """(variance, third moment) of the discrete series over the phases."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     Sp = np.ascontiguousarray(Sp, dtype=np.float64)
@@ -260,7 +290,7 @@ def exact_moments(S, Sp, kappa_u, omega_u, eps, env=None, beta=0.0):
     v = ctypes.c_double()
     m3 = ctypes.c_double()
     _check(_load().or_exact_moments(nk, nw, kappa_u, omega_u, _dp(S), _dp(Sp), kind,
-                                    sg, tabp, eps, beta, ctypes.byref(v),
+                                    sg, tabp, int(bool(mixed)), eps, beta, ctypes.byref(v),
                                     ctypes.byref(m3)), "exact_moments")
     return v.value, m3.value
 
@@ -276,6 +306,7 @@ class OraclePlan:
     omega_u: float
     env: Envelope
     beta: float = 0.0
+    mixed: bool = False
 
     @property
     def q(self):
@@ -287,27 +318,31 @@ class OraclePlan:
 
     def coeffs(self, seed):
         return coeffs(self.S, self.Sp, self.kappa_u, self.omega_u, self.eps, seed,
-                      self.env, self.beta)
+                      self.env, self.beta, self.mixed)
 
     def field(self, seed, nx, nt):
         return field_dft(self.coeffs(seed), nx, nt)
 
     def moments(self):
         return exact_moments(self.S, self.Sp, self.kappa_u, self.omega_u, self.eps,
-                             self.env, self.beta)
+                             self.env, self.beta, self.mixed)
 
 
 def make_plan(S, kappa_u, omega_u, *, target=None, eps=None, env=None, beta=0.0,
-              tol=1e-13):
-    """Oracle plan: eps from bisection on ``target`` (max sum_b2), or given."""
+              tol=1e-13, mixed=False):
+    """Oracle plan: eps from bisection on ``target`` (max sum_b2), or given;
+    ``mixed`` adds the difference interactions."""
     env = env or Envelope()
     if target is not None:
-        e, _, _, Sp, sb2 = bisect_eps(S, kappa_u, omega_u, target, env, tol=tol)
+        e, _, _, Sp, sb2 = bisect_eps(S, kappa_u, omega_u, target, env, tol=tol, mixed=mixed)
     else:
         e = float(eps)
-        Sp, sb2 = recursion(S, kappa_u, omega_u, e, env)
+        if mixed:
+            Sp, sb2, _ = recursion_mixed(S, kappa_u, omega_u, e, env)
+        else:
+            Sp, sb2 = recursion(S, kappa_u, omega_u, e, env)
     return OraclePlan(np.ascontiguousarray(S, dtype=np.float64), Sp, sb2, e, kappa_u,
-                      omega_u, env, beta)
+                      omega_u, env, beta, bool(mixed))
 
 
 def field_stats(u, nbins, lo, hi, shift=0.0):

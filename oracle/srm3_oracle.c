@@ -38,6 +38,27 @@
  * Phases: phi^s_k = 2 pi (w + 1/2) 2^-32, where w is word (e & 3) of
  * Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) at counter
  * (e >> 2) and key = seed, with e = (s*Nk + kk)*Nw + kw.
+ *
+ * Mixed-sign (difference) interactions, switched on by `mixed` (the pairs
+ * of opposite-sign frequencies of the general form, Eq.
+ * truncated_cosines_1d_wave, whose quadrant form Eq. quadrant_1d_wave
+ * writes as the -w_i + w_j and +w_i - w_j cosines, and the signed sums
+ * i_w + j_w = +-k_w of Eq. fft_2d_2_parts).  A point is a signed frequency
+ * (kk, s kw); the difference pairs of k = (kk, s kw), kw >= 1, are
+ *   i = (ia, s (kw + jw)) on sheet s,  j = (kk - ia, -s jw) on sheet -s,
+ *   0 <= ia <= kk,  1 <= jw <= Nw - 1 - kw,
+ * each unordered {i, j} once (the sheets tell i from j).  Pairs whose
+ * frequencies cancel (iw = jw) would land on omega = 0 and are left out;
+ * omega = 0 points take part in sum pairs of their own sheet only.  The
+ * bispectrum is the same formula at the signed points: |B| = eps g(i,j)
+ * sqrt(S_i S_j S_k), S and S_p at |omega| (both sheets share them), the
+ * Gaussian envelope of the signed difference omega_i - omega_j (= s (kw +
+ * 2 jw)), separable tables at |omega|.  With them S_p(k) depends on points
+ * of higher |omega|, so Eq. pure becomes a fixed point: S_p is the largest
+ * solution of S_p = S (1 - sum b_p^2(S_p)), reached by Gauss-Seidel sweeps
+ * in lexicographic order from S_p = S (each sweep can only lower S_p, and
+ * stays above every solution).  Sum interactions alone reach it in one
+ * sweep: that is the recursion of the plain model.
  */
 #include <math.h>
 #include <stdint.h>
@@ -145,6 +166,37 @@ static double or_bp2(const or_bispec *B, const double *S, const double *Sp,
     return mb * mb * dkdw / (Spi * Spj * Sk);
 }
 
+/* Envelope at signed points (ik, iw), (jk, jw) (omega indices signed):
+ * the Gaussian of the signed differences, separable tables at |omega|. */
+static double or_envelope_signed(const or_bispec *B, int ik, int iw, int jk, int jw)
+{
+    if (B->env_kind == 0) {
+        double ak = (double)(ik - jk) / (B->sigma_g * B->nk);
+        double aw = (double)(iw - jw) / (B->sigma_g * B->nw);
+        return exp(-0.5 * ak * ak) * exp(-0.5 * aw * aw);
+    }
+    int kk = ik + jk, kw = abs(iw + jw);
+    const double *a = B->env_tab;
+    const double *b = B->env_kind == 2 ? B->env_tab + (size_t)B->nk * B->nw : B->env_tab;
+    return a[(size_t)ik * B->nw + abs(iw)] * a[(size_t)jk * B->nw + abs(jw)]
+         * b[(size_t)kk * B->nw + kw];
+}
+
+/* b_p^2 of the difference pair i = (ia, s (kw + jw)), j = (kk - ia, -s jw)
+ * of k = (kk, s kw) (the sign s drops out: S, S_p at |omega|, the envelope
+ * even in the signed difference). */
+static double or_bp2_diff(const or_bispec *B, const double *S, const double *Sp,
+                          double dkdw, int kk, int kw, int ia, int jw)
+{
+    int nw = B->nw, ib = kk - ia, iw = kw + jw;
+    double Si = S[(size_t)ia * nw + iw], Sj = S[(size_t)ib * nw + jw];
+    double Sk = S[(size_t)kk * nw + kw];
+    double mb = B->eps * or_envelope_signed(B, ia, iw, ib, -jw) * sqrt(Si * Sj * Sk);
+    if (mb == 0.0) return 0.0;
+    double Spi = Sp[(size_t)ia * nw + iw], Spj = Sp[(size_t)ib * nw + jw];
+    return mb * mb * dkdw / (Spi * Spj * Sk);
+}
+
 /* Pure-spectrum recursion (Eq. pure) at a given eps, in plain lexicographic
  * order (kk outer, kw inner): every part of a pair of Pi(k) precedes k.
  * Writes S_p and sum_b2[k] = sum_{Pi(k)} b_p^2.  Returns
@@ -175,13 +227,78 @@ int or_recursion(int nk, int nw, double kappa_u, double omega_u,
     return OR_OK;
 }
 
+/* Eq. pure with sum and difference interactions (see the header): the
+ * largest fixed point S_p = S (1 - sum_{Pi(k)} b_p^2 - sum_{D(k)} b_p^2),
+ * by Gauss-Seidel sweeps over the lattice in lexicographic order, each
+ * point from the current S_p of all others, starting at S_p = S.  Stops
+ * after the first sweep in which no S_p(k) moves by more than tol S(k)
+ * (and never before the second sweep); *sweeps receives the sweeps done.
+ * Returns OR_ERR_NONPOSITIVE_PURE when some sum_b2 reaches 1 (the sweeps
+ * have no positive fixed point to approach) and OR_ERR_BISECTION when
+ * max_sweeps pass without convergence. */
+int or_recursion_mixed(int nk, int nw, double kappa_u, double omega_u,
+                       const double *S, int env_kind, double sigma_g,
+                       const double *env_tab, double eps, double tol,
+                       int max_sweeps, double *Sp, double *sum_b2, int *sweeps)
+{
+    if (nk <= 0 || nw <= 0 || !S || !Sp || !sum_b2 || max_sweeps < 2) return OR_ERR_ARG;
+    or_bispec B = {nk, nw, env_kind, sigma_g, env_tab, eps};
+    double dkdw = (kappa_u / nk) * (omega_u / nw);
+    size_t nl = (size_t)nk * nw;
+    for (size_t k = 0; k < nl; ++k) { Sp[k] = S[k]; sum_b2[k] = 0.0; }
+    for (int sw = 1; sw <= max_sweeps; ++sw) {
+        double moved = 0.0;
+        for (int kk = 0; kk < nk; ++kk) {
+            for (int kw = 0; kw < nw; ++kw) {
+                size_t k = (size_t)kk * nw + kw;
+                double acc = 0.0;
+                if (S[k] > 0.0) {
+                    for (int ik = 0; ik <= kk; ++ik)
+                        for (int iw = 0; iw <= kw; ++iw)
+                            if (or_is_canonical(kk, kw, ik, iw))
+                                acc += or_bp2(&B, S, Sp, dkdw, ik, iw, kk - ik, kw - iw);
+                    if (kw >= 1)
+                        for (int ia = 0; ia <= kk; ++ia)
+                            for (int jw = 1; jw <= nw - 1 - kw; ++jw)
+                                acc += or_bp2_diff(&B, S, Sp, dkdw, kk, kw, ia, jw);
+                }
+                double sp = S[k] * (1.0 - acc);
+                if (S[k] > 0.0 && !(acc < 1.0)) {
+                    sum_b2[k] = acc;
+                    Sp[k] = sp;
+                    if (sweeps) *sweeps = sw;
+                    return OR_ERR_NONPOSITIVE_PURE;
+                }
+                double d = fabs(sp - Sp[k]);
+                if (S[k] > 0.0 && d > moved * S[k]) moved = d / S[k];
+                sum_b2[k] = acc;
+                Sp[k] = sp;
+            }
+        }
+        if (sw >= 2 && moved <= tol) {
+            if (sweeps) *sweeps = sw;
+            return OR_OK;
+        }
+    }
+    if (sweeps) *sweeps = max_sweeps;
+    return OR_ERR_BISECTION;
+}
+
+/* The fixed-point tolerance and sweep limit of the bisection's evaluations
+ * with difference interactions. */
+#define OR_MIXED_TOL 1e-15
+#define OR_MIXED_SWEEPS 100000
+
 static double or_eval_max(int nk, int nw, double kappa_u, double omega_u,
                           const double *S, int env_kind, double sigma_g,
-                          const double *env_tab, double eps,
+                          const double *env_tab, double eps, int mixed,
                           double *Sp, double *sum_b2)
 {
-    int rc = or_recursion(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
-                          env_tab, eps, Sp, sum_b2);
+    int rc = mixed ? or_recursion_mixed(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
+                                        env_tab, eps, OR_MIXED_TOL, OR_MIXED_SWEEPS, Sp,
+                                        sum_b2, NULL)
+                   : or_recursion(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
+                                  env_tab, eps, Sp, sum_b2);
     if (rc != OR_OK) return INFINITY;
     double m = 0.0;
     for (size_t k = 0; k < (size_t)nk * nw; ++k)
@@ -196,7 +313,7 @@ static double or_eval_max(int nk, int nw, double kappa_u, double omega_u,
  * max_iter halvings.  On return Sp/sum_b2 hold the recursion at *eps_out. */
 int or_bisect_eps(int nk, int nw, double kappa_u, double omega_u,
                   const double *S, int env_kind, double sigma_g,
-                  const double *env_tab, double target, double tol,
+                  const double *env_tab, int mixed, double target, double tol,
                   int max_iter, double *eps_out, double *max_out,
                   int *iters_out, double *Sp, double *sum_b2)
 {
@@ -204,21 +321,21 @@ int or_bisect_eps(int nk, int nw, double kappa_u, double omega_u,
     double lo = 0.0, hi = 1.0;
     int it = 0;
     double fhi = or_eval_max(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
-                             env_tab, hi, Sp, sum_b2);
+                             env_tab, hi, mixed, Sp, sum_b2);
     ++it;
     while (fhi < target) {
         if (fhi == 0.0 && hi > 1e300) return OR_ERR_BISECTION; /* no pairs */
         lo = hi;
         hi *= 2.0;
         fhi = or_eval_max(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
-                          env_tab, hi, Sp, sum_b2);
+                          env_tab, hi, mixed, Sp, sum_b2);
         ++it;
     }
     double mid = hi, fm = fhi;
     for (int n = 0; n < max_iter; ++n) {
         mid = 0.5 * (lo + hi);
         fm = or_eval_max(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
-                         env_tab, mid, Sp, sum_b2);
+                         env_tab, mid, mixed, Sp, sum_b2);
         ++it;
         if (fabs(fm - target) <= tol) break;
         if (fm < target) lo = mid; else hi = mid;
@@ -228,7 +345,7 @@ int or_bisect_eps(int nk, int nw, double kappa_u, double omega_u,
         /* land on the feasible side of the bracket */
         mid = lo;
         fm = or_eval_max(nk, nw, kappa_u, omega_u, S, env_kind, sigma_g,
-                         env_tab, mid, Sp, sum_b2);
+                         env_tab, mid, mixed, Sp, sum_b2);
         ++it;
     }
     *eps_out = mid;
@@ -288,12 +405,12 @@ void or_phases(int nk, int nw, uint64_t seed, uint32_t *words, double *phi)
 
 /* ------------------------------------------------------------------------ */
 /* Coefficients C^s_k (FFT form, Sec. 4.3) for one sample, from S, S_p and
- * the phases.  C[((s*nk + kk)*nw + kw)*2 + {0,1}] = (Re, Im).  The pair
+ * the phases; with `mixed`, the difference pairs of the header too.  C[((s*nk + kk)*nw + kw)*2 + {0,1}] = (Re, Im).  The pair
  * exponential e^{i(phi_i + phi_j + beta)} is evaluated as the product of
  * the unit phasors.  OpenMP over k (each C_k is independent). */
 int or_coeffs(int nk, int nw, double kappa_u, double omega_u,
               const double *S, const double *Sp, int env_kind, double sigma_g,
-              const double *env_tab, double eps, double beta, uint64_t seed,
+              const double *env_tab, int mixed, double eps, double beta, uint64_t seed,
               double *C)
 {
     if (nk <= 0 || nw <= 0 || !S || !Sp || !C) return OR_ERR_ARG;
@@ -329,6 +446,21 @@ int or_coeffs(int nk, int nw, double kappa_u, double omega_u,
                         pr += b * (xr * cb - xi * sb);
                         pi += b * (xr * sb + xi * cb);
                     }
+                /* difference pairs: i = (ia, kw + jw) on this sheet, j =
+                 * (kk - ia, jw) on the other, phases phi^s_i + phi^{-s}_j */
+                const double *Or = zr + (size_t)(1 - s) * nl, *Oi = zi + (size_t)(1 - s) * nl;
+                if (mixed && kw >= 1)
+                    for (int ia = 0; ia <= kk; ++ia)
+                        for (int jw = 1; jw <= nw - 1 - kw; ++jw) {
+                            double b2 = or_bp2_diff(&B, S, Sp, dkdw, kk, kw, ia, jw);
+                            if (b2 == 0.0) continue;
+                            double b = sqrt(b2);
+                            size_t a = (size_t)ia * nw + (kw + jw), c = (size_t)(kk - ia) * nw + jw;
+                            double xr = Zr[a] * Or[c] - Zi[a] * Oi[c];
+                            double xi = Zr[a] * Oi[c] + Zi[a] * Or[c];
+                            pr += b * (xr * cb - xi * sb);
+                            pi += b * (xr * sb + xi * cb);
+                        }
             }
             double amp_pure = sqrt(Sp[k] > 0.0 ? Sp[k] : 0.0);
             double amp_pair = sqrt(S[k]);
@@ -422,12 +554,14 @@ int or_field_points(int nk, int nw, int nx, int nt, const double *C,
 
 /* ------------------------------------------------------------------------ */
 /* Field at selected points by the literal cosine series of
- * Eq. quadrant_1d_wave (sum interactions, one sheet at a time), with
- * x = mx dx, t = mt dt.  Costs O(#pairs) per point: tiny grids only. */
+ * Eq. quadrant_1d_wave (sum interactions, one sheet at a time; with
+ * `mixed`, its two mixed cosines per pair, written at the frequencies of
+ * their parts), with x = mx dx, t = mt dt.  Costs O(#pairs) per point:
+ * tiny grids only. */
 int or_field_series(int nk, int nw, double kappa_u, double omega_u,
                     int nx, int nt, const double *S, const double *Sp,
                     int env_kind, double sigma_g, const double *env_tab,
-                    double eps, double beta, uint64_t seed,
+                    int mixed, double eps, double beta, uint64_t seed,
                     int npts, const int *mx, const int *mt, double *u)
 {
     if (nk <= 0 || nw <= 0 || !S || !Sp || npts < 0) return OR_ERR_ARG;
@@ -462,6 +596,20 @@ int or_field_series(int nk, int nw, double kappa_u, double omega_u,
                                  * cos(theta + ph[(size_t)ik * nw + iw]
                                        + ph[(size_t)jk * nw + jw] + beta);
                         }
+                    /* the mixed cosines: kappa_k x + s (omega_i - omega_j) t
+                     * with phi^s_i + phi^{-s}_j, omega_i > omega_j */
+                    const double *po = phi + (size_t)(1 - s) * nl;
+                    if (mixed && kw >= 1)
+                        for (int ia = 0; ia <= kk; ++ia)
+                            for (int jw = 1; jw <= nw - 1 - kw; ++jw) {
+                                double b2 = or_bp2_diff(&B, S, Sp, dkdw, kk, kw, ia, jw);
+                                if (b2 == 0.0) continue;
+                                double th = ia * dk * x + (kk - ia) * dk * x
+                                          + sg * ((kw + jw) * dw) * t - sg * (jw * dw) * t;
+                                acc += 2.0 * sqrt(S[k] * dkdw) * sqrt(b2)
+                                     * cos(th + ph[(size_t)ia * nw + kw + jw]
+                                           + po[(size_t)(kk - ia) * nw + jw] + beta);
+                            }
                 }
         }
         u[p] = acc;
@@ -473,14 +621,15 @@ int or_field_series(int nk, int nw, double kappa_u, double omega_u,
 /* ------------------------------------------------------------------------ */
 /* Exact ensemble moments of the discrete series, obtained by averaging over
  * the independent uniform phases: only (pure_i, pure_j, pair_ij) triples
- * survive in E[u^3], with multiplicity 6 (i != j) or 3 (i == j):
+ * survive in E[u^3], with multiplicity 6 (i != j) or 3 (i == j), for sum
+ * and (with `mixed`) difference pairs alike:
  *   var = sum_s sum_k |C-amplitudes|^2 / 2 = sum_s sum_k 2 S(k) dk dw,
  *   m3  = sum_s sum_k sum_{Pi(k)} m_ij (1/4) P_i P_j A_ij cos(beta),
  * with P = 2 sqrt(S_p dk dw) and A_ij = 2 sqrt(S(k) dk dw) b_p(i,j).
  * The variance is summed from the amplitudes (pure^2 + pair^2). */
 int or_exact_moments(int nk, int nw, double kappa_u, double omega_u,
                      const double *S, const double *Sp, int env_kind,
-                     double sigma_g, const double *env_tab, double eps,
+                     double sigma_g, const double *env_tab, int mixed, double eps,
                      double beta, double *var, double *m3)
 {
     if (nk <= 0 || nw <= 0 || !S || !Sp || !var || !m3) return OR_ERR_ARG;
@@ -507,6 +656,18 @@ int or_exact_moments(int nk, int nw, double kappa_u, double omega_u,
                         double mult = (ik == jk && iw == jw) ? 3.0 : 6.0;
                         tri += mult * 0.25 * Pi * Pj * A * cos(beta);
                     }
+                /* difference pairs: two distinct points, multiplicity 6 */
+                if (mixed && kw >= 1)
+                    for (int ia = 0; ia <= kk; ++ia)
+                        for (int jw = 1; jw <= nw - 1 - kw; ++jw) {
+                            double b2 = or_bp2_diff(&B, S, Sp, dkdw, kk, kw, ia, jw);
+                            if (b2 == 0.0) continue;
+                            double A = 2.0 * sqrt(S[k] * dkdw) * sqrt(b2);
+                            pair2 += A * A;
+                            double Pi = 2.0 * sqrt(Sp[(size_t)ia * nw + kw + jw] * dkdw);
+                            double Pj = 2.0 * sqrt(Sp[(size_t)(kk - ia) * nw + jw] * dkdw);
+                            tri += 6.0 * 0.25 * Pi * Pj * A * cos(beta);
+                        }
             }
             v += 2.0 * 0.5 * (pure2 + pair2); /* two sheets */
             t3 += 2.0 * tri;
