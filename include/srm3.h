@@ -82,9 +82,33 @@ enum srm3_bispectrum_kind {
     SRM3_BISPECTRUM_SEPARABLE = 1
 };
 
+/* Which frequency pairs interact (the pair set of Eq. pure and of the
+ * coefficients).
+ *   SUM:   i + j = k within one sheet (the quadrant lattice of each sheet).
+ *   MIXED: also the pairs of opposite-sign frequencies of the general form
+ *          (Eq. truncated_cosines_1d_wave; the mixed cosines of Eq.
+ *          quadrant_1d_wave; the signed sums of Eq. fft_2d_2_parts): for
+ *          k = (kk, kw) on sheet s, kw >= 1, the pairs i = (ia, kw + jw) on
+ *          sheet s and j = (kk - ia, jw) on the other sheet, 0 <= ia <= kk,
+ *          1 <= jw <= n_omega - 1 - kw, with phases phi^s_i + phi^{-s}_j
+ *          (pairs that would land on omega = 0 are left out; omega = 0
+ *          points take sum pairs only).  The bispectrum is the same formula
+ *          at the signed points: the Gaussian envelope of the signed
+ *          frequency difference, kw + 2 jw here.  S_p then depends on points
+ *          of higher omega, so Eq. pure is solved as a fixed point: the
+ *          largest S_p with S_p = S (1 - sum b_p^2(S_p)), reached by
+ *          iterations that start at S_p = S and can only lower it.  About
+ *          twice the pair-terms of SUM.  GAUSS_ENVELOPE only; W is
+ *          recomputed (STORAGE_TABLE is refused, AUTO and TUNED recompute);
+ *          plans with it take no part in shape groups of a batch. */
+enum srm3_interactions {
+    SRM3_INTERACTIONS_SUM = 0,
+    SRM3_INTERACTIONS_MIXED = 1
+};
+
 typedef struct srm3_bispectrum {
     int32_t kind;             /* enum srm3_bispectrum_kind */
-    int32_t reserved;
+    int32_t interactions;     /* enum srm3_interactions (0: SUM) */
     double target_max_sum_b2; /* in (0,1): eps found so that max_k sum b_p^2
                                  equals it to 1e-13; 0: use eps as given */
     double eps;               /* used when target_max_sum_b2 == 0; >= 0 */
@@ -175,6 +199,11 @@ typedef struct srm3_info {
     int32_t precision;
     int32_t tile_r;          /* outputs per thread along omega (FP32 path) */
     int32_t root_passes_fp32;/* FP32 recursion passes used to locate eps */
+    int32_t interactions;    /* enum srm3_interactions */
+    int32_t fixed_point_iterations; /* MIXED: iterations of the final solve */
+    int64_t diff_pairs;      /* MIXED: difference pairs of one sheet, sum over k
+                                of (kk + 1)(n_omega - 1 - kw), kw >= 1; else 0.
+                                Pair-terms per sample: 2 (pairs + diff_pairs) */
 } srm3_info;
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
@@ -183,7 +212,8 @@ int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
  * sum_s sum_k 2 S_k dk dw and the third moment
  * E[u^3] = 4 eps cos(beta) (dk dw)^2 sum_k sqrt(S_k) sum_{Pi(k)} m g sqrt(S_i S_j)
  * (m = 6 for i != j, 3 for i = j; Sec. 2 moments of the quadrant form of
- * Sec. 4), the pair sum taken on the GPU in FP64.  Synchronous on the plan's
+ * Sec. 4; MIXED plans add their difference pairs with m = 6), the pair sum
+ * taken on the GPU in FP64.  Synchronous on the plan's
  * stream; allocates nk*nw doubles (stream-ordered) for the duration. */
 int srm3_plan_moments(const srm3_plan *plan, double *variance, double *third_moment);
 

@@ -15,11 +15,16 @@ namespace srm3 {
 // rebuilt per pair:
 //   A = sum_a Ek[kk-2a] sum_iw Ew[2iw-kw] y(a,iw) y(kk-a,kw-iw)
 //   C = P_k y_k + c_k e^{i beta} A
+// Mixed plans (mixed != 0) add the difference pairs: i = (a, kw + jw) on this
+// sheet-sample's sheet and j = (kk - a, jw) on the other sheet of the same
+// sample (sheet-sample ss ^ 1), 0 <= a <= kk, 1 <= jw <= nw - 1 - kw, kw >= 1,
+// W = c_k Ek[|2a - kk|] Ew[kw + 2 jw] (the signed frequency difference).
 __global__ void __launch_bounds__(256) k_pairsum_f64(
     int nk, int nw, int SS, int SSpad, int rowstride, const double2 *__restrict__ y,
     const double2 *__restrict__ y0, const double *__restrict__ Ek,
     const double *__restrict__ Ews, int ew_off, const double *__restrict__ Pk,
-    const double *__restrict__ ck, double cb, double sb, double2 *__restrict__ C) {
+    const double *__restrict__ ck, double cb, double sb, double2 *__restrict__ C,
+    int mixed) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int ss = (int)(gid % SSpad);
   const long long k = gid / SSpad;
@@ -45,6 +50,27 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
     double f = Ek[kk - 2 * a];
     ar = fma(f, rr, ar);
     ai = fma(f, ri, ai);
+  }
+  if (mixed && kw >= 1) {
+    const double2 *yo = y + (ss ^ 1);  // the other sheet of the same sample
+    for (int a = 0; a <= kk; ++a) {
+      const double2 *pa = yl + (size_t)(a * rowstride + kPad + kw) * SSpad;
+      const double2 *pb = yo + (size_t)((kk - a) * rowstride + kPad) * SSpad;
+      double rr = 0.0, ri = 0.0;
+      for (int jw = 1; jw <= nw - 1 - kw; ++jw) {
+        double2 u = pa[(size_t)jw * SSpad];
+        double2 v = pb[(size_t)jw * SSpad];
+        double w = Ews[ew_off + kw + 2 * jw];
+        double pr = u.x * v.x - u.y * v.y;
+        double pi = u.x * v.y + u.y * v.x;
+        rr = fma(w, pr, rr);
+        ri = fma(w, pi, ri);
+      }
+      const int dk = 2 * a - kk;
+      double f = Ek[dk < 0 ? -dk : dk];
+      ar = fma(f, rr, ar);
+      ai = fma(f, ri, ai);
+    }
   }
   double2 yk = (k == 0) ? y0[ss] : yl[((size_t)kk * rowstride + kPad + kw) * SSpad];
   double c = ck[k], P = Pk[k];
@@ -595,6 +621,239 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
         out.x = fmaf(P, yk.x, cf * (ar * d.cb - ai * d.sb));
         out.y = fmaf(P, yk.y, cf * (ar * d.sb + ai * d.cb));
         d.C[((size_t)ss * d.nk + kk) * nw + kw] = out;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Difference pairs of mixed plans, FP32 (W recomputed): a second persistent
+// launch after the sum pairs that adds, for k = (kk, kw), kw >= 1,
+//   C^s_k += c_k e^{i beta} sum_{a=0..kk} Ek[|2a - kk|]
+//            sum_{jw >= 1} Ew[kw + 2 jw] y^s_a[kw + jw] y^{-s}_{kk-a}[jw].
+// The same pipeline as the sum pairs, with the Toeplitz window running the
+// other way: per row pair (a, b = kk - a) -- all kk + 1 of them, the two
+// parts being on different sheets -- the producer stages, per chunk of 16
+// jw, the 16 rows jw of b from ys (the rows of y with the two sheets of each
+// lane swapped and omega = 0 zeroed, so that the packed products pair sheet
+// + of one part with sheet - of the other and jw = 0 contributes nothing)
+// and the 47 rows kws0 + jw .. of a from y, plus the 64-entry window of the
+// envelope of the signed difference d = kw + 2 jw starting at kws0 + 2 j0.
+// A register block takes U = 4 values of jw (from b) and a window of 11 rows
+// of a, of which 7 carry over to the next block.  Rows past the lattice read
+// the zero padding of y.  Kahan merge per row pair as in the sum pairs; the
+// epilogue adds the result to the coefficients the sum pairs wrote.
+struct PsDiffDesc {  // aligned as CUtensorMap
+  CUtensorMap amap;    // y: rows of SSpad/2 float4, boxes of 512 B x 16 rows
+  CUtensorMap bmap;    // ys, the same shape
+  const float *Ek;     // kappa envelope factor by |d|
+  const float *Ewd;    // omega envelope of the signed difference, d >= 0
+  const float *ck;     // pair factor c_k
+  float2 *C;           // coefficients [ss][kk][kw], updated in place
+  const int2 *order;   // super-tiles (kk, kws0) by decreasing difference cost
+  int nk, nw, SS, SSpad, rowstride, G;
+  float cb, sb;        // cos / sin of the biphase
+};
+
+__host__ __device__ __forceinline__ int psd_nch(int nw, int kws0) {
+  return (nw - kws0 + packed::CH - 1) / packed::CH;
+}
+
+template <int RS>
+__device__ __forceinline__ void ps_chunk_diff(const float4 *__restrict__ pb,
+                                              const float4 *__restrict__ pa,
+                                              const float *__restrict__ pe, int j0, int kw0,
+                                              int nw, f32x2 (&Txp)[packed::R],
+                                              f32x2 (&Txm)[packed::R], f32x2 (&Ty)[packed::R]) {
+  using namespace packed;
+  // rows of a by their offset m = U blk + v from the first row of the warp's
+  // window: every row keeps one name
+  ulonglong2 Ac[NV + U * (NB - 1)];
+#pragma unroll
+  for (int blk = 0; blk < NB; ++blk) {
+    if (j0 + blk * U > nw - 1 - kw0) break;  // the rest reads zero padding only
+    ulonglong2 Bv[U];
+#pragma unroll
+    for (int uu = 0; uu < U; ++uu) Bv[uu] = lds_pair(pb + (blk * U + uu) * RS);
+#pragma unroll
+    for (int v = (blk == 0 ? 0 : NV - U); v < NV; ++v)
+      Ac[U * blk + v] = lds_pair(pa + (U * blk + v) * RS);
+    const ulonglong2 *A = Ac + U * blk;
+    const float *pef = pe + 8 * blk;  // weights d - (kw0 + 2 (j0 + U blk)) = r + 2 uu
+    float e[NE];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float4 v4 = reinterpret_cast<const float4 *>(pef)[j];
+      e[4 * j] = v4.x;
+      e[4 * j + 1] = v4.y;
+      e[4 * j + 2] = v4.z;
+      e[4 * j + 3] = v4.w;
+    }
+    const float2 v2 = reinterpret_cast<const float2 *>(pef)[6];
+    e[12] = v2.x;
+    e[13] = v2.y;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int uu = 0; uu < U; ++uu) {
+        const int v = r + uu;
+        const f32x2 w = f2_dup(e[r + 2 * uu]);
+        const f32x2 wpx = f2_mul(w, Bv[uu].x), wpy = f2_mul(w, Bv[uu].y);
+        Txp[r] = f2_fma(wpx, A[v].x, Txp[r]);
+        Txm[r] = f2_fma(wpy, A[v].y, Txm[r]);
+        Ty[r] = f2_fma(wpx, A[v].y, Ty[r]);
+        Ty[r] = f2_fma(wpy, A[v].x, Ty[r]);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32d(
+    const __grid_constant__ PsDiffDesc d, int nunits, int *__restrict__ err) {
+  using namespace packed;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [2]
+  unsigned long long *empty = full + 2;                                         // [2]
+  volatile int *abort = reinterpret_cast<volatile int *>(full + 4);
+  float4 *sy = reinterpret_cast<float4 *>(smem_raw + 128);    // [2][STAGE_Y]
+  float2 *sw = reinterpret_cast<float2 *>(sy + 2 * STAGE_Y);  // [2][STAGE_W] (envelope)
+  float *kst = reinterpret_cast<float *>(sw + 2 * STAGE_W);   // [2 NK][NCT]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&full[0], 32);
+    mbar_init(&full[1], 32);
+    mbar_init(&empty[0], NCT);
+    mbar_init(&empty[1], NCT);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int rs = d.rowstride;
+
+  if (warp == NC) {
+    // ---------------- producer ----------------
+    unsigned q = 0;
+    bool ok = true;
+    for (int k = 0; ok; ++k) {
+      const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
+      if (u >= nunits) break;
+      const int2 t = d.order[u / d.G];
+      const int grp = u - (u / d.G) * d.G;
+      const int kk = t.x, kws0 = t.y, nch = psd_nch(d.nw, kws0);
+      const int nitems = (kk + 1) * nch;
+      const int x = grp * LANES * 4;  // first float of the group in a row of y
+      int a = 0, c = 0;
+      for (int item = 0; item < nitems; ++item, ++q) {
+        const int stage = q & 1;
+        if (q >= 2 && !mbar_wait(&empty[stage], ((q >> 1) & 1) ^ 1, abort, err)) {
+          ok = false;
+          break;
+        }
+        const int j0 = c * CH;
+        if (lane == 0) {
+          mbar_expect_tx(&full[stage], YROWS * ROW_BYTES + EWIN * (unsigned)sizeof(float));
+          float4 *dst = sy + stage * STAGE_Y;
+          // the 16 rows jw = j0 .. j0 + 15 of b = kk - a, from the swapped copy
+          tma_load_2d(dst, &d.bmap, x, (kk - a) * rs + kPad + j0, &full[stage]);
+          // the rows kws0 + j0 .. kws0 + j0 + 47 of a
+#pragma unroll
+          for (int j = 0; j < YB_BOXES; ++j)
+            tma_load_2d(dst + (CH + BOX_ROWS * j) * LANES, &d.amap, x,
+                        a * rs + kPad + kws0 + j0 + BOX_ROWS * j, &full[stage]);
+          bulk_g2s(sw + stage * STAGE_W, d.Ewd + kws0 + 2 * j0, EWIN * sizeof(float),
+                   &full[stage]);
+        }
+        mbar_arrive(&full[stage]);
+        if (++c == nch) {
+          c = 0;
+          ++a;
+        }
+      }
+    }
+    if (!ok) {  // leave no bulk copy in flight: wait (bounded) for the last two stages
+      for (unsigned j = (q >= 2 ? q - 2 : 0); j < q; ++j) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(&full[j & 1], (j >> 1) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+    return;
+  }
+
+  // ---------------- compute warps ----------------
+  float *kacc = kst + tid, *kcmp = kst + NK * NCT + tid;
+  const size_t SP = (size_t)d.SSpad / 2;
+  (void)SP;
+  unsigned q = 0;
+  for (int k = 0;; ++k) {
+    const int u = ps_unit_id(k, blockIdx.x, gridDim.x);
+    if (u >= nunits) break;
+    const int2 t = d.order[u / d.G];
+    const int grp = u - (u / d.G) * d.G;
+    const int kk = t.x, kws0 = t.y, nw = d.nw;
+    const int kw0 = kws0 + R * warp, nch = psd_nch(nw, kws0);
+    const int nitems = (kk + 1) * nch;
+    const bool tile_ok = kw0 < nw;
+#pragma unroll
+    for (int j = 0; j < NK; ++j) kacc[j * NCT] = kcmp[j * NCT] = 0.f;
+    f32x2 Txp[R], Txm[R], Ty[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Txp[r] = Txm[r] = Ty[r] = 0ull;
+    int a = 0, c = 0;
+    for (int item = 0; item < nitems; ++item, ++q) {
+      const int stage = q & 1;
+      if (!mbar_wait(&full[stage], (q >> 1) & 1, abort, err)) return;
+      if (tile_ok) {
+        const float4 *pb = sy + stage * STAGE_Y + lane;
+        const float4 *pa = pb + (CH + R * warp) * LANES;
+        const float *pe = reinterpret_cast<const float *>(sw + stage * STAGE_W) + R * warp;
+        ps_chunk_diff<LANES>(pb, pa, pe, c * CH, kw0, nw, Txp, Txm, Ty);
+      }
+      mbar_arrive(&empty[stage]);
+      if (tile_ok && c == nch - 1) {  // row pair complete: merge
+        const int dk = 2 * a - kk;
+        const float rowfac = d.Ek[dk < 0 ? -dk : dk];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float2 xp = f2_split(Txp[r]), xm = f2_split(Txm[r]), yy = f2_split(Ty[r]);
+          const float v[4] = {xp.x - xm.x, xp.y - xm.y, yy.x, yy.y};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {  // Kahan: s += rowfac v with compensation
+            float &s_ = kacc[(4 * r + j) * NCT], &cp = kcmp[(4 * r + j) * NCT];
+            const float s0 = s_, yv = fmaf(rowfac, v[j], -cp);
+            const float tt = s0 + yv;
+            cp = (tt - s0) - yv;
+            s_ = tt;
+          }
+          Txp[r] = Txm[r] = Ty[r] = 0ull;
+        }
+      }
+      if (++c == nch) {
+        c = 0;
+        ++a;
+      }
+    }
+    if (!tile_ok) continue;
+    const int ss0 = grp * 2 * LANES + 2 * lane;
+    if (ss0 >= d.SS) continue;  // padding lanes
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int kw = kw0 + r;
+      if (kw >= nw) break;
+      if (kw == 0) continue;  // omega = 0 takes no difference pairs
+      const int kidx = kk * nw + kw;
+      const float cf = d.ck[kidx];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ss = ss0 + h;
+        if (ss >= d.SS) break;
+        const float ar = kacc[(4 * r + h) * NCT] - kcmp[(4 * r + h) * NCT];
+        const float ai = kacc[(4 * r + 2 + h) * NCT] - kcmp[(4 * r + 2 + h) * NCT];
+        float2 &o = d.C[((size_t)ss * d.nk + kk) * nw + kw];
+        float2 out = o;
+        out.x += cf * (ar * d.cb - ai * d.sb);
+        out.y += cf * (ar * d.sb + ai * d.cb);
+        o = out;
       }
     }
   }

@@ -301,7 +301,10 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
                             cudaMemcpyDeviceToHost, st));
   SRM3_CUDA(cudaStreamSynchronize(st));
   p->sumS = p->h_pinned[11];
-  p->rec_bar_words = 2 + (nk + nw) / kRecBL + 1;  // barrier counter + a ticket per bulk phase
+  // barrier counter, a ticket per bulk phase, and a readiness counter per
+  // level (the fringe)
+  p->rec_bar_tickets = 2 + (nk + nw) / kRecBL + 1;
+  p->rec_bar_words = p->rec_bar_tickets + nlev;
   SRM3_CUDA(dev_alloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
   int nsm = 0, dev = 0;
@@ -349,12 +352,14 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.e2 = p->sep ? p->env_e2 : nullptr;
   A.e2k = p->sep ? p->env_b2 : nullptr;
   A.qout = (p->sep && fp64) ? p->qm : nullptr;
+  A.dsum = (p->mixed && fp64 && M == 1) ? p->Dsum : nullptr;
   A.acc = p->rec_partial;
   A.sb2 = p->sb2;
   A.G2 = fp64 ? (const void *)p->G2 : (const void *)p->G2_32;
   A.scal = p->scal;
   A.err = p->err;
   A.bar = p->rec_bar;
+  A.done = p->rec_bar + p->rec_bar_tickets;
   A.abort = p->err + kPlanes;
   A.maxb = p->rec_max;
   A.zr = p->rec_fft ? p->rec_z : nullptr;
@@ -405,6 +410,88 @@ static int run_pass(srm3_plan *p, cudaStream_t st, double x, bool fp64, PassResu
   return run_pass_multi(p, st, &x, 1, fp64, r);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-sign interactions: Eq. pure as a fixed point.  With difference pairs
+// S_p(k) depends on points of higher omega, so q = S/S_p solves
+//   q_k = 1 / (1 - x dk dw [sum_{Pi(k)} g^2 q_i q_j + sum_{D(k)} g^2 q_i q_j]).
+// The right side increases with q and with x, so iterations that start
+// below the largest-S_p (smallest-q) solution rise to it monotonically: from
+// q = 1, or from the converged q of a smaller x.  One iteration is the
+// difference sums at the current q (k_rec_diff) followed by one level pass,
+// which takes the sum pairs of every point from the values the pass has just
+// formed at lower levels -- the Gauss-Seidel order of the plain recursion --
+// and adds the difference sums before forming q_k.  The iterations stop when
+// no q_k moves by more than kFpTol relative; they give up (the solve counts
+// as failed, as above the target) after kFpMaxIters, and a pass that meets
+// sum b_p^2 >= 1 fails at once.
+constexpr double kFpTol = 4e-16;
+constexpr int kFpMaxIters = 400;
+
+__global__ void k_q_init(long long n, const double *__restrict__ S, double *__restrict__ q) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = S[i] > 0.0 ? 1.0 : 0.0;
+}
+
+// max over S > 0 of |qn - qo| / qn into *out (the bits of a double >= 0)
+__global__ void k_q_change(long long n, const double *__restrict__ S,
+                           const double *__restrict__ qn, const double *__restrict__ qo,
+                           unsigned long long *out) {
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (S[i] > 0.0 && qn[i] > 0.0) m = fmax(m, fabs(qn[i] - qo[i]) / qn[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Solve the fixed point at x from the iterate in p->qm; r: the last pass
+// (r->err != 0: no solution was reached).
+static int solve_mixed(srm3_plan *p, cudaStream_t st, double x, PassResult *r) {
+  const long long nl = (long long)p->nk * p->nw;
+  for (int it = 1; it <= kFpMaxIters; ++it) {
+    k_rec_diff<<<cdiv(nl * 32, 256), 256, 0, st>>>(p->nk, p->nw, p->S, p->qm, p->EkSq, p->EwSq,
+                                                    p->Dsum);
+    SRM3_CUDA(cudaGetLastError());
+    SRM3_CUDA(cudaMemcpyAsync(p->qprev, p->qm, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int rc = run_pass_multi(p, st, &x, 1, true, r);
+    if (rc) return rc;
+    p->fp_iters = it;
+    if (r->err) return SRM3_OK;
+    SRM3_CUDA(cudaMemsetAsync(p->fp_change, 0, sizeof(unsigned long long), st));
+    k_q_change<<<std::min(cdiv(nl, 256), 1024), 256, 0, st>>>(nl, p->S, p->qm, p->qprev,
+                                                               p->fp_change);
+    SRM3_CUDA(cudaGetLastError());
+    unsigned long long bits = 0;
+    SRM3_CUDA(cudaMemcpyAsync(&bits, p->fp_change, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    SRM3_CUDA(cudaStreamSynchronize(st));
+    double ch;
+    std::memcpy(&ch, &bits, sizeof(ch));
+    if (it >= 2 && ch <= kFpTol) return SRM3_OK;
+  }
+  r->err = 1;  // no convergence: treated as an infeasible x
+  return SRM3_OK;
+}
+
+// One FP64 evaluation of max_k sum_b2 at x: a recursion pass, or for mixed
+// plans a fixed-point solve started from the converged q of the largest x
+// below the target seen so far (when x is above it), else from q = 1.
+static int eval_fp64(srm3_plan *p, cudaStream_t st, double x, double target, PassResult *r) {
+  if (!p->mixed) return run_pass_multi(p, st, &x, 1, true, r);
+  const long long nl = (long long)p->nk * p->nw;
+  if (p->qlo_x >= 0.0 && x >= p->qlo_x)
+    SRM3_CUDA(cudaMemcpyAsync(p->qm, p->qlo, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else
+    k_q_init<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm);
+  SRM3_CUDA(cudaGetLastError());
+  int rc = solve_mixed(p, st, x, r);
+  if (rc) return rc;
+  if (!r->err && r->max_sb2 < target && x > p->qlo_x) {
+    SRM3_CUDA(cudaMemcpyAsync(p->qlo, p->qm, nl * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    p->qlo_x = x;
+  }
+  return SRM3_OK;
+}
+
 // Bracketed FP64 root search on x = eps^2 for f(x) = max_k sum_b2(x) -
 // target, which increases with x; a failed pass (some S_p <= 0) counts as
 // above target.  Illinois regula falsi (bisection while the upper end is a
@@ -428,7 +515,7 @@ static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, in
       x = b.xhi - b.fhi * (b.xhi - b.xlo) / (b.fhi - b.flo);
       if (!(x > b.xlo && x < b.xhi)) x = 0.5 * (b.xlo + b.xhi);
     }
-    int rc = run_pass(p, st, x, true, &r);
+    int rc = eval_fp64(p, st, x, target, &r);
     if (rc) return rc;
     xlast = x;
     if (r.err) {
@@ -455,6 +542,60 @@ static int illinois(srm3_plan *p, cudaStream_t st, double target, double tol, in
     }
   }
   *tables_at_best = (xlast == *xbest);
+  return SRM3_OK;
+}
+
+// eps of a mixed plan: FP64 fixed-point solves only.  The slope at q = 1
+// comes from one solve at a vanishing x (every q rounds to 1): L = sum_b2 /
+// x, sum and difference pairs.  At x0 = target / max L the sum is at least
+// the target (q >= 1), and at 0.9 (1 - target)^2 x0 it is below it (every q
+// <= 1/(1 - target) below the root); Illinois regula falsi between them,
+// each evaluation warm-started from the largest x found below the target.
+static int find_eps_mixed(srm3_plan *p, cudaStream_t st, double target, double tol) {
+  const long long nl = (long long)p->nk * p->nw;
+  PassResult r;
+  const double xt = 1e-20;
+  p->qlo_x = -1.0;
+  k_q_init<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm);
+  SRM3_CUDA(cudaGetLastError());
+  int rc = solve_mixed(p, st, xt, &r);
+  if (rc) return rc;
+  const double Lmax = r.max_sb2 / xt;
+  if (!(Lmax > 0.0))
+    return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
+  const double x0 = target / Lmax;
+  Bracket b{0.0, -target, x0, 1.0, true};
+  double xbest = -1.0;
+  PassResult best{};
+  const double xa = 0.9 * (1.0 - target) * (1.0 - target) * x0;
+  if ((rc = eval_fp64(p, st, xa, target, &r))) return rc;
+  if (!r.err && r.max_sb2 < target) {
+    b.xlo = xa;
+    b.flo = r.max_sb2 - target;
+    xbest = xa;
+    best = r;
+  }
+  if ((rc = eval_fp64(p, st, x0, target, &r))) return rc;
+  if (!r.err) {
+    b.fhi = r.max_sb2 - target;
+    b.hi_failed = false;
+    xbest = x0;
+    best = r;
+  }
+  bool at_best = !r.err;
+  if (r.err || std::fabs(r.max_sb2 - target) > tol) {
+    rc = illinois(p, st, target, tol, 200, b, &xbest, &best, &at_best);
+    if (rc) return rc;
+  }
+  if (xbest < 0.0) return fail(SRM3_ERR_BISECTION_FAILED, "eps search found no feasible point");
+  if (!at_best) {
+    if ((rc = eval_fp64(p, st, xbest, target, &best))) return rc;
+    if (best.err) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: final solve failed");
+  }
+  p->eps = std::sqrt(xbest);
+  p->max_sb2 = best.max_sb2;
+  p->min_pure = best.min_pure;
+  p->variance = 4.0 * p->dkdw * best.sumS;
   return SRM3_OK;
 }
 
@@ -732,6 +873,17 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   SRM3_CUDA(cudaMemcpyAsync(p->super_order, sup.data(), sizeof(int2) * p->nsuper,
                             cudaMemcpyHostToDevice, st));
   p->super_host = sup;
+  if (p->mixed) {  // the difference pass: (kk + 1) row pairs x ceil((nw - kws0) / 16) chunks
+    std::vector<int2> supd(p->nsuper);
+    for (int i = 0; i < p->nsuper; ++i) supd[i] = make_int2(i / nsw, (i % nsw) * sw);
+    auto cost = [&](int2 t) { return (long long)(t.x + 1) * ((p->nw - t.y + 15) / 16); };
+    std::stable_sort(supd.begin(), supd.end(),
+                     [&](int2 a, int2 b) { return cost(a) > cost(b); });
+    p->nsuper_d = p->nsuper;
+    SRM3_CUDA(dev_alloc(&p->super_order_d, sizeof(int2) * p->nsuper, st));
+    SRM3_CUDA(cudaMemcpyAsync(p->super_order_d, supd.data(), sizeof(int2) * p->nsuper,
+                              cudaMemcpyHostToDevice, st));
+  }
   *table_entries = off[p->ntiles];
   (void)want_table;  // offsets are kept either way: the autotuner may build W later
   SRM3_CUDA(dev_alloc(&p->tile_off, sizeof(long long) * p->ntiles, st));
@@ -764,13 +916,15 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   SRM3_CUDA(dev_alloc(&p->qm, nl * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->sb2, kPlanes * nl * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->EkSq, nk * sizeof(double), st));
-  SRM3_CUDA(dev_alloc(&p->EwSq, nw * sizeof(double), st));
+  // EwSq, EwSq32 hold 2 nw entries: the signed frequency difference of a
+  // difference pair (kw + 2 jw) reaches 2 nw - 2
+  SRM3_CUDA(dev_alloc(&p->EwSq, 2 * nw * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->scal, (8 + 4 * kPlanes) * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->err, (kPlanes + 1) * sizeof(int), st));
   SRM3_CUDA(cudaMemsetAsync(p->qm, 0, nl * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->qm32, kPlanes * nl * sizeof(float), st));
   SRM3_CUDA(dev_alloc(&p->EkSq32, nk * sizeof(float), st));
-  SRM3_CUDA(dev_alloc(&p->EwSq32, nw * sizeof(float), st));
+  SRM3_CUDA(dev_alloc(&p->EwSq32, 2 * nw * sizeof(float), st));
   SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kPlanes * nl * sizeof(float), st));
 
   // a1: spectrum on the lattice
@@ -782,7 +936,7 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     SRM3_CUDA(cudaMemcpyAsync(p->S, sp->table, nl * sizeof(double), cudaMemcpyHostToDevice, st));
   }
   k_env_sq<<<cdiv(nk, 256), 256, 0, st>>>(nk, p->sigma_g * nk, p->EkSq, p->EkSq32);
-  k_env_sq<<<cdiv(nw, 256), 256, 0, st>>>(nw, p->sigma_g * nw, p->EwSq, p->EwSq32);
+  k_env_sq<<<cdiv(2 * nw, 256), 256, 0, st>>>(2 * nw, p->sigma_g * nw, p->EwSq, p->EwSq32);
   SRM3_CUDA(dev_alloc(&p->G2, nl * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&p->G2_32, nl * sizeof(float), st));
   if (p->sep) {
@@ -819,7 +973,31 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   // a2: recursion, one graph node per anti-diagonal level
   int rc = setup_recursion(p, st);
   if (rc) return rc;
-  if (bs->target_max_sum_b2 > 0.0) {
+  if (p->mixed) {
+    SRM3_CUDA(dev_alloc(&p->Dsum, nl * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&p->qprev, nl * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&p->qlo, nl * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&p->fp_change, sizeof(unsigned long long), st));
+  }
+  if (p->mixed && bs->target_max_sum_b2 > 0.0) {
+    rc = find_eps_mixed(p, st, bs->target_max_sum_b2,
+                        p->precision == SRM3_FP64 ? 1e-13 : 1e-9);
+    if (rc) return rc;
+  } else if (p->mixed) {
+    PassResult r;
+    p->qlo_x = -1.0;
+    rc = eval_fp64(p, st, bs->eps * bs->eps, 2.0, &r);
+    if (rc) return rc;
+    if (r.err)
+      return fail(SRM3_ERR_NONPOSITIVE_PURE,
+                  p->fp_iters >= kFpMaxIters
+                      ? "mixed interactions: the fixed point of Eq. pure was not reached"
+                      : "sum_b2 >= 1 at some lattice point: the pure spectrum is not positive");
+    p->eps = bs->eps;
+    p->max_sb2 = r.max_sb2;
+    p->min_pure = r.min_pure;
+    p->variance = 4.0 * p->dkdw * r.sumS;
+  } else if (bs->target_max_sum_b2 > 0.0) {
     // FP64 plans meet the target to 1e-13; for FP32 plans 1e-9 is far inside
     // what their fields can resolve (1e-4 sigma) and saves an FP64 pass
     rc = find_eps(p, st, bs->target_max_sum_b2, p->precision == SRM3_FP64 ? 1e-13 : 1e-9);
@@ -846,6 +1024,11 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
       pairs += (m + 1) / 2;
     }
   p->pairs = pairs;
+  long long dpairs = 0;  // difference pairs of one sheet
+  if (p->mixed)
+    for (int kk = 0; kk < nk; ++kk)
+      for (int kw = 1; kw < nw; ++kw) dpairs += (long long)(kk + 1) * (nw - 1 - kw);
+  p->diffpairs = dpairs;
 
   rc = prepare_sampling_tables(p, st);
   if (rc) return rc;
@@ -866,6 +1049,7 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     if (p->storage == SRM3_STORAGE_AUTO) {
       p->storage = bytes <= p->table_budget ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
     }
+    if (p->mixed) p->storage = SRM3_STORAGE_RECOMPUTE;  // the table holds sum pairs only
     if (p->storage == SRM3_STORAGE_TABLE) {
       if ((rc = build_w_table(p, st))) return rc;
     } else {
@@ -890,7 +1074,7 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   // FP32 table (first d = 2 i0 - kws0 - 31, 1 mod 4) on 16-byte boundaries;
   // the table reaches d = nw + 127, past the last window.
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
-  p->ew_len = p->ew_off + nw + 128;
+  p->ew_len = p->ew_off + 2 * nw + 128;  // difference pairs reach d = 2 nw - 2
   p->nfft = std::max(p->nx, p->nt);
   if (p->sep) {  // zero-padded self-convolution grid
     p->log2cNk = 1;
@@ -917,6 +1101,12 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
                                                       (float *)p->Ews);
     SRM3_CUDA(dev_alloc(&p->ps_err, sizeof(int), st));
     SRM3_CUDA(cudaMemsetAsync(p->ps_err, 0, sizeof(int), st));
+    if (p->mixed) {  // envelope of the signed difference d = kw + 2 jw, d from 0
+      p->ewd_len = 2 * nw + 128;
+      SRM3_CUDA(dev_alloc(&p->Ewd, p->ewd_len * sizeof(float), st));
+      k_env<float><<<cdiv(p->ewd_len, 256), 256, 0, st>>>(p->ewd_len, 0, p->sigma_g * nw,
+                                                         (float *)p->Ewd);
+    }
     k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
                                                           (float2 *)p->tw);
     if (p->sep) {
@@ -984,7 +1174,8 @@ void free_plan(srm3_plan *p) {
                  p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
-                 p->sep_b ? (void *)p->env_b32 : nullptr};
+                 p->sep_b ? (void *)p->env_b32 : nullptr,
+                 p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)
@@ -1047,6 +1238,16 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   } else {
     return fail(SRM3_ERR_INVALID_ARG, "unknown bispectrum kind");
   }
+  if (bispectrum->interactions != SRM3_INTERACTIONS_SUM &&
+      bispectrum->interactions != SRM3_INTERACTIONS_MIXED)
+    return fail(SRM3_ERR_INVALID_ARG, "unknown interactions");
+  if (bispectrum->interactions == SRM3_INTERACTIONS_MIXED) {
+    if (bispectrum->kind != SRM3_BISPECTRUM_GAUSS_ENVELOPE)
+      return fail(SRM3_ERR_NOT_SUPPORTED, "mixed interactions take the Gaussian envelope only");
+    if (g.storage == SRM3_STORAGE_TABLE)
+      return fail(SRM3_ERR_NOT_SUPPORTED,
+                  "mixed interactions recompute W (the W table holds sum pairs only)");
+  }
   const double tgt = bispectrum->target_max_sum_b2;
   if (!(tgt >= 0.0 && tgt < 1.0)) return fail(SRM3_ERR_INVALID_ARG, "target must be in [0, 1)");
   if (tgt == 0.0 && !(bispectrum->eps >= 0.0))
@@ -1069,6 +1270,7 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->storage = g.storage;
   p->stream = (cudaStream_t)g.stream;
   p->sep = bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE;
+  p->mixed = bispectrum->interactions == SRM3_INTERACTIONS_MIXED;
   p->sigma_g = p->sep ? 0.25 : bispectrum->sigma_g;
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
@@ -1116,6 +1318,9 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->storage = plan->storage;
   info->precision = plan->precision;
   info->tile_r = kTileR;
+  info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
+  info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
+  info->diff_pairs = plan->diffpairs;
   return SRM3_OK;
 }
 
@@ -1127,9 +1332,13 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
 // One warp per lattice point, pairs enumerated as in the direct levels of the
 // recursion (rows a <= kk/2, centre row iw <= kw/2, i = 0 skipped); FP64.
 // part[k] = sqrt(S_k) times the point's pair sum.
+// Mixed plans add their difference pairs (two distinct points: m = 6), g
+// from the envelope of the signed frequency difference kw + 2 jw.
 __global__ void k_moment3(int nk, int nw, const double *__restrict__ S,
                           const double *__restrict__ G2, const double *__restrict__ ea,
-                          const double *__restrict__ eb, double *__restrict__ part) {
+                          const double *__restrict__ eb, int mixed,
+                          const double *__restrict__ EkSq, const double *__restrict__ EwSq,
+                          double *__restrict__ part) {
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= (long long)nk * nw) return;
@@ -1150,6 +1359,18 @@ __global__ void k_moment3(int nk, int nw, const double *__restrict__ S,
       const double m = (i == j) ? 3.0 : 6.0;
       acc += m * g * sqrt(si * sj);
     }
+    const int J = nw - 1 - kw;
+    if (mixed && kw >= 1 && J >= 1) {
+      const int E2 = (kk + 1) * J;
+      for (int e = lane; e < E2; e += 32) {
+        const int ia = e / J, jw = 1 + e - ia * J;
+        const double si = S[(size_t)ia * nw + kw + jw], sj = S[(size_t)(kk - ia) * nw + jw];
+        if (!(si > 0.0) || !(sj > 0.0)) continue;
+        const int dk = 2 * ia - kk;
+        const double g = sqrt(EkSq[dk < 0 ? -dk : dk] * EwSq[kw + 2 * jw]);
+        acc += 6.0 * g * sqrt(si * sj);
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) part[gw] = acc * sqrt(S[gw] > 0.0 ? S[gw] : 0.0);
@@ -1165,7 +1386,7 @@ SRM3_API int srm3_plan_moments(const srm3_plan *plan, double *variance, double *
   const long long threads = nl * 32;
   k_moment3<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
       plan->nk, plan->nw, plan->S, plan->G2, plan->sep ? plan->env_e : nullptr,
-      plan->sep ? plan->env_b : nullptr, part);
+      plan->sep ? plan->env_b : nullptr, plan->mixed ? 1 : 0, plan->EkSq, plan->EwSq, part);
   cudaError_t e = cudaGetLastError();
   std::vector<double> h(nl);
   if (e == cudaSuccess)

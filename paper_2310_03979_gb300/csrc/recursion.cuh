@@ -42,8 +42,13 @@ struct RecArgs {
   void *zr;
   const void *twr;
   int log2Nc, zcap;
+  // mixed-sign interactions (else NULL): the difference-pair sums of every
+  // point, sum g^2 q_i q_j over its opposite-sheet pairs at the previous
+  // iterate of the fixed point, added before q_k is formed (M = 1 only)
+  const double *dsum;
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
+  unsigned int *done;   // [nlev]: points finalized on each fringe level (zero at launch)
   int *abort;           // barrier wait timed out
   unsigned long long *maxb;  // [M]: max_k sum_b2 per plane, as the bits of a double >= 0
 };
@@ -86,6 +91,52 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsi
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Readiness of the fringe levels.  A point of level d in a fringe block
+// needs the q of its pair partners on levels [D, d): instead of a grid
+// barrier per level, each finalized point adds 1 to done[d] (release, after
+// a warp barrier over the lanes that wrote its planes), and a warp that
+// needs level l polls done[l] with acquire loads (lane 0, then a warp
+// barrier) until it holds the level's point count.  Levels complete in
+// order -- a point waits for the level below it before it is finalized -- so
+// level l complete means every level below it is too.  Waits are bounded
+// like the grid barrier; a warp that gives up (or sees another's abort)
+// raises the abort state, skips its remaining points and meets the next grid
+// barrier, which then fails for every CTA.
+__host__ __device__ __forceinline__ int level_points(int nk, int nw, int lev) {
+  return min(lev, nk - 1) - max(0, lev - nw + 1) + 1;
+}
+
+__device__ __forceinline__ bool wait_level(const unsigned int *done, unsigned int *bar,
+                                           int *abort, int want, int lev, int lane,
+                                           long long limit = 1ll << 22) {
+  int ok = 1;
+  if (lane == 0) {
+    unsigned int v;
+    long long spins = 0;
+    for (;;) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done + lev) : "memory");
+      if (v >= (unsigned)want) break;
+      if ((++spins & 255) == 0 && *(volatile int *)abort) {
+        ok = 0;
+        break;
+      }
+      if (spins > limit) {
+        ok = 0;
+        atomicOr(bar, kBarAbort);
+        atomicExch(abort, 1);
+        break;
+      }
+    }
+  }
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void publish_level(unsigned int *done, int lev, int lane) {
+  __syncwarp();
+  if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(done + lev) : "memory");
 }
 
 template <typename T, int M>
@@ -148,6 +199,7 @@ __device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, in
   // t >= 0 (a sum of non-negative terms) up to the rounding of the FFT form,
   // which can leave a small negative value, of the order of the rounding of
   // the largest sums, where every term is zero; a NaN passes through
+  if (M == 1 && A.dsum) t += (T)A.dsum[k];
   const T s2r = (T)A.scal[m] * bk2 * t;
   const T s2 = s2r < (T)0 ? (T)0 : s2r;
   A.sb2[m * A.nl + k] = (double)s2;
@@ -390,40 +442,20 @@ __device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, 
 
 constexpr int kFringeUnroll = 4;
 
-// Fringe of a point at level d in [D, D + BL): the pairs whose higher
-// element lies on a level in [D, d).  Their other element l has level
-// 1 .. d - D < BL <= D, so each such pair is {l, k - l} for exactly one
-// low lattice point l: the t(t+3)/2 points of levels 1..t, t = d - D,
-// enumerated level by level.  Adds the bulk sums and finalizes the point.
+// Fringe pairs e in [e_begin, e_end) of a point: e enumerates the low
+// element l level by level (levels 1..l hold l (l + 3) / 2 points), the
+// pair being {l, k - l}.
 template <typename T, int M>
-__device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) {
-  const long long k = (long long)kk * A.nw + kw;
-  // S_k is read beside the pair loads rather than ahead of them: a point
-  // with S_k = 0 sums its (finite) terms like any other and is zeroed at
-  // the end, which keeps one memory round trip off the level's critical path
-  const double Sk = A.S[k];
-  // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
-  T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
-  if (A.zr && lane < M && ((kk | kw) & 1) == 0) {
-    // FFT form: the bulk holds half the ordered pairs; the pair {k/2, k/2}
-    // enters the unordered sum once
-    const T hh = static_cast<const T *>(A.q)[((long long)(kk >> 1) * A.nw + (kw >> 1)) * M + lane];
-    bulk += (T)0.5 * hh * hh;
-  }
-  const int t = kk + kw - D;
-  const int nlow = t * (t + 3) / 2;
-  T acc[M];
-#pragma unroll
-  for (int m = 0; m < M; ++m) acc[m] = (T)0;
+__device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, int e_begin,
+                                             int e_end, int lane, T (&acc)[M]) {
   const int nw = A.nw;
   const T *G2 = static_cast<const T *>(A.G2);
   const T *q = static_cast<const T *>(A.q);
-  for (int e0 = lane; e0 < nlow; e0 += 32 * kFringeUnroll) {
+  for (int e0 = e_begin + lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
     T g2[kFringeUnroll], va[kFringeUnroll][M], vb[kFringeUnroll][M];
 #pragma unroll
     for (int s = 0; s < kFringeUnroll; ++s) {
-      // e -> level l of the low point (levels 1..l hold l (l + 3) / 2
-      // points) and its place rem on that level
+      // e -> level l of the low point and its place rem on that level
       const int e = e0 + 32 * s;
       int l = (int)ceilf((sqrtf(9.f + 8.f * (float)(e + 1)) - 3.f) * 0.5f);
       l = max(l, 1);
@@ -432,7 +464,7 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
       const int rem = e - (l - 1) * (l + 2) / 2;
       const int lk = rem, lw = l - rem;
       const int hk = kk - lk, hw = kw - lw;
-      const bool ok = e < nlow && hk >= 0 && hw >= 0;
+      const bool ok = e < e_end && hk >= 0 && hw >= 0;
       const int dk = 2 * lk - kk, dw = 2 * lw - kw;
       const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
       const size_t qa = ok ? ((size_t)lk * nw + lw) * M : 0;
@@ -446,18 +478,59 @@ __device__ void point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
 #pragma unroll
       for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
   }
+}
+
+// Fringe of a point at level d in [D, D + BL): the pairs whose higher
+// element lies on a level in [D, d).  Their other element l has level
+// 1 .. d - D < BL <= D, so each such pair is {l, k - l} for exactly one
+// low lattice point l: the t(t+3)/2 points of levels 1..t, t = d - D.
+// The pairs with l on levels 2..t (higher element on levels [D, d - 2]) are
+// summed once level d - 2 is complete, the two with l on level 1 -- (0, 1)
+// and (1, 0), higher element on level d - 1 -- once level d - 1 is: most of
+// a point's fringe overlaps the finalisation of the level below it.  Adds
+// the bulk sums, finalizes the point and publishes it.  Returns false when
+// a readiness wait gave up (the point is then left unpublished).
+template <typename T, int M>
+__device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) {
+  const long long k = (long long)kk * A.nw + kw;
+  // S_k is read beside the pair loads rather than ahead of them: a point
+  // with S_k = 0 sums its (finite) terms like any other and is zeroed at
+  // the end, which keeps one memory round trip off the level's critical path
+  const double Sk = A.S[k];
+  // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
+  T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
+  if (A.zr && lane < M && ((kk | kw) & 1) == 0) {
+    // FFT form: the bulk holds half the ordered pairs; the pair {k/2, k/2}
+    // enters the unordered sum once
+    const T hh = static_cast<const T *>(A.q)[((long long)(kk >> 1) * A.nw + (kw >> 1)) * M + lane];
+    bulk += (T)0.5 * hh * hh;
+  }
+  const int d = kk + kw, t = d - D;
+  T acc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) acc[m] = (T)0;
+  if (t >= 2) {
+    if (!wait_level(A.done, A.bar, A.abort, level_points(A.nk, A.nw, d - 2), d - 2, lane))
+      return false;
+    fringe_pairs<T, M>(A, kk, kw, 2, t * (t + 3) / 2, lane, acc);
+  }
+  if (t >= 1) {
+    if (!wait_level(A.done, A.bar, A.abort, level_points(A.nk, A.nw, d - 1), d - 1, lane))
+      return false;
+    fringe_pairs<T, M>(A, kk, kw, 0, 2, lane, acc);
+  }
   warp_sum<T, M>(acc);
   if (!(Sk > 0.0)) {
     point_zero<T, M>(A, k, lane);
-    return;
-  }
-  if (lane < M) {
-    T t = (T)0;
+  } else if (lane < M) {
+    T tt = (T)0;
 #pragma unroll
     for (int m = 0; m < M; ++m)
-      if (m == lane) t = acc[m];
-    finalize_plane<T, M>(A, k, lane, t + bulk);
+      if (m == lane) tt = acc[m];
+    finalize_plane<T, M>(A, k, lane, tt + bulk);
   }
+  publish_level(A.done, d, lane);
+  return true;
 }
 
 // ---- separable envelope: the bulk as an online FFT self-convolution ----
@@ -653,12 +726,17 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
       }
       if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
+    // fringe levels: readiness counters instead of a grid barrier per level
+    // (a warp that gave up skips its remaining points; the grid barrier
+    // after the block then fails for every CTA)
     const int dend = min(D + kRecBL, A.nlev);
-    for (int d = D; d < dend; ++d) {
+    bool live = true;
+    for (int d = D; d < dend && live; ++d) {
       const int lo = max(0, d - A.nw + 1), n = min(d, A.nk - 1) - lo + 1;
-      for (int i = gw; i < n; i += nwarps) point_fringe<T, M>(A, lo + i, d - lo - i, D, lane);
-      if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
+      for (int i = gw; i < n && live; i += nwarps)
+        live = point_fringe<T, M>(A, lo + i, d - lo - i, D, lane);
     }
+    if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
 }
 
@@ -708,6 +786,39 @@ __global__ void __launch_bounds__(kLinOut) k_rec_linear(int nk, int nw, const do
     const size_t k = (size_t)kk * nw + kw;
     sb2[k] = S[k] > 0.0 ? dkdw * (double)acc : 0.0;
   }
+}
+
+// Difference-pair sums of the mixed-sign interactions for every point at the
+// iterate q (FP64, q = 0 where S = 0): for k = (kk, kw), kw >= 1, S_k > 0,
+//   D_k = sum_{ia=0..kk} EkSq[|2 ia - kk|] sum_{jw=1..nw-1-kw}
+//         EwSq[kw + 2 jw] q(ia, kw + jw) q(kk - ia, jw)
+// -- i = (ia, kw + jw) on the point's sheet, j = (kk - ia, jw) on the other,
+// g^2 of the signed frequency difference kw + 2 jw (EwSq holds 2 nw
+// entries); both sheets share q, so one D serves both.  One warp per point,
+// lanes along jw (coalesced rows of q), a fixed order of additions.
+__global__ void __launch_bounds__(256) k_rec_diff(int nk, int nw, const double *__restrict__ S,
+                                                  const double *__restrict__ q,
+                                                  const double *__restrict__ EkSq,
+                                                  const double *__restrict__ EwSq,
+                                                  double *__restrict__ D) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (long long)nk * nw) return;
+  const int kk = (int)(gw / nw), kw = (int)(gw - (long long)kk * nw);
+  double acc = 0.0;
+  if (kw >= 1 && S[gw] > 0.0) {
+    const int J = nw - 1 - kw;
+    for (int ia = 0; ia <= kk; ++ia) {
+      const double *qa = q + (size_t)ia * nw + kw;  // qa[jw] = q(ia, kw + jw)
+      const double *qb = q + (size_t)(kk - ia) * nw;
+      double r = 0.0;
+      for (int jw = 1 + lane; jw <= J; jw += 32) r = fma(EwSq[kw + 2 * jw], qa[jw] * qb[jw], r);
+      const int dk = 2 * ia - kk;
+      acc = fma(EkSq[dk < 0 ? -dk : dk], r, acc);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) D[gw] = acc;
 }
 
 }  // namespace srm3

@@ -56,13 +56,16 @@ __device__ __forceinline__ double2 phasor(uint32_t w, double) {
 // Writes y^s_k = sqrt(q_k) z^s_k (0 where S = 0) into the padded layout
 // y[kk][kPad + kw][ss], ss = ss_off + 2 n + s, except that y at k = 0 goes to y0[ss]
 // and the lattice slot of k = 0 holds 0 (it takes part in no pair).  With
-// words != NULL writes the raw words[n][2][nk][nw] instead.
+// words != NULL writes the raw words[n][2][nk][nw] instead.  FP32 mixed
+// plans (ys != NULL) also get ys, the same rows with the two sheets of each
+// sample swapped in its lane ({x-, x+, y-, y+}) and the omega = 0 column
+// zero: the partners of the difference pairs, which never sit at omega = 0.
 template <typename T>
 __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
                          const uint64_t *__restrict__ dseeds, int ss_off,
                          const T *__restrict__ sqq, typename Vec2<T>::type *__restrict__ y,
                          typename Vec2<T>::type *__restrict__ y0, int SSpad, int rowstride,
-                         uint32_t *__restrict__ words) {
+                         uint32_t *__restrict__ words, float *__restrict__ ys) {
   using T2 = typename Vec2<T>::type;
   const long long nl = (long long)nk * nw;
   const long long nc = (2 * nl + 3) / 4;
@@ -102,6 +105,11 @@ __global__ void k_phases(int nk, int nw, int nsamp, SeedChunk seeds,
       float *yf = reinterpret_cast<float *>(y) + (row * (SSpad / 2) + (ss >> 1)) * 4 + (ss & 1);
       yf[0] = v.x;
       yf[2] = v.y;
+      if (ys) {
+        float *sf = ys + (row * (SSpad / 2) + (ss >> 1)) * 4 + (1 - (ss & 1));
+        sf[0] = kw == 0 ? 0.0f : (float)v.x;
+        sf[2] = kw == 0 ? 0.0f : (float)v.y;
+      }
     } else {
       y[row * SSpad + ss] = v;
     }
@@ -123,7 +131,7 @@ int ensure_workspace(srm3_plan *p, int chunk) {
     return fail(SRM3_ERR_NOT_SUPPORTED,
                 "the plan's workspace belongs to a batch and cannot grow while the batch exists");
   int cap = std::max(chunk, std::min(kMaxChunk, 64));
-  for (void **q : {&p->y, &p->y0, &p->C, &p->H}) {
+  for (void **q : {&p->y, &p->y0, &p->C, &p->H, &p->ys}) {
     if (*q) dev_free(*q, p->stream);
     *q = nullptr;
   }
@@ -135,6 +143,8 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   SRM3_CUDA(dev_alloc(&p->y0, (size_t)sp * e2, p->stream));
   SRM3_CUDA(dev_alloc(&p->C, (size_t)2 * cap * p->nk * p->nw * e2, p->stream));
   SRM3_CUDA(dev_alloc(&p->H, (size_t)cap * p->nk * p->nt * e2, p->stream));
+  if (p->mixed && p->precision == SRM3_FP32)
+    SRM3_CUDA(dev_alloc(&p->ys, (size_t)p->nk * p->rowstride * sp * e2, p->stream));
   if (p->sep) {  // the self-convolution grid of every sheet-sample of a chunk
     if (p->Zc) dev_free(p->Zc, p->stream);
     p->Zc = nullptr;
@@ -160,14 +170,17 @@ static int phases_into(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
   const long long nl = (long long)p->nk * p->nw;
   const long long nc = (2 * nl + 3) / 4;
   const int blocks = cdiv(nc * n, 256);
+  // the swapped copy of the mixed FP32 pair sum (plan workspace only)
+  float *ys = (p->mixed && p->precision == SRM3_FP32 && y == p->y) ? (float *)p->ys : nullptr;
   if (p->precision == SRM3_FP32)
     k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
                                             (const float *)p->sqq, (float2 *)y, (float2 *)y0,
-                                            sp, p->rowstride, words_out);
+                                            sp, p->rowstride, words_out, ys);
   else
     k_phases<double><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
                                              (const double *)p->sqq, (double2 *)y,
-                                             (double2 *)y0, sp, p->rowstride, words_out);
+                                             (double2 *)y0, sp, p->rowstride, words_out,
+                                             nullptr);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -178,6 +191,8 @@ static int phases_on(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
   const int sp = sspad_for(n);
   if (!words_out) {
     SRM3_CUDA(cudaMemsetAsync(p->y, 0, (size_t)p->nk * p->rowstride * sp * elem2(p), st));
+    if (p->ys)
+      SRM3_CUDA(cudaMemsetAsync(p->ys, 0, (size_t)p->nk * p->rowstride * sp * elem2(p), st));
   }
   return phases_into(p, st, seeds, dseeds, n, p->y, p->y0, sp, 0, words_out);
 }
@@ -194,9 +209,8 @@ int fill_pairsum_desc(srm3_plan *p, int n, void *C_out, PsDesc *d) {
   return fill_pairsum_desc_into(p, n, p->y, p->y0, C_out, d);
 }
 
-// The same for phasor rows y / y0 of n samples laid out for sspad_for(n).
-static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *C_out,
-                                  PsDesc *d) {
+// The driver's tensor-map encoder, looked up once.
+static int tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000 *out) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void *fn = nullptr;
@@ -207,6 +221,15 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
       return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
+  *out = encode;
+  return SRM3_OK;
+}
+
+// The same for phasor rows y / y0 of n samples laid out for sspad_for(n).
+static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *C_out,
+                                  PsDesc *d) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (int rc = tensor_map_encoder(&encode)) return rc;
   const int sp = sspad_for(n);
   std::memset(static_cast<void *>(d), 0, sizeof(*d));
   const bool table = p->storage == SRM3_STORAGE_TABLE;
@@ -284,13 +307,67 @@ int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const Ps
   return SRM3_OK;
 }
 
+// The difference-pair launch of a mixed FP32 plan over n samples whose rows
+// are in the plan workspace (y and its swapped copy ys, laid out for
+// sspad_for(n)), adding to the coefficients C_out that the sum pairs wrote.
+static int launch_pairsum_f32_diff(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (int rc = tensor_map_encoder(&encode)) return rc;
+  const int sp = sspad_for(n);
+  PsDiffDesc d;
+  std::memset(static_cast<void *>(&d), 0, sizeof(d));
+  const cuuint64_t dims[2] = {(cuuint64_t)sp * 2, (cuuint64_t)p->nk * p->rowstride};
+  const cuuint64_t strides[1] = {(cuuint64_t)sp * 2 * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)packed::LANES * 4, (cuuint32_t)packed::BOX_ROWS};
+  const cuuint32_t estr[2] = {1, 1};
+  for (int m = 0; m < 2; ++m) {
+    const CUresult r = encode(m == 0 ? &d.amap : &d.bmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                              m == 0 ? p->y : p->ys, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(SRM3_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  }
+  d.Ek = (const float *)p->Ek;
+  d.Ewd = (const float *)p->Ewd;
+  d.ck = (const float *)p->ck;
+  d.C = (float2 *)C_out;
+  d.order = p->super_order_d;
+  d.nk = p->nk;
+  d.nw = p->nw;
+  d.SS = 2 * n;
+  d.SSpad = sp;
+  d.rowstride = p->rowstride;
+  d.G = sp / (2 * packed::LANES);
+  d.cb = (float)std::cos(p->beta);
+  d.sb = (float)std::sin(p->beta);
+  const size_t smem = pairsum_f32p_smem();
+  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32d, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32d, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 100));
+  int nsm = 0, per_sm = 0;
+  SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairsum_f32d, packed::NT,
+                                                          smem));
+  if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "difference pair sum does not fit on an SM");
+  const int nunits = p->nsuper_d * d.G;
+  const int grid = std::min(nunits, nsm * per_sm);
+  if (grid == 0) return SRM3_OK;
+  k_pairsum_f32d<<<grid, packed::NT, smem, st>>>(d, nunits, p->ps_err);
+  SRM3_CUDA(cudaGetLastError());
+  return SRM3_OK;
+}
+
 static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
   const int SS = 2 * n, sp = sspad_for(n);
   const long long threads = (long long)p->nk * p->nw * sp;
   k_pairsum_f64<<<cdiv(threads, 256), 256, 0, st>>>(
       p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
       (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
-      (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
+      (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out,
+      p->mixed ? 1 : 0);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -347,12 +424,15 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
     k_pairsum_f64<<<cdiv(threads, 256), 256, 0, p->stream>>>(
         p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
         (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
-        (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out);
+        (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out,
+      p->mixed ? 1 : 0);
   } else {
     PsDesc d;
     int rc = fill_pairsum_desc(p, n, C_out, &d);
     if (rc) return rc;
-    return launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0, d.half != 0);
+    rc = launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0, d.half != 0);
+    if (rc || !p->mixed) return rc;
+    return launch_pairsum_f32_diff(p, p->stream, n, C_out);
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
@@ -446,7 +526,7 @@ static int run_chunk(srm3_plan *p, const uint64_t *seeds, int m, void *C, void *
   if ((rc = stage_begin(p, 0, 0, &rec))) return rc;
   if ((rc = run_phases(p, seeds, m, nullptr))) return rc;
   if ((rc = stage_end(p, rec))) return rc;
-  if ((rc = stage_begin(p, 1, 2LL * m * p->pairs, &rec))) return rc;
+  if ((rc = stage_begin(p, 1, 2LL * m * (p->pairs + p->diffpairs), &rec))) return rc;
   if ((rc = run_pairsum(p, m, C))) return rc;
   if ((rc = stage_end(p, rec))) return rc;
   if (!out) return SRM3_OK;
@@ -554,7 +634,9 @@ static int batch_launch(srm3_batch *b) {
   }
   for (size_t i = 0; i < b->plans.size(); ++i) {
     srm3_plan *p = b->plans[i];
-    if (p->sep) {
+    if (p->mixed && p->precision == SRM3_FP32) {  // its difference pairs, after its sum pairs
+      if ((rc = launch_pairsum_f32_diff(p, b->stream, b->counts[i], p->C))) return rc;
+    } else if (p->sep) {
       if ((rc = conv_pairsum_on(p, b->stream, b->counts[i], p->y, p->y0, p->C))) return rc;
     } else if (p->precision == SRM3_FP64 &&
                (rc = pairsum_f64_on(p, b->stream, b->counts[i], p->C))) {
@@ -712,6 +794,9 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   if (plan->precision != SRM3_FP32 || plan->sep)
     return fail(SRM3_ERR_NOT_SUPPORTED,
                 "autotuning applies to FP32 plans of the O(N^2) pair sum only");
+  if (plan->mixed)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "mixed plans recompute W: there is no storage to choose");
   int rc = ensure_workspace(plan, n);
   if (rc) return rc;
   std::vector<uint64_t> seeds(n);
@@ -823,9 +908,10 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     b->outs.push_back(outs[i]);
     b->seed_off.push_back(b->total);
     b->total += counts[i];
-    b->pair_terms += 2LL * p->pairs * counts[i];
+    b->pair_terms += 2LL * (p->pairs + p->diffpairs) * counts[i];
     int gi = -1;
-    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE && !p->sep) {
+    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE && !p->sep &&
+        !p->mixed) {
       for (size_t g = 0; g < b->groups.size() && gi < 0; ++g)
         if (same_shape(b->plans[b->groups[g].members[0]], p)) gi = (int)g;
       if (gi < 0) {

@@ -99,6 +99,22 @@ struct srm3_plan {
   void *tw_conv = nullptr;
   void *Zc = nullptr;
   long long zc_ss = 0;
+  // mixed-sign interactions: opposite-sheet pairs as well; Eq. pure then
+  // a fixed point solved by iterations of (difference sums at the previous
+  // iterate, level pass)
+  bool mixed = false;
+  int64_t diffpairs = 0;          // difference pairs of one sheet
+  int fp_iters = 0;               // iterations of the last fixed-point solve
+  double *Dsum = nullptr;         // difference-pair sums per point [nk*nw]
+  double *qprev = nullptr;        // previous iterate of q
+  double *qlo = nullptr;          // converged q at qlo_x (warm start of the search)
+  double qlo_x = -1.0;
+  unsigned long long *fp_change = nullptr;  // max relative change of q (bits)
+  void *Ewd = nullptr;            // FP32 envelope of the difference d >= 0, [ewd_len]
+  int ewd_len = 0;
+  void *ys = nullptr;             // FP32: y with the two sheets of each lane swapped
+  int nsuper_d = 0;
+  int2 *super_order_d = nullptr;  // super-tiles by decreasing difference-pair cost
   double eps = 0.0, max_sb2 = 0.0, min_pure = 1.0, variance = 0.0;
   double plan_ms = 0.0, table_bytes = 0.0, table_budget = 0.0;
   int root_passes = 0;    // FP64 recursion passes
@@ -172,7 +188,7 @@ struct srm3_plan {
   int2 *rec_pairs = nullptr;         // bulk point pairs of every phase
   int *rec_pair_off = nullptr;       // first pair of each bulk phase
   unsigned int *rec_bar = nullptr;   // grid barrier counter and bulk-phase tickets
-  int rec_bar_words = 0;
+  int rec_bar_words = 0, rec_bar_tickets = 0;
   unsigned long long *rec_max = nullptr;  // per-plane max sum_b2 of a pass (bits)
   double sumS = 0.0;                      // sum of S over the lattice
   // separable envelope: the bulk of a pass as an online FFT self-convolution

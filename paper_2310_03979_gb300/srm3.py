@@ -27,6 +27,7 @@ SRM3_SPECTRUM_KAIMAL_LORENTZIAN = 0
 SRM3_SPECTRUM_TABLE = 1
 SRM3_BISPECTRUM_GAUSS_ENVELOPE = 0
 SRM3_BISPECTRUM_SEPARABLE = 1
+SRM3_INTERACTIONS_SUM, SRM3_INTERACTIONS_MIXED = 0, 1
 SRM3_FP32, SRM3_FP64 = 0, 1
 SRM3_STORAGE_AUTO, SRM3_STORAGE_TABLE, SRM3_STORAGE_RECOMPUTE, SRM3_STORAGE_TUNED = 0, 1, 2, 3
 EXPORTED = [
@@ -58,7 +59,7 @@ class srm3_spectrum(ctypes.Structure):
 
 
 class srm3_bispectrum(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("kind", ctypes.c_int32), ("interactions", ctypes.c_int32),
                 ("target_max_sum_b2", ctypes.c_double), ("eps", ctypes.c_double),
                 ("sigma_g", ctypes.c_double), ("beta", ctypes.c_double),
                 ("env_table", ctypes.POINTER(ctypes.c_double)),
@@ -79,7 +80,9 @@ class srm3_info(ctypes.Structure):
                 ("table_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("pairs", ctypes.c_int64), ("root_passes", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32)]
+                ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32),
+                ("interactions", ctypes.c_int32), ("fixed_point_iterations", ctypes.c_int32),
+                ("diff_pairs", ctypes.c_int64)]
 
 
 class srm3_timings(ctypes.Structure):
@@ -395,7 +398,7 @@ class Plan:
 
     @classmethod
     def create(cls, wl, *, precision=None, storage=None, stream=None, table=None,
-               eps=None, target=None, budget_bytes=0.0):
+               eps=None, target=None, budget_bytes=0.0, mixed=None):
         prec = precision or wl.precision
         sp = srm3_spectrum()
         keep = None
@@ -425,6 +428,8 @@ class Plan:
         else:
             bs.target_max_sum_b2 = float(tgt)
         bs.sigma_g, bs.beta = wl.sigma_g, wl.beta
+        mx = getattr(wl, "interactions", "sum") == "mixed" if mixed is None else bool(mixed)
+        bs.interactions = SRM3_INTERACTIONS_MIXED if mx else SRM3_INTERACTIONS_SUM
         g = srm3_grid()
         g.n_kappa, g.n_omega = wl.n_kappa, wl.n_omega
         g.kappa_u, g.omega_u = wl.kappa_u, wl.omega_u

@@ -47,6 +47,9 @@ class Workload:
     sigma_e: float = 0.5
     # fixed bispectrum scale (> 0: used as given, no search on target)
     eps: float = 0.0
+    # "sum" (pairs within a sheet) or "mixed" (also the opposite-sign
+    # frequency pairs of the general form)
+    interactions: str = "sum"
 
     def envelope_table(self) -> np.ndarray:
         """Separable envelope e(kk, kw) = exp(-1/2 ((kk/(sigma_e Nk))^2 +
@@ -84,9 +87,18 @@ class Workload:
         cnt[0, 0] = 0
         return int(cnt.sum())
 
+    def diff_pairs(self) -> int:
+        """Difference (opposite-sign) pairs of one sheet: sum over kw >= 1 of
+        (kk + 1)(Nw - 1 - kw); 0 unless interactions == "mixed"."""
+        if self.interactions != "mixed":
+            return 0
+        kk = np.arange(self.n_kappa, dtype=np.int64)[:, None]
+        kw = np.arange(1, self.n_omega, dtype=np.int64)[None, :]
+        return int(((kk + 1) * (self.n_omega - 1 - kw)).sum())
+
     def pair_terms_per_sample(self) -> int:
         """One pair-term = one W_ij y_i y_j product for one sheet of one sample."""
-        return 2 * self.pairs()
+        return 2 * (self.pairs() + self.diff_pairs())
 
 
 # Tiny plain-method case: 32 x 32 lattice, FP64, one sample, 64 x 64 field.
