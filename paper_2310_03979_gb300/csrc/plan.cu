@@ -219,46 +219,109 @@ struct PassResult {
 static thread_local cudaEvent_t t_ev[2] = {nullptr, nullptr};
 
 static constexpr int kPlanes = 8;  // eps values per FP32 search pass
+// pinned host scalars of a plan build (8 + 4 kPlanes doubles): [0, kPlanes)
+// eps^2 dk dw per plane going in, [8, 8 + kPlanes) the planes' max sum_b2
+// coming back ([9] the linear pass's max), kSumSlot the sum of S
+static constexpr int kSumSlot = 8 + 4 * kPlanes - 1;
+
+// Index lists of the recursion pass, written on the device from small
+// offset tables: the lattice points in level order (level d holds kk = lo
+// .. hi, lo = max(0, d - nw + 1), hi = min(d, nk - 1)), and for bulk phase
+// ph the points of its band of levels [D, min(2D, nlev)), D = ph BL, as
+// pairs (kk, kw), (kk, kw + 2 ...) along each lattice row: row kk of phase
+// ph holds kw = lo(kk), lo(kk) + 2, ... <= hi(kk), from entry seg[ph nk + kk].
+__global__ void k_level_points(int nk, int nw, int nlev, const int *__restrict__ lev_off,
+                               int2 *__restrict__ pts) {
+  const int d = blockIdx.x;
+  if (d >= nlev) return;
+  const int lo = max(0, d - nw + 1), hi = min(d, nk - 1);
+  for (int kk = lo + threadIdx.x; kk <= hi; kk += blockDim.x)
+    pts[lev_off[d] + kk - lo] = make_int2(kk, d - kk);
+}
+
+__global__ void k_bulk_pairs(int nk, int nw, int nlev, const int *__restrict__ seg,
+                             int2 *__restrict__ pairs) {
+  const int ph = 1 + blockIdx.y, kk = blockIdx.x;
+  const int D = ph * kRecBL, dend = min(2 * D, nlev);
+  const int lo = max(0, D - kk), hi = min(nw - 1, dend - 1 - kk);
+  const int base = seg[(ph - 1) * nk + kk];
+  for (int j = threadIdx.x; lo + 2 * j <= hi; j += blockDim.x)
+    pairs[base + j] = make_int2(kk, lo + 2 * j);
+}
+
+// Resident-block counts of the recursion kernels per device (they depend on
+// the kernel and its shared memory only).
+struct RecOccupancy {
+  int nsm = 0, b64 = 0, b64x3 = 0, b32 = 0, b64f = 0, b32f = 0;
+};
+
+static int rec_occupancy(int dev, RecOccupancy *out) {
+  static std::mutex mu;
+  static RecOccupancy cache[64];
+  static bool have[64] = {};
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev < 0 || dev >= 64) return fail(SRM3_ERR_NOT_SUPPORTED, "device ordinal beyond 64");
+  if (!have[dev]) {
+    RecOccupancy o;
+    SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+    SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+    SRM3_CUDA(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64, k_rec_pass<double, 1>,
+                                                            kRecThreads, 0));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64f, k_rec_pass<double, 1>,
+                                                            kRecThreads, kRecSmem));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64x3, k_rec_pass<double, 3>,
+                                                            kRecThreads, 0));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b32, k_rec_pass<float, kPlanes>,
+                                                            kRecThreads, 0));
+    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b32f, k_rec_pass<float, kPlanes>,
+                                                            kRecThreads, kRecSmem));
+    cache[dev] = o;
+    have[dev] = true;
+  }
+  *out = cache[dev];
+  return SRM3_OK;
+}
 
 // Device state of the persistent recursion pass.
 static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   const int nk = p->nk, nw = p->nw;
   const int nlev = nk + nw - 1;
-  // lattice points in level order, and the first point of each level
-  std::vector<int2> pts;
+  // first point of each level, and the first bulk pair of each (phase, row)
   std::vector<int> lev_off(nlev + 1, 0);
-  pts.reserve((size_t)nk * nw);
-  for (int d = 0; d < nlev; ++d) {
-    const int lo = std::max(0, d - nw + 1), hi = std::min(d, nk - 1);
-    lev_off[d] = (int)pts.size();
-    for (int kk = lo; kk <= hi; ++kk) pts.push_back(make_int2(kk, d - kk));
-  }
-  lev_off[nlev] = (int)pts.size();
-  SRM3_CUDA(dev_alloc(&p->rec_items, sizeof(int2) * pts.size(), st));
-  SRM3_CUDA(cudaMemcpyAsync(p->rec_items, pts.data(), sizeof(int2) * pts.size(),
-                            cudaMemcpyHostToDevice, st));
-  SRM3_CUDA(dev_alloc(&p->rec_lev_off, sizeof(int) * (nlev + 1), st));
-  SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
-                            cudaMemcpyHostToDevice, st));
-  // bulk phase D = ph BL: the points of levels [D, min(2D, nlev)) as pairs
-  // (kk, kw), (kk, kw + 1) along each lattice row
-  std::vector<int2> pairs;
-  std::vector<int> pair_off(1, 0);
-  for (int D = kRecBL; D < nlev; D += kRecBL) {
-    const int dend = std::min(2 * D, nlev);
+  for (int d = 0; d < nlev; ++d)
+    lev_off[d + 1] = lev_off[d] + std::min(d, nk - 1) - std::max(0, d - nw + 1) + 1;
+  const int nph = std::max(0, (nlev - 1) / kRecBL);  // phases D = BL, 2 BL, ... < nlev
+  std::vector<int> seg((size_t)nph * nk + 1, 0);
+  std::vector<int> pair_off(nph + 1, 0);
+  for (int ph = 1; ph <= nph; ++ph) {
+    const int D = ph * kRecBL, dend = std::min(2 * D, nlev);
     for (int kk = 0; kk < nk; ++kk) {
       const int lo = std::max(0, D - kk), hi = std::min(nw - 1, dend - 1 - kk);
-      for (int kw = lo; kw <= hi; kw += 2) pairs.push_back(make_int2(kk, kw));
+      const size_t i = (size_t)(ph - 1) * nk + kk;
+      seg[i + 1] = seg[i] + (hi >= lo ? (hi - lo) / 2 + 1 : 0);
     }
-    pair_off.push_back((int)pairs.size());
+    pair_off[ph] = seg[(size_t)ph * nk];
   }
-  if (pairs.empty()) pairs.push_back(make_int2(0, 0));
-  SRM3_CUDA(dev_alloc(&p->rec_pairs, sizeof(int2) * pairs.size(), st));
-  SRM3_CUDA(cudaMemcpyAsync(p->rec_pairs, pairs.data(), sizeof(int2) * pairs.size(),
-                            cudaMemcpyHostToDevice, st));
+  const int npairs = std::max(1, seg[(size_t)nph * nk]);
+  int *d_seg = nullptr;
+  SRM3_CUDA(dev_alloc(&p->rec_items, sizeof(int2) * lev_off[nlev], st));
+  SRM3_CUDA(dev_alloc(&p->rec_lev_off, sizeof(int) * (nlev + 1), st));
+  SRM3_CUDA(dev_alloc(&p->rec_pairs, sizeof(int2) * npairs, st));
   SRM3_CUDA(dev_alloc(&p->rec_pair_off, sizeof(int) * pair_off.size(), st));
+  SRM3_CUDA(dev_alloc(&d_seg, sizeof(int) * seg.size(), st));
+  SRM3_CUDA(cudaMemcpyAsync(p->rec_lev_off, lev_off.data(), sizeof(int) * (nlev + 1),
+                            cudaMemcpyHostToDevice, st));
   SRM3_CUDA(cudaMemcpyAsync(p->rec_pair_off, pair_off.data(), sizeof(int) * pair_off.size(),
                             cudaMemcpyHostToDevice, st));
+  SRM3_CUDA(cudaMemcpyAsync(d_seg, seg.data(), sizeof(int) * seg.size(), cudaMemcpyHostToDevice,
+                            st));
+  k_level_points<<<nlev, 128, 0, st>>>(nk, nw, nlev, p->rec_lev_off, p->rec_items);
+  if (nph > 0) k_bulk_pairs<<<dim3(nk, nph), 128, 0, st>>>(nk, nw, nlev, d_seg, p->rec_pairs);
+  SRM3_CUDA(cudaGetLastError());
+  SRM3_CUDA(dev_free(d_seg, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(dev_alloc(&p->rec_partial, (size_t)nk * nw * 32, st));
   SRM3_CUDA(dev_alloc(&p->rec_max, kPlanes * sizeof(unsigned long long), st));
@@ -287,43 +350,31 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
       SRM3_CUDA(cudaGetLastError());
     }
   }
-  const int rec_smem = p->rec_fft ? kRecSmem : 0;
-  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
-  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
-  // sum of S (the exact variance), once: the plane-0 results of this
-  // reduction are not used
+  // sum of S (the exact variance), once, read after the next synchronisation
+  // of the stream (run_pass_multi); the plane-0 results of this reduction
+  // are not used
   SRM3_CUDA(cudaMemsetAsync(p->sb2, 0, (size_t)nk * nw * sizeof(double), st));
   k_reduce_planes<<<1, 1024, 0, st>>>((long long)nk * nw, p->S, p->sb2, p->scal);
   SRM3_CUDA(cudaGetLastError());
-  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 11, p->scal + 11, sizeof(double),
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + kSumSlot, p->scal + 11, sizeof(double),
                             cudaMemcpyDeviceToHost, st));
-  SRM3_CUDA(cudaStreamSynchronize(st));
-  p->sumS = p->h_pinned[11];
+  p->sumS = -1.0;  // not read yet
   // barrier counter, a ticket per bulk phase, and a readiness counter per
   // level (the fringe)
   p->rec_bar_tickets = 2 + (nk + nw) / kRecBL + 1;
   p->rec_bar_words = p->rec_bar_tickets + nlev;
   SRM3_CUDA(dev_alloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
-  int nsm = 0, dev = 0;
-  SRM3_CUDA(cudaGetDevice(&dev));
-  SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  int b64 = 0, b64x3 = 0, b32 = 0;
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1>,
-                                                          kRecThreads, rec_smem));
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64x3, k_rec_pass<double, 3>,
-                                                          kRecThreads, 0));
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes>,
-                                                          kRecThreads, rec_smem));
-  if (b64 < 1 || b64x3 < 1 || b32 < 1)
+  RecOccupancy occ;
+  int rc = rec_occupancy(p->device, &occ);
+  if (rc) return rc;
+  const bool f = p->rec_fft;
+  if ((f ? occ.b64f : occ.b64) < 1 || occ.b64x3 < 1 || (f ? occ.b32f : occ.b32) < 1)
     return fail(SRM3_ERR_CUDA, "recursion kernel cannot be resident");
+  const int nsm = occ.nsm;
   SRM3_CUDA(dev_alloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double), st));
-  SRM3_CUDA(cudaMemsetAsync(p->qm3, 0, 3 * (size_t)nk * nw * sizeof(double), st));
   p->rec_grid64 = nsm;
   p->rec_grid32 = nsm;
-  SRM3_CUDA(cudaStreamSynchronize(st));
   return SRM3_OK;
 }
 
@@ -387,6 +438,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   SRM3_CUDA(cudaMemcpyAsync(p->h_err, p->err, (kPlanes + 1) * sizeof(int), cudaMemcpyDeviceToHost,
                             st));
   SRM3_CUDA(cudaStreamSynchronize(st));
+  if (p->sumS < 0.0) p->sumS = p->h_pinned[kSumSlot];  // copied by setup_recursion
   float ms = 0.f;
   SRM3_CUDA(cudaEventElapsedTime(&ms, t_ev[0], t_ev[1]));
   p->t_recursion_ms += ms;
