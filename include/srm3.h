@@ -143,6 +143,19 @@ typedef struct srm3_grid {
     int32_t storage;          /* enum srm3_storage */
     void *stream;             /* cudaStream_t for all plan work; NULL = default */
     double table_budget_bytes;/* AUTO: largest W table allowed (0 = 64 GiB) */
+    /* Lattice rows [row_begin, row_end) whose coefficients the plan computes
+     * (0, 0 = all rows): one shard of a job that splits the W table and the
+     * pair sum by rows of kappa across devices -- the distributed storage of
+     * the bispectrum the paper proposes for domains past one node's memory
+     * (Sec. 4.3).  The recursion still covers the whole lattice (every row's
+     * S_p is needed); the W table, the work units and srm3_info.pairs cover
+     * the plan's rows only.  Such a plan gives coefficients (srm3_coeffs
+     * writes its rows of C and leaves the others untouched), not fields:
+     * srm3_sample and srm3_sample_host refuse it with NOT_SUPPORTED, and so
+     * does srm3_batch_create; gather every shard's rows, then call
+     * srm3_field_from_coeffs.  Not for SEPARABLE plans (their pair sum is an
+     * FFT over the whole lattice). */
+    int32_t row_begin, row_end;
 } srm3_grid;
 
 typedef struct srm3_plan srm3_plan;
@@ -193,7 +206,7 @@ typedef struct srm3_info {
     double variance;         /* exact ensemble variance sum_s sum_k 2 S dk dw */
     double table_bytes;      /* bytes of the W table (0 when recomputed) */
     double plan_ms;          /* wall time of srm3_plan_create */
-    int64_t pairs;           /* sum_k |Pi(k)| */
+    int64_t pairs;           /* sum_k |Pi(k)| over the plan's rows */
     int32_t root_passes;     /* FP64 recursion passes of the build */
     int32_t storage;         /* storage actually chosen */
     int32_t precision;

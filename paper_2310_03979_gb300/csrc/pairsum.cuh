@@ -24,12 +24,13 @@ __global__ void __launch_bounds__(256) k_pairsum_f64(
     const double2 *__restrict__ y0, const double *__restrict__ Ek,
     const double *__restrict__ Ews, int ew_off, const double *__restrict__ Pk,
     const double *__restrict__ ck, double cb, double sb, double2 *__restrict__ C,
-    int mixed) {
+    int mixed, int row_lo, int row_hi) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int ss = (int)(gid % SSpad);
   const long long k = gid / SSpad;
   if (k >= (long long)nk * nw || ss >= SS) return;
   const int kk = (int)(k / nw), kw = (int)(k - (long long)kk * nw);
+  if (kk < row_lo || kk >= row_hi) return;  // rows of another shard
   const double2 *yl = y + ss;
   double ar = 0.0, ai = 0.0;
   for (int a = 0; a <= kk / 2; ++a) {

@@ -176,13 +176,13 @@ __global__ void k_twiddles(int n, int log2n, T2 *tw) {
 // else 0.  Centre rows are stored in full (the kernel halves them).  W is
 // real: the constant biphase is applied afterwards.  One CTA per tile, its
 // threads writing the tile's float4 in storage order.
-__global__ void __launch_bounds__(256) k_build_w(int nk, int nw, int ntw,
+__global__ void __launch_bounds__(256) k_build_w(int t0, int nk, int nw, int ntw,
                                                  const long long *__restrict__ off,
                                                  const float *__restrict__ ck,
                                                  const float *__restrict__ Ek,
                                                  const float *__restrict__ Ews, int ew_off,
                                                  float *__restrict__ W) {
-  const int t = blockIdx.x;
+  const int t = t0 + blockIdx.x;  // tiles of the plan's rows
   const int kk = t / ntw, tw = t - kk * ntw;
   const int kw0 = tw * kTileR;
   const int nrow = kk / 2 + 1;
@@ -874,7 +874,8 @@ int build_w_table(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaEventCreate(&ev[0]));
   SRM3_CUDA(cudaEventCreate(&ev[1]));
   cudaEventRecord(ev[0], st);
-  k_build_w<<<p->ntiles, dim3(32, 8), 0, st>>>(p->nk, p->nw, p->ntw, p->tile_off,
+  k_build_w<<<(p->row_hi - p->row_lo) * p->ntw, dim3(32, 8), 0, st>>>(
+      p->row_lo * p->ntw, p->nk, p->nw, p->ntw, p->tile_off,
                                                (const float *)p->ck, (const float *)p->Ek,
                                                (const float *)p->Ews, p->ew_off, p->W);
   e = cudaGetLastError();
@@ -890,34 +891,25 @@ int build_w_table(srm3_plan *p, cudaStream_t st) {
   return SRM3_OK;
 }
 
+// Tiles of the FP32 pair sum.  A plan restricted to lattice rows [row_lo,
+// row_hi) (a shard of a k-sharded job) gets W-table space and work units for
+// those rows only.
 static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long *table_entries) {
   const int nk = p->nk;
   p->ntw = cdiv(p->nw, kTileR);
   p->ntiles = nk * p->ntw;
   std::vector<long long> off(p->ntiles + 1, 0);
-  std::vector<int> ids(p->ntiles);
-  std::vector<long long> cost(p->ntiles);
   for (int t = 0; t < p->ntiles; ++t) {
-    int kk = t / p->ntw, tw = t % p->ntw;
-    cost[t] = tile_entries(kk, tw);
-    off[t + 1] = off[t] + cost[t];
-    ids[t] = t;
+    const int kk = t / p->ntw, tw = t % p->ntw;
+    const bool mine = kk >= p->row_lo && kk < p->row_hi;
+    off[t + 1] = off[t] + (mine ? tile_entries(kk, tw) : 0);
   }
-  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-  std::vector<int2> order(p->ntiles);
-  for (int i = 0; i < p->ntiles; ++i) {
-    int t = ids[i];
-    order[i] = make_int2(t / p->ntw, (t % p->ntw) * kTileR);
-  }
-  SRM3_CUDA(dev_alloc(&p->tile_order, sizeof(int2) * p->ntiles, st));
-  SRM3_CUDA(cudaMemcpyAsync(p->tile_order, order.data(), sizeof(int2) * p->ntiles,
-                            cudaMemcpyHostToDevice, st));
   // super-tiles of kWarpsPerCta tiles (FP32 pair sum), most expensive first
   const int sw = kTileR * kWarpsPerCta;
   const int nsw = cdiv(p->nw, sw);
-  p->nsuper = nk * nsw;
+  p->nsuper = (p->row_hi - p->row_lo) * nsw;
   std::vector<int2> sup(p->nsuper);
-  for (int i = 0; i < p->nsuper; ++i) sup[i] = make_int2(i / nsw, (i % nsw) * sw);
+  for (int i = 0; i < p->nsuper; ++i) sup[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
   std::stable_sort(sup.begin(), sup.end(), [&](int2 a, int2 b) {
     return (long long)(a.x / 2 + 1) * (a.y + sw) > (long long)(b.x / 2 + 1) * (b.y + sw);
   });
@@ -927,7 +919,7 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
   p->super_host = sup;
   if (p->mixed) {  // the difference pass: (kk + 1) row pairs x ceil((nw - kws0) / 16) chunks
     std::vector<int2> supd(p->nsuper);
-    for (int i = 0; i < p->nsuper; ++i) supd[i] = make_int2(i / nsw, (i % nsw) * sw);
+    for (int i = 0; i < p->nsuper; ++i) supd[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
     auto cost = [&](int2 t) { return (long long)(t.x + 1) * ((p->nw - t.y + 15) / 16); };
     std::stable_sort(supd.begin(), supd.end(),
                      [&](int2 a, int2 b) { return cost(a) > cost(b); });
@@ -1068,8 +1060,8 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   }
 
   // pair count
-  long long pairs = 0;
-  for (int kk = 0; kk < nk; ++kk)
+  long long pairs = 0;  // of the plan's rows
+  for (int kk = p->row_lo; kk < p->row_hi; ++kk)
     for (int kw = 0; kw < nw; ++kw) {
       if (kk == 0 && kw == 0) continue;
       long long m = (long long)(kk + 1) * (kw + 1) - 2;
@@ -1078,7 +1070,7 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   p->pairs = pairs;
   long long dpairs = 0;  // difference pairs of one sheet
   if (p->mixed)
-    for (int kk = 0; kk < nk; ++kk)
+    for (int kk = p->row_lo; kk < p->row_hi; ++kk)
       for (int kw = 1; kw < nw; ++kw) dpairs += (long long)(kk + 1) * (nw - 1 - kw);
   p->diffpairs = dpairs;
 
@@ -1218,7 +1210,7 @@ void free_plan(srm3_plan *p) {
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   void *dev[] = {p->S,      p->qm,     p->sb2,       p->EkSq,       p->EwSq,   p->scal,
                  p->err,    p->sqq,    p->Pk,        p->ck,         p->Ek,     p->Ews,
-                 p->tw,     p->tile_order, p->tile_off, p->W,       p->y,      p->y0,
+                 p->tw,     p->tile_off, p->W,       p->y,      p->y0,
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
                  p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
@@ -1300,6 +1292,12 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
       return fail(SRM3_ERR_NOT_SUPPORTED,
                   "mixed interactions recompute W (the W table holds sum pairs only)");
   }
+  const bool all_rows = g.row_begin == 0 && g.row_end == 0;
+  if (!all_rows && !(g.row_begin >= 0 && g.row_begin < g.row_end && g.row_end <= g.n_kappa))
+    return fail(SRM3_ERR_INVALID_ARG, "rows must satisfy 0 <= row_begin < row_end <= n_kappa");
+  if (!all_rows && bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "separable plans sample by an FFT over the whole lattice: no row range");
   const double tgt = bispectrum->target_max_sum_b2;
   if (!(tgt >= 0.0 && tgt < 1.0)) return fail(SRM3_ERR_INVALID_ARG, "target must be in [0, 1)");
   if (tgt == 0.0 && !(bispectrum->eps >= 0.0))
@@ -1323,6 +1321,8 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->stream = (cudaStream_t)g.stream;
   p->sep = bispectrum->kind == SRM3_BISPECTRUM_SEPARABLE;
   p->mixed = bispectrum->interactions == SRM3_INTERACTIONS_MIXED;
+  p->row_lo = all_rows ? 0 : g.row_begin;
+  p->row_hi = all_rows ? g.n_kappa : g.row_end;
   p->sigma_g = p->sep ? 0.25 : bispectrum->sigma_g;
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);

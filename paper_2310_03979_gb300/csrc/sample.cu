@@ -367,7 +367,7 @@ static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
       p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
       (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
       (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out,
-      p->mixed ? 1 : 0);
+      p->mixed ? 1 : 0, p->row_lo, p->row_hi);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -425,7 +425,7 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
         p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
         (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
         (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out,
-      p->mixed ? 1 : 0);
+      p->mixed ? 1 : 0, p->row_lo, p->row_hi);
   } else {
     PsDesc d;
     int rc = fill_pairsum_desc(p, n, C_out, &d);
@@ -680,9 +680,22 @@ static void batch_free(srm3_batch *b) {
   delete b;
 }
 
+// A plan restricted to a range of lattice rows computes only those rows'
+// coefficients: fields need the gathered coefficients of every shard
+// (srm3_field_from_coeffs).
+static int check_all_rows(const srm3_plan *p) {
+  if (p->row_lo != 0 || p->row_hi != p->nk)
+    return fail(SRM3_ERR_NOT_SUPPORTED,
+                "the plan computes the coefficients of rows " + std::to_string(p->row_lo) + ".." +
+                    std::to_string(p->row_hi - 1) + " only: gather every shard's rows and "
+                    "call srm3_field_from_coeffs");
+  return SRM3_OK;
+}
+
 SRM3_API int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *out) {
   int rc = check_call(plan, seeds, n, out);
   if (rc || n == 0) return rc;
+  if ((rc = check_all_rows(plan))) return rc;
   const int chunk = std::min(n, kMaxChunk);
   rc = ensure_workspace(plan, chunk);
   if (rc) return rc;
@@ -697,6 +710,7 @@ SRM3_API int srm3_sample(srm3_plan *plan, const uint64_t *seeds, int n, void *ou
 SRM3_API int srm3_sample_host(srm3_plan *plan, const uint64_t *seeds, int n, void *out_host) {
   int rc = check_call(plan, seeds, n, out_host);
   if (rc || n == 0) return rc;
+  if ((rc = check_all_rows(plan))) return rc;
   const int chunk = std::min(n, kMaxChunk);
   rc = ensure_workspace(plan, chunk);
   if (rc) return rc;
@@ -871,6 +885,8 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     if (dev < 0) dev = plans[i]->device;
     if (plans[i]->device != dev)
       return fail(SRM3_ERR_NOT_SUPPORTED, "the plans of a batch must be on one device");
+    if (plans[i]->row_lo != 0 || plans[i]->row_hi != plans[i]->nk)
+      return fail(SRM3_ERR_NOT_SUPPORTED, "a batch takes plans of the whole lattice only");
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i])
         return fail(SRM3_ERR_INVALID_ARG,

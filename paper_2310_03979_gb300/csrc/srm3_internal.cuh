@@ -75,6 +75,7 @@ struct srm3_plan {
   int nk = 0, nw = 0, nx = 0, nt = 0;
   int log2nx = 0, log2nt = 0;
   double ku = 0, wu = 0, dk = 0, dw = 0, dkdw = 0;
+  int row_lo = 0, row_hi = 0;  // lattice rows whose coefficients the plan computes
   int precision = SRM3_FP32;
   int storage = SRM3_STORAGE_RECOMPUTE;
   cudaStream_t stream = nullptr;
@@ -154,7 +155,6 @@ struct srm3_plan {
   long long table_entries = 0;    // floats of the W table (built or not)
   int ps_ctas = 0;                // resident CTAs of the persistent FP32 pair sum
   int *ps_err = nullptr;          // its error word (bounded waits that ran out)
-  int2 *tile_order = nullptr;
   int nsuper = 0;
   int2 *super_order = nullptr;    // 32-wide super-tiles of the FP32 pair sum
   std::vector<int2> super_host;   // the same order on the host (batch unit lists)

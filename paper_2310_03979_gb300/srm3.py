@@ -71,7 +71,8 @@ class srm3_grid(ctypes.Structure):
                 ("kappa_u", ctypes.c_double), ("omega_u", ctypes.c_double),
                 ("n_x", ctypes.c_int32), ("n_t", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("storage", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("table_budget_bytes", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("table_budget_bytes", ctypes.c_double),
+                ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
 
 
 class srm3_info(ctypes.Structure):
@@ -398,7 +399,7 @@ class Plan:
 
     @classmethod
     def create(cls, wl, *, precision=None, storage=None, stream=None, table=None,
-               eps=None, target=None, budget_bytes=0.0, mixed=None):
+               eps=None, target=None, budget_bytes=0.0, mixed=None, rows=None):
         prec = precision or wl.precision
         sp = srm3_spectrum()
         keep = None
@@ -438,6 +439,8 @@ class Plan:
         g.storage = _STOR[storage or wl.storage]
         g.stream = stream
         g.table_budget_bytes = float(budget_bytes)
+        if rows is not None:  # one shard: lattice rows [rows[0], rows[1])
+            g.row_begin, g.row_end = int(rows[0]), int(rows[1])
         h = plan_create(sp, bs, g)
         del keep, env, env_b
         return cls(h, wl.n_kappa, wl.n_omega, wl.n_x, wl.n_t, prec)
