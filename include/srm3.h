@@ -217,6 +217,11 @@ typedef struct srm3_info {
     int64_t diff_pairs;      /* MIXED: difference pairs of one sheet, sum over k
                                 of (kk + 1)(n_omega - 1 - kw), kw >= 1; else 0.
                                 Pair-terms per sample: 2 (pairs + diff_pairs) */
+    double device_bytes;     /* device memory the plan holds now: lattice and
+                                sampling tables, recursion state, W table and
+                                the sampling workspace (which grows with the
+                                largest n sampled, up to 128 per chunk);
+                                batch buffers are the batch's */
 } srm3_info;
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
@@ -406,6 +411,17 @@ int srm3_batch_sync(srm3_batch *b);
 
 /* Pair-terms of one run: sum over plans of 2 |Pi| counts[i]. */
 int64_t srm3_batch_pair_terms(const srm3_batch *b);
+
+/* Device memory the batch allocated for itself (released by
+ * srm3_batch_destroy): per shape group with T samples in all, at most m of
+ * them from one plan, on an n_kappa x n_omega lattice with n_t-point rows,
+ * y + y0 = (n_kappa (n_omega + 128) + 1) P 8 bytes (P = 2 T sheet-samples
+ * rounded up to a multiple of 64), C = 2 T n_kappa n_omega 8, H = m n_kappa
+ * n_t 8 and 16 T of factor pointers; plus 8 bytes of seed per sample, the
+ * plan descriptors and 16 bytes per work unit.  Plans outside shape groups
+ * sample on their own workspace, which their srm3_info.device_bytes counts;
+ * the caller's output buffers are not included. */
+int64_t srm3_batch_device_bytes(const srm3_batch *b);
 
 /* Cap the batch's FP32 pair-sum launch at max_ctas CTAs (0: as many as are
  * resident, the default).  The launch is persistent and otherwise fills

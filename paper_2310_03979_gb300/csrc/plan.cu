@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <numeric>
+#include <unordered_map>
 
 #include "recursion.cuh"
 #include "srm3_internal.cuh"
@@ -867,6 +868,7 @@ static long long tile_entries(int kk, int tw) {
 // records its build time and size.
 int build_w_table(srm3_plan *p, cudaStream_t st) {
   if (p->W) return SRM3_OK;
+  AllocOwner owner(p);
   const double bytes = (double)p->table_entries * sizeof(float);
   cudaError_t e = dev_alloc(&p->W, (size_t)p->table_entries * sizeof(float), st);
   if (e != cudaSuccess) return cuda_fail(e, "dev_alloc(W table, st)");
@@ -1184,6 +1186,15 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
 // with its W table is about 9.5 GB); beyond this it goes back to the device.
 constexpr uint64_t kPoolKeepBytes = 32ull << 30;
 
+namespace {
+std::mutex g_alloc_mu;
+std::unordered_map<void *, std::pair<srm3_plan *, size_t>> g_allocs;  // block -> owner, size
+thread_local srm3_plan *g_alloc_owner = nullptr;
+}  // namespace
+
+AllocOwner::AllocOwner(srm3_plan *p) : prev(g_alloc_owner) { g_alloc_owner = p; }
+AllocOwner::~AllocOwner() { g_alloc_owner = prev; }
+
 cudaError_t dev_alloc(void **ptr, size_t bytes, cudaStream_t st) {
   static std::once_flag once[64];
   int dev = 0;
@@ -1197,10 +1208,26 @@ cudaError_t dev_alloc(void **ptr, size_t bytes, cudaStream_t st) {
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
       }
     });
-  return cudaMallocAsync(ptr, bytes, st);
+  e = cudaMallocAsync(ptr, bytes, st);
+  if (e == cudaSuccess && g_alloc_owner) {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_allocs[*ptr] = {g_alloc_owner, bytes};
+    g_alloc_owner->dev_bytes += (double)bytes;
+  }
+  return e;
 }
 
-cudaError_t dev_free(void *ptr, cudaStream_t st) { return cudaFreeAsync(ptr, st); }
+cudaError_t dev_free(void *ptr, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    auto it = g_allocs.find(ptr);
+    if (it != g_allocs.end()) {
+      it->second.first->dev_bytes -= (double)it->second.second;
+      g_allocs.erase(it);
+    }
+  }
+  return cudaFreeAsync(ptr, st);
+}
 
 void free_plan(srm3_plan *p) {
   for (auto &r : p->ev_recs) {
@@ -1327,7 +1354,11 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
   cudaGetDevice(&p->device);
-  int rc = build_plan(p, spectrum, bispectrum);
+  int rc;
+  {
+    AllocOwner owner(p);
+    rc = build_plan(p, spectrum, bispectrum);
+  }
   if (rc) {
     free_plan(p);
     delete p;
@@ -1373,6 +1404,7 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
   info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
   info->diff_pairs = plan->diffpairs;
+  info->device_bytes = plan->dev_bytes;
   return SRM3_OK;
 }
 

@@ -127,6 +127,7 @@ int sspad_for(int chunk) { return ((2 * chunk + 63) / 64) * 64; }
 
 int ensure_workspace(srm3_plan *p, int chunk) {
   if (p->ws_chunk >= chunk) return SRM3_OK;
+  AllocOwner owner(p);
   if (p->batch_refs > 0)
     return fail(SRM3_ERR_NOT_SUPPORTED,
                 "the plan's workspace belongs to a batch and cannot grow while the batch exists");
@@ -600,6 +601,7 @@ struct srm3_batch {
   bool capturing = false;         // inside srm3_batch_capture
   int max_ctas = 0;               // cap on the pair sum's CTAs (0: all resident)
   cudaEvent_t ps_ev[2] = {nullptr, nullptr};
+  long long dev_bytes = 0;        // device memory the batch allocated itself
 };
 
 using namespace srm3;
@@ -955,6 +957,8 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     const size_t cb = (size_t)2 * g.total * p->nk * p->nw * sizeof(float2);
     const size_t hb = (size_t)g.nmax * p->nk * p->nt * sizeof(float2);
     cudaStream_t st = b->stream;
+    b->dev_bytes += (long long)(g.ybytes + (size_t)g.sp * sizeof(float2) + cb + hb +
+                                2 * sizeof(float *) * g.total);
     if ((e = cudaMallocAsync(&g.y, g.ybytes, st)) != cudaSuccess ||
         (e = cudaMallocAsync(&g.y0, (size_t)g.sp * sizeof(float2), st)) != cudaSuccess ||
         (e = cudaMallocAsync(&g.C, cb, st)) != cudaSuccess ||
@@ -1001,6 +1005,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
                    });
   b->nunits = (int)units.size();
   if (!descs.empty()) {
+    b->dev_bytes += (long long)(sizeof(PsDesc) * descs.size() + sizeof(int4) * units.size());
     e = cudaMallocAsync(&b->ddesc, sizeof(PsDesc) * descs.size(), b->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch descriptors)"));
     e = cudaMemcpyAsync(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(),
@@ -1020,6 +1025,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0, b->mixed)))
       return bail(rc);
   }
+  b->dev_bytes += (long long)(sizeof(uint64_t) * b->total);
   e = cudaMallocAsync(&b->dseeds, sizeof(uint64_t) * b->total, b->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch seeds)"));
@@ -1078,6 +1084,8 @@ SRM3_API int srm3_batch_sync(srm3_batch *b) {
 }
 
 SRM3_API int64_t srm3_batch_pair_terms(const srm3_batch *b) { return b ? b->pair_terms : 0; }
+
+SRM3_API int64_t srm3_batch_device_bytes(const srm3_batch *b) { return b ? b->dev_bytes : 0; }
 
 SRM3_API int srm3_batch_set_max_ctas(srm3_batch *b, int max_ctas) {
   if (!b || max_ctas < 0) return fail(SRM3_ERR_INVALID_ARG, "batch is NULL or max_ctas < 0");

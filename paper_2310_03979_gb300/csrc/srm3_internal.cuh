@@ -59,6 +59,14 @@ cudaError_t dev_alloc(T **ptr, size_t bytes, cudaStream_t st) {
   return dev_alloc(reinterpret_cast<void **>(ptr), bytes, st);
 }
 cudaError_t dev_free(void *ptr, cudaStream_t st);
+// Device memory held by a plan: blocks from dev_alloc made while an
+// AllocOwner of the plan is in scope (on this thread) are charged to its
+// dev_bytes, and dev_free of such a block gives the bytes back.
+struct AllocOwner {
+  explicit AllocOwner(srm3_plan *p);
+  ~AllocOwner();
+  srm3_plan *prev;
+};
 // Grid-barrier timeout self-test (plan.cu): *timed_out = the abort word.
 int selftest_barrier(long long polls, int *timed_out);
 
@@ -76,6 +84,7 @@ struct srm3_plan {
   int log2nx = 0, log2nt = 0;
   double ku = 0, wu = 0, dk = 0, dw = 0, dkdw = 0;
   int row_lo = 0, row_hi = 0;  // lattice rows whose coefficients the plan computes
+  double dev_bytes = 0.0;       // device memory the plan holds (see AllocOwner)
   int precision = SRM3_FP32;
   int storage = SRM3_STORAGE_RECOMPUTE;
   cudaStream_t stream = nullptr;

@@ -14,10 +14,19 @@ batches run beside it instead of queueing behind it.  Batches admitted
 while others run overlap with them on the device.  A request's latency runs
 from its arrival to the completion of its batch.
 
-Device memory of a plan (the estimate the budget counts): the FP64/FP32
-plan tables, about 136 bytes per lattice point, plus the W table when
-stored.  Batch buffers are stream-ordered allocations of the batch and are
-released when it completes.
+Memory budget.  A plan is charged what the library reports it holds
+(srm3_info.device_bytes: lattice and sampling tables, recursion state, W
+table, sampling workspace), measured after it is built and again after each
+batch it takes part in (its workspace can grow).  A batch is charged, at
+admission, an upper bound of what it will allocate (batch_bytes_estimate:
+the shape-group buffers the library allocates -- y, C, H, factor pointers,
+seeds, work units -- and the output fields); it is admitted only when the
+cached plans, the batches in flight and it fit the budget together, else its
+requests wait for memory to come back (a batch that would exceed the budget
+with nothing in flight is admitted alone rather than never).  Unpinned plans
+are evicted, least recently used first, to make room.  A plan build or a
+batch that fails (an allocation refused by the device, for instance) fails
+its own requests (Request.error) and the server goes on serving the others.
 """
 from __future__ import annotations
 
@@ -36,8 +45,62 @@ def plan_key(wl: Workload):
             wl.lam, wl.n_x, wl.n_t, wl.precision, wl.target, wl.sigma_g, wl.beta, wl.storage)
 
 
-def plan_bytes_estimate(wl: Workload, table_bytes: float = 0.0) -> float:
-    return 136.0 * wl.n_kappa * wl.n_omega + table_bytes
+def plan_bytes(p) -> float:
+    """Device memory plan p holds now (srm3_info.device_bytes)."""
+    return float(p.info().device_bytes)
+
+
+def _sspad(n: int) -> int:
+    """Sheet-samples of n samples, rounded up to whole 64-wide groups."""
+    return ((2 * n + 63) // 64) * 64
+
+
+def _shape_key(wl: Workload):
+    return (wl.n_kappa, wl.n_omega, wl.n_x, wl.n_t, wl.kappa_u, wl.omega_u, wl.sigma_g,
+            wl.beta)
+
+
+def batch_bytes_estimate(entries) -> float:
+    """Upper bound of the device memory one batch takes: ``entries`` are
+    (workload, samples, grouped) per plan of the batch, grouped when the
+    plan joins a shape group (FP32, W recomputed, the plain pair set).  Per
+    shape group with T samples, at most m from one plan: y + y0 = (n_kappa
+    (n_omega + 128) + 1) sspad(T) 8 bytes, C = 2 T n_kappa n_omega 8, H = m
+    n_kappa n_t 8, 16 T of factor pointers (the formula of
+    srm3_batch_device_bytes); per sample 8 bytes of seed and its output field;
+    512 bytes per plan and 16 per work unit of descriptors and unit list."""
+    groups = {}
+    total = 0.0
+    for wl, n, grouped in entries:
+        es = 4 if wl.precision == "fp32" else 8
+        total += n * (8 + wl.n_x * wl.n_t * es) + 512
+        sw = 32  # outputs per work unit along omega
+        units = wl.n_kappa * ((wl.n_omega + sw - 1) // sw) * (_sspad(n) // 64)
+        total += 16 * units
+        if grouped:
+            g = groups.setdefault(_shape_key(wl), [wl, 0, 0])
+            g[1] += n
+            g[2] = max(g[2], n)
+    for wl, T, m in groups.values():
+        nk, nw = wl.n_kappa, wl.n_omega
+        total += 8.0 * ((nk * (nw + 128) + 1) * _sspad(T) + 2 * T * nk * nw + m * nk * wl.n_t)
+        total += 16.0 * T
+        total += 16 * nk * ((nw + 31) // 32) * (_sspad(T) // 64)
+    return total
+
+
+def admit(queue, max_samples: int, fits) -> list:
+    """Requests taken from the head of ``queue`` for one batch: as many as
+    keep the batch within ``max_samples`` samples and ``fits(candidates)``;
+    the rest stay queued, in order."""
+    take, total = [], 0
+    while queue and total + queue[0].n <= max_samples:
+        if not fits(take + [queue[0]]):
+            break
+        r = queue.popleft()
+        take.append(r)
+        total += r.n
+    return take
 
 
 @dataclasses.dataclass
@@ -49,6 +112,7 @@ class Request:
     admitted: float | None = None
     done: float | None = None
     out: object = None            # device tensor [n][n_x][n_t] once done
+    error: str | None = None      # why the request failed (it then has no out)
 
     @property
     def n(self) -> int:
@@ -84,8 +148,25 @@ class PlanCache:
                 self.plans.move_to_end(key)
             return p
 
-    def build(self, wl):
-        """Build and insert the plan of wl (evicting as needed); returns it."""
+    def _evict_for(self, need, reserved=0.0, keep=()):
+        """Evict unpinned plans (none whose key is in `keep`), least recently
+        used first, until need more bytes fit beside the plans and `reserved`
+        (lock held).  Returns whether they fit."""
+        while self.used + reserved + need > self.budget:
+            victim = next((k for k in self.plans if self.pins[k] == 0 and k not in keep), None)
+            if victim is None:
+                return False
+            old = self.plans.pop(victim)
+            self.used -= self.size.pop(victim)
+            self.evictions += 1
+            old.destroy()
+        return True
+
+    def build(self, wl, reserved=0.0):
+        """Build and insert the plan of wl, charged the device memory it
+        reports, evicting as needed to fit beside `reserved` bytes (batches
+        in flight); returns it.  A builder that raises leaves the cache as it
+        was and the exception goes to the caller."""
         key = plan_key(wl)
         with self.lock:
             if key in self.plans:
@@ -94,27 +175,34 @@ class PlanCache:
         t0 = time.perf_counter()
         p = self.builder(wl)
         dt = time.perf_counter() - t0
-        info_bytes = 0.0
-        try:
-            info_bytes = float(p.info().table_bytes)
-        except Exception:  # noqa: BLE001 -- stand-in plans in tests
-            info_bytes = 0.0
-        need = plan_bytes_estimate(wl, info_bytes)
+        need = plan_bytes(p)
         with self.lock:
             self.builds += 1
             self.build_seconds += dt
-            while self.used + need > self.budget:
-                victim = next((k for k in self.plans if self.pins[k] == 0), None)
-                if victim is None:
-                    break  # everything in flight: admit over budget rather than deadlock
-                old = self.plans.pop(victim)
-                self.used -= self.size.pop(victim)
-                self.evictions += 1
-                old.destroy()
+            # everything in flight: keep the plan over budget rather than deadlock
+            self._evict_for(need, reserved)
             self.plans[key] = p
             self.size[key] = need
             self.used += need
         return p
+
+    def refresh(self, wl):
+        """Charge the plan of wl what it holds now (its workspace may have
+        grown in a batch)."""
+        key = plan_key(wl)
+        with self.lock:
+            p = self.plans.get(key)
+            if p is None:
+                return
+            need = plan_bytes(p)
+            self.used += need - self.size[key]
+            self.size[key] = need
+
+    def make_room(self, need, reserved, keep=()):
+        """Evict unpinned plans outside `keep` until `need` bytes fit beside
+        the plans and `reserved`; returns whether they fit."""
+        with self.lock:
+            return self._evict_for(need, reserved, set(keep))
 
     def pin(self, wl):
         with self.lock:
@@ -151,6 +239,9 @@ class Server:
         self.queues = {"light": collections.deque(), "heavy": collections.deque()}
         self.missing = collections.deque()      # plans being built
         self.finished = []
+        self.failed = []
+        self.inflight_bytes = [0.0] * len(self.slot_class)  # charge of each slot's batch
+        self.over_budget = 0                    # batches admitted alone over the budget
         self.batches = 0
         self.launches = 0                       # kernels: phases + 2 FFT stages per plan, 1 pair sum
         self.busy = 0.0                         # seconds with a batch in flight
@@ -169,7 +260,19 @@ class Server:
                 if self._stop:
                     return
                 req = self.missing[0]
-            self.cache.build(req.wl)
+            try:
+                self.cache.build(req.wl, reserved=sum(self.inflight_bytes))
+            except Exception as e:  # noqa: BLE001 -- the spectrum's requests fail, serving goes on
+                with self._cv:
+                    key = plan_key(req.wl)
+                    keep = collections.deque()
+                    for r in self.missing:
+                        if plan_key(r.wl) == key:
+                            self._fail(r, f"plan build failed: {e}")
+                        else:
+                            keep.append(r)
+                    self.missing = keep
+                continue
             with self._cv:
                 # every waiting request whose plan now exists moves to its queue
                 keep = collections.deque()
@@ -179,6 +282,27 @@ class Server:
                     else:
                         keep.append(r)
                 self.missing = keep
+
+    def _fail(self, req, why):
+        req.error = why
+        req.done = req.done if req.done is not None else 0.0
+        self.failed.append(req)
+        self.finished.append(req)
+
+    def _entries(self, reqs):
+        """batch_bytes_estimate entries of the plans a batch of reqs uses."""
+        groups = collections.OrderedDict()
+        for r in reqs:
+            groups.setdefault(plan_key(r.wl), []).append(r)
+        out = []
+        for rs in groups.values():
+            wl = rs[0].wl
+            p = self.cache.lookup(wl)
+            info = p.info() if p is not None else None
+            grouped = (info is not None and wl.precision == "fp32" and info.storage == 2
+                       and info.interactions == 0 and wl.envelope == "gauss")
+            out.append((wl, sum(r.n for r in rs), grouped))
+        return out
 
     def _class(self, req):
         return "heavy" if 2 * req.wl.pairs() > self.heavy_terms else "light"
@@ -195,14 +319,32 @@ class Server:
     def _launch(self, slot, now):
         torch = self.torch
         q = self.queues[self.slot_class[slot]]
+        reserved = sum(self.inflight_bytes)
+        alone = not any(f is not None for f in self.inflight)
+
+        # plans that queued requests still need are not evicted for room
+        wanted = {plan_key(r.wl) for qq in self.queues.values() for r in qq}
+
+        def fits(cand):
+            need = batch_bytes_estimate(self._entries(cand))
+            if self.cache.make_room(need, reserved, keep=wanted | {plan_key(r.wl) for r in cand}):
+                return True
+            return alone and len(cand) == 1  # never hold the only possible batch forever
+
         with self._cv:
-            take, total = [], 0
-            while q and total + q[0].n <= self.max_samples:
-                r = q.popleft()
-                take.append(r)
-                total += r.n
+            take = admit(q, self.max_samples, fits)
+            # a plan evicted while its request waited (building another plan
+            # made room) is built again before the request runs
+            gone = [r for r in take if self.cache.lookup(r.wl) is None]
+            if gone:
+                take = [r for r in take if self.cache.lookup(r.wl) is not None]
+                self.missing.extend(gone)
+                self._cv.notify()
         if not take:
             return False
+        charge = batch_bytes_estimate(self._entries(take))
+        if self.cache.used + reserved + charge > self.cache.budget:
+            self.over_budget += 1
         groups = collections.OrderedDict()  # one batch entry per plan
         for r in take:
             groups.setdefault(plan_key(r.wl), []).append(r)
@@ -225,12 +367,23 @@ class Server:
                 plans.append(p)
                 counts.append(n)
                 outs.append(o)
-        b = srm3.Batch(plans, counts, outs, stream=s.cuda_stream)
-        if self.slot_class[slot] == "heavy":
-            b.set_max_ctas(self.heavy_ctas)
-        b.run(seeds)
+        try:
+            b = srm3.Batch(plans, counts, outs, stream=s.cuda_stream)
+            if self.slot_class[slot] == "heavy":
+                b.set_max_ctas(self.heavy_ctas)
+            b.run(seeds)
+        except Exception as e:  # noqa: BLE001 -- these requests fail, serving goes on
+            for rs in groups.values():
+                self.cache.unpin(rs[0].wl)
+            del outs
+            for r in take:
+                r.out = None
+                r.done = now
+                self._fail(r, f"batch failed: {e}")
+            return True
         ev = torch.cuda.Event()
         ev.record(s)
+        self.inflight_bytes[slot] = charge
         self.inflight[slot] = (b, ev, take, [rs[0].wl for rs in groups.values()], outs)
         self.batches += 1
         self.launches += 3 * len(plans) + 1
@@ -245,6 +398,8 @@ class Server:
             b.destroy()
             for wl in wls:
                 self.cache.unpin(wl)
+                self.cache.refresh(wl)
+            self.inflight_bytes[i] = 0.0
             for r in reqs:
                 r.done = now
                 self.finished.append(r)

@@ -36,6 +36,7 @@ EXPORTED = [
     "srm3_plan_moments", "srm3_selftest_timeouts",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
+    "srm3_batch_device_bytes",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
     "srm3_batch_pair_terms", "srm3_batch_destroy", "srm3_batch_enable_timing",
     "srm3_batch_pairsum_ms", "srm3_batch_set_max_ctas",
@@ -83,7 +84,7 @@ class srm3_info(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("fixed_point_iterations", ctypes.c_int32),
-                ("diff_pairs", ctypes.c_int64)]
+                ("diff_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_double)]
 
 
 class srm3_timings(ctypes.Structure):
@@ -151,6 +152,8 @@ def load(build_if_needed: bool = True):
     lib.srm3_batch_sync.argtypes = [vp]
     lib.srm3_batch_pair_terms.argtypes = [vp]
     lib.srm3_batch_pair_terms.restype = ctypes.c_int64
+    lib.srm3_batch_device_bytes.argtypes = [vp]
+    lib.srm3_batch_device_bytes.restype = ctypes.c_int64
     lib.srm3_batch_destroy.argtypes = [vp]
     lib.srm3_batch_destroy.restype = None
     lib.srm3_batch_enable_timing.argtypes = [vp, i32]
@@ -278,6 +281,11 @@ class Batch:
     @property
     def pair_terms(self) -> int:
         return int(load().srm3_batch_pair_terms(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        """Device memory the batch allocated itself (srm3_batch_device_bytes)."""
+        return int(load().srm3_batch_device_bytes(self.handle))
 
     def run(self, seeds):
         a, p = _seeds(seeds)
