@@ -55,7 +55,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="srm3", choices=["srm3", "reference"])
     ap.add_argument("--config", default="bridge",
-                    choices=["bridge", "bridge_rc", "bridge_sep", "large", "tiny", "prof128",
+                    choices=["bridge", "bridge_rc", "bridge_sep", "bridge_mixed", "large", "tiny",
+                             "prof128",
                              "uneven", "serve", "paper_bridge"],
                     help="workload; bridge is the benchmark line, the others are for "
                          "profiling and checks")
@@ -226,18 +227,26 @@ def oracle_baseline(wl, rows=48, seed=1, passes=None):
     else:
         env = oracle.Envelope("gauss", wl.sigma_g * wl.n_kappa / sub)  # same width per index
     eps = 1e-3
+    mixed = wl.interactions == "mixed"
     t0 = time.perf_counter()
-    Sp, _ = oracle.recursion(S, sub * dk, wl.omega_u, eps, env)
-    t_rec = time.perf_counter() - t0
+    if mixed:  # one Gauss-Seidel sweep of the fixed point (it takes about a dozen)
+        Sp, _, _ = oracle.recursion_mixed(S, sub * dk, wl.omega_u, eps, env, tol=1.0,
+                                          max_sweeps=2)
+        t_rec = (time.perf_counter() - t0) / 2
+    else:
+        Sp, _ = oracle.recursion(S, sub * dk, wl.omega_u, eps, env)
+        t_rec = time.perf_counter() - t0
     t0 = time.perf_counter()
-    C = oracle.coeffs(S, Sp, sub * dk, wl.omega_u, eps, seed, env)
+    C = oracle.coeffs(S, Sp, sub * dk, wl.omega_u, eps, seed, env, mixed=mixed)
     t_coef = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.field_dft(C, wl.n_x, wl.n_t)
     t_dft = time.perf_counter() - t0
     from paper_2310_03979_gb300.workloads import Workload
-    sub_pairs = Workload("sub", sub, wl.n_omega, 1.0, 1.0, 1.0, 2.0, 2, 2, ()).pairs()
-    full_pairs = wl.pairs()
+    subw = Workload("sub", sub, wl.n_omega, 1.0, 1.0, 1.0, 2.0, 2, 2, (),
+                    interactions=wl.interactions)
+    sub_pairs = subw.pairs() + subw.diff_pairs()
+    full_pairs = wl.pairs() + wl.diff_pairs()
     if passes is None:
         passes = 48  # plain bisection to 1e-13 from the [0, 2^m] bracket
     n = wl.n_samples
@@ -674,19 +683,28 @@ def main():
     es = 4 if wl.precision == "fp32" else 8
     dt = torch.float32 if es == 4 else torch.float64
     out = torch.empty((n, wl.n_x, wl.n_t), dtype=dt, device="cuda")
-    pairs = wl.pairs()
+    pairs = wl.pairs() + wl.diff_pairs()
     terms_per_step = 2 * pairs * n
+    # mixed interactions: the plan (a fixed-point solve per eps evaluation,
+    # seconds at this size) is built once beforehand and its build time is
+    # reported beside the line; a step is the sampling batch
+    prebuilt = None
+    if wl.interactions == "mixed":
+        t0 = time.perf_counter()
+        prebuilt = srm3.Plan.create(wl, stream=sptr)
+        prebuilt_ms = (time.perf_counter() - t0) * 1e3
 
     def one_step(host_out=None):
-        plan = srm3.Plan.create(wl, stream=sptr)
+        plan = prebuilt or srm3.Plan.create(wl, stream=sptr)
         srm3.enable_timing(plan.handle, True)
         if host_out is None:
             srm3.sample(plan.handle, seeds, n, out.data_ptr())
         else:
             srm3.sample_host(plan.handle, seeds, n, host_out.data_ptr())
-        t = srm3.get_timings(plan.handle)
+        t = srm3.get_timings(plan.handle, reset=prebuilt is not None)
         info = plan.info()
-        plan.destroy()
+        if prebuilt is None:
+            plan.destroy()
         return t, info
 
     for _ in range(args.warmup):
@@ -731,17 +749,22 @@ def main():
     t_last = recs[-1][0]
     chunks = math.ceil(n / 128)
     # kernels launched per step (matches the ncu launch list): spectrum 1,
-    # envelope tables 2 + g^2 1, the sum of S 1, linear pass + reduction 2,
-    # each recursion pass 1, sampling tables 4, W table 1 if stored; per
-    # 128-sample chunk: phases, pair sum, two FFT stages
-    launches_per_step = (1 + 3 + 1 + 2 + (info.root_passes + info.root_passes_fp32)
+    # envelope tables 2 + g^2 1, recursion index lists 2, the sum of S 1,
+    # linear pass + reduction 2, each recursion pass 1, sampling tables 4,
+    # W table 1 if stored; per 128-sample chunk: phases, pair sum, two FFT
+    # stages
+    launches_per_step = (1 + 3 + 2 + 1 + 2 + (info.root_passes + info.root_passes_fp32)
                          + 4 + (1 if info.storage == 1 else 0) + 4 * chunks)
     if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
         # self-convolution passes, two output FFT stages
-        launches_per_step = (1 + 3 + 1 + (info.root_passes + info.root_passes_fp32)
+        launches_per_step = (1 + 3 + 2 + 1 + (info.root_passes + info.root_passes_fp32)
                              + 4 + 1 + 6 * chunks)
+    if prebuilt is not None:
+        # sampling only: per chunk phases, sum and difference pair sums, two
+        # FFT stages
+        launches_per_step = 5 * chunks
     traffic = None
     src = os.path.join(ROOT, "paper_2310_03979_gb300", "csrc", "pairsum.cuh")
     if wl.name.startswith("bridge") and info.storage == 1 and es == 4:
@@ -760,8 +783,12 @@ def main():
                    "storage": "table" if info.storage == 1 else "recompute",
                    "precision": wl.precision, "l2": "inputs larger than L2 (W table "
                    f"{info.table_bytes / 1e9:.1f} GB, y {n * 2 * 8 * wl.n_kappa * (wl.n_omega + 128) / 1e6:.0f} MB)",
-                   "step": "plan build (spectrum, FP64 recursion + eps search, W table) + "
-                           f"{n}-sample batch"},
+                   "step": ("plan build (spectrum, FP64 recursion + eps search, W table) + "
+                            f"{n}-sample batch") if prebuilt is None else
+                           (f"{n}-sample batch on a plan built beforehand (mixed interactions: "
+                            f"{prebuilt_ms:.0f} ms to build, the FP64 fixed point of Eq. pure "
+                            "solved for every eps of the search)"),
+                   "interactions": wl.interactions},
         "samples_per_s": n * world / (ms_per_step * 1e-3),
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "stages_ms_last_step": {"plan_total": info.plan_ms, "recursion": t_last.recursion_ms,
@@ -782,7 +809,8 @@ def main():
             algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (
                 wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
             kernel="k_pairsum_f32p<table>" if info.storage == 1 else
-                   "k_pairsum_f32p<recompute>")),
+                   "k_pairsum_f32p<recompute>" if prebuilt is None else
+                   "k_pairsum_f32p<recompute> + k_pairsum_f32d (sum and difference pairs)")),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "eps": info.eps, "max_sum_b2": info.max_sum_b2,
@@ -803,7 +831,7 @@ def main():
                        "d2h_bytes_per_step": n * wl.n_x * wl.n_t * es,
                        "ms_per_step": e2e_s * 1e3}
 
-    if rank == 0 and wl.precision == "fp32" and not args.no_fp64_form:
+    if rank == 0 and wl.precision == "fp32" and not args.no_fp64_form and prebuilt is None:
         # the plain FP64 GPU form on the same workload and seeds: sampling only
         # (plans built beforehand), against the FP32 form's sampling stages
         fp64_ms, fp32_ms = [], []
@@ -829,8 +857,11 @@ def main():
             "speedup": min(fp64_ms) / min(fp32_ms),
             "note": "sampling only (plans prebuilt), same workload and seeds"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_baseline(wl, rows=128)
+        # a mixed step samples on a prebuilt plan: the oracle's step likewise
+        cb = oracle_baseline(wl, rows=128, passes=0 if prebuilt is not None else None)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if prebuilt is not None:
+        prebuilt.destroy()
     if rank == 0:
         print(json.dumps(line))
     if dist:

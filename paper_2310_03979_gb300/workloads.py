@@ -158,7 +158,15 @@ def _paper_bridge():
 
 PAPER_BRIDGE = _paper_bridge()
 
+# The bridge-span wave with the mixed-sign (difference) interactions of the
+# general form as well: the same lattice, spectrum, target and seeds, W
+# recomputed (about three times the pair-terms of the sum interactions).
+BRIDGE_MIXED = Workload("bridge_256x512_mixed_fp32", 256, 512, 0.25, 4 * math.pi, 40.0,
+                        20.0, 512, 1024, tuple(range(1, 65)), precision="fp32",
+                        storage="recompute", interactions="mixed")
+
 CONFIGS = {"tiny": TINY, "bridge": BRIDGE, "bridge_rc": BRIDGE_RC, "bridge_sep": BRIDGE_SEP,
+           "bridge_mixed": BRIDGE_MIXED,
            "large": LARGE, "prof128": PROF128, "paper_bridge": PAPER_BRIDGE}
 
 
