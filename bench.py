@@ -280,14 +280,19 @@ def run_uneven(args):
     torch.cuda.init()
     t0 = time.perf_counter()
     tuned = {}
-    for wl in wls:  # one autotune per lattice shape, on that shape's first spectrum
-        key = (wl.n_kappa, wl.n_omega)
+    per_shape = {}
+    for wl in wls:
+        k = (wl.n_kappa, wl.n_omega)
+        per_shape[k] = per_shape.get(k, 0) + wl.n_samples
+    for wl in wls:  # one autotune per lattice shape, on that shape's first spectrum, with
+        key = (wl.n_kappa, wl.n_omega)  # the samples the batch gives the shape (up to 128)
         if key in tuned:
             continue
         with srm3.Plan.create(wl, storage="table") as p:
-            r = srm3.autotune(p.handle, max(1, min(wl.n_samples, 32)))
+            r = srm3.autotune(p.handle, max(1, min(per_shape[key], 128)))
             tuned[key] = {"table_ms": r.table_ms, "recompute_ms": r.recompute_ms,
-                          "storage": "table" if r.storage == 1 else "recompute"}
+                          "storage": "table" if r.storage == 1 else "recompute",
+                          "tile": f"{r.tile_width} wide"}
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     plans = [srm3.Plan.create(wl, storage="tuned") for wl in wls]
@@ -337,7 +342,8 @@ def run_uneven(args):
     ps_ms = statistics.median(ps)
     choice = {}
     for k, v in tuned.items():
-        choice[v["storage"]] = choice.get(v["storage"], 0) + 1
+        c = f'{v["storage"]}, {v["tile"]}'
+        choice[c] = choice.get(c, 0) + 1
     line = {
         "metric": METRIC, "value": terms / (ms * 1e-3), "unit": "pair-terms/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,

@@ -222,6 +222,10 @@ typedef struct srm3_info {
                                 the sampling workspace (which grows with the
                                 largest n sampled, up to 128 per chunk);
                                 batch buffers are the batch's */
+    int32_t tile_width;      /* FP32 pair-sum work unit: 32 or 16 outputs (the
+                                autotuner's choice for the lattice shape, else
+                                32); the results do not depend on it */
+    int32_t reserved2;
 } srm3_info;
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
@@ -349,34 +353,52 @@ int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset);
 
 /* ---- Autotuning (FP32 plans) ---------------------------------------------
  * The FP32 pair sum can read W from the stored table or rebuild it from the
- * envelope factors; which is faster depends on the lattice and the number of
- * samples.  srm3_autotune times one pair-sum launch of each on this plan for
- * n samples (the phases of seeds 1..n, in the plan's workspace), keeps the
- * faster -- building the W table when it wins and the plan has none (if it
- * fits the plan's table budget), freeing it when recomputation wins -- and
- * records the choice for the plan's (n_kappa, n_omega) in this process:
- * plans created later with SRM3_STORAGE_TUNED use it.  Synchronous.
- * Errors: INVALID_ARG (n outside 1..128), NOT_SUPPORTED (FP64 plan),
- * OUT_OF_MEMORY, CUDA. */
+ * envelope factors, and its work unit can be 32 outputs wide (four compute
+ * warps) or 16 (two: less idle work in the last chunks of every row pair,
+ * which matters on short rows); which is fastest depends on the lattice and
+ * the number of samples.  srm3_autotune times one pair-sum launch of every
+ * (storage, tile) on this plan for n samples (the phases of seeds 1..n, in
+ * the plan's workspace), keeps the fastest -- building the W table when a
+ * table form wins and the plan has none (if it fits the plan's table
+ * budget), freeing it when recomputation wins -- and records the choice for
+ * the plan's (n_kappa, n_omega) in this process: plans created later with
+ * that lattice take the tile (the coefficients do not depend on it), and
+ * those created with SRM3_STORAGE_TUNED the storage too.  Synchronous.
+ * Errors: INVALID_ARG (n outside 1..128), NOT_SUPPORTED (FP64 plan, mixed
+ * or separable plan), OUT_OF_MEMORY, CUDA. */
 typedef struct srm3_tune_result {
-    double table_ms;      /* one pair-sum launch with the stored table; < 0: not tried */
-    double recompute_ms;  /* one pair-sum launch with W rebuilt in the kernel */
+    double table_ms;      /* fastest launch with the stored table; < 0: not tried */
+    double recompute_ms;  /* fastest launch with W rebuilt in the kernel */
     int32_t storage;      /* the choice: SRM3_STORAGE_TABLE or SRM3_STORAGE_RECOMPUTE */
     int32_t samples;      /* n */
+    int32_t tile_width;   /* the choice of tile: 32 or 16 outputs per work unit */
+    int32_t reserved;
+    double table_ms_w32, table_ms_w16;         /* each (storage, tile) timed; < 0: */
+    double recompute_ms_w32, recompute_ms_w16; /* not tried */
 } srm3_tune_result;
 int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *result);
+
+/* Set the FP32 pair sum's work unit of this plan to 32 or 16 outputs (what
+ * srm3_autotune would choose, set by hand).  The coefficients are the same
+ * bit for bit either way: each output's sums and their order do not depend
+ * on the unit.  Takes effect at the next sampling call or batch creation.
+ * Errors: INVALID_ARG (width not 16 or 32), NOT_SUPPORTED (FP64 or
+ * separable plan). */
+int srm3_set_tile_width(srm3_plan *plan, int width);
 
 /* ---- Batches of plans ------------------------------------------------------
  * One sampling job over m plans with uneven lattices and sample counts: the
  * phases of every plan, ONE persistent pair-sum launch over the work units
- * of all FP32 plans (cost-sorted across plans; FP64 plans get their own
- * plain launches), then the transforms, all on one stream.  FP32 plans with
- * W recomputed that share a lattice shape (n_kappa, n_omega, n_x, n_t,
- * cutoffs, envelope width, biphase) form a shape group: their samples share
- * the lanes of the pair sum -- the weights depend only on the shape, each
- * sample keeps its own pure and pair factors -- so many spectra with one or
- * a few samples each still fill the kernel; a group uses buffers of the
- * batch, not the plans' workspaces.  srm3_batch_create checks the plans
+ * of all FP32 plans (cost-sorted across plans, in the tile width of the
+ * plans that carry most of the pair-terms; FP64 plans get their own plain
+ * launches), then the transforms, all on one stream.  FP32 plans of the plain pair set that share a lattice shape
+ * (n_kappa, n_omega, n_x, n_t, cutoffs, envelope width, biphase), a storage
+ * (W recomputed, or a stored W table: the table holds the pair envelopes
+ * alone, a function of the shape) and a tile width form a shape group: their
+ * samples share the lanes of the pair sum -- the weights depend only on the
+ * shape, each sample keeps its own pure and pair factors -- so many spectra
+ * with one or a few samples each still fill the kernel; a group uses buffers
+ * of the batch, not the plans' workspaces, and the first plan's weights.  srm3_batch_create checks the plans
  * (one device, no plan twice), allocates the group buffers and sizes the
  * other plans' workspaces for their counts, and puts the descriptors and
  * the unit list on the device (at most 4096 samples per shape group).  counts[i] in 1..128;

@@ -156,35 +156,50 @@ __device__ __forceinline__ float2 f2_split(f32x2 v) {
 namespace packed {
 constexpr int R = kTileR;                 // outputs per thread (8)
 constexpr int U = 4;                      // iw per register block
-constexpr int NC = kWarpsPerCta;          // compute warps = tiles per super-tile (4)
-constexpr int NCT = 32 * NC;              // compute threads
-constexpr int NT = NCT + 32;              // plus the producer warp
-constexpr int SW = NC * R;                // super-tile width (32)
 constexpr int CH = 16;                    // iw per chunk
 constexpr int NB = CH / U;                // register blocks per chunk
 constexpr int NV = R + U - 1;             // y_b window per block (11)
 constexpr int NE = 2 * U + R - 2;         // envelope window per block (14)
-constexpr int YB_ROWS = CH + SW - 1;      // y_b rows per chunk (47)
 constexpr int BOX_ROWS = 16;              // rows per TMA tile load
-constexpr int YB_BOXES = (YB_ROWS + BOX_ROWS - 1) / BOX_ROWS;  // 3
-constexpr int YROWS = CH + YB_BOXES * BOX_ROWS;  // staged rows per chunk (64)
 constexpr int LANES = 32;                 // sample pairs per group
 constexpr int ROW_BYTES = LANES * 16;     // one staged row
-constexpr int STAGE_Y = YROWS * LANES;    // float4 per stage
-constexpr int STAGE_W = NC * R * CH;      // float2 slots per stage (W: the first half)
 constexpr int EWIN = 64;                  // (w, w) pairs per stage, envelope
 constexpr int NK = 4 * R;                 // Kahan sums per compute thread
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 static_assert(kTileU == CH && kTileR == R, "W table chunks: one 512-byte span per tile");
-static_assert(2 * (CH - 1) + SW <= EWIN && EWIN <= STAGE_W, "envelope window of a chunk");
 static_assert(NB * U == CH && (NE % 2) == 0 && CH == BOX_ROWS, "block shape");
-static_assert(kPad >= SW + CH + 1, "staged rows stay inside the zero padding of y");
+
+// Tile shape of the FP32 pair sum: NC compute warps, each one 8-wide output
+// tile, make one super-tile of SW = 8 NC outputs (a work unit with one
+// sample group).  NC = 4 (32-wide) suits long rows; NC = 2 (16-wide) halves
+// the triangle of work across a super-tile's warps in the last chunks of
+// every row pair (the low tiles of a super-tile need fewer omega values), at
+// the cost of staging 48 rows per chunk for two warps instead of 64 for four.
+// The sums of an output and their order do not depend on NC: a warp walks
+// the same chunks and register blocks of its tile either way.
+template <int NC_>
+struct Shape {
+  static constexpr int NC = NC_;                    // compute warps = tiles per super-tile
+  static constexpr int NCT = 32 * NC;               // compute threads
+  static constexpr int NT = NCT + 32;               // plus the producer warp
+  static constexpr int SW = NC * R;                 // super-tile width
+  static constexpr int YB_ROWS = CH + SW - 1;       // y_b rows per chunk
+  static constexpr int YB_BOXES = (YB_ROWS + BOX_ROWS - 1) / BOX_ROWS;
+  static constexpr int YROWS = CH + YB_BOXES * BOX_ROWS;  // staged rows per chunk
+  static constexpr int STAGE_Y = YROWS * LANES;     // float4 per stage
+  static constexpr int STAGE_W = NC * R * CH;       // float2 slots per stage (W: the first half)
+  static constexpr int CTAS_PER_SM = NC == 4 ? 2 : 3;  // the launch bounds' residency
+  static_assert(2 * (CH - 1) + SW <= EWIN && EWIN <= STAGE_W, "envelope window of a chunk");
+  static_assert(kPad >= SW + CH + 1, "staged rows stay inside the zero padding of y");
+};
 }  // namespace packed
 
+template <int NC>
 inline size_t pairsum_f32p_smem() {
   using namespace packed;
-  return 128 + (size_t)2 * STAGE_Y * sizeof(float4) + (size_t)2 * STAGE_W * sizeof(float2) +
-         (size_t)2 * NK * NCT * sizeof(float);
+  using S = Shape<NC>;
+  return 128 + (size_t)2 * S::STAGE_Y * sizeof(float4) + (size_t)2 * S::STAGE_W * sizeof(float2) +
+         (size_t)2 * NK * S::NCT * sizeof(float);
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) {
@@ -284,9 +299,9 @@ struct PsDesc {  // aligned as CUtensorMap
 __host__ __device__ __forceinline__ int ps_rowsteps(int kk, int half) {
   return half ? (kk / 2 + 2) / 2 : kk / 2 + 1;
 }
-__host__ __device__ __forceinline__ int ps_nitems(int kk, int kws0, int half) {
+__host__ __device__ __forceinline__ int ps_nitems(int kk, int kws0, int half, int sw) {
   using namespace packed;
-  return ps_rowsteps(kk, half) * ((kws0 + SW + CH - 1) / CH);
+  return ps_rowsteps(kk, half) * ((kws0 + sw + CH - 1) / CH);
 }
 // The k-th unit of CTA c out of C (snake order over the cost-sorted units).
 __device__ __forceinline__ int ps_unit_id(int k, int c, int C) {
@@ -380,11 +395,14 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
 // sorted by decreasing cost).  MIXED = false compiles the full-group path
 // alone (every descriptor has half = 0); MIXED = true also takes half-mode
 // descriptors.
-template <bool MIXED>
-__global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
-    const __grid_constant__ PsDesc d0, const PsDesc *__restrict__ descs,
-    const int4 *__restrict__ units, int nunits, int *__restrict__ err) {
+template <bool MIXED, int NCW>
+__global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CTAS_PER_SM)
+    k_pairsum_f32p(const __grid_constant__ PsDesc d0, const PsDesc *__restrict__ descs,
+                   const int4 *__restrict__ units, int nunits, int *__restrict__ err) {
   using namespace packed;
+  using S = Shape<NCW>;
+  constexpr int NC = S::NC, NCT = S::NCT, SW = S::SW, YB_BOXES = S::YB_BOXES, YROWS = S::YROWS;
+  constexpr int STAGE_Y = S::STAGE_Y, STAGE_W = S::STAGE_W;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [2]
   unsigned long long *empty = full + 2;                                         // [2]
@@ -414,7 +432,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const PsDesc &d = descs ? descs[un.x] : d0;
       const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
       const int half = MIXED ? d.half : 0;
-      const int nitems = ps_nitems(kk, kws0, half), tab = d.table, rs = d.rowstride;
+      const int nitems = ps_nitems(kk, kws0, half, SW), tab = d.table, rs = d.rowstride;
       const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
       for (int item = 0; item < nitems; ++item, ++q) {
@@ -494,7 +512,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
     const int kk = un.y, kws0 = un.z, grp = un.w, nw = d.nw, tab = d.table;
     const int kw0 = kws0 + R * warp, nch = (kws0 + SW + CH - 1) / CH;
     const int half = MIXED ? d.half : 0;
-    const int nitems = ps_nitems(kk, kws0, half);
+    const int nitems = ps_nitems(kk, kws0, half, SW);
     const int hl = half ? lane >> 4 : 0;        // which row pair of a step this lane takes
     const int ln = half ? lane & 15 : lane;     // the lane's sample pair within the group
     const size_t SP = (size_t)d.SSpad / 2;  // float4 per lattice entry
@@ -515,7 +533,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
         const float2 *pw = reinterpret_cast<const float2 *>(
             reinterpret_cast<const float *>(sw + stage * STAGE_W) + warp * R * CH);
         const float2 *pe = reinterpret_cast<const float2 *>(
-            reinterpret_cast<const float *>(sw + stage * STAGE_W) + 24 - 8 * warp);
+            reinterpret_cast<const float *>(sw + stage * STAGE_W) + (SW - R) - R * warp);
         if (half) {
           const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;
           const float4 *pb = pa + (CH + R * warp + CH - U) * (LANES / 2);
@@ -608,7 +626,7 @@ __global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32p(
       const int kidx = kk * nw + kw;
       const float4 yk4 =
           d.y[((size_t)kk * d.rowstride + kPad + kw) * SP + (size_t)grp * LANES + ln];
-      const float cf = tab ? 1.0f : ck[kidx];
+      const float cf = ck[kidx];  // the pair factor (the table holds the envelopes alone)
       const float P = Pk[kidx];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -709,9 +727,12 @@ __device__ __forceinline__ void ps_chunk_diff(const float4 *__restrict__ pb,
   }
 }
 
-__global__ void __launch_bounds__(packed::NT, 2) k_pairsum_f32d(
+__global__ void __launch_bounds__(packed::Shape<4>::NT, 2) k_pairsum_f32d(
     const __grid_constant__ PsDiffDesc d, int nunits, int *__restrict__ err) {
   using namespace packed;
+  using S = Shape<4>;
+  constexpr int NC = S::NC, NCT = S::NCT, YB_BOXES = S::YB_BOXES, YROWS = S::YROWS;
+  constexpr int STAGE_Y = S::STAGE_Y, STAGE_W = S::STAGE_W;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [2]
   unsigned long long *empty = full + 2;                                         // [2]

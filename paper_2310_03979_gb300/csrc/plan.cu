@@ -173,13 +173,14 @@ __global__ void k_twiddles(int n, int log2n, T2 *tw) {
 // a = 0..kk/2, output kw = kw0 + r, r < R, iw < L (L = kw0 + R rounded up to
 // U) -- at ((a nch + iw / U) R + r) U + iw % U, nch = L / U: chunk-major, so
 // the R rows of one omega chunk are one contiguous span the pair sum fetches
-// with a single bulk copy.  W = c_k Ek[kk-2a] Ew[2iw-kw] for iw <= kw < nw,
-// else 0.  Centre rows are stored in full (the kernel halves them).  W is
+// with a single bulk copy.  W = Ek[kk-2a] Ew[2iw-kw] for iw <= kw < nw,
+// else 0: the envelope of the pair alone, a function of the lattice shape --
+// the spectrum's pair factor c_k multiplies each output at the end, so plans
+// of one shape can share a table and the lanes of a batch.  Centre rows are stored in full (the kernel halves them).  W is
 // real: the constant biphase is applied afterwards.  One CTA per tile, its
 // threads writing the tile's float4 in storage order.
 __global__ void __launch_bounds__(256) k_build_w(int t0, int nk, int nw, int ntw,
                                                  const long long *__restrict__ off,
-                                                 const float *__restrict__ ck,
                                                  const float *__restrict__ Ek,
                                                  const float *__restrict__ Ews, int ew_off,
                                                  float *__restrict__ W) {
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(256) k_build_w(int t0, int nk, int nw, int ntw
     const int v = f % V, r = (f / V) % kTileR, ac = f / (V * kTileR);
     const int a = ac / nch, c = ac - a * nch;
     const int kw = kw0 + r, iw = c * kTileU + 4 * v;
-    const float g = kw < nw ? ck[kk * nw + kw] * Ek[kk - 2 * a] : 0.0f;
+    const float g = kw < nw ? Ek[kk - 2 * a] : 0.0f;
     const float *e = Ews + ew_off - kw;
     float4 w;
     w.x = (iw + 0 <= kw) ? g * e[2 * (iw + 0)] : 0.0f;
@@ -677,11 +678,16 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   } else {
     const int nblk = cdiv(p->nw, kLinOut);
     const size_t smem = (size_t)3 * p->nw * sizeof(float);
+    const long long nl = (long long)p->nk * p->nw;
     SRM3_CUDA(cudaFuncSetAttribute(k_rec_linear, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem));
-    k_rec_linear<<<p->nk * nblk, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32, p->EwSq32,
-                                                       p->sb2, p->dkdw);
+    // the parts go to the FP32 search state, not yet in use (8 floats per point)
+    static_assert(kLinParts <= kPlanes, "linear-pass parts fit the FP32 search state");
+    k_rec_linear<<<p->nk * nblk * kLinParts, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32,
+                                                                   p->EwSq32, p->qm32);
+    k_rec_linear_sum<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm32, p->sb2, p->dkdw);
     SRM3_CUDA(cudaGetLastError());
+    SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kLinParts * nl * sizeof(float), st));
     k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
     SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double),
                               cudaMemcpyDeviceToHost, st));
@@ -864,33 +870,43 @@ static long long tile_entries(int kk, int tw) {
   return (long long)(kk / 2 + 1) * kTileR * L;
 }
 
-// W table of an FP32 plan (tile offsets and sampling tables ready), on st;
-// records its build time and size.
-int build_w_table(srm3_plan *p, cudaStream_t st) {
+// W table of an FP32 plan (tile offsets and the envelope tables ready),
+// enqueued on st (allocation, build, CUDA events around it); finish_w_table
+// waits for it and records its time and size.  The table depends on the
+// lattice shape only, so a plan build runs it beside the recursion.
+static int start_w_table(srm3_plan *p, cudaStream_t st) {
   if (p->W) return SRM3_OK;
   AllocOwner owner(p);
-  const double bytes = (double)p->table_entries * sizeof(float);
   cudaError_t e = dev_alloc(&p->W, (size_t)p->table_entries * sizeof(float), st);
   if (e != cudaSuccess) return cuda_fail(e, "dev_alloc(W table, st)");
-  cudaEvent_t ev[2];
-  SRM3_CUDA(cudaEventCreate(&ev[0]));
-  SRM3_CUDA(cudaEventCreate(&ev[1]));
-  cudaEventRecord(ev[0], st);
+  SRM3_CUDA(cudaEventCreate(&p->w_ev[0]));
+  SRM3_CUDA(cudaEventCreate(&p->w_ev[1]));
+  SRM3_CUDA(cudaEventRecord(p->w_ev[0], st));
   k_build_w<<<(p->row_hi - p->row_lo) * p->ntw, dim3(32, 8), 0, st>>>(
-      p->row_lo * p->ntw, p->nk, p->nw, p->ntw, p->tile_off,
-                                               (const float *)p->ck, (const float *)p->Ek,
-                                               (const float *)p->Ews, p->ew_off, p->W);
-  e = cudaGetLastError();
-  cudaEventRecord(ev[1], st);
-  if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      p->row_lo * p->ntw, p->nk, p->nw, p->ntw, p->tile_off, (const float *)p->Ek,
+      (const float *)p->Ews, p->ew_off, p->W);
+  SRM3_CUDA(cudaGetLastError());
+  SRM3_CUDA(cudaEventRecord(p->w_ev[1], st));
+  return SRM3_OK;
+}
+
+static int finish_w_table(srm3_plan *p) {
+  if (!p->w_ev[1]) return SRM3_OK;
+  cudaError_t e = cudaEventSynchronize(p->w_ev[1]);
   float tms = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&tms, ev[0], ev[1]);
-  cudaEventDestroy(ev[0]);
-  cudaEventDestroy(ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&tms, p->w_ev[0], p->w_ev[1]);
+  cudaEventDestroy(p->w_ev[0]);
+  cudaEventDestroy(p->w_ev[1]);
+  p->w_ev[0] = p->w_ev[1] = nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "W table build");
   p->t_table_ms = tms;
-  p->table_bytes = bytes;
+  p->table_bytes = (double)p->table_entries * sizeof(float);
   return SRM3_OK;
+}
+
+int build_w_table(srm3_plan *p, cudaStream_t st) {
+  int rc = start_w_table(p, st);
+  return rc ? rc : finish_w_table(p);
 }
 
 // Tiles of the FP32 pair sum.  A plan restricted to lattice rows [row_lo,
@@ -906,28 +922,36 @@ static int build_tiles(srm3_plan *p, cudaStream_t st, bool want_table, long long
     const bool mine = kk >= p->row_lo && kk < p->row_hi;
     off[t + 1] = off[t] + (mine ? tile_entries(kk, tw) : 0);
   }
-  // super-tiles of kWarpsPerCta tiles (FP32 pair sum), most expensive first
-  const int sw = kTileR * kWarpsPerCta;
-  const int nsw = cdiv(p->nw, sw);
-  p->nsuper = (p->row_hi - p->row_lo) * nsw;
-  std::vector<int2> sup(p->nsuper);
-  for (int i = 0; i < p->nsuper; ++i) sup[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
-  std::stable_sort(sup.begin(), sup.end(), [&](int2 a, int2 b) {
-    return (long long)(a.x / 2 + 1) * (a.y + sw) > (long long)(b.x / 2 + 1) * (b.y + sw);
-  });
-  SRM3_CUDA(dev_alloc(&p->super_order, sizeof(int2) * p->nsuper, st));
-  SRM3_CUDA(cudaMemcpyAsync(p->super_order, sup.data(), sizeof(int2) * p->nsuper,
-                            cudaMemcpyHostToDevice, st));
-  p->super_host = sup;
-  if (p->mixed) {  // the difference pass: (kk + 1) row pairs x ceil((nw - kws0) / 16) chunks
-    std::vector<int2> supd(p->nsuper);
-    for (int i = 0; i < p->nsuper; ++i) supd[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
+  // super-tiles of the FP32 pair sum, most expensive first, for both tile
+  // shapes (32 and 16 outputs wide)
+  int nsw = 0;
+  for (int v = 0; v < 2; ++v) {
+    const int sw = kTileR * (v == 0 ? 4 : 2);
+    nsw = cdiv(p->nw, sw);
+    p->nsuper[v] = (p->row_hi - p->row_lo) * nsw;
+    std::vector<int2> sup(p->nsuper[v]);
+    for (int i = 0; i < p->nsuper[v]; ++i)
+      sup[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
+    std::stable_sort(sup.begin(), sup.end(), [&](int2 a, int2 b) {
+      return (long long)(a.x / 2 + 1) * (a.y + sw) > (long long)(b.x / 2 + 1) * (b.y + sw);
+    });
+    SRM3_CUDA(dev_alloc(&p->super_order[v], sizeof(int2) * p->nsuper[v], st));
+    SRM3_CUDA(cudaMemcpyAsync(p->super_order[v], sup.data(), sizeof(int2) * p->nsuper[v],
+                              cudaMemcpyHostToDevice, st));
+    p->super_host[v] = sup;
+  }
+  if (p->mixed) {  // the difference pass (32 wide): (kk + 1) row pairs x ceil((nw - kws0) / 16) chunks
+    const int sw = kTileR * 4;
+    nsw = cdiv(p->nw, sw);
+    const int n = (p->row_hi - p->row_lo) * nsw;
+    std::vector<int2> supd(n);
+    for (int i = 0; i < n; ++i) supd[i] = make_int2(p->row_lo + i / nsw, (i % nsw) * sw);
     auto cost = [&](int2 t) { return (long long)(t.x + 1) * ((p->nw - t.y + 15) / 16); };
     std::stable_sort(supd.begin(), supd.end(),
                      [&](int2 a, int2 b) { return cost(a) > cost(b); });
-    p->nsuper_d = p->nsuper;
-    SRM3_CUDA(dev_alloc(&p->super_order_d, sizeof(int2) * p->nsuper, st));
-    SRM3_CUDA(cudaMemcpyAsync(p->super_order_d, supd.data(), sizeof(int2) * p->nsuper,
+    p->nsuper_d = n;
+    SRM3_CUDA(dev_alloc(&p->super_order_d, sizeof(int2) * n, st));
+    SRM3_CUDA(cudaMemcpyAsync(p->super_order_d, supd.data(), sizeof(int2) * n,
                               cudaMemcpyHostToDevice, st));
   }
   *table_entries = off[p->ntiles];
@@ -1016,8 +1040,54 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
   }
   SRM3_CUDA(cudaGetLastError());
 
+  // shape tables (envelope factors, twiddles), tiles, the storage choice
+  // and the W table -- all functions of the lattice shape, ready before eps
+  // is known: the W table (the O(N^2) FP32 pair sum only; separable
+  // envelopes sample through the FFT self-convolution) is written on a
+  // stream of its own while the recursion runs
+  int rc = prepare_shape_tables(p, st);
+  if (rc) return rc;
+  cudaStream_t wst = nullptr;
+  struct WStreamGuard {
+    cudaStream_t *s;
+    ~WStreamGuard() {
+      if (*s) cudaStreamDestroy(*s);
+    }
+  } wguard{&wst};
+  if (p->precision == SRM3_FP32 && !p->sep) {
+    long long entries = 0;
+    bool maybe_table = p->storage != SRM3_STORAGE_RECOMPUTE;
+    rc = build_tiles(p, st, maybe_table, &entries);
+    if (rc) return rc;
+    p->table_entries = entries;
+    const double bytes = (double)entries * sizeof(float);
+    int tuned_nc = 4;
+    const int tuned = tune_cache_lookup(nk, nw, &tuned_nc);
+    if (tuned >= 0) p->ps_nc = tuned_nc;  // the tuned tile (results do not depend on it)
+    if (p->storage == SRM3_STORAGE_TUNED)  // the autotuner's storage for this lattice
+      p->storage = tuned >= 0 ? tuned : SRM3_STORAGE_AUTO;
+    if (p->storage == SRM3_STORAGE_AUTO) {
+      p->storage = bytes <= p->table_budget ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
+    }
+    if (p->mixed) p->storage = SRM3_STORAGE_RECOMPUTE;  // the table holds sum pairs only
+    if (p->storage == SRM3_STORAGE_TABLE) {
+      cudaEvent_t ready;
+      SRM3_CUDA(cudaStreamCreateWithFlags(&wst, cudaStreamNonBlocking));
+      SRM3_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+      SRM3_CUDA(cudaEventRecord(ready, st));  // envelope tables and tile offsets written
+      SRM3_CUDA(cudaStreamWaitEvent(wst, ready, 0));
+      cudaEventDestroy(ready);
+      if ((rc = start_w_table(p, wst))) return rc;
+    } else {
+      p->table_bytes = 0.0;
+    }
+  } else {
+    p->storage = SRM3_STORAGE_RECOMPUTE;
+    p->table_bytes = 0.0;
+  }
+
   // a2: recursion, one graph node per anti-diagonal level
-  int rc = setup_recursion(p, st);
+  rc = setup_recursion(p, st);
   if (rc) return rc;
   if (p->mixed) {
     SRM3_CUDA(dev_alloc(&p->Dsum, nl * sizeof(double), st));
@@ -1078,47 +1148,27 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
 
   rc = prepare_sampling_tables(p, st);
   if (rc) return rc;
-
-  // tiles, storage choice and the W table (the O(N^2) FP32 pair sum only;
-  // separable envelopes sample through the FFT self-convolution)
-  if (p->precision == SRM3_FP32 && !p->sep) {
-    long long entries = 0;
-    bool maybe_table = p->storage != SRM3_STORAGE_RECOMPUTE;
-    rc = build_tiles(p, st, maybe_table, &entries);
-    if (rc) return rc;
-    p->table_entries = entries;
-    const double bytes = (double)entries * sizeof(float);
-    if (p->storage == SRM3_STORAGE_TUNED) {  // the autotuner's choice for this lattice
-      const int c = tune_cache_lookup(nk, nw);
-      p->storage = c >= 0 ? c : SRM3_STORAGE_AUTO;
-    }
-    if (p->storage == SRM3_STORAGE_AUTO) {
-      p->storage = bytes <= p->table_budget ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
-    }
-    if (p->mixed) p->storage = SRM3_STORAGE_RECOMPUTE;  // the table holds sum pairs only
-    if (p->storage == SRM3_STORAGE_TABLE) {
-      if ((rc = build_w_table(p, st))) return rc;
-    } else {
-      p->table_bytes = 0.0;
-    }
-  } else {
-    p->storage = SRM3_STORAGE_RECOMPUTE;
-    p->table_bytes = 0.0;
+  // the W table built beside the recursion (its own stream) is joined here
+  if (p->w_ev[1]) {
+    SRM3_CUDA(cudaStreamWaitEvent(st, p->w_ev[1], 0));
+    if ((rc = finish_w_table(p))) return rc;
   }
   SRM3_CUDA(cudaStreamSynchronize(st));
   return SRM3_OK;
 }
 
-int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
+// The tables of the lattice shape: envelope factors by kappa and by signed
+// omega offset (and of the signed difference for mixed plans), FFT
+// twiddles, the self-convolution grid of separable plans.
+int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
   const int nk = p->nk, nw = p->nw;
-  const size_t nl = (size_t)nk * nw;
   const bool f32 = p->precision == SRM3_FP32;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   // signed envelope table Ews[ew_off + d] (terms outside the lattice meet
   // zero y, whatever their weight).  ew_off is
   // 3 mod 4, which puts the FP32 pair sum's 64-entry chunk windows of the
-  // FP32 table (first d = 2 i0 - kws0 - 31, 1 mod 4) on 16-byte boundaries;
-  // the table reaches d = nw + 127, past the last window.
+  // FP32 table (first d = 2 i0 - kws0 - (SW - 1), 1 mod 4) on 16-byte
+  // boundaries; the table reaches d = 2 nw + 127, past the last window.
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
   p->ew_len = p->ew_off + 2 * nw + 128;  // difference pairs reach d = 2 nw - 2
   p->nfft = std::max(p->nx, p->nt);
@@ -1132,16 +1182,10 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     p->log2ntwc = std::max(p->log2cNk, p->log2cNw);
   }
   p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
-  SRM3_CUDA(dev_alloc(&p->sqq, nl * es, st));
-  SRM3_CUDA(dev_alloc(&p->Pk, nl * es, st));
-  SRM3_CUDA(dev_alloc(&p->ck, nl * es, st));
   SRM3_CUDA(dev_alloc(&p->Ek, nk * es, st));
   SRM3_CUDA(dev_alloc(&p->Ews, p->ew_len * es, st));
   SRM3_CUDA(dev_alloc(&p->tw, p->nfft * 2 * es, st));
   if (f32) {
-    k_sampling_tables<float><<<cdiv(nl, 256), 256, 0, st>>>(
-        (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (float *)p->sqq, (float *)p->Pk,
-        (float *)p->ck);
     k_env<float><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (float *)p->Ek);
     k_env<float><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off, p->sigma_g * nw,
                                                       (float *)p->Ews);
@@ -1162,9 +1206,6 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
                                                                         (float2 *)p->tw_conv);
     }
   } else {
-    k_sampling_tables<double><<<cdiv(nl, 256), 256, 0, st>>>(
-        (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (double *)p->sqq, (double *)p->Pk,
-        (double *)p->ck);
     k_env<double><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (double *)p->Ek);
     k_env<double><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off,
                                                        p->sigma_g * nw, (double *)p->Ews);
@@ -1178,7 +1219,28 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
     }
   }
   SRM3_CUDA(cudaGetLastError());
-  SRM3_CUDA(cudaStreamSynchronize(st));
+  return SRM3_OK;
+}
+
+// The tables of the spectrum at the plan's eps: sqrt(q) masked by S > 0, the
+// pure factor 2 sqrt(dk dw S)(1 - sum_b2) and the pair factor 2 eps dk dw
+// sqrt(S).
+int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
+  const size_t nl = (size_t)p->nk * p->nw;
+  const bool f32 = p->precision == SRM3_FP32;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  SRM3_CUDA(dev_alloc(&p->sqq, nl * es, st));
+  SRM3_CUDA(dev_alloc(&p->Pk, nl * es, st));
+  SRM3_CUDA(dev_alloc(&p->ck, nl * es, st));
+  if (f32)
+    k_sampling_tables<float><<<cdiv(nl, 256), 256, 0, st>>>(
+        (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (float *)p->sqq, (float *)p->Pk,
+        (float *)p->ck);
+  else
+    k_sampling_tables<double><<<cdiv(nl, 256), 256, 0, st>>>(
+        (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (double *)p->sqq, (double *)p->Pk,
+        (double *)p->ck);
+  SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
 
@@ -1235,12 +1297,15 @@ void free_plan(srm3_plan *p) {
     cudaEventDestroy(r.b);
   }
   for (auto e : p->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t &e : p->w_ev)  // a W build the plan's failure left unjoined
+    if (e) cudaEventDestroy(e);
   void *dev[] = {p->S,      p->qm,     p->sb2,       p->EkSq,       p->EwSq,   p->scal,
                  p->err,    p->sqq,    p->Pk,        p->ck,         p->Ek,     p->Ews,
                  p->tw,     p->tile_off, p->W,       p->y,      p->y0,
                  p->C,      p->H,      p->qm32,      p->EkSq32,     p->EwSq32, p->rec_items,
                  p->G2,     p->G2_32,  p->qm3,
-                 p->rec_partial, p->super_order, p->rec_lev_off, p->rec_bar, p->rec_max,
+                 p->rec_partial, p->super_order[0], p->super_order[1], p->rec_lev_off,
+                 p->rec_bar, p->rec_max,
                  p->rec_pairs, p->rec_pair_off,
                  p->ps_err,  p->env_e,    p->env_e2,     p->env_e32, p->qh,
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
@@ -1401,6 +1466,7 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->storage = plan->storage;
   info->precision = plan->precision;
   info->tile_r = kTileR;
+  info->tile_width = kTileR * plan->ps_nc;
   info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
   info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
   info->diff_pairs = plan->diffpairs;

@@ -742,29 +742,33 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
 
 // Linear pass: L_k = dk dw sum_{Pi(k)} g^2 [S_i > 0][S_j > 0] (q == 1), the
 // small-eps slope of sum_b2 used to bracket eps.  No level dependencies.  A
-// CTA takes lattice row kk and kLinOut consecutive omega outputs, one
-// thread per output; per row pair (a, b = kk - a) it stages the S > 0 masks
-// of rows a and b in shared memory, and every thread sums
+// CTA takes lattice row kk, kLinOut consecutive omega outputs (one thread
+// each) and one part of the row's row pairs (a = part, part + nparts, ...):
+// per row pair (a, b = kk - a) it stages the S > 0 masks of rows a and b in
+// shared memory, and every thread sums
 //   R(kw) = sum_iw EwSq[|2 iw - kw|] m_a[iw] m_b[kw - iw]
 // over iw <= kw (iw <= kw/2 on the centre row, i = 0 skipped), weighted by
-// EkSq[kk - 2a].  FP32 terms (only the scale of eps is taken from it);
-// written to sb2 plane 0.  CTAs go in order of decreasing kk (most rows
-// first).
+// EkSq[kk - 2a], into part[part][k].  Splitting a row's row pairs over
+// kLinParts CTAs keeps the long rows (kk/2 + 1 row pairs) off the critical
+// path; k_rec_linear_sum adds the parts in a fixed order.  FP32 terms (only
+// the scale of eps is taken from it).  CTAs go in order of decreasing kk.
 constexpr int kLinOut = 128;
+constexpr int kLinParts = 8;
 
 __global__ void __launch_bounds__(kLinOut) k_rec_linear(int nk, int nw, const double *__restrict__ S,
                                                         const float *__restrict__ EkSq,
                                                         const float *__restrict__ EwSq,
-                                                        double *__restrict__ sb2, double dkdw) {
+                                                        float *__restrict__ part) {
   extern __shared__ float lin_smem[];
   float *ma = lin_smem, *mb = lin_smem + nw, *ew = lin_smem + 2 * nw;  // [nw] each
   const int nblk = (nw + kLinOut - 1) / kLinOut;
-  const int kk = nk - 1 - (int)(blockIdx.x / nblk);
-  const int kw = (int)(blockIdx.x % nblk) * kLinOut + threadIdx.x;
-  const int kwmax = min(nw, (int)(blockIdx.x % nblk) * kLinOut + kLinOut);  // outputs < kwmax
+  const int cta = (int)(blockIdx.x / kLinParts), prt = (int)(blockIdx.x % kLinParts);
+  const int kk = nk - 1 - cta / nblk;
+  const int kw = (cta % nblk) * kLinOut + threadIdx.x;
+  const int kwmax = min(nw, (cta % nblk) * kLinOut + kLinOut);  // outputs < kwmax
   for (int i = threadIdx.x; i < nw; i += blockDim.x) ew[i] = EwSq[i];
   float acc = 0.f;
-  for (int a = 0; a <= kk / 2; ++a) {
+  for (int a = prt; a <= kk / 2; a += kLinParts) {
     const int b = kk - a;
     __syncthreads();
     for (int i = threadIdx.x; i < kwmax; i += blockDim.x) {
@@ -782,10 +786,17 @@ __global__ void __launch_bounds__(kLinOut) k_rec_linear(int nk, int nw, const do
       acc = fmaf(EkSq[kk - 2 * a], r, acc);
     }
   }
-  if (kw < nw) {
-    const size_t k = (size_t)kk * nw + kw;
-    sb2[k] = S[k] > 0.0 ? dkdw * (double)acc : 0.0;
-  }
+  if (kw < nw) part[(size_t)prt * nk * nw + (size_t)kk * nw + kw] = acc;
+}
+
+__global__ void k_rec_linear_sum(long long n, const double *__restrict__ S,
+                                 const float *__restrict__ part, double *__restrict__ sb2,
+                                 double dkdw) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  float t = 0.f;
+  for (int j = 0; j < kLinParts; ++j) t += part[(size_t)j * n + k];
+  sb2[k] = S[k] > 0.0 ? dkdw * (double)t : 0.0;
 }
 
 // Difference-pair sums of the mixed-sign interactions for every point at the

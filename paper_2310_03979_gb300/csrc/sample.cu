@@ -259,7 +259,7 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
   d->Pk = (const float *)p->Pk;
   d->ck = (const float *)p->ck;
   d->C = (float2 *)C_out;
-  d->order = p->super_order;
+  d->order = p->super_order[tile_index(p->ps_nc)];
   d->nk = p->nk;
   d->nw = p->nw;
   d->SS = 2 * n;
@@ -276,36 +276,49 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
 }
 
 // One FP32 pair-sum launch on stream st: plan d0 alone (descs == NULL) or the
-// batch descs/units; the grid is the resident CTA count (persistent kernel).
-// nunits == 0 only prepares (attributes, resident CTA count).
-int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
-                       const int4 *units, int nunits, int max_ctas, bool mixed) {
-  const size_t smem = pairsum_f32p_smem();
-  const void *kf[2] = {(const void *)k_pairsum_f32p<false>, (const void *)k_pairsum_f32p<true>};
+// batch descs/units, with the tile of nc compute warps (4 or 2); the grid is
+// the resident CTA count (persistent kernel).  nunits == 0 only prepares
+// (attributes, resident CTA count).
+template <int NC>
+static int launch_pairsum_f32_nc(srm3_plan *p, cudaStream_t st, const PsDesc &d0,
+                                 const PsDesc *descs, const int4 *units, int nunits, int max_ctas,
+                                 bool mixed) {
+  const size_t smem = pairsum_f32p_smem<NC>();
+  constexpr int NT = packed::Shape<NC>::NT;
+  const void *kf[2] = {(const void *)k_pairsum_f32p<false, NC>,
+                       (const void *)k_pairsum_f32p<true, NC>};
   for (const void *f : kf) {
     SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   }
-  if (p->ps_ctas == 0) {  // resident CTAs of the persistent kernel (both forms)
+  int &ctas = p->ps_ctas[tile_index(NC)];
+  if (ctas == 0) {  // resident CTAs of the persistent kernel (both forms)
     int nsm = 0, per_sm = 1 << 30;
     SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
     for (const void *f : kf) {
       int n = 0;
-      SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, packed::NT, smem));
+      SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, NT, smem));
       per_sm = std::min(per_sm, n);
     }
     if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "FP32 pair sum does not fit on an SM");
-    p->ps_ctas = nsm * per_sm;
+    ctas = nsm * per_sm;
   }
-  int grid = std::min(nunits, p->ps_ctas);
+  int grid = std::min(nunits, ctas);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (grid == 0) return SRM3_OK;
   if (mixed)
-    k_pairsum_f32p<true><<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
+    k_pairsum_f32p<true, NC><<<grid, NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
   else
-    k_pairsum_f32p<false><<<grid, packed::NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
+    k_pairsum_f32p<false, NC><<<grid, NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
+}
+
+int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
+                       const int4 *units, int nunits, int max_ctas, bool mixed, int nc) {
+  if (nc == 2)
+    return launch_pairsum_f32_nc<2>(p, st, d0, descs, units, nunits, max_ctas, mixed);
+  return launch_pairsum_f32_nc<4>(p, st, d0, descs, units, nunits, max_ctas, mixed);
 }
 
 // The difference-pair launch of a mixed FP32 plan over n samples whose rows
@@ -343,20 +356,21 @@ static int launch_pairsum_f32_diff(srm3_plan *p, cudaStream_t st, int n, void *C
   d.G = sp / (2 * packed::LANES);
   d.cb = (float)std::cos(p->beta);
   d.sb = (float)std::sin(p->beta);
-  const size_t smem = pairsum_f32p_smem();
+  const size_t smem = pairsum_f32p_smem<4>();
   SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32d, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   SRM3_CUDA(cudaFuncSetAttribute(k_pairsum_f32d, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  100));
   int nsm = 0, per_sm = 0;
   SRM3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p->device));
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairsum_f32d, packed::NT,
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairsum_f32d,
+                                                          packed::Shape<4>::NT,
                                                           smem));
   if (per_sm < 1) return fail(SRM3_ERR_NOT_SUPPORTED, "difference pair sum does not fit on an SM");
   const int nunits = p->nsuper_d * d.G;
   const int grid = std::min(nunits, nsm * per_sm);
   if (grid == 0) return SRM3_OK;
-  k_pairsum_f32d<<<grid, packed::NT, smem, st>>>(d, nunits, p->ps_err);
+  k_pairsum_f32d<<<grid, packed::Shape<4>::NT, smem, st>>>(d, nunits, p->ps_err);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
 }
@@ -431,7 +445,8 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
     PsDesc d;
     int rc = fill_pairsum_desc(p, n, C_out, &d);
     if (rc) return rc;
-    rc = launch_pairsum_f32(p, p->stream, d, nullptr, nullptr, p->nsuper * d.G, 0, d.half != 0);
+    rc = launch_pairsum_f32(p, p->stream, d, nullptr, nullptr,
+                            p->nsuper[tile_index(p->ps_nc)] * d.G, 0, d.half != 0, p->ps_nc);
     if (rc || !p->mixed) return rc;
     return launch_pairsum_f32_diff(p, p->stream, n, C_out);
   }
@@ -548,19 +563,21 @@ static size_t elem1(const srm3_plan *p) {
   return p->precision == SRM3_FP32 ? sizeof(float) : sizeof(double);
 }
 
-// Autotuner choices per lattice shape, process-wide.
+// Autotuner choices per lattice shape, process-wide: (storage, compute warps).
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int>, int> g_tune;
+static std::map<std::pair<int, int>, std::pair<int, int>> g_tune;
 
-int tune_cache_lookup(int nk, int nw) {
+int tune_cache_lookup(int nk, int nw, int *nc) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find({nk, nw});
-  return it == g_tune.end() ? -1 : it->second;
+  if (it == g_tune.end()) return -1;
+  if (nc) *nc = it->second.second;
+  return it->second.first;
 }
 
-void tune_cache_store(int nk, int nw, int storage) {
+void tune_cache_store(int nk, int nw, int storage, int nc) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[{nk, nw}] = storage;
+  g_tune[{nk, nw}] = {storage, nc};
 }
 
 }  // namespace srm3
@@ -589,9 +606,13 @@ struct srm3_batch {
   uint64_t *dseeds = nullptr;     // device seeds the phase kernels read
   std::vector<uint64_t> hseeds;   // pageable staging copy (read before run returns)
   srm3::PsDesc *ddesc = nullptr;  // per group and per FP32 table plan
-  int4 *dunits = nullptr;         // work units of all of them, by decreasing cost
-  int nunits = 0;
-  bool mixed = false;             // some descriptor takes the half-group mode
+  // work units of all of them, by decreasing cost, per tile shape (index 0:
+  // 32 wide, 1: 16 wide -- each descriptor's plan's tile), one after the
+  // other in dunits: one persistent launch per tile shape present
+  int4 *dunits = nullptr;
+  int nunits = 0;                 // both shapes
+  int nunits_v[2] = {0, 0};
+  bool mixed_v[2] = {false, false};  // some descriptor of the shape takes the half-group mode
   srm3_plan *lead = nullptr;      // first FP32 plan: CTA count and error word of the launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -629,9 +650,11 @@ static int batch_launch(srm3_batch *b) {
     // in a capture the events must be external nodes of the graph
     const unsigned evf = b->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[0], b->stream, evf));
-    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, b->nunits,
-                                 b->max_ctas, b->mixed)))
-      return rc;
+    for (int v = 0, off = 0; v < 2; off += b->nunits_v[v], ++v)
+      if (b->nunits_v[v] > 0 &&
+          (rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits + off,
+                                   b->nunits_v[v], b->max_ctas, b->mixed_v[v], v == 0 ? 4 : 2)))
+        return rc;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
   for (size_t i = 0; i < b->plans.size(); ++i) {
@@ -804,6 +827,15 @@ SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
   return SRM3_OK;
 }
 
+SRM3_API int srm3_set_tile_width(srm3_plan *plan, int width) {
+  if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
+  if (width != 16 && width != 32) return fail(SRM3_ERR_INVALID_ARG, "width must be 16 or 32");
+  if (plan->precision != SRM3_FP32 || plan->sep)
+    return fail(SRM3_ERR_NOT_SUPPORTED, "tile shapes apply to FP32 plans of the O(N^2) pair sum");
+  plan->ps_nc = width / kTileR;
+  return SRM3_OK;
+}
+
 SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   if (!plan || !res) return fail(SRM3_ERR_INVALID_ARG, "plan and result must be non-NULL");
   if (n < 1 || n > kMaxChunk) return fail(SRM3_ERR_INVALID_ARG, "n must be in 1..128");
@@ -825,19 +857,21 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
   cudaEvent_t ev[2];
   SRM3_CUDA(cudaEventCreate(&ev[0]));
   SRM3_CUDA(cudaEventCreate(&ev[1]));
-  auto time_one = [&](int storage, double *ms) -> int {
+  auto time_one = [&](int storage, int nc, double *ms) -> int {
     plan->storage = storage;
+    plan->ps_nc = nc;
     PsDesc d;
     int r = fill_pairsum_desc(plan, n, plan->C, &d);
     if (r) return r;
-    const int nunits = plan->nsuper * d.G;
-    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0, d.half != 0)))
+    const int nunits = plan->nsuper[tile_index(nc)] * d.G;
+    if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0, d.half != 0,
+                                nc)))
       return r;
     float best = 1e30f;
     for (int rep = 0; rep < 3; ++rep) {
       SRM3_CUDA(cudaEventRecord(ev[0], plan->stream));
       if ((r = launch_pairsum_f32(plan, plan->stream, d, nullptr, nullptr, nunits, 0,
-                                  d.half != 0)))
+                                  d.half != 0, nc)))
         return r;
       SRM3_CUDA(cudaEventRecord(ev[1], plan->stream));
       SRM3_CUDA(cudaEventSynchronize(ev[1]));
@@ -848,26 +882,49 @@ SRM3_API int srm3_autotune(srm3_plan *plan, int n, srm3_tune_result *res) {
     *ms = best;
     return SRM3_OK;
   };
-  double t_tab = -1.0, t_rec = -1.0;
-  if (plan->W) rc = time_one(SRM3_STORAGE_TABLE, &t_tab);
-  if (!rc) rc = time_one(SRM3_STORAGE_RECOMPUTE, &t_rec);
+  // every (storage, tile) the plan can take: the stored table when it exists,
+  // W recomputed; 32- and 16-wide tiles
+  double t[2][2] = {{-1.0, -1.0}, {-1.0, -1.0}};  // [storage: table, recompute][tile]
+  for (int v = 0; v < 2 && !rc; ++v) {
+    const int nc = v == 0 ? 4 : 2;
+    if (plan->W) rc = time_one(SRM3_STORAGE_TABLE, nc, &t[0][v]);
+    if (!rc) rc = time_one(SRM3_STORAGE_RECOMPUTE, nc, &t[1][v]);
+  }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (rc) return rc;
-  const int choice =
-      (t_tab >= 0.0 && t_tab < t_rec) ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
+  // the default (W recomputed, 32 wide) unless another form is faster by at
+  // least kTuneMargin: single-launch timings jitter by a few per cent, and a
+  // batch runs one launch per tile width and groups plans by storage
+  constexpr double kTuneMargin = 0.03;
+  int bs = 1, bv = 0;
+  for (int st = 0; st < 2; ++st)
+    for (int v = 0; v < 2; ++v)
+      if (t[st][v] >= 0.0 && t[st][v] < t[bs][bv] * (1.0 - kTuneMargin)) {
+        bs = st;
+        bv = v;
+      }
+  const int choice = bs == 0 ? SRM3_STORAGE_TABLE : SRM3_STORAGE_RECOMPUTE;
+  const int nc = bv == 0 ? 4 : 2;
   plan->storage = choice;
+  plan->ps_nc = nc;
   if (choice == SRM3_STORAGE_RECOMPUTE && plan->W) {
     SRM3_CUDA(cudaStreamSynchronize(plan->stream));
     SRM3_CUDA(dev_free(plan->W, plan->stream));
     plan->W = nullptr;
     plan->table_bytes = 0.0;
   }
-  tune_cache_store(plan->nk, plan->nw, choice);
-  res->table_ms = t_tab;
-  res->recompute_ms = t_rec;
+  tune_cache_store(plan->nk, plan->nw, choice, nc);
+  res->table_ms = std::min(t[0][0] < 0 ? 1e30 : t[0][0], t[0][1] < 0 ? 1e30 : t[0][1]);
+  if (res->table_ms >= 1e30) res->table_ms = -1.0;
+  res->recompute_ms = std::min(t[1][0], t[1][1]);
   res->storage = choice;
   res->samples = n;
+  res->tile_width = kTileR * nc;
+  res->table_ms_w32 = t[0][0];
+  res->table_ms_w16 = t[0][1];
+  res->recompute_ms_w32 = t[1][0];
+  res->recompute_ms_w16 = t[1][1];
   SRM3_CUDA(cudaStreamSynchronize(plan->stream));
   return check_pairsum_error(plan);
 }
@@ -908,16 +965,30 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     b->own_stream = true;
   }
   std::vector<PsDesc> descs;
-  std::vector<std::pair<long long, int4>> units;
+  std::vector<std::pair<long long, int4>> units[2];  // per tile shape
+  // one tile width for the whole batch -- the width of the plans that carry
+  // most of its pair-terms (results do not depend on it): one persistent
+  // launch, no tail of a second
+  long long terms_v[2] = {0, 0};
+  for (int i = 0; i < m; ++i)
+    if (plans[i]->precision == SRM3_FP32 && !plans[i]->sep)
+      terms_v[tile_index(plans[i]->ps_nc)] += (plans[i]->pairs + plans[i]->diffpairs) * counts[i];
+  const int batch_nc = terms_v[1] > terms_v[0] ? 2 : 4;
   auto add_units = [&](srm3_plan *p, int j, const PsDesc &d) {
-    for (const int2 &t : p->super_host) {
-      const long long cost = ps_nitems(t.x, t.y, d.half);
-      for (int g = 0; g < d.G; ++g) units.push_back({cost, make_int4(j, t.x, t.y, g)});
+    const int v = tile_index(batch_nc);
+    b->mixed_v[v] = b->mixed_v[v] || d.half != 0;
+    for (const int2 &t : p->super_host[v]) {
+      const long long cost = ps_nitems(t.x, t.y, d.half, kTileR * batch_nc);
+      for (int g = 0; g < d.G; ++g) units[v].push_back({cost, make_int4(j, t.x, t.y, g)});
     }
   };
+  // plans of one shape group share the lead plan's weights (envelope windows
+  // or its W table of pair envelopes) and its tile; each sample keeps its
+  // own spectrum's factors
   auto same_shape = [](const srm3_plan *a, const srm3_plan *c) {
     return a->nk == c->nk && a->nw == c->nw && a->nx == c->nx && a->nt == c->nt &&
-           a->ku == c->ku && a->wu == c->wu && a->sigma_g == c->sigma_g && a->beta == c->beta;
+           a->ku == c->ku && a->wu == c->wu && a->sigma_g == c->sigma_g && a->beta == c->beta &&
+           a->storage == c->storage;
   };
   for (int i = 0; i < m; ++i) {
     srm3_plan *p = plans[i];
@@ -928,8 +999,8 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     b->total += counts[i];
     b->pair_terms += 2LL * (p->pairs + p->diffpairs) * counts[i];
     int gi = -1;
-    if (p->precision == SRM3_FP32 && p->storage == SRM3_STORAGE_RECOMPUTE && !p->sep &&
-        !p->mixed) {
+    if (p->precision == SRM3_FP32 && !p->sep && !p->mixed &&
+        (p->storage == SRM3_STORAGE_RECOMPUTE || (p->storage == SRM3_STORAGE_TABLE && p->W))) {
       for (size_t g = 0; g < b->groups.size() && gi < 0; ++g)
         if (same_shape(b->plans[b->groups[g].members[0]], p)) gi = (int)g;
       if (gi < 0) {
@@ -985,7 +1056,6 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     d.pk_of = g.pk_of;
     d.ck_of = g.ck_of;
     const int j = (int)descs.size();
-    b->mixed = b->mixed || d.half != 0;
     descs.push_back(d);
     add_units(p, j, d);
   }
@@ -995,24 +1065,26 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     PsDesc d;
     if ((rc = fill_pairsum_desc(p, counts[i], p->C, &d))) return bail(rc);
     const int j = (int)descs.size();
-    b->mixed = b->mixed || d.half != 0;
     descs.push_back(d);
     add_units(p, j, d);
   }
-  std::stable_sort(units.begin(), units.end(),
-                   [](const std::pair<long long, int4> &x, const std::pair<long long, int4> &y) {
-                     return x.first > y.first;
-                   });
-  b->nunits = (int)units.size();
+  std::vector<int4> u;
+  for (int v = 0; v < 2; ++v) {
+    std::stable_sort(units[v].begin(), units[v].end(),
+                     [](const std::pair<long long, int4> &x, const std::pair<long long, int4> &y) {
+                       return x.first > y.first;
+                     });
+    b->nunits_v[v] = (int)units[v].size();
+    for (const auto &un : units[v]) u.push_back(un.second);
+  }
+  b->nunits = (int)u.size();
   if (!descs.empty()) {
-    b->dev_bytes += (long long)(sizeof(PsDesc) * descs.size() + sizeof(int4) * units.size());
+    b->dev_bytes += (long long)(sizeof(PsDesc) * descs.size() + sizeof(int4) * u.size());
     e = cudaMallocAsync(&b->ddesc, sizeof(PsDesc) * descs.size(), b->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch descriptors)"));
     e = cudaMemcpyAsync(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(),
                         cudaMemcpyHostToDevice, b->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemcpyAsync(batch descriptors)"));
-    std::vector<int4> u(units.size());
-    for (size_t k = 0; k < units.size(); ++k) u[k] = units[k].second;
     e = cudaMallocAsync(&b->dunits, sizeof(int4) * u.size(), b->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch units)"));
     e = cudaMemcpyAsync(b->dunits, u.data(), sizeof(int4) * u.size(), cudaMemcpyHostToDevice,
@@ -1022,8 +1094,10 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     // kernel attributes and resident CTA count, set before any capture
     PsDesc none;
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
-    if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0, b->mixed)))
-      return bail(rc);
+    for (int v = 0; v < 2; ++v)
+      if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0,
+                                   b->mixed_v[v], v == 0 ? 4 : 2)))
+        return bail(rc);
   }
   b->dev_bytes += (long long)(sizeof(uint64_t) * b->total);
   e = cudaMallocAsync(&b->dseeds, sizeof(uint64_t) * b->total, b->stream);

@@ -162,13 +162,18 @@ struct srm3_plan {
   // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
   int ntw = 0, ntiles = 0;
   long long table_entries = 0;    // floats of the W table (built or not)
-  int ps_ctas = 0;                // resident CTAs of the persistent FP32 pair sum
+  int ps_ctas[2] = {0, 0};        // resident CTAs of the persistent FP32 pair sum, per tile shape
+  int ps_nc = 4;                  // compute warps of the FP32 pair-sum tile: 4 (32 wide) or 2 (16)
   int *ps_err = nullptr;          // its error word (bounded waits that ran out)
-  int nsuper = 0;
-  int2 *super_order = nullptr;    // 32-wide super-tiles of the FP32 pair sum
-  std::vector<int2> super_host;   // the same order on the host (batch unit lists)
+  // super-tiles of the FP32 pair sum by decreasing cost, per tile shape
+  // (index 0: 32 wide, 4 compute warps; 1: 16 wide, 2 compute warps), on the
+  // device and on the host (batch unit lists)
+  int nsuper[2] = {0, 0};
+  int2 *super_order[2] = {nullptr, nullptr};
+  std::vector<int2> super_host[2];
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
-  float *W = nullptr;             // W table (STORAGE_TABLE)
+  float *W = nullptr;             // W table (STORAGE_TABLE): the pair envelopes of the shape
+  cudaEvent_t w_ev[2] = {nullptr, nullptr};  // around its build while it runs
 
   // sampling workspace
   int ws_chunk = 0;
@@ -225,6 +230,7 @@ int run_transform(srm3_plan *p, const void *C, int n, void *out);
 // rows in H (n * nk * nt complex values in the plan's precision), which the
 // caller supplies: the plan workspace, a batch buffer or fixed scratch.
 int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out, void *H);
+int prepare_shape_tables(srm3_plan *p, cudaStream_t st);
 int prepare_sampling_tables(srm3_plan *p, cudaStream_t st);
 int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);
 int stage_end(srm3_plan *p, int rec);
@@ -232,9 +238,12 @@ int collect_timings(srm3_plan *p);
 int check_pairsum_error(srm3_plan *p);
 int sspad_for(int chunk);
 int build_w_table(srm3_plan *p, cudaStream_t st);
-// autotuner choices per lattice shape (process-wide): storage or -1
-int tune_cache_lookup(int nk, int nw);
-void tune_cache_store(int nk, int nw, int storage);
+// autotuner choices per lattice shape (process-wide): storage (or -1 when
+// the shape was never tuned) and the pair-sum tile's compute warps
+int tune_cache_lookup(int nk, int nw, int *nc = nullptr);
+void tune_cache_store(int nk, int nw, int storage, int nc);
+// tile-shape index of nc compute warps (4 -> 0, 2 -> 1)
+inline int tile_index(int nc) { return nc == 4 ? 0 : 1; }
 }  // namespace srm3
 
 static inline int ilog2_exact(int v) {

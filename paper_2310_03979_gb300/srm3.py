@@ -36,7 +36,7 @@ EXPORTED = [
     "srm3_plan_moments", "srm3_selftest_timeouts",
     "srm3_phase_words", "srm3_coeffs", "srm3_field_from_coeffs", "srm3_enable_timing",
     "srm3_get_timings", "srm3_field_from_coeffs_noalloc", "srm3_autotune",
-    "srm3_batch_device_bytes",
+    "srm3_batch_device_bytes", "srm3_set_tile_width",
     "srm3_batch_create", "srm3_batch_run", "srm3_batch_capture", "srm3_batch_sync",
     "srm3_batch_pair_terms", "srm3_batch_destroy", "srm3_batch_enable_timing",
     "srm3_batch_pairsum_ms", "srm3_batch_set_max_ctas",
@@ -49,7 +49,10 @@ SRM3_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 class srm3_tune_result(ctypes.Structure):
     _fields_ = [("table_ms", ctypes.c_double), ("recompute_ms", ctypes.c_double),
-                ("storage", ctypes.c_int32), ("samples", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("samples", ctypes.c_int32),
+                ("tile_width", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("table_ms_w32", ctypes.c_double), ("table_ms_w16", ctypes.c_double),
+                ("recompute_ms_w32", ctypes.c_double), ("recompute_ms_w16", ctypes.c_double)]
 
 
 class srm3_spectrum(ctypes.Structure):
@@ -84,7 +87,8 @@ class srm3_info(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("fixed_point_iterations", ctypes.c_int32),
-                ("diff_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_double)]
+                ("diff_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_double),
+                ("tile_width", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class srm3_timings(ctypes.Structure):
@@ -152,6 +156,7 @@ def load(build_if_needed: bool = True):
     lib.srm3_batch_sync.argtypes = [vp]
     lib.srm3_batch_pair_terms.argtypes = [vp]
     lib.srm3_batch_pair_terms.restype = ctypes.c_int64
+    lib.srm3_set_tile_width.argtypes = [vp, i32]
     lib.srm3_batch_device_bytes.argtypes = [vp]
     lib.srm3_batch_device_bytes.restype = ctypes.c_int64
     lib.srm3_batch_destroy.argtypes = [vp]
@@ -455,6 +460,10 @@ class Plan:
 
     def info(self) -> srm3_info:
         return plan_info(self.handle)
+
+    def set_tile_width(self, width: int):
+        """FP32 pair-sum work unit: 32 or 16 outputs (srm3_set_tile_width)."""
+        _check(load().srm3_set_tile_width(self.handle, int(width)))
 
     def tables(self):
         return plan_tables(self.handle, self.nk, self.nw)

@@ -61,9 +61,9 @@ def test_batch_matches_srm3_sample_direct_and_graph():
 
 
 def test_batch_holds_workspace_and_checks_arguments():
-    wl = MIX[0][0]
-    with srm3.Plan.create(wl, storage="table") as p:  # outside a shape group
-        out = torch.empty((2, wl.n_x, wl.n_t), dtype=torch.float32, device="cuda")
+    wl = W.small_case(nk=24, nw=37, nx=64, nt=128, precision="fp64")
+    with srm3.Plan.create(wl, storage="recompute") as p:  # FP64: outside shape groups
+        out = torch.empty((2, wl.n_x, wl.n_t), dtype=torch.float64, device="cuda")
         with pytest.raises(srm3.SRM3Error):
             srm3.Batch([p, p], [1, 1], [out, out])  # one plan, one workspace
         with pytest.raises(srm3.SRM3Error):
@@ -137,6 +137,89 @@ def test_uneven_batch_spectra_against_oracle(oracle_lib):
                 assert err <= 1e-4, (wl.name, s, err)
         print(f"uneven-batch spectra {[w.name for w in spectra]}: max|du|/sigma_u = "
               f"{worst:.3e} against the FP64 oracle")
+    finally:
+        for p in plans:
+            p.destroy()
+
+
+@pytest.mark.parametrize("storage,n", [("table", 3), ("recompute", 3), ("recompute", 40)])
+def test_tile_widths_give_identical_fields(storage, n):
+    """The 16-wide work unit (two compute warps) walks each output's chunks
+    and register blocks as the 32-wide one does: the fields are the same bit
+    for bit (full- and half-group modes, stored and recomputed W)."""
+    wl = W.small_case(nk=40, nw=70, nx=64, nt=256, precision="fp32")
+    seeds = list(range(11, 11 + n))
+    with srm3.Plan.create(wl, storage=storage) as p:
+        assert p.info().tile_width == 32
+        ref = p.sample(seeds)
+        p.set_tile_width(16)
+        assert p.info().tile_width == 16
+        got = p.sample(seeds)
+        torch.cuda.synchronize()
+        assert torch.equal(got, ref)
+        with pytest.raises(srm3.SRM3Error):
+            p.set_tile_width(24)
+
+
+def test_batch_with_both_tile_widths():
+    """A batch whose plans were set to different tiles runs one launch in the
+    tile of most of its pair-terms; every plan's fields equal its own
+    srm3_sample (in its own tile)."""
+    plans = [srm3.Plan.create(wl, storage=st) for wl, st, _ in MIX]
+    try:
+        for i, p in enumerate(plans):
+            if p.precision == "fp32" and i % 2 == 1:
+                p.set_tile_width(16)
+        outs = [torch.full((n, wl.n_x, wl.n_t), float("nan"), dtype=_dtype(wl), device="cuda")
+                for wl, _, n in MIX]
+        with srm3.Batch(plans, [n for _, _, n in MIX], outs) as b:
+            seeds = _seed_lists(300)
+            b.capture()
+            b.run([s for ss in seeds for s in ss])
+            b.sync()
+            for p, o, ss in zip(plans, outs, seeds):
+                ref = p.sample(ss)
+                torch.cuda.synchronize()
+                assert torch.equal(o, ref), (p.nk, p.nw)
+    finally:
+        for p in plans:
+            p.destroy()
+
+
+def test_autotune_times_every_storage_and_tile():
+    wl = W.small_case(nk=32, nw=64, nx=64, nt=128, precision="fp32", storage="table")
+    with srm3.Plan.create(wl, storage="table") as p:
+        r = srm3.autotune(p.handle, 8)
+        assert r.tile_width in (16, 32)
+        for t in (r.table_ms_w32, r.table_ms_w16, r.recompute_ms_w32, r.recompute_ms_w16):
+            assert t > 0
+        assert r.recompute_ms == min(r.recompute_ms_w32, r.recompute_ms_w16)
+        assert p.info().tile_width == r.tile_width
+    with srm3.Plan.create(wl, storage="recompute") as q:  # later plans of the shape take the tile
+        assert q.info().tile_width == r.tile_width
+
+
+def test_stored_table_plans_of_one_shape_share_lanes():
+    """Plans with stored W tables of one lattice shape form a shape group (the
+    table holds the pair envelopes of the shape; each sample applies its own
+    spectrum's pair factor): the batch equals each plan sampled alone."""
+    wls = [W.small_case(nk=24, nw=37, nx=64, nt=128, U=U, target=t)
+           for U, t in ((30.0, 0.5), (44.0, 0.35), (22.0, 0.6))]
+    counts = [3, 1, 2]
+    plans = [srm3.Plan.create(wl, storage="table") for wl in wls]
+    try:
+        assert all(p.info().table_bytes > 0 for p in plans)
+        outs = [torch.full((n, 64, 128), float("nan"), device="cuda") for n in counts]
+        seeds = [[5 + 10 * i + j for j in range(n)] for i, n in enumerate(counts)]
+        with srm3.Batch(plans, counts, outs) as b:
+            b.run([s for ss in seeds for s in ss])
+            b.sync()
+            # one shape group: the batch's own buffers hold its samples
+            assert b.device_bytes >= 24 * (37 + 128) * 64 * 8
+        for p, o, ss in zip(plans, outs, seeds):
+            ref = p.sample(ss)
+            torch.cuda.synchronize()
+            assert torch.equal(o, ref)
     finally:
         for p in plans:
             p.destroy()
