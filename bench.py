@@ -577,10 +577,10 @@ def run_paper_bridge(args):
     stage_ms = {"plan": info.plan_ms, "recursion": t3.recursion_ms, "phases": t3.phases_ms,
                 "pairsum_fft_conv": t3.pairsum_ms, "transform": t3.transform_ms,
                 "stats": s_ms}
-    # algorithmic HBM bytes per sample: transform (C in, H out and in, u out),
-    # statistics (u in)
+    # algorithmic HBM bytes per sample: transform (C in; the x stage's
+    # n_x x n_omega columns out and in; u out), statistics (u in)
     cNw = 1 << max(1, (2 * wl.n_omega - 2).bit_length())
-    per = {"transform": 2 * wl.n_kappa * wl.n_omega * 8 + 2 * wl.n_kappa * wl.n_t * 8
+    per = {"transform": 2 * wl.n_kappa * wl.n_omega * 8 + 2 * wl.n_x * wl.n_omega * 8
                         + wl.n_x * wl.n_t * 4,
            "stats": wl.n_x * wl.n_t * 4,
            # as _conv_roofline: per sheet-sample y twice, C once, padded rows 4x

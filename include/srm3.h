@@ -296,7 +296,7 @@ int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
  * others, so the values are bit-identical to srm3_field_from_coeffs.
  * Asynchronous on the plan's stream.
  *
- * Scratch: the intermediate of the two FFT stages, n_kappa * n_t complex
+ * Scratch: the intermediate of the two FFT stages, n_x * n_omega complex
  * values per coefficient set (8 bytes each in FP32, 16 in FP64), lives in a
  * fixed array of SRM3_NOALLOC_SCRATCH_BYTES that the library defines in
  * device memory, one per device.  Sets are transformed in groups that fit.
@@ -320,7 +320,7 @@ int srm3_field_from_coeffs(srm3_plan *plan, const void *C, int n, void *out);
  *
  * Errors: SRM3_ERR_INVALID_ARG for a NULL plan, n < 0, NULL buffers with
  * n > 0, or a plan whose one coefficient set needs more scratch than
- * SRM3_NOALLOC_SCRATCH_BYTES (n_kappa * n_t * 8 bytes in FP32, * 16 in FP64);
+ * SRM3_NOALLOC_SCRATCH_BYTES (n_x * n_omega * 8 bytes in FP32, * 16 in FP64);
  * SRM3_ERR_CUDA when the address lookup or a launch fails.  The message is
  * in srm3_last_error(). */
 int srm3_field_from_coeffs_noalloc(srm3_plan *plan, const void *C, int n, void *out);

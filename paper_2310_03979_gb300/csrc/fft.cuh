@@ -1,7 +1,9 @@
-// fft.cuh - the hand-written 2-D inverse FFT of the SRM3 field (t stage, then
-// x stage), shared by the sampling entry points and the no-allocation
-// transform.  Internal linkage: every translation unit that includes it
-// gets its own copy of the kernels.
+// fft.cuh - the hand-written FFTs: the 2-D inverse transform of the SRM3 field
+// (x stage over the coefficient columns, then half-length complex-to-real
+// rows), shared by the sampling entry points and the no-allocation
+// transform, and the radix-2 shared-memory stages of the separable
+// self-convolution.  Internal linkage: every translation unit that includes
+// it gets its own copy of the kernels.
 #pragma once
 
 #include "srm3_internal.cuh"
@@ -9,10 +11,8 @@
 namespace srm3 {
 namespace {
 
-// a6: inverse transform.  u[mx][mt] = Re sum_kk e^{2 pi i kk mx / nx}
-//   sum_m F[kk][m] e^{2 pi i m mt / nt}, F[kk][kw] = C^+_k,
-//   F[kk][(nt - kw) mod nt] += C^-_k (FFT form, Sec. 4.3).
-// Radix-2 decimation in time in shared memory, input in bit-reversed order,
+// Radix-2 decimation in time in shared memory (the separable
+// self-convolution's transforms), input in bit-reversed order,
 // twiddles from a table packed by stage: stage s (1-based) reads
 // e^{+2 pi i j / 2^s}, j < 2^(s-1), at twp[2^(s-1) - 1 + j], so the lanes of
 // a warp read consecutive entries in every stage.
@@ -114,67 +114,327 @@ __device__ __forceinline__ int brev(int m, int log2n) {
   return (int)(__brev((unsigned)m) >> (32 - log2n));
 }
 
+// ---------------------------------------------------------------------------
+// a6: the output transform (FFT form, Sec. 4.3).  With F[kk][m] on the
+// nx x nt grid (F[kk][kw] = C^+_k, F[kk][(nt - kw) mod nt] += C^-_k, zero
+// for kk >= nk), the field is
+//   u[mx][mt] = Re sum_{kk,m} F[kk][m] e^{2 pi i (kk mx / nx + m mt / nt)}.
+// Re z = (z + conj z) / 2, so u is the plain inverse DFT of the Hermitian
+// part F_h[kk][m] = (F[kk][m] + conj F[-kk][-m]) / 2 (indices mod nx, nt).
+// In the columns m <= nt/2, F_h is nonzero only for m < nw (nt >= 2 nw - 1):
+//   F_h[kk][m] = (P[kk][m] + conj P'[-kk][m]) / 2,
+//   P[kk][m] = C^+[kk][m] + [m = 0] C^-[kk][0],
+//   P'[kk][m] = C^-[kk][m] + [m = 0] C^+[kk][0]   (zero for kk >= nk).
+// Stage 1 (x): G[mx][m] = sum_kk F_h[kk][m] e^{2 pi i kk mx / nx} for the nw
+// columns m < nw only.  Stage 2 (t): each row X[m] = G[mx][m] is Hermitian
+// in m (u is real), so with M = nt / 2 the row is one complex inverse DFT of
+// length M: z[j] = u[mx][2j] + i u[mx][2j + 1] = sum_{m<M} Z[m] e^{2 pi i m j/M},
+//   Z[m] = (X[m] + conj X[M - m]) + i e^{2 pi i m / nt} (X[m] - conj X[M - m])
+// (the split of u into even and odd samples; X[M] = 0 as M >= nw).
+// Compared with transforming all nt columns of H[kk][mt], stage 1 runs over
+// nw columns and stage 2 over half-length rows.
+//
+// Both stages are Stockham autosort passes of radix R <= 16 (Govindaraju et
+// al., SC 2008): pass item j < L/R of a length-L transform, with Ns the
+// length already transformed, reads x[j + r L/R] (r < R), multiplies by
+// w_{Ns R}^{(j mod Ns) r}, takes a radix-R DFT in registers and writes
+// x[(j / Ns) Ns R + j mod Ns + r Ns].  Natural order in and out: the first
+// pass reads its inputs straight from global memory (forming F_h or Z on
+// the way), the last writes straight to global memory, the passes between
+// go through shared memory in place.  A thread holds 16 values (one radix-16
+// item, or 16/R items of radix R); log2 L splits into ceil(log2 L / 4)
+// passes of near-equal radix.  w_N = e^{+2 pi i / N}.
+
+// b * e^{2 pi i e / 16}, e in [0, 8) (e a constant after unrolling)
 template <typename T2>
-__global__ void k_fft_t(int nk, int nw, int nt, int log2nt,
-                        const T2 *__restrict__ C, const T2 *__restrict__ tw, T2 *__restrict__ H) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2 *buf = reinterpret_cast<T2 *>(smem_raw);
-  const int kk = blockIdx.x, n = blockIdx.y;
-  for (int m = threadIdx.x; m < fft_row_len(nt); m += blockDim.x) {
-    buf[m].x = 0;
-    buf[m].y = 0;
+__device__ __forceinline__ T2 rot16(T2 b, int e) {
+  using T = decltype(b.x);
+  constexpr double c1 = 0.92387953251128675613;  // cos(pi / 8)
+  constexpr double s1 = 0.38268343236508977173;  // sin(pi / 8)
+  constexpr double h = 0.70710678118654752440;   // cos(pi / 4)
+  T2 r;
+  switch (e) {
+    case 0:
+      return b;
+    case 2:
+      r.x = (T)h * (b.x - b.y);
+      r.y = (T)h * (b.x + b.y);
+      return r;
+    case 4:
+      r.x = -b.y;
+      r.y = b.x;
+      return r;
+    case 6:
+      r.x = -(T)h * (b.x + b.y);
+      r.y = (T)h * (b.x - b.y);
+      return r;
+    default: {
+      const T c = e == 1 ? (T)c1 : e == 3 ? (T)s1 : e == 5 ? (T)-s1 : (T)-c1;
+      const T s = (e == 1 || e == 7) ? (T)s1 : (T)c1;
+      r.x = b.x * c - b.y * s;
+      r.y = b.x * s + b.y * c;
+      return r;
+    }
   }
-  __syncthreads();
-  const T2 *Cp = C + ((size_t)(2 * n) * nk + kk) * nw;
-  const T2 *Cm = C + ((size_t)(2 * n + 1) * nk + kk) * nw;
-  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) buf[rp(brev(kw, log2nt))] = Cp[kw];
-  __syncthreads();
-  for (int kw = threadIdx.x; kw < nw; kw += blockDim.x) {
-    const int m = kw == 0 ? 0 : nt - kw;
-    const int pos = rp(brev(m, log2nt));
-    T2 v = buf[pos];
-    const T2 c = Cm[kw];
-    v.x += c.x;
-    v.y += c.y;
-    buf[pos] = v;
-  }
-  __syncthreads();
-  fft_stages<false>(buf, 1, log2nt, tw);
-  T2 *Hrow = H + ((size_t)n * nk + kk) * nt;
-  for (int m = threadIdx.x; m < nt; m += blockDim.x) Hrow[m] = buf[rp(m)];
 }
 
-template <typename T, typename T2>
-__global__ void k_fft_x(int nk, int nx, int nt, int log2nx, int TC,
-                        const T2 *__restrict__ H, const T2 *__restrict__ tw, T *__restrict__ u) {
+template <int R>
+struct Log2R {
+  static constexpr int v = R == 2 ? 1 : R == 4 ? 2 : R == 8 ? 3 : 4;
+};
+
+// v[r] <- sum_s v[s] e^{2 pi i r s / R}: radix-2 decimation in time on the
+// bit-reversed copy, every index and twiddle a compile-time constant.
+template <int R, typename T2>
+__device__ __forceinline__ void dft_inv(T2 (&v)[R]) {
+  constexpr int B = Log2R<R>::v;
+  T2 a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int rb = 0;
+#pragma unroll
+    for (int bit = 0; bit < B; ++bit) rb |= ((i >> bit) & 1) << (B - 1 - bit);
+    a[i] = v[rb];
+  }
+#pragma unroll
+  for (int st = 0; st < B; ++st) {
+    const int h = 1 << st;
+#pragma unroll
+    for (int g = 0; g < R; g += 2 * h)
+#pragma unroll
+      for (int j = 0; j < h; ++j) {
+        const T2 t = rot16(a[g + j + h], j * (8 >> st));  // w_{2h}^j
+        const T2 x = a[g + j];
+        a[g + j].x = x.x + t.x;
+        a[g + j].y = x.y + t.y;
+        a[g + j + h].x = x.x - t.x;
+        a[g + j + h].y = x.y - t.y;
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = a[i];
+}
+
+// Pass plan of a length-2^l transform: ceil(l / 4) passes, pass p of radix
+// 2^tx_lr(l, p) (larger radices first).
+__host__ __device__ constexpr int tx_npass(int l) { return (l + 3) >> 2; }
+__host__ __device__ constexpr int tx_lr(int l, int p) {
+  return l / tx_npass(l) + (p < l - (l / tx_npass(l)) * tx_npass(l) ? 1 : 0);
+}
+// Entries of the pass-twiddle table: passes p >= 1 in order, pass p holding
+// w_{Ns R}^{k r} at k R + r (k < Ns, r < R; Ns = the length its earlier
+// passes transformed), so that an item's R twiddles are one contiguous run.
+__host__ __device__ constexpr int tx_twlen(int l) {
+  int n = 0, ns = 1;
+  for (int p = 0; p < tx_npass(l); ++p) {
+    ns <<= tx_lr(l, p);
+    if (p >= 1) n += ns;
+  }
+  return n;
+}
+
+// Shared-memory position of entry i of one transform: one pad entry per 16,
+// which spreads the first pass's stride-R writes over the banks.
+__device__ __forceinline__ int sp16(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int tx_len(int L) { return L + (L >> 4); }
+__host__ __device__ constexpr int tx_tpt(int L) { return L >= 16 ? L >> 4 : 1; }
+
+// The R twiddles of one item (16-byte loads; the tables start 16-byte aligned
+// and every run is an even number of entries).
+template <int R, typename T2>
+__device__ __forceinline__ void load_tw(const T2 *__restrict__ p, T2 (&w)[R]) {
+  if constexpr (sizeof(T2) == 8) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      const float4 t = __ldg(q + i);
+      w[2 * i].x = t.x;
+      w[2 * i].y = t.y;
+      w[2 * i + 1].x = t.z;
+      w[2 * i + 1].y = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) w[i] = __ldg(p + i);
+  }
+}
+
+// One Stockham pass of radix R (see above).  tpt threads per transform, jt
+// this thread's index among them; items jt, jt + tpt, ... < L/R.  twp: this
+// pass's run of the pass-twiddle table.  FIRST: inputs from src(i) (global);
+// else from sm (shared, padded positions).  LAST: outputs to dst(i, v)
+// (global); else to sm.
+template <int R, bool FIRST, bool LAST, typename T2, class Src, class Dst>
+__device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
+                                              const T2 *__restrict__ twp, T2 *sm, Src &src,
+                                              Dst &dst) {
+  constexpr int NI = 16 / R;
+  const int LR = L / R;
+  T2 v[NI][R];
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int j = jt + it * tpt;
+    if (j < LR) {
+      if constexpr (FIRST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[it][r] = src(j + r * LR);
+      } else {
+        if (LR % 16 == 0) {  // (j + r LR) >> 4 = (j >> 4) + r LR / 16
+          const int a = sp16(j), st = LR + (LR >> 4);
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[it][r] = sm[a + r * st];
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[it][r] = sm[sp16(j + r * LR)];
+        }
+        T2 w[R];
+        load_tw<R>(twp + (j & (Ns - 1)) * R, w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
+      }
+      dft_inv<R>(v[it]);
+    }
+  }
+  if constexpr (!FIRST && !LAST) __syncthreads();  // in place: all reads before any write
+#pragma unroll
+  for (int it = 0; it < NI; ++it) {
+    const int j = jt + it * tpt;
+    if (j < LR) {
+      const int k = j & (Ns - 1);
+      const int b = (j - k) * R + k;
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst(b + r * Ns, v[it][r]);
+      } else if (Ns % 16 == 0) {
+        const int a = sp16(b), st = Ns + (Ns >> 4);
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[a + r * st] = v[it][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) sm[sp16(b + r * Ns)] = v[it][r];
+      }
+    }
+  }
+  if constexpr (!LAST) __syncthreads();
+}
+
+// Passes p, p + 1, ... of the inverse DFT of length 2^l (1 <= l <= 13),
+// unrolled at compile time so that each pass keeps only its own 16 values
+// live; Ns is the length transformed by the passes before p, toff the
+// offset of pass p's run in the pass-twiddle table tw.
+template <int l, int p, typename T2, class Src, class Dst>
+__device__ __forceinline__ void stockham_passes(int Ns, int toff, int tpt, int jt,
+                                                const T2 *__restrict__ tw, T2 *sm, Src &src,
+                                                Dst &dst) {
+  if constexpr (p < tx_npass(l)) {
+    constexpr int lr = tx_lr(l, p);
+    stockham_pass<(1 << lr), p == 0, p == tx_npass(l) - 1>(1 << l, Ns, tpt, jt, tw + toff, sm,
+                                                           src, dst);
+    stockham_passes<l, p + 1>(Ns << lr, p == 0 ? 0 : toff + (Ns << lr), tpt, jt, tw, sm, src,
+                              dst);
+  }
+}
+
+// Stage 1: TC columns m0 + c of one coefficient set per CTA (blockIdx.y =
+// set), thread (c, jt) = (t mod TC, t / TC); TC consecutive columns make the
+// reads of C and the writes of G runs of TC complex values.  G is
+// [set][nx][nw].  Column stride in shared memory: colstride entries.  twp:
+// the pass-twiddle table of length nx.
+template <int LOG2NX, typename T2>
+__global__ void __launch_bounds__(512) k_tx_cols(int nk, int nw, int TC, int colstride,
+                                                  const T2 *__restrict__ C,
+                                                  const T2 *__restrict__ twp,
+                                                  T2 *__restrict__ G) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T2 *buf = reinterpret_cast<T2 *>(smem_raw);
-  const int mt0 = blockIdx.x * TC, n = blockIdx.y, cs = fft_col_stride(nx);
-  // Inputs kk >= nk are zero.  With nk <= nkp = 2^q, the entries x[kk +
-  // j nkp] (j < 2^r, r = log2nx - q) sit at bit-reversed positions brev(kk)
-  // + brev_r(j), one aligned group of 2^r, and only j = 0 is nonzero; the
-  // first r stages of butterflies turn such a group into 2^r copies of
-  // x[kk].  The copies are written here and the stages start at r + 1;
-  // every position is written, so the buffer needs no clearing.
-  int q = 0;
-  while ((1 << q) < nk) ++q;
-  const int r = log2nx - q, rep = 1 << r;
-  const T2 *Hn = H + (size_t)n * nk * nt + mt0;
-  for (int idx = threadIdx.x; idx < (TC << q); idx += blockDim.x) {
-    const int kk = idx / TC, c = idx - kk * TC;
+  using T = decltype(T2::x);
+  constexpr int L = 1 << LOG2NX;
+  const int n = blockIdx.y;
+  const int c = threadIdx.x & (TC - 1), jt = threadIdx.x / TC;
+  const int m = blockIdx.x * TC + c;
+  const bool live = m < nw;
+  const T2 *Cp = C + (size_t)(2 * n) * nk * nw;
+  const T2 *Cm = Cp + (size_t)nk * nw;
+  T2 *col = reinterpret_cast<T2 *>(smem_raw) + c * colstride;
+  T2 *Gn = G + (size_t)n * L * nw;
+  auto src = [&](int kk) -> T2 {  // F_h[kk][m]
     T2 v;
     v.x = 0;
     v.y = 0;
-    if (kk < nk) v = Hn[(size_t)kk * nt + c];
-    T2 *dst = buf + c * cs + brev(kk, log2nx);
-    for (int j = 0; j < rep; ++j) dst[j] = v;
-  }
-  __syncthreads();
-  fft_stages<true>(buf, TC, log2nx, tw, r + 1);
-  T *un = u + (size_t)n * nx * nt + mt0;
-  for (int idx = threadIdx.x; idx < nx * TC; idx += blockDim.x) {
-    const int mx = idx / TC, c = idx - mx * TC;
-    un[(size_t)mx * nt + c] = buf[c * cs + mx].x;
+    if (!live) return v;
+    if (kk < nk) {
+      v = Cp[(size_t)kk * nw + m];
+      if (m == 0) {
+        const T2 w = Cm[(size_t)kk * nw];
+        v.x += w.x;
+        v.y += w.y;
+      }
+    }
+    const int k2 = kk == 0 ? 0 : L - kk;
+    if (k2 < nk) {
+      T2 w = Cm[(size_t)k2 * nw + m];
+      if (m == 0) {
+        const T2 a = Cp[(size_t)k2 * nw];
+        w.x += a.x;
+        w.y += a.y;
+      }
+      v.x += w.x;
+      v.y -= w.y;
+    }
+    v.x *= (T)0.5;
+    v.y *= (T)0.5;
+    return v;
+  };
+  auto dst = [&](int i, T2 v) {
+    if (live) Gn[(size_t)i * nw + m] = v;
+  };
+  stockham_passes<LOG2NX, 0>(1, 0, tx_tpt(L), jt, twp, col, src, dst);
+}
+
+// Stage 2: RB rows mx of one set per CTA, thread (row, jt) = (t / tpt,
+// t mod tpt); the row's output is the nt = 2M real values u[set][mx][.].
+// twp: the pass-twiddle table of length M; twz[m] = e^{2 pi i m / nt}, m < M.
+template <int LOG2M, typename T, typename T2>
+__global__ void __launch_bounds__(512) k_tx_rows(int nx, int nw, int rowstride,
+                                                 const T2 *__restrict__ G,
+                                                 const T2 *__restrict__ twp,
+                                                 const T2 *__restrict__ twz, T *__restrict__ u) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int M = 1 << LOG2M, tpt = tx_tpt(M);
+  const int n = blockIdx.y;
+  const int row = threadIdx.x / tpt, jt = threadIdx.x & (tpt - 1);
+  const int rb = blockDim.x / tpt, mx = blockIdx.x * rb + row;
+  const T2 *X = G + ((size_t)n * nx + mx) * nw;
+  T2 *buf = reinterpret_cast<T2 *>(smem_raw) + row * rowstride;
+  T *urow = u + ((size_t)n * nx + mx) * (size_t)(2 * M);
+  auto src = [&](int m) -> T2 {  // Z[m]
+    T2 a, b;
+    a.x = 0;
+    a.y = 0;
+    b = a;
+    if (m < nw) a = X[m];
+    if (M - m < nw) b = X[M - m];
+    if (m >= nw && M - m >= nw) return a;  // zero
+    const T2 w = twz[m];
+    const T dx = a.x - b.x, dy = a.y + b.y;  // X[m] - conj X[M - m]
+    const T wx = w.x * dx - w.y * dy, wy = w.x * dy + w.y * dx;
+    T2 z;
+    z.x = (a.x + b.x) - wy;
+    z.y = (a.y - b.y) + wx;
+    return z;
+  };
+  const bool vec = (reinterpret_cast<uintptr_t>(u) & (sizeof(T2) - 1)) == 0;
+  auto dst = [&](int i, T2 v) {
+    if (vec) {
+      reinterpret_cast<T2 *>(urow)[i] = v;
+    } else {
+      urow[2 * i] = v.x;
+      urow[2 * i + 1] = v.y;
+    }
+  };
+  if constexpr (LOG2M == 0) {  // nt = 2: z[0] = Z[0]
+    if (jt == 0) dst(0, src(0));
+  } else {
+    stockham_passes<LOG2M, 0>(1, 0, tpt, jt, twp, buf, src, dst);
   }
 }
 

@@ -14,8 +14,8 @@ constexpr int kMaxDevices = 64;
 
 }  // namespace
 
-// The t-stage rows of one group of coefficient sets, [set][kk][mt] complex.
-// Never read before the t stage of the same call has written it.
+// The x-stage columns of one group of coefficient sets, [set][mx][kw]
+// complex.  Never read before the x stage of the same call has written it.
 static __device__ __align__(256) unsigned char srm3_noalloc_scratch[kScratchBytes];
 
 namespace srm3 {
@@ -62,13 +62,13 @@ struct DeviceGuard {
   }
 };
 
-// The transform of n sets in groups whose t-stage rows fit the scratch, by
+// The transform of n sets in groups whose x-stage columns fit the scratch, by
 // the launch sequence of srm3_field_from_coeffs (transform_on) with the
 // scratch in place of the plan workspace.
 int field_noalloc(srm3_plan *p, const void *C, int n, void *out, void *scratch) {
   const size_t e2 = p->precision == SRM3_FP32 ? sizeof(float2) : sizeof(double2);
   const size_t e1 = p->precision == SRM3_FP32 ? sizeof(float) : sizeof(double);
-  const size_t perH = (size_t)p->nk * p->nt * e2;
+  const size_t perH = transform_elems(p) * e2;
   const size_t perC = (size_t)2 * p->nk * p->nw * e2;
   const size_t perU = (size_t)p->nx * p->nt * e1;
   // gridDim.y carries the set index: at most 65535 sets per launch.
@@ -91,11 +91,11 @@ SRM3_API int srm3_field_from_coeffs_noalloc(srm3_plan *plan, const void *C, int 
   if (!plan) return fail(SRM3_ERR_INVALID_ARG, "plan is NULL");
   if (n < 0 || (n > 0 && (!C || !out))) return fail(SRM3_ERR_INVALID_ARG, "bad C/out/n");
   const size_t e2 = plan->precision == SRM3_FP32 ? sizeof(float2) : sizeof(double2);
-  const size_t perH = (size_t)plan->nk * plan->nt * e2;
+  const size_t perH = transform_elems(plan) * e2;
   if (perH > kScratchBytes)
     return fail(SRM3_ERR_INVALID_ARG,
                 "srm3_field_from_coeffs_noalloc: one coefficient set needs " +
-                    std::to_string(perH) + " bytes of scratch (n_kappa * n_t complex values), "
+                    std::to_string(perH) + " bytes of scratch (n_x * n_omega complex values), "
                     "more than the SRM3_NOALLOC_SCRATCH_BYTES = " +
                     std::to_string(kScratchBytes) + " it has; use srm3_field_from_coeffs");
   if (n == 0) return SRM3_OK;

@@ -150,6 +150,38 @@ __global__ void k_env(int len, int off, double sigma_n, T *out) {
 // packed by stage: entry 2^(s-1) - 1 + j holds e^{+2 pi i m / n} with
 // m = j 2^(log2n - s) (= e^{+2 pi i j / 2^s}), j < 2^(s-1), s = 1..log2n; the
 // last entry is unused.
+// Twiddles of the output transform: the pass-twiddle tables of lengths nx
+// and nt / 2 (tx_twlen entries each: pass p >= 1 of the length-2^l transform
+// holds w_{Ns R}^{k r} at k R + r), then e^{2 pi i m / nt}, m < nt / 2.
+template <typename T2>
+__global__ void k_tx_twiddles(int lx, int lm, T2 *tw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n1 = tx_twlen(lx), n2 = tx_twlen(lm), M = 1 << lm;
+  if (e >= n1 + n2 + M) return;
+  long long num = 0, den = 1;  // angle 2 pi num / den
+  if (e >= n1 + n2) {
+    num = e - n1 - n2;
+    den = 2 * M;
+  } else {
+    const int l = e < n1 ? lx : lm;
+    int q = e < n1 ? e : e - n1, ns = 1 << tx_lr(l, 0);
+    for (int p = 1; p < tx_npass(l); ++p) {
+      const int R = 1 << tx_lr(l, p);
+      if (q < ns * R) {
+        num = (long long)(q / R) * (q % R);
+        den = (long long)ns * R;
+        break;
+      }
+      q -= ns * R;
+      ns *= R;
+    }
+  }
+  double sn, cs;
+  sincospi(2.0 * (double)num / (double)den, &sn, &cs);
+  tw[e].x = cs;
+  tw[e].y = sn;
+}
+
 template <typename T2>
 __global__ void k_twiddles(int n, int log2n, T2 *tw) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1171,7 +1203,6 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
   // boundaries; the table reaches d = 2 nw + 127, past the last window.
   p->ew_off = ((nw + 32 + 7) / 8) * 8 + 7;
   p->ew_len = p->ew_off + 2 * nw + 128;  // difference pairs reach d = 2 nw - 2
-  p->nfft = std::max(p->nx, p->nt);
   if (p->sep) {  // zero-padded self-convolution grid
     p->log2cNk = 1;
     while ((1 << p->log2cNk) < 2 * nk - 1) ++p->log2cNk;
@@ -1184,7 +1215,8 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
   p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
   SRM3_CUDA(dev_alloc(&p->Ek, nk * es, st));
   SRM3_CUDA(dev_alloc(&p->Ews, p->ew_len * es, st));
-  SRM3_CUDA(dev_alloc(&p->tw, p->nfft * 2 * es, st));
+  const int tw_n = tx_twlen(p->log2nx) + tx_twlen(p->log2nt - 1) + p->nt / 2;
+  SRM3_CUDA(dev_alloc(&p->tw, (size_t)tw_n * 2 * es, st));
   if (f32) {
     k_env<float><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (float *)p->Ek);
     k_env<float><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off, p->sigma_g * nw,
@@ -1197,8 +1229,8 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
       k_env<float><<<cdiv(p->ewd_len, 256), 256, 0, st>>>(p->ewd_len, 0, p->sigma_g * nw,
                                                          (float *)p->Ewd);
     }
-    k_twiddles<float2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
-                                                          (float2 *)p->tw);
+    k_tx_twiddles<float2><<<cdiv(tw_n, 256), 256, 0, st>>>(p->log2nx, p->log2nt - 1,
+                                                            (float2 *)p->tw);
     if (p->sep) {
       SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2), st));
       k_twiddles<float2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
@@ -1209,8 +1241,8 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
     k_env<double><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (double *)p->Ek);
     k_env<double><<<cdiv(p->ew_len, 256), 256, 0, st>>>(p->ew_len, p->ew_off,
                                                        p->sigma_g * nw, (double *)p->Ews);
-    k_twiddles<double2><<<cdiv(p->nfft, 256), 256, 0, st>>>(p->nfft, ilog2_exact(p->nfft),
-                                                           (double2 *)p->tw);
+    k_tx_twiddles<double2><<<cdiv(tw_n, 256), 256, 0, st>>>(p->log2nx, p->log2nt - 1,
+                                                             (double2 *)p->tw);
     if (p->sep) {
       SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2), st));
       k_twiddles<double2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,

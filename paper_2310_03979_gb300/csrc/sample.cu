@@ -143,7 +143,7 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   SRM3_CUDA(dev_alloc(&p->y, (size_t)p->nk * p->rowstride * sp * e2, p->stream));
   SRM3_CUDA(dev_alloc(&p->y0, (size_t)sp * e2, p->stream));
   SRM3_CUDA(dev_alloc(&p->C, (size_t)2 * cap * p->nk * p->nw * e2, p->stream));
-  SRM3_CUDA(dev_alloc(&p->H, (size_t)cap * p->nk * p->nt * e2, p->stream));
+  SRM3_CUDA(dev_alloc(&p->H, (size_t)cap * transform_elems(p) * e2, p->stream));
   if (p->mixed && p->precision == SRM3_FP32)
     SRM3_CUDA(dev_alloc(&p->ys, (size_t)p->nk * p->rowstride * sp * e2, p->stream));
   if (p->sep) {  // the self-convolution grid of every sheet-sample of a chunk
@@ -167,7 +167,7 @@ static int phases_into(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
                        uint32_t *words_out) {
   SeedChunk sc;
   std::memset(&sc, 0, sizeof(sc));
-  if (!dseeds) std::memcpy(sc.s, seeds, sizeof(uint64_t) * n);
+  if (!dseeds && seeds) std::memcpy(sc.s, seeds, sizeof(uint64_t) * n);
   const long long nl = (long long)p->nk * p->nw;
   const long long nc = (2 * nl + 3) / 4;
   const int blocks = cdiv(nc * n, 256);
@@ -452,35 +452,6 @@ int run_pairsum(srm3_plan *p, int n, void *C_out) {
   }
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
-}
-
-template <typename T, typename T2>
-static int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2 *H) {
-  const size_t e2 = sizeof(T2);
-  const size_t smem_t = (size_t)fft_row_len(p->nt) * e2;
-  int TC = 16;
-  while (TC > 1 && ((size_t)TC * fft_col_stride(p->nx) * e2 > 96 * 1024 || TC > p->nt)) TC >>= 1;
-  const size_t smem_x = (size_t)TC * fft_col_stride(p->nx) * e2;
-  const int lim = 200 * 1024;
-  SRM3_CUDA(cudaFuncSetAttribute(k_fft_t<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  SRM3_CUDA(cudaFuncSetAttribute(k_fft_x<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
-  k_fft_t<T2><<<dim3(p->nk, n), 256, smem_t, st>>>(p->nk, p->nw, p->nt, p->log2nt, C,
-                                                          (const T2 *)p->tw, H);
-  SRM3_CUDA(cudaGetLastError());
-  k_fft_x<T, T2><<<dim3(p->nt / TC, n), 512, smem_x, st>>>(
-      p->nk, p->nx, p->nt, p->log2nx, TC, (const T2 *)H, (const T2 *)p->tw, out);
-  SRM3_CUDA(cudaGetLastError());
-  return SRM3_OK;
-}
-
-// The transform of n coefficient sets with the t-stage rows in H (n*nk*nt
-// complex), on stream st.
-int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out, void *H) {
-  if (p->precision == SRM3_FP32)
-    return transform_impl<float, float2>(p, st, (const float2 *)C, n, (float *)out,
-                                         (float2 *)H);
-  return transform_impl<double, double2>(p, st, (const double2 *)C, n, (double *)out,
-                                         (double2 *)H);
 }
 
 int run_transform(srm3_plan *p, const void *C, int n, void *out) {
@@ -1026,7 +997,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     g.sp = sspad_for(g.total);
     g.ybytes = (size_t)p->nk * p->rowstride * g.sp * sizeof(float2);
     const size_t cb = (size_t)2 * g.total * p->nk * p->nw * sizeof(float2);
-    const size_t hb = (size_t)g.nmax * p->nk * p->nt * sizeof(float2);
+    const size_t hb = (size_t)g.nmax * transform_elems(p) * sizeof(float2);
     cudaStream_t st = b->stream;
     b->dev_bytes += (long long)(g.ybytes + (size_t)g.sp * sizeof(float2) + cb + hb +
                                 2 * sizeof(float *) * g.total);

@@ -156,8 +156,8 @@ struct srm3_plan {
   void *Ek = nullptr;     // envelope factor along kappa, |d| < nk
   void *Ews = nullptr;    // envelope factor along omega, signed d, offset ew_off
   int ew_off = 0, ew_len = 0;
-  void *tw = nullptr;     // FFT twiddles e^{+2 pi i j / nfft}, j < nfft
-  int nfft = 0;
+  void *tw = nullptr;     // output-transform twiddles: pass tables of lengths nx and
+                          // nt / 2, then e^{2 pi i m / nt}, m < nt / 2
 
   // FP32 tiled pair sum: tiles (kk, kw0) in decreasing-cost order
   int ntw = 0, ntiles = 0;
@@ -226,10 +226,14 @@ int ensure_workspace(srm3_plan *p, int chunk);
 int run_phases(srm3_plan *p, const uint64_t *seeds, int n, uint32_t *words_out);
 int run_pairsum(srm3_plan *p, int n, void *C_out);
 int run_transform(srm3_plan *p, const void *C, int n, void *out);
-// The two FFT stages for n coefficient sets on stream st with the t-stage
-// rows in H (n * nk * nt complex values in the plan's precision), which the
-// caller supplies: the plan workspace, a batch buffer or fixed scratch.
+// The two FFT stages for n coefficient sets on stream st with the x-stage
+// columns in H (n * transform_elems(p) complex values in the plan's
+// precision), which the caller supplies: the plan workspace, a batch buffer
+// or fixed scratch.
 int transform_on(srm3_plan *p, cudaStream_t st, const void *C, int n, void *out, void *H);
+// Complex values of the transform's intermediate per coefficient set: the
+// x-stage output G[nx][nw].
+inline size_t transform_elems(const srm3_plan *p) { return (size_t)p->nx * p->nw; }
 int prepare_shape_tables(srm3_plan *p, cudaStream_t st);
 int prepare_sampling_tables(srm3_plan *p, cudaStream_t st);
 int stage_begin(srm3_plan *p, int stage, long long pair_terms, int *rec);

@@ -65,8 +65,9 @@ def batch_bytes_estimate(entries) -> float:
     (workload, samples, grouped) per plan of the batch, grouped when the
     plan joins a shape group (FP32, W recomputed, the plain pair set).  Per
     shape group with T samples, at most m from one plan: y + y0 = (n_kappa
-    (n_omega + 128) + 1) sspad(T) 8 bytes, C = 2 T n_kappa n_omega 8, H = m
-    n_kappa n_t 8, 16 T of factor pointers (the formula of
+    (n_omega + 128) + 1) sspad(T) 8 bytes, C = 2 T n_kappa n_omega 8, the
+    transform's intermediate m n_x n_omega 8, 16 T of factor pointers (the
+    formula of
     srm3_batch_device_bytes); per sample 8 bytes of seed and its output field;
     512 bytes per plan and 16 per work unit of descriptors and unit list."""
     groups = {}
@@ -83,7 +84,7 @@ def batch_bytes_estimate(entries) -> float:
             g[2] = max(g[2], n)
     for wl, T, m in groups.values():
         nk, nw = wl.n_kappa, wl.n_omega
-        total += 8.0 * ((nk * (nw + 128) + 1) * _sspad(T) + 2 * T * nk * nw + m * nk * wl.n_t)
+        total += 8.0 * ((nk * (nw + 128) + 1) * _sspad(T) + 2 * T * nk * nw + m * wl.n_x * nw)
         total += 16.0 * T
         total += 16 * nk * ((nw + 31) // 32) * (_sspad(T) // 64)
     return total

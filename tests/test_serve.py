@@ -120,8 +120,9 @@ def test_batch_bytes_estimate_adds_up():
     alone = serve.batch_bytes_estimate([(wl, 5, False), (wl, 3, False)])
     fields = 8 * (64 * 128 * 4 + 8)
     assert alone >= fields
-    # a shape group of 8 samples: y + y0 for 64 sheet-samples, C, H for 5
-    group = 8.0 * ((24 * (37 + 128) + 1) * 64 + 2 * 8 * 24 * 37 + 5 * 24 * 128) + 16 * 8
+    # a shape group of 8 samples: y + y0 for 64 sheet-samples, C, and the
+    # transform's intermediate (n_x n_omega) for 5
+    group = 8.0 * ((24 * (37 + 128) + 1) * 64 + 2 * 8 * 24 * 37 + 5 * 64 * 37) + 16 * 8
     assert grouped - alone >= group
 
 

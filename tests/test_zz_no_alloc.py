@@ -3,7 +3,7 @@
 
 Its fields are compared with those of srm3_field_from_coeffs (the existing
 entry point) on two calls in a row.  Both run one launch sequence (the same
-kernels, launch shapes and order; only the buffer of the t-stage rows
+kernels, launch shapes and order; only the buffer of the x-stage columns
 differs) and every set is transformed on its own, so the fields must be
 bit-identical: the tests compare with torch.equal, which also catches a
 change of grouping or launch shape that moves the last bits.  The file is
@@ -74,11 +74,12 @@ def test_noalloc_several_groups_and_no_device_allocation():
 
 @pytest.mark.gpu
 def test_noalloc_rejects_plan_beyond_scratch():
-    # 257 * 8192 complex FP64 values per set = 33.7 MB > 16 MiB of scratch.
-    wl = W.small_case(nk=257, nw=16, nx=512, nt=8192, precision="fp64")
+    # n_x * n_omega = 8192 * 257 complex FP64 values per set = 33.7 MB > 16 MiB
+    # of scratch.
+    wl = W.small_case(nk=16, nw=257, nx=8192, nt=1024, precision="fp64")
     with srm3.Plan.create(wl, eps=0.0) as p:
-        C = torch.zeros((1, 2, 257, 16, 2), dtype=torch.float64, device="cuda")
-        out = torch.zeros((1, 512, 8192), dtype=torch.float64, device="cuda")
+        C = torch.zeros((1, 2, 16, 257, 2), dtype=torch.float64, device="cuda")
+        out = torch.zeros((1, 8192, 1024), dtype=torch.float64, device="cuda")
         rc = srm3.load().srm3_field_from_coeffs_noalloc(
             p.handle, ctypes.c_void_p(C.data_ptr()), 1, ctypes.c_void_p(out.data_ptr()))
         assert rc == -1  # SRM3_ERR_INVALID_ARG
