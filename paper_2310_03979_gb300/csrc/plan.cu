@@ -89,6 +89,27 @@ __global__ void k_g2(int nk, int nw, const double *__restrict__ EkSq,
   G2_32[i] = (float)v;
 }
 
+// The Gaussian envelope of the recursion in separable form.  On the pairs of
+// a point, i + j = k, so with c = (n - 1)/2 per axis
+//   (i - j)^2 = 2 (i - c)^2 + 2 (j - c)^2 - (k - 2c)^2
+// and g^2(i, j) = exp(-(dk/s_k)^2 - (dw/s_w)^2) = a^2_i a^2_j b^2_k with
+//   a^2_i = exp(-2 ((ik - ck)/s_k)^2 - 2 ((iw - cw)/s_w)^2),
+//   b^2_k = exp(((kk - 2 ck)/s_k)^2 + ((kw - 2 cw)/s_w)^2).
+// Centring at c keeps a^2 in [exp(-E/2), 1] and b^2 in [1, exp(E)], E =
+// ((nk - 1)/s_k)^2 + ((nw - 1)/s_w)^2; every pair term stays a product of
+// positive factors, so the sums keep their relative accuracy.
+__global__ void k_gauss_sep(int nk, int nw, double sk, double sw, double *__restrict__ a2,
+                            double *__restrict__ b2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk * nw) return;
+  const int ik = i / nw, iw = i - ik * nw;
+  const double ck = 0.5 * (nk - 1), cw = 0.5 * (nw - 1);
+  const double uk = (ik - ck) / sk, uw = (iw - cw) / sw;
+  const double vk = (ik - 2.0 * ck) / sk, vw = (iw - 2.0 * cw) / sw;
+  a2[i] = exp(-2.0 * (uk * uk + uw * uw));
+  b2[i] = exp(vk * vk + vw * vw);
+}
+
 
 // Per-plane reductions (one CTA per plane): max sum_b2, min (1 - sum_b2)
 // over S > 0 and sum S into scal[8 + 4m + {1,2,3}].
@@ -253,6 +274,8 @@ struct PassResult {
 static thread_local cudaEvent_t t_ev[2] = {nullptr, nullptr};
 
 static constexpr int kPlanes = 8;  // eps values per FP32 search pass
+// largest exponent range of the separable Gaussian factors (k_gauss_sep)
+static constexpr double kSepExpMax = 40.0;
 // pinned host scalars of a plan build (8 + 4 kPlanes doubles): [0, kPlanes)
 // eps^2 dk dw per plane going in, [8, 8 + kPlanes) the planes' max sum_b2
 // coming back ([9] the linear pass's max), kSumSlot the sum of S
@@ -286,9 +309,33 @@ __global__ void k_bulk_pairs(int nk, int nw, int nlev, const int *__restrict__ s
 // Resident-block counts of the recursion kernels per device (they depend on
 // the kernel and its shared memory only).
 struct RecOccupancy {
-  int nsm = 0, b64 = 0, b64x3 = 0, b32 = 0, b64f = 0, b32f = 0;
+  int nsm = 0, b64 = 0, b32 = 0, b64f = 0, b32f = 0;
 };
 
+template <bool SEP>
+static int rec_occupancy_of(RecOccupancy &o) {
+  int b64 = 0, b64f = 0, b32 = 0, b32f = 0;
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1, SEP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes, SEP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1, SEP>,
+                                                          kRecThreads, 0));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64f, k_rec_pass<double, 1, SEP>,
+                                                          kRecThreads, kRecSmem));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes, SEP>,
+                                                          kRecThreads, 0));
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32f, k_rec_pass<float, kPlanes, SEP>,
+                                                          kRecThreads, kRecSmem));
+  o.b64 = std::min(o.b64, b64);
+  o.b64f = std::min(o.b64f, b64f);
+  o.b32 = std::min(o.b32, b32);
+  o.b32f = std::min(o.b32f, b32f);
+  return SRM3_OK;
+}
+
+// Resident CTAs per SM of every recursion kernel variant (the minimum over
+// the plain and separable forms), per device.
 static int rec_occupancy(int dev, RecOccupancy *out) {
   static std::mutex mu;
   static RecOccupancy cache[64];
@@ -297,21 +344,11 @@ static int rec_occupancy(int dev, RecOccupancy *out) {
   if (dev < 0 || dev >= 64) return fail(SRM3_ERR_NOT_SUPPORTED, "device ordinal beyond 64");
   if (!have[dev]) {
     RecOccupancy o;
-    SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
-    SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+    o.b64 = o.b64f = o.b32 = o.b32f = 1 << 30;
     SRM3_CUDA(cudaDeviceGetAttribute(&o.nsm, cudaDevAttrMultiProcessorCount, dev));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64, k_rec_pass<double, 1>,
-                                                            kRecThreads, 0));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64f, k_rec_pass<double, 1>,
-                                                            kRecThreads, kRecSmem));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b64x3, k_rec_pass<double, 3>,
-                                                            kRecThreads, 0));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b32, k_rec_pass<float, kPlanes>,
-                                                            kRecThreads, 0));
-    SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.b32f, k_rec_pass<float, kPlanes>,
-                                                            kRecThreads, kRecSmem));
+    int rc = rec_occupancy_of<false>(o);
+    if (!rc) rc = rec_occupancy_of<true>(o);
+    if (rc) return rc;
     cache[dev] = o;
     have[dev] = true;
   }
@@ -393,17 +430,17 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + kSumSlot, p->scal + 11, sizeof(double),
                             cudaMemcpyDeviceToHost, st));
   p->sumS = -1.0;  // not read yet
-  // barrier counter, a ticket per bulk phase, and a readiness counter per
-  // level (the fringe)
+  // barrier counter, a ticket per bulk phase, and the fringe progress of
+  // every lattice row
   p->rec_bar_tickets = 2 + (nk + nw) / kRecBL + 1;
-  p->rec_bar_words = p->rec_bar_tickets + nlev;
+  p->rec_bar_words = p->rec_bar_tickets + nk;
   SRM3_CUDA(dev_alloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
   RecOccupancy occ;
   int rc = rec_occupancy(p->device, &occ);
   if (rc) return rc;
   const bool f = p->rec_fft;
-  if ((f ? occ.b64f : occ.b64) < 1 || occ.b64x3 < 1 || (f ? occ.b32f : occ.b32) < 1)
+  if ((f ? occ.b64f : occ.b64) < 1 || (f ? occ.b32f : occ.b32) < 1)
     return fail(SRM3_ERR_CUDA, "recursion kernel cannot be resident");
   const int nsm = occ.nsm;
   SRM3_CUDA(dev_alloc(&p->qm3, 3 * (size_t)nk * nw * sizeof(double), st));
@@ -431,12 +468,12 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.pairs = p->rec_pairs;
   A.pair_off = p->rec_pair_off;
   A.S = p->S;
-  if (p->sep && fp64 && M != 1)
-    return fail(SRM3_ERR_NOT_SUPPORTED, "separable envelope: one-plane FP64 passes only");
-  A.q = !fp64 ? (void *)p->qm32 : (M == 1 ? (p->sep ? (void *)p->qh : (void *)p->qm) : (void *)p->qm3);
-  A.e2 = p->sep ? p->env_e2 : nullptr;
-  A.e2k = p->sep ? p->env_b2 : nullptr;
-  A.qout = (p->sep && fp64) ? p->qm : nullptr;
+  if (fp64 && M != 1) return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes one plane");
+  const bool sepf = p->rec_sep;
+  A.q = !fp64 ? (void *)p->qm32 : (sepf ? (void *)p->qh : (void *)p->qm);
+  A.e2 = sepf ? (p->sep ? p->env_e2 : p->rs_a2) : nullptr;
+  A.e2k = sepf ? (p->sep ? p->env_b2 : p->rs_b2) : nullptr;
+  A.qout = (sepf && fp64) ? p->qm : nullptr;
   A.dsum = (p->mixed && fp64 && M == 1) ? p->Dsum : nullptr;
   A.acc = p->rec_partial;
   A.sb2 = p->sb2;
@@ -444,7 +481,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.scal = p->scal;
   A.err = p->err;
   A.bar = p->rec_bar;
-  A.done = p->rec_bar + p->rec_bar_tickets;
+  A.row_done = p->rec_bar + p->rec_bar_tickets;
   A.abort = p->err + kPlanes;
   A.maxb = p->rec_max;
   A.zr = p->rec_fft ? p->rec_z : nullptr;
@@ -454,17 +491,12 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   const int smem = p->rec_fft ? kRecSmem : 0;
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
-  if (fp64 && M == 1)
-    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 1>, p->rec_grid64,
-                                          kRecThreads, args, smem, st));
-  else if (fp64 && M == 3)
-    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<double, 3>, p->rec_grid64,
-                                          kRecThreads, args, 0, st));
-  else if (fp64)
-    return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes 1 or 3 planes");
-  else
-    SRM3_CUDA(cudaLaunchCooperativeKernel((const void *)k_rec_pass<float, kPlanes>,
-                                          p->rec_grid32, kRecThreads, args, smem, st));
+  const void *kern = fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>
+                                  : (const void *)k_rec_pass<double, 1, false>)
+                          : (sepf ? (const void *)k_rec_pass<float, kPlanes, true>
+                                  : (const void *)k_rec_pass<float, kPlanes, false>);
+  SRM3_CUDA(cudaLaunchCooperativeKernel(kern, fp64 ? p->rec_grid64 : p->rec_grid32, kRecThreads,
+                                        args, smem, st));
   SRM3_CUDA(cudaGetLastError());
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, M * sizeof(unsigned long long),
@@ -1069,6 +1101,16 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     }
   } else {
     k_g2<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->EkSq, p->EwSq, p->G2, p->G2_32);
+    if (p->rec_sep) {
+      // Gaussian envelope in separable form for the recursion (the sampling
+      // path keeps W = c_k g(i, j))
+      SRM3_CUDA(dev_alloc(&p->rs_a2, nl * sizeof(double), st));
+      SRM3_CUDA(dev_alloc(&p->rs_b2, nl * sizeof(double), st));
+      SRM3_CUDA(dev_alloc(&p->qh, nl * sizeof(double), st));
+      SRM3_CUDA(cudaMemsetAsync(p->qh, 0, nl * sizeof(double), st));
+      k_gauss_sep<<<cdiv(nl, 256), 256, 0, st>>>(nk, nw, p->sigma_g * nk, p->sigma_g * nw,
+                                                 p->rs_a2, p->rs_b2);
+    }
   }
   SRM3_CUDA(cudaGetLastError());
 
@@ -1343,7 +1385,8 @@ void free_plan(srm3_plan *p) {
                  p->tw_conv, p->Zc, p->rec_z, p->tw_rec32, p->tw_rec64,
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr,
-                 p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d};
+                 p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d,
+                 p->rs_a2, p->rs_b2};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)
@@ -1448,6 +1491,16 @@ SRM3_API int srm3_plan_create(const srm3_spectrum *spectrum, const srm3_bispectr
   p->row_lo = all_rows ? 0 : g.row_begin;
   p->row_hi = all_rows ? g.n_kappa : g.row_end;
   p->sigma_g = p->sep ? 0.25 : bispectrum->sigma_g;
+  {
+    // the separable form of the Gaussian envelope needs the exponent range
+    // E of its factors to fit the FP32 search passes (products down to
+    // exp(-E), b^2 up to exp(E)); wider ranges (sigma_g below ~0.22) keep
+    // the g^2 table
+    const double sk = p->sigma_g * g.n_kappa, sw = p->sigma_g * g.n_omega;
+    const double E = (g.n_kappa - 1) * (g.n_kappa - 1) / (sk * sk) +
+                     (g.n_omega - 1) * (g.n_omega - 1) / (sw * sw);
+    p->rec_sep = p->sep || (!p->mixed && E <= kSepExpMax);
+  }
   p->beta = bispectrum->beta;
   p->table_budget = g.table_budget_bytes > 0 ? g.table_budget_bytes : 64.0 * (1ull << 30);
   cudaGetDevice(&p->device);

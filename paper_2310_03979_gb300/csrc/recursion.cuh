@@ -48,7 +48,7 @@ struct RecArgs {
   const double *dsum;
   int *err;             // [M]: some S_p <= 0 on this plane
   unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
-  unsigned int *done;   // [nlev]: points finalized on each fringe level (zero at launch)
+  unsigned int *row_done;  // [nk]: 1 + the last fringe level each lattice row has finished (zero at launch)
   int *abort;           // barrier wait timed out
   unsigned long long *maxb;  // [M]: max_k sum_b2 per plane, as the bits of a double >= 0
 };
@@ -93,52 +93,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, int *abort, unsi
   return s_ok != 0;
 }
 
-// Readiness of the fringe levels.  A point of level d in a fringe block
-// needs the q of its pair partners on levels [D, d): instead of a grid
-// barrier per level, each finalized point adds 1 to done[d] (release, after
-// a warp barrier over the lanes that wrote its planes), and a warp that
-// needs level l polls done[l] with acquire loads (lane 0, then a warp
-// barrier) until it holds the level's point count.  Levels complete in
-// order -- a point waits for the level below it before it is finalized -- so
-// level l complete means every level below it is too.  Waits are bounded
-// like the grid barrier; a warp that gives up (or sees another's abort)
-// raises the abort state, skips its remaining points and meets the next grid
-// barrier, which then fails for every CTA.
-__host__ __device__ __forceinline__ int level_points(int nk, int nw, int lev) {
-  return min(lev, nk - 1) - max(0, lev - nw + 1) + 1;
-}
-
-__device__ __forceinline__ bool wait_level(const unsigned int *done, unsigned int *bar,
-                                           int *abort, int want, int lev, int lane,
-                                           long long limit = 1ll << 22) {
-  int ok = 1;
-  if (lane == 0) {
-    unsigned int v;
-    long long spins = 0;
-    for (;;) {
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(done + lev) : "memory");
-      if (v >= (unsigned)want) break;
-      if ((++spins & 255) == 0 && *(volatile int *)abort) {
-        ok = 0;
-        break;
-      }
-      if (spins > limit) {
-        ok = 0;
-        atomicOr(bar, kBarAbort);
-        atomicExch(abort, 1);
-        break;
-      }
-    }
-  }
-  __syncwarp();
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void publish_level(unsigned int *done, int lev, int lane) {
-  __syncwarp();
-  if (lane == 0) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(done + lev) : "memory");
-}
-
 template <typename T, int M>
 struct PlaneVec;
 template <>
@@ -167,20 +121,27 @@ struct PlaneVec<float, 8> {
   }
 };
 
-// One pair term g^2(i, j) q_i q_j added to acc (all planes).
-template <typename T, int M>
+// One pair term g^2(i, j) q_i q_j added to acc (all planes).  SEP: the
+// pair factor is carried by h = a^2 q (g^2 = a_i^2 a_j^2 b_k^2), so the term
+// is h_i h_j and no g^2 is read.
+template <typename T, int M, bool SEP>
 __device__ __forceinline__ void add_pair(const RecArgs &A, int kk, int kw, int ia, int iw, int ja,
                                          int jw, T (&acc)[M]) {
   const int nw = A.nw;
-  const T *G2 = static_cast<const T *>(A.G2);
   const T *q = static_cast<const T *>(A.q);
-  const int dk = 2 * ia - kk, dw = 2 * iw - kw;
-  const T g2 = G2[(size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw)];
   T va[M], vb[M];
   PlaneVec<T, M>::load(q + ((size_t)ia * nw + iw) * M, va);
   PlaneVec<T, M>::load(q + ((size_t)ja * nw + jw) * M, vb);
+  if constexpr (SEP) {
 #pragma unroll
-  for (int m = 0; m < M; ++m) acc[m] = fma(g2, va[m] * vb[m], acc[m]);
+    for (int m = 0; m < M; ++m) acc[m] = fma(va[m], vb[m], acc[m]);
+  } else {
+    const T *G2 = static_cast<const T *>(A.G2);
+    const int dk = 2 * ia - kk, dw = 2 * iw - kw;
+    const T g2 = G2[(size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw)];
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = fma(g2, va[m] * vb[m], acc[m]);
+  }
 }
 
 template <typename T, int M>
@@ -207,7 +168,9 @@ __device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, in
   atomicMax(A.maxb + m, (unsigned long long)__double_as_longlong((double)s2));
   if (s2 < (T)1) {
     const T qk = (T)1 / ((T)1 - s2);
-    q[k * M + m] = A.e2 ? ek2 * qk : qk;
+    // separable forms: h_0 = 0 (the origin is never part of a pair), so
+    // that masked pair slots, which read the origin, add nothing
+    q[k * M + m] = A.e2 ? (k == 0 ? (T)0 : ek2 * qk) : qk;
     if (A.qout) A.qout[k] = (double)qk;
   } else {
     q[k * M + m] = (T)0;
@@ -235,7 +198,7 @@ __device__ __forceinline__ void point_zero(const RecArgs &A, long long k, int la
 // Levels below kRecBL: the whole canonical pair sum of the point (one warp),
 // rows a <= kk/2 laid end to end as a*(kw+1) + iw, the centre row a = kk - a
 // keeping iw <= kw/2, i = 0 skipped.
-template <typename T, int M>
+template <typename T, int M, bool SEP>
 __device__ void point_direct(const RecArgs &A, int kk, int kw, int lane) {
   const long long k = (long long)kk * A.nw + kw;
   if (!(A.S[k] > 0.0)) {
@@ -250,7 +213,7 @@ __device__ void point_direct(const RecArgs &A, int kk, int kw, int lane) {
     const int a = e / W, iw = e - a * W, b = kk - a;
     const int lim = (a == b) ? kw / 2 : kw;
     if ((a == 0 && iw == 0) || iw > lim) continue;
-    add_pair<T, M>(A, kk, kw, a, iw, b, kw - iw, acc);
+    add_pair<T, M, SEP>(A, kk, kw, a, iw, b, kw - iw, acc);
   }
   warp_sum<T, M>(acc);
   if (lane == 0) finalize<T, M>(A, k, acc);
@@ -274,7 +237,7 @@ constexpr int kBulkUnroll = 4;
 // < n with i = (a0 + v, iw0 - v) and j = k - i; uok: the lane's omega slot
 // lies inside the sliver.  Offsets step linearly with v; the canonical
 // limits (centre row, i != 0, iw <= kw) mask the rest.
-template <typename T, int M>
+template <typename T, int M, bool SEP>
 __device__ __forceinline__ void bulk_rows(int kk, int kw, int nw, const T *__restrict__ G2,
                                           const T *__restrict__ q, int n, int v0, int a0,
                                           int iw0, bool uok, T (&acc)[M]) {
@@ -292,18 +255,23 @@ __device__ __forceinline__ void bulk_rows(int kk, int kw, int nw, const T *__res
       const int gi = ok ? (dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
       const int qa = ok ? qa0 + vs * qstep : 0;
       const int qb = ok ? qb0 - vs * qstep : 0;
-      g2[s] = ok ? G2[gi] : (T)0;
+      if constexpr (!SEP) g2[s] = ok ? G2[gi] : (T)0;
       PlaneVec<T, M>::load(q + qa, va[s]);
       PlaneVec<T, M>::load(q + qb, vb[s]);
     }
 #pragma unroll
     for (int s = 0; s < kBulkUnroll; ++s)
 #pragma unroll
-      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
+      for (int m = 0; m < M; ++m) {
+        if constexpr (SEP)
+          acc[m] = fma(va[s][m], vb[s][m], acc[m]);
+        else
+          acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
+      }
   }
 }
 
-template <typename T, int M>
+template <typename T, int M, bool SEP>
 __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   const long long k = (long long)kk * A.nw + kw;
   if (!(A.S[k] > 0.0)) return;
@@ -326,9 +294,9 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
   // rows v = nR + m: left sliver, j = (kk - aL0 - m, base - kk + aL0 + m + u).
   // Each lane takes the rows of its parity rs, right then left: the order of
   // one sequence over v.
-  bulk_rows<T, M>(kk, kw, nw, G2, q, nR, rs, aR0, base - aR0 + u, u >= uR0, acc);
-  bulk_rows<T, M>(kk, kw, nw, G2, q, nL, (rs + nR) & 1, aL0, kw - base + kk - aL0 - u, u >= uL0,
-                  acc);
+  bulk_rows<T, M, SEP>(kk, kw, nw, G2, q, nR, rs, aR0, base - aR0 + u, u >= uR0, acc);
+  bulk_rows<T, M, SEP>(kk, kw, nw, G2, q, nL, (rs + nR) & 1, aL0, kw - base + kk - aL0 - u,
+                       u >= uL0, acc);
   warp_sum<T, M>(acc);
   if (lane == 0) {
     T *ac = static_cast<T *>(A.acc);
@@ -351,7 +319,7 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
 // a masked slot reading point (0, 0) with weight 0.
 constexpr int kPairUnroll = 2;
 
-template <bool RIGHT, typename T, int M>
+template <bool RIGHT, typename T, int M, bool SEP>
 __device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__restrict__ G2,
                                            const T *__restrict__ q, int base, int u, int rs,
                                            const int (&alo)[2], const int (&ahi)[2],
@@ -381,7 +349,7 @@ __device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__re
       const int qh = any ? (RIGHT ? (a * nw + hw) * M : (b * nw + hw) * M) : 0;
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        g2[s][p] = okp[p] ? G2[gi[p]] : (T)0;
+        if constexpr (!SEP) g2[s][p] = okp[p] ? G2[gi[p]] : (T)0;
         PlaneVec<T, M>::load(q + ql[p], vl[s][p]);
       }
       PlaneVec<T, M>::load(q + qh, vh[s]);
@@ -390,13 +358,18 @@ __device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__re
     for (int s = 0; s < kPairUnroll; ++s)
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        acc0[m] = fma(g2[s][0], vh[s][m] * vl[s][0][m], acc0[m]);
-        acc1[m] = fma(g2[s][1], vh[s][m] * vl[s][1][m], acc1[m]);
+        if constexpr (SEP) {
+          acc0[m] = fma(vh[s][m], vl[s][0][m], acc0[m]);
+          acc1[m] = fma(vh[s][m], vl[s][1][m], acc1[m]);
+        } else {
+          acc0[m] = fma(g2[s][0], vh[s][m] * vl[s][0][m], acc0[m]);
+          acc1[m] = fma(g2[s][1], vh[s][m] * vl[s][1][m], acc1[m]);
+        }
       }
   }
 }
 
-template <typename T, int M>
+template <typename T, int M, bool SEP>
 __device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, int lane) {
   const int base = D - kRecBL, arow = kk / 2 + 1, nw = A.nw;
   const int u = lane & (kRecBL - 1), rs = lane >> 4;
@@ -424,9 +397,9 @@ __device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, 
   const T *G2 = static_cast<const T *>(A.G2);
   const T *q = static_cast<const T *>(A.q);
   if (max(aRhi[0], aRhi[1]) >= 0)
-    bulk_rows2<true, T, M>(kk, kw, nw, G2, q, base, u, rs, aRlo, aRhi, uR, acc0, acc1);
+    bulk_rows2<true, T, M, SEP>(kk, kw, nw, G2, q, base, u, rs, aRlo, aRhi, uR, acc0, acc1);
   if (max(aLhi[0], aLhi[1]) >= 0)
-    bulk_rows2<false, T, M>(kk, kw, nw, G2, q, base, u, rs, aLlo, aLhi, uL, acc0, acc1);
+    bulk_rows2<false, T, M, SEP>(kk, kw, nw, G2, q, base, u, rs, aLlo, aLhi, uL, acc0, acc1);
   warp_sum<T, M>(acc0);
   warp_sum<T, M>(acc1);
   if (lane == 0) {
@@ -442,16 +415,17 @@ __device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, 
 
 constexpr int kFringeUnroll = 4;
 
-// Fringe pairs e in [e_begin, e_end) of a point: e enumerates the low
-// element l level by level (levels 1..l hold l (l + 3) / 2 points), the
-// pair being {l, k - l}.
-template <typename T, int M>
-__device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, int e_begin,
-                                             int e_end, int lane, T (&acc)[M]) {
+// Fringe pairs of a point whose low element l = (lk, lw) has lw >= 1: e in
+// [0, e_end) enumerates l level by level (levels 1..t hold t (t + 3) / 2
+// points), the pair being {l, k - l}; the pairs with lw = 0 are masked
+// (fringe_column takes them).
+template <typename T, int M, bool SEP>
+__device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, int e_end,
+                                             int lane, T (&acc)[M]) {
   const int nw = A.nw;
   const T *G2 = static_cast<const T *>(A.G2);
   const T *q = static_cast<const T *>(A.q);
-  for (int e0 = e_begin + lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
+  for (int e0 = lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
     T g2[kFringeUnroll], va[kFringeUnroll][M], vb[kFringeUnroll][M];
 #pragma unroll
     for (int s = 0; s < kFringeUnroll; ++s) {
@@ -464,19 +438,109 @@ __device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, i
       const int rem = e - (l - 1) * (l + 2) / 2;
       const int lk = rem, lw = l - rem;
       const int hk = kk - lk, hw = kw - lw;
-      const bool ok = e < e_end && hk >= 0 && hw >= 0;
-      const int dk = 2 * lk - kk, dw = 2 * lw - kw;
-      const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+      const bool ok = e < e_end && lw >= 1 && hk >= 0 && hw >= 0;
       const size_t qa = ok ? ((size_t)lk * nw + lw) * M : 0;
       const size_t qb = ok ? ((size_t)hk * nw + hw) * M : 0;
-      g2[s] = ok ? G2[gi] : (T)0;
+      if constexpr (!SEP) {
+        const int dk = 2 * lk - kk, dw = 2 * lw - kw;
+        const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
+        g2[s] = ok ? G2[gi] : (T)0;
+      }
       PlaneVec<T, M>::load(q + qa, va[s]);
       PlaneVec<T, M>::load(q + qb, vb[s]);
     }
 #pragma unroll
     for (int s = 0; s < kFringeUnroll; ++s)
 #pragma unroll
-      for (int m = 0; m < M; ++m) acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
+      for (int m = 0; m < M; ++m) {
+        if constexpr (SEP)
+          acc[m] = fma(va[s][m], vb[s][m], acc[m]);
+        else
+          acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
+      }
+  }
+}
+
+// The fringe pairs {(lk, 0), (kk - lk, kw)}, lk = 1..t (t < 32), one lane each.
+template <typename T, int M, bool SEP>
+__device__ __forceinline__ void fringe_column(const RecArgs &A, int kk, int kw, int t, int lane,
+                                              T (&acc)[M]) {
+  const int nw = A.nw, lk = lane + 1;
+  const bool ok = lk <= t && lk <= kk;
+  const T *q = static_cast<const T *>(A.q);
+  T va[M], vb[M];
+  PlaneVec<T, M>::load(q + (ok ? (size_t)lk * nw * M : 0), va);
+  PlaneVec<T, M>::load(q + (ok ? ((size_t)(kk - lk) * nw + kw) * M : 0), vb);
+  if constexpr (SEP) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = fma(va[m], vb[m], acc[m]);
+  } else {
+    const T *G2 = static_cast<const T *>(A.G2);
+    const int dk = 2 * lk - kk;
+    const T g2 = ok ? G2[(size_t)(dk < 0 ? -dk : dk) * nw + kw] : (T)0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = fma(g2, va[m] * vb[m], acc[m]);
+  }
+}
+
+// The fringe runs by lattice rows: warp w of a CTA walks row kk = row0 + w
+// (row0 = kRowWarps g for the CTA's row group g) through the block's levels
+// in order.  A point (kk, kw) on level d needs, besides points of its own
+// row (finished earlier by the same warp), the point (kk - 1, kw) on level
+// d - 1 (the pair {(1, 0), k - (1, 0)}) and points (kk - lk, kw - lw) with
+// lk, lw >= 1 on levels <= d - 2.  Finishing (kk - 1, kw) required (kk - 2,
+// kw) finished, and so on down the rows, so row kk - 1 having finished level
+// d - 1 implies that row kk - lk has finished level d - lk, and row kk - 1
+// having finished level d - 2 (the point (kk - 1, kw - 1)) that row kk - lk
+// has finished level d - 1 - lk: one wait on the row below covers every
+// lower row.  Levels below the block are complete at its start (grid
+// barrier).  A row's progress (1 + its last finished level) is kept in
+// shared memory for the next warp of the CTA and, for the CTA's last row, in
+// row_done for the first warp of the next row group.  Waits are bounded like
+// the grid barrier; a warp that gives up raises the abort state and the grid
+// barrier after the block then fails for every CTA.
+constexpr int kRowWarps = kRecThreads / 32;
+
+__device__ __forceinline__ bool wait_row(const RecArgs &A, const volatile unsigned int *s_done,
+                                         int row, int row0, int lev, int lane,
+                                         long long limit = 1ll << 22) {
+  int ok = 1;
+  if (lane == 0) {
+    long long spins = 0;
+    for (;;) {
+      unsigned int v;
+      if (row >= row0)
+        v = s_done[row - row0];
+      else
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(A.row_done + row)
+                     : "memory");
+      if (v > (unsigned int)lev) break;
+      if ((++spins & 255) == 0 && *(volatile int *)A.abort) {
+        ok = 0;
+        break;
+      }
+      if (spins > limit) {
+        ok = 0;
+        atomicOr(A.bar, kBarAbort);
+        atomicExch(A.abort, 1);
+        break;
+      }
+    }
+    __threadfence_block();
+  }
+  __syncwarp();
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void publish_row(const RecArgs &A, volatile unsigned int *s_done, int w,
+                                            int kk, int d, int lane) {
+  __syncwarp();
+  if (lane == 0) {
+    if (w == kRowWarps - 1)
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(A.row_done + kk), "r"(d + 1)
+                   : "memory");
+    __threadfence_block();
+    s_done[w] = (unsigned int)(d + 1);
   }
 }
 
@@ -484,18 +548,18 @@ __device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, i
 // element lies on a level in [D, d).  Their other element l has level
 // 1 .. d - D < BL <= D, so each such pair is {l, k - l} for exactly one
 // low lattice point l: the t(t+3)/2 points of levels 1..t, t = d - D.
-// The pairs with l on levels 2..t (higher element on levels [D, d - 2]) are
-// summed once level d - 2 is complete, the two with l on level 1 -- (0, 1)
-// and (1, 0), higher element on level d - 1 -- once level d - 1 is: most of
-// a point's fringe overlaps the finalisation of the level below it.  Adds
-// the bulk sums, finalizes the point and publishes it.  Returns false when
-// a readiness wait gave up (the point is then left unpublished).
-template <typename T, int M>
-__device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) {
+// The pairs with lw >= 1 are summed once row kk - 1 has finished level
+// d - 2, the t with lw = 0 once it has finished level d - 1: most of a
+// point's fringe overlaps the finalisation of the point below it.  Adds
+// the bulk sums, finalizes the point and publishes the row's progress.
+// Returns false when a wait gave up (the point is then left unpublished).
+template <typename T, int M, bool SEP>
+__device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int row0, int w,
+                             volatile unsigned int *s_done, int lane) {
   const long long k = (long long)kk * A.nw + kw;
   // S_k is read beside the pair loads rather than ahead of them: a point
   // with S_k = 0 sums its (finite) terms like any other and is zeroed at
-  // the end, which keeps one memory round trip off the level's critical path
+  // the end, which keeps one memory round trip off the critical path
   const double Sk = A.S[k];
   // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
   T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
@@ -509,15 +573,13 @@ __device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
   T acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = (T)0;
-  if (t >= 2) {
-    if (!wait_level(A.done, A.bar, A.abort, level_points(A.nk, A.nw, d - 2), d - 2, lane))
-      return false;
-    fringe_pairs<T, M>(A, kk, kw, 2, t * (t + 3) / 2, lane, acc);
+  if (t >= 1 && kw >= 1) {
+    if (kk >= 1 && d - 2 >= D && !wait_row(A, s_done, kk - 1, row0, d - 2, lane)) return false;
+    fringe_pairs<T, M, SEP>(A, kk, kw, t * (t + 3) / 2, lane, acc);
   }
-  if (t >= 1) {
-    if (!wait_level(A.done, A.bar, A.abort, level_points(A.nk, A.nw, d - 1), d - 1, lane))
-      return false;
-    fringe_pairs<T, M>(A, kk, kw, 0, 2, lane, acc);
+  if (t >= 1 && kk >= 1) {
+    if (!wait_row(A, s_done, kk - 1, row0, d - 1, lane)) return false;
+    fringe_column<T, M, SEP>(A, kk, kw, t, lane, acc);
   }
   warp_sum<T, M>(acc);
   if (!(Sk > 0.0)) {
@@ -529,8 +591,33 @@ __device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int lane) 
       if (m == lane) tt = acc[m];
     finalize_plane<T, M>(A, k, lane, tt + bulk);
   }
-  publish_level(A.done, d, lane);
+  publish_row(A, s_done, w, kk, d, lane);
   return true;
+}
+
+// The fringe of block [D, D + BL): row groups of kRowWarps rows over the
+// CTAs (group g on CTA g - g_lo mod gridDim.x, a CTA's groups in increasing
+// order, so every wait is on a group started earlier).  Returns false when a
+// wait gave up.
+template <typename T, int M, bool SEP>
+__device__ bool fringe_rows(const RecArgs &A, int D, volatile unsigned int *s_done, int lane) {
+  const int w = threadIdx.x >> 5;
+  const int dend = min(D + kRecBL, A.nlev);
+  const int r_lo = max(0, D - A.nw + 1), r_hi = min(A.nk - 1, dend - 1);
+  const int g_lo = r_lo / kRowWarps, g_hi = r_hi / kRowWarps;
+  bool live = true;
+  for (int g = g_lo + (int)blockIdx.x; g <= g_hi; g += gridDim.x) {  // uniform over the CTA
+    const int row0 = g * kRowWarps, kk = row0 + w;
+    if (lane == 0) s_done[w] = 0;
+    __syncthreads();
+    if (kk >= r_lo && kk <= r_hi) {
+      const int kw0 = max(0, D - kk), kw1 = min(A.nw - 1, dend - 1 - kk);
+      for (int kw = kw0; kw <= kw1 && live; ++kw)
+        live = point_fringe<T, M, SEP>(A, kk, kw, D, row0, w, s_done, lane);
+    }
+    __syncthreads();
+  }
+  return live;
 }
 
 // ---- separable envelope: the bulk as an online FFT self-convolution ----
@@ -667,8 +754,11 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
 // point's sums are formed by one warp at a time in a fixed order, so the
 // result does not depend on scheduling.  T = double, M = 1 is the exact
 // pass; T = float, M = 8 evaluates eight eps values at once to locate eps.
-template <typename T, int M>
+// SEP: the envelope is separable on i + j = k (g^2 = a_i^2 a_j^2 b_k^2), q
+// holds h = a^2 q and the pair terms are h_i h_j (no g^2 read).
+template <typename T, int M, bool SEP>
 __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
+  __shared__ unsigned int s_done[kRowWarps];
   const int lane = threadIdx.x & 31;
   // consecutive points (neighbours on a level, of similar cost) go to
   // different SMs
@@ -688,7 +778,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
   const int d0 = min(kRecBL, A.nlev);
   for (int d = 0; d < d0; ++d) {
     const int lo = max(0, d - A.nw + 1), n = min(d, A.nk - 1) - lo + 1;
-    for (int i = gw; i < n; i += nwarps) point_direct<T, M>(A, lo + i, d - lo - i, lane);
+    for (int i = gw; i < n; i += nwarps) point_direct<T, M, SEP>(A, lo + i, d - lo - i, lane);
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
   for (int D = kRecBL, ph = 1; D < A.nlev; D += kRecBL, ++ph) {
@@ -717,25 +807,18 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
         if constexpr (kPairs) {
           const int2 pt = A.pairs[pb + t];
           const bool has1 = pt.y + 1 <= min(A.nw - 1, dend - 1 - pt.x);
-          point2_bulk<T, M>(A, pt.x, pt.y, has1, D, lane);
+          point2_bulk<T, M, SEP>(A, pt.x, pt.y, has1, D, lane);
         } else {
           const int2 pt = A.pts[pb + t];
-          point_bulk<T, M>(A, pt.x, pt.y, D, lane);
+          point_bulk<T, M, SEP>(A, pt.x, pt.y, D, lane);
         }
         t = __shfl_sync(0xffffffffu, tn, 0);
       }
       if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
-    // fringe levels: readiness counters instead of a grid barrier per level
-    // (a warp that gave up skips its remaining points; the grid barrier
-    // after the block then fails for every CTA)
-    const int dend = min(D + kRecBL, A.nlev);
-    bool live = true;
-    for (int d = D; d < dend && live; ++d) {
-      const int lo = max(0, d - A.nw + 1), n = min(d, A.nk - 1) - lo + 1;
-      for (int i = gw; i < n && live; i += nwarps)
-        live = point_fringe<T, M>(A, lo + i, d - lo - i, D, lane);
-    }
+    // fringe levels by lattice rows (a warp that gave up skips its remaining
+    // points; the grid barrier after the block then fails for every CTA)
+    fringe_rows<T, M, SEP>(A, D, s_done, lane);
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
 }

@@ -102,6 +102,10 @@ struct srm3_plan {
   float *env_b32 = nullptr;
   bool sep_b = false;                           // b has tables of its own
   double *qh = nullptr;                         // h = e^2 q of the FP64 passes
+  // the recursion in separable form: the separable kind, or the Gaussian
+  // envelope split on i + j = k (a^2 per point in rs_a2, b^2 in rs_b2)
+  bool rec_sep = false;
+  double *rs_a2 = nullptr, *rs_b2 = nullptr;
   // FFT self-convolution grid of the separable pair sum (powers of two,
   // cNk >= 2 nk - 1, cNw >= 2 nw - 1), its twiddles e^{+2 pi i j / ntwc},
   // and the workspace of zc_ss sheet-samples (complex, plan precision)
