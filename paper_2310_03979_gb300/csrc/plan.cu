@@ -111,6 +111,37 @@ __global__ void k_gauss_sep(int nk, int nw, double sk, double sw, double *__rest
 }
 
 
+// dsb2[k] = (sb2 of plane m1 - sb2 of plane m0) / (x1 - x0): the slope in x
+// of every point's sum_b2 between two FP32 search planes.
+__global__ void k_sb2_slope(long long n, const double *__restrict__ s0,
+                            const double *__restrict__ s1, double inv_dx,
+                            double *__restrict__ dsb2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dsb2[i] = (s1[i] - s0[i]) * inv_dx;
+}
+
+// The tables of an FP64 pass at x moved to x + dx to first order: sum_b2 +=
+// dx dsb2 (clamped at 0), q = 1/(1 - sum_b2) (0 where S = 0, or where
+// sum_b2 >= 1, which also sets *err); max_k sum_b2 into *maxb (bits of a
+// double >= 0, zeroed before).
+__global__ void k_sb2_shift(long long n, const double *__restrict__ S, double *__restrict__ sb2,
+                            const double *__restrict__ dsb2, double dx, double *__restrict__ q,
+                            unsigned long long *maxb, int *err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (!(S[i] > 0.0)) return;  // zero tables, as the pass left them
+  double v = fma(dx, dsb2[i], sb2[i]);
+  v = v < 0.0 ? 0.0 : v;
+  sb2[i] = v;
+  atomicMax(maxb, (unsigned long long)__double_as_longlong(v));
+  if (v < 1.0) {
+    q[i] = 1.0 / (1.0 - v);
+  } else {
+    q[i] = 0.0;
+    atomicOr(err, 1);
+  }
+}
+
 // Per-plane reductions (one CTA per plane): max sum_b2, min (1 - sum_b2)
 // over S > 0 and sum S into scal[8 + 4m + {1,2,3}].
 __global__ void k_reduce_planes(long long n, const double *__restrict__ S,
@@ -276,6 +307,10 @@ static thread_local cudaEvent_t t_ev[2] = {nullptr, nullptr};
 static constexpr int kPlanes = 8;  // eps values per FP32 search pass
 // largest exponent range of the separable Gaussian factors (k_gauss_sep)
 static constexpr double kSepExpMax = 40.0;
+// targets at least this loose may take the first-order table shift of
+// find_eps, for steps up to kShiftMax of x
+static constexpr double kShiftTol = 1e-10;
+static constexpr double kShiftMax = 1e-5;
 // pinned host scalars of a plan build (8 + 4 kPlanes doubles): [0, kPlanes)
 // eps^2 dk dw per plane going in, [8, 8 + kPlanes) the planes' max sum_b2
 // coming back ([9] the linear pass's max), kSumSlot the sum of S
@@ -315,18 +350,17 @@ struct RecOccupancy {
 template <bool SEP>
 static int rec_occupancy_of(RecOccupancy &o) {
   int b64 = 0, b64f = 0, b32 = 0, b32f = 0;
+  constexpr int sm = kRecSmem + kFringeSmem;
   SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 1, SEP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes, SEP>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRecSmem));
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1, SEP>,
-                                                          kRecThreads, 0));
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64f, k_rec_pass<double, 1, SEP>,
-                                                          kRecThreads, kRecSmem));
+                                                          kRecThreads, sm));
+  b64f = b64;
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes, SEP>,
-                                                          kRecThreads, 0));
-  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32f, k_rec_pass<float, kPlanes, SEP>,
-                                                          kRecThreads, kRecSmem));
+                                                          kRecThreads, sm));
+  b32f = b32;
   o.b64 = std::min(o.b64, b64);
   o.b64f = std::min(o.b64f, b64f);
   o.b32 = std::min(o.b32, b32);
@@ -488,7 +522,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.twr = fp64 ? p->tw_rec64 : p->tw_rec32;
   A.log2Nc = p->rec_log2Nc;
   A.zcap = kRecSmem / (fp64 ? (int)sizeof(double2) : (int)sizeof(float2));
-  const int smem = p->rec_fft ? kRecSmem : 0;
+  const int smem = kRecSmem + kFringeSmem;  // the FFT form's grids and the fringe's state
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
   const void *kern = fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>
@@ -717,6 +751,26 @@ static int find_eps_mixed(srm3_plan *p, cudaStream_t st, double target, double t
   return SRM3_OK;
 }
 
+// The tables of the last FP64 pass (sum_b2 plane 0, q) moved by dx in x to
+// first order with the slopes in p->dsb2; r: the new max_k sum_b2 and
+// whether some sum_b2 reached 1.
+static int shift_tables(srm3_plan *p, cudaStream_t st, double dx, PassResult *r) {
+  const long long nl = (long long)p->nk * p->nw;
+  SRM3_CUDA(cudaMemsetAsync(p->rec_max, 0, sizeof(unsigned long long), st));
+  SRM3_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+  k_sb2_shift<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->sb2, p->dsb2, dx, p->qm, p->rec_max,
+                                             p->err);
+  SRM3_CUDA(cudaGetLastError());
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st));
+  SRM3_CUDA(cudaMemcpyAsync(p->h_err, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  r->max_sb2 = p->h_pinned[8];  // the bits of a double, copied as such
+  r->min_pure = 1.0 - r->max_sb2;
+  r->err = p->h_err[0];
+  return SRM3_OK;
+}
+
 // eps from max_k sum_b2 = target.  The linear pass (q == 1) gives the
 // bracket [0, target / max L], since q >= 1 makes x L an under-estimate of
 // sum_b2.  FP32 passes, each evaluating kPlanes values of x at once, cut
@@ -862,6 +916,34 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     }
   }
 
+  // Loose targets (FP32 plans, tol >= kShiftTol): the slope in x of every
+  // point's sum_b2, from the two planes of the last FP32 pass around x32.
+  // After the FP64 pass at x32 the Newton root x1 is typically within 1e-7
+  // x32; the tables are then moved there to first order, sum_b2(x1) =
+  // sum_b2(x32) + (x1 - x32) dsb2 and q = 1/(1 - sum_b2), instead of a
+  // second pass.  The error is the FP32 slope's (~1e-3 relative) times the
+  // step plus the curvature term, ~1e-10 relative at a 1e-7 step, far below
+  // the FP32 rounding of the tables these plans sample with; the result is
+  // accepted only when its max_k sum_b2 meets the target within tol.  The
+  // slopes need FP32 sums accurate relative to each point: not the FFT form
+  // of the separable bulk, whose rounding is bounded relative to the largest
+  // sums only (it keeps the second FP64 pass).
+  bool shift_ok = false;
+  if (tol >= kShiftTol && !p->rec_fft && hi_ok && slope32 > 0.0) {
+    int m = -1;
+    for (int i = 0; i + 1 < kPlanes && m < 0; ++i)
+      if (xs[i] <= x32 && x32 <= xs[i + 1] && !r[i].err && !r[i + 1].err) m = i;
+    if (m >= 0) {
+      const long long nl = (long long)p->nk * p->nw;
+      if (!p->dsb2) SRM3_CUDA(dev_alloc(&p->dsb2, nl * sizeof(double), st));
+      k_sb2_slope<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->sb2 + (size_t)m * nl,
+                                                 p->sb2 + (size_t)(m + 1) * nl,
+                                                 1.0 / (xs[m + 1] - xs[m]), p->dsb2);
+      SRM3_CUDA(cudaGetLastError());
+      shift_ok = true;
+    }
+  }
+
   // FP64 stage: Newton steps from x32 with the FP32 slope, then secant steps
   // on the FP64 values, all inside an FP64 bracket; Illinois if they leave
   // it or stall.
@@ -871,6 +953,7 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   bool converged = false, at_best = false;
   double x = x32, xp = 0.0, fp = 0.0;
   bool have_prev = false;
+  p->eps_shifted = false;
   for (int it = 0; it < 6; ++it) {
     PassResult q1;
     rc = run_pass(p, st, x, true, &q1);
@@ -898,6 +981,23 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     if (std::fabs(f) <= tol) {
       converged = true;
       break;
+    }
+    if (it == 0 && shift_ok) {
+      const double x1 = x - f / slope32;
+      if (x1 > b.xlo && (b.hi_failed || x1 < b.xhi) && std::fabs(x1 - x) <= kShiftMax * x) {
+        PassResult q2;
+        rc = shift_tables(p, st, x1 - x, &q2);
+        if (rc) return rc;
+        at_best = false;  // the tables have left x
+        if (!q2.err && std::fabs(q2.max_sb2 - target) <= tol) {
+          q2.sumS = q1.sumS;
+          best = q2;
+          xbest = x1;
+          at_best = converged = true;
+          p->eps_shifted = true;
+          break;
+        }
+      }
     }
     const double s = (have_prev && f != fp) ? (f - fp) / (x - xp) : slope32;
     if (!(s > 0.0)) break;
@@ -1386,7 +1486,7 @@ void free_plan(srm3_plan *p) {
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr,
                  p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d,
-                 p->rs_a2, p->rs_b2};
+                 p->rs_a2, p->rs_b2, p->dsb2};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)

@@ -152,38 +152,48 @@ __device__ __forceinline__ void warp_sum(T (&v)[M]) {
 }
 
 // q_k and sum_b2(k) of plane m from the point's complete pair sum t.
+// 1/x, correctly rounded (the same value as the division)
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
+// ek2 = a_k^2, bk2 = b_k^2 (1 for non-separable envelopes), ds: the
+// difference-pair sum of mixed plans (0 otherwise).
 template <typename T, int M>
-__device__ __forceinline__ void finalize_plane(const RecArgs &A, long long k, int m, T t) {
+__device__ __forceinline__ T finalize_plane(const RecArgs &A, long long k, int m, T t, double ek2d,
+                                            double bk2d, double ds) {
   T *q = static_cast<T *>(A.q);
-  const T ek2 = A.e2 ? (T)A.e2[k] : (T)1;    // a_k^2
-  const T bk2 = A.e2k ? (T)A.e2k[k] : (T)1;  // b_k^2
+  const T ek2 = (T)ek2d, bk2 = (T)bk2d;
   // t >= 0 (a sum of non-negative terms) up to the rounding of the FFT form,
   // which can leave a small negative value, of the order of the rounding of
   // the largest sums, where every term is zero; a NaN passes through
-  if (M == 1 && A.dsum) t += (T)A.dsum[k];
+  if (M == 1 && A.dsum) t += (T)ds;
   const T s2r = (T)A.scal[m] * bk2 * t;
   const T s2 = s2r < (T)0 ? (T)0 : s2r;
   A.sb2[m * A.nl + k] = (double)s2;
   // non-negative doubles order as their bit patterns
   atomicMax(A.maxb + m, (unsigned long long)__double_as_longlong((double)s2));
   if (s2 < (T)1) {
-    const T qk = (T)1 / ((T)1 - s2);
+    const T qk = recip_rn((T)1 - s2);
     // separable forms: h_0 = 0 (the origin is never part of a pair), so
     // that masked pair slots, which read the origin, add nothing
-    q[k * M + m] = A.e2 ? (k == 0 ? (T)0 : ek2 * qk) : qk;
+    const T h = A.e2 ? (k == 0 ? (T)0 : ek2 * qk) : qk;
+    q[k * M + m] = h;
     if (A.qout) A.qout[k] = (double)qk;
-  } else {
-    q[k * M + m] = (T)0;
-    if (A.qout) A.qout[k] = 0.0;
-    atomicOr(A.err + m, 1);
+    return h;
   }
+  q[k * M + m] = (T)0;
+  if (A.qout) A.qout[k] = 0.0;
+  atomicOr(A.err + m, 1);
+  return (T)0;
 }
 
 // All planes of a point (lane 0 only).
 template <typename T, int M>
 __device__ __forceinline__ void finalize(const RecArgs &A, long long k, const T (&t)[M]) {
+  const double ek2 = A.e2 ? A.e2[k] : 1.0, bk2 = A.e2k ? A.e2k[k] : 1.0;
+  const double ds = (M == 1 && A.dsum) ? A.dsum[k] : 0.0;
 #pragma unroll
-  for (int m = 0; m < M; ++m) finalize_plane<T, M>(A, k, m, t[m]);
+  for (int m = 0; m < M; ++m) finalize_plane<T, M>(A, k, m, t[m], ek2, bk2, ds);
 }
 
 template <typename T, int M>
@@ -413,76 +423,6 @@ __device__ void point2_bulk(const RecArgs &A, int kk, int kw, bool has1, int D, 
   }
 }
 
-constexpr int kFringeUnroll = 4;
-
-// Fringe pairs of a point whose low element l = (lk, lw) has lw >= 1: e in
-// [0, e_end) enumerates l level by level (levels 1..t hold t (t + 3) / 2
-// points), the pair being {l, k - l}; the pairs with lw = 0 are masked
-// (fringe_column takes them).
-template <typename T, int M, bool SEP>
-__device__ __forceinline__ void fringe_pairs(const RecArgs &A, int kk, int kw, int e_end,
-                                             int lane, T (&acc)[M]) {
-  const int nw = A.nw;
-  const T *G2 = static_cast<const T *>(A.G2);
-  const T *q = static_cast<const T *>(A.q);
-  for (int e0 = lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
-    T g2[kFringeUnroll], va[kFringeUnroll][M], vb[kFringeUnroll][M];
-#pragma unroll
-    for (int s = 0; s < kFringeUnroll; ++s) {
-      // e -> level l of the low point and its place rem on that level
-      const int e = e0 + 32 * s;
-      int l = (int)ceilf((sqrtf(9.f + 8.f * (float)(e + 1)) - 3.f) * 0.5f);
-      l = max(l, 1);
-      while (l * (l + 3) / 2 <= e) ++l;
-      while (l > 1 && (l - 1) * (l + 2) / 2 > e) --l;
-      const int rem = e - (l - 1) * (l + 2) / 2;
-      const int lk = rem, lw = l - rem;
-      const int hk = kk - lk, hw = kw - lw;
-      const bool ok = e < e_end && lw >= 1 && hk >= 0 && hw >= 0;
-      const size_t qa = ok ? ((size_t)lk * nw + lw) * M : 0;
-      const size_t qb = ok ? ((size_t)hk * nw + hw) * M : 0;
-      if constexpr (!SEP) {
-        const int dk = 2 * lk - kk, dw = 2 * lw - kw;
-        const size_t gi = ok ? (size_t)(dk < 0 ? -dk : dk) * nw + (dw < 0 ? -dw : dw) : 0;
-        g2[s] = ok ? G2[gi] : (T)0;
-      }
-      PlaneVec<T, M>::load(q + qa, va[s]);
-      PlaneVec<T, M>::load(q + qb, vb[s]);
-    }
-#pragma unroll
-    for (int s = 0; s < kFringeUnroll; ++s)
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        if constexpr (SEP)
-          acc[m] = fma(va[s][m], vb[s][m], acc[m]);
-        else
-          acc[m] = fma(g2[s], va[s][m] * vb[s][m], acc[m]);
-      }
-  }
-}
-
-// The fringe pairs {(lk, 0), (kk - lk, kw)}, lk = 1..t (t < 32), one lane each.
-template <typename T, int M, bool SEP>
-__device__ __forceinline__ void fringe_column(const RecArgs &A, int kk, int kw, int t, int lane,
-                                              T (&acc)[M]) {
-  const int nw = A.nw, lk = lane + 1;
-  const bool ok = lk <= t && lk <= kk;
-  const T *q = static_cast<const T *>(A.q);
-  T va[M], vb[M];
-  PlaneVec<T, M>::load(q + (ok ? (size_t)lk * nw * M : 0), va);
-  PlaneVec<T, M>::load(q + (ok ? ((size_t)(kk - lk) * nw + kw) * M : 0), vb);
-  if constexpr (SEP) {
-#pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] = fma(va[m], vb[m], acc[m]);
-  } else {
-    const T *G2 = static_cast<const T *>(A.G2);
-    const int dk = 2 * lk - kk;
-    const T g2 = ok ? G2[(size_t)(dk < 0 ? -dk : dk) * nw + kw] : (T)0;
-#pragma unroll
-    for (int m = 0; m < M; ++m) acc[m] = fma(g2, va[m] * vb[m], acc[m]);
-  }
-}
-
 // The fringe runs by lattice rows: warp w of a CTA walks row kk = row0 + w
 // (row0 = kRowWarps g for the CTA's row group g) through the block's levels
 // in order.  A point (kk, kw) on level d needs, besides points of its own
@@ -499,7 +439,106 @@ __device__ __forceinline__ void fringe_column(const RecArgs &A, int kk, int kw, 
 // row_done for the first warp of the next row group.  Waits are bounded like
 // the grid barrier; a warp that gives up raises the abort state and the grid
 // barrier after the block then fails for every CTA.
+//
+// The values a point reads are on chip where they can be: the h (or q) of
+// the group's points on the block's levels (written there as they are
+// finalized), the lattice corner (levels < BL: the low element of every
+// fringe pair), and each point's S and bulk sum (prefetched at the block's
+// start).  Only partners on rows below the group come from global memory,
+// through L2 (they were written by another SM).
 constexpr int kRowWarps = kRecThreads / 32;
+
+template <typename T, int M>
+struct FringeSmem {
+  T band[kRowWarps][kRecBL][M];    // by (row - row0, level - D)
+  T corner[kRecBL][kRecBL][M];     // h(lk, lw) for lk + lw < BL, else 0
+  T bulk[kRowWarps][kRecBL][M];    // bulk sum of the row's point on level D + t
+  double S[kRowWarps][kRecBL];
+  double e2[kRowWarps][kRecBL];    // a_k^2, b_k^2 (separable forms), difference sums (mixed)
+  double e2k[kRowWarps][kRecBL];
+  double ds[kRowWarps][kRecBL];
+};
+constexpr int kFringeSmem = 32768;  // bytes, the larger of the FP32 and FP64 layouts
+static_assert(sizeof(FringeSmem<float, 8>) <= kFringeSmem &&
+                  sizeof(FringeSmem<double, 1>) <= kFringeSmem,
+              "fringe shared memory");
+
+// M planes of a point from shared or global memory (generic address); the
+// global ones are read through L2 (ld.cg), never from a stale L1 line.
+template <typename T, int M>
+struct PlaneLd;
+template <>
+struct PlaneLd<float, 8> {
+  static __device__ __forceinline__ void smem(const float *p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4 *>(p)[0];
+    const float4 b = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  static __device__ __forceinline__ void gmem(const float *p, float (&v)[8]) {
+    const float4 a = __ldcg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldcg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <>
+struct PlaneLd<double, 1> {
+  static __device__ __forceinline__ void smem(const double *p, double (&v)[1]) { v[0] = *p; }
+  static __device__ __forceinline__ void gmem(const double *p, double (&v)[1]) { v[0] = __ldcg(p); }
+};
+
+// One fringe pair {l, k - l}, l = (lk, lw): the partner p = k - l on level
+// d - |l| from the band (rows of the group) or from global memory, zero
+// when the pair does not exist (ok false); then its term into acc, with h_l
+// from the corner.  The loads of several pairs are issued before their terms.
+template <typename T, int M>
+__device__ __forceinline__ void fringe_load(const RecArgs &A, const FringeSmem<T, M> &F, int kk,
+                                            int kw, int D, int w, int lk, int lw, bool ok,
+                                            T (&vp)[M]) {
+  if (!ok) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) vp[m] = (T)0;
+    return;
+  }
+  const int ep = kk + kw - lk - lw - D;  // level of the partner - D
+  if (lk <= w)
+    PlaneLd<T, M>::smem(&F.band[w - lk][ep][0], vp);
+  else
+    PlaneLd<T, M>::gmem(static_cast<const T *>(A.q) + ((size_t)(kk - lk) * A.nw + kw - lw) * M,
+                        vp);
+}
+
+template <typename T, int M, bool SEP>
+__device__ __forceinline__ void fringe_fma(const RecArgs &A, const FringeSmem<T, M> &F, int kk,
+                                           int kw, int lk, int lw, bool ok, const T (&vp)[M],
+                                           T (&acc)[M]) {
+  T vl[M];
+  PlaneLd<T, M>::smem(&F.corner[ok ? lk : 0][ok ? lw : 0][0], vl);
+  if constexpr (SEP) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = fma(vl[m], vp[m], acc[m]);
+  } else {
+    const int dk = 2 * lk - kk, dw = 2 * lw - kw;
+    const T g2 = ok ? static_cast<const T *>(A.G2)[(size_t)(dk < 0 ? -dk : dk) * A.nw +
+                                                     (dw < 0 ? -dw : dw)]
+                    : (T)0;
+#pragma unroll
+    for (int m = 0; m < M; ++m) acc[m] = fma(g2, vl[m] * vp[m], acc[m]);
+  }
+}
+
+// e -> the low point l = (lk, lw) of the e-th fringe pair: levels 1..L of
+// the corner hold L (L + 3) / 2 points, enumerated level by level
+__device__ __forceinline__ int2 fringe_point(int e) {
+  int l = (int)ceilf((sqrtf(9.f + 8.f * (float)(e + 1)) - 3.f) * 0.5f);
+  l = max(l, 1);
+  while (l * (l + 3) / 2 <= e) ++l;
+  while (l > 1 && (l - 1) * (l + 2) / 2 > e) --l;
+  const int lk = e - (l - 1) * (l + 2) / 2;
+  return make_int2(lk, l - lk);
+}
+constexpr int kFringeUnroll = 3;
 
 __device__ __forceinline__ bool wait_row(const RecArgs &A, const volatile unsigned int *s_done,
                                          int row, int row0, int lev, int lane,
@@ -551,45 +590,59 @@ __device__ __forceinline__ void publish_row(const RecArgs &A, volatile unsigned 
 // The pairs with lw >= 1 are summed once row kk - 1 has finished level
 // d - 2, the t with lw = 0 once it has finished level d - 1: most of a
 // point's fringe overlaps the finalisation of the point below it.  Adds
-// the bulk sums, finalizes the point and publishes the row's progress.
+// the bulk sum, finalizes the point and publishes the row's progress.
 // Returns false when a wait gave up (the point is then left unpublished).
 template <typename T, int M, bool SEP>
-__device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int row0, int w,
-                             volatile unsigned int *s_done, int lane) {
+__device__ bool point_fringe(const RecArgs &A, FringeSmem<T, M> &F, int kk, int kw, int D,
+                             int row0, int w, volatile unsigned int *s_done, int lane) {
   const long long k = (long long)kk * A.nw + kw;
-  // S_k is read beside the pair loads rather than ahead of them: a point
-  // with S_k = 0 sums its (finite) terms like any other and is zeroed at
-  // the end, which keeps one memory round trip off the critical path
-  const double Sk = A.S[k];
-  // lane m < M finalizes plane m; its bulk sum is loaded ahead of the pairs
-  T bulk = lane < M ? static_cast<const T *>(A.acc)[k * M + lane] : (T)0;
-  if (A.zr && lane < M && ((kk | kw) & 1) == 0) {
-    // FFT form: the bulk holds half the ordered pairs; the pair {k/2, k/2}
-    // enters the unordered sum once
-    const T hh = static_cast<const T *>(A.q)[((long long)(kk >> 1) * A.nw + (kw >> 1)) * M + lane];
-    bulk += (T)0.5 * hh * hh;
-  }
   const int d = kk + kw, t = d - D;
   T acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = (T)0;
   if (t >= 1 && kw >= 1) {
     if (kk >= 1 && d - 2 >= D && !wait_row(A, s_done, kk - 1, row0, d - 2, lane)) return false;
-    fringe_pairs<T, M, SEP>(A, kk, kw, t * (t + 3) / 2, lane, acc);
+    // e enumerates l level by level; lw = 0 is left to the column below
+    const int e_end = t * (t + 3) / 2;
+    for (int e0 = lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
+      T vp[kFringeUnroll][M];
+      int2 lp[kFringeUnroll];
+      bool ok[kFringeUnroll];
+#pragma unroll
+      for (int s = 0; s < kFringeUnroll; ++s) {
+        const int e = e0 + 32 * s;
+        lp[s] = fringe_point(e);
+        ok[s] = e < e_end && lp[s].y >= 1 && lp[s].x <= kk && lp[s].y <= kw;
+        fringe_load<T, M>(A, F, kk, kw, D, w, lp[s].x, lp[s].y, ok[s], vp[s]);
+      }
+#pragma unroll
+      for (int s = 0; s < kFringeUnroll; ++s)
+        fringe_fma<T, M, SEP>(A, F, kk, kw, lp[s].x, lp[s].y, ok[s], vp[s], acc);
+    }
   }
   if (t >= 1 && kk >= 1) {
     if (!wait_row(A, s_done, kk - 1, row0, d - 1, lane)) return false;
-    fringe_column<T, M, SEP>(A, kk, kw, t, lane, acc);
+    // the pairs {(lk, 0), (kk - lk, kw)}, lk = 1..t, one lane each
+    const int lk = lane + 1;
+    const bool ok = lk <= t && lk <= kk;
+    T vp[M];
+    fringe_load<T, M>(A, F, kk, kw, D, w, lk, 0, ok, vp);
+    fringe_fma<T, M, SEP>(A, F, kk, kw, lk, 0, ok, vp, acc);
   }
   warp_sum<T, M>(acc);
-  if (!(Sk > 0.0)) {
-    point_zero<T, M>(A, k, lane);
-  } else if (lane < M) {
-    T tt = (T)0;
+  if (lane < M) {
+    T h = (T)0;
+    if (!(F.S[w][t] > 0.0)) {
+      point_zero<T, M>(A, k, lane);
+    } else {
+      T tt = (T)0;
 #pragma unroll
-    for (int m = 0; m < M; ++m)
-      if (m == lane) tt = acc[m];
-    finalize_plane<T, M>(A, k, lane, tt + bulk);
+      for (int m = 0; m < M; ++m)
+        if (m == lane) tt = acc[m];
+      h = finalize_plane<T, M>(A, k, lane, tt + F.bulk[w][t][lane], F.e2[w][t], F.e2k[w][t],
+                               F.ds[w][t]);
+    }
+    F.band[w][t][lane] = h;
   }
   publish_row(A, s_done, w, kk, d, lane);
   return true;
@@ -600,7 +653,8 @@ __device__ bool point_fringe(const RecArgs &A, int kk, int kw, int D, int row0, 
 // order, so every wait is on a group started earlier).  Returns false when a
 // wait gave up.
 template <typename T, int M, bool SEP>
-__device__ bool fringe_rows(const RecArgs &A, int D, volatile unsigned int *s_done, int lane) {
+__device__ bool fringe_rows(const RecArgs &A, FringeSmem<T, M> &F, int D,
+                            volatile unsigned int *s_done, int lane) {
   const int w = threadIdx.x >> 5;
   const int dend = min(D + kRecBL, A.nlev);
   const int r_lo = max(0, D - A.nw + 1), r_hi = min(A.nk - 1, dend - 1);
@@ -612,12 +666,46 @@ __device__ bool fringe_rows(const RecArgs &A, int D, volatile unsigned int *s_do
     __syncthreads();
     if (kk >= r_lo && kk <= r_hi) {
       const int kw0 = max(0, D - kk), kw1 = min(A.nw - 1, dend - 1 - kk);
+      const int t0 = kk + kw0 - D, np = kw1 - kw0 + 1;
+      // S and the bulk sums of the row's points (written by other SMs before
+      // the grid barrier: read through L2); FFT form: half the diagonal term
+      for (int i = lane; i < np * M; i += 32) {
+        const int pi = i / M, m = i - pi * M, kw = kw0 + pi, t = t0 + pi;
+        const long long k = (long long)kk * A.nw + kw;
+        T b = __ldcg(static_cast<const T *>(A.acc) + k * M + m);
+        if (A.zr && ((kk | kw) & 1) == 0) {
+          const T hh = __ldcg(static_cast<const T *>(A.q) +
+                              ((long long)(kk >> 1) * A.nw + (kw >> 1)) * M + m);
+          b += (T)0.5 * hh * hh;
+        }
+        F.bulk[w][t][m] = b;
+        if (m == 0) {
+          F.S[w][t] = A.S[k];
+          F.e2[w][t] = A.e2 ? A.e2[k] : 1.0;
+          F.e2k[w][t] = A.e2k ? A.e2k[k] : 1.0;
+          F.ds[w][t] = (M == 1 && A.dsum) ? __ldcg(A.dsum + k) : 0.0;
+        }
+      }
+      __syncwarp();
       for (int kw = kw0; kw <= kw1 && live; ++kw)
-        live = point_fringe<T, M, SEP>(A, kk, kw, D, row0, w, s_done, lane);
+        live = point_fringe<T, M, SEP>(A, F, kk, kw, D, row0, w, s_done, lane);
     }
     __syncthreads();
   }
   return live;
+}
+
+// The lattice corner (levels < BL, final after the direct levels) into the
+// fringe's shared memory; visible after the next CTA barrier.
+template <typename T, int M>
+__device__ void load_corner(const RecArgs &A, FringeSmem<T, M> &F) {
+  for (int i = threadIdx.x; i < kRecBL * kRecBL * M; i += blockDim.x) {
+    const int lk = i / (kRecBL * M), lw = (i / M) % kRecBL, m = i % M;
+    T v = (T)0;
+    if (lk + lw < kRecBL && lk < A.nk && lw < A.nw)
+      v = __ldcg(static_cast<const T *>(A.q) + ((size_t)lk * A.nw + lw) * M + m);
+    F.corner[lk][lw][m] = v;
+  }
 }
 
 // ---- separable envelope: the bulk as an online FFT self-convolution ----
@@ -759,6 +847,9 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
 template <typename T, int M, bool SEP>
 __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
   __shared__ unsigned int s_done[kRowWarps];
+  // dynamic shared memory: kRecSmem for the FFT form's grids, then the fringe's
+  extern __shared__ __align__(16) unsigned char rec_smem[];
+  FringeSmem<T, M> &F = *reinterpret_cast<FringeSmem<T, M> *>(rec_smem + kRecSmem);
   const int lane = threadIdx.x & 31;
   // consecutive points (neighbours on a level, of similar cost) go to
   // different SMs
@@ -781,9 +872,9 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     for (int i = gw; i < n; i += nwarps) point_direct<T, M, SEP>(A, lo + i, d - lo - i, lane);
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
+  load_corner<T, M>(A, F);  // levels < BL are final: read after the next barrier
   for (int D = kRecBL, ph = 1; D < A.nlev; D += kRecBL, ++ph) {
     if (A.zr) {  // separable envelope: the bulk by one FFT product
-      extern __shared__ __align__(16) unsigned char rec_smem[];
       const int log2L = (31 - __clz(kRecBL)) + (__ffs(D / kRecBL) - 1);
       if (!sep_product<T, M>(A, D - (1 << log2L), log2L, g,
                              reinterpret_cast<typename Vec2<T>::type *>(rec_smem)))
@@ -818,7 +909,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     }
     // fringe levels by lattice rows (a warp that gave up skips its remaining
     // points; the grid barrier after the block then fails for every CTA)
-    fringe_rows<T, M, SEP>(A, D, s_done, lane);
+    fringe_rows<T, M, SEP>(A, F, D, s_done, lane);
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
 }

@@ -120,6 +120,8 @@ struct srm3_plan {
   int64_t diffpairs = 0;          // difference pairs of one sheet
   int fp_iters = 0;               // iterations of the last fixed-point solve
   double *Dsum = nullptr;         // difference-pair sums per point [nk*nw]
+  double *dsb2 = nullptr;         // d sum_b2 / dx per point from two FP32 search planes
+  bool eps_shifted = false;       // the final tables are an FP64 pass moved to eps to first order
   double *qprev = nullptr;        // previous iterate of q
   double *qlo = nullptr;          // converged q at qlo_x (warm start of the search)
   double qlo_x = -1.0;
