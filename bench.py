@@ -36,7 +36,7 @@ METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 l
 # super-tile), reads scaled by the W table size (x 15.41), writes by the
 # coefficient count (x 4).  Valid only for the kernel source it was measured
 # on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
-PAIRSUM_TRAFFIC = {"bytes": 665.51e6 * 15.41 + 31.88e6 * 4, "source_sha256": "564a3068d1dd846a"}
+PAIRSUM_TRAFFIC = {"bytes": 665.55e6 * 15.41 + 31.94e6 * 4, "source_sha256": "0890f2076167e26e"}
 FP32_LANES_PER_SM = 128
 
 
@@ -755,17 +755,22 @@ def main():
     t_last = recs[-1][0]
     chunks = math.ceil(n / 128)
     # kernels launched per step (matches the ncu launch list): spectrum 1,
-    # envelope tables 2 + g^2 1, recursion index lists 2, the sum of S 1,
-    # linear pass + reduction 2, each recursion pass 1, sampling tables 4,
-    # W table 1 if stored; per 128-sample chunk: phases, pair sum, two FFT
+    # envelope tables 2 + g^2 1, separable factors 1 (Gaussian envelope in
+    # separable form), recursion index lists 2, the sum of S 2, linear pass
+    # 2 + its reduction 2, each recursion pass 1, slope and move of the
+    # tables 2 (FP32 plans whose tables were moved), sampling tables 4, W
+    # table 1 if stored; per 128-sample chunk: phases, pair sum, two FFT
     # stages
-    launches_per_step = (1 + 3 + 2 + 1 + 2 + (info.root_passes + info.root_passes_fp32)
-                         + 4 + (1 if info.storage == 1 else 0) + 4 * chunks)
+    flags = info.recursion_flags
+    sep_gauss = 1 if (flags & srm3.SRM3_REC_SEPARABLE) and wl.envelope == "gauss" else 0
+    moved = 2 if flags & srm3.SRM3_REC_TABLES_MOVED else 0
+    launches_per_step = (1 + 3 + sep_gauss + 2 + 2 + 4 + (info.root_passes + info.root_passes_fp32)
+                         + moved + 4 + (1 if info.storage == 1 else 0) + 4 * chunks)
     if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
         # self-convolution passes, two output FFT stages
-        launches_per_step = (1 + 3 + 2 + 1 + (info.root_passes + info.root_passes_fp32)
+        launches_per_step = (1 + 3 + 2 + 2 + (info.root_passes + info.root_passes_fp32)
                              + 4 + 1 + 6 * chunks)
     if prebuilt is not None:
         # sampling only: per chunk phases, sum and difference pair sums, two

@@ -225,8 +225,17 @@ typedef struct srm3_info {
     int32_t tile_width;      /* FP32 pair-sum work unit: 32 or 16 outputs (the
                                 autotuner's choice for the lattice shape, else
                                 32); the results do not depend on it */
-    int32_t reserved2;
+    int32_t recursion_flags; /* bit 0 (SRM3_REC_SEPARABLE): the recursion ran in
+                                separable form, g^2(i,j) = a_i^2 a_j^2 b_k^2 on the
+                                pairs of k (the separable kind, or the Gaussian
+                                envelope split on i + j = k, Sec. 4.1 Eq. pure);
+                                bit 1 (SRM3_REC_TABLES_MOVED): the tables are those
+                                of the FP64 pass at the FP32 root estimate, moved to
+                                the final eps to first order (FP32 plans) */
 } srm3_info;
+
+#define SRM3_REC_SEPARABLE 1
+#define SRM3_REC_TABLES_MOVED 2
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
 

@@ -128,50 +128,81 @@ __global__ void k_sb2_shift(long long n, const double *__restrict__ S, double *_
                             const double *__restrict__ dsb2, double dx, double *__restrict__ q,
                             unsigned long long *maxb, int *err) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (!(S[i] > 0.0)) return;  // zero tables, as the pass left them
-  double v = fma(dx, dsb2[i], sb2[i]);
-  v = v < 0.0 ? 0.0 : v;
-  sb2[i] = v;
-  atomicMax(maxb, (unsigned long long)__double_as_longlong(v));
-  if (v < 1.0) {
-    q[i] = 1.0 / (1.0 - v);
-  } else {
-    q[i] = 0.0;
-    atomicOr(err, 1);
+  double v = 0.0;
+  if (i < n && S[i] > 0.0) {  // S = 0: zero tables, as the pass left them
+    v = fma(dx, dsb2[i], sb2[i]);
+    v = v < 0.0 ? 0.0 : v;
+    sb2[i] = v;
+    if (v < 1.0) {
+      q[i] = 1.0 / (1.0 - v);
+    } else {
+      q[i] = 0.0;
+      atomicOr(err, 1);
+    }
   }
+  double m = v;  // warp maximum first: one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(maxb, (unsigned long long)__double_as_longlong(m));
 }
 
-// Per-plane reductions (one CTA per plane): max sum_b2, min (1 - sum_b2)
-// over S > 0 and sum S into scal[8 + 4m + {1,2,3}].
-__global__ void k_reduce_planes(long long n, const double *__restrict__ S,
-                                const double *__restrict__ sb2, double *__restrict__ scal) {
-  const int m = blockIdx.x;
-  const double *v = sb2 + (size_t)m * n;
+// Reductions of plane 0 of sum_b2 and of S: max sum_b2, min (1 - sum_b2)
+// over S > 0 and sum S, into scal[9], scal[10], scal[11].  k_reduce_part
+// leaves one partial per CTA (kReduceCtas of them) and k_reduce_final
+// combines them in CTA order, so that the sum does not depend on scheduling.
+constexpr int kReduceCtas = 256;
+
+__global__ void __launch_bounds__(256) k_reduce_part(long long n, const double *__restrict__ S,
+                                                     const double *__restrict__ sb2,
+                                                     double *__restrict__ part) {
   double mx = 0.0, mn = 1.0, sum = 0.0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    mx = fmax(mx, v[i]);
-    if (S[i] > 0.0) mn = fmin(mn, 1.0 - v[i]);
-    sum += S[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = sb2[i], s = S[i];
+    mx = fmax(mx, v);
+    if (s > 0.0) mn = fmin(mn, 1.0 - v);
+    sum += s;
   }
   for (int o = 16; o > 0; o >>= 1) {
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
     sum += __shfl_xor_sync(0xffffffffu, sum, o);
   }
-  __shared__ double a[32], b[32], c[32];
+  __shared__ double a[8], b[8], c[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) { a[warp] = mx; b[warp] = mn; c[warp] = sum; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nwp = blockDim.x >> 5;
-    for (int w = 1; w < nwp; ++w) { mx = fmax(mx, a[w]); mn = fmin(mn, b[w]); }
+    for (int w = 1; w < 8; ++w) { mx = fmax(mx, a[w]); mn = fmin(mn, b[w]); }
     sum = 0.0;
-    for (int w = 0; w < nwp; ++w) sum += c[w];
-    scal[8 + 4 * m + 1] = mx;
-    scal[8 + 4 * m + 2] = mn;
-    scal[8 + 4 * m + 3] = sum;
+    for (int w = 0; w < 8; ++w) sum += c[w];
+    part[3 * blockIdx.x] = mx;
+    part[3 * blockIdx.x + 1] = mn;
+    part[3 * blockIdx.x + 2] = sum;
   }
+}
+
+__global__ void k_reduce_final(int nparts, const double *__restrict__ part,
+                               double *__restrict__ scal) {
+  if (threadIdx.x != 0) return;
+  double mx = 0.0, mn = 1.0, sum = 0.0;
+  for (int j = 0; j < nparts; ++j) {
+    mx = fmax(mx, part[3 * j]);
+    mn = fmin(mn, part[3 * j + 1]);
+    sum += part[3 * j + 2];
+  }
+  scal[9] = mx;
+  scal[10] = mn;
+  scal[11] = sum;
+}
+
+static int reduce_plane0(srm3_plan *p, cudaStream_t st) {
+  const long long nl = (long long)p->nk * p->nw;
+  if (!p->red_part) SRM3_CUDA(dev_alloc(&p->red_part, 3 * kReduceCtas * sizeof(double), st));
+  const int ctas = (int)std::min<long long>(kReduceCtas, (nl + 255) / 256);
+  k_reduce_part<<<ctas, 256, 0, st>>>(nl, p->S, p->sb2, p->red_part);
+  k_reduce_final<<<1, 32, 0, st>>>(ctas, p->red_part, p->scal);
+  return cudaGetLastError() == cudaSuccess ? SRM3_OK : fail(SRM3_ERR_CUDA, "plane reduction");
 }
 
 // ---------------------------------------------------------------------------
@@ -459,8 +490,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   // of the stream (run_pass_multi); the plane-0 results of this reduction
   // are not used
   SRM3_CUDA(cudaMemsetAsync(p->sb2, 0, (size_t)nk * nw * sizeof(double), st));
-  k_reduce_planes<<<1, 1024, 0, st>>>((long long)nk * nw, p->S, p->sb2, p->scal);
-  SRM3_CUDA(cudaGetLastError());
+  if (int rc0 = reduce_plane0(p, st)) return rc0;
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + kSumSlot, p->scal + 11, sizeof(double),
                             cudaMemcpyDeviceToHost, st));
   p->sumS = -1.0;  // not read yet
@@ -806,7 +836,7 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     k_rec_linear_sum<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm32, p->sb2, p->dkdw);
     SRM3_CUDA(cudaGetLastError());
     SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kLinParts * nl * sizeof(float), st));
-    k_reduce_planes<<<1, 1024, 0, st>>>((long long)p->nk * p->nw, p->S, p->sb2, p->scal);
+    if (int rc1 = reduce_plane0(p, st)) return rc1;
     SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double),
                               cudaMemcpyDeviceToHost, st));
     SRM3_CUDA(cudaStreamSynchronize(st));
@@ -1486,7 +1516,7 @@ void free_plan(srm3_plan *p) {
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr,
                  p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d,
-                 p->rs_a2, p->rs_b2, p->dsb2};
+                 p->rs_a2, p->rs_b2, p->dsb2, p->red_part};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)
@@ -1652,6 +1682,8 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->precision = plan->precision;
   info->tile_r = kTileR;
   info->tile_width = kTileR * plan->ps_nc;
+  info->recursion_flags = (plan->rec_sep ? SRM3_REC_SEPARABLE : 0) |
+                          (plan->eps_shifted ? SRM3_REC_TABLES_MOVED : 0);
   info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
   info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
   info->diff_pairs = plan->diffpairs;

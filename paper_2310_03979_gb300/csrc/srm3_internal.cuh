@@ -121,6 +121,7 @@ struct srm3_plan {
   int fp_iters = 0;               // iterations of the last fixed-point solve
   double *Dsum = nullptr;         // difference-pair sums per point [nk*nw]
   double *dsb2 = nullptr;         // d sum_b2 / dx per point from two FP32 search planes
+  double *red_part = nullptr;     // per-CTA partials of the plane reduction
   bool eps_shifted = false;       // the final tables are an FP64 pass moved to eps to first order
   double *qprev = nullptr;        // previous iterate of q
   double *qlo = nullptr;          // converged q at qlo_x (warm start of the search)

@@ -79,6 +79,9 @@ class srm3_grid(ctypes.Structure):
                 ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
 
 
+SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED = 1, 2  # srm3_info.recursion_flags
+
+
 class srm3_info(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_sum_b2", ctypes.c_double),
                 ("min_pure_ratio", ctypes.c_double), ("variance", ctypes.c_double),
@@ -88,7 +91,7 @@ class srm3_info(ctypes.Structure):
                 ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("fixed_point_iterations", ctypes.c_int32),
                 ("diff_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_double),
-                ("tile_width", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("tile_width", ctypes.c_int32), ("recursion_flags", ctypes.c_int32)]
 
 
 class srm3_timings(ctypes.Structure):

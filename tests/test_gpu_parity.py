@@ -67,6 +67,39 @@ def test_plan_tables_and_eps(oracle_lib, precision):
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=rel, atol=1e-15)
     assert info.variance == pytest.approx(op.moments()[0], rel=1e-12)
     assert np.all(q >= 1.0) and info.min_pure_ratio > 0
+    # the Gaussian envelope (sigma_g = 0.25) runs the recursion in separable
+    # form; FP32 plans take one FP64 pass and the first-order move of the
+    # tables to the root, FP64 plans exact passes to the end
+    assert info.recursion_flags & srm3.SRM3_REC_SEPARABLE
+    moved = bool(info.recursion_flags & srm3.SRM3_REC_TABLES_MOVED)
+    assert moved == (precision == "fp32")
+    if moved:
+        assert info.root_passes == 1
+
+
+@pytest.mark.parametrize("sigma_g,separable", [(0.15, False), (0.35, True)])
+def test_recursion_envelope_width(oracle_lib, sigma_g, separable):
+    """The Gaussian envelope splits as a^2_i a^2_j b^2_k on the pairs of a
+    point; the recursion uses the split while the factors' exponent range
+    ((Nk-1)/(sg Nk))^2 + ((Nw-1)/(sg Nw))^2 stays within 40, else the g^2
+    table.  Both forms against the oracle's g^2 at a common eps, through
+    several bulk phases and fringe blocks, and the eps search of an FP32
+    plan with its tables moved to the root."""
+    import dataclasses
+    wl = dataclasses.replace(W.small_case(nk=48, nw=72, nx=64, nt=256), sigma_g=sigma_g)
+    op = oracle_plan(wl)
+    with srm3.Plan.create(wl, eps=op.eps, precision="fp64") as p:
+        _, q, sb2 = p.tables()
+        assert bool(p.info().recursion_flags & srm3.SRM3_REC_SEPARABLE) == separable
+    np.testing.assert_allclose(q, op.q, rtol=2e-14)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
+    with srm3.Plan.create(wl, precision="fp32") as p:
+        _, q, sb2 = p.tables()
+        info = p.info()
+    assert info.eps == pytest.approx(op.eps, rel=2e-8)
+    assert abs(info.max_sum_b2 - wl.target) <= 1e-9
+    np.testing.assert_allclose(q, op.q, rtol=2e-8)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-8, atol=1e-15)
 
 
 @pytest.mark.parametrize("nk,nw", [(40, 33), (96, 64), (130, 20), (12, 200)])
