@@ -457,8 +457,12 @@ struct FringeSmem {
   double e2[kRowWarps][kRecBL];    // a_k^2, b_k^2 (separable forms), difference sums (mixed)
   double e2k[kRowWarps][kRecBL];
   double ds[kRowWarps][kRecBL];
+  // the low points (lk, lw), lw >= 1, of the fringe pairs in level order:
+  // the first t (t + 1) / 2 entries are those of a point t levels into its block
+  unsigned char pl[kRecBL * (kRecBL - 1) / 2][2];
+  int colnz;  // some corner point (lk, 0), 1 <= lk < BL, has h != 0
 };
-constexpr int kFringeSmem = 32768;  // bytes, the larger of the FP32 and FP64 layouts
+constexpr int kFringeSmem = 33792;  // bytes, the larger of the FP32 and FP64 layouts
 static_assert(sizeof(FringeSmem<float, 8>) <= kFringeSmem &&
                   sizeof(FringeSmem<double, 1>) <= kFringeSmem,
               "fringe shared memory");
@@ -528,16 +532,6 @@ __device__ __forceinline__ void fringe_fma(const RecArgs &A, const FringeSmem<T,
   }
 }
 
-// e -> the low point l = (lk, lw) of the e-th fringe pair: levels 1..L of
-// the corner hold L (L + 3) / 2 points, enumerated level by level
-__device__ __forceinline__ int2 fringe_point(int e) {
-  int l = (int)ceilf((sqrtf(9.f + 8.f * (float)(e + 1)) - 3.f) * 0.5f);
-  l = max(l, 1);
-  while (l * (l + 3) / 2 <= e) ++l;
-  while (l > 1 && (l - 1) * (l + 2) / 2 > e) --l;
-  const int lk = e - (l - 1) * (l + 2) / 2;
-  return make_int2(lk, l - lk);
-}
 constexpr int kFringeUnroll = 3;
 
 __device__ __forceinline__ bool wait_row(const RecArgs &A, const volatile unsigned int *s_done,
@@ -587,11 +581,14 @@ __device__ __forceinline__ void publish_row(const RecArgs &A, volatile unsigned 
 // element lies on a level in [D, d).  Their other element l has level
 // 1 .. d - D < BL <= D, so each such pair is {l, k - l} for exactly one
 // low lattice point l: the t(t+3)/2 points of levels 1..t, t = d - D.
-// The pairs with lw >= 1 are summed once row kk - 1 has finished level
-// d - 2, the t with lw = 0 once it has finished level d - 1: most of a
-// point's fringe overlaps the finalisation of the point below it.  Adds
-// the bulk sum, finalizes the point and publishes the row's progress.
-// Returns false when a wait gave up (the point is then left unpublished).
+// The t(t+1)/2 pairs with lw >= 1 are summed, reduced over the warp and
+// added to the bulk sum once row kk - 1 has finished level d - 2; the t with
+// lw = 0 (zero unless some corner point (lk, 0) has h != 0: the workloads'
+// spectra vanish at omega = 0) once it has finished level d - 1, which also
+// keeps the rows' progress a chain.  So after that last wait only the
+// finalisation (and, where they are not zero, the column pairs) remain.
+// Publishes the row's progress.  Returns false when a wait gave up (the
+// point is then left unpublished).
 template <typename T, int M, bool SEP>
 __device__ bool point_fringe(const RecArgs &A, FringeSmem<T, M> &F, int kk, int kw, int D,
                              int row0, int w, volatile unsigned int *s_done, int lane) {
@@ -602,8 +599,7 @@ __device__ bool point_fringe(const RecArgs &A, FringeSmem<T, M> &F, int kk, int 
   for (int m = 0; m < M; ++m) acc[m] = (T)0;
   if (t >= 1 && kw >= 1) {
     if (kk >= 1 && d - 2 >= D && !wait_row(A, s_done, kk - 1, row0, d - 2, lane)) return false;
-    // e enumerates l level by level; lw = 0 is left to the column below
-    const int e_end = t * (t + 3) / 2;
+    const int e_end = t * (t + 1) / 2;
     for (int e0 = lane; e0 < e_end; e0 += 32 * kFringeUnroll) {
       T vp[kFringeUnroll][M];
       int2 lp[kFringeUnroll];
@@ -611,8 +607,9 @@ __device__ bool point_fringe(const RecArgs &A, FringeSmem<T, M> &F, int kk, int 
 #pragma unroll
       for (int s = 0; s < kFringeUnroll; ++s) {
         const int e = e0 + 32 * s;
-        lp[s] = fringe_point(e);
-        ok[s] = e < e_end && lp[s].y >= 1 && lp[s].x <= kk && lp[s].y <= kw;
+        const int ec = e < e_end ? e : 0;
+        lp[s] = make_int2(F.pl[ec][0], F.pl[ec][1]);
+        ok[s] = e < e_end && lp[s].x <= kk && lp[s].y <= kw;
         fringe_load<T, M>(A, F, kk, kw, D, w, lp[s].x, lp[s].y, ok[s], vp[s]);
       }
 #pragma unroll
@@ -620,28 +617,34 @@ __device__ bool point_fringe(const RecArgs &A, FringeSmem<T, M> &F, int kk, int 
         fringe_fma<T, M, SEP>(A, F, kk, kw, lp[s].x, lp[s].y, ok[s], vp[s], acc);
     }
   }
+  warp_sum<T, M>(acc);  // every lane holds the sums of every plane
+  T tt = (T)0;
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+    if (m == lane) tt = acc[m];
+  if (lane < M) tt += F.bulk[w][t][lane];
   if (t >= 1 && kk >= 1) {
     if (!wait_row(A, s_done, kk - 1, row0, d - 1, lane)) return false;
-    // the pairs {(lk, 0), (kk - lk, kw)}, lk = 1..t, one lane each
-    const int lk = lane + 1;
-    const bool ok = lk <= t && lk <= kk;
-    T vp[M];
-    fringe_load<T, M>(A, F, kk, kw, D, w, lk, 0, ok, vp);
-    fringe_fma<T, M, SEP>(A, F, kk, kw, lk, 0, ok, vp, acc);
-  }
-  warp_sum<T, M>(acc);
-  if (lane < M) {
-    T h = (T)0;
-    if (!(F.S[w][t] > 0.0)) {
-      point_zero<T, M>(A, k, lane);
-    } else {
-      T tt = (T)0;
+    if (F.colnz) {  // the pairs {(lk, 0), (kk - lk, kw)}, lk = 1..t, one lane each
+      const int lk = lane + 1;
+      const bool ok = lk <= t && lk <= kk;
+      T vp[M], c[M];
+#pragma unroll
+      for (int m = 0; m < M; ++m) c[m] = (T)0;
+      fringe_load<T, M>(A, F, kk, kw, D, w, lk, 0, ok, vp);
+      fringe_fma<T, M, SEP>(A, F, kk, kw, lk, 0, ok, vp, c);
+      warp_sum<T, M>(c);
 #pragma unroll
       for (int m = 0; m < M; ++m)
-        if (m == lane) tt = acc[m];
-      h = finalize_plane<T, M>(A, k, lane, tt + F.bulk[w][t][lane], F.e2[w][t], F.e2k[w][t],
-                               F.ds[w][t]);
+        if (m == lane) tt += c[m];
     }
+  }
+  if (lane < M) {
+    T h = (T)0;
+    if (!(F.S[w][t] > 0.0))
+      point_zero<T, M>(A, k, lane);
+    else
+      h = finalize_plane<T, M>(A, k, lane, tt, F.e2[w][t], F.e2k[w][t], F.ds[w][t]);
     F.band[w][t][lane] = h;
   }
   publish_row(A, s_done, w, kk, d, lane);
@@ -705,6 +708,25 @@ __device__ void load_corner(const RecArgs &A, FringeSmem<T, M> &F) {
     if (lk + lw < kRecBL && lk < A.nk && lw < A.nw)
       v = __ldcg(static_cast<const T *>(A.q) + ((size_t)lk * A.nw + lw) * M + m);
     F.corner[lk][lw][m] = v;
+  }
+  if (threadIdx.x == 0) {  // pair table: level L = 1..BL-1, lk = 0..L-1, lw = L - lk
+    int e = 0;
+    for (int L = 1; L < kRecBL; ++L)
+      for (int lk = 0; lk < L; ++lk, ++e) {
+        F.pl[e][0] = (unsigned char)lk;
+        F.pl[e][1] = (unsigned char)(L - lk);
+      }
+    F.colnz = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // column points (lk, 0), 1 <= lk < BL
+    int nz = 0;
+    for (int i = threadIdx.x; i < (kRecBL - 1) * M; i += 32) {
+      const int lk = 1 + i / M, m = i % M;
+      nz |= F.corner[lk][0][m] != (T)0;
+    }
+    nz = __any_sync(0xffffffffu, nz);
+    if (threadIdx.x == 0) F.colnz = nz;
   }
 }
 
