@@ -417,15 +417,46 @@ def run_serve(args):
         b.sync()
         t_group = time.perf_counter() - t1
     del outs
-    rate = 0.7 * (len(pool) / t_group) / 0.1   # requests/s for 70 % of the large-class capacity
+    # and of the small class: one batch of two samples of every pool spectrum
+    plans_s = [cache.lookup(small(U, z)) for U, z in pool]
+    outs_s = [torch.empty((2, 64, 64), device="cuda") for _ in pool]
+    with srm3.Batch(plans_s, [2] * len(pool), outs_s) as b:
+        seeds_s = list(range(2 * len(pool)))
+        b.run(seeds_s)
+        b.sync()
+        t1 = time.perf_counter()
+        b.run(seeds_s)
+        b.sync()
+        t_small = (time.perf_counter() - t1) / (2 * len(pool))
+    del outs_s
+    # requests/s at which the GPU would be 70 % busy with the 10 % / 90 % mix,
+    # each class at the per-request cost of a full batch
+    rate0 = 0.7 / (0.1 * t_group / len(pool) + 0.9 * t_small)
+
+    def stream(n, rate, gen, rid0):
+        gaps = gen.exponential(1.0 / rate, size=n)
+        arrivals = np.cumsum(gaps) - gaps[0]
+        out = []
+        for i in range(n):
+            U, z = pool[int(gen.integers(0, len(pool)))]
+            wl = large(U, z) if gen.uniform() < 0.1 else small(U, z)
+            out.append(serve.Request(rid0 + i, wl, (rid0 + 1_000_000 + i,),
+                                     arrival=float(arrivals[i])))
+        return out
+
+    # a pilot stream (its own seed) at that rate measures how busy the server
+    # really keeps the GPU -- requests arriving alone are sampled alone, at
+    # more than a full batch's cost each -- and the rate is scaled to 70 %
+    pilot = serve.Server(budget_bytes=150e9, light_slots=1, heavy_slots=1, max_samples=512,
+                         cache=cache)
+    preqs = stream(max(500, args.requests // 10), rate0,
+                   np.random.Generator(np.random.PCG64(55)), 10_000_000)
+    pwall = pilot.run(preqs)
+    pbusy = pilot.busy / pwall
+    pilot.close()
+    rate = rate0 * min(1.5, max(0.2, 0.7 / max(pbusy, 1e-3)))
     nreq = args.requests
-    gaps = rng.exponential(1.0 / rate, size=nreq)
-    arrivals = np.cumsum(gaps) - gaps[0]
-    reqs = []
-    for i in range(nreq):
-        U, z = pool[int(rng.integers(0, len(pool)))]
-        wl = large(U, z) if rng.uniform() < 0.1 else small(U, z)
-        reqs.append(serve.Request(i, wl, (1_000_000 + i,), arrival=float(arrivals[i])))
+    reqs = stream(nreq, rate, rng, 0)
     srv = serve.Server(budget_bytes=150e9, light_slots=1, heavy_slots=1, max_samples=512,
                        cache=cache)
     host = {}
@@ -488,7 +519,9 @@ def run_serve(args):
         "busy_fraction": srv.busy / wall, "batches": srv.batches,
         "plan_cache": {"warm_build_s": t_warm, "plans": nplans,
                        "builds": cache.builds, "evictions": cache.evictions},
-        "large_group_ms": t_group * 1e3,
+        "large_group_ms": t_group * 1e3, "small_request_ms": t_small * 1e3,
+        "rate_calibration": {"full_batch_rate_per_s": rate0, "pilot_requests": len(preqs),
+                             "pilot_busy_fraction": pbusy},
         "audit": {"requests": audited, "max_abs_du_over_sigma": worst, "tolerance": 1e-4},
         "gpu_launches": srv.launches, "clocks": clocks,
         "e2e": {"value": terms / wall, "unit": "pair-terms/s", "h2d_bytes_per_step": 8 * nreq,
