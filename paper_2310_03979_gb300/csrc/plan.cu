@@ -552,7 +552,8 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.twr = fp64 ? p->tw_rec64 : p->tw_rec32;
   A.log2Nc = p->rec_log2Nc;
   A.zcap = kRecSmem / (fp64 ? (int)sizeof(double2) : (int)sizeof(float2));
-  const int smem = kRecSmem + kFringeSmem;  // the FFT form's grids and the fringe's state
+  // the fringe's state, and the FFT form's grids where it is used
+  const int smem = kFringeSmem + (p->rec_fft ? kRecSmem : 0);
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
   const void *kern = fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>

@@ -869,9 +869,11 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
 template <typename T, int M, bool SEP>
 __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
   __shared__ unsigned int s_done[kRowWarps];
-  // dynamic shared memory: kRecSmem for the FFT form's grids, then the fringe's
+  // dynamic shared memory: the fringe's state, then (FFT form of the
+  // separable bulk only) kRecSmem for its grids -- the other passes leave that
+  // space to the L1 cache of their bulk loads
   extern __shared__ __align__(16) unsigned char rec_smem[];
-  FringeSmem<T, M> &F = *reinterpret_cast<FringeSmem<T, M> *>(rec_smem + kRecSmem);
+  FringeSmem<T, M> &F = *reinterpret_cast<FringeSmem<T, M> *>(rec_smem);
   const int lane = threadIdx.x & 31;
   // consecutive points (neighbours on a level, of similar cost) go to
   // different SMs
@@ -899,7 +901,7 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
     if (A.zr) {  // separable envelope: the bulk by one FFT product
       const int log2L = (31 - __clz(kRecBL)) + (__ffs(D / kRecBL) - 1);
       if (!sep_product<T, M>(A, D - (1 << log2L), log2L, g,
-                             reinterpret_cast<typename Vec2<T>::type *>(rec_smem)))
+                             reinterpret_cast<typename Vec2<T>::type *>(rec_smem + kFringeSmem)))
         return;
     } else {
       // bulk: warps take points in turn from the phase's ticket counter
