@@ -130,24 +130,39 @@ def _pairsum_roofline_fp64(terms_per_s, **extra):
     return out
 
 
-def _pairsum_roofline(terms_per_s, traffic=None, **extra):
+def _pairsum_roofline(terms_per_s, traffic=None, separable=False, sep_share=None, **extra):
     """Roofline object of the FP32 pair sum from its kernel-only rate.
 
     The bound is the FP32 pipe.  A pair-term is 6 FP32-pipe lane operations
-    (2 FMUL + 4 FFMA, 10 flop), so the fraction is pair-terms/s x 6 over the
-    pipe's lane-operation rate, 152 SM x 128 lanes x the maximum SM clock.
-    The same rate in flops (10 per pair-term against 2 flop per lane-cycle)
-    is given beside it: its ceiling is 10/12 because an FMUL fills a lane
-    slot for one flop."""
+    (2 FMUL + 4 FFMA, 10 flop: the weight times one phasor, then the complex
+    product accumulated), so the fraction is pair-terms/s x 6 over the pipe's
+    lane-operation rate, 152 SM x 128 lanes x the maximum SM clock.  The same
+    rate in flops (10 per pair-term against 2 flop per lane-cycle) is given
+    beside it: its ceiling is 10/12 because an FMUL fills a lane slot for one
+    flop.  In separable form (the Gaussian envelope's weights folded into the
+    phasor rows and the per-row-pair and per-output factors) a pair-term is
+    the complex product accumulated alone: 4 FFMA, 8 flop."""
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     nsm = n_sm()
     lane_rate = FP32_LANES_PER_SM * nsm * sm_max * 1e6  # lane-ops/s
-    ops = 6.0 * terms_per_s
-    flops = 10.0 * terms_per_s
+    # sep_share: the fraction of the pair-terms in separable form (a batch
+    # of plans in both forms)
+    share = (1.0 if separable else 0.0) if sep_share is None else float(sep_share)
+    per_ops, per_flop = 6.0 - 2.0 * share, 10.0 - 2.0 * share
+    ops = per_ops * terms_per_s
+    flops = per_flop * terms_per_s
+    if share == 0.0:
+        unit_txt = "6 FP32-pipe lane-ops (2 FMUL + 4 FFMA = 10 flop) per pair-term"
+    elif share == 1.0:
+        unit_txt = "4 FP32-pipe lane-ops (4 FFMA = 8 flop) per pair-term, separable form"
+    else:
+        unit_txt = (f"{per_ops:.3f} FP32-pipe lane-ops per pair-term: 4 (4 FFMA) for the "
+                    f"{100 * share:.1f} % of pair-terms in separable form, 6 (2 FMUL + 4 FFMA) "
+                    "for the rest")
     out = {"bound": "alu", "achieved": ops / 1e12, "peak": lane_rate / 1e12,
            "unit": "T FP32-pipe lane-ops/s", "frac": ops / lane_rate, "traffic": traffic,
-           "per_unit": "6 FP32-pipe lane-ops (2 FMUL + 4 FFMA = 10 flop) per pair-term",
+           "per_unit": unit_txt,
            "flops": {"achieved": flops / 1e12, "peak": 2.0 * lane_rate / 1e12,
                      "unit": "TFLOP/s", "frac": flops / (2.0 * lane_rate)},
            "peak_source": f"derived: {nsm} SM x {FP32_LANES_PER_SM} FP32 lanes x "
@@ -340,6 +355,11 @@ def run_uneven(args):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
     ps_ms = statistics.median(ps)
+    sep_terms = 0  # pair-terms of plans whose pair sum runs in separable form
+    for p, c in zip(plans, counts):
+        inf = p.info()
+        if inf.recursion_flags & srm3.SRM3_PAIRSUM_SEPARABLE:
+            sep_terms += 2 * inf.pairs * c
     choice = {}
     for k, v in tuned.items():
         c = f'{v["storage"]}, {v["tile"]}'
@@ -359,7 +379,7 @@ def run_uneven(args):
         "wall_ms_per_step": wall * 1e3 / args.steps,
         "plan_build_s_all_spectra": t_plans, "autotune_s": t_tune,
         "autotune_choices": choice,
-        "roofline": _pairsum_roofline(terms / (ps_ms * 1e-3),
+        "roofline": _pairsum_roofline(terms / (ps_ms * 1e-3), sep_share=sep_terms / terms,
                                       kernel="k_pairsum_f32p (batched, one launch)"),
         "gpu_launches": (3 * len(wls) + 1) * args.steps,
         "clocks": clocks,
@@ -850,9 +870,12 @@ def main():
                                                  kernel="k_pairsum_f64") if es == 8
                      else _pairsum_roofline(
             terms_per_launch / (avg_launch_ms * 1e-3), traffic,
+            separable=bool(info.recursion_flags & srm3.SRM3_PAIRSUM_SEPARABLE),
             algorithmic_bytes_per_launch=info.table_bytes + n * 2 * 8 * (
                 wl.n_kappa * (wl.n_omega + 128) + wl.n_kappa * wl.n_omega),
             kernel="k_pairsum_f32p<table>" if info.storage == 1 else
+                   "k_pairsum_f32p<recompute, separable>" if (
+                       prebuilt is None and info.recursion_flags & srm3.SRM3_PAIRSUM_SEPARABLE) else
                    "k_pairsum_f32p<recompute>" if prebuilt is None else
                    "k_pairsum_f32p<recompute> + k_pairsum_f32d (sum and difference pairs)")),
         "gpu_launches": launches_per_step * args.steps,

@@ -231,11 +231,16 @@ typedef struct srm3_info {
                                 envelope split on i + j = k, Sec. 4.1 Eq. pure);
                                 bit 1 (SRM3_REC_TABLES_MOVED): the tables are those
                                 of the FP64 pass at the FP32 root estimate, moved to
-                                the final eps to first order (FP32 plans) */
+                                the final eps to first order (FP32 plans);
+                                bit 2 (SRM3_PAIRSUM_SEPARABLE): the FP32 pair sum
+                                runs in separable form, g = a_i a_j b_k with the
+                                omega factor folded into the phasor rows (W
+                                recomputed, Gaussian envelope, Sec. 4.3) */
 } srm3_info;
 
 #define SRM3_REC_SEPARABLE 1
 #define SRM3_REC_TABLES_MOVED 2
+#define SRM3_PAIRSUM_SEPARABLE 4
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
 

@@ -290,6 +290,12 @@ struct PsDesc {  // aligned as CUtensorMap
   // half-warps then take two row pairs of a work item (a = 2i and 2i + 1),
   // reading 256-byte rows through a tensor map with 64-float boxes
   int half;
+  // sep = 1: W recomputed in separable form, g(i, j) = a_i a_j b_k on the
+  // pairs of k -- the omega factor a_w is in y, the kappa factor aK[row]
+  // weights each row pair, b_k is in ck: the register blocks multiply y
+  // rows alone and no envelope window is staged
+  int sep;
+  const float *aK;
   float cb, sb;          // cos / sin of the biphase
 };
 
@@ -318,7 +324,7 @@ __device__ __forceinline__ int4 ps_get_unit(int u, const PsDesc &d0,
 
 // One staged chunk for one compute warp: all register blocks of the chunk.
 // RS: float4 per staged row (32, or 16 in half mode).
-template <bool TABLE, int RS>
+template <bool TABLE, int RS, bool SEPW = false>
 __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
                                          const float4 *__restrict__ pb,
                                          const float2 *__restrict__ pw,
@@ -342,7 +348,20 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
       Bc[m0 + vv] = lds_pair(pb + (m0 + vv - U * (NB - 1)) * RS);
     }
     const ulonglong2 *B = Bc + m0;
-    if (TABLE) {
+    if constexpr (SEPW) {
+      // separable form: the weights are in the rows, four packed FMAs per
+      // product of two sheet-samples
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int uu = 0; uu < U; ++uu) {
+          const int v = r - uu + U - 1;
+          Txp[r] = f2_fma(A[uu].x, B[v].x, Txp[r]);
+          Txm[r] = f2_fma(A[uu].y, B[v].y, Txm[r]);
+          Ty[r] = f2_fma(A[uu].x, B[v].y, Ty[r]);
+          Ty[r] = f2_fma(A[uu].y, B[v].x, Ty[r]);
+        }
+    } else if (TABLE) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const float4 w4 =
@@ -453,7 +472,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
             }
           const unsigned tx = YROWS * ROW_BYTES +
                               (tab ? ntile * R * CH * (unsigned)sizeof(float)
-                                   : EWIN * (unsigned)sizeof(float));
+                                   : (d.sep ? 0u : EWIN * (unsigned)sizeof(float)));
           mbar_expect_tx(&full[stage], tx);
           // one row pair (full rows), or two in half mode (half rows each; a
           // second row pair past the centre repeats the first and is
@@ -470,8 +489,9 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
                           &full[stage]);
           }
           if (!tab) {
-            bulk_g2s(sw + stage * STAGE_W, d.Ew + d.ew_off + 2 * i0 - kws0 - (SW - 1),
-                     EWIN * sizeof(float), &full[stage]);
+            if (!d.sep)
+              bulk_g2s(sw + stage * STAGE_W, d.Ew + d.ew_off + 2 * i0 - kws0 - (SW - 1),
+                       EWIN * sizeof(float), &full[stage]);
           } else {
             for (int t = 0; t < NC; ++t) {  // the tiles counted above
               const int k0 = kws0 + R * t;
@@ -537,12 +557,17 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
         if (half) {
           const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;
           const float4 *pb = pa + (CH + R * warp + CH - U) * (LANES / 2);
-          ps_chunk<false, LANES / 2>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+          if (d.sep)
+            ps_chunk<false, LANES / 2, true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+          else
+            ps_chunk<false, LANES / 2>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
         } else {
           const float4 *pa = sy + stage * STAGE_Y + lane;
           const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
           if (tab)
             ps_chunk<true, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
+          else if (d.sep)
+            ps_chunk<false, LANES, true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
           else
             ps_chunk<false, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
         }
@@ -556,9 +581,14 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
         const int ah = half ? 2 * a + hl : a;  // this lane's row pair
         const bool live = ah <= kk / 2;
         const int b = kk - (live ? ah : a);
-        const float rowfac = tab ? 1.0f : (live ? d.Ek[kk - 2 * ah] : 0.0f);
+        // the row pair's kappa weight: none for the table (in W), the
+        // envelope at kk - 2a, or in separable form aK[a] aK[kk - a]
+        auto rw = [&](int a_) {
+          return d.sep ? d.aK[a_] * d.aK[kk - a_] : d.Ek[kk - 2 * a_];
+        };
+        const float rowfac = tab ? 1.0f : (live ? rw(ah) : 0.0f);
         const bool odd_live = half && 2 * a + 1 <= kk / 2;
-        const float rowfac_odd = odd_live ? d.Ek[kk - 2 * (2 * a + 1)] : 0.0f;
+        const float rowfac_odd = odd_live ? rw(2 * a + 1) : 0.0f;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const float2 xp = f2_split(Txp[r]), xm = f2_split(Txm[r]), yy = f2_split(Ty[r]);
@@ -572,7 +602,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
                   tab ? d.W[my_base +
                             (((long long)ah * (my_L / CH) + ((kw >> 1) / CH)) * R + r) * CH +
                             ((kw >> 1) % CH)]
-                      : d.Ew[d.ew_off];
+                      : (d.sep ? 1.0f : d.Ew[d.ew_off]);
               v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
               v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
               v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));

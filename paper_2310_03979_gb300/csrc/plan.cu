@@ -221,6 +221,34 @@ __global__ void k_sampling_tables(int n, double dkdw, double eps,
   ck[k] = (T)(pos ? 2.0 * eps * dkdw * sqrt(s) : 0.0);
 }
 
+// The separable form of the FP32 pair sum (Gaussian envelope): on the pairs
+// of k, (i - j)^2 = 2 (i - c)^2 + 2 (j - c)^2 - (k - 2c)^2 per axis (c =
+// (n - 1)/2), so g(i, j) = exp(-1/2 ((ik - jk)/sk)^2 - 1/2 ((iw - jw)/sw)^2)
+// = a_i a_j b_k with a = exp(-((ik - ck)/sk)^2 - ((iw - cw)/sw)^2) and b =
+// exp(1/2 ((kk - 2ck)/sk)^2 + 1/2 ((kw - 2cw)/sw)^2).  The pair sum then
+// multiplies scaled phasor rows, sum (a_w y)_i (a_w y)_j per lattice row
+// pair, weighted by aK[a] aK[kk - a] and at the end by c_k b_k; the pure term
+// P_k y_k = (P_k / a_w) (a_w y)_k.  Factor ranges within [exp(-E/2), 1] and
+// [1, exp(E)] (E <= 40), as the recursion's (k_gauss_sep).
+__global__ void k_sep_sampling(int nk, int nw, double sk, double sw, const float *__restrict__ sqq,
+                               const float *__restrict__ Pk, const float *__restrict__ ck,
+                               float *__restrict__ sqq_s, float *__restrict__ Pk_s,
+                               float *__restrict__ ck_s, float *__restrict__ aK) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk * nw) return;
+  const int kk = i / nw, kw = i - kk * nw;
+  const double ck0 = 0.5 * (nk - 1), cw0 = 0.5 * (nw - 1);
+  const double uw = (kw - cw0) / sw, vk = (kk - 2.0 * ck0) / sk, vw = (kw - 2.0 * cw0) / sw;
+  const double aw = exp(-uw * uw), b = exp(0.5 * (vk * vk + vw * vw));
+  sqq_s[i] = (float)((double)sqq[i] * aw);
+  Pk_s[i] = (float)((double)Pk[i] / aw);
+  ck_s[i] = (float)((double)ck[i] * b);
+  if (kw == 0) {
+    const double uk = (kk - ck0) / sk;
+    aK[kk] = (float)exp(-uk * uk);
+  }
+}
+
 template <typename T>
 __global__ void k_env(int len, int off, double sigma_n, T *out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1437,10 +1465,20 @@ int prepare_sampling_tables(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(dev_alloc(&p->sqq, nl * es, st));
   SRM3_CUDA(dev_alloc(&p->Pk, nl * es, st));
   SRM3_CUDA(dev_alloc(&p->ck, nl * es, st));
-  if (f32)
+  if (f32) {
     k_sampling_tables<float><<<cdiv(nl, 256), 256, 0, st>>>(
         (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (float *)p->sqq, (float *)p->Pk,
         (float *)p->ck);
+    if (pairsum_sep_capable(p)) {
+      SRM3_CUDA(dev_alloc(&p->sqq_s, nl * sizeof(float), st));
+      SRM3_CUDA(dev_alloc(&p->Pk_s, nl * sizeof(float), st));
+      SRM3_CUDA(dev_alloc(&p->ck_s, nl * sizeof(float), st));
+      SRM3_CUDA(dev_alloc(&p->aK, p->nk * sizeof(float), st));
+      k_sep_sampling<<<cdiv(nl, 256), 256, 0, st>>>(
+          p->nk, p->nw, p->sigma_g * p->nk, p->sigma_g * p->nw, (const float *)p->sqq,
+          (const float *)p->Pk, (const float *)p->ck, p->sqq_s, p->Pk_s, p->ck_s, p->aK);
+    }
+  }
   else
     k_sampling_tables<double><<<cdiv(nl, 256), 256, 0, st>>>(
         (int)nl, p->dkdw, p->eps, p->S, p->qm, p->sb2, (double *)p->sqq, (double *)p->Pk,
@@ -1517,7 +1555,7 @@ void free_plan(srm3_plan *p) {
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr,
                  p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d,
-                 p->rs_a2, p->rs_b2, p->dsb2, p->red_part};
+                 p->rs_a2, p->rs_b2, p->dsb2, p->red_part, p->sqq_s, p->Pk_s, p->ck_s, p->aK};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)
@@ -1684,7 +1722,8 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->tile_r = kTileR;
   info->tile_width = kTileR * plan->ps_nc;
   info->recursion_flags = (plan->rec_sep ? SRM3_REC_SEPARABLE : 0) |
-                          (plan->eps_shifted ? SRM3_REC_TABLES_MOVED : 0);
+                          (plan->eps_shifted ? SRM3_REC_TABLES_MOVED : 0) |
+                          (pairsum_sep_now(plan) ? SRM3_PAIRSUM_SEPARABLE : 0);
   info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
   info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
   info->diff_pairs = plan->diffpairs;

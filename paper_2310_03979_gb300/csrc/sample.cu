@@ -173,10 +173,13 @@ static int phases_into(srm3_plan *p, cudaStream_t st, const uint64_t *seeds,
   const int blocks = cdiv(nc * n, 256);
   // the swapped copy of the mixed FP32 pair sum (plan workspace only)
   float *ys = (p->mixed && p->precision == SRM3_FP32 && y == p->y) ? (float *)p->ys : nullptr;
+  // the separable pair sum takes the rows with the omega factor folded in
+  // (not the raw Philox words, which do not depend on the table)
+  const float *sq32 = pairsum_sep_now(p) ? p->sqq_s : (const float *)p->sqq;
   if (p->precision == SRM3_FP32)
-    k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
-                                            (const float *)p->sqq, (float2 *)y, (float2 *)y0,
-                                            sp, p->rowstride, words_out, ys);
+    k_phases<float><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off, sq32,
+                                            (float2 *)y, (float2 *)y0, sp, p->rowstride,
+                                            words_out, ys);
   else
     k_phases<double><<<blocks, 256, 0, st>>>(p->nk, p->nw, n, sc, dseeds, ss_off,
                                              (const double *)p->sqq, (double2 *)y,
@@ -256,8 +259,11 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
   d->Ew = (const float *)p->Ews;
   d->W = table ? p->W : nullptr;
   d->toff = table ? p->tile_off : nullptr;
-  d->Pk = (const float *)p->Pk;
-  d->ck = (const float *)p->ck;
+  const bool sepf = pairsum_sep_now(p);
+  d->Pk = sepf ? p->Pk_s : (const float *)p->Pk;
+  d->ck = sepf ? p->ck_s : (const float *)p->ck;
+  d->sep = sepf ? 1 : 0;
+  d->aK = sepf ? p->aK : nullptr;
   d->C = (float2 *)C_out;
   d->order = p->super_order[tile_index(p->ps_nc)];
   d->nk = p->nk;
@@ -1011,9 +1017,10 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     std::vector<const float *> pk(g.total), ck(g.total);
     for (size_t mm = 0; mm < g.members.size(); ++mm) {
       srm3_plan *q = b->plans[g.members[mm]];
+      const bool sepf = pairsum_sep_now(q);  // as the group's descriptor (same shape and storage)
       for (int j = 0; j < b->counts[g.members[mm]]; ++j) {
-        pk[g.sample_off[mm] + j] = (const float *)q->Pk;
-        ck[g.sample_off[mm] + j] = (const float *)q->ck;
+        pk[g.sample_off[mm] + j] = sepf ? q->Pk_s : (const float *)q->Pk;
+        ck[g.sample_off[mm] + j] = sepf ? q->ck_s : (const float *)q->ck;
       }
     }
     if ((e = cudaMemcpyAsync(g.pk_of, pk.data(), sizeof(float *) * g.total,

@@ -160,6 +160,12 @@ struct srm3_plan {
   void *sqq = nullptr;    // sqrt(q) masked by S > 0, [nk*nw]
   void *Pk = nullptr;     // pure factor 2 sqrt(dk dw S) (1 - sb2), [nk*nw]
   void *ck = nullptr;     // pair factor 2 eps dk dw sqrt(S), [nk*nw]
+  // the FP32 pair sum in separable form (Gaussian envelope, W recomputed):
+  // g(i, j) = a_i a_j b_k on the pairs of k, the omega factor a_w folded
+  // into y (sqq_s = sqrt(q) a_w), the kappa factor a_k per lattice row
+  // (aK, applied per row pair), b_k into the pair factor (ck_s = ck b_k) and
+  // 1/a_w into the pure factor (Pk_s = Pk / a_w); FP32, [nk*nw] (aK [nk])
+  float *sqq_s = nullptr, *Pk_s = nullptr, *ck_s = nullptr, *aK = nullptr;
   void *Ek = nullptr;     // envelope factor along kappa, |d| < nk
   void *Ews = nullptr;    // envelope factor along omega, signed d, offset ew_off
   int ew_off = 0, ew_len = 0;
@@ -261,4 +267,15 @@ static inline int ilog2_exact(int v) {
   int l = 0;
   while ((1 << l) < v) ++l;
   return ((1 << l) == v) ? l : -1;
+}
+
+// The FP32 pair sum may take the separable form (plan tables sqq_s, Pk_s,
+// ck_s, aK): a Gaussian envelope whose factors' exponent range fits (the
+// recursion's separable form), sum interactions only; it does take it while
+// the plan's W is recomputed.
+inline bool pairsum_sep_capable(const srm3_plan *p) {
+  return p->precision == SRM3_FP32 && p->rec_sep && !p->sep && !p->mixed;
+}
+inline bool pairsum_sep_now(const srm3_plan *p) {
+  return pairsum_sep_capable(p) && p->sqq_s && p->storage == SRM3_STORAGE_RECOMPUTE;
 }

@@ -79,7 +79,7 @@ class srm3_grid(ctypes.Structure):
                 ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
 
 
-SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED = 1, 2  # srm3_info.recursion_flags
+SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED, SRM3_PAIRSUM_SEPARABLE = 1, 2, 4  # srm3_info.recursion_flags
 
 
 class srm3_info(ctypes.Structure):

@@ -130,7 +130,12 @@ def test_coefficients(oracle_lib, precision, storage):
     seeds = [3, 11]
     with srm3.Plan.create(wl, precision=precision, storage=storage, eps=op.eps) as p:
         C = _cplx(p.coeffs(seeds))
-        assert p.info().storage == {"recompute": 2, "table": 1}[storage]
+        info = p.info()
+        assert info.storage == {"recompute": 2, "table": 1}[storage]
+        # W recomputed for the Gaussian envelope: the FP32 pair sum multiplies
+        # phasor rows scaled by the envelope's separable factors
+        sepf = bool(info.recursion_flags & srm3.SRM3_PAIRSUM_SEPARABLE)
+        assert sepf == (precision == "fp32" and storage == "recompute")
     tol = 1e-11 if precision == "fp64" else 2e-6
     for i, s in enumerate(seeds):
         ref = op.coeffs(s)
