@@ -350,17 +350,22 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
     const ulonglong2 *B = Bc + m0;
     if constexpr (SEPW) {
       // separable form: the weights are in the rows, four packed FMAs per
-      // product of two sheet-samples
+      // product of two sheet-samples; omega outermost and the two updates
+      // of Ty[r] in separate sweeps over the outputs, so that no FMA waits
+      // on the one before it (every accumulator's terms keep their order)
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+      for (int uu = 0; uu < U; ++uu) {
 #pragma unroll
-        for (int uu = 0; uu < U; ++uu) {
+        for (int r = 0; r < R; ++r) {
           const int v = r - uu + U - 1;
           Txp[r] = f2_fma(A[uu].x, B[v].x, Txp[r]);
           Txm[r] = f2_fma(A[uu].y, B[v].y, Txm[r]);
-          Ty[r] = f2_fma(A[uu].x, B[v].y, Ty[r]);
-          Ty[r] = f2_fma(A[uu].y, B[v].x, Ty[r]);
         }
+#pragma unroll
+        for (int r = 0; r < R; ++r) Ty[r] = f2_fma(A[uu].x, B[r - uu + U - 1].y, Ty[r]);
+#pragma unroll
+        for (int r = 0; r < R; ++r) Ty[r] = f2_fma(A[uu].y, B[r - uu + U - 1].x, Ty[r]);
+      }
     } else if (TABLE) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
