@@ -811,14 +811,16 @@ def main():
     # envelope tables 2 + g^2 1, separable factors 1 (Gaussian envelope in
     # separable form), recursion index lists 2, the sum of S 2, linear pass
     # 2 + its reduction 2, each recursion pass 1, slope and move of the
-    # tables 2 (FP32 plans whose tables were moved), sampling tables 4, W
-    # table 1 if stored; per 128-sample chunk: phases, pair sum, two FFT
-    # stages
+    # tables 2 (FP32 plans whose tables were moved), sampling tables 4 (+1
+    # for the separable pair sum's), W table 1 if stored; per 128-sample
+    # chunk: phases, pair sum, two FFT stages
     flags = info.recursion_flags
     sep_gauss = 1 if (flags & srm3.SRM3_REC_SEPARABLE) and wl.envelope == "gauss" else 0
     moved = 2 if flags & srm3.SRM3_REC_TABLES_MOVED else 0
+    # the separable pair sum's scaled tables (FP32 Gaussian plans, either storage)
+    sep_tables = 1 if sep_gauss and es == 4 and getattr(wl, "interactions", "sum") == "sum" else 0
     launches_per_step = (1 + 3 + sep_gauss + 2 + 2 + 4 + (info.root_passes + info.root_passes_fp32)
-                         + moved + 4 + (1 if info.storage == 1 else 0) + 4 * chunks)
+                         + moved + 4 + sep_tables + (1 if info.storage == 1 else 0) + 4 * chunks)
     if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT

@@ -184,16 +184,25 @@ __global__ void __launch_bounds__(256) k_reduce_part(long long n, const double *
 
 __global__ void k_reduce_final(int nparts, const double *__restrict__ part,
                                double *__restrict__ scal) {
-  if (threadIdx.x != 0) return;
+  // one warp: lane l combines partials l, l + 32, ... in order, then a fixed
+  // butterfly -- the same order on every run
+  const int lane = threadIdx.x;
   double mx = 0.0, mn = 1.0, sum = 0.0;
-  for (int j = 0; j < nparts; ++j) {
+  for (int j = lane; j < nparts; j += 32) {
     mx = fmax(mx, part[3 * j]);
     mn = fmin(mn, part[3 * j + 1]);
     sum += part[3 * j + 2];
   }
-  scal[9] = mx;
-  scal[10] = mn;
-  scal[11] = sum;
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  if (lane == 0) {
+    scal[9] = mx;
+    scal[10] = mn;
+    scal[11] = sum;
+  }
 }
 
 static int reduce_plane0(srm3_plan *p, cudaStream_t st) {
