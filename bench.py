@@ -819,8 +819,13 @@ def main():
     moved = 2 if flags & srm3.SRM3_REC_TABLES_MOVED else 0
     # the separable pair sum's scaled tables (FP32 Gaussian plans, either storage)
     sep_tables = 1 if sep_gauss and es == 4 and getattr(wl, "interactions", "sum") == "sum" else 0
+    # coarse start of the eps search: its own kernels (subsampled spectrum,
+    # envelope tables, index lists, reductions, linear pass, passes), and no
+    # linear pass (4 kernels) on the plan's lattice
+    coarse = info.coarse_launches - (4 if flags & srm3.SRM3_REC_COARSE_START else 0)
     launches_per_step = (1 + 3 + sep_gauss + 2 + 2 + 4 + (info.root_passes + info.root_passes_fp32)
-                         + moved + 4 + sep_tables + (1 if info.storage == 1 else 0) + 4 * chunks)
+                         + moved + 4 + sep_tables + (1 if info.storage == 1 else 0) + 4 * chunks
+                         + coarse)
     if wl.envelope != "gauss":
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
@@ -862,6 +867,8 @@ def main():
                                 "recursion_fp32_ms": t_last.recursion_fp32_ms,
                                 "recursion_fp32_passes": t_last.recursion_passes_fp32,
                                 "recursion_fp64_ms": t_last.recursion_fp64_ms,
+                                "eps_search_coarse_ms": t_last.coarse_ms,
+                                "eps_search_coarse_passes": t_last.recursion_passes_coarse,
                                 "table": t_last.table_ms, "phases": t_last.phases_ms,
                                 "pairsum": t_last.pairsum_ms,
                                 "transform": t_last.transform_ms},

@@ -235,12 +235,25 @@ typedef struct srm3_info {
                                 bit 2 (SRM3_PAIRSUM_SEPARABLE): the FP32 pair sum
                                 runs in separable form, g = a_i a_j b_k with the
                                 omega factor folded into the phasor rows (W
-                                recomputed, Gaussian envelope, Sec. 4.3) */
+                                recomputed, Gaussian envelope, Sec. 4.3);
+                                bit 3 (SRM3_REC_COARSE_START): the eps search
+                                started from the root of the same search on a
+                                coarser lattice (coarse_fk, coarse_fw below) and
+                                one FP32 pass on this lattice bracketed it (no
+                                linear bound on this lattice) */
+    int32_t coarse_fk, coarse_fw; /* the coarse lattice of the eps search takes
+                                every coarse_fk-th kappa and coarse_fw-th omega
+                                point of this one (1, 1: no coarse search; plans
+                                with a target, sum interactions, Gaussian
+                                envelope, at least 65536 points) */
+    int32_t coarse_launches;  /* kernels the coarse search launched */
+    int32_t coarse_passes;    /* its FP32 recursion passes */
 } srm3_info;
 
 #define SRM3_REC_SEPARABLE 1
 #define SRM3_REC_TABLES_MOVED 2
 #define SRM3_PAIRSUM_SEPARABLE 4
+#define SRM3_REC_COARSE_START 8
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
 
@@ -355,7 +368,9 @@ typedef struct srm3_timings {
     double recursion_fp32_ms;  /* part of recursion_ms spent in FP32 search passes */
     double recursion_fp64_ms;  /* part of recursion_ms spent in FP64 passes */
     int32_t recursion_passes_fp32;
-    int32_t reserved;
+    int32_t recursion_passes_coarse; /* FP32 passes of the coarse eps search */
+    double coarse_ms;      /* the coarse eps search, its tables included (its
+                              passes are also part of recursion_ms) */
 } srm3_timings;
 
 /* on != 0: bracket every sampling-stage launch with CUDA events. */

@@ -111,13 +111,14 @@ __global__ void k_gauss_sep(int nk, int nw, double sk, double sw, double *__rest
 }
 
 
-// dsb2[k] = (sb2 of plane m1 - sb2 of plane m0) / (x1 - x0): the slope in x
-// of every point's sum_b2 between two FP32 search planes.
+// dsb2[k] = w0 s0[k] + w1 s1[k] + w2 s2[k]: the slope in x of every point's
+// sum_b2 from FP32 search planes (the derivative weights of the Lagrange
+// polynomial through them).
 __global__ void k_sb2_slope(long long n, const double *__restrict__ s0,
-                            const double *__restrict__ s1, double inv_dx,
-                            double *__restrict__ dsb2) {
+                            const double *__restrict__ s1, const double *__restrict__ s2,
+                            double w0, double w1, double w2, double *__restrict__ dsb2) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dsb2[i] = (s1[i] - s0[i]) * inv_dx;
+  if (i < n) dsb2[i] = fma(w0, s0[i], fma(w1, s1[i], w2 * s2[i]));
 }
 
 // The tables of an FP64 pass at x moved to x + dx to first order: sum_b2 +=
@@ -211,6 +212,7 @@ static int reduce_plane0(srm3_plan *p, cudaStream_t st) {
   const int ctas = (int)std::min<long long>(kReduceCtas, (nl + 255) / 256);
   k_reduce_part<<<ctas, 256, 0, st>>>(nl, p->S, p->sb2, p->red_part);
   k_reduce_final<<<1, 32, 0, st>>>(ctas, p->red_part, p->scal);
+  p->n_launch += 2;
   return cudaGetLastError() == cudaSuccess ? SRM3_OK : fail(SRM3_ERR_CUDA, "plane reduction");
 }
 
@@ -494,6 +496,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   k_level_points<<<nlev, 128, 0, st>>>(nk, nw, nlev, p->rec_lev_off, p->rec_items);
   if (nph > 0) k_bulk_pairs<<<dim3(nk, nph), 128, 0, st>>>(nk, nw, nlev, d_seg, p->rec_pairs);
   SRM3_CUDA(cudaGetLastError());
+  p->n_launch += nph > 0 ? 2 : 1;
   SRM3_CUDA(dev_free(d_seg, st));
   // running bulk sums: up to 32 bytes per point (8 FP32 planes or 3 FP64)
   SRM3_CUDA(dev_alloc(&p->rec_partial, (size_t)nk * nw * 32, st));
@@ -521,6 +524,7 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
       k_twiddles<double2><<<cdiv(ntw, 256), 256, 0, st>>>(ntw, ilog2_exact(ntw),
                                                           (double2 *)p->tw_rec64);
       SRM3_CUDA(cudaGetLastError());
+      p->n_launch += 2;
     }
   }
   // sum of S (the exact variance), once, read after the next synchronisation
@@ -600,6 +604,7 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   SRM3_CUDA(cudaLaunchCooperativeKernel(kern, fp64 ? p->rec_grid64 : p->rec_grid32, kRecThreads,
                                         args, smem, st));
   SRM3_CUDA(cudaGetLastError());
+  p->n_launch += 1;
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, M * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st));
@@ -839,18 +844,47 @@ static int shift_tables(srm3_plan *p, cudaStream_t st, double dx, PassResult *r)
   return SRM3_OK;
 }
 
-// eps from max_k sum_b2 = target.  The linear pass (q == 1) gives the
-// bracket [0, target / max L], since q >= 1 makes x L an under-estimate of
-// sum_b2.  FP32 passes, each evaluating kPlanes values of x at once, cut
-// the bracket into kPlanes + 1 parts per pass until it is ~1e-3 wide; the
-// root is then located to the FP32 pass's accuracy by inverse quadratic
-// interpolation.  One three-plane FP64 pass around that estimate gives the
-// root to near FP64 accuracy by the same interpolation, and a single-plane
-// FP64 pass at it produces the tables; if |f| > tol there, Illinois on the
-// FP64 bracket continues.  The tables left in the plan are those of the
-// final FP64 pass.
-static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
-  double Lmax = 0.0;
+// ---------------------------------------------------------------------------
+// eps from max_k sum_b2 = target (plans without mixed interactions).
+//
+// FP32 stage.  Each FP32 pass evaluates f(x) = max_k sum_b2 - target at
+// kPlanes values of x = eps^2 at once.  The root is bracketed in one of two
+// ways:
+//  * coarse start (lattices of at least kCoarsePoints points): the same
+//    search on a coarser lattice -- every fk-th kappa and fw-th omega point
+//    of this one, fk, fw powers of two keeping at least kCoarseMinDim points
+//    per axis -- whose sums are the same quadrature of Eq. pure's pair
+//    integral on a coarser grid, places the root within a few 1e-3; one pass
+//    here over +-kCoarseWindow around it then brackets the root and samples
+//    f finely enough around it for the steps below.  If that pass does not
+//    bracket the root, the wide search follows, keeping its points.
+//  * wide search: the linear pass (q == 1) bounds the root by target / max
+//    L, as q >= 1 makes x L an under-estimate of sum_b2; the first pass
+//    samples [(1 - target)^2 x0, x0] (x0 = target / Lmax, with margins), the
+//    second zooms on the first pass's quadratic estimate, later ones (only
+//    when the root was not inside) subdivide the bracket.
+// Inverse quadratic interpolation through the bracket and its nearest
+// feasible neighbour then gives x32, and the quadratic's slope at the root.
+//
+// FP64 stage: Newton steps from x32 with the FP32 slope, then secant steps
+// on the FP64 values inside an FP64 bracket; Illinois if they leave it or
+// stall.  Loose targets (FP32 plans) may instead move the tables of the
+// first FP64 pass to the Newton root to first order (shift_tables).  The
+// tables left in the plan are those of the final FP64 pass, or of that move.
+
+static constexpr int kCoarseMinDim = 64;
+static constexpr long long kCoarsePoints = 1LL << 16;
+static constexpr double kCoarseWindow = 0.015;
+
+struct Search32 {
+  std::vector<std::pair<double, double>> pts;  // (x, f); f = +inf: failed pass
+  double xs[kPlanes];
+  PassResult r[kPlanes];  // the last pass
+  double x0 = -1.0;       // target / Lmax once the wide search has run
+};
+
+// Lmax = max_k L_k, the small-x slope of sum_b2 (wide search).
+static int linear_bound(srm3_plan *p, cudaStream_t st, double *Lmax) {
   if (p->sep) {
     // separable envelope: the slope at q = 1 from one FP32 pass at a
     // vanishing x (every q rounds to 1), L = sum_b2 / x
@@ -860,91 +894,98 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     for (int m = 0; m < kPlanes; ++m) xs0[m] = xt;
     int rc0 = run_pass_multi(p, st, xs0, kPlanes, false, r0);
     if (rc0) return rc0;
-    Lmax = r0[0].max_sb2 / xt;
-  } else {
-    const int nblk = cdiv(p->nw, kLinOut);
-    const size_t smem = (size_t)3 * p->nw * sizeof(float);
-    const long long nl = (long long)p->nk * p->nw;
-    SRM3_CUDA(cudaFuncSetAttribute(k_rec_linear, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
-    // the parts go to the FP32 search state, not yet in use (8 floats per point)
-    static_assert(kLinParts <= kPlanes, "linear-pass parts fit the FP32 search state");
-    k_rec_linear<<<p->nk * nblk * kLinParts, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32,
-                                                                   p->EwSq32, p->qm32);
-    k_rec_linear_sum<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm32, p->sb2, p->dkdw);
-    SRM3_CUDA(cudaGetLastError());
-    SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kLinParts * nl * sizeof(float), st));
-    if (int rc1 = reduce_plane0(p, st)) return rc1;
-    SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double),
-                              cudaMemcpyDeviceToHost, st));
-    SRM3_CUDA(cudaStreamSynchronize(st));
-    Lmax = p->h_pinned[9];
+    *Lmax = r0[0].max_sb2 / xt;
+    return SRM3_OK;
   }
+  const int nblk = cdiv(p->nw, kLinOut);
+  const size_t smem = (size_t)3 * p->nw * sizeof(float);
+  const long long nl = (long long)p->nk * p->nw;
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_linear, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  // the parts go to the FP32 search state, not yet in use (8 floats per point)
+  static_assert(kLinParts <= kPlanes, "linear-pass parts fit the FP32 search state");
+  k_rec_linear<<<p->nk * nblk * kLinParts, kLinOut, smem, st>>>(p->nk, p->nw, p->S, p->EkSq32,
+                                                                 p->EwSq32, p->qm32);
+  k_rec_linear_sum<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->qm32, p->sb2, p->dkdw);
+  SRM3_CUDA(cudaGetLastError());
+  p->n_launch += 2;
+  SRM3_CUDA(cudaMemsetAsync(p->qm32, 0, kLinParts * nl * sizeof(float), st));
+  if (int rc1 = reduce_plane0(p, st)) return rc1;
+  SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 9, p->scal + 9, sizeof(double),
+                            cudaMemcpyDeviceToHost, st));
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  *Lmax = p->h_pinned[9];
+  return SRM3_OK;
+}
+
+// Index of the first point of s.pts (sorted) at or above the target, or
+// pts.size() when every point is below it.
+static size_t first_above(const Search32 &s) {
+  size_t j = 0;
+  while (j < s.pts.size() && s.pts[j].second < 0) ++j;
+  return j;
+}
+
+static double quad_root(double xa, double fa, double xb, double fb, double xc, double fc) {
+  return xa * fb * fc / ((fa - fb) * (fa - fc)) + xb * fa * fc / ((fb - fa) * (fb - fc)) +
+         xc * fa * fb / ((fc - fa) * (fc - fb));
+}
+
+// The wide search, adding to the points s already holds; returns with a
+// bracket whose upper end is feasible, or fails.
+static int wide_search(srm3_plan *p, cudaStream_t st, double target, Search32 &s) {
+  double Lmax = 0.0;
+  int rc = linear_bound(p, st, &Lmax);
+  if (rc) return rc;
   if (!(Lmax > 0.0))
     return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
-
-  // FP32 stage: eight values of x = eps^2 per pass.  At the root every
-  // sum_b2 <= target, so q <= 1/(1 - target) and x* lies in
-  // [(1 - target)^2 x0, x0], x0 = target / Lmax (q >= 1 gives the upper end);
-  // the first pass samples that range (with a margin for the FP32 Lmax).
-  // The second pass centres its planes on the first pass's quadratic
-  // estimate, half-width four times that estimate's distance from the
-  // secant root, so that the slope at the root comes out of closely spaced
-  // planes.  Later passes (only when the root was not inside) subdivide the
-  // bracket.  Inverse quadratic interpolation through the bracket and its
-  // nearest feasible neighbour gives x32.
+  // at the root every sum_b2 <= target, so q <= 1/(1 - target) and x* lies
+  // in [(1 - target)^2 x0, x0] (q >= 1 gives the upper end); the first pass
+  // samples that range, with a margin for the FP32 Lmax.  The second pass
+  // centres its planes on the first pass's quadratic estimate, half-width
+  // four times that estimate's distance from the secant root.
   const double x0 = target / Lmax;
-  PassResult r[kPlanes];
-  double xs[kPlanes];
-  int rc;
-  std::vector<std::pair<double, double>> pts;  // (x, f); f = +inf: failed pass
-  pts.push_back({0.0, -target});
+  s.x0 = x0;
   double lo = 0.9 * (1.0 - target) * (1.0 - target) * x0, hi = 1.01 * x0;
   bool hi_known = false;
   double zoom_c = 0.0, zoom_w = 0.0;  // centre and half-width of the second pass
-  auto quad_root = [](double xa, double fa, double xb, double fb, double xc, double fc) {
-    return xa * fb * fc / ((fa - fb) * (fa - fc)) + xb * fa * fc / ((fb - fa) * (fb - fc)) +
-           xc * fa * fb / ((fc - fa) * (fc - fb));
-  };
   for (int pass = 0; pass < 12; ++pass) {
     for (int m = 0; m < kPlanes; ++m) {
       if (pass == 0)
-        xs[m] = lo + (hi - lo) * m / (kPlanes - 1);
+        s.xs[m] = lo + (hi - lo) * m / (kPlanes - 1);
       else if (pass == 1 && zoom_w > 0.0)
-        xs[m] = zoom_c - zoom_w + 2.0 * zoom_w * m / (kPlanes - 1);
+        s.xs[m] = zoom_c - zoom_w + 2.0 * zoom_w * m / (kPlanes - 1);
       else
-        xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1)
-                         : lo + (hi - lo) * (m + 1) / kPlanes;
+        s.xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1)
+                           : lo + (hi - lo) * (m + 1) / kPlanes;
     }
-    rc = run_pass_multi(p, st, xs, kPlanes, false, r);
+    rc = run_pass_multi(p, st, s.xs, kPlanes, false, s.r);
     if (rc) return rc;
     for (int m = 0; m < kPlanes; ++m)
-      pts.push_back({xs[m], r[m].err ? INFINITY : r[m].max_sb2 - target});
-    std::sort(pts.begin(), pts.end());
-    // bracket: last point below target before the first point at/above it
-    size_t j = 0;
-    while (j < pts.size() && pts[j].second < 0) ++j;
-    if (j == pts.size()) {  // every point below target: move the range up
-      lo = pts.back().first;
+      s.pts.push_back({s.xs[m], s.r[m].err ? INFINITY : s.r[m].max_sb2 - target});
+    std::sort(s.pts.begin(), s.pts.end());
+    const size_t j = first_above(s);
+    if (j == s.pts.size()) {  // every point below target: move the range up
+      lo = s.pts.back().first;
       hi = 2.0 * lo;
       hi_known = false;
       continue;
     }
-    lo = pts[j - 1].first;
-    hi = pts[j].first;
+    lo = s.pts[j - 1].first;
+    hi = s.pts[j].first;
     hi_known = true;
-    if (pass >= 1 && std::isfinite(pts[j].second)) break;
+    if (pass >= 1 && std::isfinite(s.pts[j].second)) return SRM3_OK;
     zoom_w = 0.0;
-    if (pass == 0 && std::isfinite(pts[j].second) &&
-        ((j + 1 < pts.size() && std::isfinite(pts[j + 1].second)) || j >= 2)) {
+    if (pass == 0 && std::isfinite(s.pts[j].second) &&
+        ((j + 1 < s.pts.size() && std::isfinite(s.pts[j + 1].second)) || j >= 2)) {
       // quadratic through the bracket and its feasible neighbour above, else
       // the one below
-      const double xl = pts[j - 1].first, fl = pts[j - 1].second;
-      const double xh = pts[j].first, fh = pts[j].second;
+      const double xl = s.pts[j - 1].first, fl = s.pts[j - 1].second;
+      const double xh = s.pts[j].first, fh = s.pts[j].second;
       const double xsec = xl - fl * (xh - xl) / (fh - fl);
-      const bool above = j + 1 < pts.size() && std::isfinite(pts[j + 1].second);
-      const double xq = above ? quad_root(xl, fl, xh, fh, pts[j + 1].first, pts[j + 1].second)
-                              : quad_root(pts[j - 2].first, pts[j - 2].second, xl, fl, xh, fh);
+      const bool above = j + 1 < s.pts.size() && std::isfinite(s.pts[j + 1].second);
+      const double xq = above ? quad_root(xl, fl, xh, fh, s.pts[j + 1].first, s.pts[j + 1].second)
+                              : quad_root(s.pts[j - 2].first, s.pts[j - 2].second, xl, fl, xh, fh);
       if (xq > xl && xq < xh) {
         zoom_c = xq;
         zoom_w = std::max(4.0 * std::fabs(xq - xsec), 2e-4 * xq);
@@ -953,60 +994,232 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     }
   }
   if (!hi_known) return fail(SRM3_ERR_BISECTION_FAILED, "eps search: target not bracketed");
-  size_t jb = 0;
-  while (jb < pts.size() && pts[jb].second < 0) ++jb;
-  const bool hi_ok = std::isfinite(pts[jb].second);
-  auto iq = [](double x0_, double f0, double x1, double f1, double x2, double f2) {
-    return x0_ * f1 * f2 / ((f0 - f1) * (f0 - f2)) + x1 * f0 * f2 / ((f1 - f0) * (f1 - f2)) +
-           x2 * f0 * f1 / ((f2 - f0) * (f2 - f1));
-  };
-  double x32 = 0.5 * (lo + hi), d32 = 0.5 * (hi - lo) / hi, slope32 = 0.0;
-  if (hi_ok) {
-    const double xl = pts[jb - 1].first, fl = pts[jb - 1].second;
-    const double xh = pts[jb].first, fh = pts[jb].second;
-    const double xsec = xl - fl * (xh - xl) / (fh - fl);
-    x32 = xsec;
-    if (jb + 1 < pts.size() && std::isfinite(pts[jb + 1].second))
-      x32 = iq(xl, fl, xh, fh, pts[jb + 1].first, pts[jb + 1].second);
-    else if (jb >= 2)
-      x32 = iq(pts[jb - 2].first, pts[jb - 2].second, xl, fl, xh, fh);
-    if (!(x32 > xl && x32 < xh)) x32 = xsec;
-    d32 = std::fabs(x32 - xsec) / x32;
-    slope32 = (fh - fl) / (xh - xl);
-    if (jb + 1 < pts.size() && std::isfinite(pts[jb + 1].second)) {
-      // slope at the root of the quadratic through the three points
-      const double xa = xl, fa = fl, xb = xh, fb = fh;
-      const double xc = pts[jb + 1].first, fc = pts[jb + 1].second;
-      const double dxdf = -xa * (fb + fc) / ((fa - fb) * (fa - fc)) -
-                          xb * (fa + fc) / ((fb - fa) * (fb - fc)) -
-                          xc * (fa + fb) / ((fc - fa) * (fc - fb));
-      if (dxdf > 0.0) slope32 = 1.0 / dxdf;
+  return SRM3_OK;
+}
+
+// x32 from the points of s: inverse quadratic interpolation through the
+// bracket and its nearest feasible neighbour (the secant root when that
+// leaves the bracket); *slope = df/dx at the root (0 when unknown).
+// Returns false when the bracket's upper end failed (no interpolation).
+static bool root_fp32(const Search32 &s, double *x32, double *slope) {
+  const size_t jb = first_above(s);
+  *slope = 0.0;
+  if (jb == 0 || jb == s.pts.size() || !std::isfinite(s.pts[jb].second)) {
+    if (jb > 0 && jb < s.pts.size()) *x32 = 0.5 * (s.pts[jb - 1].first + s.pts[jb].first);
+    return false;
+  }
+  const double xl = s.pts[jb - 1].first, fl = s.pts[jb - 1].second;
+  const double xh = s.pts[jb].first, fh = s.pts[jb].second;
+  const double xsec = xl - fl * (xh - xl) / (fh - fl);
+  const bool above = jb + 1 < s.pts.size() && std::isfinite(s.pts[jb + 1].second);
+  double x = xsec;
+  if (above)
+    x = quad_root(xl, fl, xh, fh, s.pts[jb + 1].first, s.pts[jb + 1].second);
+  else if (jb >= 2)
+    x = quad_root(s.pts[jb - 2].first, s.pts[jb - 2].second, xl, fl, xh, fh);
+  if (!(x > xl && x < xh)) x = xsec;
+  *x32 = x;
+  *slope = (fh - fl) / (xh - xl);
+  if (above) {
+    // slope at the root of the quadratic through the three points
+    const double xa = xl, fa = fl, xb = xh, fb = fh;
+    const double xc = s.pts[jb + 1].first, fc = s.pts[jb + 1].second;
+    const double dxdf = -xa * (fb + fc) / ((fa - fb) * (fa - fc)) -
+                        xb * (fa + fc) / ((fb - fa) * (fb - fc)) -
+                        xc * (fa + fb) / ((fc - fa) * (fc - fb));
+    if (dxdf > 0.0) *slope = 1.0 / dxdf;
+  }
+  return true;
+}
+
+// S on the coarse lattice: every fk-th kappa and fw-th omega point.
+__global__ void k_subsample(int nw, int fk, int fw, int nkc, int nwc, const double *__restrict__ S,
+                            double *__restrict__ Sc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nkc * nwc) return;
+  const int kc = i / nwc, wc = i - kc * nwc;
+  Sc[i] = S[(size_t)kc * fk * nw + (size_t)wc * fw];
+}
+
+// The root of the FP32 search on the coarse lattice into *xc (-1: the
+// lattice is too small for a coarse start).  The coarse plan borrows the
+// plan's pinned host scalars; its device state is freed in stream order.
+static int coarse_root(srm3_plan *p, cudaStream_t st, double target, double *xc) {
+  *xc = -1.0;
+  int fk = 1, fw = 1;
+  while (p->nk / (2 * fk) >= kCoarseMinDim) fk *= 2;
+  while (p->nw / (2 * fw) >= kCoarseMinDim) fw *= 2;
+  if ((long long)p->nk * p->nw < kCoarsePoints || fk * fw < 4) return SRM3_OK;
+  // the sum of S of this plan, copied to the shared pinned slot by
+  // setup_recursion, is read before the coarse plan reuses the slot
+  SRM3_CUDA(cudaStreamSynchronize(st));
+  if (p->sumS < 0.0) p->sumS = p->h_pinned[kSumSlot];
+  srm3_plan c;
+  c.nk = p->nk / fk;
+  c.nw = p->nw / fw;
+  c.dk = p->dk * fk;
+  c.dw = p->dw * fw;
+  c.dkdw = c.dk * c.dw;
+  c.precision = SRM3_FP32;
+  c.device = p->device;
+  c.rec_sep = p->rec_sep;
+  c.sigma_g = p->sigma_g;
+  c.h_pinned = p->h_pinned;
+  c.h_err = p->h_err;
+  struct Cleanup {
+    srm3_plan *c;
+    cudaStream_t st;
+    ~Cleanup() {
+      void *dev[] = {c->S,        c->sb2,       c->scal,    c->err,          c->qm32,
+                     c->EkSq,     c->EkSq32,    c->EwSq,    c->EwSq32,       c->G2,
+                     c->G2_32,    c->rs_a2,     c->rs_b2,   c->qm3,          c->rec_items,
+                     c->rec_lev_off, c->rec_pairs, c->rec_pair_off, c->rec_partial,
+                     c->rec_max,  c->rec_bar,   c->red_part};
+      for (void *d : dev)
+        if (d) dev_free(d, st);
+    }
+  } cleanup{&c, st};
+  const int nkc = c.nk, nwc = c.nw;
+  const long long nlc = (long long)nkc * nwc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SRM3_CUDA(cudaEventCreate(&e0));
+  SRM3_CUDA(cudaEventCreate(&e1));
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } evg{e0, e1};
+  SRM3_CUDA(cudaEventRecord(e0, st));
+  SRM3_CUDA(dev_alloc(&c.S, nlc * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&c.sb2, kPlanes * nlc * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&c.scal, (8 + 4 * kPlanes) * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&c.err, (kPlanes + 1) * sizeof(int), st));
+  SRM3_CUDA(dev_alloc(&c.qm32, kPlanes * nlc * sizeof(float), st));
+  SRM3_CUDA(cudaMemsetAsync(c.qm32, 0, kPlanes * nlc * sizeof(float), st));
+  SRM3_CUDA(dev_alloc(&c.EkSq, nkc * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&c.EkSq32, nkc * sizeof(float), st));
+  SRM3_CUDA(dev_alloc(&c.EwSq, 2 * nwc * sizeof(double), st));
+  SRM3_CUDA(dev_alloc(&c.EwSq32, 2 * nwc * sizeof(float), st));
+  k_subsample<<<cdiv(nlc, 256), 256, 0, st>>>(p->nw, fk, fw, nkc, nwc, p->S, c.S);
+  // the envelope's widths in the coarse lattice's index units: the same
+  // function of frequency as on this lattice
+  const double sk = p->sigma_g * p->nk / fk, sw = p->sigma_g * p->nw / fw;
+  k_env_sq<<<cdiv(nkc, 256), 256, 0, st>>>(nkc, sk, c.EkSq, c.EkSq32);
+  k_env_sq<<<cdiv(2 * nwc, 256), 256, 0, st>>>(2 * nwc, sw, c.EwSq, c.EwSq32);
+  c.n_launch += 3;
+  if (c.rec_sep) {
+    SRM3_CUDA(dev_alloc(&c.rs_a2, nlc * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&c.rs_b2, nlc * sizeof(double), st));
+    k_gauss_sep<<<cdiv(nlc, 256), 256, 0, st>>>(nkc, nwc, sk, sw, c.rs_a2, c.rs_b2);
+  } else {
+    SRM3_CUDA(dev_alloc(&c.G2, nlc * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&c.G2_32, nlc * sizeof(float), st));
+    k_g2<<<cdiv(nlc, 256), 256, 0, st>>>(nkc, nwc, c.EkSq, c.EwSq, c.G2, c.G2_32);
+  }
+  c.n_launch += 1;
+  SRM3_CUDA(cudaGetLastError());
+  int rc = setup_recursion(&c, st);
+  if (rc) return rc;
+  Search32 s;
+  s.pts.push_back({0.0, -target});
+  // a coarse lattice without pairs or without a root (its support can
+  // differ from this lattice's) leaves the search to the wide form
+  rc = wide_search(&c, st, target, s);
+  if (rc && rc != SRM3_ERR_BISECTION_FAILED) return rc;
+  double x = 0.0, slope = 0.0;
+  const bool ok = !rc && root_fp32(s, &x, &slope);
+  SRM3_CUDA(cudaEventRecord(e1, st));
+  SRM3_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SRM3_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  p->t_coarse_ms = ms;
+  p->t_recursion_ms += c.t_recursion_ms;
+  p->coarse_passes = c.root_passes32;
+  p->coarse_launches = c.n_launch;
+  p->coarse_fk = fk;
+  p->coarse_fw = fw;
+  if (ok) *xc = x;
+  return SRM3_OK;
+}
+
+static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
+  int rc;
+  Search32 s;
+  s.pts.push_back({0.0, -target});
+  p->coarse_start = false;
+  if (!p->sep) {
+    double xc = -1.0;
+    rc = coarse_root(p, st, target, &xc);
+    if (rc) return rc;
+    if (xc > 0.0) {
+      for (int m = 0; m < kPlanes; ++m)
+        s.xs[m] = xc * (1.0 + kCoarseWindow * (2.0 * m / (kPlanes - 1) - 1.0));
+      rc = run_pass_multi(p, st, s.xs, kPlanes, false, s.r);
+      if (rc) return rc;
+      for (int m = 0; m < kPlanes; ++m)
+        s.pts.push_back({s.xs[m], s.r[m].err ? INFINITY : s.r[m].max_sb2 - target});
+      std::sort(s.pts.begin(), s.pts.end());
+      const size_t j = first_above(s);
+      p->coarse_start = j >= 2 && j < s.pts.size() && std::isfinite(s.pts[j].second);
     }
   }
+  if (!p->coarse_start) {
+    rc = wide_search(p, st, target, s);
+    if (rc) return rc;
+  }
+  double x32 = 0.0, slope32 = 0.0;
+  const bool hi_ok = root_fp32(s, &x32, &slope32);
 
   // Loose targets (FP32 plans, tol >= kShiftTol): the slope in x of every
-  // point's sum_b2, from the two planes of the last FP32 pass around x32.
-  // After the FP64 pass at x32 the Newton root x1 is typically within 1e-7
-  // x32; the tables are then moved there to first order, sum_b2(x1) =
-  // sum_b2(x32) + (x1 - x32) dsb2 and q = 1/(1 - sum_b2), instead of a
-  // second pass.  The error is the FP32 slope's (~1e-3 relative) times the
-  // step plus the curvature term, ~1e-10 relative at a 1e-7 step, far below
-  // the FP32 rounding of the tables these plans sample with; the result is
-  // accepted only when its max_k sum_b2 meets the target within tol.  The
-  // slopes need FP32 sums accurate relative to each point: not the FFT form
-  // of the separable bulk, whose rounding is bounded relative to the largest
-  // sums only (it keeps the second FP64 pass).
+  // point's sum_b2 at x32, the derivative of the quadratic through the three
+  // planes of the last FP32 pass nearest x32 (two when only two are
+  // feasible).  After the FP64 pass at x32 the Newton root x1 is typically
+  // within 1e-7 x32; the tables are then moved there to first order,
+  // sum_b2(x1) = sum_b2(x32) + (x1 - x32) dsb2 and q = 1/(1 - sum_b2),
+  // instead of a second pass.  The error is the slope's (~1e-4 relative:
+  // FP32 sums over planes a few 1e-3 apart, and the quadratic's remainder)
+  // times the step plus the curvature term, ~1e-11 relative at a 1e-7 step,
+  // far below the FP32 rounding of the tables these plans sample with; the
+  // result is accepted only when its max_k sum_b2 meets the target within
+  // tol.  The slopes need FP32 sums accurate relative to each point: not the
+  // FFT form of the separable bulk, whose rounding is bounded relative to
+  // the largest sums only (it keeps the second FP64 pass).
   bool shift_ok = false;
   if (tol >= kShiftTol && !p->rec_fft && hi_ok && slope32 > 0.0) {
     int m = -1;
     for (int i = 0; i + 1 < kPlanes && m < 0; ++i)
-      if (xs[i] <= x32 && x32 <= xs[i + 1] && !r[i].err && !r[i + 1].err) m = i;
+      if (s.xs[i] <= x32 && x32 <= s.xs[i + 1] && !s.r[i].err && !s.r[i + 1].err) m = i;
     if (m >= 0) {
+      // the third plane: the nearer feasible neighbour of the pair
+      int m3 = -1;
+      const bool below = m >= 1 && !s.r[m - 1].err;
+      const bool above = m + 2 < kPlanes && !s.r[m + 2].err;
+      if (below && above)
+        m3 = (x32 - s.xs[m - 1] <= s.xs[m + 2] - x32) ? m - 1 : m + 2;
+      else if (below)
+        m3 = m - 1;
+      else if (above)
+        m3 = m + 2;
+      double w0, w1, w2 = 0.0;
+      const double xa = s.xs[m], xb = s.xs[m + 1];
+      if (m3 >= 0) {
+        // derivative at x32 of the Lagrange quadratic through the three planes
+        const double xc3 = s.xs[m3];
+        w0 = ((x32 - xb) + (x32 - xc3)) / ((xa - xb) * (xa - xc3));
+        w1 = ((x32 - xa) + (x32 - xc3)) / ((xb - xa) * (xb - xc3));
+        w2 = ((x32 - xa) + (x32 - xb)) / ((xc3 - xa) * (xc3 - xb));
+      } else {
+        w1 = 1.0 / (xb - xa);
+        w0 = -w1;
+        m3 = m;
+      }
       const long long nl = (long long)p->nk * p->nw;
       if (!p->dsb2) SRM3_CUDA(dev_alloc(&p->dsb2, nl * sizeof(double), st));
       k_sb2_slope<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->sb2 + (size_t)m * nl,
                                                  p->sb2 + (size_t)(m + 1) * nl,
-                                                 1.0 / (xs[m + 1] - xs[m]), p->dsb2);
+                                                 p->sb2 + (size_t)m3 * nl, w0, w1, w2, p->dsb2);
       SRM3_CUDA(cudaGetLastError());
       shift_ok = true;
     }
@@ -1014,8 +1227,12 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
 
   // FP64 stage: Newton steps from x32 with the FP32 slope, then secant steps
   // on the FP64 values, all inside an FP64 bracket; Illinois if they leave
-  // it or stall.
-  Bracket b{0.0, -target, 4.0 * x0, 1.0, true};  // upper end not yet evaluated in FP64
+  // it or stall.  The bracket's upper end is not yet evaluated in FP64: any
+  // x above the root serves (the linear bound x0, else four times the FP32
+  // bracket's upper end).
+  const size_t jb = first_above(s);
+  const double xup = s.x0 > 0.0 ? s.x0 : s.pts[std::min(jb, s.pts.size() - 1)].first;
+  Bracket b{0.0, -target, 4.0 * xup, 1.0, true};
   double xbest = -1.0;
   PassResult best{};
   bool converged = false, at_best = false;
@@ -1732,7 +1949,12 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->tile_width = kTileR * plan->ps_nc;
   info->recursion_flags = (plan->rec_sep ? SRM3_REC_SEPARABLE : 0) |
                           (plan->eps_shifted ? SRM3_REC_TABLES_MOVED : 0) |
-                          (pairsum_sep_now(plan) ? SRM3_PAIRSUM_SEPARABLE : 0);
+                          (pairsum_sep_now(plan) ? SRM3_PAIRSUM_SEPARABLE : 0) |
+                          (plan->coarse_start ? SRM3_REC_COARSE_START : 0);
+  info->coarse_fk = plan->coarse_fk;
+  info->coarse_fw = plan->coarse_fw;
+  info->coarse_launches = plan->coarse_launches;
+  info->coarse_passes = plan->coarse_passes;
   info->interactions = plan->mixed ? SRM3_INTERACTIONS_MIXED : SRM3_INTERACTIONS_SUM;
   info->fixed_point_iterations = plan->mixed ? plan->fp_iters : 0;
   info->diff_pairs = plan->diffpairs;

@@ -789,6 +789,8 @@ SRM3_API int srm3_get_timings(srm3_plan *plan, srm3_timings *t, int reset) {
   t->recursion_fp32_ms = plan->t_rec32_ms;
   t->recursion_fp64_ms = plan->t_rec64_ms;
   t->recursion_passes_fp32 = plan->root_passes32;
+  t->recursion_passes_coarse = plan->coarse_passes;
+  t->coarse_ms = plan->t_coarse_ms;
   t->table_ms = plan->t_table_ms;
   t->phases_ms = plan->t_stage_ms[0];
   t->pairsum_ms = plan->t_stage_ms[1];

@@ -123,6 +123,13 @@ struct srm3_plan {
   double *dsb2 = nullptr;         // d sum_b2 / dx per point from two FP32 search planes
   double *red_part = nullptr;     // per-CTA partials of the plane reduction
   bool eps_shifted = false;       // the final tables are an FP64 pass moved to eps to first order
+  // eps search from the root on a coarser lattice (every coarse_fk-th kappa,
+  // coarse_fw-th omega point): its kernels, passes and time; coarse_start
+  // when one pass on this lattice then bracketed the root
+  bool coarse_start = false;
+  int coarse_fk = 1, coarse_fw = 1, coarse_launches = 0, coarse_passes = 0;
+  double t_coarse_ms = 0.0;
+  int n_launch = 0;               // recursion-stage kernels launched (counted where launched)
   double *qprev = nullptr;        // previous iterate of q
   double *qlo = nullptr;          // converged q at qlo_x (warm start of the search)
   double qlo_x = -1.0;

@@ -79,7 +79,9 @@ class srm3_grid(ctypes.Structure):
                 ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
 
 
-SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED, SRM3_PAIRSUM_SEPARABLE = 1, 2, 4  # srm3_info.recursion_flags
+# srm3_info.recursion_flags
+SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED, SRM3_PAIRSUM_SEPARABLE = 1, 2, 4
+SRM3_REC_COARSE_START = 8
 
 
 class srm3_info(ctypes.Structure):
@@ -91,7 +93,9 @@ class srm3_info(ctypes.Structure):
                 ("tile_r", ctypes.c_int32), ("root_passes_fp32", ctypes.c_int32),
                 ("interactions", ctypes.c_int32), ("fixed_point_iterations", ctypes.c_int32),
                 ("diff_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_double),
-                ("tile_width", ctypes.c_int32), ("recursion_flags", ctypes.c_int32)]
+                ("tile_width", ctypes.c_int32), ("recursion_flags", ctypes.c_int32),
+                ("coarse_fk", ctypes.c_int32), ("coarse_fw", ctypes.c_int32),
+                ("coarse_launches", ctypes.c_int32), ("coarse_passes", ctypes.c_int32)]
 
 
 class srm3_timings(ctypes.Structure):
@@ -100,7 +104,8 @@ class srm3_timings(ctypes.Structure):
                 ("transform_ms", ctypes.c_double), ("recursion_passes", ctypes.c_int32),
                 ("pairsum_launches", ctypes.c_int32), ("pair_terms", ctypes.c_int64),
                 ("recursion_fp32_ms", ctypes.c_double), ("recursion_fp64_ms", ctypes.c_double),
-                ("recursion_passes_fp32", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("recursion_passes_fp32", ctypes.c_int32),
+                ("recursion_passes_coarse", ctypes.c_int32), ("coarse_ms", ctypes.c_double)]
 
 
 class srm3_stats_result(ctypes.Structure):

@@ -42,6 +42,10 @@ def test_bridge_plan_against_oracle():
         S, q, sb2 = p.tables()
     assert abs(info.eps - g["eps"]) <= 2e-8 * g["eps"]
     assert abs(info.max_sum_b2 - g["max_sum_b2"]) <= 1e-9
+    # the eps search started from the root on the 64 x 64 lattice of every
+    # fourth kappa and eighth omega point, bracketed by one FP32 pass here
+    assert info.recursion_flags & srm3.SRM3_REC_COARSE_START
+    assert (info.coarse_fk, info.coarse_fw) == (4, 8)
     assert abs(info.variance - g["variance"]) <= 1e-12 * g["variance"]
     pts = [tuple(x) for x in g["points"]]
     qg, sg = np.array(g["q"]), np.array(g["sum_b2"])

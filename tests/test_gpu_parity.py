@@ -102,6 +102,40 @@ def test_recursion_envelope_width(oracle_lib, sigma_g, separable):
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-8, atol=1e-15)
 
 
+@pytest.mark.parametrize("mask", ["full", "no_coarse_pairs", "window_missed"])
+def test_eps_search_coarse_start(mask):
+    """The eps search of a 256 x 256 lattice starts from the root on the
+    64 x 64 lattice of every fourth point per axis.  Since b_p^2 = x dk dw g^2
+    q_i q_j, sum_b2 depends on S only through its support, so supports that
+    the coarse lattice misreads steer the search down its fallbacks: S = 0 on
+    the columns kw = 0 mod 4 leaves the coarse lattice without pairs, S = 0
+    on kw = 2 mod 4 puts its root far from this lattice's (outside the
+    bracketing pass's window).  Each way the FP32 plan meets the target to
+    1e-9 and its eps agrees with the FP64 plan's (target to 1e-13, FP64
+    passes to the end) to 2e-8."""
+    wl = W.small_case(nk=256, nw=256, nx=256, nt=512, seeds=(1,))
+    S = oracle.kaimal_lorentzian(256, 256, wl.kappa_u, wl.omega_u, wl.U, wl.z, wl.z0,
+                                 wl.k_vk, wl.lam)
+    if mask == "no_coarse_pairs":
+        S[:, 0::4] = 0.0
+    elif mask == "window_missed":
+        S[:, 2::4] = 0.0
+    res = {}
+    for precision in ("fp64", "fp32"):
+        with srm3.Plan.create(wl, table=S, precision=precision) as p:
+            res[precision] = p.info()
+    i32, i64 = res["fp32"], res["fp64"]
+    for info in (i32, i64):
+        assert (info.coarse_fk, info.coarse_fw) == (4, 4)
+        started = bool(info.recursion_flags & srm3.SRM3_REC_COARSE_START)
+        assert started == (mask == "full")
+    assert abs(i64.max_sum_b2 - wl.target) <= 1e-13
+    assert abs(i32.max_sum_b2 - wl.target) <= 1e-9
+    assert i32.eps == pytest.approx(i64.eps, rel=2e-8)
+    if mask == "no_coarse_pairs":
+        assert i32.coarse_passes == 0  # the coarse linear bound found no pairs
+
+
 @pytest.mark.parametrize("nk,nw", [(40, 33), (96, 64), (130, 20), (12, 200)])
 def test_recursion_at_fixed_eps(oracle_lib, nk, nw):
     """Same eps on both sides: the anti-diagonal recursion equals the
