@@ -6,6 +6,8 @@
 // it gets its own copy of the kernels.
 #pragma once
 
+#include <utility>
+
 #include "srm3_internal.cuh"
 
 namespace srm3 {
@@ -215,6 +217,90 @@ __device__ __forceinline__ void dft_inv(T2 (&v)[R]) {
   for (int i = 0; i < R; ++i) v[i] = a[i];
 }
 
+// The same DFT when some inputs are zero by construction: bit r of VMASK is
+// set when v[r] may be nonzero (the others must be zero).  Each butterfly
+// of the decimation in time is resolved at compile time from the zero
+// pattern its stage inherits: both operands zero, skipped; the rotated one
+// zero, a copy (x +- 0 = x); the other zero, the rotated operand and its
+// negation (0 +- t = +-t); else computed as in dft_inv.  IEEE arithmetic does
+// not let the compiler drop the additions of zeros by itself.  The results
+// equal dft_inv's up to the sign of zero outputs.
+template <int R>
+__host__ __device__ constexpr unsigned dit_in_mask(unsigned vmask) {
+  unsigned m = 0;
+  for (int i = 0; i < R; ++i) {
+    int rb = 0;
+    for (int bit = 0; bit < Log2R<R>::v; ++bit)
+      rb |= ((i >> bit) & 1) << (Log2R<R>::v - 1 - bit);
+    if ((vmask >> rb) & 1u) m |= 1u << i;
+  }
+  return m;
+}
+template <int R>
+__host__ __device__ constexpr unsigned dit_next_mask(unsigned m, int st) {
+  const int h = 1 << st;
+  unsigned o = 0;
+  for (int g = 0; g < R; g += 2 * h)
+    for (int j = 0; j < h; ++j)
+      if (((m >> (g + j)) & 1u) || ((m >> (g + j + h)) & 1u))
+        o |= (1u << (g + j)) | (1u << (g + j + h));
+  return o;
+}
+template <int R, int ST, unsigned M, int B, typename T2>
+__device__ __forceinline__ void dit_bfly(T2 (&a)[R]) {
+  constexpr int h = 1 << ST, j = B % h, i0 = (B / h) * 2 * h + j, i1 = i0 + h;
+  constexpr bool n0 = (M >> i0) & 1u, n1 = (M >> i1) & 1u;
+  if constexpr (n0 && n1) {
+    const T2 t = rot16(a[i1], j * (8 >> ST));
+    const T2 x = a[i0];
+    a[i0].x = x.x + t.x;
+    a[i0].y = x.y + t.y;
+    a[i1].x = x.x - t.x;
+    a[i1].y = x.y - t.y;
+  } else if constexpr (n0) {
+    a[i1] = a[i0];
+  } else if constexpr (n1) {
+    const T2 t = rot16(a[i1], j * (8 >> ST));
+    a[i0] = t;
+    a[i1].x = -t.x;
+    a[i1].y = -t.y;
+  }
+}
+template <int R, int ST, unsigned M, typename T2, int... Bs>
+__device__ __forceinline__ void dit_stage(T2 (&a)[R], std::integer_sequence<int, Bs...>) {
+  (dit_bfly<R, ST, M, Bs>(a), ...);
+}
+template <int R, int ST, unsigned M, typename T2>
+__device__ __forceinline__ void dit_stages(T2 (&a)[R]) {
+  if constexpr (ST < Log2R<R>::v) {
+    dit_stage<R, ST, M>(a, std::make_integer_sequence<int, R / 2>{});
+    dit_stages<R, ST + 1, dit_next_mask<R>(M, ST)>(a);
+  }
+}
+template <int R, unsigned VMASK, typename T2>
+__device__ __forceinline__ void dft_inv_masked(T2 (&v)[R]) {
+  constexpr int B = Log2R<R>::v;
+  T2 a[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    int rb = 0;
+#pragma unroll
+    for (int bit = 0; bit < B; ++bit) rb |= ((i >> bit) & 1) << (B - 1 - bit);
+    a[i] = v[rb];
+  }
+  dit_stages<R, 0, dit_in_mask<R>(VMASK)>(a);
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = a[i];
+}
+
+// Inputs of the first pass of a length-L transform that can be nonzero:
+// with R the first radix, the blocks r < nz and r >= R - nz of the L/R-long
+// input runs (both ends of the spectrum); nz = 0 or nz >= R/2: all.
+__host__ __device__ constexpr unsigned tx_in_mask(int R, int nz) {
+  return (nz <= 0 || 2 * nz >= R) ? (R >= 32 ? 0xffffffffu : (1u << R) - 1u)
+                                   : ((1u << nz) - 1u) | (((1u << nz) - 1u) << (R - nz));
+}
+
 // Pass plan of a length-2^l transform: ceil(l / 4) passes, pass p of radix
 // 2^tx_lr(l, p) (larger radices first).
 __host__ __device__ constexpr int tx_npass(int l) { return (l + 3) >> 2; }
@@ -264,7 +350,7 @@ __device__ __forceinline__ void load_tw(const T2 *__restrict__ p, T2 (&w)[R]) {
 // pass's run of the pass-twiddle table.  FIRST: inputs from src(i) (global);
 // else from sm (shared, padded positions).  LAST: outputs to dst(i, v)
 // (global); else to sm.
-template <int R, bool FIRST, bool LAST, typename T2, class Src, class Dst>
+template <int R, bool FIRST, bool LAST, unsigned VMASK, typename T2, class Src, class Dst>
 __device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
                                               const T2 *__restrict__ twp, T2 *sm, Src &src,
                                               Dst &dst) {
@@ -277,7 +363,14 @@ __device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
     if (j < LR) {
       if constexpr (FIRST) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[it][r] = src(j + r * LR);
+        for (int r = 0; r < R; ++r) {
+          if ((VMASK >> r) & 1u) {
+            v[it][r] = src(j + r * LR);
+          } else {
+            v[it][r].x = 0;
+            v[it][r].y = 0;
+          }
+        }
       } else {
         if (LR % 16 == 0) {  // (j + r LR) >> 4 = (j >> 4) + r LR / 16
           const int a = sp16(j), st = LR + (LR >> 4);
@@ -292,7 +385,10 @@ __device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
 #pragma unroll
         for (int r = 1; r < R; ++r) v[it][r] = cmul(v[it][r], w[r]);
       }
-      dft_inv<R>(v[it]);
+      if constexpr (FIRST && VMASK != tx_in_mask(R, 0))
+        dft_inv_masked<R, VMASK>(v[it]);
+      else
+        dft_inv<R>(v[it]);
     }
   }
   if constexpr (!FIRST && !LAST) __syncthreads();  // in place: all reads before any write
@@ -322,16 +418,18 @@ __device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
 // unrolled at compile time so that each pass keeps only its own 16 values
 // live; Ns is the length transformed by the passes before p, toff the
 // offset of pass p's run in the pass-twiddle table tw.
-template <int l, int p, typename T2, class Src, class Dst>
+// NZ: the nonzero input blocks of the first pass (tx_in_mask; 0 = all).
+template <int l, int p, int NZ, typename T2, class Src, class Dst>
 __device__ __forceinline__ void stockham_passes(int Ns, int toff, int tpt, int jt,
                                                 const T2 *__restrict__ tw, T2 *sm, Src &src,
                                                 Dst &dst) {
   if constexpr (p < tx_npass(l)) {
     constexpr int lr = tx_lr(l, p);
-    stockham_pass<(1 << lr), p == 0, p == tx_npass(l) - 1>(1 << l, Ns, tpt, jt, tw + toff, sm,
-                                                           src, dst);
-    stockham_passes<l, p + 1>(Ns << lr, p == 0 ? 0 : toff + (Ns << lr), tpt, jt, tw, sm, src,
-                              dst);
+    constexpr unsigned vm = tx_in_mask(1 << lr, p == 0 ? NZ : 0);
+    stockham_pass<(1 << lr), p == 0, p == tx_npass(l) - 1, vm>(1 << l, Ns, tpt, jt, tw + toff,
+                                                               sm, src, dst);
+    stockham_passes<l, p + 1, NZ>(Ns << lr, p == 0 ? 0 : toff + (Ns << lr), tpt, jt, tw, sm,
+                                  src, dst);
   }
 }
 
@@ -340,7 +438,7 @@ __device__ __forceinline__ void stockham_passes(int Ns, int toff, int tpt, int j
 // reads of C and the writes of G runs of TC complex values.  G is
 // [set][nx][nw].  Column stride in shared memory: colstride entries.  twp:
 // the pass-twiddle table of length nx.
-template <int LOG2NX, typename T2>
+template <int LOG2NX, typename T2, int NZ = 0>
 __global__ void __launch_bounds__(512) k_tx_cols(int nk, int nw, int TC, int colstride,
                                                   const T2 *__restrict__ C,
                                                   const T2 *__restrict__ twp,
@@ -387,13 +485,13 @@ __global__ void __launch_bounds__(512) k_tx_cols(int nk, int nw, int TC, int col
   auto dst = [&](int i, T2 v) {
     if (live) Gn[(size_t)i * nw + m] = v;
   };
-  stockham_passes<LOG2NX, 0>(1, 0, tx_tpt(L), jt, twp, col, src, dst);
+  stockham_passes<LOG2NX, 0, NZ>(1, 0, tx_tpt(L), jt, twp, col, src, dst);
 }
 
 // Stage 2: RB rows mx of one set per CTA, thread (row, jt) = (t / tpt,
 // t mod tpt); the row's output is the nt = 2M real values u[set][mx][.].
 // twp: the pass-twiddle table of length M; twz[m] = e^{2 pi i m / nt}, m < M.
-template <int LOG2M, typename T, typename T2>
+template <int LOG2M, typename T, typename T2, int NZ = 0>
 __global__ void __launch_bounds__(512) k_tx_rows(int nx, int nw, int rowstride,
                                                  const T2 *__restrict__ G,
                                                  const T2 *__restrict__ twp,
@@ -434,7 +532,7 @@ __global__ void __launch_bounds__(512) k_tx_rows(int nx, int nw, int rowstride,
   if constexpr (LOG2M == 0) {  // nt = 2: z[0] = Z[0]
     if (jt == 0) dst(0, src(0));
   } else {
-    stockham_passes<LOG2M, 0>(1, 0, tpt, jt, twp, buf, src, dst);
+    stockham_passes<LOG2M, 0, NZ>(1, 0, tpt, jt, twp, buf, src, dst);
   }
 }
 

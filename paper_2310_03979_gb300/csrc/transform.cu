@@ -59,6 +59,32 @@ void with_log2(int v, F &&f) {
   }
 }
 
+// Nonzero input blocks of a stage's first pass (tx_in_mask): a length-2^l
+// transform whose inputs vanish except at the n indices of each end of the
+// spectrum (kk < nk or nx - kk < nk in x; m < nw or M - m < nw in t).  The
+// smallest of 1, 2, 4 blocks (of 2^l / R each, R the first radix) that
+// covers them, else 0 (all).  Pruned passes are compiled for FP32 and
+// transforms of 64 points or more.
+int tx_nz(int l, int n, bool fp32) {
+  if (!fp32 || l < 6) return 0;
+  const int R = 1 << tx_lr(l, 0), LR = (1 << l) / R;
+  for (int nz = 1; nz <= 4 && 2 * nz < R; nz *= 2)
+    if ((long long)nz * LR >= n) return nz;
+  return 0;
+}
+
+// f(integral_constant NZ) for NZ in {0, 1, 2, 4} equal to nz (0 alone when
+// the pruned forms are not compiled for this type and length).
+template <bool PRUNE, class F>
+void with_nz(int nz, F &&f) {
+  if constexpr (PRUNE) {
+    if (nz == 1) return f(std::integral_constant<int, 1>{});
+    if (nz == 2) return f(std::integral_constant<int, 2>{});
+    if (nz == 4) return f(std::integral_constant<int, 4>{});
+  }
+  f(std::integral_constant<int, 0>{});
+}
+
 template <typename T, typename T2>
 int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2 *G) {
   const TxShape s = tx_shape(p, sizeof(T2));
@@ -66,25 +92,33 @@ int transform_impl(srm3_plan *p, cudaStream_t st, const T2 *C, int n, T *out, T2
   const T2 *tw1 = (const T2 *)p->tw, *tw2 = tw1 + tx_twlen(p->log2nx);
   const T2 *twz = tw2 + tx_twlen(p->log2nt - 1);
   cudaError_t e = cudaSuccess;
+  constexpr bool f32 = std::is_same<T, float>::value;
   with_log2<1, 13>(p->log2nx, [&](auto c) {
     constexpr int l = decltype(c)::value;
-    e = cudaFuncSetAttribute(k_tx_cols<l, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess) {
-      k_tx_cols<l, T2><<<dim3(cdiv(p->nw, s.TC), n), s.TC * tx_tpt(1 << l), s.smem1, st>>>(
-          p->nk, p->nw, s.TC, s.colstride, C, tw1, G);
-      e = cudaGetLastError();
-    }
+    with_nz<f32 && l >= 6>(tx_nz(l, p->nk, f32), [&](auto z) {
+      constexpr int nz = decltype(z)::value;
+      e = cudaFuncSetAttribute(k_tx_cols<l, T2, nz>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               lim);
+      if (e == cudaSuccess) {
+        k_tx_cols<l, T2, nz><<<dim3(cdiv(p->nw, s.TC), n), s.TC * tx_tpt(1 << l), s.smem1, st>>>(
+            p->nk, p->nw, s.TC, s.colstride, C, tw1, G);
+        e = cudaGetLastError();
+      }
+    });
   });
   if (e != cudaSuccess) return cuda_fail(e, "output transform, x stage");
   with_log2<0, 12>(p->log2nt - 1, [&](auto c) {
     constexpr int l = decltype(c)::value;
-    e = cudaFuncSetAttribute(k_tx_rows<l, T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             lim);
-    if (e == cudaSuccess) {
-      k_tx_rows<l, T, T2><<<dim3(p->nx / s.rb, n), s.rb * tx_tpt(1 << l), s.smem2, st>>>(
-          p->nx, p->nw, s.rowstride, G, tw2, twz, out);
-      e = cudaGetLastError();
-    }
+    with_nz<f32 && l >= 6>(tx_nz(l, p->nw, f32), [&](auto z) {
+      constexpr int nz = decltype(z)::value;
+      e = cudaFuncSetAttribute(k_tx_rows<l, T, T2, nz>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      if (e == cudaSuccess) {
+        k_tx_rows<l, T, T2, nz><<<dim3(p->nx / s.rb, n), s.rb * tx_tpt(1 << l), s.smem2, st>>>(
+            p->nx, p->nw, s.rowstride, G, tw2, twz, out);
+        e = cudaGetLastError();
+      }
+    });
   });
   if (e != cudaSuccess) return cuda_fail(e, "output transform, t stage");
   return SRM3_OK;

@@ -267,6 +267,37 @@ def test_transform_alone(oracle_lib, precision):
         assert np.abs(u[i] - cu).max() <= tol * np.abs(cu).max()
 
 
+# (nk, nw, nx, nt): lattices that leave most inputs of a stage's first pass
+# zero, so that the FP32 transform takes its pruned first passes -- x stage
+# with 1, 4, 4 nonzero blocks at each end, t stage with 2, 1, 2 (blocks of
+# L/R inputs, R = 16 the first radix at these lengths)
+PRUNED_CASES = [(8, 16, 128, 256), (30, 7, 128, 256), (40, 20, 256, 512)]
+
+
+@pytest.mark.parametrize("nk,nw,nx,nt", PRUNED_CASES)
+def test_transform_pruned_first_passes(oracle_lib, nk, nw, nx, nt):
+    """The first pass of each transform stage skips the butterflies of inputs
+    that are zero by construction (coefficients only at kk < nk or nx - kk
+    < nk, and the t rows only at m < nw or nt/2 - m < nw): against the
+    oracle's direct double sum and cuFFT, 2e-6 of max|u|."""
+    rng = np.random.default_rng(nk * 1000 + nw)
+    wl = W.small_case(nk=nk, nw=nw, nx=nx, nt=nt, precision="fp32")
+    Cn = rng.normal(size=(2, 2, nk, nw)) + 1j * rng.normal(size=(2, 2, nk, nw))
+    C = torch.tensor(np.stack([Cn.real, Cn.imag], -1), dtype=torch.float32, device="cuda")
+    with srm3.Plan.create(wl, eps=0.0) as p:
+        u = p.field_from_coeffs(C).cpu().numpy()
+    for i in range(2):
+        ref = oracle.field_dft(Cn[i], nx, nt)
+        assert np.abs(u[i] - ref).max() <= 2e-6 * np.abs(ref).max()
+        F = torch.zeros((nx, nt), dtype=torch.complex128, device="cuda")
+        Ct = torch.tensor(Cn[i], device="cuda")
+        F[:nk, :nw] += Ct[0]
+        idx = (-torch.arange(nw, device="cuda")) % nt
+        F[:nk].index_add_(1, idx, Ct[1])
+        cu = (torch.fft.ifft2(F) * (nx * nt)).real.cpu().numpy()
+        assert np.abs(u[i] - cu).max() <= 2e-6 * np.abs(cu).max()
+
+
 def test_batch_composition_and_chunking(oracle_lib):
     """A seed's field is bit-identical alone, inside a batch, and across the
     internal 128-sample chunk boundary."""
