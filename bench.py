@@ -830,8 +830,9 @@ def main():
         # the bracketing pass is an FP32 pass (counted above) instead of the
         # linear pass; conv twiddles 1; per chunk phases, three FFT
         # self-convolution passes, two output FFT stages
+        # (+ the coarse search's kernels: its bound is a pass as well)
         launches_per_step = (1 + 3 + 2 + 2 + (info.root_passes + info.root_passes_fp32)
-                             + 4 + 1 + 6 * chunks)
+                             + 4 + 1 + 6 * chunks + info.coarse_launches)
     if prebuilt is not None:
         # sampling only: per chunk phases, sum and difference pair sums, two
         # FFT stages

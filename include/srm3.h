@@ -244,8 +244,8 @@ typedef struct srm3_info {
     int32_t coarse_fk, coarse_fw; /* the coarse lattice of the eps search takes
                                 every coarse_fk-th kappa and coarse_fw-th omega
                                 point of this one (1, 1: no coarse search; plans
-                                with a target, sum interactions, Gaussian
-                                envelope, at least 65536 points) */
+                                with a target, sum interactions and at least
+                                65536 points, either envelope kind) */
     int32_t coarse_launches;  /* kernels the coarse search launched */
     int32_t coarse_passes;    /* its FP32 recursion passes */
 } srm3_info;

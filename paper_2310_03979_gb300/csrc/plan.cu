@@ -1063,6 +1063,7 @@ static int coarse_root(srm3_plan *p, cudaStream_t st, double target, double *xc)
   c.precision = SRM3_FP32;
   c.device = p->device;
   c.rec_sep = p->rec_sep;
+  c.sep = p->sep;
   c.sigma_g = p->sigma_g;
   c.h_pinned = p->h_pinned;
   c.h_err = p->h_err;
@@ -1074,7 +1075,8 @@ static int coarse_root(srm3_plan *p, cudaStream_t st, double target, double *xc)
                      c->EkSq,     c->EkSq32,    c->EwSq,    c->EwSq32,       c->G2,
                      c->G2_32,    c->rs_a2,     c->rs_b2,   c->qm3,          c->rec_items,
                      c->rec_lev_off, c->rec_pairs, c->rec_pair_off, c->rec_partial,
-                     c->rec_max,  c->rec_bar,   c->red_part};
+                     c->rec_max,  c->rec_bar,   c->red_part, c->env_e2,      c->env_b2,
+                     c->rec_z,    c->tw_rec32,  c->tw_rec64};
       for (void *d : dev)
         if (d) dev_free(d, st);
     }
@@ -1103,13 +1105,25 @@ static int coarse_root(srm3_plan *p, cudaStream_t st, double target, double *xc)
   SRM3_CUDA(dev_alloc(&c.EwSq, 2 * nwc * sizeof(double), st));
   SRM3_CUDA(dev_alloc(&c.EwSq32, 2 * nwc * sizeof(float), st));
   k_subsample<<<cdiv(nlc, 256), 256, 0, st>>>(p->nw, fk, fw, nkc, nwc, p->S, c.S);
+  c.n_launch += 1;
   // the envelope's widths in the coarse lattice's index units: the same
   // function of frequency as on this lattice
   const double sk = p->sigma_g * p->nk / fk, sw = p->sigma_g * p->nw / fw;
-  k_env_sq<<<cdiv(nkc, 256), 256, 0, st>>>(nkc, sk, c.EkSq, c.EkSq32);
-  k_env_sq<<<cdiv(2 * nwc, 256), 256, 0, st>>>(2 * nwc, sw, c.EwSq, c.EwSq32);
-  c.n_launch += 3;
-  if (c.rec_sep) {
+  if (c.sep) {
+    // separable kind: the factors a^2 and b^2 at the coarse points
+    SRM3_CUDA(dev_alloc(&c.env_e2, nlc * sizeof(double), st));
+    SRM3_CUDA(dev_alloc(&c.env_b2, nlc * sizeof(double), st));
+    k_subsample<<<cdiv(nlc, 256), 256, 0, st>>>(p->nw, fk, fw, nkc, nwc, p->env_e2, c.env_e2);
+    k_subsample<<<cdiv(nlc, 256), 256, 0, st>>>(p->nw, fk, fw, nkc, nwc, p->env_b2, c.env_b2);
+    c.n_launch += 2;
+  } else {
+    k_env_sq<<<cdiv(nkc, 256), 256, 0, st>>>(nkc, sk, c.EkSq, c.EkSq32);
+    k_env_sq<<<cdiv(2 * nwc, 256), 256, 0, st>>>(2 * nwc, sw, c.EwSq, c.EwSq32);
+    c.n_launch += 2;
+  }
+  if (c.sep) {
+    // no g^2 table: the separable recursion takes the pair factor from a^2
+  } else if (c.rec_sep) {
     SRM3_CUDA(dev_alloc(&c.rs_a2, nlc * sizeof(double), st));
     SRM3_CUDA(dev_alloc(&c.rs_b2, nlc * sizeof(double), st));
     k_gauss_sep<<<cdiv(nlc, 256), 256, 0, st>>>(nkc, nwc, sk, sw, c.rs_a2, c.rs_b2);
@@ -1118,7 +1132,7 @@ static int coarse_root(srm3_plan *p, cudaStream_t st, double target, double *xc)
     SRM3_CUDA(dev_alloc(&c.G2_32, nlc * sizeof(float), st));
     k_g2<<<cdiv(nlc, 256), 256, 0, st>>>(nkc, nwc, c.EkSq, c.EwSq, c.G2, c.G2_32);
   }
-  c.n_launch += 1;
+  c.n_launch += c.sep ? 0 : 1;
   SRM3_CUDA(cudaGetLastError());
   int rc = setup_recursion(&c, st);
   if (rc) return rc;
@@ -1149,7 +1163,7 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   Search32 s;
   s.pts.push_back({0.0, -target});
   p->coarse_start = false;
-  if (!p->sep) {
+  {
     double xc = -1.0;
     rc = coarse_root(p, st, target, &xc);
     if (rc) return rc;

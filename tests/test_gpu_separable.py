@@ -66,6 +66,31 @@ def test_separable_plan_tables_and_eps(oracle_lib, precision, envelope):
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=rel, atol=1e-15)
 
 
+@pytest.mark.parametrize("envelope", ["separable", "sum"])
+def test_separable_eps_search_coarse_start(envelope):
+    """A 256 x 256 lattice with a separable envelope: the eps search starts
+    from the root on the 64 x 64 lattice of every fourth point (the factors
+    a^2 and b^2 taken at those points), and the FP32 plan's eps agrees with
+    the FP64 plan's (target to 1e-13, FP64 passes to the end) to 2e-8."""
+    res = {}
+    for precision in ("fp64", "fp32"):
+        wl = sep_case(nk=256, nw=256, nx=256, nt=512, seeds=(1,), precision=precision,
+                      envelope=envelope)
+        with srm3.Plan.create(wl) as p:
+            res[precision] = p.info()
+    for info in res.values():
+        assert (info.coarse_fk, info.coarse_fw) == (4, 4)
+        # the smooth Gaussian factors place the coarse root inside the window;
+        # the sum envelope's b ~ 1/sqrt(kk kw) weights the lattice's lowest
+        # points, where the coarse quadrature differs most (either way of the
+        # search is correct)
+        if envelope == "separable":
+            assert info.recursion_flags & srm3.SRM3_REC_COARSE_START
+    assert abs(res["fp64"].max_sum_b2 - wl.target) <= 1e-13
+    assert abs(res["fp32"].max_sum_b2 - wl.target) <= 1e-9
+    assert res["fp32"].eps == pytest.approx(res["fp64"].eps, rel=2e-8)
+
+
 @pytest.mark.parametrize("nk,nw", [(24, 37), (40, 70), (1, 9), (9, 1), (100, 180)])
 def test_separable_recursion_at_fixed_eps(oracle_lib, nk, nw):
     """The bulk of a separable pass is an online FFT self-convolution of h
