@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsrm3.so")
-SOURCES = ["plan.cu", "sample.cu", "transform.cu", "noalloc.cu", "stats.cu"]
+SOURCES = ["plan.cu", "sample.cu", "transform.cu", "conv.cu", "noalloc.cu", "stats.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

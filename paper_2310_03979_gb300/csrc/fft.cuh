@@ -418,19 +418,32 @@ __device__ __forceinline__ void stockham_pass(int L, int Ns, int tpt, int jt,
 // unrolled at compile time so that each pass keeps only its own 16 values
 // live; Ns is the length transformed by the passes before p, toff the
 // offset of pass p's run in the pass-twiddle table tw.
-// NZ: the nonzero input blocks of the first pass (tx_in_mask; 0 = all).
-template <int l, int p, int NZ, typename T2, class Src, class Dst>
+// VM0: the inputs of the first pass that can be nonzero (bit r: the block
+// r of L/R inputs, R the first radix; 0 = all).
+template <int l, int p, unsigned VM0, typename T2, class Src, class Dst>
 __device__ __forceinline__ void stockham_passes(int Ns, int toff, int tpt, int jt,
                                                 const T2 *__restrict__ tw, T2 *sm, Src &src,
                                                 Dst &dst) {
   if constexpr (p < tx_npass(l)) {
     constexpr int lr = tx_lr(l, p);
-    constexpr unsigned vm = tx_in_mask(1 << lr, p == 0 ? NZ : 0);
+    constexpr unsigned vm = (p == 0 && VM0 != 0u) ? VM0 : tx_in_mask(1 << lr, 0);
     stockham_pass<(1 << lr), p == 0, p == tx_npass(l) - 1, vm>(1 << l, Ns, tpt, jt, tw + toff,
                                                                sm, src, dst);
-    stockham_passes<l, p + 1, NZ>(Ns << lr, p == 0 ? 0 : toff + (Ns << lr), tpt, jt, tw, sm,
-                                  src, dst);
+    stockham_passes<l, p + 1, VM0>(Ns << lr, p == 0 ? 0 : toff + (Ns << lr), tpt, jt, tw, sm,
+                                   src, dst);
   }
+}
+
+// The first pass's mask for inputs at both ends of the spectrum (nz blocks
+// each, tx_in_mask) or at the low end only (the lower half of the blocks:
+// a zero-padded sequence of at most L/2 entries).
+template <int l>
+__host__ __device__ constexpr unsigned tx_mask_ends(int nz) {
+  return tx_in_mask(1 << tx_lr(l, 0), nz);
+}
+template <int l>
+__host__ __device__ constexpr unsigned tx_mask_low_half() {
+  return (1u << ((1 << tx_lr(l, 0)) / 2)) - 1u;
 }
 
 // Stage 1: TC columns m0 + c of one coefficient set per CTA (blockIdx.y =
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(512) k_tx_cols(int nk, int nw, int TC, int col
   auto dst = [&](int i, T2 v) {
     if (live) Gn[(size_t)i * nw + m] = v;
   };
-  stockham_passes<LOG2NX, 0, NZ>(1, 0, tx_tpt(L), jt, twp, col, src, dst);
+  stockham_passes<LOG2NX, 0, tx_mask_ends<LOG2NX>(NZ)>(1, 0, tx_tpt(L), jt, twp, col, src, dst);
 }
 
 // Stage 2: RB rows mx of one set per CTA, thread (row, jt) = (t / tpt,
@@ -532,7 +545,7 @@ __global__ void __launch_bounds__(512) k_tx_rows(int nx, int nw, int rowstride,
   if constexpr (LOG2M == 0) {  // nt = 2: z[0] = Z[0]
     if (jt == 0) dst(0, src(0));
   } else {
-    stockham_passes<LOG2M, 0, NZ>(1, 0, tpt, jt, twp, buf, src, dst);
+    stockham_passes<LOG2M, 0, tx_mask_ends<LOG2M>(NZ)>(1, 0, tpt, jt, twp, buf, src, dst);
   }
 }
 

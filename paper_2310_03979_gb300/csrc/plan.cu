@@ -1651,7 +1651,6 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
     while ((1 << p->log2cNw) < 2 * nw - 1) ++p->log2cNw;
     p->cNk = 1 << p->log2cNk;
     p->cNw = 1 << p->log2cNw;
-    p->log2ntwc = std::max(p->log2cNk, p->log2cNw);
   }
   p->rowstride = nw + 2 * kPad;  // y row length, workspace or batch buffers
   SRM3_CUDA(dev_alloc(&p->Ek, nk * es, st));
@@ -1673,10 +1672,11 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
     k_tx_twiddles<float2><<<cdiv(tw_n, 256), 256, 0, st>>>(p->log2nx, p->log2nt - 1,
                                                             (float2 *)p->tw);
     if (p->sep) {
-      SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(float2), st));
-      k_twiddles<float2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
-                                                                        p->log2ntwc,
-                                                                        (float2 *)p->tw_conv);
+      // pass twiddles of the self-convolution's lengths Nk, then Nw
+      const int ntwc = tx_twlen(p->log2cNk) + tx_twlen(p->log2cNw) + (1 << p->log2cNw);
+      SRM3_CUDA(dev_alloc(&p->tw_conv, (size_t)ntwc * sizeof(float2), st));
+      k_tx_twiddles<float2><<<cdiv(ntwc, 256), 256, 0, st>>>(p->log2cNk, p->log2cNw,
+                                                            (float2 *)p->tw_conv);
     }
   } else {
     k_env<double><<<cdiv(nk, 256), 256, 0, st>>>(nk, 0, p->sigma_g * nk, (double *)p->Ek);
@@ -1685,10 +1685,11 @@ int prepare_shape_tables(srm3_plan *p, cudaStream_t st) {
     k_tx_twiddles<double2><<<cdiv(tw_n, 256), 256, 0, st>>>(p->log2nx, p->log2nt - 1,
                                                              (double2 *)p->tw);
     if (p->sep) {
-      SRM3_CUDA(dev_alloc(&p->tw_conv, ((size_t)1 << p->log2ntwc) * sizeof(double2), st));
-      k_twiddles<double2><<<cdiv(1 << p->log2ntwc, 256), 256, 0, st>>>(1 << p->log2ntwc,
-                                                                         p->log2ntwc,
-                                                                         (double2 *)p->tw_conv);
+      // pass twiddles of the self-convolution's lengths Nk, then Nw
+      const int ntwc = tx_twlen(p->log2cNk) + tx_twlen(p->log2cNw) + (1 << p->log2cNw);
+      SRM3_CUDA(dev_alloc(&p->tw_conv, (size_t)ntwc * sizeof(double2), st));
+      k_tx_twiddles<double2><<<cdiv(ntwc, 256), 256, 0, st>>>(p->log2cNk, p->log2cNw,
+                                                            (double2 *)p->tw_conv);
     }
   }
   SRM3_CUDA(cudaGetLastError());

@@ -10,7 +10,6 @@
 
 #include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
-#include "conv.cuh"
 #include "fft.cuh"
 #include "pairsum.cuh"
 #include "srm3_internal.cuh"
@@ -146,10 +145,10 @@ int ensure_workspace(srm3_plan *p, int chunk) {
   SRM3_CUDA(dev_alloc(&p->H, (size_t)cap * transform_elems(p) * e2, p->stream));
   if (p->mixed && p->precision == SRM3_FP32)
     SRM3_CUDA(dev_alloc(&p->ys, (size_t)p->nk * p->rowstride * sp * e2, p->stream));
-  if (p->sep) {  // the self-convolution grid of every sheet-sample of a chunk
+  if (p->sep) {  // the self-convolution grid's n_kappa rows, every sheet-sample of a chunk
     if (p->Zc) dev_free(p->Zc, p->stream);
     p->Zc = nullptr;
-    SRM3_CUDA(dev_alloc(&p->Zc, (size_t)2 * cap * p->cNk * p->cNw * e2, p->stream));
+    SRM3_CUDA(dev_alloc(&p->Zc, (size_t)2 * cap * p->nk * p->cNw * e2, p->stream));
     p->zc_ss = 2LL * cap;
   }
   // stream-ordered blocks: usable from any stream (batches) once this passes
@@ -391,50 +390,6 @@ static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
       p->mixed ? 1 : 0, p->row_lo, p->row_hi);
   SRM3_CUDA(cudaGetLastError());
   return SRM3_OK;
-}
-
-// The separable pair sum of n samples (y / y0 laid out for sspad_for(n)) by
-// FFT self-convolution on stream st (conv.cuh), into C_out.
-template <typename T>
-static int conv_pairsum_impl(srm3_plan *p, cudaStream_t st, int n, const void *y, const void *y0,
-                             void *C_out) {
-  using T2 = typename Vec2<T>::type;
-  const int SS = 2 * n, sp = sspad_for(n);
-  if (SS > p->zc_ss) return fail(SRM3_ERR_INVALID_ARG, "separable pair sum: workspace too small");
-  const T *e = std::is_same<T, float>::value ? (const T *)p->env_e32 : (const T *)p->env_e;
-  const T2 *tw = (const T2 *)p->tw_conv;
-  T2 *Z = (T2 *)p->Zc;
-  const size_t srow = (size_t)fft_row_len(p->cNw) * sizeof(T2);
-  int TC = 16;
-  while (TC > 1 && (size_t)TC * fft_col_stride(p->cNk) * sizeof(T2) > 96 * 1024) TC >>= 1;
-  TC = std::min(TC, p->cNw);
-  const size_t scol = (size_t)TC * fft_col_stride(p->cNk) * sizeof(T2);
-  if (srow > 200 * 1024 || scol > 200 * 1024)
-    return fail(SRM3_ERR_NOT_SUPPORTED,
-                "separable pair sum: a padded row or column does not fit in shared memory");
-  SRM3_CUDA(cudaFuncSetAttribute(k_conv_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)srow));
-  SRM3_CUDA(cudaFuncSetAttribute(k_conv_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)scol));
-  SRM3_CUDA(cudaFuncSetAttribute(k_conv_out<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)srow));
-  k_conv_rows<T><<<dim3(p->nk, SS), 256, srow, st>>>(p->nk, p->nw, p->log2cNw, p->cNk, sp,
-                                                      p->rowstride, y, e, tw, Z);
-  k_conv_cols<T><<<dim3(p->cNw / TC, SS), 512, scol, st>>>(p->nk, p->log2cNk, p->cNw, TC, tw,
-                                                            Z);
-  const T *eb = std::is_same<T, float>::value ? (const T *)p->env_b32 : (const T *)p->env_b;
-  k_conv_out<T><<<dim3(p->nk, SS), 256, srow, st>>>(
-      p->nk, p->nw, p->log2cNw, p->cNk, sp, p->rowstride, y, (const T2 *)y0, e, eb,
-      (const T *)p->Pk, (const T *)p->ck, (T)std::cos(p->beta), (T)std::sin(p->beta), tw, Z,
-      (T2 *)C_out);
-  SRM3_CUDA(cudaGetLastError());
-  return SRM3_OK;
-}
-
-int conv_pairsum_on(srm3_plan *p, cudaStream_t st, int n, const void *y, const void *y0,
-                    void *C_out) {
-  return p->precision == SRM3_FP32 ? conv_pairsum_impl<float>(p, st, n, y, y0, C_out)
-                                   : conv_pairsum_impl<double>(p, st, n, y, y0, C_out);
 }
 
 int run_pairsum(srm3_plan *p, int n, void *C_out) {

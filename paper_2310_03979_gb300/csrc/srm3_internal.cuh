@@ -109,7 +109,7 @@ struct srm3_plan {
   // FFT self-convolution grid of the separable pair sum (powers of two,
   // cNk >= 2 nk - 1, cNw >= 2 nw - 1), its twiddles e^{+2 pi i j / ntwc},
   // and the workspace of zc_ss sheet-samples (complex, plan precision)
-  int cNk = 0, cNw = 0, log2cNk = 0, log2cNw = 0, log2ntwc = 0;
+  int cNk = 0, cNw = 0, log2cNk = 0, log2cNw = 0;
   void *tw_conv = nullptr;
   void *Zc = nullptr;
   long long zc_ss = 0;
@@ -261,6 +261,10 @@ int stage_end(srm3_plan *p, int rec);
 int collect_timings(srm3_plan *p);
 int check_pairsum_error(srm3_plan *p);
 int sspad_for(int chunk);
+// The separable pair sum (FFT self-convolution, conv.cu) of n samples whose
+// phasor rows y / y0 are laid out for sspad_for(n), on stream st.
+int conv_pairsum_on(srm3_plan *p, cudaStream_t st, int n, const void *y, const void *y0,
+                    void *C_out);
 int build_w_table(srm3_plan *p, cudaStream_t st);
 // autotuner choices per lattice shape (process-wide): storage (or -1 when
 // the shape was never tuned) and the pair-sum tile's compute warps
