@@ -817,6 +817,8 @@ def main():
     flags = info.recursion_flags
     sep_gauss = 1 if (flags & srm3.SRM3_REC_SEPARABLE) and wl.envelope == "gauss" else 0
     moved = 2 if flags & srm3.SRM3_REC_TABLES_MOVED else 0
+    # tables interpolated from a three-plane FP64 pass (FP64 plans): 1 kernel
+    moved += 1 if flags & srm3.SRM3_REC_TABLES_INTERPOLATED else 0
     # the separable pair sum's scaled tables (FP32 Gaussian plans, either storage)
     sep_tables = 1 if sep_gauss and es == 4 and getattr(wl, "interactions", "sum") == "sum" else 0
     # coarse start of the eps search: its own kernels (subsampled spectrum,

@@ -240,7 +240,12 @@ typedef struct srm3_info {
                                 started from the root of the same search on a
                                 coarser lattice (coarse_fk, coarse_fw below) and
                                 one FP32 pass on this lattice bracketed it (no
-                                linear bound on this lattice) */
+                                linear bound on this lattice);
+                                bit 4 (SRM3_REC_TABLES_INTERPOLATED): the tables
+                                are those of one FP64 pass at three eps^2 values
+                                x32 (1 +- 2e-6) around the FP32 root, taken per
+                                point at the final eps^2 by the quadratic through
+                                the three (FP64 plans) */
     int32_t coarse_fk, coarse_fw; /* the coarse lattice of the eps search takes
                                 every coarse_fk-th kappa and coarse_fw-th omega
                                 point of this one (1, 1: no coarse search; plans
@@ -254,6 +259,7 @@ typedef struct srm3_info {
 #define SRM3_REC_TABLES_MOVED 2
 #define SRM3_PAIRSUM_SEPARABLE 4
 #define SRM3_REC_COARSE_START 8
+#define SRM3_REC_TABLES_INTERPOLATED 16
 
 int srm3_plan_info(const srm3_plan *plan, srm3_info *info);
 

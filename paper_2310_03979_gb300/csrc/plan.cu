@@ -147,6 +147,37 @@ __global__ void k_sb2_shift(long long n, const double *__restrict__ S, double *_
     atomicMax(maxb, (unsigned long long)__double_as_longlong(m));
 }
 
+// The tables at x from an FP64 pass at three values x_m around it: per
+// point the quadratic through (x_m, sum_b2_m) taken at x (Lagrange weights
+// w_m), clamped at 0, and q = 1/(1 - sum_b2) (0 where S = 0, or where
+// sum_b2 >= 1, which also sets *err); into plane 0 of sum_b2 and into q;
+// max_k sum_b2 into *maxb (bits of a double >= 0, zeroed before).
+__global__ void k_sb2_interp3(long long n, const double *__restrict__ S, double *__restrict__ sb2,
+                              double w0, double w1, double w2, double *__restrict__ q,
+                              unsigned long long *maxb, int *err) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < n) {
+    if (S[i] > 0.0) {
+      v = fma(w0, sb2[i], fma(w1, sb2[n + i], w2 * sb2[2 * n + i]));
+      v = v < 0.0 ? 0.0 : v;
+      if (v < 1.0) {
+        q[i] = 1.0 / (1.0 - v);
+      } else {
+        q[i] = 0.0;
+        atomicOr(err, 1);
+      }
+    } else {
+      q[i] = 0.0;
+    }
+    sb2[i] = v;
+  }
+  double m = v;  // warp maximum first: one atomic per warp
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(maxb, (unsigned long long)__double_as_longlong(m));
+}
+
 // Reductions of plane 0 of sum_b2 and of S: max sum_b2, min (1 - sum_b2)
 // over S > 0 and sum S, into scal[9], scal[10], scal[11].  k_reduce_part
 // leaves one partial per CTA (kReduceCtas of them) and k_reduce_final
@@ -381,6 +412,10 @@ static constexpr double kSepExpMax = 40.0;
 // find_eps, for steps up to kShiftMax of x
 static constexpr double kShiftTol = 1e-10;
 static constexpr double kShiftMax = 1e-5;
+// tighter targets: one FP64 pass at x32 (1 + {-d, 0, d}), d = kInterpDel, and
+// the tables interpolated to a root within kInterpReach x32 of x32
+static constexpr double kInterpDel = 2e-6;
+static constexpr double kInterpReach = 1e-5;
 // pinned host scalars of a plan build (8 + 4 kPlanes doubles): [0, kPlanes)
 // eps^2 dk dw per plane going in, [8, 8 + kPlanes) the planes' max sum_b2
 // coming back ([9] the linear pass's max), kSumSlot the sum of S
@@ -425,8 +460,14 @@ static int rec_occupancy_of(RecOccupancy &o) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes, SEP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 3, SEP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1, SEP>,
                                                           kRecThreads, sm));
+  int b64x3 = 0;
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64x3, k_rec_pass<double, 3, SEP>,
+                                                          kRecThreads, sm));
+  b64 = std::min(b64, b64x3);
   b64f = b64;
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes, SEP>,
                                                           kRecThreads, sm));
@@ -573,12 +614,17 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.pairs = p->rec_pairs;
   A.pair_off = p->rec_pair_off;
   A.S = p->S;
-  if (fp64 && M != 1) return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes one plane");
+  if (fp64 && M != 1 && M != 3)
+    return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes one or three planes");
+  if (fp64 && M == 3 && (p->rec_fft || p->mixed))
+    return fail(SRM3_ERR_INVALID_ARG, "three-plane FP64 pass: direct bulk, sum pairs only");
   const bool sepf = p->rec_sep;
-  A.q = !fp64 ? (void *)p->qm32 : (sepf ? (void *)p->qh : (void *)p->qm);
+  const bool x3 = fp64 && M == 3;
+  if (x3 && sepf && !p->qo3) SRM3_CUDA(dev_alloc(&p->qo3, 3 * (size_t)p->nk * p->nw * sizeof(double), st));
+  A.q = !fp64 ? (void *)p->qm32 : x3 ? (void *)p->qm3 : (sepf ? (void *)p->qh : (void *)p->qm);
   A.e2 = sepf ? (p->sep ? p->env_e2 : p->rs_a2) : nullptr;
   A.e2k = sepf ? (p->sep ? p->env_b2 : p->rs_b2) : nullptr;
-  A.qout = (sepf && fp64) ? p->qm : nullptr;
+  A.qout = (sepf && fp64) ? (x3 ? p->qo3 : p->qm) : nullptr;
   A.dsum = (p->mixed && fp64 && M == 1) ? p->Dsum : nullptr;
   A.acc = p->rec_partial;
   A.sb2 = p->sb2;
@@ -597,10 +643,13 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   const int smem = kFringeSmem + (p->rec_fft ? kRecSmem : 0);
   void *args[] = {&A};
   SRM3_CUDA(cudaEventRecord(t_ev[0], st));
-  const void *kern = fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>
-                                  : (const void *)k_rec_pass<double, 1, false>)
-                          : (sepf ? (const void *)k_rec_pass<float, kPlanes, true>
-                                  : (const void *)k_rec_pass<float, kPlanes, false>);
+  const void *kern =
+      x3 ? (sepf ? (const void *)k_rec_pass<double, 3, true>
+                 : (const void *)k_rec_pass<double, 3, false>)
+      : fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>
+                     : (const void *)k_rec_pass<double, 1, false>)
+             : (sepf ? (const void *)k_rec_pass<float, kPlanes, true>
+                     : (const void *)k_rec_pass<float, kPlanes, false>);
   SRM3_CUDA(cudaLaunchCooperativeKernel(kern, fp64 ? p->rec_grid64 : p->rec_grid32, kRecThreads,
                                         args, smem, st));
   SRM3_CUDA(cudaGetLastError());
@@ -941,19 +990,23 @@ static int wide_search(srm3_plan *p, cudaStream_t st, double target, Search32 &s
     return fail(SRM3_ERR_BISECTION_FAILED, "no bispectral pairs: max_k sum_b2 is 0 for every eps");
   // at the root every sum_b2 <= target, so q <= 1/(1 - target) and x* lies
   // in [(1 - target)^2 x0, x0] (q >= 1 gives the upper end); the first pass
-  // samples that range, with a margin for the FP32 Lmax.  The second pass
-  // centres its planes on the first pass's quadratic estimate, half-width
-  // four times that estimate's distance from the secant root.
+  // samples that range, with a margin for the FP32 Lmax.  Each later pass
+  // centres its planes on the quadratic estimate of the passes so far,
+  // half-width four times that estimate's distance from the secant root
+  // (at least 2e-4 of it, at most half its distance to the bracket's ends),
+  // until the root lies between two planes of one pass -- normally after
+  // the second pass; a zoom that missed the root takes a third.
   const double x0 = target / Lmax;
   s.x0 = x0;
   double lo = 0.9 * (1.0 - target) * (1.0 - target) * x0, hi = 1.01 * x0;
   bool hi_known = false;
-  double zoom_c = 0.0, zoom_w = 0.0;  // centre and half-width of the second pass
+  double zoom_c = 0.0, zoom_w = 0.0;  // centre and half-width of the next zoom
   for (int pass = 0; pass < 12; ++pass) {
+    const double lo_pass = lo, hi_pass = hi;  // the range the planes below cover
     for (int m = 0; m < kPlanes; ++m) {
       if (pass == 0)
         s.xs[m] = lo + (hi - lo) * m / (kPlanes - 1);
-      else if (pass == 1 && zoom_w > 0.0)
+      else if (zoom_w > 0.0)
         s.xs[m] = zoom_c - zoom_w + 2.0 * zoom_w * m / (kPlanes - 1);
       else
         s.xs[m] = hi_known ? lo + (hi - lo) * (m + 1) / (kPlanes + 1)
@@ -969,14 +1022,19 @@ static int wide_search(srm3_plan *p, cudaStream_t st, double target, Search32 &s
       lo = s.pts.back().first;
       hi = 2.0 * lo;
       hi_known = false;
+      zoom_w = 0.0;
       continue;
     }
     lo = s.pts[j - 1].first;
     hi = s.pts[j].first;
     hi_known = true;
-    if (pass >= 1 && std::isfinite(s.pts[j].second)) return SRM3_OK;
+    // done when both ends of the bracket are planes of this pass (a zoom, or
+    // a subdivision of the last bracket)
+    const double h =
+        pass == 0 ? 0.0 : (zoom_w > 0.0 ? 2.0 * zoom_w : hi_pass - lo_pass) / (kPlanes - 1);
+    if (pass >= 1 && std::isfinite(s.pts[j].second) && hi - lo <= 1.01 * h) return SRM3_OK;
     zoom_w = 0.0;
-    if (pass == 0 && std::isfinite(s.pts[j].second) &&
+    if (std::isfinite(s.pts[j].second) &&
         ((j + 1 < s.pts.size() && std::isfinite(s.pts[j + 1].second)) || j >= 2)) {
       // quadratic through the bracket and its feasible neighbour above, else
       // the one below
@@ -1253,7 +1311,79 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   double x = x32, xp = 0.0, fp = 0.0;
   bool have_prev = false;
   p->eps_shifted = false;
-  for (int it = 0; it < 6; ++it) {
+  p->eps_interp = false;
+  // Tight targets (FP64 plans, direct bulk, sum pairs): one FP64 pass at the
+  // three values x32 (1 + {-d, 0, d}); the root xr of the inverse quadratic
+  // through the three (x, f), and every point's tables interpolated to it by
+  // the quadratic through its three values -- an error of the order of the
+  // third derivative times d^3 (~1e-17 relative), below the FP64 rounding of
+  // the sums.  Accepted when the interpolated max meets the target within
+  // tol; else the three values join the bracket and the steps below go on
+  // from xr.
+  auto note = [&](double xv, double f) {
+    if (f < 0) {
+      if (xv > b.xlo) {
+        b.xlo = xv;
+        b.flo = f;
+      }
+    } else if (b.hi_failed || xv < b.xhi) {
+      b.xhi = xv;
+      b.fhi = f;
+      b.hi_failed = false;
+    }
+  };
+  if (tol < kShiftTol && !p->rec_fft && !p->mixed && hi_ok) {
+    double x3[3] = {x32 * (1.0 - kInterpDel), x32, x32 * (1.0 + kInterpDel)};
+    PassResult r3[3];
+    rc = run_pass_multi(p, st, x3, 3, true, r3);
+    if (rc) return rc;
+    bool ok3 = true;
+    double f3[3];
+    for (int m = 0; m < 3; ++m) {
+      if (r3[m].err) {
+        ok3 = false;
+        b.xhi = std::min(b.xhi, x3[m]);
+        b.hi_failed = true;
+        continue;
+      }
+      f3[m] = r3[m].max_sb2 - target;
+      note(x3[m], f3[m]);
+    }
+    if (ok3 && f3[2] > f3[0]) {
+      slope32 = (f3[2] - f3[0]) / (x3[2] - x3[0]);
+      const double xr = quad_root(x3[0], f3[0], x3[1], f3[1], x3[2], f3[2]);
+      // the next point of the steps below in any case (beyond the reach, x32
+      // was off: xr is an extrapolation, still the best estimate)
+      if (xr > b.xlo && (b.hi_failed || xr < b.xhi)) x = xr;
+      if (xr > b.xlo && (b.hi_failed || xr < b.xhi) && std::fabs(xr - x32) <= kInterpReach * x32) {
+        const double w0 = (xr - x3[1]) * (xr - x3[2]) / ((x3[0] - x3[1]) * (x3[0] - x3[2]));
+        const double w1 = (xr - x3[0]) * (xr - x3[2]) / ((x3[1] - x3[0]) * (x3[1] - x3[2]));
+        const double w2 = (xr - x3[0]) * (xr - x3[1]) / ((x3[2] - x3[0]) * (x3[2] - x3[1]));
+        const long long nl = (long long)p->nk * p->nw;
+        SRM3_CUDA(cudaMemsetAsync(p->rec_max, 0, sizeof(unsigned long long), st));
+        SRM3_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+        k_sb2_interp3<<<cdiv(nl, 256), 256, 0, st>>>(nl, p->S, p->sb2, w0, w1, w2, p->qm,
+                                                     p->rec_max, p->err);
+        SRM3_CUDA(cudaGetLastError());
+        SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, st));
+        SRM3_CUDA(cudaMemcpyAsync(p->h_err, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRM3_CUDA(cudaStreamSynchronize(st));
+        const double mx = p->h_pinned[8];  // the bits of a double, copied as such
+        x = xr;
+        if (!p->h_err[0] && std::fabs(mx - target) <= tol) {
+          best.max_sb2 = mx;
+          best.min_pure = 1.0 - mx;
+          best.sumS = r3[1].sumS;
+          best.err = 0;
+          xbest = xr;
+          converged = at_best = true;
+          p->eps_interp = true;
+        }
+      }
+    }
+  }
+  for (int it = 0; it < 6 && !converged; ++it) {
     PassResult q1;
     rc = run_pass(p, st, x, true, &q1);
     if (rc) return rc;
@@ -1796,7 +1926,8 @@ void free_plan(srm3_plan *p) {
                  p->sep_b ? p->env_b : nullptr, p->sep_b ? p->env_b2 : nullptr,
                  p->sep_b ? (void *)p->env_b32 : nullptr,
                  p->Dsum, p->qprev, p->qlo, p->fp_change, p->Ewd, p->ys, p->super_order_d,
-                 p->rs_a2, p->rs_b2, p->dsb2, p->red_part, p->sqq_s, p->Pk_s, p->ck_s, p->aK};
+                 p->rs_a2, p->rs_b2, p->dsb2, p->red_part, p->sqq_s, p->Pk_s, p->ck_s, p->aK,
+                 p->qo3};
   // no plan work may be in flight; the blocks go back to the pool
   cudaDeviceSynchronize();
   for (void *d : dev)
@@ -1964,6 +2095,7 @@ SRM3_API int srm3_plan_info(const srm3_plan *plan, srm3_info *info) {
   info->tile_width = kTileR * plan->ps_nc;
   info->recursion_flags = (plan->rec_sep ? SRM3_REC_SEPARABLE : 0) |
                           (plan->eps_shifted ? SRM3_REC_TABLES_MOVED : 0) |
+                          (plan->eps_interp ? SRM3_REC_TABLES_INTERPOLATED : 0) |
                           (pairsum_sep_now(plan) ? SRM3_PAIRSUM_SEPARABLE : 0) |
                           (plan->coarse_start ? SRM3_REC_COARSE_START : 0);
   info->coarse_fk = plan->coarse_fk;

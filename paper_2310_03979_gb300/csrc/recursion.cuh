@@ -31,7 +31,7 @@ struct RecArgs {
   const double *scal;   // [M]: eps^2 dk dw per plane
   // separable envelope (else NULL): e^2 per point.  The pair sums then run
   // over h = e^2 q (stored in q, G2 all ones), sum_b2(k) takes the factor
-  // e_k^2, and the FP64 pass writes q itself to qout
+  // e_k^2, and the FP64 pass writes q itself to qout ([M][nl])
   const double *e2;   // a^2: h = a^2 q
   const double *e2k;  // b^2: the factor of sum_b2(k)
   double *qout;
@@ -178,11 +178,11 @@ __device__ __forceinline__ T finalize_plane(const RecArgs &A, long long k, int m
     // that masked pair slots, which read the origin, add nothing
     const T h = A.e2 ? (k == 0 ? (T)0 : ek2 * qk) : qk;
     q[k * M + m] = h;
-    if (A.qout) A.qout[k] = (double)qk;
+    if (A.qout) A.qout[m * A.nl + k] = (double)qk;
     return h;
   }
   q[k * M + m] = (T)0;
-  if (A.qout) A.qout[k] = 0.0;
+  if (A.qout) A.qout[m * A.nl + k] = 0.0;
   atomicOr(A.err + m, 1);
   return (T)0;
 }
@@ -202,7 +202,7 @@ __device__ __forceinline__ void point_zero(const RecArgs &A, long long k, int la
     A.sb2[lane * A.nl + k] = 0.0;
     static_cast<T *>(A.q)[k * M + lane] = (T)0;
   }
-  if (lane == 0 && A.qout) A.qout[k] = 0.0;
+  if (lane < M && A.qout) A.qout[lane * A.nl + k] = 0.0;
 }
 
 // Levels below kRecBL: the whole canonical pair sum of the point (one warp),
@@ -490,6 +490,19 @@ template <>
 struct PlaneLd<double, 1> {
   static __device__ __forceinline__ void smem(const double *p, double (&v)[1]) { v[0] = *p; }
   static __device__ __forceinline__ void gmem(const double *p, double (&v)[1]) { v[0] = __ldcg(p); }
+};
+template <>
+struct PlaneLd<double, 3> {
+  static __device__ __forceinline__ void smem(const double *p, double (&v)[3]) {
+    v[0] = p[0];
+    v[1] = p[1];
+    v[2] = p[2];
+  }
+  static __device__ __forceinline__ void gmem(const double *p, double (&v)[3]) {
+    v[0] = __ldcg(p);
+    v[1] = __ldcg(p + 1);
+    v[2] = __ldcg(p + 2);
+  }
 };
 
 // One fringe pair {l, k - l}, l = (lk, lw): the partner p = k - l on level
@@ -863,7 +876,8 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
 // (b_p^2 = eps^2 g^2 dk dw q_i q_j for |B| = eps g sqrt(S_i S_j S_k)).  Each
 // point's sums are formed by one warp at a time in a fixed order, so the
 // result does not depend on scheduling.  T = double, M = 1 is the exact
-// pass; T = float, M = 8 evaluates eight eps values at once to locate eps.
+// pass, M = 3 the same at three eps values (the last pass of FP64 plans);
+// T = float, M = 8 evaluates eight eps values at once to locate eps.
 // SEP: the envelope is separable on i + j = k (g^2 = a_i^2 a_j^2 b_k^2), q
 // holds h = a^2 q and the pair terms are h_i h_j (no g^2 read).
 template <typename T, int M, bool SEP>

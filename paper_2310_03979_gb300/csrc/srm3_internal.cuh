@@ -123,6 +123,8 @@ struct srm3_plan {
   double *dsb2 = nullptr;         // d sum_b2 / dx per point from two FP32 search planes
   double *red_part = nullptr;     // per-CTA partials of the plane reduction
   bool eps_shifted = false;       // the final tables are an FP64 pass moved to eps to first order
+  bool eps_interp = false;        // ... or interpolated to eps from an FP64 pass at three eps values
+  double *qo3 = nullptr;          // q of the three-plane FP64 pass, separable form ([3][nl])
   // eps search from the root on a coarser lattice (every coarse_fk-th kappa,
   // coarse_fw-th omega point): its kernels, passes and time; coarse_start
   // when one pass on this lattice then bracketed the root

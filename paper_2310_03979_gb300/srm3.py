@@ -81,7 +81,7 @@ class srm3_grid(ctypes.Structure):
 
 # srm3_info.recursion_flags
 SRM3_REC_SEPARABLE, SRM3_REC_TABLES_MOVED, SRM3_PAIRSUM_SEPARABLE = 1, 2, 4
-SRM3_REC_COARSE_START = 8
+SRM3_REC_COARSE_START, SRM3_REC_TABLES_INTERPOLATED = 8, 16
 
 
 class srm3_info(ctypes.Structure):

@@ -69,12 +69,13 @@ def test_plan_tables_and_eps(oracle_lib, precision):
     assert np.all(q >= 1.0) and info.min_pure_ratio > 0
     # the Gaussian envelope (sigma_g = 0.25) runs the recursion in separable
     # form; FP32 plans take one FP64 pass and the first-order move of the
-    # tables to the root, FP64 plans exact passes to the end
+    # tables to the root, FP64 plans one FP64 pass at three values of eps^2
+    # around the FP32 root and the tables interpolated to the root
     assert info.recursion_flags & srm3.SRM3_REC_SEPARABLE
     moved = bool(info.recursion_flags & srm3.SRM3_REC_TABLES_MOVED)
-    assert moved == (precision == "fp32")
-    if moved:
-        assert info.root_passes == 1
+    interp = bool(info.recursion_flags & srm3.SRM3_REC_TABLES_INTERPOLATED)
+    assert moved == (precision == "fp32") and interp == (precision == "fp64")
+    assert info.root_passes == 1
 
 
 @pytest.mark.parametrize("sigma_g,separable", [(0.15, False), (0.35, True)])
@@ -93,6 +94,16 @@ def test_recursion_envelope_width(oracle_lib, sigma_g, separable):
         assert bool(p.info().recursion_flags & srm3.SRM3_REC_SEPARABLE) == separable
     np.testing.assert_allclose(q, op.q, rtol=2e-14)
     np.testing.assert_allclose(sb2, op.sum_b2, rtol=2e-14, atol=1e-16)
+    # the eps search of an FP64 plan: tables interpolated from the three-plane
+    # FP64 pass, in either form of the recursion
+    with srm3.Plan.create(wl, precision="fp64") as p:
+        _, q, sb2 = p.tables()
+        info = p.info()
+    assert info.recursion_flags & srm3.SRM3_REC_TABLES_INTERPOLATED
+    assert info.eps == pytest.approx(op.eps, rel=1e-11)
+    assert abs(info.max_sum_b2 - wl.target) <= 1e-13
+    np.testing.assert_allclose(q, op.q, rtol=1e-11)
+    np.testing.assert_allclose(sb2, op.sum_b2, rtol=1e-11, atol=1e-16)
     with srm3.Plan.create(wl, precision="fp32") as p:
         _, q, sb2 = p.tables()
         info = p.info()
