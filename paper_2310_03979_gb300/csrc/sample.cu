@@ -393,26 +393,15 @@ static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
 }
 
 int run_pairsum(srm3_plan *p, int n, void *C_out) {
-  const int SS = 2 * n, sp = sspad_for(n);
   if (p->sep) return conv_pairsum_on(p, p->stream, n, p->y, p->y0, C_out);
-  if (p->precision == SRM3_FP64) {
-    const long long threads = (long long)p->nk * p->nw * sp;
-    k_pairsum_f64<<<cdiv(threads, 256), 256, 0, p->stream>>>(
-        p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
-        (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
-        (const double *)p->ck, std::cos(p->beta), std::sin(p->beta), (double2 *)C_out,
-      p->mixed ? 1 : 0, p->row_lo, p->row_hi);
-  } else {
-    PsDesc d;
-    int rc = fill_pairsum_desc(p, n, C_out, &d);
-    if (rc) return rc;
-    rc = launch_pairsum_f32(p, p->stream, d, nullptr, nullptr,
-                            p->nsuper[tile_index(p->ps_nc)] * d.G, 0, d.half != 0, p->ps_nc);
-    if (rc || !p->mixed) return rc;
-    return launch_pairsum_f32_diff(p, p->stream, n, C_out);
-  }
-  SRM3_CUDA(cudaGetLastError());
-  return SRM3_OK;
+  if (p->precision == SRM3_FP64) return pairsum_f64_on(p, p->stream, n, C_out);
+  PsDesc d;
+  int rc = fill_pairsum_desc(p, n, C_out, &d);
+  if (rc) return rc;
+  rc = launch_pairsum_f32(p, p->stream, d, nullptr, nullptr,
+                          p->nsuper[tile_index(p->ps_nc)] * d.G, 0, d.half != 0, p->ps_nc);
+  if (rc || !p->mixed) return rc;
+  return launch_pairsum_f32_diff(p, p->stream, n, C_out);
 }
 
 int run_transform(srm3_plan *p, const void *C, int n, void *out) {
