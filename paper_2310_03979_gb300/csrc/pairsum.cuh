@@ -419,7 +419,12 @@ __device__ __forceinline__ void ps_chunk(const float4 *__restrict__ pa,
 // sorted by decreasing cost).  MIXED = false compiles the full-group path
 // alone (every descriptor has half = 0); MIXED = true also takes half-mode
 // descriptors.
-template <bool MIXED, int NCW>
+// FORM: kPsSeparable when every descriptor of the launch has W recomputed in
+// separable form (the kernel holds those register blocks alone), else
+// kPsAnyForm (each descriptor's form decided at run time).
+constexpr int kPsAnyForm = 0, kPsSeparable = 2;
+
+template <bool MIXED, int NCW, int FORM = kPsAnyForm>
 __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CTAS_PER_SM)
     k_pairsum_f32p(const __grid_constant__ PsDesc d0, const PsDesc *__restrict__ descs,
                    const int4 *__restrict__ units, int nunits, int *__restrict__ err) {
@@ -456,7 +461,9 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
       const PsDesc &d = descs ? descs[un.x] : d0;
       const int kk = un.y, kws0 = un.z, nch = (kws0 + SW + CH - 1) / CH;
       const int half = MIXED ? d.half : 0;
-      const int nitems = ps_nitems(kk, kws0, half, SW), tab = d.table, rs = d.rowstride;
+      const int nitems = ps_nitems(kk, kws0, half, SW), rs = d.rowstride;
+      const bool tab = FORM == kPsAnyForm && d.table != 0;
+      const bool sepf = FORM == kPsSeparable || d.sep != 0;
       const int x = un.w * LANES * 4;  // first float of the group in a row of y
       int a = 0, c = 0;
       for (int item = 0; item < nitems; ++item, ++q) {
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
             }
           const unsigned tx = YROWS * ROW_BYTES +
                               (tab ? ntile * R * CH * (unsigned)sizeof(float)
-                                   : (d.sep ? 0u : EWIN * (unsigned)sizeof(float)));
+                                   : (sepf ? 0u : EWIN * (unsigned)sizeof(float)));
           mbar_expect_tx(&full[stage], tx);
           // one row pair (full rows), or two in half mode (half rows each; a
           // second row pair past the centre repeats the first and is
@@ -494,7 +501,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
                           &full[stage]);
           }
           if (!tab) {
-            if (!d.sep)
+            if (!sepf)
               bulk_g2s(sw + stage * STAGE_W, d.Ew + d.ew_off + 2 * i0 - kws0 - (SW - 1),
                        EWIN * sizeof(float), &full[stage]);
           } else {
@@ -534,7 +541,9 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
     if (u >= nunits) break;
     const int4 un = ps_get_unit(u, d0, units);
     const PsDesc &d = descs ? descs[un.x] : d0;
-    const int kk = un.y, kws0 = un.z, grp = un.w, nw = d.nw, tab = d.table;
+    const int kk = un.y, kws0 = un.z, grp = un.w, nw = d.nw;
+    const bool tab = FORM == kPsAnyForm && d.table != 0;
+    const bool sepf = FORM == kPsSeparable || d.sep != 0;
     const int kw0 = kws0 + R * warp, nch = (kws0 + SW + CH - 1) / CH;
     const int half = MIXED ? d.half : 0;
     const int nitems = ps_nitems(kk, kws0, half, SW);
@@ -562,7 +571,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
         if (half) {
           const float4 *pa = sy + stage * STAGE_Y + hl * YROWS * (LANES / 2) + ln;
           const float4 *pb = pa + (CH + R * warp + CH - U) * (LANES / 2);
-          if (d.sep)
+          if (sepf)
             ps_chunk<false, LANES / 2, true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
           else
             ps_chunk<false, LANES / 2>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
@@ -571,7 +580,7 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
           const float4 *pb = pa + (CH + R * warp + CH - U) * LANES;
           if (tab)
             ps_chunk<true, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
-          else if (d.sep)
+          else if (sepf)
             ps_chunk<false, LANES, true>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
           else
             ps_chunk<false, LANES>(pa, pb, pw, pe, i0, kw0, Txp, Txm, Ty);
@@ -588,8 +597,11 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
         const int b = kk - (live ? ah : a);
         // the row pair's kappa weight: none for the table (in W), the
         // envelope at kk - 2a, or in separable form aK[a] aK[kk - a]
+        // (the merge and the epilogue round every operation explicitly, so
+        // that the kernel compiled for one weight form gives the bits of the
+        // general one: a sample's result does not depend on the launch)
         auto rw = [&](int a_) {
-          return d.sep ? d.aK[a_] * d.aK[kk - a_] : d.Ek[kk - 2 * a_];
+          return sepf ? __fmul_rn(d.aK[a_], d.aK[kk - a_]) : d.Ek[kk - 2 * a_];
         };
         const float rowfac = tab ? 1.0f : (live ? rw(ah) : 0.0f);
         const bool odd_live = half && 2 * a + 1 <= kk / 2;
@@ -607,11 +619,14 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
                   tab ? d.W[my_base +
                             (((long long)ah * (my_L / CH) + ((kw >> 1) / CH)) * R + r) * CH +
                             ((kw >> 1) % CH)]
-                      : (d.sep ? 1.0f : d.Ew[d.ew_off]);
-              v[0] = 0.5f * (v[0] + w0 * (h.x * h.x - h.z * h.z));
-              v[1] = 0.5f * (v[1] + w0 * (h.y * h.y - h.w * h.w));
-              v[2] = 0.5f * (v[2] + w0 * (2.f * h.x * h.z));
-              v[3] = 0.5f * (v[3] + w0 * (2.f * h.y * h.w));
+                      : (sepf ? 1.0f : d.Ew[d.ew_off]);
+              const float t[4] = {__fsub_rn(__fmul_rn(h.x, h.x), __fmul_rn(h.z, h.z)),
+                                  __fsub_rn(__fmul_rn(h.y, h.y), __fmul_rn(h.w, h.w)),
+                                  __fmul_rn(__fmul_rn(2.f, h.x), h.z),
+                                  __fmul_rn(__fmul_rn(2.f, h.y), h.w)};
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                v[j] = __fmul_rn(0.5f, __fadd_rn(v[j], __fmul_rn(w0, t[j])));
             } else {
 #pragma unroll
               for (int j = 0; j < 4; ++j) v[j] *= 0.5f;
@@ -672,8 +687,8 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
         const float ar = kacc[(4 * r + h) * NCT] - kcmp[(4 * r + h) * NCT];
         const float ai = kacc[(4 * r + 2 + h) * NCT] - kcmp[(4 * r + 2 + h) * NCT];
         float2 out;
-        out.x = fmaf(P, yk.x, cf * (ar * d.cb - ai * d.sb));
-        out.y = fmaf(P, yk.y, cf * (ar * d.sb + ai * d.cb));
+        out.x = fmaf(P, yk.x, __fmul_rn(cf, __fsub_rn(__fmul_rn(ar, d.cb), __fmul_rn(ai, d.sb))));
+        out.y = fmaf(P, yk.y, __fmul_rn(cf, __fadd_rn(__fmul_rn(ar, d.sb), __fmul_rn(ai, d.cb))));
         d.C[((size_t)ss * d.nk + kk) * nw + kw] = out;
       }
     }

@@ -287,11 +287,14 @@ static int fill_pairsum_desc_into(srm3_plan *p, int n, void *y, void *y0, void *
 template <int NC>
 static int launch_pairsum_f32_nc(srm3_plan *p, cudaStream_t st, const PsDesc &d0,
                                  const PsDesc *descs, const int4 *units, int nunits, int max_ctas,
-                                 bool mixed) {
+                                 bool mixed, int form) {
   const size_t smem = pairsum_f32p_smem<NC>();
   constexpr int NT = packed::Shape<NC>::NT;
-  const void *kf[2] = {(const void *)k_pairsum_f32p<false, NC>,
-                       (const void *)k_pairsum_f32p<true, NC>};
+  // every instantiation: the general form and the separable form alone
+  const void *kf[4] = {(const void *)k_pairsum_f32p<false, NC>,
+                       (const void *)k_pairsum_f32p<true, NC>,
+                       (const void *)k_pairsum_f32p<false, NC, kPsSeparable>,
+                       (const void *)k_pairsum_f32p<true, NC, kPsSeparable>};
   for (const void *f : kf) {
     SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     SRM3_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -311,7 +314,13 @@ static int launch_pairsum_f32_nc(srm3_plan *p, cudaStream_t st, const PsDesc &d0
   int grid = std::min(nunits, ctas);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   if (grid == 0) return SRM3_OK;
-  if (mixed)
+  if (form == kPsSeparable && mixed)
+    k_pairsum_f32p<true, NC, kPsSeparable><<<grid, NT, smem, st>>>(d0, descs, units, nunits,
+                                                                   p->ps_err);
+  else if (form == kPsSeparable)
+    k_pairsum_f32p<false, NC, kPsSeparable><<<grid, NT, smem, st>>>(d0, descs, units, nunits,
+                                                                    p->ps_err);
+  else if (mixed)
     k_pairsum_f32p<true, NC><<<grid, NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
   else
     k_pairsum_f32p<false, NC><<<grid, NT, smem, st>>>(d0, descs, units, nunits, p->ps_err);
@@ -319,11 +328,25 @@ static int launch_pairsum_f32_nc(srm3_plan *p, cudaStream_t st, const PsDesc &d0
   return SRM3_OK;
 }
 
+// The instantiation for a descriptor's weight form: the separable form has
+// one of its own (its register blocks alone: 166 registers and no spills
+// against 168 and spills, 6 % faster on the bridge lattice); the stored
+// table and the weighted recompute form take the general kernel (compiled
+// for the table alone it spilled more and ran 0.3 % slower).
+static int ps_form_of(const PsDesc &d) {
+  return !d.table && d.sep ? kPsSeparable : kPsAnyForm;
+}
+
+// form: kPsSeparable when every descriptor of the launch has the separable
+// weight form, else kPsAnyForm; -1: that of d0 for a single-plan launch
+// (descs == NULL).
 int launch_pairsum_f32(srm3_plan *p, cudaStream_t st, const PsDesc &d0, const PsDesc *descs,
-                       const int4 *units, int nunits, int max_ctas, bool mixed, int nc) {
+                       const int4 *units, int nunits, int max_ctas, bool mixed, int nc,
+                       int form = -1) {
+  if (form < 0) form = descs ? kPsAnyForm : ps_form_of(d0);
   if (nc == 2)
-    return launch_pairsum_f32_nc<2>(p, st, d0, descs, units, nunits, max_ctas, mixed);
-  return launch_pairsum_f32_nc<4>(p, st, d0, descs, units, nunits, max_ctas, mixed);
+    return launch_pairsum_f32_nc<2>(p, st, d0, descs, units, nunits, max_ctas, mixed, form);
+  return launch_pairsum_f32_nc<4>(p, st, d0, descs, units, nunits, max_ctas, mixed, form);
 }
 
 // The difference-pair launch of a mixed FP32 plan over n samples whose rows
@@ -534,6 +557,7 @@ struct srm3_batch {
   int nunits = 0;                 // both shapes
   int nunits_v[2] = {0, 0};
   bool mixed_v[2] = {false, false};  // some descriptor of the shape takes the half-group mode
+  int ps_form = 0;                   // the weight form common to every descriptor (kPsAnyForm: none)
   srm3_plan *lead = nullptr;      // first FP32 plan: CTA count and error word of the launch
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -574,7 +598,8 @@ static int batch_launch(srm3_batch *b) {
     for (int v = 0, off = 0; v < 2; off += b->nunits_v[v], ++v)
       if (b->nunits_v[v] > 0 &&
           (rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits + off,
-                                   b->nunits_v[v], b->max_ctas, b->mixed_v[v], v == 0 ? 4 : 2)))
+                                   b->nunits_v[v], b->max_ctas, b->mixed_v[v], v == 0 ? 4 : 2,
+                                   b->ps_form)))
         return rc;
     if (b->timing) SRM3_CUDA(cudaEventRecordWithFlags(b->ps_ev[1], b->stream, evf));
   }
@@ -1004,6 +1029,9 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
   b->nunits = (int)u.size();
   if (!descs.empty()) {
     b->dev_bytes += (long long)(sizeof(PsDesc) * descs.size() + sizeof(int4) * u.size());
+    b->ps_form = ps_form_of(descs[0]);
+    for (const PsDesc &dd : descs)
+      if (ps_form_of(dd) != b->ps_form) b->ps_form = kPsAnyForm;
     e = cudaMallocAsync(&b->ddesc, sizeof(PsDesc) * descs.size(), b->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMallocAsync(batch descriptors)"));
     e = cudaMemcpyAsync(b->ddesc, descs.data(), sizeof(PsDesc) * descs.size(),
@@ -1020,7 +1048,7 @@ SRM3_API int srm3_batch_create(srm3_plan *const *plans, const int32_t *counts,
     std::memset(static_cast<void *>(&none), 0, sizeof(none));
     for (int v = 0; v < 2; ++v)
       if ((rc = launch_pairsum_f32(b->lead, b->stream, none, b->ddesc, b->dunits, 0, 0,
-                                   b->mixed_v[v], v == 0 ? 4 : 2)))
+                                   b->mixed_v[v], v == 0 ? 4 : 2, b->ps_form)))
         return bail(rc);
   }
   b->dev_bytes += (long long)(sizeof(uint64_t) * b->total);
