@@ -551,8 +551,6 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
     const int ln = half ? lane & 15 : lane;     // the lane's sample pair within the group
     const size_t SP = (size_t)d.SSpad / 2;  // float4 per lattice entry
     const bool tile_ok = kw0 < nw;
-    const int my_L = ((kw0 + R + kTileU - 1) / kTileU) * kTileU;
-    const long long my_base = (tab && tile_ok) ? d.toff[kk * d.ntw + kw0 / R] : -1;
 #pragma unroll
     for (int j = 0; j < NK; ++j) kacc[j * NCT] = kcmp[j * NCT] = 0.f;
     f32x2 Txp[R], Txm[R], Ty[R];
@@ -615,8 +613,11 @@ __global__ void __launch_bounds__(packed::Shape<NCW>::NT, packed::Shape<NCW>::CT
             if ((kw & 1) == 0 && kw < nw) {
               const float4 h = d.y[((size_t)ah * d.rowstride + kPad + (kw >> 1)) * SP +
                                    (size_t)grp * LANES + ln];
+              // the tile's offset in the table and its padded row length,
+              // formed here (once per unit) rather than kept across the chunks
+              const int my_L = ((kw0 + R + kTileU - 1) / kTileU) * kTileU;
               const float w0 =
-                  tab ? d.W[my_base +
+                  tab ? d.W[d.toff[kk * d.ntw + kw0 / R] +
                             (((long long)ah * (my_L / CH) + ((kw >> 1) / CH)) * R + r) * CH +
                             ((kw >> 1) % CH)]
                       : (sepf ? 1.0f : d.Ew[d.ew_off]);
