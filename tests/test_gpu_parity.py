@@ -147,6 +147,25 @@ def test_eps_search_coarse_start(mask):
         assert i32.coarse_passes == 0  # the coarse linear bound found no pairs
 
 
+@pytest.mark.parametrize("nk,nw,fk,fw", [(300, 260, 4, 4), (1100, 60, 16, 1)])
+def test_eps_search_coarse_start_ragged(nk, nw, fk, fw):
+    """Lattices that the coarse factors do not divide (the coarse lattice takes
+    points 0, fk, 2 fk, ... below n_kappa), and one coarsened along kappa
+    alone: the FP32 plan meets the target to 1e-9 and agrees with the FP64
+    plan to 2e-8."""
+    pow2 = lambda n: 1 << max(1, (2 * n - 1).bit_length())  # noqa: E731
+    wl = W.small_case(nk=nk, nw=nw, nx=pow2(nk), nt=pow2(nw), seeds=(1,))
+    res = {}
+    for precision in ("fp64", "fp32"):
+        with srm3.Plan.create(wl, precision=precision) as p:
+            res[precision] = p.info()
+    for info in res.values():
+        assert (info.coarse_fk, info.coarse_fw) == (fk, fw)
+    assert abs(res["fp64"].max_sum_b2 - wl.target) <= 1e-13
+    assert abs(res["fp32"].max_sum_b2 - wl.target) <= 1e-9
+    assert res["fp32"].eps == pytest.approx(res["fp64"].eps, rel=2e-8)
+
+
 @pytest.mark.parametrize("nk,nw", [(40, 33), (96, 64), (130, 20), (12, 200)])
 def test_recursion_at_fixed_eps(oracle_lib, nk, nw):
     """Same eps on both sides: the anti-diagonal recursion equals the
