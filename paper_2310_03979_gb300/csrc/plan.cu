@@ -623,6 +623,8 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
 
 // One recursion pass at x_m = eps_m^2 for m < M planes: the FP64 pass
 // (M = 1, writes qm) or the FP32 search pass (M = kPlanes, writes qm32).
+static int start_w_table(srm3_plan *p, cudaStream_t st);
+
 static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M, bool fp64,
                           PassResult *r) {
   for (int m = 0; m < M; ++m) p->h_pinned[m] = x[m] * p->dkdw;
@@ -680,6 +682,10 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
                                         args, smem, st));
   SRM3_CUDA(cudaGetLastError());
   p->n_launch += 1;
+  if (fp64 && p->w_deferred) {  // the W table, on the room the pass leaves
+    p->w_deferred = false;
+    if (int rcw = start_w_table(p, p->w_stream)) return rcw;
+  }
   SRM3_CUDA(cudaEventRecord(t_ev[1], st));
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + 8, p->rec_max, M * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st));
@@ -1710,7 +1716,11 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
       SRM3_CUDA(cudaEventRecord(ready, st));  // envelope tables and tile offsets written
       SRM3_CUDA(cudaStreamWaitEvent(wst, ready, 0));
       cudaEventDestroy(ready);
-      if ((rc = start_w_table(p, wst))) return rc;
+      // launched beside the first FP64 recursion pass (run_pass_multi): that
+      // pass leaves room on every SM (one CTA of 512 threads at 94
+      // registers), the FP32 passes and the kernels before them do not
+      p->w_stream = wst;
+      p->w_deferred = true;
     } else {
       p->table_bytes = 0.0;
     }
@@ -1764,19 +1774,25 @@ int build_plan(srm3_plan *p, const srm3_spectrum *sp, const srm3_bispectrum *bs)
     p->variance = 4.0 * p->dkdw * r.sumS;
   }
 
-  // pair count
+  if (p->w_deferred) {  // no FP64 pass ran: the W table now
+    p->w_deferred = false;
+    if ((rc = start_w_table(p, wst))) return rc;
+  }
+  // pair count: point (kk, kw) has floor(((kk + 1)(kw + 1) - 1) / 2) unordered
+  // pairs (i, j != 0); per row, with c = kk + 1 and T = nw (nw + 1) / 2, the sum
+  // over kw is (c T - nw - e) / 2, e the number of even c (kw + 1): nw for
+  // even c, floor(nw / 2) for odd c
   long long pairs = 0;  // of the plan's rows
-  for (int kk = p->row_lo; kk < p->row_hi; ++kk)
-    for (int kw = 0; kw < nw; ++kw) {
-      if (kk == 0 && kw == 0) continue;
-      long long m = (long long)(kk + 1) * (kw + 1) - 2;
-      pairs += (m + 1) / 2;
-    }
+  const long long T = (long long)nw * (nw + 1) / 2;
+  for (int kk = p->row_lo; kk < p->row_hi; ++kk) {
+    const long long c = kk + 1, e = (c % 2 == 0) ? nw : nw / 2;
+    pairs += (c * T - nw - e) / 2;
+  }
   p->pairs = pairs;
-  long long dpairs = 0;  // difference pairs of one sheet
+  long long dpairs = 0;  // difference pairs of one sheet: (kk + 1) (nw - 1 - kw), kw >= 1
   if (p->mixed)
     for (int kk = p->row_lo; kk < p->row_hi; ++kk)
-      for (int kw = 1; kw < nw; ++kw) dpairs += (long long)(kk + 1) * (nw - 1 - kw);
+      dpairs += (long long)(kk + 1) * ((long long)(nw - 1) * (nw - 2) / 2);
   p->diffpairs = dpairs;
 
   rc = prepare_sampling_tables(p, st);

@@ -196,6 +196,10 @@ struct srm3_plan {
   long long *tile_off = nullptr;  // W-table offset per tile id (kk*ntw + tw)
   float *W = nullptr;             // W table (STORAGE_TABLE): the pair envelopes of the shape
   cudaEvent_t w_ev[2] = {nullptr, nullptr};  // around its build while it runs
+  // the W build's stream during plan creation, and whether the build is still
+  // to be launched (it starts right after the first FP64 recursion pass, beside it)
+  cudaStream_t w_stream = nullptr;
+  bool w_deferred = false;
 
   // sampling workspace
   int ws_chunk = 0;
