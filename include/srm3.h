@@ -124,7 +124,7 @@ typedef struct srm3_bispectrum {
 
 enum srm3_precision {
     SRM3_FP32 = 0, /* tiled FP32 pair sum with compensated merge, FP32 FFT */
-    SRM3_FP64 = 1  /* plain FP64 pair sum (one thread per k), FP64 FFT */
+    SRM3_FP64 = 1  /* plain FP64 pair sum (one warp per k and sheet-sample), FP64 FFT */
 };
 enum srm3_storage {
     SRM3_STORAGE_AUTO = 0,     /* table if it fits the budget, else recompute */

@@ -10,69 +10,69 @@
 namespace srm3 {
 
 // ---------------------------------------------------------------------------
-// a4 + a5, plain FP64 form: one thread per (k, sheet-sample), exact
-// canonical half (centre row iw <= kw/2), W_ij = c_k Ek[|ik-jk|] Ew[iw-jw]
-// rebuilt per pair:
-//   A = sum_a Ek[kk-2a] sum_iw Ew[2iw-kw] y(a,iw) y(kk-a,kw-iw)
+// a4 + a5, plain FP64 form: one warp per (k, sheet-sample), exact canonical
+// half (centre row iw <= kw/2), W_ij = c_k Ek[|ik-jk|] Ew[iw-jw] rebuilt per
+// pair:
+//   A = sum_a sum_iw Ek[kk-2a] Ew[2iw-kw] y(a,iw) y(kk-a,kw-iw)
 //   C = P_k y_k + c_k e^{i beta} A
+// The point's terms are laid end to end (row pairs a <= kk/2 of kw + 1 terms,
+// the centre row to kw/2), lane l taking terms l, l + 32, ...; a fixed
+// butterfly adds the lanes' sums.  A warp per (k, sheet-sample) keeps every
+// lane of the narrow FP64 pipe busy however few samples share a launch, and
+// the order of every sum is the same for any launch.
 // Mixed plans (mixed != 0) add the difference pairs: i = (a, kw + jw) on this
 // sheet-sample's sheet and j = (kk - a, jw) on the other sheet of the same
 // sample (sheet-sample ss ^ 1), 0 <= a <= kk, 1 <= jw <= nw - 1 - kw, kw >= 1,
-// W = c_k Ek[|2a - kk|] Ew[kw + 2 jw] (the signed frequency difference).
+// W = c_k Ek[|2a - kk|] Ew[kw + 2 jw] (the signed frequency difference), laid
+// out after the sum pairs in the same way.
 __global__ void __launch_bounds__(256) k_pairsum_f64(
     int nk, int nw, int SS, int SSpad, int rowstride, const double2 *__restrict__ y,
     const double2 *__restrict__ y0, const double *__restrict__ Ek,
     const double *__restrict__ Ews, int ew_off, const double *__restrict__ Pk,
     const double *__restrict__ ck, double cb, double sb, double2 *__restrict__ C,
     int mixed, int row_lo, int row_hi) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int ss = (int)(gid % SSpad);
-  const long long k = gid / SSpad;
-  if (k >= (long long)nk * nw || ss >= SS) return;
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long nl = (long long)nk * nw;
+  if (gw >= nl * SS) return;  // uniform over the warp
+  const long long k = gw / SS;
+  const int ss = (int)(gw - k * SS);
   const int kk = (int)(k / nw), kw = (int)(k - (long long)kk * nw);
   if (kk < row_lo || kk >= row_hi) return;  // rows of another shard
   const double2 *yl = y + ss;
   double ar = 0.0, ai = 0.0;
-  for (int a = 0; a <= kk / 2; ++a) {
-    const int b = kk - a;
-    const int lim = (a == b) ? kw / 2 : kw;
-    const double2 *pa = yl + (size_t)(a * rowstride + kPad) * SSpad;
-    const double2 *pb = yl + (size_t)(b * rowstride + kPad + kw) * SSpad;
-    double rr = 0.0, ri = 0.0;
-    for (int iw = 0; iw <= lim; ++iw) {
-      double2 u = pa[(size_t)iw * SSpad];
-      double2 v = pb[-(long long)iw * SSpad];
-      double w = Ews[ew_off + 2 * iw - kw];
-      double pr = u.x * v.x - u.y * v.y;
-      double pi = u.x * v.y + u.y * v.x;
-      rr = fma(w, pr, rr);
-      ri = fma(w, pi, ri);
-    }
-    double f = Ek[kk - 2 * a];
-    ar = fma(f, rr, ar);
-    ai = fma(f, ri, ai);
+  const int W = kw + 1, E = (kk / 2 + 1) * W;
+  for (int e = lane; e < E; e += 32) {
+    const int a = e / W, iw = e - a * W, b = kk - a;
+    if (iw > ((a == b) ? kw / 2 : kw)) continue;
+    const double2 u = yl[(size_t)(a * rowstride + kPad + iw) * SSpad];
+    const double2 v = yl[(size_t)(b * rowstride + kPad + kw - iw) * SSpad];
+    const double w = Ek[kk - 2 * a] * Ews[ew_off + 2 * iw - kw];
+    const double pr = u.x * v.x - u.y * v.y;
+    const double pi = u.x * v.y + u.y * v.x;
+    ar = fma(w, pr, ar);
+    ai = fma(w, pi, ai);
   }
-  if (mixed && kw >= 1) {
+  if (mixed && kw >= 1 && kw < nw - 1) {
     const double2 *yo = y + (ss ^ 1);  // the other sheet of the same sample
-    for (int a = 0; a <= kk; ++a) {
-      const double2 *pa = yl + (size_t)(a * rowstride + kPad + kw) * SSpad;
-      const double2 *pb = yo + (size_t)((kk - a) * rowstride + kPad) * SSpad;
-      double rr = 0.0, ri = 0.0;
-      for (int jw = 1; jw <= nw - 1 - kw; ++jw) {
-        double2 u = pa[(size_t)jw * SSpad];
-        double2 v = pb[(size_t)jw * SSpad];
-        double w = Ews[ew_off + kw + 2 * jw];
-        double pr = u.x * v.x - u.y * v.y;
-        double pi = u.x * v.y + u.y * v.x;
-        rr = fma(w, pr, rr);
-        ri = fma(w, pi, ri);
-      }
+    const int L = nw - 1 - kw, E2 = (kk + 1) * L;
+    for (int e = lane; e < E2; e += 32) {
+      const int a = e / L, jw = 1 + e - a * L;
+      const double2 u = yl[(size_t)(a * rowstride + kPad + kw + jw) * SSpad];
+      const double2 v = yo[(size_t)((kk - a) * rowstride + kPad + jw) * SSpad];
       const int dk = 2 * a - kk;
-      double f = Ek[dk < 0 ? -dk : dk];
-      ar = fma(f, rr, ar);
-      ai = fma(f, ri, ai);
+      const double w = Ek[dk < 0 ? -dk : dk] * Ews[ew_off + kw + 2 * jw];
+      const double pr = u.x * v.x - u.y * v.y;
+      const double pi = u.x * v.y + u.y * v.x;
+      ar = fma(w, pr, ar);
+      ai = fma(w, pi, ai);
     }
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+  }
+  if (lane != 0) return;
   double2 yk = (k == 0) ? y0[ss] : yl[((size_t)kk * rowstride + kPad + kw) * SSpad];
   double c = ck[k], P = Pk[k];
   double pr = c * (ar * cb - ai * sb), pim = c * (ar * sb + ai * cb);

@@ -405,7 +405,7 @@ static int launch_pairsum_f32_diff(srm3_plan *p, cudaStream_t st, int n, void *C
 
 static int pairsum_f64_on(srm3_plan *p, cudaStream_t st, int n, void *C_out) {
   const int SS = 2 * n, sp = sspad_for(n);
-  const long long threads = (long long)p->nk * p->nw * sp;
+  const long long threads = (long long)p->nk * p->nw * SS * 32;  // a warp per (k, sheet-sample)
   k_pairsum_f64<<<cdiv(threads, 256), 256, 0, st>>>(
       p->nk, p->nw, SS, sp, p->rowstride, (const double2 *)p->y, (const double2 *)p->y0,
       (const double *)p->Ek, (const double *)p->Ews, p->ew_off, (const double *)p->Pk,
