@@ -36,7 +36,7 @@ METRIC = "3rd-order SRM wave pair-terms/s & samples/s at stated error; p50/p99 l
 # super-tile), reads scaled by the W table size (x 15.41), writes by the
 # coefficient count (x 4).  Valid only for the kernel source it was measured
 # on (sha256 prefix of csrc/pairsum.cuh); otherwise reported as null.
-PAIRSUM_TRAFFIC = {"bytes": 664.72e6 * 15.41 + 31.31e6 * 4, "source_sha256": "21a8a8b904d94459"}
+PAIRSUM_TRAFFIC = {"bytes": 664.46e6 * 15.41 + 31.16e6 * 4, "source_sha256": "4c3a66e484486035"}
 FP32_LANES_PER_SM = 128
 
 
