@@ -451,8 +451,12 @@ static void pinned_put(void *p) {
 // offset tables: the lattice points in level order (level d holds kk = lo
 // .. hi, lo = max(0, d - nw + 1), hi = min(d, nk - 1)), and for bulk phase
 // ph the points of its band of levels [D, min(2D, nlev)), D = ph BL, as
-// pairs (kk, kw), (kk, kw + 2 ...) along each lattice row: row kk of phase
-// ph holds kw = lo(kk), lo(kk) + 2, ... <= hi(kk), from entry seg[ph nk + kk].
+// pairs (kk, kw), (kk, kw + 1) along each lattice row: row kk of phase ph
+// holds the pairs starting at kw = lo(kk), lo(kk) + 2, ... <= hi(kk).  A
+// phase lists first, row by row, the pairs whose first point lies below
+// level D + BL (the points of the fringe block that follows the phase),
+// from entry seg[2 (ph - 1) nk + kk], then the others, from entry
+// seg[(2 (ph - 1) + 1) nk + kk].
 __global__ void k_level_points(int nk, int nw, int nlev, const int *__restrict__ lev_off,
                                int2 *__restrict__ pts) {
   const int d = blockIdx.x;
@@ -467,9 +471,11 @@ __global__ void k_bulk_pairs(int nk, int nw, int nlev, const int *__restrict__ s
   const int ph = 1 + blockIdx.y, kk = blockIdx.x;
   const int D = ph * kRecBL, dend = min(2 * D, nlev);
   const int lo = max(0, D - kk), hi = min(nw - 1, dend - 1 - kk);
-  const int base = seg[(ph - 1) * nk + kk];
+  const int hu = min(hi, D + kRecBL - 1 - kk);  // last first point of the fringe block
+  const int nu = hu >= lo ? (hu - lo) / 2 + 1 : 0;
+  const int bu = seg[2 * (ph - 1) * nk + kk], bd = seg[(2 * (ph - 1) + 1) * nk + kk];
   for (int j = threadIdx.x; lo + 2 * j <= hi; j += blockDim.x)
-    pairs[base + j] = make_int2(kk, lo + 2 * j);
+    pairs[j < nu ? bu + j : bd + j - nu] = make_int2(kk, lo + 2 * j);
 }
 
 // Resident-block counts of the recursion kernels per device (they depend on
@@ -536,18 +542,25 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   for (int d = 0; d < nlev; ++d)
     lev_off[d + 1] = lev_off[d] + std::min(d, nk - 1) - std::max(0, d - nw + 1) + 1;
   const int nph = std::max(0, (nlev - 1) / kRecBL);  // phases D = BL, 2 BL, ... < nlev
-  std::vector<int> seg((size_t)nph * nk + 1, 0);
-  std::vector<int> pair_off(nph + 1, 0);
+  std::vector<int> seg((size_t)2 * nph * nk + 1, 0);
+  // pair_off[0 .. nph]: first pair of each phase (and the end); then
+  // pair_off[nph + 1 + ph]: the first pair of phase ph past the fringe block
+  std::vector<int> pair_off(2 * (nph + 1), 0);
   for (int ph = 1; ph <= nph; ++ph) {
     const int D = ph * kRecBL, dend = std::min(2 * D, nlev);
-    for (int kk = 0; kk < nk; ++kk) {
-      const int lo = std::max(0, D - kk), hi = std::min(nw - 1, dend - 1 - kk);
-      const size_t i = (size_t)(ph - 1) * nk + kk;
-      seg[i + 1] = seg[i] + (hi >= lo ? (hi - lo) / 2 + 1 : 0);
-    }
-    pair_off[ph] = seg[(size_t)ph * nk];
+    for (int part = 0; part < 2; ++part)
+      for (int kk = 0; kk < nk; ++kk) {
+        const int lo = std::max(0, D - kk), hi = std::min(nw - 1, dend - 1 - kk);
+        const int hu = std::min(hi, D + kRecBL - 1 - kk);
+        const int nall = hi >= lo ? (hi - lo) / 2 + 1 : 0;
+        const int nu = hu >= lo ? (hu - lo) / 2 + 1 : 0;
+        const size_t i = (size_t)(2 * (ph - 1) + part) * nk + kk;
+        seg[i + 1] = seg[i] + (part == 0 ? nu : nall - nu);
+      }
+    pair_off[nph + 1 + ph] = seg[(size_t)(2 * (ph - 1) + 1) * nk];
+    pair_off[ph] = seg[(size_t)2 * ph * nk];
   }
-  const int npairs = std::max(1, seg[(size_t)nph * nk]);
+  const int npairs = std::max(1, seg[(size_t)2 * nph * nk]);
   int *d_seg = nullptr;
   SRM3_CUDA(dev_alloc(&p->rec_items, sizeof(int2) * lev_off[nlev], st));
   SRM3_CUDA(dev_alloc(&p->rec_lev_off, sizeof(int) * (nlev + 1), st));
@@ -602,9 +615,10 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
   SRM3_CUDA(cudaMemcpyAsync(p->h_pinned + kSumSlot, p->scal + 11, sizeof(double),
                             cudaMemcpyDeviceToHost, st));
   p->sumS = -1.0;  // not read yet
-  // barrier counter, a ticket per bulk phase, and the fringe progress of
-  // every lattice row
-  p->rec_bar_tickets = 2 + (nk + nw) / kRecBL + 1;
+  // barrier counter, two tickets per bulk phase (its points of the next
+  // fringe block, then the others), and the fringe progress of every
+  // lattice row
+  p->rec_bar_tickets = 2 + 2 * ((nk + nw) / kRecBL + 1);
   p->rec_bar_words = p->rec_bar_tickets + nk;
   SRM3_CUDA(dev_alloc(&p->rec_bar, p->rec_bar_words * sizeof(unsigned int), st));
   SRM3_CUDA(cudaMemsetAsync(p->rec_bar, 0, p->rec_bar_words * sizeof(unsigned int), st));
@@ -641,6 +655,8 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
   A.pt_off = p->rec_lev_off;
   A.pairs = p->rec_pairs;
   A.pair_off = p->rec_pair_off;
+  A.pair_mid = p->rec_pair_off + (A.nlev - 1) / kRecBL + 1;
+  A.tk_def = (p->nk + p->nw) / kRecBL + 1;
   A.S = p->S;
   if (fp64 && M != 1 && M != 3)
     return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes one or three planes");

@@ -20,9 +20,12 @@ struct RecArgs {
   const int *pt_off;    // first point of each level, nlev + 1 entries
   // bulk phase ph (D = ph BL) works on point pairs (kk, kw), (kk, kw + 1)
   // of its band of levels [D, min(2D, nlev)): starts pairs[pair_off[ph - 1]
-  // .. pair_off[ph])
+  // .. pair_off[ph]), those of the fringe block [D, D + BL) that follows
+  // the phase first (up to pair_mid[ph])
   const int2 *pairs;
   const int *pair_off;
+  const int *pair_mid;
+  int tk_def;           // bar[tk_def + ph]: ticket of the rest of bulk phase ph
   const double *S;
   void *q;              // [nl][M] of T: q = S/S_p (0 where S = 0), plane fastest
   void *acc;            // [nl][M] of T: pair sums gathered by the bulk phases
@@ -47,7 +50,7 @@ struct RecArgs {
   // iterate of the fixed point, added before q_k is formed (M = 1 only)
   const double *dsum;
   int *err;             // [M]: some S_p <= 0 on this plane
-  unsigned int *bar;    // [0] grid barrier arrivals, [1 + i] ticket of bulk phase i (zero at launch)
+  unsigned int *bar;    // [0] grid barrier arrivals, [i] and [tk_def + i] tickets of bulk phase i (zero at launch)
   unsigned int *row_done;  // [nk]: 1 + the last fringe level each lattice row has finished (zero at launch)
   int *abort;           // barrier wait timed out
   unsigned long long *maxb;  // [M]: max_k sum_b2 per plane, as the bits of a double >= 0
@@ -862,15 +865,44 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
   return grid_barrier(A.bar, A.abort, nb * g++);
 }
 
+// Bulk items [b, e) of phase D (point pairs of the FP32 search pass, else
+// points) drawn by whole warps from the ticket counter tk, the next ticket
+// drawn while the current item is summed.
+template <typename T, int M, bool SEP>
+__device__ __forceinline__ void bulk_items(const RecArgs &A, unsigned int *tk, int b, int e,
+                                           int D, int lane) {
+  constexpr bool kPairs = sizeof(T) == sizeof(float);
+  const int dend = min(2 * D, A.nlev);
+  int t = 0;
+  if (lane == 0) t = (int)atomicAdd(tk, 1u);
+  t = __shfl_sync(0xffffffffu, t, 0);
+  while (b + t < e) {
+    int tn = 0;
+    if (lane == 0) tn = (int)atomicAdd(tk, 1u);
+    if constexpr (kPairs) {
+      const int2 pt = A.pairs[b + t];
+      const bool has1 = pt.y + 1 <= min(A.nw - 1, dend - 1 - pt.x);
+      point2_bulk<T, M, SEP>(A, pt.x, pt.y, has1, D, lane);
+    } else {
+      const int2 pt = A.pts[b + t];
+      point_bulk<T, M, SEP>(A, pt.x, pt.y, D, lane);
+    }
+    t = __shfl_sync(0xffffffffu, tn, 0);
+  }
+}
+
 // One recursion pass.  Levels d = kk + kw: every part of a pair of Pi(k)
 // lies on a lower level.  Each pair {i, j} of a point is assigned to the
 // higher of its two levels, M(i, j) in [ceil(d/2), d).  The pass runs:
 //   levels 0 .. BL-1 directly, one grid barrier per level;
 //   then for D = BL, 2 BL, ...: a bulk phase adding every pair with
 //   M in [D - BL, D) to every point of levels [D, 2D) (M >= d/2 bounds the
-//   points that have any), one barrier, and for each level d of [D, D + BL)
-//   the fringe (pairs with M in [D, d)) and the finalisation of q, with a
-//   barrier after each level.
+//   points that have any) -- its points of levels [D, D + BL) first, then
+//   one barrier, then for each level d of [D, D + BL) the fringe (pairs with
+//   M in [D, d)) and the finalisation of q by the CTAs of the lattice's row
+//   groups while every other CTA adds the phase's pairs to the points of
+//   levels [D + BL, 2D) (which no fringe level of the block reads; the
+//   fringe CTAs join them when their rows are done), and a barrier.
 // Per plane m (one eps value each)
 //   sum_b2(k) = eps_m^2 dk dw sum_{Pi(k)} g^2 q_i q_j,  q_k = 1/(1 - sum_b2)
 // (b_p^2 = eps^2 g^2 dk dw q_i q_j for |B| = eps g sqrt(S_i S_j S_k)).  Each
@@ -918,36 +950,25 @@ __global__ void __launch_bounds__(kRecThreads, 1) k_rec_pass(RecArgs A) {
                              reinterpret_cast<typename Vec2<T>::type *>(rec_smem + kFringeSmem)))
         return;
     } else {
-      // bulk: warps take points in turn from the phase's ticket counter
-      // (the next ticket is drawn while the current point is summed)
+      // bulk: warps take items in turn from the phase's ticket counters
       // (the FP32 search pass, bound by its q loads, takes the points in
-      // pairs; the FP64 pass, bound by its FP64 pipe, one at a time)
+      // pairs; the FP64 pass, bound by its FP64 pipe, one at a time); the
+      // items of the fringe block [D, D + BL) before the barrier
       constexpr bool kPairs = sizeof(T) == sizeof(float);
       const int pb = kPairs ? A.pair_off[ph - 1] : A.pt_off[D];
-      const int pe = kPairs ? A.pair_off[ph] : A.pt_off[min(2 * D, A.nlev)];
-      const int dend = min(2 * D, A.nlev);
-      unsigned int *tk = A.bar + ph;
-      int t = 0;
-      if (lane == 0) t = (int)atomicAdd(tk, 1u);
-      t = __shfl_sync(0xffffffffu, t, 0);
-      while (pb + t < pe) {
-        int tn = 0;
-        if (lane == 0) tn = (int)atomicAdd(tk, 1u);
-        if constexpr (kPairs) {
-          const int2 pt = A.pairs[pb + t];
-          const bool has1 = pt.y + 1 <= min(A.nw - 1, dend - 1 - pt.x);
-          point2_bulk<T, M, SEP>(A, pt.x, pt.y, has1, D, lane);
-        } else {
-          const int2 pt = A.pts[pb + t];
-          point_bulk<T, M, SEP>(A, pt.x, pt.y, D, lane);
-        }
-        t = __shfl_sync(0xffffffffu, tn, 0);
-      }
+      const int pm = kPairs ? A.pair_mid[ph] : A.pt_off[min(D + kRecBL, A.nlev)];
+      bulk_items<T, M, SEP>(A, A.bar + ph, pb, pm, D, lane);
       if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
     }
     // fringe levels by lattice rows (a warp that gave up skips its remaining
     // points; the grid barrier after the block then fails for every CTA)
     fringe_rows<T, M, SEP>(A, F, D, s_done, lane);
+    if (!A.zr) {  // the rest of the bulk phase, beside the fringe
+      constexpr bool kPairs = sizeof(T) == sizeof(float);
+      const int pm = kPairs ? A.pair_mid[ph] : A.pt_off[min(D + kRecBL, A.nlev)];
+      const int pe = kPairs ? A.pair_off[ph] : A.pt_off[min(2 * D, A.nlev)];
+      bulk_items<T, M, SEP>(A, A.bar + A.tk_def + ph, pm, pe, D, lane);
+    }
     if (!grid_barrier(A.bar, A.abort, nb * g++)) return;
   }
 }
