@@ -867,7 +867,9 @@ __device__ bool sep_product(const RecArgs &A, int l0, int log2L, unsigned int &g
 
 // Bulk items [b, e) of phase D (point pairs of the FP32 search pass, else
 // points) drawn by whole warps from the ticket counter tk, the next ticket
-// drawn while the current item is summed.
+// drawn while the current item is summed.  Tickets run from the end of the
+// range: items of higher lattice rows (more row pairs, the longer ones) are
+// drawn first, so that the short ones fill the tail before the barrier.
 template <typename T, int M, bool SEP>
 __device__ __forceinline__ void bulk_items(const RecArgs &A, unsigned int *tk, int b, int e,
                                            int D, int lane) {
@@ -880,11 +882,11 @@ __device__ __forceinline__ void bulk_items(const RecArgs &A, unsigned int *tk, i
     int tn = 0;
     if (lane == 0) tn = (int)atomicAdd(tk, 1u);
     if constexpr (kPairs) {
-      const int2 pt = A.pairs[b + t];
+      const int2 pt = A.pairs[e - 1 - t];
       const bool has1 = pt.y + 1 <= min(A.nw - 1, dend - 1 - pt.x);
       point2_bulk<T, M, SEP>(A, pt.x, pt.y, has1, D, lane);
     } else {
-      const int2 pt = A.pts[b + t];
+      const int2 pt = A.pts[e - 1 - t];
       point_bulk<T, M, SEP>(A, pt.x, pt.y, D, lane);
     }
     t = __shfl_sync(0xffffffffu, tn, 0);
