@@ -406,6 +406,9 @@ struct PassResult {
 static thread_local cudaEvent_t t_ev[2] = {nullptr, nullptr};
 
 static constexpr int kPlanes = 8;  // eps values per FP32 search pass
+// eps values of the FP32 pass over the window around the coarse-lattice root
+// (plans without the FFT form of the separable bulk)
+static constexpr int kWindowPlanes = 4;
 // largest exponent range of the separable Gaussian factors (k_gauss_sep)
 static constexpr double kSepExpMax = 40.0;
 // targets at least this loose may take the first-order table shift of
@@ -492,6 +495,8 @@ static int rec_occupancy_of(RecOccupancy &o) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kPlanes, SEP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<float, kWindowPlanes, SEP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaFuncSetAttribute(k_rec_pass<double, 3, SEP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, k_rec_pass<double, 1, SEP>,
@@ -503,6 +508,10 @@ static int rec_occupancy_of(RecOccupancy &o) {
   b64f = b64;
   SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b32, k_rec_pass<float, kPlanes, SEP>,
                                                           kRecThreads, sm));
+  int b32w = 0;
+  SRM3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &b32w, k_rec_pass<float, kWindowPlanes, SEP>, kRecThreads, sm));
+  b32 = std::min(b32, b32w);
   b32f = b32;
   o.b64 = std::min(o.b64, b64);
   o.b64f = std::min(o.b64f, b64f);
@@ -636,7 +645,8 @@ static int setup_recursion(srm3_plan *p, cudaStream_t st) {
 }
 
 // One recursion pass at x_m = eps_m^2 for m < M planes: the FP64 pass
-// (M = 1, writes qm) or the FP32 search pass (M = kPlanes, writes qm32).
+// (M = 1, writes qm; M = 3 writes qm3) or the FP32 search pass (M = kPlanes,
+// or kWindowPlanes without the FFT form of the bulk; writes qm32).
 static int start_w_table(srm3_plan *p, cudaStream_t st);
 
 static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M, bool fp64,
@@ -662,6 +672,8 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
     return fail(SRM3_ERR_INVALID_ARG, "FP64 recursion pass takes one or three planes");
   if (fp64 && M == 3 && (p->rec_fft || p->mixed))
     return fail(SRM3_ERR_INVALID_ARG, "three-plane FP64 pass: direct bulk, sum pairs only");
+  if (!fp64 && M != kPlanes && (M != kWindowPlanes || p->rec_fft))
+    return fail(SRM3_ERR_INVALID_ARG, "FP32 recursion pass: 8 planes, or 4 with the direct bulk");
   const bool sepf = p->rec_sep;
   const bool x3 = fp64 && M == 3;
   if (x3 && sepf && !p->qo3) SRM3_CUDA(dev_alloc(&p->qo3, 3 * (size_t)p->nk * p->nw * sizeof(double), st));
@@ -692,6 +704,8 @@ static int run_pass_multi(srm3_plan *p, cudaStream_t st, const double *x, int M,
                  : (const void *)k_rec_pass<double, 3, false>)
       : fp64 ? (sepf ? (const void *)k_rec_pass<double, 1, true>
                      : (const void *)k_rec_pass<double, 1, false>)
+      : M == kWindowPlanes ? (sepf ? (const void *)k_rec_pass<float, kWindowPlanes, true>
+                                   : (const void *)k_rec_pass<float, kWindowPlanes, false>)
              : (sepf ? (const void *)k_rec_pass<float, kPlanes, true>
                      : (const void *)k_rec_pass<float, kPlanes, false>);
   SRM3_CUDA(cudaLaunchCooperativeKernel(kern, fp64 ? p->rec_grid64 : p->rec_grid32, kRecThreads,
@@ -975,6 +989,7 @@ static constexpr double kCoarseWindow = 0.015;
 
 struct Search32 {
   std::vector<std::pair<double, double>> pts;  // (x, f); f = +inf: failed pass
+  int np = kPlanes;       // planes of the last pass
   double xs[kPlanes];
   PassResult r[kPlanes];  // the last pass
   double x0 = -1.0;       // target / Lmax once the wide search has run
@@ -1051,6 +1066,7 @@ static int wide_search(srm3_plan *p, cudaStream_t st, double target, Search32 &s
   double zoom_c = 0.0, zoom_w = 0.0;  // centre and half-width of the next zoom
   for (int pass = 0; pass < 12; ++pass) {
     const double lo_pass = lo, hi_pass = hi;  // the range the planes below cover
+    s.np = kPlanes;
     for (int m = 0; m < kPlanes; ++m) {
       if (pass == 0)
         s.xs[m] = lo + (hi - lo) * m / (kPlanes - 1);
@@ -1274,11 +1290,15 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
     rc = coarse_root(p, st, target, &xc);
     if (rc) return rc;
     if (xc > 0.0) {
-      for (int m = 0; m < kPlanes; ++m)
-        s.xs[m] = xc * (1.0 + kCoarseWindow * (2.0 * m / (kPlanes - 1) - 1.0));
-      rc = run_pass_multi(p, st, s.xs, kPlanes, false, s.r);
+      // four planes over the window (its spacing of 1 % still leaves x32
+      // within ~1e-6 of the root, far inside the FP64 stage's reach), eight
+      // for the FFT form of the separable bulk, which keeps exact passes
+      s.np = p->rec_fft ? kPlanes : kWindowPlanes;
+      for (int m = 0; m < s.np; ++m)
+        s.xs[m] = xc * (1.0 + kCoarseWindow * (2.0 * m / (s.np - 1) - 1.0));
+      rc = run_pass_multi(p, st, s.xs, s.np, false, s.r);
       if (rc) return rc;
-      for (int m = 0; m < kPlanes; ++m)
+      for (int m = 0; m < s.np; ++m)
         s.pts.push_back({s.xs[m], s.r[m].err ? INFINITY : s.r[m].max_sb2 - target});
       std::sort(s.pts.begin(), s.pts.end());
       const size_t j = first_above(s);
@@ -1309,13 +1329,13 @@ static int find_eps(srm3_plan *p, cudaStream_t st, double target, double tol) {
   bool shift_ok = false;
   if (tol >= kShiftTol && !p->rec_fft && hi_ok && slope32 > 0.0) {
     int m = -1;
-    for (int i = 0; i + 1 < kPlanes && m < 0; ++i)
+    for (int i = 0; i + 1 < s.np && m < 0; ++i)
       if (s.xs[i] <= x32 && x32 <= s.xs[i + 1] && !s.r[i].err && !s.r[i + 1].err) m = i;
     if (m >= 0) {
       // the third plane: the nearer feasible neighbour of the pair
       int m3 = -1;
       const bool below = m >= 1 && !s.r[m - 1].err;
-      const bool above = m + 2 < kPlanes && !s.r[m + 2].err;
+      const bool above = m + 2 < s.np && !s.r[m + 2].err;
       if (below && above)
         m3 = (x32 - s.xs[m - 1] <= s.xs[m + 2] - x32) ? m - 1 : m + 2;
       else if (below)

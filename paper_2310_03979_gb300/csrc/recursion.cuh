@@ -124,6 +124,19 @@ struct PlaneVec<float, 8> {
   }
 };
 
+// Four FP32 planes (the window pass around the coarse-lattice root): one
+// 128-bit load.
+template <>
+struct PlaneVec<float, 4> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+};
+
 // One pair term g^2(i, j) q_i q_j added to acc (all planes).  SEP: the
 // pair factor is carried by h = a^2 q (g^2 = a_i^2 a_j^2 b_k^2), so the term
 // is h_i h_j and no g^2 is read.
@@ -487,6 +500,17 @@ struct PlaneLd<float, 8> {
     const float4 b = __ldcg(reinterpret_cast<const float4 *>(p) + 1);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <>
+struct PlaneLd<float, 4> {
+  static __device__ __forceinline__ void smem(const float *p, float (&v)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  static __device__ __forceinline__ void gmem(const float *p, float (&v)[4]) {
+    const float4 a = __ldcg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   }
 };
 template <>
