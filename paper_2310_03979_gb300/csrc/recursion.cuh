@@ -342,8 +342,13 @@ __device__ void point_bulk(const RecArgs &A, int kk, int kw, int D, int lane) {
 // (kk - a) + u).  Rows a run over the union of the two points' ranges, the
 // lanes of row parity rs taking every other row; each point keeps its own
 // limits (the sliver's u and row ranges, i != 0, the centre row, iw <= kw),
-// a masked slot reading point (0, 0) with weight 0.
-constexpr int kPairUnroll = 2;
+// a masked slot reading point (0, 0) with weight 0.  Rows in flight per
+// step: 4 with four planes (the eps-search window pass, room in its
+// registers), else 2.
+template <int M>
+__host__ __device__ constexpr int pair_unroll() {
+  return M == 4 ? 4 : 2;
+}
 
 template <bool RIGHT, typename T, int M, bool SEP>
 __device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__restrict__ G2,
@@ -351,6 +356,7 @@ __device__ __forceinline__ void bulk_rows2(int kk, int kw, int nw, const T *__re
                                            const int (&alo)[2], const int (&ahi)[2],
                                            const bool (&uok)[2], T (&acc0)[M], T (&acc1)[M]) {
   const int a_first = min(alo[0], alo[1]), a_last = max(ahi[0], ahi[1]);
+  constexpr int kPairUnroll = pair_unroll<M>();
   for (int a00 = a_first + rs; a00 <= a_last; a00 += 2 * kPairUnroll) {
     T g2[kPairUnroll][2], vh[kPairUnroll][M], vl[kPairUnroll][2][M];
 #pragma unroll
