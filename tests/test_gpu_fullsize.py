@@ -44,8 +44,11 @@ def test_bridge_plan_against_oracle():
     assert abs(info.max_sum_b2 - g["max_sum_b2"]) <= 1e-9
     # the eps search started from the root on the 64 x 64 lattice of every
     # fourth kappa and eighth omega point, bracketed by one FP32 pass here
+    # (four planes over the window around that root) and finished by one FP64
+    # pass with the tables moved to the root
     assert info.recursion_flags & srm3.SRM3_REC_COARSE_START
     assert (info.coarse_fk, info.coarse_fw) == (4, 8)
+    assert (info.root_passes_fp32, info.root_passes) == (1, 1)
     assert abs(info.variance - g["variance"]) <= 1e-12 * g["variance"]
     pts = [tuple(x) for x in g["points"]]
     qg, sg = np.array(g["q"]), np.array(g["sum_b2"])
